@@ -1,0 +1,201 @@
+/*
+ * polyline.h -- C ABI of the GB300 (sm_103a) hybrid 3-D reconstruction for
+ * mechanically scanned polyline arrays.
+ *
+ * Method: Wang, Li, Zhao, Sun, "Near-Field Millimeter-Wave Imaging via Arrays
+ * in the Shape of Polyline" (arXiv 2109.02842), Sec. II. Equation numbers are
+ * the paper's printed numbering: (1) monostatic echo, (2) FT over the scan
+ * axis, (5) monostatic dispersion, (7) time-domain inversion, (8a)/(8b)
+ * filtered back-projection with an inverse NUFFT, (9) inverse FFT over k_z,
+ * (10) multistatic echo, (18) multistatic dispersion, (19a)/(19b)
+ * multistatic filtered back-projection.
+ *
+ * Problem statement (Sec. II-A/B): array geometry (circle radius, section
+ * count, chord length, element positions), scan positions, frequency samples
+ * and complex echoes in; a complex 3-D image out.
+ *
+ * Conventions for every call:
+ *  - Every call returns a pl_status; nothing throws across the ABI. On an
+ *    error, pl_last_error() returns a message for the calling thread.
+ *  - Complex data are interleaved single precision (re, im) = 8 bytes, C order.
+ *  - "device" pointers are CUDA global-memory pointers on the current device
+ *    (e.g. a torch tensor's data_ptr()); "host" pointers are CPU memory.
+ *  - The caller owns echo and image buffers. A plan owns its workspace and
+ *    copies the geometry, scan, frequency and grid descriptions at creation.
+ *  - Streams are cudaStream_t values passed as void* (NULL = legacy default).
+ *  - A plan is not thread-safe: one execute at a time per plan.
+ *  - There is no CPU fallback: without a usable CUDA device every compute
+ *    call fails with PL_ERR_CUDA.
+ */
+#ifndef POLYLINE_H
+#define POLYLINE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PL_OK = 0,
+    PL_ERR_ARG = 1,          /* NULL pointer, bad size or bad option */
+    PL_ERR_GEOMETRY = 2,     /* element/pair indices or positions invalid */
+    PL_ERR_FREQ = 3,         /* frequencies not finite, positive, strictly ascending */
+    PL_ERR_EVANESCENT = 4,   /* every (k_z, f) term is evanescent */
+    PL_ERR_NONFINITE = 5,    /* NaN/Inf in an input description */
+    PL_ERR_CUDA = 6,         /* a CUDA runtime call or kernel failed */
+    PL_ERR_OOM = 7,          /* device allocation failed */
+    PL_ERR_TIMEOUT = 8,      /* a bounded device-side wait gave up */
+    PL_ERR_UNSUPPORTED = 9   /* valid request this build does not support */
+} pl_status;
+
+/* Array topology, Sec. II-A (monostatic) and II-B (multistatic), Fig. 1.
+ * mode 0: one channel per element, Tx = Rx at elem_xy[c]; echo model Eq. (1).
+ * mode 1: one channel per (Tx, Rx) pair, pair c uses elem_xy[pair_tx[c]] and
+ *         elem_xy[pair_rx[c]]; echo model Eq. (10). Pairs may be any subset
+ *         (the paper pairs within a section, Sec. III).
+ * radius, n_sections, chord_len describe the polyline (informational; the
+ * element positions are authoritative). All arrays are host memory and are
+ * copied by pl_plan_create. elem_section may be NULL. */
+typedef struct {
+    int mode;
+    double radius;
+    int n_sections;
+    double chord_len;
+    int n_elem;
+    const double *elem_xy;      /* host [n_elem][2], metres */
+    const int *elem_section;    /* host [n_elem] or NULL */
+    int n_pairs;                /* mode 1 only */
+    const int *pair_tx;         /* host [n_pairs], mode 1 only */
+    const int *pair_rx;         /* host [n_pairs], mode 1 only */
+} pl_geometry;
+
+/* Mechanical scan along z (Sec. II-A): z'_n = z0 + n*dz, n < n.
+ * n_pad: length N_p >= n of the zero-padded transform over z (Eq. 2);
+ * 0 selects n. The image is periodic in z with period N_p*dz. */
+typedef struct {
+    double z0;
+    double dz;
+    int n;
+    int n_pad;
+} pl_scan;
+
+/* Frequency samples f_m (Hz), finite, positive, strictly ascending. k_0 of
+ * Eq. (8a) is the wavenumber of f_hz[0]. Host memory, copied. */
+typedef struct {
+    const double *f_hz;
+    int n;
+} pl_freqs;
+
+/* Voxel centres x0 + i*dx (i < nx), y0 + j*dy, z0 + p*dz. The image is
+ * complex64 [nz][ny][nx]. When z0 = scan.z0 + q*scan.dz for an integer q,
+ * dz = scan.dz and q + nz <= N_p, the z inverse transform is an FFT;
+ * otherwise it is an explicit DFT onto the voxel heights (Eq. 9). */
+typedef struct {
+    double x0, dx;
+    double y0, dy;
+    double z0, dz;
+    int nx, ny, nz;
+} pl_grid;
+
+/* Numerical options. Zero-initialise and set what you need.
+ * precision: 0 = FP32 everywhere (default);
+ *            1 = range-profile table stored as BF16 pairs (FP32 accumulate).
+ * nufft_sigma: oversampling of the range-profile grid (default 2.0).
+ * nufft_w: interpolation taps (even, 4..12; default 6).
+ * tile_u: k_z bins per back-projection block (8 or 16; 0 = default 16). */
+typedef struct {
+    int precision;
+    double nufft_sigma;
+    int nufft_w;
+    int tile_u;
+    int reserved[8];
+} pl_options;
+
+typedef struct pl_plan pl_plan;
+
+/* Read-only description of a plan (sizes a caller may need). */
+typedef struct {
+    int mode, n_chan, n_scan, n_pad, n_f;
+    int nx, ny, nz;
+    int table_len;        /* L: rows of the range-profile table */
+    int fine_len;         /* n_f of the type-1 NUFFT grid */
+    int slab_rows;        /* R: table rows a back-projection block stages */
+    int nufft_w;
+    double nufft_sigma;
+    double table_h;       /* range step h of the table (m) */
+    double table_l0;      /* range of table row 0 (m) */
+    int z_transform_fft;  /* 1: z inverse transform is an FFT, 0: DFT */
+    int launches_per_execute;
+    size_t workspace_bytes;
+    double updates_per_execute;  /* n_chan * nx * ny * nz * n_f */
+} pl_info;
+
+/* Stage identifiers for timing and workspace access. */
+enum {
+    PL_STAGE_ZFFT = 0,        /* Eq. (2): transform over the scan axis */
+    PL_STAGE_RANGE_TABLE = 1, /* Eq. (8a)/(19a): compensation + NUFFT spread + fine FFT */
+    PL_STAGE_BACKPROJECT = 2, /* Eq. (8b)/(19b): interpolation + carrier + channel sum */
+    PL_STAGE_ZIFFT = 3,       /* Eq. (9): inverse transform over k_z */
+    PL_NUM_STAGES = 4
+};
+
+/* Create a plan: validates the inputs, allocates device workspace on the
+ * current device and precomputes the per-(k_z, f) tables on the GPU.
+ * opt may be NULL for defaults. On success *out is a new plan. */
+pl_status pl_plan_create(pl_plan **out, const pl_geometry *geom, const pl_scan *scan,
+                         const pl_freqs *freqs, const pl_grid *grid, const pl_options *opt);
+
+/* Reconstruct one scan. echo_dev: device complex64 [n_chan][n_scan][n_f]
+ * (channel-major, frequency fastest); image_dev: device complex64
+ * [nz][ny][nx]. Asynchronous on `stream`; the buffers must stay valid until
+ * the stream reaches the end of this call's work. */
+pl_status pl_execute(pl_plan *plan, const void *echo_dev, void *image_dev, void *stream);
+
+/* Same reconstruction from HOST buffers: copies the echo to the device,
+ * reconstructs, copies the image back and synchronises `stream` before
+ * returning. Pinned host memory gives the fastest copies. */
+pl_status pl_execute_host(pl_plan *plan, const void *echo_host, void *image_host,
+                          void *stream);
+
+pl_status pl_plan_destroy(pl_plan *plan);
+pl_status pl_plan_get_info(const pl_plan *plan, pl_info *info);
+
+/* Device pointer and size of an intermediate buffer, valid until the plan is
+ * destroyed (for inspection and tests):
+ *  PL_STAGE_ZFFT        -> spectrum S, complex64 [n_chan][n_pad][n_f]
+ *  PL_STAGE_RANGE_TABLE -> table b, complex64 (or bf16 pairs) [n_chan][L][n_pad]
+ *  PL_STAGE_BACKPROJECT -> image spectrum G, complex64 [n_pad][ny][nx] */
+pl_status pl_plan_workspace(pl_plan *plan, int stage, void **dev_ptr, size_t *bytes);
+
+/* Per-stage timing with CUDA events recorded on the execute stream.
+ * enable != 0 starts recording (and clears the sums). pl_plan_stage_times
+ * waits for the recorded events and returns, per stage, the summed
+ * milliseconds and the number of launches timed since the last clear. */
+pl_status pl_plan_set_timing(pl_plan *plan, int enable);
+pl_status pl_plan_stage_times(pl_plan *plan, double ms[PL_NUM_STAGES],
+                              int launches[PL_NUM_STAGES]);
+
+/* Scene simulation on the GPU (input synthesis, not part of the
+ * reconstruction): echo of point scatterers, Eq. (1) for Tx = Rx and Eq. (10)
+ * in general,
+ *   echo[c][n][m] = sum_t amp_t exp(-j k_m (R_T + R_R)),  k_m = 2 pi f_m / c.
+ * tx_xy, rx_xy: host [n_chan][2]; f_hz: host [n_f]; pts: host [n_pts][3];
+ * amp: host [n_pts][2] (complex). echo_dev: device complex64
+ * [n_chan][n_scan][n_f]. Phases are formed in FP32 after an FP64 split of
+ * the range; accuracy ~1e-5 rad. Synchronises `stream` before returning. */
+pl_status pl_synth_echo(int n_chan, const double *tx_xy, const double *rx_xy,
+                        double z0, double dz, int n_scan, const double *f_hz, int n_f,
+                        int n_pts, const double *pts, const double *amp,
+                        void *echo_dev, void *stream);
+
+const char *pl_status_string(pl_status s);
+const char *pl_last_error(void);
+/* Library version as major*10000 + minor*100 + patch. */
+int pl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLYLINE_H */

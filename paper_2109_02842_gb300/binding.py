@@ -1,0 +1,273 @@
+"""ctypes binding of libpolyline (include/polyline.h): argument marshalling only.
+
+Every computation runs in the CUDA library. Device buffers are torch CUDA
+tensors (complex64), streams are torch streams. If the library has not been
+built, loading fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpolyline.so")
+
+PL_STAGE_ZFFT, PL_STAGE_RANGE_TABLE, PL_STAGE_BACKPROJECT, PL_STAGE_ZIFFT = range(4)
+STAGE_NAMES = ("zfft", "range_table", "backproject", "zifft")
+
+_D = ctypes.c_double
+_I = ctypes.c_int
+_P = ctypes.c_void_p
+
+
+class PlGeometry(ctypes.Structure):
+    _fields_ = [("mode", _I), ("radius", _D), ("n_sections", _I), ("chord_len", _D),
+                ("n_elem", _I), ("elem_xy", _P), ("elem_section", _P), ("n_pairs", _I),
+                ("pair_tx", _P), ("pair_rx", _P)]
+
+
+class PlScan(ctypes.Structure):
+    _fields_ = [("z0", _D), ("dz", _D), ("n", _I), ("n_pad", _I)]
+
+
+class PlFreqs(ctypes.Structure):
+    _fields_ = [("f_hz", _P), ("n", _I)]
+
+
+class PlGrid(ctypes.Structure):
+    _fields_ = [("x0", _D), ("dx", _D), ("y0", _D), ("dy", _D), ("z0", _D), ("dz", _D),
+                ("nx", _I), ("ny", _I), ("nz", _I)]
+
+
+class PlOptions(ctypes.Structure):
+    _fields_ = [("precision", _I), ("nufft_sigma", _D), ("nufft_w", _I), ("tile_u", _I),
+                ("reserved", _I * 8)]
+
+
+class PlInfo(ctypes.Structure):
+    _fields_ = [("mode", _I), ("n_chan", _I), ("n_scan", _I), ("n_pad", _I), ("n_f", _I),
+                ("nx", _I), ("ny", _I), ("nz", _I), ("table_len", _I), ("fine_len", _I),
+                ("slab_rows", _I), ("nufft_w", _I), ("nufft_sigma", _D), ("table_h", _D),
+                ("table_l0", _D), ("z_transform_fft", _I), ("launches_per_execute", _I),
+                ("workspace_bytes", ctypes.c_size_t), ("updates_per_execute", _D)]
+
+
+EXPORTED = ("pl_plan_create", "pl_execute", "pl_execute_host", "pl_plan_destroy",
+            "pl_plan_get_info", "pl_plan_workspace", "pl_plan_set_timing",
+            "pl_plan_stage_times", "pl_synth_echo", "pl_status_string", "pl_last_error",
+            "pl_version")
+
+_lib = None
+
+
+class PolylineError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (%d): %s" % (status_string(status), status, msg))
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load libpolyline.so; raises if it is missing (build it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libpolyline.so not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    lib.pl_plan_create.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(PlGeometry),
+                                   ctypes.POINTER(PlScan), ctypes.POINTER(PlFreqs),
+                                   ctypes.POINTER(PlGrid), ctypes.POINTER(PlOptions)]
+    lib.pl_execute.argtypes = [_P, _P, _P, _P]
+    lib.pl_execute_host.argtypes = [_P, _P, _P, _P]
+    lib.pl_plan_destroy.argtypes = [_P]
+    lib.pl_plan_get_info.argtypes = [_P, ctypes.POINTER(PlInfo)]
+    lib.pl_plan_workspace.argtypes = [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t)]
+    lib.pl_plan_set_timing.argtypes = [_P, _I]
+    lib.pl_plan_stage_times.argtypes = [_P, ctypes.POINTER(_D), ctypes.POINTER(_I)]
+    lib.pl_synth_echo.argtypes = [_I, _P, _P, _D, _D, _I, _P, _I, _I, _P, _P, _P, _P]
+    lib.pl_status_string.restype = ctypes.c_char_p
+    lib.pl_status_string.argtypes = [_I]
+    lib.pl_last_error.restype = ctypes.c_char_p
+    lib.pl_version.restype = _I
+    for name in ("pl_plan_create", "pl_execute", "pl_execute_host", "pl_plan_destroy",
+                 "pl_plan_get_info", "pl_plan_workspace", "pl_plan_set_timing",
+                 "pl_plan_stage_times", "pl_synth_echo"):
+        getattr(lib, name).restype = _I
+    _lib = lib
+    return lib
+
+
+def status_string(s: int) -> str:
+    return load().pl_status_string(s).decode()
+
+
+def _check(status: int):
+    if status != 0:
+        raise PolylineError(status, load().pl_last_error().decode())
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_P)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return _P(stream.cuda_stream)
+
+
+class _DevArray:
+    """Exposes a raw device pointer to torch via __cuda_array_interface__."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (ptr, False), "version": 3, "strides": None}
+
+
+class Plan:
+    """A reconstruction plan (pl_plan_create / pl_execute / pl_plan_destroy)."""
+
+    def __init__(self, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad=0,
+                 pair_tx=None, pair_rx=None, radius=0.0, n_sections=0, chord_len=0.0,
+                 elem_section=None, precision=0, nufft_sigma=0.0, nufft_w=0, tile_u=0):
+        lib = load()
+        self._keep = []
+        exy = _f64(elem_xy).reshape(-1, 2)
+        sec = None if elem_section is None else _i32(elem_section)
+        ptx = None if pair_tx is None else _i32(pair_tx)
+        prx = None if pair_rx is None else _i32(pair_rx)
+        f = _f64(f_hz).ravel()
+        self._keep += [exy, sec, ptx, prx, f]
+        geom = PlGeometry(int(mode), float(radius), int(n_sections), float(chord_len),
+                          exy.shape[0], _ptr(exy), _ptr(sec),
+                          0 if ptx is None else ptx.size, _ptr(ptx), _ptr(prx))
+        scan = PlScan(float(scan_z0), float(scan_dz), int(n_scan), int(n_pad))
+        freqs = PlFreqs(_ptr(f), f.size)
+        g = PlGrid(float(grid["x0"]), float(grid["dx"]), float(grid["y0"]), float(grid["dy"]),
+                   float(grid["z0"]), float(grid["dz"]), int(grid["nx"]), int(grid["ny"]),
+                   int(grid["nz"]))
+        opt = PlOptions(int(precision), float(nufft_sigma), int(nufft_w), int(tile_u))
+        h = _P()
+        _check(lib.pl_plan_create(ctypes.byref(h), geom, scan, freqs, g, opt))
+        self._h = h
+        self.info = self.get_info()
+
+    @classmethod
+    def from_workload(cls, w, **opts):
+        return cls(w.mode, w.elem_xy, w.z0, w.dz, w.n_scan, w.f_hz, w.grid, n_pad=w.n_pad,
+                   pair_tx=w.pair_tx if w.mode == 1 else None,
+                   pair_rx=w.pair_rx if w.mode == 1 else None, radius=w.radius,
+                   n_sections=w.n_sections, chord_len=w.chord_len, elem_section=w.elem_section,
+                   **opts)
+
+    def get_info(self) -> dict:
+        i = PlInfo()
+        _check(load().pl_plan_get_info(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in PlInfo._fields_}
+
+    @property
+    def echo_shape(self):
+        return (self.info["n_chan"], self.info["n_scan"], self.info["n_f"])
+
+    @property
+    def image_shape(self):
+        return (self.info["nz"], self.info["ny"], self.info["nx"])
+
+    def execute(self, echo, image=None, stream=None):
+        """echo: CUDA complex64 [n_chan][n_scan][n_f]; returns image [nz][ny][nx]."""
+        import torch
+        assert echo.is_cuda and echo.dtype == torch.complex64 and echo.is_contiguous()
+        assert tuple(echo.shape) == self.echo_shape
+        if image is None:
+            image = torch.empty(self.image_shape, dtype=torch.complex64, device=echo.device)
+        assert image.is_cuda and image.dtype == torch.complex64 and image.is_contiguous()
+        assert tuple(image.shape) == self.image_shape
+        _check(load().pl_execute(self._h, _P(echo.data_ptr()), _P(image.data_ptr()),
+                                 _stream_handle(stream)))
+        return image
+
+    def execute_host(self, echo, image=None, stream=None):
+        """Host buffers in and out (copies inside the call); returns a NumPy image."""
+        if image is None:
+            image = np.empty(self.image_shape, dtype=np.complex64)
+        import torch
+        if isinstance(echo, torch.Tensor):
+            assert not echo.is_cuda and echo.dtype == torch.complex64 and echo.is_contiguous()
+            eptr = echo.data_ptr()
+        else:
+            assert echo.dtype == np.complex64 and echo.flags.c_contiguous
+            eptr = echo.ctypes.data
+        if isinstance(image, torch.Tensor):
+            iptr = image.data_ptr()
+        else:
+            iptr = image.ctypes.data
+        _check(load().pl_execute_host(self._h, _P(eptr), _P(iptr), _stream_handle(stream)))
+        return image
+
+    def workspace(self, stage):
+        """Torch view (complex64) of an intermediate buffer."""
+        import torch
+        ptr = _P()
+        nbytes = ctypes.c_size_t()
+        _check(load().pl_plan_workspace(self._h, int(stage), ctypes.byref(ptr),
+                                        ctypes.byref(nbytes)))
+        i = self.info
+        if stage == PL_STAGE_ZFFT:
+            shape = (i["n_chan"], i["n_pad"], i["n_f"])
+        elif stage == PL_STAGE_RANGE_TABLE:
+            shape = (i["n_chan"], i["table_len"], i["n_pad"])
+            if nbytes.value == np.prod(shape) * 4:   # BF16 pairs
+                raw = torch.as_tensor(_DevArray(ptr.value, shape + (2,), "<i2"), device="cuda")
+                return raw.view(torch.bfloat16)
+        else:
+            shape = (i["n_pad"], i["ny"], i["nx"])
+        return torch.as_tensor(_DevArray(ptr.value, shape, "<c8"), device="cuda")
+
+    def set_timing(self, enable: bool = True):
+        _check(load().pl_plan_set_timing(self._h, 1 if enable else 0))
+
+    def stage_times(self):
+        """{stage: (total_ms, launches)} since the last call / set_timing."""
+        ms = (_D * 4)()
+        n = (_I * 4)()
+        _check(load().pl_plan_stage_times(self._h, ms, n))
+        return {STAGE_NAMES[s]: (ms[s], n[s]) for s in range(4)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pl_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def synth_echo(tx_xy, rx_xy, z0, dz, n_scan, f_hz, pts, amp, out=None, stream=None):
+    """Point-scatterer echo on the GPU (Eq. 1 / Eq. 10); returns CUDA complex64."""
+    import torch
+    tx = _f64(tx_xy).reshape(-1, 2)
+    rx = _f64(rx_xy).reshape(-1, 2)
+    f = _f64(f_hz).ravel()
+    p = _f64(pts).reshape(-1, 3)
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(amp, np.complex128), (p.shape[0],)))
+    a = _f64(np.stack([a.real, a.imag], 1))
+    if out is None:
+        out = torch.empty((tx.shape[0], n_scan, f.size), dtype=torch.complex64, device="cuda")
+    _check(load().pl_synth_echo(tx.shape[0], _ptr(tx), _ptr(rx), float(z0), float(dz),
+                                int(n_scan), _ptr(f), f.size, p.shape[0], _ptr(p), _ptr(a),
+                                _P(out.data_ptr()), _stream_handle(stream)))
+    return out

@@ -1,0 +1,599 @@
+// Host side of libpolyline: argument validation, plan construction (sizes,
+// device workspace, plan-time tables) and the C ABI of include/polyline.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/polyline.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+pl_status fail(pl_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+pl_status cuda_fail(cudaError_t e, const char *where) {
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PL_ERR_OOM : PL_ERR_CUDA;
+}
+
+#define PL_CUDA(call, where)                                   \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);    \
+    } while (0)
+
+bool finite(double v) { return std::isfinite(v); }
+
+// Gauss-Legendre nodes and weights on [0, 1] by Newton's method on the
+// Legendre polynomial P_n (three-term recurrence); textbook construction.
+void gauss_legendre01(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = 0.5 * (z + 1.0);
+        w[i] = 1.0 / ((1.0 - z * z) * dp * dp);   // = (2 / ((1-z^2) P'^2)) / 2
+    }
+}
+
+bool smooth_plan(int n, FftPlan &p) {
+    p.n = n;
+    p.n_stages = 0;
+    int r = n;
+    const int order[4] = {4, 2, 3, 5};
+    for (int oi = 0; oi < 4; ++oi) {
+        while (r % order[oi] == 0) {
+            if (p.n_stages == 16) return false;
+            p.radix[p.n_stages++] = order[oi];
+            r /= order[oi];
+        }
+    }
+    return r == 1 && n > 1;
+}
+
+// min / max distance from (px, py) to the rectangle [x0,x1] x [y0,y1]
+void rect_dist(double px, double py, double x0, double x1, double y0, double y1, double &dmin,
+               double &dmax) {
+    const double cx = std::min(std::max(px, x0), x1);
+    const double cy = std::min(std::max(py, y0), y1);
+    dmin = std::hypot(px - cx, py - cy);
+    dmax = 0.0;
+    const double xs[2] = {x0, x1}, ys[2] = {y0, y1};
+    for (double xx : xs)
+        for (double yy : ys) dmax = std::max(dmax, std::hypot(px - xx, py - yy));
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count, size_t &total) {
+    total += count * sizeof(T);
+    return cudaMalloc((void **)p, std::max<size_t>(count, 1) * sizeof(T));
+}
+
+}  // namespace
+
+struct pl_plan {
+    // problem
+    int mode = 0, C = 0, N = 0, Np = 0, M = 0;
+    double z0s = 0, dzs = 0;
+    pl_grid grid{};
+    int precision = 0;
+    int tile_u = 16;
+    int device = 0;
+    // nufft
+    NufftDesc nd{};
+    double sigma = 2.0;
+    int R = 0;
+    // transforms
+    bool fwd_fft = true, inv_fft = true;
+    int inv_off = 0;
+    FftPlan zplan{};
+    // device memory
+    double *d_chxy = nullptr, *d_k = nullptr, *d_kc = nullptr, *d_kspan = nullptr;
+    double *d_glx = nullptr, *d_glw = nullptr;
+    float *d_kcf = nullptr, *d_xg = nullptr, *d_dec = nullptr;
+    float2 *d_alpha = nullptr, *d_twz = nullptr, *d_twfine = nullptr;
+    float2 *d_Tfwd = nullptr, *d_Tinv = nullptr;
+    float2 *d_S = nullptr, *d_G = nullptr;
+    void *d_table = nullptr;
+    size_t table_bytes = 0;
+    float2 *d_echo_in = nullptr, *d_img_out = nullptr;   // pl_execute_host staging
+    size_t workspace = 0;
+    int n_gl = 0;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> recorded;
+    size_t ev_next = 0;
+
+    ~pl_plan() {
+        void *ptrs[] = {d_chxy, d_k,    d_kc,   d_kspan, d_glx,  d_glw,     d_kcf,
+                        d_xg,   d_dec,  d_alpha, d_twz,  d_twfine, d_Tfwd, d_Tinv,
+                        d_S,    d_G,    d_table, d_echo_in, d_img_out};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    }
+
+    cudaEvent_t next_event() {
+        if (ev_next == ev_pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            ev_pool.push_back(e);
+        }
+        return ev_pool[ev_next++];
+    }
+};
+
+namespace {
+
+pl_status validate(const pl_geometry *g, const pl_scan *s, const pl_freqs *f, const pl_grid *gr) {
+    if (!g || !s || !f || !gr) return fail(PL_ERR_ARG, "NULL descriptor");
+    if (g->mode != 0 && g->mode != 1) return fail(PL_ERR_ARG, "geometry.mode must be 0 or 1");
+    if (g->n_elem <= 0 || !g->elem_xy) return fail(PL_ERR_GEOMETRY, "no elements");
+    for (int i = 0; i < 2 * g->n_elem; ++i)
+        if (!finite(g->elem_xy[i])) return fail(PL_ERR_NONFINITE, "element position not finite");
+    if (g->mode == 1) {
+        if (g->n_pairs <= 0 || !g->pair_tx || !g->pair_rx)
+            return fail(PL_ERR_GEOMETRY, "multistatic geometry needs pairs");
+        for (int i = 0; i < g->n_pairs; ++i)
+            if (g->pair_tx[i] < 0 || g->pair_tx[i] >= g->n_elem || g->pair_rx[i] < 0 ||
+                g->pair_rx[i] >= g->n_elem)
+                return fail(PL_ERR_GEOMETRY, "pair index out of range");
+    }
+    if (s->n <= 0) return fail(PL_ERR_ARG, "scan.n must be positive");
+    if (!finite(s->z0) || !finite(s->dz)) return fail(PL_ERR_NONFINITE, "scan not finite");
+    if (!(s->dz > 0)) return fail(PL_ERR_ARG, "scan.dz must be positive");
+    if (s->n_pad != 0 && s->n_pad < s->n) return fail(PL_ERR_ARG, "scan.n_pad < scan.n");
+    if (f->n <= 0 || !f->f_hz) return fail(PL_ERR_FREQ, "no frequencies");
+    for (int m = 0; m < f->n; ++m) {
+        if (!finite(f->f_hz[m])) return fail(PL_ERR_NONFINITE, "frequency not finite");
+        if (!(f->f_hz[m] > 0)) return fail(PL_ERR_FREQ, "frequency must be positive");
+        if (m > 0 && !(f->f_hz[m] > f->f_hz[m - 1]))
+            return fail(PL_ERR_FREQ, "frequencies must be strictly ascending");
+    }
+    const double gv[6] = {gr->x0, gr->dx, gr->y0, gr->dy, gr->z0, gr->dz};
+    for (double v : gv)
+        if (!finite(v)) return fail(PL_ERR_NONFINITE, "grid not finite");
+    if (gr->nx <= 0 || gr->ny <= 0 || gr->nz <= 0) return fail(PL_ERR_ARG, "empty image grid");
+    if (!(gr->dx > 0) || !(gr->dy > 0)) return fail(PL_ERR_ARG, "grid.dx, grid.dy must be positive");
+    if (gr->nz > 1 && !(gr->dz > 0)) return fail(PL_ERR_ARG, "grid.dz must be positive");
+    return PL_OK;
+}
+
+pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const pl_freqs *f,
+                     const pl_grid *gr, const pl_options *opt) {
+    pl_options o{};
+    if (opt) o = *opt;
+    if (o.nufft_sigma == 0) o.nufft_sigma = 2.0;
+    if (o.nufft_w == 0) o.nufft_w = 6;
+    if (o.tile_u == 0) o.tile_u = 16;
+    if (!(o.nufft_sigma >= 1.2 && o.nufft_sigma <= 8.0))
+        return fail(PL_ERR_ARG, "nufft_sigma must be in [1.2, 8]");
+    if (o.nufft_w < 4 || o.nufft_w > 12 || (o.nufft_w & 1))
+        return fail(PL_ERR_ARG, "nufft_w must be even, 4..12");
+    if (o.tile_u != 8 && o.tile_u != 16) return fail(PL_ERR_ARG, "tile_u must be 8 or 16");
+    if (o.precision != 0 && o.precision != 1) return fail(PL_ERR_ARG, "precision must be 0 or 1");
+
+    PL_CUDA(cudaGetDevice(&P->device), "cudaGetDevice");
+    P->mode = g->mode;
+    P->C = g->mode == 0 ? g->n_elem : g->n_pairs;
+    P->N = s->n;
+    P->Np = s->n_pad ? s->n_pad : s->n;
+    P->M = f->n;
+    P->z0s = s->z0;
+    P->dzs = s->dz;
+    P->grid = *gr;
+    P->precision = o.precision;
+    P->tile_u = o.tile_u;
+    P->sigma = o.nufft_sigma;
+
+    // channel positions (xT, yT, xR, yR)
+    std::vector<double> chxy(4 * (size_t)P->C);
+    for (int c = 0; c < P->C; ++c) {
+        const int et = g->mode == 0 ? c : g->pair_tx[c];
+        const int er = g->mode == 0 ? c : g->pair_rx[c];
+        chxy[4 * c + 0] = g->elem_xy[2 * et];
+        chxy[4 * c + 1] = g->elem_xy[2 * et + 1];
+        chxy[4 * c + 2] = g->elem_xy[2 * er];
+        chxy[4 * c + 3] = g->elem_xy[2 * er + 1];
+    }
+    std::vector<double> k(P->M);
+    for (int m = 0; m < P->M; ++m) k[m] = PL_TWO_PI * f->f_hz[m] / PL_C0;
+
+    size_t &ws = P->workspace;
+    PL_CUDA(dalloc(&P->d_chxy, chxy.size(), ws), "cudaMalloc");
+    PL_CUDA(dalloc(&P->d_k, k.size(), ws), "cudaMalloc");
+    PL_CUDA(dalloc(&P->d_kc, P->Np, ws), "cudaMalloc");
+    PL_CUDA(dalloc(&P->d_kcf, P->Np, ws), "cudaMalloc");
+    PL_CUDA(dalloc(&P->d_kspan, P->Np, ws), "cudaMalloc");
+    PL_CUDA(cudaMemcpy(P->d_chxy, chxy.data(), chxy.size() * 8, cudaMemcpyHostToDevice), "copy");
+    PL_CUDA(cudaMemcpy(P->d_k, k.data(), k.size() * 8, cudaMemcpyHostToDevice), "copy");
+
+    cudaStream_t st = 0;
+    PL_CUDA(launch_setup_kz(P->mode, P->Np, P->dzs, P->M, P->d_k, P->d_kc, P->d_kcf,
+                            P->d_kspan, st), "setup_kz");
+    std::vector<double> kspan(P->Np);
+    PL_CUDA(cudaMemcpy(kspan.data(), P->d_kspan, P->Np * 8, cudaMemcpyDeviceToHost), "copy");
+    double kmax = 0.0;
+    for (double v : kspan) kmax = std::max(kmax, v);
+    if (!(kmax > 0.0)) {
+        // a single frequency (or all bins evanescent but one): use a nominal band
+        bool alive = false;
+        std::vector<double> kc(P->Np);
+        PL_CUDA(cudaMemcpy(kc.data(), P->d_kc, P->Np * 8, cudaMemcpyDeviceToHost), "copy");
+        for (double v : kc) alive = alive || v > 0.0;
+        if (!alive) return fail(PL_ERR_EVANESCENT, "every (k_z, f) term is evanescent");
+        kmax = 1.0;   // every live bin has one source at kappa'' = 0
+    }
+
+    // NUFFT geometry
+    const int W = o.nufft_w;
+    const double h = PL_TWO_PI / (o.nufft_sigma * kmax);
+    const int TX = backproject_tile_x(), TY = backproject_tile_y();
+    const double hs_pix = 0.5 * std::hypot((TX - 1) * gr->dx, (TY - 1) * gr->dy);
+    const double hs = P->mode == 0 ? hs_pix : 2.0 * hs_pix;
+    P->R = (int)std::ceil(2.0 * hs / h) + W + 5;
+    const int ntx = (gr->nx + TX - 1) / TX, nty = (gr->ny + TY - 1) / TY;
+    const double rx0 = gr->x0, rx1 = gr->x0 + (ntx * TX - 1) * gr->dx;
+    const double ry0 = gr->y0, ry1 = gr->y0 + (nty * TY - 1) * gr->dy;
+    double amin = 1e300, amax = -1e300;
+    for (int c = 0; c < P->C; ++c) {
+        double lo, hi, lo2 = 0, hi2 = 0;
+        rect_dist(chxy[4 * c], chxy[4 * c + 1], rx0, rx1, ry0, ry1, lo, hi);
+        if (P->mode == 1) rect_dist(chxy[4 * c + 2], chxy[4 * c + 3], rx0, rx1, ry0, ry1, lo2, hi2);
+        amin = std::min(amin, lo + lo2);
+        amax = std::max(amax, hi + hi2);
+    }
+    int L = (int)std::ceil((amax - amin) / h) + 2 * P->R + 6;
+    L += L & 1;
+    if (L > 4096) return fail(PL_ERR_UNSUPPORTED, "range-profile table too long (grid too large for the band)");
+    int fine = 64, lg = 6;
+    while (fine < 2 * L) { fine <<= 1; ++lg; }
+
+    NufftDesc &d = P->nd;
+    d.mode = P->mode;
+    d.n_chan = P->C;
+    d.n_pad = P->Np;
+    d.n_f = P->M;
+    d.L = L;
+    d.fine = fine;
+    d.log2_fine = lg;
+    d.w = W;
+    d.w1 = 7;
+    d.beta = (float)(0.97 * M_PI * (1.0 - 0.5 / o.nufft_sigma) * W);
+    d.beta1 = (float)(2.30 * d.w1);
+    d.h = h;
+    d.l0 = amin - h * (P->R + 2);
+    if (range_table_smem_bytes(d) > 200 * 1024)
+        return fail(PL_ERR_UNSUPPORTED, "range-profile table too long for shared memory");
+
+    // plan-time tables
+    std::vector<double> glx, glw;
+    P->n_gl = 48;
+    gauss_legendre01(P->n_gl, glx, glw);
+    PL_CUDA(dalloc(&P->d_glx, glx.size(), ws), "cudaMalloc");
+    PL_CUDA(dalloc(&P->d_glw, glw.size(), ws), "cudaMalloc");
+    PL_CUDA(cudaMemcpy(P->d_glx, glx.data(), glx.size() * 8, cudaMemcpyHostToDevice), "copy");
+    PL_CUDA(cudaMemcpy(P->d_glw, glw.data(), glw.size() * 8, cudaMemcpyHostToDevice), "copy");
+    PL_CUDA(dalloc(&P->d_xg, (size_t)P->Np * P->M, ws), "cudaMalloc");
+    PL_CUDA(dalloc(&P->d_alpha, (size_t)P->Np * P->M, ws), "cudaMalloc");
+    PL_CUDA(dalloc(&P->d_dec, (size_t)L, ws), "cudaMalloc");
+    PL_CUDA(dalloc(&P->d_twfine, (size_t)fine / 2, ws), "cudaMalloc");
+    PL_CUDA(launch_setup_sources(d, P->dzs, P->d_k, P->d_kc, P->d_glx, P->d_glw, P->n_gl,
+                                 P->d_xg, P->d_alpha, st), "setup_sources");
+    PL_CUDA(launch_setup_deconv(d, P->d_glx, P->d_glw, P->n_gl, P->d_dec, st), "setup_deconv");
+    PL_CUDA(launch_twiddles(fine, fine / 2, +1, P->d_twfine, st), "twiddles");
+
+    // transforms over z
+    const bool smooth = smooth_plan(P->Np, P->zplan) && P->Np <= 512;
+    P->fwd_fft = smooth;
+    if (smooth) {
+        PL_CUDA(dalloc(&P->d_twz, (size_t)P->Np, ws), "cudaMalloc");
+        PL_CUDA(launch_twiddles(P->Np, P->Np, -1, P->d_twz, st), "twiddles");
+    } else {
+        PL_CUDA(dalloc(&P->d_Tfwd, (size_t)P->Np * P->N, ws), "cudaMalloc");
+        PL_CUDA(launch_dft_matrix_fwd(P->Np, P->N, P->d_Tfwd, st), "dft_matrix_fwd");
+    }
+    const double q = (gr->z0 - s->z0) / s->dz;
+    const long long qi = std::llround(q);
+    const bool on_grid = (gr->nz == 1 || std::fabs(gr->dz - s->dz) <= 1e-9 * s->dz) &&
+                         std::fabs(q - (double)qi) <= 1e-6 && qi >= 0 && qi + gr->nz <= P->Np;
+    P->inv_fft = smooth && on_grid;
+    P->inv_off = (int)qi;
+    if (!P->inv_fft) {
+        PL_CUDA(dalloc(&P->d_Tinv, (size_t)gr->nz * P->Np, ws), "cudaMalloc");
+        PL_CUDA(launch_dft_matrix_inv(P->Np, P->dzs, P->z0s, gr->nz, gr->z0, gr->dz, P->d_Tinv, st),
+                "dft_matrix_inv");
+    }
+
+    // data workspace
+    PL_CUDA(dalloc(&P->d_S, (size_t)P->C * P->Np * P->M, ws), "cudaMalloc");
+    P->table_bytes = (size_t)P->C * L * P->Np * (P->precision == 1 ? 4 : 8);
+    ws += P->table_bytes;
+    PL_CUDA(cudaMalloc(&P->d_table, P->table_bytes), "cudaMalloc");
+    PL_CUDA(dalloc(&P->d_G, (size_t)P->Np * gr->nx * gr->ny, ws), "cudaMalloc");
+    PL_CUDA(cudaDeviceSynchronize(), "plan setup");
+    return PL_OK;
+}
+
+pl_status run(pl_plan *P, const float2 *echo, float2 *image, cudaStream_t st) {
+    cudaEvent_t ev[PL_NUM_STAGES][2] = {};
+    if (P->timing) {
+        for (int sidx = 0; sidx < PL_NUM_STAGES; ++sidx) {
+            ev[sidx][0] = P->next_event();
+            ev[sidx][1] = P->next_event();
+            if (!ev[sidx][0] || !ev[sidx][1]) return fail(PL_ERR_CUDA, "cudaEventCreate failed");
+        }
+    }
+    auto mark = [&](int sidx, int which) -> cudaError_t {
+        if (!P->timing) return cudaSuccess;
+        return cudaEventRecord(ev[sidx][which], st);
+    };
+    const NufftDesc &d = P->nd;
+    // a1: transform over the scan axis, Eq. (2)
+    PL_CUDA(mark(0, 0), "event");
+    if (P->fwd_fft)
+        PL_CUDA(launch_fft_strided(echo, P->d_S, P->C, P->N, P->M, P->zplan, P->d_twz, -1, 1.0f,
+                                   P->Np, 0, st), "zfft");
+    else
+        PL_CUDA(launch_dft_strided(echo, P->d_S, P->C, P->N, P->M, P->Np, P->d_Tfwd, 1.0f, st),
+                "zdft");
+    PL_CUDA(mark(0, 1), "event");
+    // a2-a4: compensation + NUFFT spread + fine FFT + deconvolution, Eq. (8a)
+    PL_CUDA(mark(1, 0), "event");
+    PL_CUDA(launch_range_table(d, P->d_S, P->d_alpha, P->d_xg, P->d_dec, P->d_twfine,
+                               P->d_table, P->precision == 1, st), "range_table");
+    PL_CUDA(mark(1, 1), "event");
+    // a5: back-projection with the coherent channel sum, Eq. (8b)
+    BpDesc bp{};
+    bp.mode = P->mode;
+    bp.n_chan = P->C;
+    bp.n_pad = P->Np;
+    bp.L = d.L;
+    bp.R = P->R;
+    bp.nx = P->grid.nx;
+    bp.ny = P->grid.ny;
+    bp.x0 = P->grid.x0;
+    bp.dx = P->grid.dx;
+    bp.y0 = P->grid.y0;
+    bp.dy = P->grid.dy;
+    bp.h = d.h;
+    bp.l0 = d.l0;
+    bp.inv_h = (float)(1.0 / d.h);
+    bp.beta = d.beta;
+    bp.two_over_w = 2.0f / d.w;
+    bp.w = d.w;
+    bp.tile_u = P->tile_u;
+    bp.bf16 = P->precision == 1;
+    PL_CUDA(mark(2, 0), "event");
+    PL_CUDA(launch_backproject(bp, P->d_table, P->d_chxy, P->d_kc, P->d_kcf, P->d_G, st),
+            "backproject");
+    PL_CUDA(mark(2, 1), "event");
+    // a6: inverse transform over k_z, Eq. (9)
+    PL_CUDA(mark(3, 0), "event");
+    const int P2 = P->grid.nx * P->grid.ny;
+    if (P->inv_fft)
+        PL_CUDA(launch_fft_strided(P->d_G, image, 1, P->Np, P2, P->zplan, P->d_twz, +1,
+                                   1.0f / P->Np, P->grid.nz, P->inv_off, st), "zifft");
+    else
+        PL_CUDA(launch_dft_strided(P->d_G, image, 1, P->Np, P2, P->grid.nz, P->d_Tinv,
+                                   1.0f / P->Np, st), "zidft");
+    PL_CUDA(mark(3, 1), "event");
+    if (P->timing)
+        for (int sidx = 0; sidx < PL_NUM_STAGES; ++sidx)
+            P->recorded.push_back({sidx, {ev[sidx][0], ev[sidx][1]}});
+    return PL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pl_status_string(pl_status s) {
+    switch (s) {
+        case PL_OK: return "ok";
+        case PL_ERR_ARG: return "invalid argument";
+        case PL_ERR_GEOMETRY: return "invalid geometry";
+        case PL_ERR_FREQ: return "invalid frequencies";
+        case PL_ERR_EVANESCENT: return "all terms evanescent";
+        case PL_ERR_NONFINITE: return "non-finite input";
+        case PL_ERR_CUDA: return "CUDA error";
+        case PL_ERR_OOM: return "out of device memory";
+        case PL_ERR_TIMEOUT: return "device wait timed out";
+        case PL_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *pl_last_error(void) { return g_err.c_str(); }
+
+int pl_version(void) { return 100; }
+
+pl_status pl_plan_create(pl_plan **out, const pl_geometry *geom, const pl_scan *scan,
+                         const pl_freqs *freqs, const pl_grid *grid, const pl_options *opt) {
+    if (!out) return fail(PL_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    pl_status s = validate(geom, scan, freqs, grid);
+    if (s != PL_OK) return s;
+    pl_plan *P = new (std::nothrow) pl_plan();
+    if (!P) return fail(PL_ERR_OOM, "host allocation failed");
+    s = build_plan(P, geom, scan, freqs, grid, opt);
+    if (s != PL_OK) {
+        delete P;
+        return s;
+    }
+    *out = P;
+    return PL_OK;
+}
+
+pl_status pl_plan_destroy(pl_plan *plan) {
+    if (!plan) return fail(PL_ERR_ARG, "plan is NULL");
+    delete plan;
+    return PL_OK;
+}
+
+pl_status pl_execute(pl_plan *plan, const void *echo_dev, void *image_dev, void *stream) {
+    if (!plan || !echo_dev || !image_dev) return fail(PL_ERR_ARG, "NULL argument");
+    return run(plan, (const float2 *)echo_dev, (float2 *)image_dev, (cudaStream_t)stream);
+}
+
+pl_status pl_execute_host(pl_plan *plan, const void *echo_host, void *image_host, void *stream) {
+    if (!plan || !echo_host || !image_host) return fail(PL_ERR_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t in_bytes = (size_t)plan->C * plan->N * plan->M * sizeof(float2);
+    const size_t out_bytes =
+        (size_t)plan->grid.nx * plan->grid.ny * plan->grid.nz * sizeof(float2);
+    if (!plan->d_echo_in) {
+        PL_CUDA(cudaMalloc(&plan->d_echo_in, in_bytes), "cudaMalloc");
+        PL_CUDA(cudaMalloc(&plan->d_img_out, out_bytes), "cudaMalloc");
+        plan->workspace += in_bytes + out_bytes;
+    }
+    PL_CUDA(cudaMemcpyAsync(plan->d_echo_in, echo_host, in_bytes, cudaMemcpyHostToDevice, st),
+            "copy echo");
+    pl_status s = run(plan, plan->d_echo_in, plan->d_img_out, st);
+    if (s != PL_OK) return s;
+    PL_CUDA(cudaMemcpyAsync(image_host, plan->d_img_out, out_bytes, cudaMemcpyDeviceToHost, st),
+            "copy image");
+    PL_CUDA(cudaStreamSynchronize(st), "execute_host");
+    return PL_OK;
+}
+
+pl_status pl_plan_get_info(const pl_plan *P, pl_info *info) {
+    if (!P || !info) return fail(PL_ERR_ARG, "NULL argument");
+    pl_info i{};
+    i.mode = P->mode;
+    i.n_chan = P->C;
+    i.n_scan = P->N;
+    i.n_pad = P->Np;
+    i.n_f = P->M;
+    i.nx = P->grid.nx;
+    i.ny = P->grid.ny;
+    i.nz = P->grid.nz;
+    i.table_len = P->nd.L;
+    i.fine_len = P->nd.fine;
+    i.slab_rows = P->R;
+    i.nufft_w = P->nd.w;
+    i.nufft_sigma = P->sigma;
+    i.table_h = P->nd.h;
+    i.table_l0 = P->nd.l0;
+    i.z_transform_fft = P->inv_fft ? 1 : 0;
+    i.launches_per_execute = 4;
+    i.workspace_bytes = P->workspace;
+    i.updates_per_execute = (double)P->C * P->grid.nx * P->grid.ny * P->grid.nz * P->M;
+    *info = i;
+    return PL_OK;
+}
+
+pl_status pl_plan_workspace(pl_plan *P, int stage, void **dev_ptr, size_t *bytes) {
+    if (!P || !dev_ptr || !bytes) return fail(PL_ERR_ARG, "NULL argument");
+    switch (stage) {
+        case PL_STAGE_ZFFT:
+            *dev_ptr = P->d_S;
+            *bytes = (size_t)P->C * P->Np * P->M * sizeof(float2);
+            return PL_OK;
+        case PL_STAGE_RANGE_TABLE:
+            *dev_ptr = P->d_table;
+            *bytes = P->table_bytes;
+            return PL_OK;
+        case PL_STAGE_BACKPROJECT:
+            *dev_ptr = P->d_G;
+            *bytes = (size_t)P->Np * P->grid.nx * P->grid.ny * sizeof(float2);
+            return PL_OK;
+    }
+    return fail(PL_ERR_ARG, "no workspace for this stage");
+}
+
+pl_status pl_plan_set_timing(pl_plan *P, int enable) {
+    if (!P) return fail(PL_ERR_ARG, "plan is NULL");
+    P->timing = enable != 0;
+    P->recorded.clear();
+    P->ev_next = 0;
+    return PL_OK;
+}
+
+pl_status pl_plan_stage_times(pl_plan *P, double ms[PL_NUM_STAGES], int launches[PL_NUM_STAGES]) {
+    if (!P || !ms || !launches) return fail(PL_ERR_ARG, "NULL argument");
+    for (int s = 0; s < PL_NUM_STAGES; ++s) {
+        ms[s] = 0.0;
+        launches[s] = 0;
+    }
+    for (auto &r : P->recorded) {
+        PL_CUDA(cudaEventSynchronize(r.second.second), "cudaEventSynchronize");
+        float t = 0.f;
+        PL_CUDA(cudaEventElapsedTime(&t, r.second.first, r.second.second), "cudaEventElapsedTime");
+        ms[r.first] += t;
+        launches[r.first] += 1;
+    }
+    P->recorded.clear();
+    P->ev_next = 0;
+    return PL_OK;
+}
+
+pl_status pl_synth_echo(int n_chan, const double *tx_xy, const double *rx_xy, double z0, double dz,
+                        int n_scan, const double *f_hz, int n_f, int n_pts, const double *pts,
+                        const double *amp, void *echo_dev, void *stream) {
+    if (n_chan <= 0 || n_scan <= 0 || n_f <= 0 || n_pts < 0 || !tx_xy || !rx_xy || !f_hz ||
+        !echo_dev || (n_pts > 0 && (!pts || !amp)))
+        return fail(PL_ERR_ARG, "bad pl_synth_echo arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<float4> ch(n_chan);
+    for (int c = 0; c < n_chan; ++c)
+        ch[c] = make_float4((float)tx_xy[2 * c], (float)tx_xy[2 * c + 1], (float)rx_xy[2 * c],
+                            (float)rx_xy[2 * c + 1]);
+    std::vector<float> k(n_f);
+    for (int m = 0; m < n_f; ++m) k[m] = (float)(PL_TWO_PI * f_hz[m] / PL_C0);
+    const int np = std::max(n_pts, 1);
+    std::vector<float4> p(np, make_float4(0.f, 0.f, 0.f, 0.f));
+    std::vector<float2> a(np, make_float2(0.f, 0.f));
+    for (int t = 0; t < n_pts; ++t) {
+        p[t] = make_float4((float)pts[3 * t], (float)pts[3 * t + 1], (float)pts[3 * t + 2], 0.f);
+        a[t] = make_float2((float)amp[2 * t], (float)amp[2 * t + 1]);
+    }
+    float4 *d_ch = nullptr, *d_p = nullptr;
+    float *d_k = nullptr;
+    float2 *d_a = nullptr;
+    cudaError_t e = cudaMalloc(&d_ch, ch.size() * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&d_p, p.size() * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&d_k, k.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&d_a, a.size() * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ch, ch.data(), ch.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_p, p.data(), p.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_k, k.data(), k.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_a, a.data(), a.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_synth_echo(n_chan, d_ch, n_scan, (float)z0, (float)dz, n_f, d_k, n_pts, d_p, d_a,
+                              (float2 *)echo_dev, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_ch);
+    cudaFree(d_p);
+    cudaFree(d_k);
+    cudaFree(d_a);
+    if (e != cudaSuccess) return cuda_fail(e, "pl_synth_echo");
+    return PL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,177 @@
+// Plan-time tables: everything that depends only on the geometry, the scan
+// and the band, computed once per plan on the GPU in double precision.
+//
+// For bin u (k_z,u) and frequency m (k_m), Sec. II-A/B:
+//   kappa_um = sqrt(4 k_m^2 - k_z,u^2)      monostatic, Eq. (5)
+//   kappa_um = sqrt(k_m^2 - k_z,u^2 / 4)    multistatic, Eq. (18)
+// terms with kappa^2 <= 0 are evanescent and dropped.
+//
+// Step (8a) is an inverse transform from the nonuniform kappa' to range l.
+// It is evaluated as a type-3 nonuniform FFT (Lee & Greengard, SIAM Rev. 47
+// (2005); Barnett et al., SIAM J. Sci. Comput. 41 (2019)) on a range grid
+// l_i = l0 + i h, i < L, h = 2 pi / (sigma K):
+//   q(l) e^{j kappa_c l} = sum_m c_m e^{j kappa_m l}
+//   ~= h e^{j kappa_c l} sum_i phi(l - l_i) b_i,
+//   b_i = sum_m (c_m / phihat(kappa''_m)) e^{j kappa''_m l_i},
+// with kappa''= kappa - kappa_c centred on the band of bin u, phi the ES
+// kernel of width w cells and phihat its Fourier transform. The carrier
+// e^{j kappa_c l} plays the role of e^{j kappa_0 rho} in Eq. (8b): the paper's
+// split kappa = kappa_0 + kappa' with the reference moved to the band centre,
+// which halves the band the interpolation has to resolve.
+// b_i itself is a type-1 transform (nonuniform sources -> uniform rows),
+// computed by spreading onto a fine periodic grid, an FFT, and division by
+// the spreading kernel's transform (range_table.cu).
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+__device__ __forceinline__ double kz_of(int u, int n_pad, double dz) {
+    const int ut = (2 * u < n_pad) ? u : u - n_pad;
+    return PL_TWO_PI * (double)ut / ((double)n_pad * dz);
+}
+
+__device__ __forceinline__ double kappa_sq(int mode, double k, double kz) {
+    return mode == 0 ? 4.0 * k * k - kz * kz : k * k - 0.25 * kz * kz;
+}
+
+__global__ void k_setup_kz(int mode, int n_pad, double dz, int n_f, const double *k, double *kc,
+                           float *kc_f, double *kspan) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n_pad) return;
+    const double kz = kz_of(u, n_pad, dz);
+    double lo = 0.0, hi = 0.0;
+    bool any = false;
+    for (int m = 0; m < n_f; ++m) {
+        const double q = kappa_sq(mode, k[m], kz);
+        if (q <= 0.0) continue;
+        const double kap = sqrt(q);
+        if (!any) { lo = hi = kap; any = true; }
+        lo = fmin(lo, kap);
+        hi = fmax(hi, kap);
+    }
+    kc[u] = any ? 0.5 * (lo + hi) : 0.0;
+    kc_f[u] = (float)kc[u];
+    kspan[u] = any ? hi - lo : 0.0;
+}
+
+// phihat(kappa) / h = 2 * int_0^{w/2} ES(t) cos(kappa h t) dt by Gauss-Legendre
+// nodes gl_x (on [0,1]) and weights gl_w.
+__device__ double es_transform(double omega, int w, double beta, const double *gl_x,
+                               const double *gl_w, int n_gl) {
+    const double half = 0.5 * w;
+    double s = 0.0;
+    for (int i = 0; i < n_gl; ++i) {
+        const double t = half * gl_x[i];
+        s += gl_w[i] * es_kernel_d(t, 2.0 / w, beta) * cos(omega * t);
+    }
+    return 2.0 * half * s;
+}
+
+__global__ void k_setup_sources(NufftDesc d, double dz, const double *k, const double *kc,
+                                const double *gl_x, const double *gl_w, int n_gl, float *xg,
+                                float2 *alpha) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= d.n_pad * d.n_f) return;
+    const int u = idx / d.n_f;
+    const int m = idx - u * d.n_f;
+    const double kz = kz_of(u, d.n_pad, dz);
+    const double q = kappa_sq(d.mode, k[m], kz);
+    if (q <= 0.0) {            // evanescent: no source
+        xg[idx] = 0.0f;
+        alpha[idx] = make_float2(0.f, 0.f);
+        return;
+    }
+    const double kpp = sqrt(q) - kc[u];                // kappa'' in [-K/2, K/2]
+    const double theta = kpp * d.h;                    // radians per table row
+    xg[idx] = (float)(theta * d.fine / PL_TWO_PI);     // position on the fine grid
+    const double phihat = d.h * es_transform(theta, d.w, d.beta, gl_x, gl_w, n_gl);
+    // c_m = S k_m (the k dk weight of Eq. 7); centre the type-1 output index
+    // at row L/2 and put row 0 at l0.
+    const double ph = kpp * (d.l0 + d.h * (double)(d.L / 2));
+    const double red = ph - PL_TWO_PI * rint(ph / PL_TWO_PI);
+    const double mag = k[m] / phihat;
+    alpha[idx] = make_float2((float)(mag * cos(red)), (float)(mag * sin(red)));
+}
+
+__global__ void k_setup_deconv(NufftDesc d, const double *gl_x, const double *gl_w, int n_gl,
+                               float *dec) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.L) return;
+    const int j = i - d.L / 2;
+    const double omega = PL_TWO_PI * (double)j / (double)d.fine;
+    dec[i] = (float)(1.0 / es_transform(omega, d.w1, d.beta1, gl_x, gl_w, n_gl));
+}
+
+__global__ void k_twiddles(int n, int count, int sgn, float2 *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    double s, c;
+    sincospi(2.0 * (double)k / (double)n, &s, &c);
+    out[k] = make_float2((float)c, (float)(sgn * s));
+}
+
+__global__ void k_dft_matrix_fwd(int n_pad, int n_scan, float2 *T) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_pad * n_scan) return;
+    const int u = idx / n_scan;
+    const int n = idx - u * n_scan;
+    const long long r = ((long long)u * n) % n_pad;
+    double s, c;
+    sincospi(2.0 * (double)r / (double)n_pad, &s, &c);
+    T[idx] = make_float2((float)c, (float)(-s));
+}
+
+__global__ void k_dft_matrix_inv(int n_pad, double dz, double z0_scan, int nz, double zv0,
+                                 double dzv, float2 *T) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nz * n_pad) return;
+    const int p = idx / n_pad;
+    const int u = idx - p * n_pad;
+    const double ph = kz_of(u, n_pad, dz) * (zv0 + p * dzv - z0_scan);
+    const double red = ph - PL_TWO_PI * rint(ph / PL_TWO_PI);
+    T[idx] = make_float2((float)cos(red), (float)sin(red));
+}
+
+inline int blocks(long long n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_setup_kz(int mode, int n_pad, double dz, int n_f, const double *k,
+                            double *kc, float *kc_f, double *kspan, cudaStream_t st) {
+    k_setup_kz<<<blocks(n_pad, 128), 128, 0, st>>>(mode, n_pad, dz, n_f, k, kc, kc_f, kspan);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup_sources(const NufftDesc &d, double dz, const double *k,
+                                 const double *kc, const double *gl_x, const double *gl_w,
+                                 int n_gl, float *xg, float2 *alpha, cudaStream_t st) {
+    k_setup_sources<<<blocks((long long)d.n_pad * d.n_f, 128), 128, 0, st>>>(
+        d, dz, k, kc, gl_x, gl_w, n_gl, xg, alpha);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup_deconv(const NufftDesc &d, const double *gl_x, const double *gl_w,
+                                int n_gl, float *dec, cudaStream_t st) {
+    k_setup_deconv<<<blocks(d.L, 128), 128, 0, st>>>(d, gl_x, gl_w, n_gl, dec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_twiddles(int n, int count, int sgn, float2 *out, cudaStream_t st) {
+    k_twiddles<<<blocks(count, 128), 128, 0, st>>>(n, count, sgn, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dft_matrix_fwd(int n_pad, int n_scan, float2 *T, cudaStream_t st) {
+    k_dft_matrix_fwd<<<blocks((long long)n_pad * n_scan, 128), 128, 0, st>>>(n_pad, n_scan, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dft_matrix_inv(int n_pad, double dz, double z0_scan, int nz, double zv0,
+                                  double dzv, float2 *T, cudaStream_t st) {
+    k_dft_matrix_inv<<<blocks((long long)nz * n_pad, 128), 128, 0, st>>>(n_pad, dz, z0_scan, nz,
+                                                                       zv0, dzv, T);
+    return cudaGetLastError();
+}

@@ -1,0 +1,183 @@
+// Transforms along the scan axis (Sec. II-A, Eq. 2) and along k_z (Eq. 9).
+//
+// Both act on the middle axis of a [batch][n][inner] complex64 array whose
+// inner axis is contiguous: the echo s[c][n][m] (forward, zero-padded to N_p)
+// and the image spectrum G[u][pixel] (inverse). One block stages a
+// [n][IB] column panel in shared memory (coalesced 128-byte rows), runs a
+// mixed-radix (2, 3, 4, 5) Stockham autosort FFT on all IB columns at once
+// and writes the requested output rows. Lengths with another prime factor,
+// and inverse transforms onto voxel heights off the scan grid, use the
+// tiled direct DFT kernel below with a precomputed phase matrix.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+constexpr int kFftIB = 16;   // columns per block
+
+// Small DFT of radix R on v[] in place, exponent sign `sgn` (-1 forward).
+// W_R^{rq} is read from the length-N table of exp(-2 pi i k / N).
+template <int R>
+__device__ __forceinline__ void small_dft(float2 (&v)[5], const float2 *tw, int N, int sgn) {
+    float2 o[R];
+    const int step = N / R;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        float2 acc = v[0];
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            float2 w = tw[((r * q) % R) * step];
+            if (sgn > 0) w.y = -w.y;
+            acc = cadd(acc, cmul(v[r], w));
+        }
+        o[q] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[q] = o[q];
+}
+
+template <int R>
+__device__ __forceinline__ void stockham_stage(const float2 *src, float2 *dst, const float2 *tw,
+                                               int N, int Ns, int sgn) {
+    const int items = (N / R) * kFftIB;
+    const int nr = N / R;
+    const int tw_step = N / (Ns * R);
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int j = it / kFftIB;
+        const int col = it - j * kFftIB;
+        const int k = j % Ns;
+        float2 v[5];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float2 x = src[(j + r * nr) * kFftIB + col];
+            if (r > 0) {
+                float2 w = tw[(k * r * tw_step) % N];
+                if (sgn > 0) w.y = -w.y;
+                x = cmul(x, w);
+            }
+            v[r] = x;
+        }
+        small_dft<R>(v, tw, N, sgn);
+        const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int q = 0; q < R; ++q) dst[(base + q * Ns) * kFftIB + col] = v[q];
+    }
+}
+
+// in:  [batch][n_in][I]  (rows n >= n_in are zero padding)
+// out: [batch][out_rows][I], out row r = transform index (r + out_off) mod N
+__global__ void __launch_bounds__(256)
+k_fft_strided(const float2 *__restrict__ in, float2 *__restrict__ out, int n_in, int I,
+              FftPlan plan, const float2 *__restrict__ tw_g, int sgn, float scale,
+              int out_rows, int out_off) {
+    extern __shared__ float2 smem[];
+    const int N = plan.n;
+    float2 *buf0 = smem;
+    float2 *buf1 = smem + N * kFftIB;
+    float2 *tw = smem + 2 * N * kFftIB;
+    const int i0 = blockIdx.x * kFftIB;
+    const size_t b = blockIdx.y;
+
+    for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
+    for (int idx = threadIdx.x; idx < N * kFftIB; idx += blockDim.x) {
+        const int n = idx / kFftIB;
+        const int col = idx - n * kFftIB;
+        float2 v = make_float2(0.f, 0.f);
+        if (n < n_in && i0 + col < I) v = in[(b * n_in + n) * (size_t)I + i0 + col];
+        buf0[idx] = v;
+    }
+    __syncthreads();
+
+    float2 *src = buf0, *dst = buf1;
+    int Ns = 1;
+    for (int s = 0; s < plan.n_stages; ++s) {
+        const int R = plan.radix[s];
+        if (R == 4) stockham_stage<4>(src, dst, tw, N, Ns, sgn);
+        else if (R == 2) stockham_stage<2>(src, dst, tw, N, Ns, sgn);
+        else if (R == 3) stockham_stage<3>(src, dst, tw, N, Ns, sgn);
+        else stockham_stage<5>(src, dst, tw, N, Ns, sgn);
+        __syncthreads();
+        float2 *t = src; src = dst; dst = t;
+        Ns *= R;
+    }
+
+    for (int idx = threadIdx.x; idx < out_rows * kFftIB; idx += blockDim.x) {
+        const int r = idx / kFftIB;
+        const int col = idx - r * kFftIB;
+        if (i0 + col >= I) continue;
+        int sr = r + out_off;
+        sr %= N;
+        out[(b * out_rows + r) * (size_t)I + i0 + col] = cscale(src[sr * kFftIB + col], scale);
+    }
+}
+
+// Direct DFT along the middle axis with an explicit phase matrix:
+//   out[b][r][i] = scale * sum_{n < n_in} in[b][n][i] * T[r][n]
+// 32 x 32 output tile per block, 256 threads, 4 outputs each.
+__global__ void __launch_bounds__(256)
+k_dft_strided(const float2 *__restrict__ in, float2 *__restrict__ out, int n_in, int I,
+              int out_rows, const float2 *__restrict__ T, float scale) {
+    __shared__ float2 xs[32][33];
+    __shared__ float2 ts[32][33];
+    const int tx = threadIdx.x & 31;
+    const int ty = threadIdx.x >> 5;   // 0..7
+    const int i = blockIdx.x * 32 + tx;
+    const int r0 = blockIdx.y * 32;
+    const size_t b = blockIdx.z;
+    float2 acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
+    for (int n0 = 0; n0 < n_in; n0 += 32) {
+        for (int q = 0; q < 4; ++q) {
+            const int nn = ty * 4 + q;
+            const int n = n0 + nn;
+            xs[nn][tx] = (n < n_in && i < I) ? in[(b * n_in + n) * (size_t)I + i]
+                                             : make_float2(0.f, 0.f);
+            const int rr = r0 + ty * 4 + q;
+            ts[ty * 4 + q][tx] = (rr < out_rows && n0 + tx < n_in)
+                                     ? T[(size_t)rr * n_in + n0 + tx] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int nn = 0; nn < 32; ++nn) {
+            const float2 x = xs[nn][tx];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 t = ts[ty * 4 + q][nn];
+                acc[q].x += x.x * t.x - x.y * t.y;
+                acc[q].y += x.x * t.y + x.y * t.x;
+            }
+        }
+        __syncthreads();
+    }
+    if (i < I) {
+        for (int q = 0; q < 4; ++q) {
+            const int r = r0 + ty * 4 + q;
+            if (r < out_rows) out[(b * out_rows + r) * (size_t)I + i] = cscale(acc[q], scale);
+        }
+    }
+}
+
+}  // namespace
+
+size_t fft_strided_smem_bytes(int n) { return (size_t)(2 * n * kFftIB + n) * sizeof(float2); }
+
+cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_in, int I,
+                               const FftPlan &plan, const float2 *tw, int sgn, float scale,
+                               int out_rows, int out_off, cudaStream_t st) {
+    const size_t smem = fft_strided_smem_bytes(plan.n);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_strided, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((I + kFftIB - 1) / kFftIB, batch);
+    k_fft_strided<<<grid, 256, smem, st>>>(in, out, n_in, I, plan, tw, sgn, scale, out_rows,
+                                           out_off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dft_strided(const float2 *in, float2 *out, int batch, int n_in, int I,
+                               int out_rows, const float2 *T, float scale, cudaStream_t st) {
+    dim3 grid((I + 31) / 32, (out_rows + 31) / 32, batch);
+    k_dft_strided<<<grid, 256, 0, st>>>(in, out, n_in, I, out_rows, T, scale);
+    return cudaGetLastError();
+}

@@ -1,0 +1,235 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerance (the FP32 path): relative L2 error <= 1e-4 over the compared
+outputs; the maximum per-voxel magnitude error is printed beside it. The
+BF16-table variant is held to 1e-2. Inputs are seeded point-target scenes
+from the shared generator; echoes come from the oracle's echo model.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_02842_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-4
+TOL_BF16 = 1e-2
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def report(name, got, ref):
+    e = rel(got, ref)
+    mx = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    print("%s: rel L2 %.3e, max |err| / max |ref| %.3e" % (name, e, mx))
+    return e
+
+
+@pytest.fixture(scope="module")
+def binding():
+    from paper_2109_02842_gb300 import build, binding as b
+    build.build()
+    b.load()
+    assert torch.cuda.is_available()
+    return b
+
+
+def scene_echo(w, seed=0, n_pts=None):
+    pts, amp = (w.pts, w.amp) if n_pts is None else (w.pts[:n_pts], w.amp[:n_pts])
+    clean = oracle.synth_echo(w.tx_xy, w.rx_xy, w.z_scan, w.f_hz, pts, amp)
+    return wl.add_noise(clean, w.snr_db, wl.rng_for(100, seed)).astype(np.complex64)
+
+
+def run_gpu(binding, w, echo, **opts):
+    plan = binding.Plan.from_workload(w, **opts)
+    img = plan.execute(torch.from_numpy(echo).cuda())
+    torch.cuda.synchronize()
+    return plan, img.cpu().numpy()
+
+
+def small_multi(n_tx=2, n_rx=16, nx=32, ny=32):
+    w = wl.small_mono(seed=0)
+    xy, sec, ptx, prx, L = wl.multistatic_array(0.5, 4, 60.0, n_tx, n_rx)
+    w.mode, w.elem_xy, w.elem_section, w.pair_tx, w.pair_rx = 1, xy, sec, ptx, prx
+    w.grid = dict(w.grid, nx=nx, ny=ny)
+    return w
+
+
+# --- stage parity ------------------------------------------------------------
+
+@pytest.mark.parametrize("n_pad", [64, 67])
+def test_zfft_stage_matches_dft(binding, n_pad):
+    w = wl.small_mono(seed=0)
+    w.n_pad = n_pad                      # 64: Stockham FFT; 67: direct DFT
+    echo = scene_echo(w)
+    plan, _ = run_gpu(binding, w, echo)
+    S = plan.workspace(binding.PL_STAGE_ZFFT).cpu().numpy()
+    assert report("S n_pad=%d" % n_pad, S, oracle.zdft(echo, n_pad)) < 1e-5
+
+
+def test_kspace_image_matches_exact_sum(binding):
+    w = wl.small_mono(seed=1)
+    echo = scene_echo(w, 1)
+    plan, _ = run_gpu(binding, w, echo)
+    G = plan.workspace(binding.PL_STAGE_BACKPROJECT).cpu().numpy().reshape(w.n_pad, -1)
+    S = oracle.zdft(echo, w.n_pad)
+    ref = oracle.hybrid_spectral(0, w.tx_xy, w.rx_xy, S, w.dz, w.f_hz, w.pix_xy())
+    assert report("G small mono", G, ref) < TOL_FP32
+
+
+# --- end-to-end images ----------------------------------------------------------
+
+def image_ref(w, echo, pix=None):
+    pix = w.pix_xy() if pix is None else pix
+    return oracle.hybrid_exact(w.mode, w.tx_xy, w.rx_xy, echo, w.z_scan, w.f_hz, w.n_pad, pix,
+                               w.axis("z"))
+
+
+def test_small_mono_image(binding):
+    w = wl.small_mono(seed=0)
+    echo = scene_echo(w)
+    _, img = run_gpu(binding, w, echo)
+    ref = image_ref(w, echo)
+    assert report("image small mono", img.reshape(w.grid["nz"], -1), ref) < TOL_FP32
+
+
+def test_small_multi_image(binding):
+    w = small_multi()
+    echo = scene_echo(w)
+    _, img = run_gpu(binding, w, echo)
+    ref = image_ref(w, echo)
+    assert report("image small multi", img.reshape(w.grid["nz"], -1), ref) < TOL_FP32
+
+
+def test_gpu_mono_equals_multi_colocated(binding):
+    w = wl.small_mono(seed=2)
+    echo = scene_echo(w, 2)
+    _, g0 = run_gpu(binding, w, echo)
+    w1 = wl.small_mono(seed=2)
+    n = w1.elem_xy.shape[0]
+    w1.mode, w1.pair_tx, w1.pair_rx = 1, np.arange(n), np.arange(n)
+    _, g1 = run_gpu(binding, w1, echo)
+    assert rel(g1, g0) < 2 * TOL_FP32
+
+
+def test_ragged_grid_and_offgrid_z(binding):
+    # nx, ny not multiples of the 16 x 16 tile; z voxels off the scan grid
+    w = wl.small_mono(seed=3)
+    w.grid = dict(w.grid, nx=37, ny=23, nz=7, z0=-0.031, dz=0.0093)
+    echo = scene_echo(w, 3)
+    plan, img = run_gpu(binding, w, echo)
+    assert plan.info["z_transform_fft"] == 0
+    assert report("image ragged", img.reshape(7, -1), image_ref(w, echo)) < TOL_FP32
+
+
+def test_scan_grid_ifft_path_with_offset(binding):
+    # voxel heights on the scan grid, shifted by 5 scan steps: inverse FFT path
+    w = wl.small_mono(seed=4)
+    w.grid = dict(w.grid, z0=w.z0 + 5 * w.dz, dz=w.dz, nz=20)
+    echo = scene_echo(w, 4)
+    plan, img = run_gpu(binding, w, echo)
+    assert plan.info["z_transform_fft"] == 1
+    assert report("image ifft path", img.reshape(20, -1), image_ref(w, echo)) < TOL_FP32
+
+
+def test_single_frequency_and_single_scan(binding):
+    w = wl.small_mono(seed=5)
+    w.f_hz = w.f_hz[:1]
+    w.n_scan, w.n_pad = 1, 1
+    w.grid = dict(w.grid, nz=1, z0=w.z0, dz=w.dz)
+    echo = scene_echo(w, 5)
+    _, img = run_gpu(binding, w, echo)
+    assert report("image 1 freq 1 scan", img.reshape(1, -1), image_ref(w, echo)) < TOL_FP32
+
+
+def test_bf16_table_variant(binding):
+    w = wl.small_mono(seed=0)
+    echo = scene_echo(w)
+    _, img = run_gpu(binding, w, echo, precision=1)
+    assert report("image bf16 table", img.reshape(w.grid["nz"], -1), image_ref(w, echo)) < TOL_BF16
+
+
+def test_execute_host_matches_device(binding):
+    w = wl.small_mono(seed=6)
+    echo = scene_echo(w, 6)
+    plan, img = run_gpu(binding, w, echo)
+    img_h = plan.execute_host(echo)
+    assert np.array_equal(img_h, img)
+
+
+def test_stage_timing(binding):
+    w = wl.small_mono(seed=0)
+    plan = binding.Plan.from_workload(w)
+    e = torch.from_numpy(scene_echo(w)).cuda()
+    plan.set_timing(True)
+    for _ in range(3):
+        plan.execute(e)
+    t = plan.stage_times()
+    assert all(v[1] == 3 and v[0] > 0 for v in t.values()), t
+
+
+def test_invalid_inputs_are_rejected(binding):
+    w = wl.small_mono(seed=0)
+    with pytest.raises(binding.PolylineError) as ei:       # descending frequencies
+        binding.Plan(0, w.elem_xy, w.z0, w.dz, w.n_scan, w.f_hz[::-1], w.grid)
+    assert ei.value.status == 3
+    with pytest.raises(binding.PolylineError) as ei:       # empty grid
+        binding.Plan(0, w.elem_xy, w.z0, w.dz, w.n_scan, w.f_hz, dict(w.grid, nx=0))
+    assert ei.value.status == 1
+    with pytest.raises(binding.PolylineError) as ei:       # pair index out of range
+        binding.Plan(1, w.elem_xy, w.z0, w.dz, w.n_scan, w.f_hz, w.grid, pair_tx=[0, 999],
+                     pair_rx=[1, 2])
+    assert ei.value.status == 2
+    with pytest.raises(binding.PolylineError) as ei:       # non-finite position
+        xy = w.elem_xy.copy()
+        xy[3, 1] = np.nan
+        binding.Plan(0, xy, w.z0, w.dz, w.n_scan, w.f_hz, w.grid)
+    assert ei.value.status == 5
+    with pytest.raises(binding.PolylineError) as ei:       # n_pad < n
+        binding.Plan(0, w.elem_xy, w.z0, w.dz, w.n_scan, w.f_hz, w.grid, n_pad=4)
+    assert ei.value.status == 1
+
+
+def test_evanescent_bins_are_dropped(binding):
+    # dz so coarse that |k_z| > 2k for the outer bins: they contribute nothing,
+    # exactly as in the oracle (the k_z = 0 bin always propagates).
+    w = wl.small_mono(seed=0)
+    w.dz, w.n_scan, w.n_pad = 0.05, 8, 8
+    w.z0 = -3.5 * w.dz
+    w.f_hz = np.linspace(0.3e9, 0.5e9, 8)
+    w.grid = dict(w.grid, nz=8, z0=w.z0, dz=w.dz)
+    echo = scene_echo(w, 9)
+    _, img = run_gpu(binding, w, echo)
+    assert report("image evanescent bins", img.reshape(8, -1), image_ref(w, echo)) < TOL_FP32
+
+
+def test_gpu_echo_synthesis_matches_oracle(binding):
+    w = wl.small_mono(seed=7)
+    got = binding.synth_echo(w.tx_xy, w.rx_xy, w.z0, w.dz, w.n_scan, w.f_hz, w.pts, w.amp)
+    ref = oracle.synth_echo(w.tx_xy, w.rx_xy, w.z_scan, w.f_hz, w.pts, w.amp)
+    assert rel(got.cpu().numpy(), ref) < 1e-3
+
+
+# --- full sizes, sampled outputs --------------------------------------------------
+
+def sampled_columns(w, n, seed):
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(w.grid["nx"] * w.grid["ny"], size=n, replace=False)
+    return idx
+
+
+@pytest.mark.parametrize("which", ["full_mono", "multi"])
+def test_full_size_sampled_columns(binding, which):
+    w = wl.WORKLOADS[which](seed=0)
+    echo = scene_echo(w, 0, n_pts=24)
+    _, img = run_gpu(binding, w, echo)
+    idx = sampled_columns(w, 48, 1)
+    ref = image_ref(w, echo, w.pix_xy()[idx])
+    got = img.reshape(w.grid["nz"], -1)[:, idx]
+    assert report("image %s sampled" % which, got, ref) < TOL_FP32
