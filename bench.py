@@ -1,0 +1,358 @@
+"""Benchmark of the polyline-array hybrid reconstruction on GB300.
+
+One step = one full reconstruction of one scan (z-FFT, NUFFT range table,
+back-projection with the coherent channel sum, z inverse FFT) of the
+full-size monostatic workload: 8 chords of R = 0.6 m over 120 deg with 48
+elements each (384), 200 scans at 5 mm, 64 frequencies 24-34 GHz,
+256 x 256 x 200 voxels; elliptic-cylinder scene of 2000 + 20 points, 30 dB.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line. `value` = element-voxel-frequency updates per second
+(C * Nx * Ny * Nz * M per scan) with inputs resident in HBM, timed with CUDA
+events on the launch stream; `e2e` = the same through pl_execute_host with
+pinned host buffers (copies inside the timed region). For N > 1 (torchrun)
+each rank reconstructs its own scans (independent replicas, no collective on
+the data path); `value` is the sum over ranks over the slowest rank's time.
+`--impl reference` times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP32_LANES_PER_SM = 128
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+MUFU_PER_SM_CLK = 16
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--no-oracle", action="store_true", help="skip the CPU baseline leg")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current source of the kernel (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p)).get(kernel, {})
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2109_02842_gb300", "csrc", d.get("source", "x"))
+    if not os.path.exists(src) or d.get("workload") != workload:
+        return None
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    return d.get("bytes_per_launch") if sha == d.get("sha1") else None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index: int, path: str):
+        self.path = path
+        self.proc = None
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), "--query-gpu=" + CLOCK_QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names[1:], parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def backproject_flops_per_update(w_taps: int) -> int:
+    # w complex-by-real MACs (4w flop) + carrier phase product (1) +
+    # complex multiply-accumulate (8); the sine/cosine pair is 2 MUFU ops.
+    return 4 * w_taps + 9
+
+
+def oracle_baseline(w, echo_np, gpu_image=None, n_cols=256, n_chan=None, seed=1):
+    """Time the FP64 oracle on a bounded sample -- P sampled (x, y) columns x
+    all z, optionally over the first n_chan channels only -- and scale to the
+    metric's unit; optionally return the GPU image's error on those columns
+    (only when every channel is used)."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed)
+    P = w.grid["nx"] * w.grid["ny"]
+    C = w.n_chan
+    cs = C if n_chan is None else min(n_chan, C)
+    idx = np.sort(rng.choice(P, size=min(n_cols, P), replace=False))
+    pix = w.pix_xy()[idx]
+    t0 = time.perf_counter()
+    S = oracle.zdft(echo_np[:cs], w.n_pad)
+    t1 = time.perf_counter()
+    G = oracle.hybrid_spectral(w.mode, w.tx_xy[:cs], w.rx_xy[:cs], S, w.dz, w.f_hz, pix)
+    g = oracle.zidft(G, w.dz, w.z0, w.axis("z"))
+    t2 = time.perf_counter()
+    # full-scan time: z-DFT over all channels + per-column work over all columns
+    t_full = (t1 - t0) * C / cs + (t2 - t1) * (C / cs) * (P / idx.size)
+    upd = w.updates_per_scan()
+    out = {"value": upd / t_full, "unit": "updates/s", "cores": oracle.num_threads(),
+           "kind": "oracle",
+           "sample": "FP64 exact-sum hybrid on %d of %d channels: z-DFT (%.2f s) + %d of %d "
+                     "(x,y) columns x all %d z (%.2f s), scaled to the full scan" %
+                     (cs, C, t1 - t0, idx.size, P, w.grid["nz"], t2 - t1),
+           "seconds": t2 - t0}
+    err = None
+    if gpu_image is not None and cs == C:
+        got = gpu_image.reshape(w.grid["nz"], -1)[:, idx]
+        mx = float(np.max(np.abs(got - g)) / np.max(np.abs(g)))
+        err = {"rel_l2": float(np.linalg.norm(got - g) / np.linalg.norm(g)),
+               "max_abs_over_max_ref": mx, "columns": int(idx.size)}
+    return out, err
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2109_02842_gb300 import workloads as wl
+    oracle.build()
+    w = wl.full_mono(seed=0)
+    rng = np.random.default_rng(7)
+    echo = (rng.standard_normal((w.n_chan, w.n_scan, w.n_f)) +
+            1j * rng.standard_normal((w.n_chan, w.n_scan, w.n_f)))
+    for _ in range(args.warmup):
+        oracle_baseline(w, echo, n_cols=64, n_chan=48)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        b, _ = oracle_baseline(w, echo, n_cols=64, n_chan=48)
+        vals.append(b["value"])
+        secs.append(b["seconds"])
+    v = statistics.mean(vals)
+    base = b
+    base["value"] = v
+    line = {"impl": "reference", "metric": "element-voxel-freq updates/s (FP64 CPU oracle)",
+            "value": v, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name},
+            "cpu_baseline": base,
+            "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import numpy as np
+    import torch
+    from paper_2109_02842_gb300 import binding, build as nbuild, workloads as wl
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    nbuild.build()
+    binding.load()
+    dev = torch.device("cuda", local)
+
+    w = wl.full_mono(seed=rank)
+    plan = binding.Plan.from_workload(w, precision=args.precision)
+    info = plan.info
+    # inputs resident in HBM: scene echo synthesised on the GPU + 30 dB noise
+    echo = binding.synth_echo(w.tx_xy, w.rx_xy, w.z0, w.dz, w.n_scan, w.f_hz, w.pts, w.amp)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234 + rank)
+    p_sig = float(torch.mean(echo.abs() ** 2))
+    noise = torch.randn(echo.shape, dtype=torch.complex64, device=dev, generator=gen)
+    echo += math.sqrt(p_sig * 10 ** (-w.snr_db / 10)) * noise
+    del noise
+    image = torch.empty(plan.image_shape, dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        plan.execute(echo, image)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    plan.set_timing(True)
+    clocks = ClockSampler(local, os.path.join(tempfile.gettempdir(),
+                                              "pl_bench_clocks_rank%d.csv" % rank))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()                       # L2 flush between steps, outside the events
+        starts[i].record(stream)
+        plan.execute(echo, image)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    stage = plan.stage_times()
+    plan.set_timing(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    upd = w.updates_per_scan()
+    value = world * upd / (ms * 1e-3)
+
+    # end to end through the C ABI with pinned host buffers
+    echo_h = echo.cpu().pin_memory()
+    image_h = torch.empty(plan.image_shape, dtype=torch.complex64).pin_memory()
+    for _ in range(2):
+        plan.execute_host(echo_h, image_h)
+    e2e_t = []
+    for _ in range(args.steps):
+        ta = time.perf_counter()
+        plan.execute_host(echo_h, image_h)
+        e2e_t.append(time.perf_counter() - ta)
+    e2e_s = statistics.mean(e2e_t)
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # roofline of the dominant kernel (back-projection), live CUDA-event times
+    bp_ms, bp_n = stage["backproject"]
+    bp_avg_s = bp_ms / max(bp_n, 1) * 1e-3
+    pix_updates = info["n_chan"] * info["nx"] * info["ny"] * info["n_pad"]
+    flops = pix_updates * backproject_flops_per_update(info["nufft_w"])
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops / bp_avg_s / 1e12
+    traffic = kernel_traffic("backproject", w.name)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": traffic,
+                "kernel": "k_backproject", "launch_ms": bp_avg_s * 1e3,
+                "flop_per_launch": flops,
+                "peak_basis": "FP32: 152 SM x 128 lanes x 2 flop x 2070 MHz (recipe unit "
+                              "counts and max clock)",
+                "mufu_frac": (2 * pix_updates / bp_avg_s) /
+                             (N_SM * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6)}
+    stage_avg = {k: v[0] / max(v[1], 1) for k, v in stage.items()}
+
+    cpu, acc = None, None
+    if rank == 0 and world == 1 and not args.no_oracle:
+        # accuracy leg and CPU baseline on an oracle-made echo (24 points)
+        import oracle
+        oracle.build()
+        clean = oracle.synth_echo(w.tx_xy, w.rx_xy, w.z_scan, w.f_hz, w.pts[:24], w.amp[:24])
+        e_np = wl.add_noise(clean, w.snr_db, wl.rng_for(100, 0)).astype(np.complex64)
+        img = plan.execute(torch.from_numpy(e_np).to(dev)).cpu().numpy()
+        cpu, acc = oracle_baseline(w, e_np, img, n_cols=256)
+
+    peaks, peak_src = measured_peaks()
+    line = {
+        "metric": "element-voxel-freq updates/s at rel. L2 err <= 1e-3 vs FP64 oracle",
+        "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 0 else "f32+bf16",
+        "data": "synthetic",
+        "config": {"workload": w.name, "mode": "monostatic", "n_chan": info["n_chan"],
+                   "n_scan": info["n_scan"], "n_f": info["n_f"],
+                   "grid": [info["nx"], info["ny"], info["nz"]], "n_pad": info["n_pad"],
+                   "precision": "fp32" if args.precision == 0 else "bf16-table",
+                   "nufft_w": info["nufft_w"], "nufft_sigma": info["nufft_sigma"],
+                   "parallelism": "replicas%d" % world,
+                   "l2": "flushed before every step (256 MiB write, outside the step events)"},
+        "scans_per_s": world / (ms * 1e-3),
+        "e2e": {"value": world * upd / e2e_s, "unit": "updates/s",
+                "h2d_bytes_per_step": int(echo.numel() * 8),
+                "d2h_bytes_per_step": int(image.numel() * 8),
+                "scans_per_s": world / e2e_s},
+        "gpu_launches": info["launches_per_execute"] * args.steps,
+        "roofline": roofline,
+        "stage_ms": stage_avg,
+        "clocks": clk,
+        "wall_s_timed_region": wall,
+        "accuracy_vs_oracle": acc,
+        "cpu_baseline": cpu,
+        "peaks_source": peak_src,
+        "hbm_peak_gbs": peaks.get("hbm_gbs"),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -103,13 +103,17 @@ typedef struct {
  *            1 = range-profile table stored as BF16 pairs (FP32 accumulate).
  * nufft_sigma: oversampling of the range-profile grid (default 2.0).
  * nufft_w: interpolation taps (even, 4..12; default 6).
- * tile_u: k_z bins per back-projection block (8 or 16; 0 = default 16). */
+ * tile_u: k_z bins per back-projection block (8, 16, 20 or 24; 0 = chosen
+ *         from n_pad).
+ * block_config: back-projection block shape (0 = default; 1 = 8-channel chunks,
+ *         3 blocks per SM; 2 = 16-channel chunks, 2 blocks per SM). */
 typedef struct {
     int precision;
     double nufft_sigma;
     int nufft_w;
     int tile_u;
-    int reserved[8];
+    int block_config;
+    int reserved[7];
 } pl_options;
 
 typedef struct pl_plan pl_plan;
@@ -164,7 +168,9 @@ pl_status pl_plan_get_info(const pl_plan *plan, pl_info *info);
 /* Device pointer and size of an intermediate buffer, valid until the plan is
  * destroyed (for inspection and tests):
  *  PL_STAGE_ZFFT        -> spectrum S, complex64 [n_chan][n_pad][n_f]
- *  PL_STAGE_RANGE_TABLE -> table b, complex64 (or bf16 pairs) [n_chan][L][n_pad]
+ *  PL_STAGE_RANGE_TABLE -> table b, [n_chan][L][ceil(n_pad/2)] rows of k_z bin pairs
+ *                          {re_u, re_u+1, im_u, im_u+1} (float32, or bfloat16 when
+ *                          precision = 1)
  *  PL_STAGE_BACKPROJECT -> image spectrum G, complex64 [n_pad][ny][nx] */
 pl_status pl_plan_workspace(pl_plan *plan, int stage, void **dev_ptr, size_t *bytes);
 

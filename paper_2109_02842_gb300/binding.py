@@ -43,7 +43,7 @@ class PlGrid(ctypes.Structure):
 
 class PlOptions(ctypes.Structure):
     _fields_ = [("precision", _I), ("nufft_sigma", _D), ("nufft_w", _I), ("tile_u", _I),
-                ("reserved", _I * 8)]
+                ("block_config", _I), ("reserved", _I * 7)]
 
 
 class PlInfo(ctypes.Structure):
@@ -140,7 +140,8 @@ class Plan:
 
     def __init__(self, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad=0,
                  pair_tx=None, pair_rx=None, radius=0.0, n_sections=0, chord_len=0.0,
-                 elem_section=None, precision=0, nufft_sigma=0.0, nufft_w=0, tile_u=0):
+                 elem_section=None, precision=0, nufft_sigma=0.0, nufft_w=0, tile_u=0,
+                 block_config=0):
         lib = load()
         self._keep = []
         exy = _f64(elem_xy).reshape(-1, 2)
@@ -157,7 +158,8 @@ class Plan:
         g = PlGrid(float(grid["x0"]), float(grid["dx"]), float(grid["y0"]), float(grid["dy"]),
                    float(grid["z0"]), float(grid["dz"]), int(grid["nx"]), int(grid["ny"]),
                    int(grid["nz"]))
-        opt = PlOptions(int(precision), float(nufft_sigma), int(nufft_w), int(tile_u))
+        opt = PlOptions(int(precision), float(nufft_sigma), int(nufft_w), int(tile_u),
+                        int(block_config))
         h = _P()
         _check(lib.pl_plan_create(ctypes.byref(h), geom, scan, freqs, g, opt))
         self._h = h
@@ -226,10 +228,12 @@ class Plan:
         if stage == PL_STAGE_ZFFT:
             shape = (i["n_chan"], i["n_pad"], i["n_f"])
         elif stage == PL_STAGE_RANGE_TABLE:
-            shape = (i["n_chan"], i["table_len"], i["n_pad"])
-            if nbytes.value == np.prod(shape) * 4:   # BF16 pairs
-                raw = torch.as_tensor(_DevArray(ptr.value, shape + (2,), "<i2"), device="cuda")
+            # rows of planar bin pairs {re_u, re_u+1, im_u, im_u+1}
+            shape = (i["n_chan"], i["table_len"], (i["n_pad"] + 1) // 2, 4)
+            if nbytes.value == np.prod(shape) * 2:   # BF16
+                raw = torch.as_tensor(_DevArray(ptr.value, shape, "<i2"), device="cuda")
                 return raw.view(torch.bfloat16)
+            return torch.as_tensor(_DevArray(ptr.value, shape, "<f4"), device="cuda")
         else:
             shape = (i["n_pad"], i["ny"], i["nx"])
         return torch.as_tensor(_DevArray(ptr.value, shape, "<c8"), device="cuda")

@@ -1,25 +1,38 @@
 // Back-projection, step (8b) / (19b) of the paper, with the coherent sum over
 // every channel (all sections) and the k_z tile of one block:
 //
-//   G_u(x,y) = sum_c  h e^{j kappa_c,u a_c(x,y)}  sum_{t<w} phi(a_c - l_{i0+t}) b_c[i0+t][u]
+//   G_u(x,y) = sum_c  e^{j kappa_c,u a_c(x,y)}  sum_{t<w} phi(a_c - l_{i0+t}) b_c[i0+t][u]
 //
 // a_c = rho (monostatic) or rho_T + rho_R (multistatic), phi the ES kernel on
-// the table grid l_i = l0 + i h (setup.cu explains the factorisation).
+// the table grid l_i = l0 + i h (setup.cu explains the factorisation; the
+// table already carries the factor h).
 //
-// Block = 16 x 16 pixels x `UT` consecutive k_z bins; thread = one pixel with
-// UT complex accumulators in registers. Channels are processed in chunks of
-// CC. For each chunk the block
-//  1. forms, in FP64, the range a_c* of the tile centre for every channel and
-//     the first table row i_lo of the R-row window that covers the tile;
-//  2. stages b_c[i_lo .. i_lo+R)[u0 .. u0+UT) in shared memory, multiplied by
-//     E_c,u = h e^{j kappa_c,u a_c*} -- the only place the large phase
-//     kappa a (up to ~2e3 rad) is needed, so it is formed and range-reduced
-//     in FP64 once per (block, channel, bin);
-//  3. per pixel forms the small offset delta = a_c - a_c* in FP32 without
-//     cancellation (difference of squares against the tile centre), the tap
-//     weights once, and then for each bin one w-tap interpolation, the
-//     residual carrier e^{j kappa_c,u delta} (|phase| < ~60 rad, FP32) and a
-//     complex multiply-accumulate.
+// Block = (16 PX) x 16 pixels x UT consecutive k_z bins; thread = PX
+// x-adjacent pixels with their UT bins in registers. With PX = 2 the two
+// pixels' table windows differ by at most one row (the plan checks that the
+// range step between neighbours is below h), so the thread loads w + 1 taps
+// once per bin pair and uses them for both pixels: 1.75 instead of 3 shared
+// 128-bit loads per update, which is what bounds this kernel (each such load
+// costs a warp four shared-memory wavefronts). Channels are processed in chunks of CC, with the
+// table window of chunk k+1 copied into shared memory (cp.async, double
+// buffered) while chunk k is computed. Per chunk:
+//  * the plan-time geometry of (tile, channel) gives the range a* of the tile
+//    centre as a float pair and the first row i_lo of the R-row window;
+//  * phi_c,u = kappa_c,u a* mod 2 pi is formed once per (block, channel, bin)
+//    as a float-float product with a two-constant reduction (Dekker /
+//    Cody-Waite; phases reach ~2e3 rad, the result is good to ~3e-7 rad);
+//  * per pixel: delta = a - a* in FP32 without cancellation (difference of
+//    squares against the tile centre), tap weights from per-tap polynomials
+//    of the ES kernel (fitted at plan time), then for each pair of bins:
+//    w 128-bit shared loads, the interpolation, the carrier
+//    e^{j (kappa_c,u delta + phi_c,u)} (|arg| < ~70 rad, FP32 sin/cos) and
+//    the complex multiply-accumulate, all as packed FP32x2 operations.
+//
+// The table holds bins in planar pairs {re_u, re_u+1, im_u, im_u+1}, so one
+// shared load feeds two bins and the complex multiply-accumulate needs no
+// shuffles: with X = (re_u, re_u+1), Y = (im_u, im_u+1) interpolated and
+// C, S the cosines and sines of the two carriers, Re += X.C - Y.S and
+// Im += X.S + Y.C as four FP32x2 FMAs into two FP32x2 accumulators.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -28,189 +41,315 @@
 namespace {
 
 constexpr int TX = 16, TY = 16;
-constexpr int CC = 16;             // channels per staged chunk
+constexpr float kTwoPiHi = 6.28318548202514648f;          // float(2 pi)
+constexpr float kTwoPiLo = -1.7484556e-7f;                // 2 pi - float(2 pi)
+constexpr float kInvTwoPi = 0.159154943091895336f;
 
-struct ChanGeo {
-    float dxt, dyt, rt;            // tile centre minus Tx position, its distance
-    float dxr, dyr, rr;            // same for Rx (multistatic)
-    float off;                     // a_c* - l_{i_lo} (m)
-    int ilo;
-};
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-template <int UT>
-__device__ __forceinline__ float2 load_tab(const void *tab, size_t idx, int bf16) {
-    if (bf16) {
-        const __nv_bfloat162 v = reinterpret_cast<const __nv_bfloat162 *>(tab)[idx];
-        return __bfloat1622float2(v);
-    }
-    return reinterpret_cast<const float2 *>(tab)[idx];
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// kappa * a mod 2 pi with kappa = kh + kl, a = ah + al (float pairs)
+__device__ __forceinline__ float phase_ff(float kh, float kl, float ah, float al) {
+    const float p = kh * ah;
+    float e = fmaf(kh, ah, -p);
+    e = fmaf(kh, al, e);
+    e = fmaf(kl, ah, e);
+    const float n = rintf(p * kInvTwoPi);
+    float r = fmaf(-n, kTwoPiHi, p);
+    r = fmaf(-n, kTwoPiLo, r);
+    return r + e;
 }
 
-template <int UT, int W>
-__global__ void __launch_bounds__(TX * TY)
-k_backproject(BpDesc p, const void *__restrict__ table, const double *__restrict__ ch_xy,
-              const double *__restrict__ kc, const float *__restrict__ kc_f,
-              float2 *__restrict__ G) {
-    constexpr int US = UT + 1;                         // padded row stride (float2)
-    extern __shared__ float2 smem[];
-    float2 *slab = smem;                               // [CC][R][US]
-    float2 *Es = slab + CC * p.R * US;                 // [CC][UT]
-    ChanGeo *geo = reinterpret_cast<ChanGeo *>(Es + CC * UT);
-    double *ac = reinterpret_cast<double *>(geo + CC);
+template <int UT, int W, int CC>
+struct BpSmem {
+    static constexpr int NP = UT / 2;
+    static constexpr int RS = NP + 1;                   // padded row stride (float4)
+    static size_t bytes(int R, int n_chan, int bf16) {
+        size_t s = 2 * (size_t)CC * R * RS * sizeof(float4);       // slab, 2 buffers
+        if (bf16) s += 2 * (size_t)CC * R * NP * sizeof(uint2);    // raw BF16 staging
+        s += 2 * (size_t)CC * sizeof(TileGeo);                      // geometry, 2 buffers
+        s += (size_t)CC * NP * sizeof(float4);                     // (kc, kc, phi, phi)
+        s += (size_t)n_chan * sizeof(int);                          // i_lo of every channel
+        return s;
+    }
+};
+
+template <int UT, int W, int CC, int MINB, int PX>
+__global__ void __launch_bounds__(TX * TY, MINB)
+k_backproject(BpDesc p, const void *__restrict__ table, const TileGeo *__restrict__ tgeo,
+              const float2 *__restrict__ kc_hl, float2 *__restrict__ G) {
+    using SM = BpSmem<UT, W, CC>;
+    constexpr int NP = SM::NP;
+    constexpr int RS = SM::RS;
+    constexpr int ND = W + 2;                           // polynomial coefficients per tap
+    constexpr int WT = W + PX - 1;                      // taps loaded per bin pair
+    constexpr int TXP = TX * PX;                        // pixels per block along x
+    extern __shared__ float4 smem4[];
+    float4 *slab = smem4;                                       // [2][CC][R][RS]
+    uint2 *raw = reinterpret_cast<uint2 *>(slab + 2 * CC * p.R * RS);   // [2][CC][R][NP]
+    TileGeo *geo = reinterpret_cast<TileGeo *>(p.bf16 ? (void *)(raw + 2 * CC * p.R * NP)
+                                                        : (void *)raw);  // [2][CC]
+    float4 *kphi = reinterpret_cast<float4 *>(geo + 2 * CC);          // [CC][NP]
+    int *ilo_s = reinterpret_cast<int *>(kphi + CC * NP);             // [n_chan]
 
     const int lx = threadIdx.x % TX;
     const int ly = threadIdx.x / TX;
-    const int ix_lo = blockIdx.x * TX;
-    const int iy_lo = blockIdx.y * TY;
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
     const int u0 = blockIdx.z * UT;
-    const int ix = ix_lo + lx;
-    const int iy = iy_lo + ly;
-    // tile centre (continuous) and this pixel's offset from it
-    const double xc = p.x0 + (ix_lo + 0.5 * (TX - 1)) * p.dx;
-    const double yc = p.y0 + (iy_lo + 0.5 * (TY - 1)) * p.dy;
-    const float ddx = (float)((lx - 0.5 * (TX - 1)) * p.dx);
+    const int ix = blockIdx.x * TXP + PX * lx;
+    const int iy = blockIdx.y * TY + ly;
+    const int np2 = (p.n_pad + 1) / 2;
+    const int pair0 = u0 / 2;
+    float ddx[PX];
+#pragma unroll
+    for (int k = 0; k < PX; ++k) ddx[k] = (float)((PX * lx + k - 0.5 * (TXP - 1)) * p.dx);
     const float ddy = (float)((ly - 0.5 * (TY - 1)) * p.dy);
-    const double halfrows = 0.5 * (p.R - 1);
+    const TileGeo *tg = tgeo + (size_t)tile * p.n_chan;
+    const size_t row_pairs = (size_t)np2;
 
-    float kcu[UT];
-    float2 acc[UT];
-#pragma unroll
-    for (int u = 0; u < UT; ++u) {
-        kcu[u] = (u0 + u < p.n_pad) ? kc_f[u0 + u] : 0.0f;
-        acc[u] = make_float2(0.f, 0.f);
-    }
+    for (int c = threadIdx.x; c < p.n_chan; c += blockDim.x) ilo_s[c] = tg[c].ilo;
+    __syncthreads();
 
-    for (int c0 = 0; c0 < p.n_chan; c0 += CC) {
+    // issue the asynchronous copies of chunk `ck` into buffer `buf`
+    auto issue = [&](int ck, int buf) {
+        const int c0 = ck * CC;
         const int ncc = min(CC, p.n_chan - c0);
-        __syncthreads();
-        if (threadIdx.x < ncc) {
-            const int c = c0 + threadIdx.x;
-            const double dxt = xc - ch_xy[4 * c + 0], dyt = yc - ch_xy[4 * c + 1];
-            const double rt = sqrt(dxt * dxt + dyt * dyt);
-            double a = rt;
-            ChanGeo g;
-            g.dxt = (float)dxt; g.dyt = (float)dyt; g.rt = (float)rt;
-            g.dxr = g.dyr = g.rr = 0.f;
-            if (p.mode == 1) {
-                const double dxr = xc - ch_xy[4 * c + 2], dyr = yc - ch_xy[4 * c + 3];
-                const double rr = sqrt(dxr * dxr + dyr * dyr);
-                a += rr;
-                g.dxr = (float)dxr; g.dyr = (float)dyr; g.rr = (float)rr;
-            }
-            int ilo = (int)floor((a - p.l0) / p.h - halfrows);
-            ilo = max(0, min(ilo, p.L - p.R));
-            g.ilo = ilo;
-            g.off = (float)(a - (p.l0 + ilo * p.h));
-            geo[threadIdx.x] = g;
-            ac[threadIdx.x] = a;
+        const int per_c = p.R * NP;
+        for (int idx = threadIdx.x; idx < ncc * per_c; idx += blockDim.x) {
+            const int cl = idx / per_c;
+            const int rem = idx - cl * per_c;
+            const int r = rem / NP;
+            const int q = rem - r * NP;
+            const int pair = min(pair0 + q, np2 - 1);   // bins past N_p are masked by kc = 0
+            const size_t ti = ((size_t)(c0 + cl) * p.L + ilo_s[c0 + cl] + r) * row_pairs + pair;
+            if (p.bf16)
+                cp_async8(raw + ((buf * CC + cl) * p.R + r) * NP + q,
+                          reinterpret_cast<const uint2 *>(table) + ti);
+            else
+                cp_async16(slab + ((buf * CC + cl) * p.R + r) * RS + q,
+                           reinterpret_cast<const float4 *>(table) + ti);
+        }
+        constexpr int G4 = sizeof(TileGeo) / 16;
+        for (int idx = threadIdx.x; idx < ncc * G4; idx += blockDim.x)
+            cp_async16(reinterpret_cast<float4 *>(geo + buf * CC) + idx,
+                       reinterpret_cast<const float4 *>(tg + c0) + idx);
+        cp_commit();
+    };
+
+    float2 aRe[PX][NP], aIm[PX][NP];
+#pragma unroll
+    for (int k = 0; k < PX; ++k)
+#pragma unroll
+        for (int q = 0; q < NP; ++q) aRe[k][q] = aIm[k][q] = f2(0.f, 0.f);
+
+    const int n_chunks = (p.n_chan + CC - 1) / CC;
+    issue(0, 0);
+    for (int ck = 0; ck < n_chunks; ++ck) {
+        const int buf = ck & 1;
+        const int ncc = min(CC, p.n_chan - ck * CC);
+        if (ck + 1 < n_chunks) {
+            issue(ck + 1, buf ^ 1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < ncc * UT; idx += blockDim.x) {
-            const int cl = idx / UT;
-            const int u = idx - cl * UT;
-            float2 e = make_float2(0.f, 0.f);
-            if (u0 + u < p.n_pad) {
-                const double ph = kc[u0 + u] * ac[cl];
-                const double red = ph - PL_TWO_PI * rint(ph * (1.0 / PL_TWO_PI));
-                float s, co;
-                sincosf((float)red, &s, &co);
-                e = make_float2((float)p.h * co, (float)p.h * s);
-            }
-            Es[idx] = e;
+        // per (channel, bin pair): kappa and the reference phase
+        for (int idx = threadIdx.x; idx < ncc * NP; idx += blockDim.x) {
+            const int cl = idx / NP;
+            const int q = idx - cl * NP;
+            const TileGeo &g = geo[buf * CC + cl];
+            const int u = u0 + 2 * q;
+            const float2 k0 = u < p.n_pad ? kc_hl[u] : f2(0.f, 0.f);
+            const float2 k1 = u + 1 < p.n_pad ? kc_hl[u + 1] : f2(0.f, 0.f);
+            kphi[cl * NP + q] = make_float4(k0.x, k1.x, phase_ff(k0.x, k0.y, g.a_hi, g.a_lo),
+                                            phase_ff(k1.x, k1.y, g.a_hi, g.a_lo));
         }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < ncc * p.R * UT; idx += blockDim.x) {
-            const int cl = idx / (p.R * UT);
-            const int rem = idx - cl * p.R * UT;
-            const int r = rem / UT;
-            const int u = rem - r * UT;
-            float2 v = make_float2(0.f, 0.f);
-            if (u0 + u < p.n_pad) {
-                const size_t ti = ((size_t)(c0 + cl) * p.L + geo[cl].ilo + r) * p.n_pad + u0 + u;
-                v = cmul(load_tab<UT>(table, ti, p.bf16), Es[cl * UT + u]);
+        if (p.bf16) {
+            for (int idx = threadIdx.x; idx < ncc * p.R * NP; idx += blockDim.x) {
+                const int cl = idx / (p.R * NP);
+                const int rem = idx - cl * p.R * NP;
+                const int r = rem / NP;
+                const int q = rem - r * NP;
+                const uint2 v = raw[((buf * CC + cl) * p.R + r) * NP + q];
+                const float2 re = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.x));
+                const float2 im = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.y));
+                slab[((buf * CC + cl) * p.R + r) * RS + q] = make_float4(re.x, re.y, im.x, im.y);
             }
-            slab[(cl * p.R + r) * US + u] = v;
         }
         __syncthreads();
 
+        const float4 *slab_b = slab + buf * CC * p.R * RS;
         for (int cl = 0; cl < ncc; ++cl) {
-            const ChanGeo g = geo[cl];
-            // delta = a - a* from rho^2 - rho*^2 = d(2D + d), no cancellation
-            float ex = g.dxt + ddx, ey = g.dyt + ddy;
-            float num = ddx * (2.0f * g.dxt + ddx) + ddy * (2.0f * g.dyt + ddy);
-            float delta = num / (sqrtf(ex * ex + ey * ey) + g.rt);
-            if (p.mode == 1) {
-                ex = g.dxr + ddx; ey = g.dyr + ddy;
-                num = ddx * (2.0f * g.dxr + ddx) + ddy * (2.0f * g.dyr + ddy);
-                delta += num / (sqrtf(ex * ex + ey * ey) + g.rr);
+            const TileGeo g = geo[buf * CC + cl];
+            float delta[PX], pos[PX];
+            int i0[PX];
+#pragma unroll
+            for (int k = 0; k < PX; ++k) {
+                // delta = a - a* from rho^2 - rho*^2 = d (2 D + d): no cancellation
+                float ex = g.dxt + ddx[k], ey = g.dyt + ddy;
+                float num = fmaf(ddx[k], 2.0f * g.dxt + ddx[k], ddy * (2.0f * g.dyt + ddy));
+                float r2 = fmaf(ex, ex, ey * ey);
+                float dl = num * __frcp_rn(fmaf(r2, rsqrtf(r2), g.rt));
+                if (p.mode == 1) {
+                    ex = g.dxr + ddx[k]; ey = g.dyr + ddy;
+                    num = fmaf(ddx[k], 2.0f * g.dxr + ddx[k], ddy * (2.0f * g.dyr + ddy));
+                    r2 = fmaf(ex, ex, ey * ey);
+                    dl += num * __frcp_rn(fmaf(r2, rsqrtf(r2), g.rr));
+                }
+                delta[k] = dl;
+                pos[k] = (dl + g.off) * p.inv_h;
+                i0[k] = (int)ceilf(pos[k] - 0.5f * W);
             }
-            const float pos = (delta + g.off) * p.inv_h;
-            int i0 = (int)ceilf(pos - 0.5f * W);
-            i0 = max(0, min(i0, p.R - W));
-            float wt[W];
+            int base = i0[0];
 #pragma unroll
-            for (int t = 0; t < W; ++t) wt[t] = es_kernel(pos - (float)(i0 + t), p.two_over_w, p.beta);
-            const float2 *row = slab + (cl * p.R + i0) * US;
+            for (int k = 1; k < PX; ++k) base = min(base, i0[k]);
+            base = max(0, min(base, p.R - WT));
+            // tap weights: per-tap polynomial in s = 2 (pos - i0 - (w/2 - 1)) - 1,
+            // placed at slot (i0 - base) + t of the WT loaded taps
+            float2 wt[PX][WT];
 #pragma unroll
-            for (int u = 0; u < UT; ++u) {
-                float2 v = make_float2(0.f, 0.f);
+            for (int k = 0; k < PX; ++k) {
+                const int o = min(max(i0[k] - base, 0), PX - 1);
+                const float s = fmaf(2.0f, pos[k] - (float)(base + o), -(float)(W - 1));
+                float w[W];
 #pragma unroll
                 for (int t = 0; t < W; ++t) {
-                    const float2 bv = row[t * US + u];
-                    v.x = fmaf(wt[t], bv.x, v.x);
-                    v.y = fmaf(wt[t], bv.y, v.y);
+                    float acc = p.coef[t][ND - 1];
+#pragma unroll
+                    for (int d = ND - 2; d >= 0; --d) acc = fmaf(acc, s, p.coef[t][d]);
+                    w[t] = acc;
                 }
-                float s, co;
-                __sincosf(kcu[u] * delta, &s, &co);
-                acc[u].x = fmaf(v.x, co, fmaf(-v.y, s, acc[u].x));
-                acc[u].y = fmaf(v.x, s, fmaf(v.y, co, acc[u].y));
+#pragma unroll
+                for (int t = 0; t < WT; ++t) {
+                    float v = 0.f;
+#pragma unroll
+                    for (int oo = 0; oo < PX; ++oo)
+                        if (t - oo >= 0 && t - oo < W && o == oo) v = w[t - oo];
+                    wt[k][t] = f2(v, v);
+                }
+            }
+            const float4 *row = slab_b + (cl * p.R + base) * RS;
+            const float4 *kp = kphi + cl * NP;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                float2 X[PX], Y[PX];
+#pragma unroll
+                for (int k = 0; k < PX; ++k) X[k] = Y[k] = f2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < WT; ++t) {
+                    const float4 b = row[t * RS + q];
+#pragma unroll
+                    for (int k = 0; k < PX; ++k) {
+                        X[k] = __ffma2_rn(wt[k][t], f2(b.x, b.y), X[k]);
+                        Y[k] = __ffma2_rn(wt[k][t], f2(b.z, b.w), Y[k]);
+                    }
+                }
+                const float4 kk = kp[q];
+#pragma unroll
+                for (int k = 0; k < PX; ++k) {
+                    const float2 arg = __ffma2_rn(f2(kk.x, kk.y), f2(delta[k], delta[k]),
+                                                  f2(kk.z, kk.w));
+                    float s0, c0, s1, c1;
+                    __sincosf(arg.x, &s0, &c0);
+                    __sincosf(arg.y, &s1, &c1);
+                    const float2 C = f2(c0, c1), S = f2(s0, s1), nS = f2(-s0, -s1);
+                    aRe[k][q] = __ffma2_rn(Y[k], nS, __ffma2_rn(X[k], C, aRe[k][q]));
+                    aIm[k][q] = __ffma2_rn(Y[k], C, __ffma2_rn(X[k], S, aIm[k][q]));
+                }
             }
         }
+        __syncthreads();
     }
 
-    if (ix < p.nx && iy < p.ny) {
+    if (iy < p.ny) {
         const size_t plane = (size_t)p.nx * p.ny;
-        const size_t pix = (size_t)iy * p.nx + ix;
 #pragma unroll
-        for (int u = 0; u < UT; ++u)
-            if (u0 + u < p.n_pad) G[(u0 + u) * plane + pix] = acc[u];
+        for (int k = 0; k < PX; ++k) {
+            if (ix + k >= p.nx) continue;
+            const size_t pix = (size_t)iy * p.nx + ix + k;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const int u = u0 + 2 * q;
+                if (u < p.n_pad) G[u * plane + pix] = f2(aRe[k][q].x, aIm[k][q].x);
+                if (u + 1 < p.n_pad) G[(u + 1) * plane + pix] = f2(aRe[k][q].y, aIm[k][q].y);
+            }
+        }
     }
 }
 
-template <int UT, int W>
-cudaError_t launch_t(const BpDesc &p, const void *table, const double *ch_xy, const double *kc,
-                     const float *kc_f, float2 *G, cudaStream_t st) {
-    const size_t smem = (size_t)CC * p.R * (UT + 1) * sizeof(float2) +
-                        (size_t)CC * UT * sizeof(float2) + CC * sizeof(ChanGeo) +
-                        CC * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_backproject<UT, W>,
+template <int UT, int W, int CC, int MINB, int PX>
+cudaError_t launch_t(const BpDesc &p, const void *table, const TileGeo *tgeo, const float2 *kc_hl,
+                     float2 *G, cudaStream_t st) {
+    const size_t smem = BpSmem<UT, W, CC>::bytes(p.R, p.n_chan, p.bf16);
+    cudaError_t e = cudaFuncSetAttribute(k_backproject<UT, W, CC, MINB, PX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.n_pad + UT - 1) / UT);
-    k_backproject<UT, W><<<grid, TX * TY, smem, st>>>(p, table, ch_xy, kc, kc_f, G);
+    dim3 grid((p.nx + TX * PX - 1) / (TX * PX), (p.ny + TY - 1) / TY, (p.n_pad + UT - 1) / UT);
+    k_backproject<UT, W, CC, MINB, PX><<<grid, TX * TY, smem, st>>>(p, table, tgeo, kc_hl, G);
     return cudaGetLastError();
 }
 
-template <int UT>
-cudaError_t launch_w(const BpDesc &p, const void *table, const double *ch_xy, const double *kc,
-                     const float *kc_f, float2 *G, cudaStream_t st) {
+// Block configurations: k_z bins per block (UT), channels per staged chunk
+// (CC), resident blocks per SM (MINB) and pixels per thread (PX).
+//   block_config 1: CC = 8,  3 blocks/SM (80 registers per thread), PX = 1
+//   block_config 2: CC = 16, 2 blocks/SM (128 registers per thread), PX = 1
+//   block_config 3: CC = 8,  2 blocks/SM, PX = 2 (two pixels share the taps)
+template <int UT, int CC, int MINB, int PX>
+cudaError_t launch_w(const BpDesc &p, const void *table, const TileGeo *tgeo, const float2 *kc_hl,
+                     float2 *G, cudaStream_t st) {
     switch (p.w) {
-        case 4: return launch_t<UT, 4>(p, table, ch_xy, kc, kc_f, G, st);
-        case 6: return launch_t<UT, 6>(p, table, ch_xy, kc, kc_f, G, st);
-        case 8: return launch_t<UT, 8>(p, table, ch_xy, kc, kc_f, G, st);
-        case 10: return launch_t<UT, 10>(p, table, ch_xy, kc, kc_f, G, st);
-        case 12: return launch_t<UT, 12>(p, table, ch_xy, kc, kc_f, G, st);
+        case 4: return launch_t<UT, 4, CC, MINB, PX>(p, table, tgeo, kc_hl, G, st);
+        case 6: return launch_t<UT, 6, CC, MINB, PX>(p, table, tgeo, kc_hl, G, st);
+        case 8: return launch_t<UT, 8, CC, MINB, PX>(p, table, tgeo, kc_hl, G, st);
+        case 10: return launch_t<UT, 10, 8, 2, 1>(p, table, tgeo, kc_hl, G, st);
+        case 12: return launch_t<UT, 12, 8, 2, 1>(p, table, tgeo, kc_hl, G, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
+template <int UT>
+cudaError_t launch_u(const BpDesc &p, const void *table, const TileGeo *tgeo, const float2 *kc_hl,
+                     float2 *G, cudaStream_t st) {
+    if (p.block_config == 2) return launch_w<UT, 16, 2, 1>(p, table, tgeo, kc_hl, G, st);
+    if (p.block_config == 3) return launch_w<UT, 8, 2, 2>(p, table, tgeo, kc_hl, G, st);
+    return launch_w<UT, 8, 3, 1>(p, table, tgeo, kc_hl, G, st);
+}
+
 }  // namespace
 
-int backproject_tile_x() { return TX; }
+int backproject_tile_x(int block_config) { return block_config == 3 ? 2 * TX : TX; }
 int backproject_tile_y() { return TY; }
 
-cudaError_t launch_backproject(const BpDesc &p, const void *table, const double *ch_xy,
-                               const double *kc, const float *kc_f, float2 *G, cudaStream_t st) {
-    if (p.tile_u == 8) return launch_w<8>(p, table, ch_xy, kc, kc_f, G, st);
-    return launch_w<16>(p, table, ch_xy, kc, kc_f, G, st);
+size_t backproject_smem_bytes(int R, int tile_u, int n_chan, int bf16, int block_config) {
+    const int CC = block_config == 2 ? 16 : 8;   // configs 1 and 3 stage 8 channels
+    const int np = tile_u / 2;
+    size_t s = 2 * (size_t)CC * R * (np + 1) * sizeof(float4);
+    if (bf16) s += 2 * (size_t)CC * R * np * sizeof(uint2);
+    s += 2 * (size_t)CC * sizeof(TileGeo) + (size_t)CC * np * sizeof(float4);
+    s += (size_t)n_chan * sizeof(int);
+    return s;
+}
+
+cudaError_t launch_backproject(const BpDesc &p, const void *table, const TileGeo *tgeo,
+                               const float2 *kc_hl, float2 *G, cudaStream_t st) {
+    switch (p.tile_u) {
+        case 8: return launch_u<8>(p, table, tgeo, kc_hl, G, st);
+        case 16: return launch_u<16>(p, table, tgeo, kc_hl, G, st);
+        case 20: return launch_u<20>(p, table, tgeo, kc_hl, G, st);
+        case 24: return launch_u<24>(p, table, tgeo, kc_hl, G, st);
+        default: return cudaErrorInvalidValue;
+    }
 }

@@ -15,10 +15,11 @@ cudaError_t launch_dft_strided(const float2 *in, float2 *out, int batch, int n_i
                                int out_rows, const float2 *T, float scale, cudaStream_t st);
 
 // ---- setup.cu --------------------------------------------------------------
-// Per k_z bin: kappa range over propagating frequencies; kc = centre (double),
-// kspan = kappa_max - kappa_min (0 when every frequency is evanescent).
+// Per k_z bin: kappa range over propagating frequencies; kc = centre (double
+// and as a float pair hi + lo), kspan = kappa_max - kappa_min (0 when every
+// frequency is evanescent).
 cudaError_t launch_setup_kz(int mode, int n_pad, double dz, int n_f, const double *k,
-                            double *kc, float *kc_f, double *kspan, cudaStream_t st);
+                            double *kc, float2 *kc_hl, double *kspan, cudaStream_t st);
 // Per (k_z, f): spreading position (fine cells) and source factor alpha.
 cudaError_t launch_setup_sources(const NufftDesc &d, double dz, const double *k,
                                  const double *kc, const double *gl_x, const double *gl_w,
@@ -42,6 +43,17 @@ cudaError_t launch_range_table(const NufftDesc &d, const float2 *S, const float2
                                void *table, int bf16, cudaStream_t st);
 
 // ---- backproject.cu ------------------------------------------------------------
+// Plan-time geometry of one (pixel tile, channel): offsets of the tile centre
+// from the Tx / Rx position and their distances (FP32), the tile-centre range
+// a* as a float pair, the first table row i_lo of the R-row window covering the
+// tile, and off = a* - l_{i_lo}. 48 bytes (three 16-byte copies).
+struct TileGeo {
+    float dxt, dyt, rt, dxr;
+    float dyr, rr, off, a_hi;
+    float a_lo;
+    int ilo;
+    float pad0, pad1;
+};
 struct BpDesc {
     int mode, n_chan, n_pad, L, R;
     int nx, ny;
@@ -50,11 +62,20 @@ struct BpDesc {
     float inv_h;
     float beta, two_over_w;
     int w, tile_u;
+    int block_config;     // 1: 8-channel chunks, 3 blocks/SM; 2: 16-channel chunks, 2 blocks/SM;
+                          // 3: 8-channel chunks, 2 blocks/SM, two pixels per thread
+    int tile_px;          // pixels per block along x (16 or 32)
     int bf16;
+    // ES kernel tap weights as polynomials: weight_t(s) = sum_d coef[t][d] s^d,
+    // s in (-1, 1] the offset of the pixel inside its first table cell
+    float coef[12][14];
 };
-cudaError_t launch_backproject(const BpDesc &p, const void *table, const double *ch_xy,
-                               const double *kc, const float *kc_f, float2 *G, cudaStream_t st);
-int backproject_tile_x();
+size_t backproject_smem_bytes(int R, int tile_u, int n_chan, int bf16, int block_config);
+cudaError_t launch_backproject(const BpDesc &p, const void *table, const TileGeo *tgeo,
+                               const float2 *kc_hl, float2 *G, cudaStream_t st);
+cudaError_t launch_setup_tile_geo(const BpDesc &p, const double *ch_xy, TileGeo *tgeo,
+                                  cudaStream_t st);
+int backproject_tile_x(int block_config);
 int backproject_tile_y();
 
 // ---- synth.cu ----------------------------------------------------------------

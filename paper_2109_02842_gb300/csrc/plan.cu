@@ -60,6 +60,39 @@ void gauss_legendre01(int n, std::vector<double> &x, std::vector<double> &w) {
     }
 }
 
+// Chebyshev interpolation of ES tap t on s in [-1, 1] at D+1 nodes, returned
+// as monomial coefficients in s (textbook construction, double precision).
+void es_tap_polynomial(int W, double beta, int t, int D, float *mono) {
+    const int n = D + 1;
+    auto es = [&](double x) {
+        const double z = 2.0 * x / W;
+        const double q = 1.0 - z * z;
+        return q > 0.0 ? std::exp(beta * (std::sqrt(q) - 1.0)) : 0.0;
+    };
+    std::vector<double> fx(n), c(n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        const double s = std::cos(M_PI * (j + 0.5) / n);
+        fx[j] = es(0.5 * (s + 1.0) + 0.5 * W - 1.0 - t);
+    }
+    for (int k = 0; k < n; ++k) {
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) acc += fx[j] * std::cos(M_PI * k * (j + 0.5) / n);
+        c[k] = 2.0 * acc / n;
+    }
+    c[0] *= 0.5;
+    std::vector<std::vector<double>> T(n, std::vector<double>(n, 0.0));
+    T[0][0] = 1.0;
+    if (n > 1) T[1][1] = 1.0;
+    for (int k = 1; k + 1 < n; ++k)
+        for (int i = 0; i < n; ++i)
+            T[k + 1][i] = (i > 0 ? 2.0 * T[k][i - 1] : 0.0) - T[k - 1][i];
+    for (int i = 0; i < n; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k) acc += c[k] * T[k][i];
+        mono[i] = (float)acc;
+    }
+}
+
 bool smooth_plan(int n, FftPlan &p) {
     p.n = n;
     p.n_stages = 0;
@@ -102,11 +135,14 @@ struct pl_plan {
     pl_grid grid{};
     int precision = 0;
     int tile_u = 16;
+    int block_config = 1;
     int device = 0;
     // nufft
     NufftDesc nd{};
     double sigma = 2.0;
     int R = 0;
+    float coef[12][14] = {};
+    BpDesc bp{};
     // transforms
     bool fwd_fft = true, inv_fft = true;
     int inv_off = 0;
@@ -114,7 +150,9 @@ struct pl_plan {
     // device memory
     double *d_chxy = nullptr, *d_k = nullptr, *d_kc = nullptr, *d_kspan = nullptr;
     double *d_glx = nullptr, *d_glw = nullptr;
-    float *d_kcf = nullptr, *d_xg = nullptr, *d_dec = nullptr;
+    float *d_xg = nullptr, *d_dec = nullptr;
+    float2 *d_kchl = nullptr;
+    TileGeo *d_tgeo = nullptr;
     float2 *d_alpha = nullptr, *d_twz = nullptr, *d_twfine = nullptr;
     float2 *d_Tfwd = nullptr, *d_Tinv = nullptr;
     float2 *d_S = nullptr, *d_G = nullptr;
@@ -130,7 +168,7 @@ struct pl_plan {
     size_t ev_next = 0;
 
     ~pl_plan() {
-        void *ptrs[] = {d_chxy, d_k,    d_kc,   d_kspan, d_glx,  d_glw,     d_kcf,
+        void *ptrs[] = {d_chxy, d_k,    d_kc,   d_kspan, d_glx,  d_glw,     d_kchl, d_tgeo,
                         d_xg,   d_dec,  d_alpha, d_twz,  d_twfine, d_Tfwd, d_Tinv,
                         d_S,    d_G,    d_table, d_echo_in, d_img_out};
         for (void *p : ptrs)
@@ -184,18 +222,47 @@ pl_status validate(const pl_geometry *g, const pl_scan *s, const pl_freqs *f, co
     return PL_OK;
 }
 
+BpDesc make_bp(const pl_plan *P) {
+    const NufftDesc &d = P->nd;
+    BpDesc bp{};
+    bp.mode = P->mode;
+    bp.n_chan = P->C;
+    bp.n_pad = P->Np;
+    bp.L = d.L;
+    bp.R = P->R;
+    bp.nx = P->grid.nx;
+    bp.ny = P->grid.ny;
+    bp.x0 = P->grid.x0;
+    bp.dx = P->grid.dx;
+    bp.y0 = P->grid.y0;
+    bp.dy = P->grid.dy;
+    bp.h = d.h;
+    bp.l0 = d.l0;
+    bp.inv_h = (float)(1.0 / d.h);
+    bp.beta = d.beta;
+    bp.two_over_w = 2.0f / d.w;
+    bp.w = d.w;
+    bp.tile_u = P->tile_u;
+    bp.block_config = P->block_config;
+    bp.tile_px = backproject_tile_x(P->block_config);
+    bp.bf16 = P->precision == 1;
+    std::memcpy(bp.coef, P->coef, sizeof(bp.coef));
+    return bp;
+}
+
 pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const pl_freqs *f,
                      const pl_grid *gr, const pl_options *opt) {
     pl_options o{};
     if (opt) o = *opt;
     if (o.nufft_sigma == 0) o.nufft_sigma = 2.0;
     if (o.nufft_w == 0) o.nufft_w = 6;
-    if (o.tile_u == 0) o.tile_u = 16;
+
     if (!(o.nufft_sigma >= 1.2 && o.nufft_sigma <= 8.0))
         return fail(PL_ERR_ARG, "nufft_sigma must be in [1.2, 8]");
     if (o.nufft_w < 4 || o.nufft_w > 12 || (o.nufft_w & 1))
         return fail(PL_ERR_ARG, "nufft_w must be even, 4..12");
-    if (o.tile_u != 8 && o.tile_u != 16) return fail(PL_ERR_ARG, "tile_u must be 8 or 16");
+    if (o.tile_u != 0 && o.tile_u != 8 && o.tile_u != 16 && o.tile_u != 20 && o.tile_u != 24)
+        return fail(PL_ERR_ARG, "tile_u must be 0, 8, 16, 20 or 24");
     if (o.precision != 0 && o.precision != 1) return fail(PL_ERR_ARG, "precision must be 0 or 1");
 
     PL_CUDA(cudaGetDevice(&P->device), "cudaGetDevice");
@@ -209,6 +276,14 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     P->grid = *gr;
     P->precision = o.precision;
     P->tile_u = o.tile_u;
+    if (o.block_config < 0 || o.block_config > 3)
+        return fail(PL_ERR_ARG, "block_config must be 0, 1, 2 or 3");
+    P->block_config = o.block_config;
+    if (P->tile_u == 0) {   // fewest padded k_z bins; 20 only when it wastes less than 16
+        const int n = s->n_pad ? s->n_pad : s->n;
+        const int w16 = (n + 15) / 16 * 16 - n, w20 = (n + 19) / 20 * 20 - n;
+        P->tile_u = w20 < w16 ? 20 : 16;
+    }
     P->sigma = o.nufft_sigma;
 
     // channel positions (xT, yT, xR, yR)
@@ -228,13 +303,13 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     PL_CUDA(dalloc(&P->d_chxy, chxy.size(), ws), "cudaMalloc");
     PL_CUDA(dalloc(&P->d_k, k.size(), ws), "cudaMalloc");
     PL_CUDA(dalloc(&P->d_kc, P->Np, ws), "cudaMalloc");
-    PL_CUDA(dalloc(&P->d_kcf, P->Np, ws), "cudaMalloc");
+    PL_CUDA(dalloc(&P->d_kchl, P->Np, ws), "cudaMalloc");
     PL_CUDA(dalloc(&P->d_kspan, P->Np, ws), "cudaMalloc");
     PL_CUDA(cudaMemcpy(P->d_chxy, chxy.data(), chxy.size() * 8, cudaMemcpyHostToDevice), "copy");
     PL_CUDA(cudaMemcpy(P->d_k, k.data(), k.size() * 8, cudaMemcpyHostToDevice), "copy");
 
     cudaStream_t st = 0;
-    PL_CUDA(launch_setup_kz(P->mode, P->Np, P->dzs, P->M, P->d_k, P->d_kc, P->d_kcf,
+    PL_CUDA(launch_setup_kz(P->mode, P->Np, P->dzs, P->M, P->d_k, P->d_kc, P->d_kchl,
                             P->d_kspan, st), "setup_kz");
     std::vector<double> kspan(P->Np);
     PL_CUDA(cudaMemcpy(kspan.data(), P->d_kspan, P->Np * 8, cudaMemcpyDeviceToHost), "copy");
@@ -253,10 +328,17 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     // NUFFT geometry
     const int W = o.nufft_w;
     const double h = PL_TWO_PI / (o.nufft_sigma * kmax);
-    const int TX = backproject_tile_x(), TY = backproject_tile_y();
+    // two pixels per thread when x-neighbours are less than one table row
+    // apart in range (then their tap windows differ by at most one row)
+    const double da_step = (P->mode == 0 ? 1.0 : 2.0) * gr->dx;
+    const bool px2_ok = da_step < 0.999 * h && W <= 8;
+    if (P->block_config == 3 && !px2_ok)
+        return fail(PL_ERR_UNSUPPORTED, "block_config 3 needs an x step below the table step");
+    if (P->block_config == 0) P->block_config = px2_ok ? 3 : 1;
+    const int TX = backproject_tile_x(P->block_config), TY = backproject_tile_y();
     const double hs_pix = 0.5 * std::hypot((TX - 1) * gr->dx, (TY - 1) * gr->dy);
     const double hs = P->mode == 0 ? hs_pix : 2.0 * hs_pix;
-    P->R = (int)std::ceil(2.0 * hs / h) + W + 5;
+    P->R = (int)std::ceil(2.0 * hs / h) + W + (P->block_config == 3 ? 1 : 0) + 5;
     const int ntx = (gr->nx + TX - 1) / TX, nty = (gr->ny + TY - 1) / TY;
     const double rx0 = gr->x0, rx1 = gr->x0 + (ntx * TX - 1) * gr->dx;
     const double ry0 = gr->y0, ry1 = gr->y0 + (nty * TY - 1) * gr->dy;
@@ -290,6 +372,10 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     d.l0 = amin - h * (P->R + 2);
     if (range_table_smem_bytes(d) > 200 * 1024)
         return fail(PL_ERR_UNSUPPORTED, "range-profile table too long for shared memory");
+    if (P->C > 8192) return fail(PL_ERR_UNSUPPORTED, "more than 8192 channels");
+    if (backproject_smem_bytes(P->R, P->tile_u, P->C, P->precision, P->block_config) > 200 * 1024)
+        return fail(PL_ERR_UNSUPPORTED, "table window too tall for shared memory (grid too coarse)");
+    for (int tp = 0; tp < W; ++tp) es_tap_polynomial(W, (double)d.beta, tp, W + 1, P->coef[tp]);
 
     // plan-time tables
     std::vector<double> glx, glw;
@@ -330,9 +416,19 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
                 "dft_matrix_inv");
     }
 
+    // per (pixel tile, channel) geometry of the back-projection
+    P->bp = make_bp(P);
+    {
+        const int tpx = backproject_tile_x(P->block_config);
+        const size_t ntiles = (size_t)((gr->nx + tpx - 1) / tpx) * ((gr->ny + 15) / 16);
+        PL_CUDA(dalloc(&P->d_tgeo, ntiles * P->C, ws), "cudaMalloc");
+        PL_CUDA(launch_setup_tile_geo(P->bp, P->d_chxy, P->d_tgeo, st), "setup_tile_geo");
+    }
+
     // data workspace
     PL_CUDA(dalloc(&P->d_S, (size_t)P->C * P->Np * P->M, ws), "cudaMalloc");
-    P->table_bytes = (size_t)P->C * L * P->Np * (P->precision == 1 ? 4 : 8);
+    // table rows: k_z bins in planar pairs, N_p rounded up to even
+    P->table_bytes = (size_t)P->C * L * ((P->Np + 1) / 2) * (P->precision == 1 ? 8 : 16);
     ws += P->table_bytes;
     PL_CUDA(cudaMalloc(&P->d_table, P->table_bytes), "cudaMalloc");
     PL_CUDA(dalloc(&P->d_G, (size_t)P->Np * gr->nx * gr->ny, ws), "cudaMalloc");
@@ -369,28 +465,8 @@ pl_status run(pl_plan *P, const float2 *echo, float2 *image, cudaStream_t st) {
                                P->d_table, P->precision == 1, st), "range_table");
     PL_CUDA(mark(1, 1), "event");
     // a5: back-projection with the coherent channel sum, Eq. (8b)
-    BpDesc bp{};
-    bp.mode = P->mode;
-    bp.n_chan = P->C;
-    bp.n_pad = P->Np;
-    bp.L = d.L;
-    bp.R = P->R;
-    bp.nx = P->grid.nx;
-    bp.ny = P->grid.ny;
-    bp.x0 = P->grid.x0;
-    bp.dx = P->grid.dx;
-    bp.y0 = P->grid.y0;
-    bp.dy = P->grid.dy;
-    bp.h = d.h;
-    bp.l0 = d.l0;
-    bp.inv_h = (float)(1.0 / d.h);
-    bp.beta = d.beta;
-    bp.two_over_w = 2.0f / d.w;
-    bp.w = d.w;
-    bp.tile_u = P->tile_u;
-    bp.bf16 = P->precision == 1;
     PL_CUDA(mark(2, 0), "event");
-    PL_CUDA(launch_backproject(bp, P->d_table, P->d_chxy, P->d_kc, P->d_kcf, P->d_G, st),
+    PL_CUDA(launch_backproject(P->bp, P->d_table, P->d_tgeo, P->d_kchl, P->d_G, st),
             "backproject");
     PL_CUDA(mark(2, 1), "event");
     // a6: inverse transform over k_z, Eq. (9)

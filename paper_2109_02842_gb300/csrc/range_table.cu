@@ -13,7 +13,8 @@
 // One warp owns one (c, u) problem at a time and its fine grid in shared
 // memory; a block of 8 warps covers 16 consecutive k_z bins of one channel
 // and writes the [L][16] output panel as coalesced 128-byte rows of the
-// table b[c][i][u] (u fastest), the layout the back-projection stages.
+// table b[c][i][u] (u fastest, in planar pairs {re_u, re_u+1, im_u, im_u+1},
+// N_p rounded up to even), the layout the back-projection stages.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -93,20 +94,34 @@ k_range_table(NufftDesc d, const float2 *__restrict__ S, const float2 *__restric
     }
     __syncthreads();
 
-    const int nu = min(kUB, d.n_pad - u0);
+    // table rows hold k_z bins in planar pairs: {re_u, re_u+1, im_u, im_u+1}
+    const int np2 = (d.n_pad + 1) / 2;
+    const int p0 = u0 / 2;
+    const int npair = min(kUB / 2, np2 - p0);
     if (!bf16) {
-        float2 *b = reinterpret_cast<float2 *>(table) + (size_t)c * d.L * d.n_pad;
-        for (int idx = threadIdx.x; idx < d.L * kUB; idx += blockDim.x) {
-            const int i = idx / kUB;
-            const int ul = idx - i * kUB;
-            if (ul < nu) b[(size_t)i * d.n_pad + u0 + ul] = panel[idx];
+        float4 *b = reinterpret_cast<float4 *>(table) + (size_t)c * d.L * np2;
+        for (int idx = threadIdx.x; idx < d.L * (kUB / 2); idx += blockDim.x) {
+            const int i = idx / (kUB / 2);
+            const int pp = idx - i * (kUB / 2);
+            if (pp >= npair) continue;
+            const float2 a = panel[i * kUB + 2 * pp];
+            const float2 e = panel[i * kUB + 2 * pp + 1];
+            b[(size_t)i * np2 + p0 + pp] = make_float4(a.x, e.x, a.y, e.y);
         }
     } else {
-        __nv_bfloat162 *b = reinterpret_cast<__nv_bfloat162 *>(table) + (size_t)c * d.L * d.n_pad;
-        for (int idx = threadIdx.x; idx < d.L * kUB; idx += blockDim.x) {
-            const int i = idx / kUB;
-            const int ul = idx - i * kUB;
-            if (ul < nu) b[(size_t)i * d.n_pad + u0 + ul] = __float22bfloat162_rn(panel[idx]);
+        uint2 *b = reinterpret_cast<uint2 *>(table) + (size_t)c * d.L * np2;
+        for (int idx = threadIdx.x; idx < d.L * (kUB / 2); idx += blockDim.x) {
+            const int i = idx / (kUB / 2);
+            const int pp = idx - i * (kUB / 2);
+            if (pp >= npair) continue;
+            const float2 a = panel[i * kUB + 2 * pp];
+            const float2 e = panel[i * kUB + 2 * pp + 1];
+            __nv_bfloat162 re = __floats2bfloat162_rn(a.x, e.x);
+            __nv_bfloat162 im = __floats2bfloat162_rn(a.y, e.y);
+            uint2 v;
+            v.x = *reinterpret_cast<unsigned *>(&re);
+            v.y = *reinterpret_cast<unsigned *>(&im);
+            b[(size_t)i * np2 + p0 + pp] = v;
         }
     }
 }

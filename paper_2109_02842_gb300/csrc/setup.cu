@@ -38,7 +38,7 @@ __device__ __forceinline__ double kappa_sq(int mode, double k, double kz) {
 }
 
 __global__ void k_setup_kz(int mode, int n_pad, double dz, int n_f, const double *k, double *kc,
-                           float *kc_f, double *kspan) {
+                           float2 *kc_hl, double *kspan) {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n_pad) return;
     const double kz = kz_of(u, n_pad, dz);
@@ -53,7 +53,8 @@ __global__ void k_setup_kz(int mode, int n_pad, double dz, int n_f, const double
         hi = fmax(hi, kap);
     }
     kc[u] = any ? 0.5 * (lo + hi) : 0.0;
-    kc_f[u] = (float)kc[u];
+    const float kh = (float)kc[u];
+    kc_hl[u] = make_float2(kh, (float)(kc[u] - (double)kh));
     kspan[u] = any ? hi - lo : 0.0;
 }
 
@@ -92,7 +93,8 @@ __global__ void k_setup_sources(NufftDesc d, double dz, const double *k, const d
     // at row L/2 and put row 0 at l0.
     const double ph = kpp * (d.l0 + d.h * (double)(d.L / 2));
     const double red = ph - PL_TWO_PI * rint(ph / PL_TWO_PI);
-    const double mag = k[m] / phihat;
+    // the interpolation's factor h is folded in here as well
+    const double mag = d.h * k[m] / phihat;
     alpha[idx] = make_float2((float)(mag * cos(red)), (float)(mag * sin(red)));
 }
 
@@ -135,13 +137,45 @@ __global__ void k_dft_matrix_inv(int n_pad, double dz, double z0_scan, int nz, d
     T[idx] = make_float2((float)cos(red), (float)sin(red));
 }
 
+// Geometry of every (tile_px x 16 pixel tile, channel) for the back-projection.
+__global__ void k_setup_tile_geo(BpDesc p, int ntx, int nty, const double *ch_xy, TileGeo *out) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)ntx * nty * p.n_chan) return;
+    const int c = (int)(idx % p.n_chan);
+    const int tile = (int)(idx / p.n_chan);
+    const int tx = tile % ntx, ty = tile / ntx;
+    const int TX = p.tile_px, TY = 16;
+    const double xc = p.x0 + (tx * TX + 0.5 * (TX - 1)) * p.dx;
+    const double yc = p.y0 + (ty * TY + 0.5 * (TY - 1)) * p.dy;
+    const double dxt = xc - ch_xy[4 * c + 0], dyt = yc - ch_xy[4 * c + 1];
+    const double rt = sqrt(dxt * dxt + dyt * dyt);
+    double a = rt;
+    TileGeo g;
+    g.dxt = (float)dxt; g.dyt = (float)dyt; g.rt = (float)rt;
+    g.dxr = g.dyr = g.rr = 0.f;
+    if (p.mode == 1) {
+        const double dxr = xc - ch_xy[4 * c + 2], dyr = yc - ch_xy[4 * c + 3];
+        const double rr = sqrt(dxr * dxr + dyr * dyr);
+        a += rr;
+        g.dxr = (float)dxr; g.dyr = (float)dyr; g.rr = (float)rr;
+    }
+    int ilo = (int)floor((a - p.l0) / p.h - 0.5 * (p.R - 1));
+    ilo = max(0, min(ilo, p.L - p.R));
+    g.ilo = ilo;
+    g.off = (float)(a - (p.l0 + ilo * p.h));
+    g.a_hi = (float)a;
+    g.a_lo = (float)(a - (double)g.a_hi);
+    g.pad0 = g.pad1 = 0.f;
+    out[idx] = g;
+}
+
 inline int blocks(long long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
 cudaError_t launch_setup_kz(int mode, int n_pad, double dz, int n_f, const double *k,
-                            double *kc, float *kc_f, double *kspan, cudaStream_t st) {
-    k_setup_kz<<<blocks(n_pad, 128), 128, 0, st>>>(mode, n_pad, dz, n_f, k, kc, kc_f, kspan);
+                            double *kc, float2 *kc_hl, double *kspan, cudaStream_t st) {
+    k_setup_kz<<<blocks(n_pad, 128), 128, 0, st>>>(mode, n_pad, dz, n_f, k, kc, kc_hl, kspan);
     return cudaGetLastError();
 }
 
@@ -173,5 +207,13 @@ cudaError_t launch_dft_matrix_inv(int n_pad, double dz, double z0_scan, int nz, 
                                   double dzv, float2 *T, cudaStream_t st) {
     k_dft_matrix_inv<<<blocks((long long)nz * n_pad, 128), 128, 0, st>>>(n_pad, dz, z0_scan, nz,
                                                                        zv0, dzv, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup_tile_geo(const BpDesc &p, const double *ch_xy, TileGeo *tgeo,
+                                  cudaStream_t st) {
+    const int ntx = (p.nx + p.tile_px - 1) / p.tile_px, nty = (p.ny + 15) / 16;
+    k_setup_tile_geo<<<blocks((long long)ntx * nty * p.n_chan, 128), 128, 0, st>>>(p, ntx, nty,
+                                                                                   ch_xy, tgeo);
     return cudaGetLastError();
 }
