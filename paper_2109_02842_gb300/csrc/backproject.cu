@@ -112,10 +112,13 @@ k_backproject(BpDesc p, const void *__restrict__ table, const TileGeo *__restric
     const int iy = blockIdx.y * TY + ly;
     const int np2 = (p.n_pad + 1) / 2;
     const int pair0 = u0 / 2;
+    // pixel offsets from the tile centre, formed in FP32 only: under register
+    // pressure the compiler may recompute them inside the channel loop, and a
+    // double expression there would run on the (slow) FP64 pipe
     float ddx[PX];
 #pragma unroll
-    for (int k = 0; k < PX; ++k) ddx[k] = (float)((PX * lx + k - 0.5 * (TXP - 1)) * p.dx);
-    const float ddy = (float)((ly - 0.5 * (TY - 1)) * p.dy);
+    for (int k = 0; k < PX; ++k) ddx[k] = ((float)(PX * lx + k) - 0.5f * (TXP - 1)) * p.dxf;
+    const float ddy = ((float)ly - 0.5f * (TY - 1)) * p.dyf;
     const TileGeo *tg = tgeo + (size_t)tile * p.n_chan;
     const size_t row_pairs = (size_t)np2;
 

@@ -60,6 +60,7 @@ struct BpDesc {
     double x0, dx, y0, dy;
     double h, l0;
     float inv_h;
+    float dxf, dyf;       // dx, dy in FP32
     float beta, two_over_w;
     int w, tile_u;
     int block_config;     // 1: 8-channel chunks, 3 blocks/SM; 2: 16-channel chunks, 2 blocks/SM;

@@ -239,6 +239,8 @@ BpDesc make_bp(const pl_plan *P) {
     bp.h = d.h;
     bp.l0 = d.l0;
     bp.inv_h = (float)(1.0 / d.h);
+    bp.dxf = (float)P->grid.dx;
+    bp.dyf = (float)P->grid.dy;
     bp.beta = d.beta;
     bp.two_over_w = 2.0f / d.w;
     bp.w = d.w;
