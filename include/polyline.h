@@ -195,6 +195,34 @@ pl_status pl_synth_echo(int n_chan, const double *tx_xy, const double *rx_xy,
                         int n_pts, const double *pts, const double *amp,
                         void *echo_dev, void *stream);
 
+/* Allocation-free variant of pl_synth_echo (the paper has no counterpart; it
+ * exists for callers that cannot allocate device memory, e.g. code running
+ * while another component owns the device allocator, or services that must
+ * not touch the allocator after start-up).
+ *
+ * Same arguments and same result as pl_synth_echo, but the device-side copies
+ * of the inputs live in a fixed scratch array inside the library (a static
+ * __device__ variable of about 1.3 MB that every device loading the library
+ * holds until exit) instead of buffers allocated per call: this call never
+ * calls cudaMalloc or cudaFree. Limits: n_chan <= PL_STATIC_MAX_CHANNELS,
+ * n_f <= PL_STATIC_MAX_FREQS, n_pts <= PL_STATIC_MAX_POINTS; larger sizes
+ * return PL_ERR_ARG with a message in pl_last_error().
+ *  - The first call on a device looks up the scratch address for that device
+ *    (with it current) and caches it; make that first call before any stream
+ *    capture.
+ *  - All calls share the one scratch array, which keeps the last call's
+ *    contents. Calls whose GPU work overlaps (e.g. on two streams) race on it:
+ *    issue them on one stream or order them.
+ *  - The host arrays are copied before the call returns; the echo is complete
+ *    when `stream` reaches the end of this call's work (no synchronisation). */
+#define PL_STATIC_MAX_CHANNELS 4096
+#define PL_STATIC_MAX_FREQS 512
+#define PL_STATIC_MAX_POINTS 16384
+pl_status pl_synth_echo_static(int n_chan, const double *tx_xy, const double *rx_xy,
+                               double z0, double dz, int n_scan, const double *f_hz, int n_f,
+                               int n_pts, const double *pts, const double *amp,
+                               void *echo_dev, void *stream);
+
 const char *pl_status_string(pl_status s);
 const char *pl_last_error(void);
 /* Library version as major*10000 + minor*100 + patch. */

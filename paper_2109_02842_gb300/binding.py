@@ -56,8 +56,8 @@ class PlInfo(ctypes.Structure):
 
 EXPORTED = ("pl_plan_create", "pl_execute", "pl_execute_host", "pl_plan_destroy",
             "pl_plan_get_info", "pl_plan_workspace", "pl_plan_set_timing",
-            "pl_plan_stage_times", "pl_synth_echo", "pl_status_string", "pl_last_error",
-            "pl_version")
+            "pl_plan_stage_times", "pl_synth_echo", "pl_synth_echo_static",
+            "pl_status_string", "pl_last_error", "pl_version")
 
 _lib = None
 
@@ -87,13 +87,14 @@ def load(path: str = LIB_PATH):
     lib.pl_plan_set_timing.argtypes = [_P, _I]
     lib.pl_plan_stage_times.argtypes = [_P, ctypes.POINTER(_D), ctypes.POINTER(_I)]
     lib.pl_synth_echo.argtypes = [_I, _P, _P, _D, _D, _I, _P, _I, _I, _P, _P, _P, _P]
+    lib.pl_synth_echo_static.argtypes = [_I, _P, _P, _D, _D, _I, _P, _I, _I, _P, _P, _P, _P]
     lib.pl_status_string.restype = ctypes.c_char_p
     lib.pl_status_string.argtypes = [_I]
     lib.pl_last_error.restype = ctypes.c_char_p
     lib.pl_version.restype = _I
     for name in ("pl_plan_create", "pl_execute", "pl_execute_host", "pl_plan_destroy",
                  "pl_plan_get_info", "pl_plan_workspace", "pl_plan_set_timing",
-                 "pl_plan_stage_times", "pl_synth_echo"):
+                 "pl_plan_stage_times", "pl_synth_echo", "pl_synth_echo_static"):
         getattr(lib, name).restype = _I
     _lib = lib
     return lib
@@ -274,4 +275,23 @@ def synth_echo(tx_xy, rx_xy, z0, dz, n_scan, f_hz, pts, amp, out=None, stream=No
     _check(load().pl_synth_echo(tx.shape[0], _ptr(tx), _ptr(rx), float(z0), float(dz),
                                 int(n_scan), _ptr(f), f.size, p.shape[0], _ptr(p), _ptr(a),
                                 _P(out.data_ptr()), _stream_handle(stream)))
+    return out
+
+
+def synth_echo_static(tx_xy, rx_xy, z0, dz, n_scan, f_hz, pts, amp, out=None, stream=None):
+    """Same as synth_echo through pl_synth_echo_static, which allocates no
+    device memory (for callers that cannot allocate; see include/polyline.h).
+    Asynchronous on `stream`."""
+    import torch
+    tx = _f64(tx_xy).reshape(-1, 2)
+    rx = _f64(rx_xy).reshape(-1, 2)
+    f = _f64(f_hz).ravel()
+    p = _f64(pts).reshape(-1, 3)
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(amp, np.complex128), (p.shape[0],)))
+    a = _f64(np.stack([a.real, a.imag], 1))
+    if out is None:
+        out = torch.empty((tx.shape[0], n_scan, f.size), dtype=torch.complex64, device="cuda")
+    _check(load().pl_synth_echo_static(tx.shape[0], _ptr(tx), _ptr(rx), float(z0), float(dz),
+                                       int(n_scan), _ptr(f), f.size, p.shape[0], _ptr(p),
+                                       _ptr(a), _P(out.data_ptr()), _stream_handle(stream)))
     return out

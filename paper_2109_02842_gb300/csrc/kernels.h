@@ -79,6 +79,11 @@ cudaError_t launch_setup_tile_geo(const BpDesc &p, const double *ch_xy, TileGeo 
 int backproject_tile_x(int block_config);
 int backproject_tile_y();
 
+// ---- plan.cu: error reporting for other translation units ----------------------
+#include "../../include/polyline.h"
+pl_status pl_internal_fail(pl_status s, const char *msg);
+pl_status pl_internal_cuda_fail(cudaError_t e, const char *where);
+
 // ---- synth.cu ----------------------------------------------------------------
 cudaError_t launch_synth_echo(int n_chan, const float4 *ch, int n_scan, float z0, float dz,
                               int n_f, const float *k, int n_pts, const float4 *pts,

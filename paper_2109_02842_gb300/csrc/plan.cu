@@ -489,6 +489,9 @@ pl_status run(pl_plan *P, const float2 *echo, float2 *image, cudaStream_t st) {
 
 }  // namespace
 
+pl_status pl_internal_fail(pl_status s, const char *msg) { return fail(s, msg); }
+pl_status pl_internal_cuda_fail(cudaError_t e, const char *where) { return cuda_fail(e, where); }
+
 extern "C" {
 
 const char *pl_status_string(pl_status s) {
