@@ -38,9 +38,10 @@ cudaError_t launch_dft_matrix_inv(int n_pad, double dz, double z0_scan, int nz, 
 
 // ---- range_table.cu ----------------------------------------------------------
 size_t range_table_smem_bytes(const NufftDesc &d);
-cudaError_t launch_range_table(const NufftDesc &d, const float2 *S, const float2 *alpha,
-                               const float *xg, const float *dec, const float2 *tw_fine,
-                               void *table, int bf16, cudaStream_t st);
+// tw_fine: exp(-2 pi i k / fine), k < fine; fp: radix plan of `fine`.
+cudaError_t launch_range_table(const NufftDesc &d, const FftPlan &fp, const float2 *S,
+                               const float2 *alpha, const float *xg, const float *dec,
+                               const float2 *tw_fine, void *table, int bf16, cudaStream_t st);
 
 // ---- backproject.cu ------------------------------------------------------------
 // Plan-time geometry of one (pixel tile, channel): offsets of the tile centre

@@ -147,6 +147,7 @@ struct pl_plan {
     bool fwd_fft = true, inv_fft = true;
     int inv_off = 0;
     FftPlan zplan{};
+    FftPlan fineplan{};
     // device memory
     double *d_chxy = nullptr, *d_k = nullptr, *d_kc = nullptr, *d_kspan = nullptr;
     double *d_glx = nullptr, *d_glw = nullptr;
@@ -352,7 +353,9 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         amin = std::min(amin, lo + lo2);
         amax = std::max(amax, hi + hi2);
     }
-    int L = (int)std::ceil((amax - amin) / h) + 2 * P->R + 6;
+    // every tile's R-row window [i_lo, i_lo + R), centred on its range, fits:
+    // l0 = amin - ((R+1)/2 + 2) h, L = (amax - amin)/h + R + 6
+    int L = (int)std::ceil((amax - amin) / h) + P->R + 6;
     L += L & 1;
     if (L > 4096) return fail(PL_ERR_UNSUPPORTED, "range-profile table too long (grid too large for the band)");
     int fine = 64, lg = 6;
@@ -371,7 +374,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     d.beta = (float)(0.97 * M_PI * (1.0 - 0.5 / o.nufft_sigma) * W);
     d.beta1 = (float)(2.30 * d.w1);
     d.h = h;
-    d.l0 = amin - h * (P->R + 2);
+    d.l0 = amin - h * (0.5 * (P->R + 1) + 2.0);
     if (range_table_smem_bytes(d) > 200 * 1024)
         return fail(PL_ERR_UNSUPPORTED, "range-profile table too long for shared memory");
     if (P->C > 8192) return fail(PL_ERR_UNSUPPORTED, "more than 8192 channels");
@@ -390,11 +393,12 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     PL_CUDA(dalloc(&P->d_xg, (size_t)P->Np * P->M, ws), "cudaMalloc");
     PL_CUDA(dalloc(&P->d_alpha, (size_t)P->Np * P->M, ws), "cudaMalloc");
     PL_CUDA(dalloc(&P->d_dec, (size_t)L, ws), "cudaMalloc");
-    PL_CUDA(dalloc(&P->d_twfine, (size_t)fine / 2, ws), "cudaMalloc");
+    PL_CUDA(dalloc(&P->d_twfine, (size_t)fine, ws), "cudaMalloc");
     PL_CUDA(launch_setup_sources(d, P->dzs, P->d_k, P->d_kc, P->d_glx, P->d_glw, P->n_gl,
                                  P->d_xg, P->d_alpha, st), "setup_sources");
     PL_CUDA(launch_setup_deconv(d, P->d_glx, P->d_glw, P->n_gl, P->d_dec, st), "setup_deconv");
-    PL_CUDA(launch_twiddles(fine, fine / 2, +1, P->d_twfine, st), "twiddles");
+    PL_CUDA(launch_twiddles(fine, fine, -1, P->d_twfine, st), "twiddles");
+    if (!smooth_plan(fine, P->fineplan)) return fail(PL_ERR_UNSUPPORTED, "fine grid length");
 
     // transforms over z
     const bool smooth = smooth_plan(P->Np, P->zplan) && P->Np <= 512;
@@ -463,8 +467,8 @@ pl_status run(pl_plan *P, const float2 *echo, float2 *image, cudaStream_t st) {
     PL_CUDA(mark(0, 1), "event");
     // a2-a4: compensation + NUFFT spread + fine FFT + deconvolution, Eq. (8a)
     PL_CUDA(mark(1, 0), "event");
-    PL_CUDA(launch_range_table(d, P->d_S, P->d_alpha, P->d_xg, P->d_dec, P->d_twfine,
-                               P->d_table, P->precision == 1, st), "range_table");
+    PL_CUDA(launch_range_table(d, P->fineplan, P->d_S, P->d_alpha, P->d_xg, P->d_dec,
+                               P->d_twfine, P->d_table, P->precision == 1, st), "range_table");
     PL_CUDA(mark(1, 1), "event");
     // a5: back-projection with the coherent channel sum, Eq. (8b)
     PL_CUDA(mark(2, 0), "event");

@@ -10,136 +10,118 @@
 // radix-2 FFT in shared memory, and divided by the spreading kernel's
 // transform.
 //
-// One warp owns one (c, u) problem at a time and its fine grid in shared
-// memory; a block of 8 warps covers 16 consecutive k_z bins of one channel
-// and writes the [L][16] output panel as coalesced 128-byte rows of the
-// table b[c][i][u] (u fastest, in planar pairs {re_u, re_u+1, im_u, im_u+1},
-// N_p rounded up to even), the layout the back-projection stages.
+// A block covers UB consecutive k_z bins of one channel: their fine grids are
+// the rows of a [UB][fine] array in shared memory (bin-major, so the atomics
+// of neighbouring sources of one bin hit neighbouring banks), transformed
+// together by the block-wide mixed-radix Stockham FFT, and the deconvolved
+// rows j = i - L/2 are written as coalesced rows of the table b[c][i][u]
+// (u fastest, in planar pairs {re_u, re_u+1, im_u, im_u+1}, N_p rounded up to
+// even), the layout the back-projection stages.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
 #include "kernels.h"
+#include "stockham.cuh"
 
 namespace {
 
-constexpr int kUB = 16;       // k_z bins per block
-constexpr int kWarps = 8;
-
-__global__ void __launch_bounds__(kWarps * 32)
-k_range_table(NufftDesc d, const float2 *__restrict__ S, const float2 *__restrict__ alpha,
-              const float *__restrict__ xg, const float *__restrict__ dec,
-              const float2 *__restrict__ tw_g, void *__restrict__ table, int bf16) {
+template <int UB>
+__global__ void __launch_bounds__(256)
+k_range_table(NufftDesc d, FftPlan fp, const float2 *__restrict__ S,
+              const float2 *__restrict__ alpha, const float *__restrict__ xg,
+              const float *__restrict__ dec, const float2 *__restrict__ tw_g,
+              void *__restrict__ table, int bf16) {
     extern __shared__ float2 smem[];
     const int fine = d.fine;
-    const int lg = d.log2_fine;
-    float2 *tw = smem;                                  // fine/2: e^{+2 pi i q / fine}
-    float2 *panel = tw + fine / 2;                      // [L][kUB]
-    float2 *grids = panel + d.L * kUB;                  // [kWarps][fine]
-    const int warp = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
-    float2 *grid = grids + warp * fine;
+    float2 *tw = smem;                          // [fine]: exp(-2 pi i k / fine)
+    float2 *buf0 = tw + fine;                   // [UB][fine]
+    float2 *buf1 = buf0 + UB * fine;            // [UB][fine]
     const int c = blockIdx.y;
-    const int u0 = blockIdx.x * kUB;
+    const int u0 = blockIdx.x * UB;
     const float two_over_w1 = 2.0f / d.w1;
     const float half_w1 = 0.5f * d.w1;
 
-    for (int q = threadIdx.x; q < fine / 2; q += blockDim.x) tw[q] = tw_g[q];
+    for (int k = threadIdx.x; k < fine; k += blockDim.x) tw[k] = tw_g[k];
+    for (int k = threadIdx.x; k < UB * fine; k += blockDim.x) buf0[k] = make_float2(0.f, 0.f);
     __syncthreads();
 
-    for (int ul = warp; ul < kUB; ul += kWarps) {
+    // spread (compensation fused): source m of bin u onto row u of the grid
+    for (int idx = threadIdx.x; idx < UB * d.n_f; idx += blockDim.x) {
+        const int ul = idx / d.n_f;
+        const int m = idx - ul * d.n_f;
         const int u = u0 + ul;
-        if (u >= d.n_pad) {
-            for (int i = lane; i < d.L; i += 32) panel[i * kUB + ul] = make_float2(0.f, 0.f);
-            continue;
+        if (u >= d.n_pad) continue;
+        const float2 a = cmul(S[((size_t)c * d.n_pad + u) * d.n_f + m], alpha[u * d.n_f + m]);
+        if (a.x == 0.f && a.y == 0.f) continue;
+        const float x = xg[u * d.n_f + m];
+        const int g0 = (int)ceilf(x - half_w1);
+        float2 *row = buf0 + ul * fine;
+        for (int t = 0; t < d.w1; ++t) {
+            const int g = g0 + t;
+            const float wgt = es_kernel((float)g - x, two_over_w1, d.beta1);
+            float2 *cell = row + (g & (fine - 1));
+            atomicAdd(&cell->x, a.x * wgt);
+            atomicAdd(&cell->y, a.y * wgt);
         }
-        for (int g = lane; g < fine; g += 32) grid[g] = make_float2(0.f, 0.f);
-        __syncwarp();
-        // spread (compensation fused): sources to bit-reversed fine-grid slots
-        const float2 *Su = S + ((size_t)c * d.n_pad + u) * d.n_f;
-        for (int m = lane; m < d.n_f; m += 32) {
-            const float2 a = cmul(Su[m], alpha[u * d.n_f + m]);
-            if (a.x == 0.f && a.y == 0.f) continue;
-            const float x = xg[u * d.n_f + m];
-            const int g0 = (int)ceilf(x - half_w1);
-            for (int t = 0; t < d.w1; ++t) {
-                const int g = g0 + t;
-                const float wgt = es_kernel((float)g - x, two_over_w1, d.beta1);
-                const int gi = __brev((unsigned)(g & (fine - 1))) >> (32 - lg);
-                atomicAdd(&grid[gi].x, a.x * wgt);
-                atomicAdd(&grid[gi].y, a.y * wgt);
-            }
-        }
-        __syncwarp();
-        // in-place radix-2 decimation-in-time FFT, exponent +
-        for (int s = 0; s < lg; ++s) {
-            const int half = 1 << s;
-            for (int bf = lane; bf < fine / 2; bf += 32) {
-                const int k = bf & (half - 1);
-                const int i0 = ((bf >> s) << (s + 1)) + k;
-                const int i1 = i0 + half;
-                const float2 w = tw[k << (lg - 1 - s)];
-                const float2 v0 = grid[i0];
-                const float2 v1 = cmul(grid[i1], w);
-                grid[i0] = cadd(v0, v1);
-                grid[i1] = csub(v0, v1);
-            }
-            __syncwarp();
-        }
-        // deconvolve and keep rows j = i - L/2
-        for (int i = lane; i < d.L; i += 32) {
-            const int gi = (i - d.L / 2) & (fine - 1);
-            panel[i * kUB + ul] = cscale(grid[gi], dec[i]);
-        }
-        __syncwarp();
     }
     __syncthreads();
 
-    // table rows hold k_z bins in planar pairs: {re_u, re_u+1, im_u, im_u+1}
+    // inverse transform of every row (exponent +)
+    const float2 *res = stockham_run<false>(buf0, buf1, tw, fp, +1, UB, fine, 1);
+
+    // deconvolve, keep rows j = i - L/2, write planar bin pairs
     const int np2 = (d.n_pad + 1) / 2;
     const int p0 = u0 / 2;
-    const int npair = min(kUB / 2, np2 - p0);
-    if (!bf16) {
-        float4 *b = reinterpret_cast<float4 *>(table) + (size_t)c * d.L * np2;
-        for (int idx = threadIdx.x; idx < d.L * (kUB / 2); idx += blockDim.x) {
-            const int i = idx / (kUB / 2);
-            const int pp = idx - i * (kUB / 2);
-            if (pp >= npair) continue;
-            const float2 a = panel[i * kUB + 2 * pp];
-            const float2 e = panel[i * kUB + 2 * pp + 1];
-            b[(size_t)i * np2 + p0 + pp] = make_float4(a.x, e.x, a.y, e.y);
-        }
-    } else {
-        uint2 *b = reinterpret_cast<uint2 *>(table) + (size_t)c * d.L * np2;
-        for (int idx = threadIdx.x; idx < d.L * (kUB / 2); idx += blockDim.x) {
-            const int i = idx / (kUB / 2);
-            const int pp = idx - i * (kUB / 2);
-            if (pp >= npair) continue;
-            const float2 a = panel[i * kUB + 2 * pp];
-            const float2 e = panel[i * kUB + 2 * pp + 1];
+    constexpr int NPR = UB / 2;
+    for (int idx = threadIdx.x; idx < d.L * NPR; idx += blockDim.x) {
+        const int i = idx / NPR;
+        const int q = idx - i * NPR;
+        if (p0 + q >= np2) continue;
+        const int j = (i - d.L / 2) & (fine - 1);
+        const float s = dec[i];
+        const float2 a = cscale(res[(2 * q) * fine + j], s);
+        const float2 e = cscale(res[(2 * q + 1) * fine + j], s);
+        const size_t o = ((size_t)c * d.L + i) * np2 + p0 + q;
+        if (!bf16) {
+            reinterpret_cast<float4 *>(table)[o] = make_float4(a.x, e.x, a.y, e.y);
+        } else {
             __nv_bfloat162 re = __floats2bfloat162_rn(a.x, e.x);
             __nv_bfloat162 im = __floats2bfloat162_rn(a.y, e.y);
             uint2 v;
             v.x = *reinterpret_cast<unsigned *>(&re);
             v.y = *reinterpret_cast<unsigned *>(&im);
-            b[(size_t)i * np2 + p0 + pp] = v;
+            reinterpret_cast<uint2 *>(table)[o] = v;
         }
     }
 }
 
+inline int bins_per_block(int fine) { return fine <= 512 ? 16 : (fine <= 1024 ? 8 : 4); }
+
 }  // namespace
 
 size_t range_table_smem_bytes(const NufftDesc &d) {
-    return (size_t)(d.fine / 2 + d.L * kUB + kWarps * d.fine) * sizeof(float2);
+    return (size_t)(d.fine + 2 * bins_per_block(d.fine) * d.fine) * sizeof(float2);
 }
 
-cudaError_t launch_range_table(const NufftDesc &d, const float2 *S, const float2 *alpha,
-                               const float *xg, const float *dec, const float2 *tw_fine,
-                               void *table, int bf16, cudaStream_t st) {
+template <int UB>
+cudaError_t launch_ub(const NufftDesc &d, const FftPlan &fp, const float2 *S, const float2 *alpha,
+                      const float *xg, const float *dec, const float2 *tw_fine, void *table,
+                      int bf16, cudaStream_t st) {
     const size_t smem = range_table_smem_bytes(d);
-    cudaError_t e = cudaFuncSetAttribute(k_range_table,
+    cudaError_t e = cudaFuncSetAttribute(k_range_table<UB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((d.n_pad + kUB - 1) / kUB, d.n_chan);
-    k_range_table<<<grid, kWarps * 32, smem, st>>>(d, S, alpha, xg, dec, tw_fine, table, bf16);
+    dim3 grid((d.n_pad + UB - 1) / UB, d.n_chan);
+    k_range_table<UB><<<grid, 256, smem, st>>>(d, fp, S, alpha, xg, dec, tw_fine, table, bf16);
     return cudaGetLastError();
+}
+
+cudaError_t launch_range_table(const NufftDesc &d, const FftPlan &fp, const float2 *S,
+                               const float2 *alpha, const float *xg, const float *dec,
+                               const float2 *tw_fine, void *table, int bf16, cudaStream_t st) {
+    switch (bins_per_block(d.fine)) {
+        case 16: return launch_ub<16>(d, fp, S, alpha, xg, dec, tw_fine, table, bf16, st);
+        case 8: return launch_ub<8>(d, fp, S, alpha, xg, dec, tw_fine, table, bf16, st);
+        default: return launch_ub<4>(d, fp, S, alpha, xg, dec, tw_fine, table, bf16, st);
+    }
 }

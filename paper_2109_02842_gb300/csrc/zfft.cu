@@ -3,66 +3,18 @@
 // Both act on the middle axis of a [batch][n][inner] complex64 array whose
 // inner axis is contiguous: the echo s[c][n][m] (forward, zero-padded to N_p)
 // and the image spectrum G[u][pixel] (inverse). One block stages a
-// [n][IB] column panel in shared memory (coalesced 128-byte rows), runs a
+// [n][IB] column panel in shared memory (coalesced row segments), runs a
 // mixed-radix (2, 3, 4, 5) Stockham autosort FFT on all IB columns at once
 // and writes the requested output rows. Lengths with another prime factor,
 // and inverse transforms onto voxel heights off the scan grid, use the
 // tiled direct DFT kernel below with a precomputed phase matrix.
 #include "common.cuh"
 #include "kernels.h"
+#include "stockham.cuh"
 
 namespace {
 
-constexpr int kFftIB = 16;   // columns per block
-
-// Small DFT of radix R on v[] in place, exponent sign `sgn` (-1 forward).
-// W_R^{rq} is read from the length-N table of exp(-2 pi i k / N).
-template <int R>
-__device__ __forceinline__ void small_dft(float2 (&v)[5], const float2 *tw, int N, int sgn) {
-    float2 o[R];
-    const int step = N / R;
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-        float2 acc = v[0];
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-            float2 w = tw[((r * q) % R) * step];
-            if (sgn > 0) w.y = -w.y;
-            acc = cadd(acc, cmul(v[r], w));
-        }
-        o[q] = acc;
-    }
-#pragma unroll
-    for (int q = 0; q < R; ++q) v[q] = o[q];
-}
-
-template <int R>
-__device__ __forceinline__ void stockham_stage(const float2 *src, float2 *dst, const float2 *tw,
-                                               int N, int Ns, int sgn) {
-    const int items = (N / R) * kFftIB;
-    const int nr = N / R;
-    const int tw_step = N / (Ns * R);
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int j = it / kFftIB;
-        const int col = it - j * kFftIB;
-        const int k = j % Ns;
-        float2 v[5];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            float2 x = src[(j + r * nr) * kFftIB + col];
-            if (r > 0) {
-                float2 w = tw[(k * r * tw_step) % N];
-                if (sgn > 0) w.y = -w.y;
-                x = cmul(x, w);
-            }
-            v[r] = x;
-        }
-        small_dft<R>(v, tw, N, sgn);
-        const int base = (j / Ns) * Ns * R + k;
-#pragma unroll
-        for (int q = 0; q < R; ++q) dst[(base + q * Ns) * kFftIB + col] = v[q];
-    }
-}
+constexpr int kFftIB = 16;   // columns per block (128-byte rows)
 
 // in:  [batch][n_in][I]  (rows n >= n_in are zero padding)
 // out: [batch][out_rows][I], out row r = transform index (r + out_off) mod N
@@ -88,18 +40,7 @@ k_fft_strided(const float2 *__restrict__ in, float2 *__restrict__ out, int n_in,
     }
     __syncthreads();
 
-    float2 *src = buf0, *dst = buf1;
-    int Ns = 1;
-    for (int s = 0; s < plan.n_stages; ++s) {
-        const int R = plan.radix[s];
-        if (R == 4) stockham_stage<4>(src, dst, tw, N, Ns, sgn);
-        else if (R == 2) stockham_stage<2>(src, dst, tw, N, Ns, sgn);
-        else if (R == 3) stockham_stage<3>(src, dst, tw, N, Ns, sgn);
-        else stockham_stage<5>(src, dst, tw, N, Ns, sgn);
-        __syncthreads();
-        float2 *t = src; src = dst; dst = t;
-        Ns *= R;
-    }
+    const float2 *src = stockham_run<true>(buf0, buf1, tw, plan, sgn, kFftIB, 1, kFftIB);
 
     for (int idx = threadIdx.x; idx < out_rows * kFftIB; idx += blockDim.x) {
         const int r = idx / kFftIB;
