@@ -195,6 +195,63 @@ pl_status pl_synth_echo(int n_chan, const double *tx_xy, const double *rx_xy,
                         int n_pts, const double *pts, const double *amp,
                         void *echo_dev, void *stream);
 
+/* ---- Batches of uneven scans (one persistent launch) --------------------
+ * A batch reconstructs n_scenes independent scans whose geometry, scan,
+ * band and grid may all differ. pl_execute_batch replays one CUDA graph:
+ * the per-scene transforms over z (Eq. 2), then ONE persistent kernel that
+ * pulls work items from a device queue -- every scene's range-table blocks
+ * (Eq. 8a/19a) first, then every scene's back-projection tiles (Eq. 8b/19b),
+ * largest scenes first -- and finally the per-scene inverse transforms
+ * (Eq. 9). A back-projection item waits for its scene's range table through a
+ * per-scene counter; the wait is bounded (wait_timeout_ms) and gives up with
+ * PL_ERR_TIMEOUT instead of hanging.
+ *
+ * Block shape: all scenes share one (tile_u, block_config). With autotune = 1
+ * (and tile_u = block_config = 0) pl_batch_create times the candidate shapes
+ * on this batch and keeps the fastest; the choice is cached per batch
+ * signature for the life of the process. The persistent path needs
+ * nufft_w = 6 and a fine grid <= 512 points in every scene; otherwise the
+ * batch falls back to per-scene launches inside the same graph (see
+ * pl_batch_info.persistent). */
+typedef struct pl_batch pl_batch;
+
+typedef struct {
+    int tile_u;              /* 0 = default 16 (or autotuned) */
+    int block_config;        /* 0 = default 1 (or autotuned) */
+    int autotune;            /* 1: choose tile_u / block_config by timing */
+    double wait_timeout_ms;  /* bound of a device-side wait (0 = 2000 ms) */
+    int debug_unsatisfiable; /* test hook: scene 0's tiles wait for one more range-table
+                              * block than exists, so the bounded wait must expire */
+    int reserved[7];
+} pl_batch_options;
+
+typedef struct {
+    int n_scenes;
+    int tile_u, block_config;
+    int autotuned;             /* 1 if the shape came from timing (or its cache) */
+    int persistent;            /* 1: one persistent launch; 0: per-scene launches */
+    int persistent_blocks;     /* resident blocks of the persistent launch */
+    int work_items;            /* range-table + back-projection items */
+    int launches_per_execute;  /* kernel launches in the graph */
+    double tune_best_ms, tune_default_ms;  /* batch time of the chosen / default shape */
+    double updates_per_execute;            /* sum of n_chan * nx * ny * nz * n_f */
+    size_t workspace_bytes;
+} pl_batch_info;
+
+/* geoms, scans, freqs, grids: arrays of n_scenes host descriptors; opts may
+ * be NULL or an array of n_scenes (precision and NUFFT fields are used; the
+ * block shape comes from bopt). bopt may be NULL. */
+pl_status pl_batch_create(pl_batch **out, int n_scenes, const pl_geometry *geoms,
+                          const pl_scan *scans, const pl_freqs *freqs, const pl_grid *grids,
+                          const pl_options *opts, const pl_batch_options *bopt);
+/* echo_dev[i], image_dev[i]: device buffers of scene i (layouts as in
+ * pl_execute). The pointer arrays are host memory. Runs on `stream` and
+ * synchronises it before returning (the wait status is read back). */
+pl_status pl_execute_batch(pl_batch *batch, const void *const *echo_dev,
+                           void *const *image_dev, void *stream);
+pl_status pl_batch_get_info(const pl_batch *batch, pl_batch_info *info);
+pl_status pl_batch_destroy(pl_batch *batch);
+
 /* Allocation-free variant of pl_synth_echo (the paper has no counterpart; it
  * exists for callers that cannot allocate device memory, e.g. code running
  * while another component owns the device allocator, or services that must

@@ -54,9 +54,22 @@ class PlInfo(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t), ("updates_per_execute", _D)]
 
 
+class PlBatchOptions(ctypes.Structure):
+    _fields_ = [("tile_u", _I), ("block_config", _I), ("autotune", _I),
+                ("wait_timeout_ms", _D), ("debug_unsatisfiable", _I), ("reserved", _I * 7)]
+
+
+class PlBatchInfo(ctypes.Structure):
+    _fields_ = [("n_scenes", _I), ("tile_u", _I), ("block_config", _I), ("autotuned", _I),
+                ("persistent", _I), ("persistent_blocks", _I), ("work_items", _I),
+                ("launches_per_execute", _I), ("tune_best_ms", _D), ("tune_default_ms", _D),
+                ("updates_per_execute", _D), ("workspace_bytes", ctypes.c_size_t)]
+
+
 EXPORTED = ("pl_plan_create", "pl_execute", "pl_execute_host", "pl_plan_destroy",
             "pl_plan_get_info", "pl_plan_workspace", "pl_plan_set_timing",
             "pl_plan_stage_times", "pl_synth_echo", "pl_synth_echo_static",
+            "pl_batch_create", "pl_execute_batch", "pl_batch_get_info", "pl_batch_destroy",
             "pl_status_string", "pl_last_error", "pl_version")
 
 _lib = None
@@ -88,13 +101,21 @@ def load(path: str = LIB_PATH):
     lib.pl_plan_stage_times.argtypes = [_P, ctypes.POINTER(_D), ctypes.POINTER(_I)]
     lib.pl_synth_echo.argtypes = [_I, _P, _P, _D, _D, _I, _P, _I, _I, _P, _P, _P, _P]
     lib.pl_synth_echo_static.argtypes = [_I, _P, _P, _D, _D, _I, _P, _I, _I, _P, _P, _P, _P]
+    lib.pl_batch_create.argtypes = [ctypes.POINTER(_P), _I, ctypes.POINTER(PlGeometry),
+                                    ctypes.POINTER(PlScan), ctypes.POINTER(PlFreqs),
+                                    ctypes.POINTER(PlGrid), ctypes.POINTER(PlOptions),
+                                    ctypes.POINTER(PlBatchOptions)]
+    lib.pl_execute_batch.argtypes = [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P]
+    lib.pl_batch_get_info.argtypes = [_P, ctypes.POINTER(PlBatchInfo)]
+    lib.pl_batch_destroy.argtypes = [_P]
     lib.pl_status_string.restype = ctypes.c_char_p
     lib.pl_status_string.argtypes = [_I]
     lib.pl_last_error.restype = ctypes.c_char_p
     lib.pl_version.restype = _I
     for name in ("pl_plan_create", "pl_execute", "pl_execute_host", "pl_plan_destroy",
                  "pl_plan_get_info", "pl_plan_workspace", "pl_plan_set_timing",
-                 "pl_plan_stage_times", "pl_synth_echo", "pl_synth_echo_static"):
+                 "pl_plan_stage_times", "pl_synth_echo", "pl_synth_echo_static",
+                 "pl_batch_create", "pl_execute_batch", "pl_batch_get_info", "pl_batch_destroy"):
         getattr(lib, name).restype = _I
     _lib = lib
     return lib
@@ -136,6 +157,34 @@ class _DevArray:
                                          "data": (ptr, False), "version": 3, "strides": None}
 
 
+def _descriptors(keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad, pair_tx,
+                 pair_rx, radius, n_sections, chord_len, elem_section, precision, nufft_sigma,
+                 nufft_w, tile_u, block_config):
+    exy = _f64(elem_xy).reshape(-1, 2)
+    sec = None if elem_section is None else _i32(elem_section)
+    ptx = None if pair_tx is None else _i32(pair_tx)
+    prx = None if pair_rx is None else _i32(pair_rx)
+    f = _f64(f_hz).ravel()
+    keep += [exy, sec, ptx, prx, f]
+    geom = PlGeometry(int(mode), float(radius), int(n_sections), float(chord_len),
+                      exy.shape[0], _ptr(exy), _ptr(sec),
+                      0 if ptx is None else ptx.size, _ptr(ptx), _ptr(prx))
+    scan = PlScan(float(scan_z0), float(scan_dz), int(n_scan), int(n_pad))
+    freqs = PlFreqs(_ptr(f), f.size)
+    g = PlGrid(float(grid["x0"]), float(grid["dx"]), float(grid["y0"]), float(grid["dy"]),
+               float(grid["z0"]), float(grid["dz"]), int(grid["nx"]), int(grid["ny"]),
+               int(grid["nz"]))
+    opt = PlOptions(int(precision), float(nufft_sigma), int(nufft_w), int(tile_u),
+                    int(block_config))
+    return geom, scan, freqs, g, opt
+
+
+def _workload_args(w):
+    return (w.mode, w.elem_xy, w.z0, w.dz, w.n_scan, w.f_hz, w.grid, w.n_pad,
+            w.pair_tx if w.mode == 1 else None, w.pair_rx if w.mode == 1 else None, w.radius,
+            w.n_sections, w.chord_len, w.elem_section)
+
+
 class Plan:
     """A reconstruction plan (pl_plan_create / pl_execute / pl_plan_destroy)."""
 
@@ -145,22 +194,10 @@ class Plan:
                  block_config=0):
         lib = load()
         self._keep = []
-        exy = _f64(elem_xy).reshape(-1, 2)
-        sec = None if elem_section is None else _i32(elem_section)
-        ptx = None if pair_tx is None else _i32(pair_tx)
-        prx = None if pair_rx is None else _i32(pair_rx)
-        f = _f64(f_hz).ravel()
-        self._keep += [exy, sec, ptx, prx, f]
-        geom = PlGeometry(int(mode), float(radius), int(n_sections), float(chord_len),
-                          exy.shape[0], _ptr(exy), _ptr(sec),
-                          0 if ptx is None else ptx.size, _ptr(ptx), _ptr(prx))
-        scan = PlScan(float(scan_z0), float(scan_dz), int(n_scan), int(n_pad))
-        freqs = PlFreqs(_ptr(f), f.size)
-        g = PlGrid(float(grid["x0"]), float(grid["dx"]), float(grid["y0"]), float(grid["dy"]),
-                   float(grid["z0"]), float(grid["dz"]), int(grid["nx"]), int(grid["ny"]),
-                   int(grid["nz"]))
-        opt = PlOptions(int(precision), float(nufft_sigma), int(nufft_w), int(tile_u),
-                        int(block_config))
+        geom, scan, freqs, g, opt = _descriptors(
+            self._keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad, pair_tx,
+            pair_rx, radius, n_sections, chord_len, elem_section, precision, nufft_sigma,
+            nufft_w, tile_u, block_config)
         h = _P()
         _check(lib.pl_plan_create(ctypes.byref(h), geom, scan, freqs, g, opt))
         self._h = h
@@ -295,3 +332,57 @@ def synth_echo_static(tx_xy, rx_xy, z0, dz, n_scan, f_hz, pts, amp, out=None, st
                                        int(n_scan), _ptr(f), f.size, p.shape[0], _ptr(p),
                                        _ptr(a), _P(out.data_ptr()), _stream_handle(stream)))
     return out
+
+
+class Batch:
+    """Uneven scans reconstructed together (pl_batch_create / pl_execute_batch):
+    per-scene z transforms around one persistent range-table + back-projection
+    launch, replayed as a CUDA graph."""
+
+    def __init__(self, workloads, precision=0, nufft_sigma=0.0, nufft_w=0, tile_u=0,
+                 block_config=0, autotune=False, wait_timeout_ms=0.0, debug_unsatisfiable=0):
+        lib = load()
+        self._keep = []
+        n = len(workloads)
+        G, S, F, R, O = ((PlGeometry * n)(), (PlScan * n)(), (PlFreqs * n)(), (PlGrid * n)(),
+                         (PlOptions * n)())
+        for i, w in enumerate(workloads):
+            G[i], S[i], F[i], R[i], O[i] = _descriptors(
+                self._keep, *_workload_args(w), precision, nufft_sigma, nufft_w, 0, 0)
+        bo = PlBatchOptions(int(tile_u), int(block_config), 1 if autotune else 0,
+                            float(wait_timeout_ms), int(debug_unsatisfiable))
+        h = _P()
+        _check(lib.pl_batch_create(ctypes.byref(h), n, G, S, F, R, O, ctypes.byref(bo)))
+        self._h = h
+        self.n = n
+        self.echo_shapes = [(w.n_chan, w.n_scan, w.n_f) for w in workloads]
+        self.image_shapes = [(w.grid["nz"], w.grid["ny"], w.grid["nx"]) for w in workloads]
+        self.info = self.get_info()
+
+    def get_info(self) -> dict:
+        i = PlBatchInfo()
+        _check(load().pl_batch_get_info(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in PlBatchInfo._fields_}
+
+    def execute(self, echos, images=None, stream=None):
+        import torch
+        if images is None:
+            images = [torch.empty(s, dtype=torch.complex64, device=e.device)
+                      for s, e in zip(self.image_shapes, echos)]
+        for e, s in zip(echos, self.echo_shapes):
+            assert e.is_cuda and e.dtype == torch.complex64 and tuple(e.shape) == s
+        ep = (_P * self.n)(*[e.data_ptr() for e in echos])
+        ip = (_P * self.n)(*[im.data_ptr() for im in images])
+        _check(load().pl_execute_batch(self._h, ep, ip, _stream_handle(stream)))
+        return images
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pl_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -68,13 +68,16 @@ struct BpDesc {
                           // 3: 8-channel chunks, 2 blocks/SM, two pixels per thread
     int tile_px;          // pixels per block along x (16 or 32)
     int bf16;
-    // ES kernel tap weights as polynomials: weight_t(s) = sum_d coef[t][d] s^d,
-    // s in (-1, 1] the offset of the pixel inside its first table cell
-    float coef[12][14];
+};
+// ES kernel tap weights as polynomials: weight_t(s) = sum_d c[t][d] s^d,
+// s in (-1, 1] the offset of the pixel inside its first table cell.
+struct CoefTable {
+    float c[12][14];
 };
 size_t backproject_smem_bytes(int R, int tile_u, int n_chan, int bf16, int block_config);
-cudaError_t launch_backproject(const BpDesc &p, const void *table, const TileGeo *tgeo,
-                               const float2 *kc_hl, float2 *G, cudaStream_t st);
+cudaError_t launch_backproject(const BpDesc &p, const CoefTable &ct, const void *table,
+                               const TileGeo *tgeo, const float2 *kc_hl, float2 *G,
+                               cudaStream_t st);
 cudaError_t launch_setup_tile_geo(const BpDesc &p, const double *ch_xy, TileGeo *tgeo,
                                   cudaStream_t st);
 int backproject_tile_x(int block_config);

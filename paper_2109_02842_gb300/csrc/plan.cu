@@ -12,6 +12,7 @@
 #include "../../include/polyline.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "plan_internal.h"
 
 namespace {
 
@@ -128,64 +129,6 @@ cudaError_t dalloc(T **p, size_t count, size_t &total) {
 
 }  // namespace
 
-struct pl_plan {
-    // problem
-    int mode = 0, C = 0, N = 0, Np = 0, M = 0;
-    double z0s = 0, dzs = 0;
-    pl_grid grid{};
-    int precision = 0;
-    int tile_u = 16;
-    int block_config = 1;
-    int device = 0;
-    // nufft
-    NufftDesc nd{};
-    double sigma = 2.0;
-    int R = 0;
-    float coef[12][14] = {};
-    BpDesc bp{};
-    // transforms
-    bool fwd_fft = true, inv_fft = true;
-    int inv_off = 0;
-    FftPlan zplan{};
-    FftPlan fineplan{};
-    // device memory
-    double *d_chxy = nullptr, *d_k = nullptr, *d_kc = nullptr, *d_kspan = nullptr;
-    double *d_glx = nullptr, *d_glw = nullptr;
-    float *d_xg = nullptr, *d_dec = nullptr;
-    float2 *d_kchl = nullptr;
-    TileGeo *d_tgeo = nullptr;
-    float2 *d_alpha = nullptr, *d_twz = nullptr, *d_twfine = nullptr;
-    float2 *d_Tfwd = nullptr, *d_Tinv = nullptr;
-    float2 *d_S = nullptr, *d_G = nullptr;
-    void *d_table = nullptr;
-    size_t table_bytes = 0;
-    float2 *d_echo_in = nullptr, *d_img_out = nullptr;   // pl_execute_host staging
-    size_t workspace = 0;
-    int n_gl = 0;
-    // timing
-    bool timing = false;
-    std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> recorded;
-    size_t ev_next = 0;
-
-    ~pl_plan() {
-        void *ptrs[] = {d_chxy, d_k,    d_kc,   d_kspan, d_glx,  d_glw,     d_kchl, d_tgeo,
-                        d_xg,   d_dec,  d_alpha, d_twz,  d_twfine, d_Tfwd, d_Tinv,
-                        d_S,    d_G,    d_table, d_echo_in, d_img_out};
-        for (void *p : ptrs)
-            if (p) cudaFree(p);
-        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
-    }
-
-    cudaEvent_t next_event() {
-        if (ev_next == ev_pool.size()) {
-            cudaEvent_t e;
-            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-            ev_pool.push_back(e);
-        }
-        return ev_pool[ev_next++];
-    }
-};
 
 namespace {
 
@@ -249,7 +192,6 @@ BpDesc make_bp(const pl_plan *P) {
     bp.block_config = P->block_config;
     bp.tile_px = backproject_tile_x(P->block_config);
     bp.bf16 = P->precision == 1;
-    std::memcpy(bp.coef, P->coef, sizeof(bp.coef));
     return bp;
 }
 
@@ -380,7 +322,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     if (P->C > 8192) return fail(PL_ERR_UNSUPPORTED, "more than 8192 channels");
     if (backproject_smem_bytes(P->R, P->tile_u, P->C, P->precision, P->block_config) > 200 * 1024)
         return fail(PL_ERR_UNSUPPORTED, "table window too tall for shared memory (grid too coarse)");
-    for (int tp = 0; tp < W; ++tp) es_tap_polynomial(W, (double)d.beta, tp, W + 1, P->coef[tp]);
+    for (int tp = 0; tp < W; ++tp) es_tap_polynomial(W, (double)d.beta, tp, W + 1, P->coef.c[tp]);
 
     // plan-time tables
     std::vector<double> glx, glw;
@@ -442,6 +384,43 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     return PL_OK;
 }
 
+}  // namespace
+
+pl_status pl_stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st) {
+    if (P->fwd_fft)
+        PL_CUDA(launch_fft_strided(echo, P->d_S, P->C, P->N, P->M, P->zplan, P->d_twz, -1, 1.0f,
+                                   P->Np, 0, st), "zfft");
+    else
+        PL_CUDA(launch_dft_strided(echo, P->d_S, P->C, P->N, P->M, P->Np, P->d_Tfwd, 1.0f, st),
+                "zdft");
+    return PL_OK;
+}
+
+pl_status pl_stage_range_table(pl_plan *P, cudaStream_t st) {
+    PL_CUDA(launch_range_table(P->nd, P->fineplan, P->d_S, P->d_alpha, P->d_xg, P->d_dec,
+                               P->d_twfine, P->d_table, P->precision == 1, st), "range_table");
+    return PL_OK;
+}
+
+pl_status pl_stage_backproject(pl_plan *P, cudaStream_t st) {
+    PL_CUDA(launch_backproject(P->bp, P->coef, P->d_table, P->d_tgeo, P->d_kchl, P->d_G, st),
+            "backproject");
+    return PL_OK;
+}
+
+pl_status pl_stage_zifft(pl_plan *P, float2 *image, cudaStream_t st) {
+    const int P2 = P->grid.nx * P->grid.ny;
+    if (P->inv_fft)
+        PL_CUDA(launch_fft_strided(P->d_G, image, 1, P->Np, P2, P->zplan, P->d_twz, +1,
+                                   1.0f / P->Np, P->grid.nz, P->inv_off, st), "zifft");
+    else
+        PL_CUDA(launch_dft_strided(P->d_G, image, 1, P->Np, P2, P->grid.nz, P->d_Tinv,
+                                   1.0f / P->Np, st), "zidft");
+    return PL_OK;
+}
+
+namespace {
+
 pl_status run(pl_plan *P, const float2 *echo, float2 *image, cudaStream_t st) {
     cudaEvent_t ev[PL_NUM_STAGES][2] = {};
     if (P->timing) {
@@ -455,35 +434,22 @@ pl_status run(pl_plan *P, const float2 *echo, float2 *image, cudaStream_t st) {
         if (!P->timing) return cudaSuccess;
         return cudaEventRecord(ev[sidx][which], st);
     };
-    const NufftDesc &d = P->nd;
+    pl_status s;
     // a1: transform over the scan axis, Eq. (2)
     PL_CUDA(mark(0, 0), "event");
-    if (P->fwd_fft)
-        PL_CUDA(launch_fft_strided(echo, P->d_S, P->C, P->N, P->M, P->zplan, P->d_twz, -1, 1.0f,
-                                   P->Np, 0, st), "zfft");
-    else
-        PL_CUDA(launch_dft_strided(echo, P->d_S, P->C, P->N, P->M, P->Np, P->d_Tfwd, 1.0f, st),
-                "zdft");
+    if ((s = pl_stage_zfft(P, echo, st)) != PL_OK) return s;
     PL_CUDA(mark(0, 1), "event");
     // a2-a4: compensation + NUFFT spread + fine FFT + deconvolution, Eq. (8a)
     PL_CUDA(mark(1, 0), "event");
-    PL_CUDA(launch_range_table(d, P->fineplan, P->d_S, P->d_alpha, P->d_xg, P->d_dec,
-                               P->d_twfine, P->d_table, P->precision == 1, st), "range_table");
+    if ((s = pl_stage_range_table(P, st)) != PL_OK) return s;
     PL_CUDA(mark(1, 1), "event");
     // a5: back-projection with the coherent channel sum, Eq. (8b)
     PL_CUDA(mark(2, 0), "event");
-    PL_CUDA(launch_backproject(P->bp, P->d_table, P->d_tgeo, P->d_kchl, P->d_G, st),
-            "backproject");
+    if ((s = pl_stage_backproject(P, st)) != PL_OK) return s;
     PL_CUDA(mark(2, 1), "event");
     // a6: inverse transform over k_z, Eq. (9)
     PL_CUDA(mark(3, 0), "event");
-    const int P2 = P->grid.nx * P->grid.ny;
-    if (P->inv_fft)
-        PL_CUDA(launch_fft_strided(P->d_G, image, 1, P->Np, P2, P->zplan, P->d_twz, +1,
-                                   1.0f / P->Np, P->grid.nz, P->inv_off, st), "zifft");
-    else
-        PL_CUDA(launch_dft_strided(P->d_G, image, 1, P->Np, P2, P->grid.nz, P->d_Tinv,
-                                   1.0f / P->Np, st), "zidft");
+    if ((s = pl_stage_zifft(P, image, st)) != PL_OK) return s;
     PL_CUDA(mark(3, 1), "event");
     if (P->timing)
         for (int sidx = 0; sidx < PL_NUM_STAGES; ++sidx)

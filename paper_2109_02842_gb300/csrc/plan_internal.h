@@ -1,0 +1,83 @@
+// Internal: the plan object and stage helpers shared by plan.cu and batch.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <utility>
+#include <vector>
+
+#include "../../include/polyline.h"
+#include "common.cuh"
+#include "kernels.h"
+
+struct pl_plan {
+    // problem
+    int mode = 0, C = 0, N = 0, Np = 0, M = 0;
+    double z0s = 0, dzs = 0;
+    pl_grid grid{};
+    int precision = 0;
+    int tile_u = 16;
+    int block_config = 1;
+    int device = 0;
+    // nufft
+    NufftDesc nd{};
+    double sigma = 2.0;
+    int R = 0;
+    CoefTable coef{};
+    BpDesc bp{};
+    // transforms
+    bool fwd_fft = true, inv_fft = true;
+    int inv_off = 0;
+    FftPlan zplan{};
+    FftPlan fineplan{};
+    // device memory
+    double *d_chxy = nullptr, *d_k = nullptr, *d_kc = nullptr, *d_kspan = nullptr;
+    double *d_glx = nullptr, *d_glw = nullptr;
+    float *d_xg = nullptr, *d_dec = nullptr;
+    float2 *d_kchl = nullptr;
+    TileGeo *d_tgeo = nullptr;
+    float2 *d_alpha = nullptr, *d_twz = nullptr, *d_twfine = nullptr;
+    float2 *d_Tfwd = nullptr, *d_Tinv = nullptr;
+    float2 *d_S = nullptr, *d_G = nullptr;
+    void *d_table = nullptr;
+    size_t table_bytes = 0;
+    float2 *d_echo_in = nullptr, *d_img_out = nullptr;   // pl_execute_host staging
+    size_t workspace = 0;
+    int n_gl = 0;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> recorded;
+    size_t ev_next = 0;
+
+    ~pl_plan() {
+        void *ptrs[] = {d_chxy, d_k,    d_kc,   d_kspan, d_glx,  d_glw,     d_kchl, d_tgeo,
+                        d_xg,   d_dec,  d_alpha, d_twz,  d_twfine, d_Tfwd, d_Tinv,
+                        d_S,    d_G,    d_table, d_echo_in, d_img_out};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    }
+
+    cudaEvent_t next_event() {
+        if (ev_next == ev_pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            ev_pool.push_back(e);
+        }
+        return ev_pool[ev_next++];
+    }
+};
+
+// Return the mapped status (and set the thread's error message) on a CUDA error.
+#define PL_CUDA_RET(call)                                                   \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return pl_internal_cuda_fail(e_, #call);     \
+    } while (0)
+
+// Launch one stage of a plan on `st` (no timing events, no synchronisation).
+pl_status pl_stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st);
+pl_status pl_stage_range_table(pl_plan *P, cudaStream_t st);
+pl_status pl_stage_backproject(pl_plan *P, cudaStream_t st);
+pl_status pl_stage_zifft(pl_plan *P, float2 *image, cudaStream_t st);
