@@ -252,6 +252,67 @@ pl_status pl_execute_batch(pl_batch *batch, const void *const *echo_dev,
 pl_status pl_batch_get_info(const pl_batch *batch, pl_batch_info *info);
 pl_status pl_batch_destroy(pl_batch *batch);
 
+/* ---- Learned fast path (the paper has no learned component) --------------
+ * Kernels of the 3-D convolutional encoder-decoder that maps a cheap
+ * reconstruction (half the frequencies, low NUFFT oversampling) to the full
+ * one; the network and its training loop are driven from
+ * paper_2109_02842_gb300/learned.py. All volumes are channels-last device
+ * arrays x[v][c], v = (z H + y) W + x. BF16 tensors are bfloat16, others FP32.
+ * All calls are asynchronous on `stream`.
+ *
+ * pl_nn_conv3d: out[v][co] = act(bias[co] + sum_{tap,ci} w[co][tap Cin + ci]
+ *   x[v + off(tap)][ci]); 3x3x3 taps tap = (dz 3 + dy) 3 + dx at offset
+ *   (dz-1, dy-1, dx-1), zero padding; x BF16 [V][Cin]; w BF16
+ *   [Cout][pl_nn_padded_k(Cin)] (row tail zero); bias FP32 [Cout] or NULL;
+ *   relu != 0 applies max(., 0); out BF16 (out_bf16 != 0) or FP32 [V][Cout].
+ *   BF16 tensor-core MMA with FP32 accumulation.
+ * pl_nn_conv3d_wgrad: gw[co][tap Cin + ci] += sum_v gy[v][co] x[v+off][ci] and
+ *   gb[co] += sum_v gy[v][co] (gb may be NULL); x, gy BF16; gw, gb FP32;
+ *   Cout <= 32, 49-64 or 113-128. `work` is caller-owned device scratch of at
+ *   least pl_nn_wgrad_workspace(...) bytes for per-chunk partial sums, which
+ *   are added in a fixed order (bitwise reproducible gradients).
+ * pl_nn_weight_flip: wt[ci][(26 - tap) Cout + co] = w[co][tap Cin + ci], the
+ *   weights of the transposed convolution (input gradient = pl_nn_conv3d of
+ *   the output gradient with wt, Cin and Cout swapped).
+ * pl_nn_elementwise op: 0 out(BF16) = a(FP32) where b(BF16) > 0 else 0 (ReLU
+ *   backward); 1 out(BF16) = a(FP32); 2 out(BF16) = a + b (BF16); 3 out(FP32) += a(FP32).
+ * pl_nn_resample op (D, H, W = the fine size for 0/1, the coarse size for 2/3):
+ *   0 BF16 2x2x2 mean pool; 1 its adjoint, FP32 accumulate into the fine
+ *   gradient; 2 BF16 nearest x2 upsampling; 3 its adjoint (FP32 sum of the 8
+ *   children).
+ * pl_nn_features: feat BF16 [V][3] = (Re g / s, Im g / s, |g| / s) of a
+ *   complex64 volume, s = max |g| written to *scale (device FP32).
+ * pl_nn_loss: sums[0] = sum |t/s|^2, sums[1] = sum |pred - t/s|^2 (device
+ *   FP32[2], fixed-order reduction; the relative L2 loss is sums[1]/sums[0]);
+ *   grad (FP32 [V][2], may be NULL) = 2 (pred - t/s) / sums[0]; pred FP32
+ *   [V][2], target complex64.
+ * pl_nn_residual: pred[v] += gain (Re img[v], Im img[v]) / s.
+ * pl_nn_to_complex: img[v] = s (pred[v][0] + j pred[v][1]).
+ * pl_nn_adam: one bias-corrected Adam step (Kingma & Ba 2015) on FP32
+ *   parameters p with gradient g and moments m, v; refreshes the BF16 copy
+ *   p_bf16 when not NULL. */
+int pl_nn_padded_k(int cin);
+pl_status pl_nn_conv3d(const void *x, const void *w, const float *bias, void *out, int D, int H,
+                       int W, int Cin, int Cout, int relu, int out_bf16, void *stream);
+size_t pl_nn_wgrad_workspace(int D, int H, int W, int Cin, int Cout);
+pl_status pl_nn_conv3d_wgrad(const void *x, const void *gy, float *gw, float *gb, void *work,
+                             size_t work_bytes, int D, int H, int W, int Cin, int Cout,
+                             void *stream);
+pl_status pl_nn_weight_flip(const void *w, void *wt, int Cin, int Cout, void *stream);
+pl_status pl_nn_elementwise(int op, const void *a, const void *b, void *out, size_t n,
+                            void *stream);
+pl_status pl_nn_resample(int op, const void *x, void *y, int D, int H, int W, int C,
+                         void *stream);
+pl_status pl_nn_features(const void *img, void *feat, float *scale, size_t n, void *stream);
+pl_status pl_nn_loss(const float *pred, const void *target, const float *scale, float *sums,
+                     float *grad, size_t n, void *stream);
+pl_status pl_nn_residual(float *pred, const void *img, const float *scale, float gain, size_t n,
+                         void *stream);
+pl_status pl_nn_to_complex(const float *pred, const float *scale, void *img, size_t n,
+                           void *stream);
+pl_status pl_nn_adam(float *p, const float *g, float *m, float *v, void *p_bf16, size_t n,
+                     float lr, float b1, float b2, float eps, int step, void *stream);
+
 /* Allocation-free variant of pl_synth_echo (the paper has no counterpart; it
  * exists for callers that cannot allocate device memory, e.g. code running
  * while another component owns the device allocator, or services that must

@@ -72,11 +72,10 @@ def upsample2(x):
 
 
 def features(g):
-    """|g| / max|g|, cos(arg g), sin(arg g) of a complex volume -> [D,H,W,3]."""
+    """Re g / s, Im g / s, |g| / s of a complex volume, s = max |g| -> [D,H,W,3]."""
     a = np.abs(g)
     s = a.max() if a.max() > 0 else 1.0
-    ph = np.angle(g)
-    return np.stack([a / s, np.cos(ph), np.sin(ph)], axis=-1), s
+    return np.stack([g.real / s, g.imag / s, a / s], axis=-1), s
 
 
 def rel_l2_loss(pred, target):

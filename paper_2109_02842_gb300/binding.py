@@ -70,6 +70,9 @@ EXPORTED = ("pl_plan_create", "pl_execute", "pl_execute_host", "pl_plan_destroy"
             "pl_plan_get_info", "pl_plan_workspace", "pl_plan_set_timing",
             "pl_plan_stage_times", "pl_synth_echo", "pl_synth_echo_static",
             "pl_batch_create", "pl_execute_batch", "pl_batch_get_info", "pl_batch_destroy",
+            "pl_nn_padded_k", "pl_nn_conv3d", "pl_nn_wgrad_workspace", "pl_nn_conv3d_wgrad",
+            "pl_nn_weight_flip", "pl_nn_elementwise", "pl_nn_resample", "pl_nn_features",
+            "pl_nn_loss", "pl_nn_residual", "pl_nn_to_complex", "pl_nn_adam",
             "pl_status_string", "pl_last_error", "pl_version")
 
 _lib = None

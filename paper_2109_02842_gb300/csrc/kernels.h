@@ -92,3 +92,24 @@ pl_status pl_internal_cuda_fail(cudaError_t e, const char *where);
 cudaError_t launch_synth_echo(int n_chan, const float4 *ch, int n_scan, float z0, float dz,
                               int n_f, const float *k, int n_pts, const float4 *pts,
                               const float2 *amp, float2 *echo, cudaStream_t st);
+
+// ---- nn.cu: learned fast path -------------------------------------------------
+cudaError_t nn_conv3d(const void *x, const void *w, const float *bias, void *out, int D, int H,
+                      int W, int Cin, int Cout, int Kp, int relu, int out_bf16, cudaStream_t st);
+size_t nn_wgrad_work_floats(int D, int H, int W, int Cin, int Cout, int Kp);
+cudaError_t nn_conv3d_wgrad(const void *x, const void *gy, float *gw, float *gb, float *work,
+                            int D, int H, int W, int Cin, int Cout, int Kp, cudaStream_t st);
+cudaError_t nn_residual(float *pred, const void *img, const float *scale, float gain, size_t n,
+                        cudaStream_t st);
+cudaError_t nn_weight_flip(const void *w, void *wt, int Cin, int Cout, int Kp, int Kpt,
+                           cudaStream_t st);
+cudaError_t nn_elementwise(int op, const void *a, const void *b, void *out, size_t n,
+                           cudaStream_t st);
+cudaError_t nn_resample(int op, const void *x, void *y, int D, int H, int W, int C, cudaStream_t st);
+cudaError_t nn_features(const void *img, void *feat, float *scale, size_t n, cudaStream_t st);
+cudaError_t nn_loss(const float *pred, const void *target, const float *scale, float *sums,
+                    float *grad, size_t n, cudaStream_t st);
+cudaError_t nn_to_complex(const float *pred, const float *scale, void *img, size_t n,
+                          cudaStream_t st);
+cudaError_t nn_adam(float *p, const float *g, float *m, float *v, void *pb, size_t n, float lr,
+                    float b1, float b2, float eps, int step, cudaStream_t st);

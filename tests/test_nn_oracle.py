@@ -64,9 +64,9 @@ def test_loss_gradient_and_features():
                - g[1, 2, 3, 0]) < 1e-6
     z = rng.standard_normal((2, 3, 4)) + 1j * rng.standard_normal((2, 3, 4))
     f, s = nn.features(z)
-    assert np.isclose(f[..., 0].max(), 1.0)
-    assert np.allclose(f[..., 1] ** 2 + f[..., 2] ** 2, 1.0)
-    assert np.allclose(f[..., 0] * s * (f[..., 1] + 1j * f[..., 2]), z)
+    assert np.isclose(f[..., 2].max(), 1.0)
+    assert np.allclose(f[..., 0] ** 2 + f[..., 1] ** 2, f[..., 2] ** 2)
+    assert np.allclose(s * (f[..., 0] + 1j * f[..., 1]), z)
 
 
 def test_adam_first_step_is_signed_lr():
