@@ -103,10 +103,15 @@ typedef struct {
  *            1 = range-profile table stored as BF16 pairs (FP32 accumulate).
  * nufft_sigma: oversampling of the range-profile grid (default 2.0).
  * nufft_w: interpolation taps (even, 4..12; default 6).
- * tile_u: k_z bins per back-projection block (8, 16, 20 or 24; 0 = chosen
- *         from n_pad).
- * block_config: back-projection block shape (0 = default; 1 = 8-channel chunks,
- *         3 blocks per SM; 2 = 16-channel chunks, 2 blocks per SM). */
+ * tile_u: k_z bins per back-projection block (8, 16, 20 or 24; 32 or 40 with
+ *         block_config 4; 0 = chosen from n_pad).
+ * block_config: back-projection block shape (0 = default: 3 when the x step
+ *         is below the table step, else 1; 1 = one pixel per thread, 8-channel
+ *         chunks, 3 blocks per SM; 2 = one pixel per thread, 16-channel chunks;
+ *         3 = two pixels per thread sharing the tap window; 4 = interpolation
+ *         on the tensor cores (BF16 hi/lo split, mma.sync), 16 x 8 pixel blocks,
+ *         needs precision 0 and nufft_w 4, 6 or 8; with 4 the range-table
+ *         workspace holds the [channel][hi/lo][column][row] BF16 layout). */
 typedef struct {
     int precision;
     double nufft_sigma;

@@ -233,7 +233,8 @@ pl_status build_queue(pl_batch *B, int tile_u, double timeout_ms, int debug) {
     B->block_config = B->plans[0]->block_config;
     B->persistent = true;
     for (pl_plan *p : B->plans)
-        if (p->nd.w != 6 || p->nd.fine > 512 || p->block_config != B->block_config)
+        if (p->nd.w != 6 || p->nd.fine > 512 || p->block_config != B->block_config ||
+            p->block_config == 4)
             B->persistent = false;
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);

@@ -67,6 +67,7 @@ struct BpDesc {
     int block_config;     // 1: 8-channel chunks, 3 blocks/SM; 2: 16-channel chunks, 2 blocks/SM;
                           // 3: 8-channel chunks, 2 blocks/SM, two pixels per thread
     int tile_px;          // pixels per block along x (16 or 32)
+    int tile_py;          // pixels per block along y (16, or 8 for block_config 4)
     int bf16;
 };
 // ES kernel tap weights as polynomials: weight_t(s) = sum_d c[t][d] s^d,
@@ -81,6 +82,14 @@ cudaError_t launch_backproject(const BpDesc &p, const CoefTable &ct, const void 
 cudaError_t launch_setup_tile_geo(const BpDesc &p, const double *ch_xy, TileGeo *tgeo,
                                   cudaStream_t st);
 int backproject_tile_x(int block_config);
+// tensor-core variant (block_config 4), backproject_tc.cu
+int backproject_tc_tile_x();
+int backproject_tc_tile_y();
+int backproject_tc_window_rows(int R);
+size_t backproject_tc_smem_bytes(int S, int tile_u, int n_chan);
+cudaError_t launch_backproject_tc(const BpDesc &p, const CoefTable &ct, const void *table,
+                                  const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int S,
+                                  int tc_rows, int tc_cols, cudaStream_t st);
 int backproject_tile_y();
 
 // ---- plan.cu: error reporting for other translation units ----------------------

@@ -190,7 +190,8 @@ BpDesc make_bp(const pl_plan *P) {
     bp.w = d.w;
     bp.tile_u = P->tile_u;
     bp.block_config = P->block_config;
-    bp.tile_px = backproject_tile_x(P->block_config);
+    bp.tile_px = P->block_config == 4 ? backproject_tc_tile_x() : backproject_tile_x(P->block_config);
+    bp.tile_py = P->block_config == 4 ? backproject_tc_tile_y() : backproject_tile_y();
     bp.bf16 = P->precision == 1;
     return bp;
 }
@@ -206,8 +207,9 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         return fail(PL_ERR_ARG, "nufft_sigma must be in [1.2, 8]");
     if (o.nufft_w < 4 || o.nufft_w > 12 || (o.nufft_w & 1))
         return fail(PL_ERR_ARG, "nufft_w must be even, 4..12");
-    if (o.tile_u != 0 && o.tile_u != 8 && o.tile_u != 16 && o.tile_u != 20 && o.tile_u != 24)
-        return fail(PL_ERR_ARG, "tile_u must be 0, 8, 16, 20 or 24");
+    if (o.tile_u != 0 && o.tile_u != 8 && o.tile_u != 16 && o.tile_u != 20 && o.tile_u != 24 &&
+        o.tile_u != 32 && o.tile_u != 40)
+        return fail(PL_ERR_ARG, "tile_u must be 0, 8, 16, 20, 24, 32 or 40");
     if (o.precision != 0 && o.precision != 1) return fail(PL_ERR_ARG, "precision must be 0 or 1");
 
     PL_CUDA(cudaGetDevice(&P->device), "cudaGetDevice");
@@ -221,13 +223,24 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     P->grid = *gr;
     P->precision = o.precision;
     P->tile_u = o.tile_u;
-    if (o.block_config < 0 || o.block_config > 3)
-        return fail(PL_ERR_ARG, "block_config must be 0, 1, 2 or 3");
+    if (o.block_config < 0 || o.block_config > 4)
+        return fail(PL_ERR_ARG, "block_config must be 0..4");
     P->block_config = o.block_config;
-    if (P->tile_u == 0) {   // fewest padded k_z bins; 20 only when it wastes less than 16
+    if (P->block_config == 4 && (o.precision != 0 || (o.nufft_w != 4 && o.nufft_w != 6 && o.nufft_w != 8)))
+        return fail(PL_ERR_UNSUPPORTED, "block_config 4 needs precision 0 and nufft_w 4, 6 or 8");
+    {
         const int n = s->n_pad ? s->n_pad : s->n;
-        const int w16 = (n + 15) / 16 * 16 - n, w20 = (n + 19) / 20 * 20 - n;
-        P->tile_u = w20 < w16 ? 20 : 16;
+        if (P->block_config == 4) {     // tensor-core variant: 32 or 40 bins per block
+            if (P->tile_u != 32 && P->tile_u != 40) {
+                const int w32 = (n + 31) / 32 * 32 - n, w40 = (n + 39) / 40 * 40 - n;
+                P->tile_u = w40 < w32 ? 40 : 32;
+            }
+        } else if (P->tile_u == 0) {    // fewest padded bins; 20 only when it wastes less than 16
+            const int w16 = (n + 15) / 16 * 16 - n, w20 = (n + 19) / 20 * 20 - n;
+            P->tile_u = w20 < w16 ? 20 : 16;
+        } else if (P->tile_u > 24) {
+            return fail(PL_ERR_ARG, "tile_u 32 and 40 need block_config 4");
+        }
     }
     P->sigma = o.nufft_sigma;
 
@@ -280,7 +293,8 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     if (P->block_config == 3 && !px2_ok)
         return fail(PL_ERR_UNSUPPORTED, "block_config 3 needs an x step below the table step");
     if (P->block_config == 0) P->block_config = px2_ok ? 3 : 1;
-    const int TX = backproject_tile_x(P->block_config), TY = backproject_tile_y();
+    const int TX = P->block_config == 4 ? backproject_tc_tile_x() : backproject_tile_x(P->block_config);
+    const int TY = P->block_config == 4 ? backproject_tc_tile_y() : backproject_tile_y();
     const double hs_pix = 0.5 * std::hypot((TX - 1) * gr->dx, (TY - 1) * gr->dy);
     const double hs = P->mode == 0 ? hs_pix : 2.0 * hs_pix;
     P->R = (int)std::ceil(2.0 * hs / h) + W + (P->block_config == 3 ? 1 : 0) + 5;
@@ -320,7 +334,13 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     if (range_table_smem_bytes(d) > 200 * 1024)
         return fail(PL_ERR_UNSUPPORTED, "range-profile table too long for shared memory");
     if (P->C > 8192) return fail(PL_ERR_UNSUPPORTED, "more than 8192 channels");
-    if (backproject_smem_bytes(P->R, P->tile_u, P->C, P->precision, P->block_config) > 200 * 1024)
+    if (P->block_config == 4) {
+        P->tc_S = backproject_tc_window_rows(P->R);
+        d.tc_rows = (L + P->tc_S + 7) / 8 * 8;
+        d.tc_cols = 2 * ((P->Np + P->tile_u - 1) / P->tile_u * P->tile_u);
+        if (backproject_tc_smem_bytes(P->tc_S, P->tile_u, P->C) > 200 * 1024)
+            return fail(PL_ERR_UNSUPPORTED, "table window too tall for shared memory (grid too coarse)");
+    } else if (backproject_smem_bytes(P->R, P->tile_u, P->C, P->precision, P->block_config) > 200 * 1024)
         return fail(PL_ERR_UNSUPPORTED, "table window too tall for shared memory (grid too coarse)");
     for (int tp = 0; tp < W; ++tp) es_tap_polynomial(W, (double)d.beta, tp, W + 1, P->coef.c[tp]);
 
@@ -367,18 +387,24 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     // per (pixel tile, channel) geometry of the back-projection
     P->bp = make_bp(P);
     {
-        const int tpx = backproject_tile_x(P->block_config);
-        const size_t ntiles = (size_t)((gr->nx + tpx - 1) / tpx) * ((gr->ny + 15) / 16);
+        const int tpx = P->bp.tile_px, tpy = P->bp.tile_py;
+        const size_t ntiles = (size_t)((gr->nx + tpx - 1) / tpx) * ((gr->ny + tpy - 1) / tpy);
         PL_CUDA(dalloc(&P->d_tgeo, ntiles * P->C, ws), "cudaMalloc");
         PL_CUDA(launch_setup_tile_geo(P->bp, P->d_chxy, P->d_tgeo, st), "setup_tile_geo");
     }
 
     // data workspace
     PL_CUDA(dalloc(&P->d_S, (size_t)P->C * P->Np * P->M, ws), "cudaMalloc");
-    // table rows: k_z bins in planar pairs, N_p rounded up to even
-    P->table_bytes = (size_t)P->C * L * ((P->Np + 1) / 2) * (P->precision == 1 ? 8 : 16);
+    // table rows: k_z bins in planar pairs, N_p rounded up to even; or the
+    // tensor-core layout [c][hi/lo][column][row] BF16 (zero beyond what the
+    // range table writes)
+    if (P->block_config == 4)
+        P->table_bytes = (size_t)P->C * 2 * d.tc_cols * d.tc_rows * 2;
+    else
+        P->table_bytes = (size_t)P->C * L * ((P->Np + 1) / 2) * (P->precision == 1 ? 8 : 16);
     ws += P->table_bytes;
     PL_CUDA(cudaMalloc(&P->d_table, P->table_bytes), "cudaMalloc");
+    if (P->block_config == 4) PL_CUDA(cudaMemset(P->d_table, 0, P->table_bytes), "cudaMemset");
     PL_CUDA(dalloc(&P->d_G, (size_t)P->Np * gr->nx * gr->ny, ws), "cudaMalloc");
     PL_CUDA(cudaDeviceSynchronize(), "plan setup");
     return PL_OK;
@@ -397,12 +423,19 @@ pl_status pl_stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st) {
 }
 
 pl_status pl_stage_range_table(pl_plan *P, cudaStream_t st) {
+    const int fmt = P->block_config == 4 ? 2 : (P->precision == 1 ? 1 : 0);
     PL_CUDA(launch_range_table(P->nd, P->fineplan, P->d_S, P->d_alpha, P->d_xg, P->d_dec,
-                               P->d_twfine, P->d_table, P->precision == 1, st), "range_table");
+                               P->d_twfine, P->d_table, fmt, st), "range_table");
     return PL_OK;
 }
 
 pl_status pl_stage_backproject(pl_plan *P, cudaStream_t st) {
+    if (P->block_config == 4) {
+        PL_CUDA(launch_backproject_tc(P->bp, P->coef, P->d_table, P->d_tgeo, P->d_kchl, P->d_G,
+                                      P->tc_S, P->nd.tc_rows, P->nd.tc_cols, st),
+                "backproject_tc");
+        return PL_OK;
+    }
     PL_CUDA(launch_backproject(P->bp, P->coef, P->d_table, P->d_tgeo, P->d_kchl, P->d_G, st),
             "backproject");
     return PL_OK;

@@ -23,6 +23,7 @@ struct pl_plan {
     NufftDesc nd{};
     double sigma = 2.0;
     int R = 0;
+    int tc_S = 0;          // tensor-core variant: window rows staged per channel
     CoefTable coef{};
     BpDesc bp{};
     // transforms

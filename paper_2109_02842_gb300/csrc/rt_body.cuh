@@ -55,7 +55,28 @@ __device__ __forceinline__ void rt_block(const NufftDesc &d, const FftPlan &fp,
     // inverse transform of every row (exponent +)
     const float2 *res = stockham_run<false>(buf0, buf1, tw, fp, +1, UB, fine, 1);
 
-    // deconvolve, keep rows j = i - L/2, write planar bin pairs
+    // deconvolve, keep rows j = i - L/2
+    if (bf16 == 2) {
+        // tensor-core layout: [c][plane hi/lo][column 2u + (re, im)][row], BF16 hi and
+        // the BF16 residual lo = x - hi, rows contiguous
+        for (int idx = threadIdx.x; idx < 2 * UB * d.L; idx += blockDim.x) {
+            const int cl = idx / d.L;
+            const int i = idx - cl * d.L;
+            const int ul = cl >> 1;
+            if (u0 + ul >= d.n_pad) continue;
+            const int j = (i - d.L / 2) & (fine - 1);
+            const float2 v = cscale(res[ul * fine + j], dec[i]);
+            const float x = (cl & 1) ? v.y : v.x;
+            const __nv_bfloat16 hi = __float2bfloat16(x);
+            const __nv_bfloat16 lo = __float2bfloat16(x - __bfloat162float(hi));
+            const size_t col = 2 * (size_t)u0 + cl;
+            __nv_bfloat16 *tb = reinterpret_cast<__nv_bfloat16 *>(table);
+            tb[(((size_t)c * 2 + 0) * d.tc_cols + col) * d.tc_rows + i] = hi;
+            tb[(((size_t)c * 2 + 1) * d.tc_cols + col) * d.tc_rows + i] = lo;
+        }
+        return;
+    }
+    // planar bin pairs
     const int np2 = (d.n_pad + 1) / 2;
     const int p0 = u0 / 2;
     constexpr int NPR = UB / 2;

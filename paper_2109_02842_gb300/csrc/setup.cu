@@ -144,7 +144,7 @@ __global__ void k_setup_tile_geo(BpDesc p, int ntx, int nty, const double *ch_xy
     const int c = (int)(idx % p.n_chan);
     const int tile = (int)(idx / p.n_chan);
     const int tx = tile % ntx, ty = tile / ntx;
-    const int TX = p.tile_px, TY = 16;
+    const int TX = p.tile_px, TY = p.tile_py;
     const double xc = p.x0 + (tx * TX + 0.5 * (TX - 1)) * p.dx;
     const double yc = p.y0 + (ty * TY + 0.5 * (TY - 1)) * p.dy;
     const double dxt = xc - ch_xy[4 * c + 0], dyt = yc - ch_xy[4 * c + 1];
@@ -212,7 +212,7 @@ cudaError_t launch_dft_matrix_inv(int n_pad, double dz, double z0_scan, int nz, 
 
 cudaError_t launch_setup_tile_geo(const BpDesc &p, const double *ch_xy, TileGeo *tgeo,
                                   cudaStream_t st) {
-    const int ntx = (p.nx + p.tile_px - 1) / p.tile_px, nty = (p.ny + 15) / 16;
+    const int ntx = (p.nx + p.tile_px - 1) / p.tile_px, nty = (p.ny + p.tile_py - 1) / p.tile_py;
     k_setup_tile_geo<<<blocks((long long)ntx * nty * p.n_chan, 128), 128, 0, st>>>(p, ntx, nty,
                                                                                    ch_xy, tgeo);
     return cudaGetLastError();

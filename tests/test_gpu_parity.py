@@ -233,3 +233,32 @@ def test_full_size_sampled_columns(binding, which):
     ref = image_ref(w, echo, w.pix_xy()[idx])
     got = img.reshape(w.grid["nz"], -1)[:, idx]
     assert report("image %s sampled" % which, got, ref) < TOL_FP32
+
+
+# --- tensor-core interpolation (block_config 4) -----------------------------------
+
+@pytest.mark.parametrize("case", ["small_mono", "small_multi", "ragged"])
+def test_tensor_core_variant_small(binding, case):
+    if case == "small_mono":
+        w = wl.small_mono(seed=0)
+    elif case == "small_multi":
+        w = small_multi()
+    else:
+        w = wl.small_mono(seed=3)
+        w.grid = dict(w.grid, nx=37, ny=23, nz=7, z0=-0.031, dz=0.0093)
+    echo = scene_echo(w)
+    plan, img = run_gpu(binding, w, echo, block_config=4)
+    assert plan.info["nufft_w"] == 6
+    ref = image_ref(w, echo)
+    assert report("image tc %s" % case, img.reshape(w.grid["nz"], -1), ref) < TOL_FP32
+
+
+@pytest.mark.parametrize("which", ["full_mono", "multi"])
+def test_tensor_core_variant_full_size_sampled(binding, which):
+    w = wl.WORKLOADS[which](seed=0)
+    echo = scene_echo(w, 0, n_pts=24)
+    _, img = run_gpu(binding, w, echo, block_config=4)
+    idx = sampled_columns(w, 48, 1)
+    ref = image_ref(w, echo, w.pix_xy()[idx])
+    got = img.reshape(w.grid["nz"], -1)[:, idx]
+    assert report("image tc %s sampled" % which, got, ref) < TOL_FP32
