@@ -1,262 +1,334 @@
-// Back-projection (step 8b / 19b) with the interpolation on the tensor cores.
+// Back-projection (step 8b / 19b) on the fifth-generation tensor cores.
 //
-// Same sum as backproject.cu,
-//   G_u(x,y) = sum_c e^{j (kappa_c,u delta + phi_c,u)} sum_t phi(a_c - l_{i0+t}) b_c[i0+t][u],
-// but for each channel the w-tap interpolation of a warp's 16 pixels is a
-// small dense product
-//   X[p][col] = sum_{k < 16} A[p][k] B[k][col],   col = 2u + (re, im),
-// with A[p][k] the ES weight of pixel p at window row base + k (zero outside
-// its w taps) and B the table rows base .. base+15. Both operands are split
-// into BF16 hi + lo parts and the product is hi.hi + hi.lo + lo.hi on
-// mma.sync m16n8k16 with FP32 accumulation (relative error ~1e-5, below the
-// NUFFT's). The FP32 pipe keeps only the carrier sin/cos and the complex
-// multiply-accumulate.
+// With the band centre kappa_T shared by the k_z bins of a block (the range
+// table is built with that centre for every bin of the group), the carrier
+// e^{j kappa_T a_c(p)} depends on the pixel and the channel only, so it goes
+// into the interpolation weights and the whole channel sum becomes a chain
+// of dense products accumulated in tensor memory:
 //
-// Block = 16 x 8 pixels (8 warps, each a 4 x 4 pixel block) x 4 NJ k_z bins.
-// Thread (g, t) of a warp owns pixels g and g + 8 of its block and bins
-// u = 4 j + t, j < NJ, exactly the rows and columns of its mma accumulator
-// fragments, so products feed the carrier without data movement.
+//   G[p][u] = sum_c sum_k A_c[p][k] B_c[k][u],
+//   A_c[p][k] = phi(a_c(p) - l_{i_c + k}) e^{j kappa_T a_c(p)},  B_c[k][u] = b_c[i_c + k][u],
 //
-// The table comes in a tensor-core layout written by the range-table kernel:
-// [channel][plane hi/lo][column][row] BF16, rows contiguous. A chunk of CCH
-// channels' windows (S rows from the channel's first row rounded down to 8)
-// is copied into shared memory with cp.async, double buffered.
+// p one of the block's 128 pixels (the MMA's M), k one of the 16 KS table rows
+// of the block's window for channel c (starting at i_c, chosen at plan time
+// so that every pixel's w taps fall inside), u the block's UT k_z bins.
+// Complex products are two real ones: with B's columns (re_u, im_u),
+// P = sum Re(A) B and Q = sum Im(A) B give G = (P_re - Q_im, P_im + Q_re).
+// Operands are BF16; for FP32-level accuracy each is split into hi + lo
+// and the product taken as hi.hi + hi.lo + lo.hi (SPLIT = 3), relative
+// error ~1e-5; SPLIT = 1 takes hi.hi only (~1e-3).
+//
+// Block = 16 x 8 pixels x UT bins, 10 warps:
+//  * warps 0-7 build A: warp w owns TMEM lanes 32 (w % 4) .. +31 (its
+//    pixels) for the channels of parity w / 4. Per channel a thread forms
+//    its pixel's range offset, the w tap weights (per-tap polynomials of the
+//    ES kernel), the carrier, the BF16 hi/lo parts, shifts them to the taps'
+//    position in the 16 KS-row window and writes the row to TMEM
+//    (tcgen05.st); one A buffer per parity, so one parity is being written
+//    while the MMAs read the other;
+//  * warp 8 (one thread) issues the tcgen05.mma chain of each channel and
+//    commits its completion to the barriers that free the A buffer and the
+//    table slot;
+//  * warp 9 (one thread) streams the table windows with TMA: one 4-D box
+//    (8 columns x 16 KS rows x UT/4 column groups x hi/lo) per channel into
+//    a ring of smem slots. The table is stored [c][hi/lo][column group][row][8],
+//    which is the MN-major no-swizzle layout the MMA reads, and a window may
+//    start at any row.
+// At the end the accumulators (P, Q: 2 x 2 UT FP32 columns) are read back
+// with tcgen05.ld and written as G[u][y][x].
+//
+// Every wait is bounded (a clock budget); a wait that runs out sets a bit in
+// *err, the block skips the rest of its work and still waits (bounded) for
+// its own copies and products before releasing tensor memory.
 #include <cuda_bf16.h>
 
 #include "bp_body.cuh"
 #include "common.cuh"
 #include "kernels.h"
+#include "tc05.cuh"
 
 namespace {
 
 constexpr int TCX = 16, TCY = 8;
-constexpr int APAD = 24;          // A staging row stride (bf16), conflict-free fragment loads
+constexpr int NCW = 8;                       // A-building warps
+constexpr int NTHREADS = (NCW + 2) * 32;     // + MMA warp + TMA warp
 
-__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4],
-                                         const unsigned (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__device__ __forceinline__ unsigned ldp(const __nv_bfloat16 *p) {
-    return *reinterpret_cast<const unsigned *>(p);
-}
-
-template <int NJ, int CCH>
-struct TcSmem {
-    static constexpr int NCOL = 8 * NJ;   // 2 columns (re, im) per bin, 4 NJ bins
-    static size_t bytes(int S, int n_chan) {
-        return (size_t)2 * CCH * 2 * NCOL * S * sizeof(__nv_bfloat16) +   // windows, 2 buffers
-               (size_t)2 * CCH * sizeof(TileGeo) +                       // geometry
-               (size_t)CCH * 4 * NJ * sizeof(float2) +                    // (kappa, phi)
-               (size_t)8 * 2 * 16 * APAD * sizeof(__nv_bfloat16) +         // A staging per warp
-               (size_t)8 * 16 * sizeof(float) +                           // delta per warp pixel
-               (size_t)n_chan * sizeof(int);                              // first rows
+// Put the NT words t at word offset wo of an NW-word row, zeros elsewhere
+// (a barrel shift over the bits of wo; words pushed past NW are dropped).
+template <int NW, int NT>
+__device__ __forceinline__ void place(const uint32_t (&t)[NT], int wo, uint32_t (&r)[NW]) {
+#pragma unroll
+    for (int j = 0; j < NW; ++j) r[j] = j < NT ? t[j] : 0u;
+#pragma unroll
+    for (int b = 1; b < NW; b <<= 1) {
+        const bool on = (wo & b) != 0;
+#pragma unroll
+        for (int j = NW - 1; j >= 0; --j) r[j] = on ? (j >= b ? r[j - b] : 0u) : r[j];
     }
-};
+}
 
-template <int W, int NJ, int CCH>
-__global__ void __launch_bounds__(256, 2)
-k_backproject_tc(BpDesc p, CoefTable ct, const __nv_bfloat16 *__restrict__ table,
+__device__ __forceinline__ uint32_t bf2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+// BF16 pair (a, b) and the BF16 pair of its residuals
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo) {
+    hi = bf2(a, b);
+    lo = bf2(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xffff0000u));
+}
+
+template <int W, int KS, int SPLIT>
+__global__ void __launch_bounds__(NTHREADS, 2)
+k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUtensorMap tmap,
                  const TileGeo *__restrict__ tgeo, const float2 *__restrict__ kc_hl,
-                 float2 *__restrict__ G, int S, int tc_rows, int tc_cols) {
-    constexpr int NCOL = 8 * NJ;
-    constexpr int UT = 4 * NJ;
-    constexpr int ND = W + 2;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __nv_bfloat16 *win = reinterpret_cast<__nv_bfloat16 *>(smem);      // [2][CCH][2][NCOL][S]
-    TileGeo *geo = reinterpret_cast<TileGeo *>(win + (size_t)2 * CCH * 2 * NCOL * S);
-    float2 *kphi = reinterpret_cast<float2 *>(geo + 2 * CCH);          // [CCH][UT]
-    __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(kphi + CCH * UT);   // [8][2][16][APAD]
-    float *dls = reinterpret_cast<float *>(As + 8 * 2 * 16 * APAD);    // [8][16]
-    int *ilo8 = reinterpret_cast<int *>(dls + 8 * 16);                 // [n_chan]
+                 float2 *__restrict__ G, int *err) {
+    constexpr int NPL = SPLIT == 3 ? 4 : 2;     // A planes: (re, im) x (hi[, lo])
+    constexpr int NW = 8 * KS;                  // 32-bit words of an A row (16 KS BF16)
+    constexpr int NT = W / 2 + 1;               // words of the taps after the parity shift
+    constexpr int ND = W + 2;                   // polynomial coefficients per tap
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *b_full = reinterpret_cast<uint64_t *>(smem + (size_t)ta.nst * ta.slot_bytes);
+    uint64_t *b_empty = b_full + ta.nst;
+    uint64_t *a_full = b_empty + ta.nst;        // [2], 4 arrivals (the parity's warps)
+    uint64_t *a_empty = a_full + 2;             // [2], MMA completion
+    uint64_t *acc_full = a_empty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_full + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    const int wx = warp & 3, wy = warp >> 2;
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-    const int u0 = blockIdx.z * UT;
-    const TileGeo *tg = tgeo + (size_t)tile * p.n_chan;
-    // the pixel this lane prepares (lanes 16-31 repeat lanes 0-15)
-    const int pp = lane & 15;
-    const float ddx = ((float)(wx * 4 + (pp & 3)) - 0.5f * (TCX - 1)) * p.dxf;
-    const float ddy = ((float)(wy * 4 + (pp >> 2)) - 0.5f * (TCY - 1)) * p.dyf;
-    __nv_bfloat16 *Aw = As + warp * 2 * 16 * APAD;
+    const int u0 = blockIdx.z * ta.UT;
+    const int C = p.n_chan;
+    const TileGeo *tg = tgeo + (size_t)tile * C;
+    const long long budget = ta.budget;
 
-    for (int c = threadIdx.x; c < p.n_chan; c += blockDim.x) ilo8[c] = tg[c].ilo & ~7;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ta.nst; ++s) {
+            tc05::mbar_init(&b_full[s], 1);
+            tc05::mbar_init(&b_empty[s], 1);
+        }
+        for (int k = 0; k < 2; ++k) {
+            tc05::mbar_init(&a_full[k], 4);
+            tc05::mbar_init(&a_empty[k], 1);
+        }
+        tc05::mbar_init(acc_full, 1);
+        tc05::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc05::tmem_alloc(tmem_slot, ta.tmem_cols);
+        tc05::tmem_relinquish();
+    }
+    tc05::fence_before_sync();
     __syncthreads();
+    tc05::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t N = 2 * ta.UT;
 
-    auto issue = [&](int ck, int buf) {
-        const int c0 = ck * CCH;
-        const int ncc = min(CCH, p.n_chan - c0);
-        const int cpc = S / 8;                             // 16-byte chunks per column
-        const int per_c = 2 * NCOL * cpc;
-        for (int idx = threadIdx.x; idx < ncc * per_c; idx += blockDim.x) {
-            const int cl = idx / per_c;
-            int rem = idx - cl * per_c;
-            const int plane = rem / (NCOL * cpc);
-            rem -= plane * NCOL * cpc;
-            const int col = rem / cpc;
-            const int ch = rem - col * cpc;
-            const __nv_bfloat16 *src =
-                table + (((size_t)(c0 + cl) * 2 + plane) * tc_cols + 2 * u0 + col) * tc_rows +
-                ilo8[c0 + cl] + 8 * ch;
-            __nv_bfloat16 *dst = win + ((((size_t)buf * CCH + cl) * 2 + plane) * NCOL + col) * S +
-                                 8 * ch;
-            bp::cp_async16(dst, src);
-        }
-        constexpr int G4 = sizeof(TileGeo) / 16;
-        for (int idx = threadIdx.x; idx < ncc * G4; idx += blockDim.x)
-            bp::cp_async16(reinterpret_cast<float4 *>(geo + buf * CCH) + idx,
-                           reinterpret_cast<const float4 *>(tg + c0) + idx);
-        bp::cp_commit();
-    };
-
-    float2 acc[NJ][2];
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) acc[j][0] = acc[j][1] = make_float2(0.f, 0.f);
-
-    const int n_chunks = (p.n_chan + CCH - 1) / CCH;
-    issue(0, 0);
-    for (int ck = 0; ck < n_chunks; ++ck) {
-        const int buf = ck & 1;
-        const int ncc = min(CCH, p.n_chan - ck * CCH);
-        if (ck + 1 < n_chunks) {
-            issue(ck + 1, buf ^ 1);
-            bp::cp_wait<1>();
-        } else {
-            bp::cp_wait<0>();
-        }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < ncc * UT; idx += blockDim.x) {
-            const int cl = idx / UT;
-            const int u = u0 + (idx - cl * UT);
-            const TileGeo &gg = geo[buf * CCH + cl];
-            const float2 k = u < p.n_pad ? kc_hl[u] : make_float2(0.f, 0.f);
-            kphi[idx] = make_float2(k.x, bp::phase_ff(k.x, k.y, gg.a_hi, gg.a_lo));
-        }
-        __syncthreads();
-
-        for (int cl = 0; cl < ncc; ++cl) {
-            const TileGeo gc = geo[buf * CCH + cl];
-            // geometry of pixel pp: delta = a - a* without cancellation
-            float ex = gc.dxt + ddx, ey = gc.dyt + ddy;
-            float num = fmaf(ddx, 2.0f * gc.dxt + ddx, ddy * (2.0f * gc.dyt + ddy));
+    if (warp < NCW) {
+        // ------------------------------------------------ A rows (weights)
+        const int q = warp & 3, par = warp >> 2;
+        const int pix = 32 * q + lane;
+        const int px = pix % TCX, py = pix / TCX;
+        const float ddx = ((float)px - 0.5f * (TCX - 1)) * p.dxf;
+        const float ddy = ((float)py - 0.5f * (TCY - 1)) * p.dyf;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+        const uint32_t abuf = lane_base + ta.acol + par * (NPL * KS * 8);
+        const float2 kT = kc_hl[u0];
+        bool ok = true;
+        int it = 0;
+        for (int c = par; c < C; c += 2, ++it) {
+            const TileGeo g = tg[c];
+            // delta = a - a* from rho^2 - rho*^2 = d (2 D + d): no cancellation
+            float ex = g.dxt + ddx, ey = g.dyt + ddy;
+            float num = fmaf(ddx, 2.0f * g.dxt + ddx, ddy * (2.0f * g.dyt + ddy));
             float r2 = fmaf(ex, ex, ey * ey);
-            float delta = num * __frcp_rn(fmaf(r2, rsqrtf(r2), gc.rt));
+            float dl = num * __frcp_rn(fmaf(r2, rsqrtf(r2), g.rt));
             if (p.mode == 1) {
-                ex = gc.dxr + ddx; ey = gc.dyr + ddy;
-                num = fmaf(ddx, 2.0f * gc.dxr + ddx, ddy * (2.0f * gc.dyr + ddy));
+                ex = g.dxr + ddx;
+                ey = g.dyr + ddy;
+                num = fmaf(ddx, 2.0f * g.dxr + ddx, ddy * (2.0f * g.dyr + ddy));
                 r2 = fmaf(ex, ex, ey * ey);
-                delta += num * __frcp_rn(fmaf(r2, rsqrtf(r2), gc.rr));
+                dl += num * __frcp_rn(fmaf(r2, rsqrtf(r2), g.rr));
             }
-            // position in window rows (row 0 = the channel's first row rounded to 8)
-            const float pos = (delta + gc.off) * p.inv_h + (float)(gc.ilo & 7);
-            const int i0 = (int)ceilf(pos - 0.5f * W);
-            int base = __reduce_min_sync(0xffffffffu, i0) & ~1;
-            base = max(0, min(base, S - 16));
-            const int o = min(max(i0 - base, 0), 16 - W);
-            const float s = fmaf(2.0f, pos - (float)(base + o), -(float)(W - 1));
-            // A operand: zero this warp's 16 x 16 (x2 planes), then the w taps
+            // taps: rows o .. o + w - 1 of the window, weights from the per-tap
+            // polynomials in s = 2 (pos - o) - (w - 1)
+            const float pos = (dl + g.off) * p.inv_h;
+            const int o = min(max((int)ceilf(pos - 0.5f * W), 0), 16 * KS - W);
+            const float s = fmaf(2.0f, pos - (float)o, -(float)(W - 1));
+            float w[W];
+#pragma unroll
+            for (int t = 0; t < W; ++t) {
+                float acc = ct.c[t][ND - 1];
+#pragma unroll
+                for (int d = ND - 2; d >= 0; --d) acc = fmaf(acc, s, ct.c[t][d]);
+                w[t] = acc;
+            }
+            // carrier e^{j kappa_T a} = e^{j (kappa_T delta + (kappa_T a* mod 2 pi))}
+            const float th = fmaf(kT.x, dl, bp::phase_ff(kT.x, kT.y, g.a_hi, g.a_lo));
+            float sn, cs;
+            __sincosf(th, &sn, &cs);
+            // element o of the row starts word o / 2; an odd o puts a zero first
+            const bool odd = (o & 1) != 0;
+            float e[W + 2];
+#pragma unroll
+            for (int k = 0; k < W + 2; ++k) {
+                const float ev = k < W ? w[k] : 0.f;
+                const float od = (k >= 1 && k <= W) ? w[k - 1] : 0.f;
+                e[k] = odd ? od : ev;
+            }
+            uint32_t rows[NPL][NW];
             {
-                uint4 *z = reinterpret_cast<uint4 *>(Aw);
-                const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
-                for (int k = lane; k < 2 * 16 * APAD / 8; k += 32) z[k] = zero;
+                uint32_t tw[NPL][NT];
+#pragma unroll
+                for (int j = 0; j < NT; ++j) {
+                    const float r0 = e[2 * j] * cs, r1 = e[2 * j + 1] * cs;
+                    const float i0 = e[2 * j] * sn, i1 = e[2 * j + 1] * sn;
+                    if (SPLIT == 3) {
+                        split2(r0, r1, tw[0][j], tw[1][j]);
+                        split2(i0, i1, tw[2][j], tw[NPL - 1][j]);
+                    } else {
+                        tw[0][j] = bf2(r0, r1);
+                        tw[1][j] = bf2(i0, i1);
+                    }
+                }
+#pragma unroll
+                for (int pl = 0; pl < NPL; ++pl) place<NW, NT>(tw[pl], o >> 1, rows[pl]);
             }
+            // the products of channel c - 2 must be done with this buffer
+            if (it > 0) ok = tc05::mbar_wait(&a_empty[par], (it - 1) & 1, budget);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            tc05::fence_after_sync();
+#pragma unroll
+            for (int pl = 0; pl < NPL; ++pl)
+#pragma unroll
+                for (int ks = 0; ks < KS; ++ks) {
+                    uint32_t v[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j] = rows[pl][8 * ks + j];
+                    tc05::tmem_st8(abuf + (pl * KS + ks) * 8, v);
+                }
+            tc05::tmem_wait_st();
+            tc05::fence_before_sync();
             __syncwarp();
+            if (lane == 0) tc05::mbar_arrive(&a_full[par]);
+        }
+        if (!ok && lane == 0) atomicOr(err, 1);
+
+        // ------------------------------------------------ epilogue
+        bool done = tc05::mbar_wait(acc_full, 0, budget);
+        done = __all_sync(0xffffffffu, done);
+        if (done) {
+            tc05::fence_after_sync();
+            const int ix = blockIdx.x * TCX + px, iy = blockIdx.y * TCY + py;
+            const bool inside = ix < p.nx && iy < p.ny;
+            const size_t plane = (size_t)p.nx * p.ny;
+            const size_t pofs = (size_t)iy * p.nx + ix;
+            for (int ch = par; ch < (int)(N / 16); ch += 2) {
+                uint32_t pv[16], qv[16];
+                tc05::tmem_ld16(lane_base + 16 * ch, pv);
+                tc05::tmem_ld16(lane_base + N + 16 * ch, qv);
+                tc05::tmem_wait_ld();
+                if (!inside) continue;
 #pragma unroll
-            for (int tap = 0; tap < W; ++tap) {
-                float wv = ct.c[tap][ND - 1];
-#pragma unroll
-                for (int d = ND - 2; d >= 0; --d) wv = fmaf(wv, s, ct.c[tap][d]);
-                if ((tap < W / 2) == (lane < 16)) {
-                    const __nv_bfloat16 hi = __float2bfloat16(wv);
-                    Aw[pp * APAD + o + tap] = hi;
-                    Aw[16 * APAD + pp * APAD + o + tap] = __float2bfloat16(wv - __bfloat162float(hi));
+                for (int b = 0; b < 8; ++b) {
+                    const int u = u0 + 8 * ch + b;
+                    if (u < p.n_pad)
+                        G[u * plane + pofs] = make_float2(
+                            __uint_as_float(pv[2 * b]) - __uint_as_float(qv[2 * b + 1]),
+                            __uint_as_float(pv[2 * b + 1]) + __uint_as_float(qv[2 * b]));
                 }
             }
-            if (lane < 16) dls[warp * 16 + pp] = delta;
-            __syncwarp();
-            unsigned ah[4], al[4];
-            ah[0] = ldp(Aw + g * APAD + 2 * t);
-            ah[1] = ldp(Aw + (g + 8) * APAD + 2 * t);
-            ah[2] = ldp(Aw + g * APAD + 2 * t + 8);
-            ah[3] = ldp(Aw + (g + 8) * APAD + 2 * t + 8);
-            al[0] = ldp(Aw + 16 * APAD + g * APAD + 2 * t);
-            al[1] = ldp(Aw + 16 * APAD + (g + 8) * APAD + 2 * t);
-            al[2] = ldp(Aw + 16 * APAD + g * APAD + 2 * t + 8);
-            al[3] = ldp(Aw + 16 * APAD + (g + 8) * APAD + 2 * t + 8);
-            const float d0 = dls[warp * 16 + g], d1 = dls[warp * 16 + g + 8];
-            const __nv_bfloat16 *wh = win + ((size_t)(buf * CCH + cl) * 2 + 0) * NCOL * S + base + 2 * t;
-            const __nv_bfloat16 *wl = wh + NCOL * S;
-            const float2 *kp = kphi + cl * UT;
+        } else if (lane == 0) {
+            atomicOr(err, 2);
+        }
+    } else if (warp == NCW) {
+        // ------------------------------------------------ MMA issue
+        if (lane == 0) {
+            const uint32_t sbase = tc05::smem_addr(smem);
+            const uint32_t plane_bytes = (uint32_t)ta.NG * 16 * KS * 16;
+            const uint32_t sbo = 16 * KS * 16;     // column-group stride; 128 B between 8-row groups
+            bool ok = true;
+            for (int c = 0; c < C; ++c) {
+                const int par = c & 1, it = c >> 1, slot = c % ta.nst, round = c / ta.nst;
+                ok = tc05::mbar_wait(&b_full[slot], round & 1, budget) &&
+                     tc05::mbar_wait(&a_full[par], it & 1, budget);
+                if (!ok) break;
+                tc05::fence_after_sync();
+                const uint32_t bs = sbase + slot * ta.slot_bytes;
+                const uint32_t a0 = tmem + ta.acol + par * (NPL * KS * 8);
 #pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-                const int col = 8 * j + g;
-                unsigned bh[2], bl[2];
-                bh[0] = ldp(wh + col * S);
-                bh[1] = ldp(wh + col * S + 8);
-                bl[0] = ldp(wl + col * S);
-                bl[1] = ldp(wl + col * S + 8);
-                float x[4] = {0.f, 0.f, 0.f, 0.f};
-                mma16816(x, ah, bh);
-                mma16816(x, ah, bl);
-                mma16816(x, al, bh);
-                // x: (pixel g: re, im), (pixel g+8: re, im) of bin 4j + t
-                const float2 k = kp[4 * j + t];
-                float s0, c0, s1, c1;
-                __sincosf(fmaf(k.x, d0, k.y), &s0, &c0);
-                __sincosf(fmaf(k.x, d1, k.y), &s1, &c1);
-                acc[j][0].x = fmaf(x[0], c0, fmaf(-x[1], s0, acc[j][0].x));
-                acc[j][0].y = fmaf(x[0], s0, fmaf(x[1], c0, acc[j][0].y));
-                acc[j][1].x = fmaf(x[2], c1, fmaf(-x[3], s1, acc[j][1].x));
-                acc[j][1].y = fmaf(x[2], s1, fmaf(x[3], c1, acc[j][1].y));
+                for (int ks = 0; ks < KS; ++ks) {
+                    const uint64_t bh = tc05::smem_desc(bs + ks * 256, 128, sbo);
+                    const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+                    if (SPLIT == 3) {
+                        const uint64_t bl = tc05::smem_desc(bs + plane_bytes + ks * 256, 128, sbo);
+                        tc05::mma_ts(tmem, a0 + (0 * KS + ks) * 8, bh, ta.idesc, acc);
+                        tc05::mma_ts(tmem, a0 + (0 * KS + ks) * 8, bl, ta.idesc, 1u);
+                        tc05::mma_ts(tmem, a0 + (1 * KS + ks) * 8, bh, ta.idesc, 1u);
+                        tc05::mma_ts(tmem + N, a0 + (2 * KS + ks) * 8, bh, ta.idesc, acc);
+                        tc05::mma_ts(tmem + N, a0 + (2 * KS + ks) * 8, bl, ta.idesc, 1u);
+                        tc05::mma_ts(tmem + N, a0 + (3 * KS + ks) * 8, bh, ta.idesc, 1u);
+                    } else {
+                        tc05::mma_ts(tmem, a0 + ks * 8, bh, ta.idesc, acc);
+                        tc05::mma_ts(tmem + N, a0 + (KS + ks) * 8, bh, ta.idesc, acc);
+                    }
+                }
+                tc05::mma_commit(&a_empty[par]);
+                tc05::mma_commit(&b_empty[slot]);
             }
-            __syncwarp();
+            if (!ok) atomicOr(err, 4);
+            tc05::mma_commit(acc_full);
         }
-        __syncthreads();
-    }
-
-    const size_t plane_sz = (size_t)p.nx * p.ny;
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-        const int u = u0 + 4 * j + t;
-        if (u >= p.n_pad) continue;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int pl = g + 8 * h;
-            const int ix = blockIdx.x * TCX + wx * 4 + (pl & 3);
-            const int iy = blockIdx.y * TCY + wy * 4 + (pl >> 2);
-            if (ix < p.nx && iy < p.ny) G[u * plane_sz + (size_t)iy * p.nx + ix] = acc[j][h];
+    } else {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            bool ok = true;
+            int issued = 0;
+            for (int c = 0; c < C; ++c) {
+                const int slot = c % ta.nst, round = c / ta.nst;
+                if (round > 0) ok = tc05::mbar_wait(&b_empty[slot], (round - 1) & 1, budget);
+                if (!ok) break;
+                const int ilo = tg[c].ilo;
+                tc05::mbar_arrive_expect_tx(&b_full[slot], ta.slot_bytes);
+                tc05::tma_load_4d(smem + (size_t)slot * ta.slot_bytes, &tmap, &b_full[slot], 0,
+                                  ilo, u0 / 4, 2 * c);
+                issued = c + 1;
+            }
+            if (!ok) atomicOr(err, 8);
+            // every issued copy has landed before the block can exit
+            for (int s = 0; s < ta.nst && s < issued; ++s) {
+                const int n_s = (issued - 1 - s) / ta.nst + 1;   // copies into slot s
+                if (!tc05::mbar_wait(&b_full[s], (n_s - 1) & 1, budget)) atomicOr(err, 16);
+            }
         }
     }
+    tc05::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc05::tmem_dealloc(tmem, ta.tmem_cols);
 }
 
-template <int W, int NJ, int CCH>
-cudaError_t launch_tc_t(const BpDesc &p, const CoefTable &ct, const void *table,
-                        const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int S, int tc_rows,
-                        int tc_cols, cudaStream_t st) {
-    const size_t smem = TcSmem<NJ, CCH>::bytes(S, p.n_chan);
-    cudaError_t e = cudaFuncSetAttribute(k_backproject_tc<W, NJ, CCH>,
+template <int W, int KS, int SPLIT>
+cudaError_t launch_t(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
+                     const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
+                     cudaStream_t st) {
+    const size_t smem = backproject_tc_smem_bytes(ta);
+    cudaError_t e = cudaFuncSetAttribute(k_backproject_tc<W, KS, SPLIT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((p.nx + TCX - 1) / TCX, (p.ny + TCY - 1) / TCY, (p.n_pad + 4 * NJ - 1) / (4 * NJ));
-    k_backproject_tc<W, NJ, CCH><<<grid, 256, smem, st>>>(
-        p, ct, (const __nv_bfloat16 *)table, tgeo, kc_hl, G, S, tc_rows, tc_cols);
+    dim3 grid((p.nx + TCX - 1) / TCX, (p.ny + TCY - 1) / TCY, ta.n_utiles);
+    k_backproject_tc<W, KS, SPLIT><<<grid, NTHREADS, smem, st>>>(p, ct, ta, tm, tgeo, kc_hl, G,
+                                                                  err);
     return cudaGetLastError();
 }
 
-template <int NJ, int CCH>
-cudaError_t launch_tc_w(const BpDesc &p, const CoefTable &ct, const void *table,
-                        const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int S, int tc_rows,
-                        int tc_cols, cudaStream_t st) {
+template <int KS, int SPLIT>
+cudaError_t launch_w(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
+                     const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
+                     cudaStream_t st) {
     switch (p.w) {
-        case 4: return launch_tc_t<4, NJ, CCH>(p, ct, table, tgeo, kc_hl, G, S, tc_rows, tc_cols, st);
-        case 6: return launch_tc_t<6, NJ, CCH>(p, ct, table, tgeo, kc_hl, G, S, tc_rows, tc_cols, st);
-        case 8: return launch_tc_t<8, NJ, CCH>(p, ct, table, tgeo, kc_hl, G, S, tc_rows, tc_cols, st);
+        case 4: return launch_t<4, KS, SPLIT>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        case 6: return launch_t<6, KS, SPLIT>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        case 8: return launch_t<8, KS, SPLIT>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -266,25 +338,21 @@ cudaError_t launch_tc_w(const BpDesc &p, const CoefTable &ct, const void *table,
 int backproject_tc_tile_x() { return TCX; }
 int backproject_tc_tile_y() { return TCY; }
 
-// Window rows staged per channel: at least R + 18 (even base + 16-row window
-// + the 0-7 rows of rounding the first row down to 8), = 8 mod 16 so that
-// fragment loads are free of bank conflicts.
-int backproject_tc_window_rows(int R) {
-    int s = R + 18;
-    s = (s + 7) / 8 * 8;
-    if ((s / 8) % 2 == 0) s += 8;
-    return s;
+size_t backproject_tc_smem_bytes(const TcArgs &ta) {
+    const size_t s = (size_t)ta.nst * ta.slot_bytes + (2 * (size_t)ta.nst + 5) * 8 + 16;
+    // at most 2 blocks per SM (256 TMEM columns each), 1 when a block takes 512
+    const size_t floor_b = ta.tmem_cols > 256 ? 120 * 1024 : 80 * 1024;
+    return s < floor_b ? floor_b : s;
 }
 
-size_t backproject_tc_smem_bytes(int S, int tile_u, int n_chan) {
-    if (tile_u == 40) return TcSmem<10, 3>::bytes(S, n_chan);
-    return TcSmem<8, 4>::bytes(S, n_chan);
-}
-
-cudaError_t launch_backproject_tc(const BpDesc &p, const CoefTable &ct, const void *table,
-                                  const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int S,
-                                  int tc_rows, int tc_cols, cudaStream_t st) {
-    if (p.tile_u == 40)
-        return launch_tc_w<10, 3>(p, ct, table, tgeo, kc_hl, G, S, tc_rows, tc_cols, st);
-    return launch_tc_w<8, 4>(p, ct, table, tgeo, kc_hl, G, S, tc_rows, tc_cols, st);
+cudaError_t launch_backproject_tc(const BpDesc &p, const CoefTable &ct, const TcArgs &ta,
+                                  const CUtensorMap &tm, const TileGeo *tgeo, const float2 *kc_hl,
+                                  float2 *G, int *err, cudaStream_t st) {
+    if (ta.ks == 1)
+        return ta.split == 3 ? launch_w<1, 3>(p, ct, ta, tm, tgeo, kc_hl, G, err, st)
+                             : launch_w<1, 1>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+    if (ta.ks == 2)
+        return ta.split == 3 ? launch_w<2, 3>(p, ct, ta, tm, tgeo, kc_hl, G, err, st)
+                             : launch_w<2, 1>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+    return cudaErrorInvalidValue;
 }

@@ -58,5 +58,5 @@ struct NufftDesc {
     int w1;            // type-1 spreading taps
     float beta, beta1;
     double h, l0;      // table step and origin (m)
-    int tc_rows, tc_cols;   // tensor-core table layout: rows per column, columns per plane
+    int tc_ngt;        // tensor-core table layout: column groups (4 bins) per plane
 };

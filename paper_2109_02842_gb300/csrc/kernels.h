@@ -1,6 +1,7 @@
 // Launch wrappers of the CUDA kernels (internal to libpolyline).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 
@@ -17,8 +18,10 @@ cudaError_t launch_dft_strided(const float2 *in, float2 *out, int batch, int n_i
 // ---- setup.cu --------------------------------------------------------------
 // Per k_z bin: kappa range over propagating frequencies; kc = centre (double
 // and as a float pair hi + lo), kspan = kappa_max - kappa_min (0 when every
-// frequency is evanescent).
-cudaError_t launch_setup_kz(int mode, int n_pad, double dz, int n_f, const double *k,
+// frequency is evanescent). With group > 1 the range is taken over the group
+// of bins [group floor(u / group), + group) and every bin of it gets the
+// group's centre and span.
+cudaError_t launch_setup_kz(int mode, int n_pad, double dz, int n_f, const double *k, int group,
                             double *kc, float2 *kc_hl, double *kspan, cudaStream_t st);
 // Per (k_z, f): spreading position (fine cells) and source factor alpha.
 cudaError_t launch_setup_sources(const NufftDesc &d, double dz, const double *k,
@@ -41,7 +44,7 @@ size_t range_table_smem_bytes(const NufftDesc &d);
 // tw_fine: exp(-2 pi i k / fine), k < fine; fp: radix plan of `fine`.
 cudaError_t launch_range_table(const NufftDesc &d, const FftPlan &fp, const float2 *S,
                                const float2 *alpha, const float *xg, const float *dec,
-                               const float2 *tw_fine, void *table, int bf16, cudaStream_t st);
+                               const float2 *tw_fine, void *table, int fmt, cudaStream_t st);
 
 // ---- backproject.cu ------------------------------------------------------------
 // Plan-time geometry of one (pixel tile, channel): offsets of the tile centre
@@ -83,13 +86,29 @@ cudaError_t launch_setup_tile_geo(const BpDesc &p, const double *ch_xy, TileGeo 
                                   cudaStream_t st);
 int backproject_tile_x(int block_config);
 // tensor-core variant (block_config 4), backproject_tc.cu
+struct TcArgs {
+    int UT;              // k_z bins per block (multiple of 8; the MMA's N is 2 UT)
+    int NG;              // column groups per block, UT / 4
+    int n_utiles;        // blocks along k_z
+    int nst;             // table-window slots in shared memory
+    unsigned slot_bytes; // one channel's window: planes x NG x 16 ks rows x 16 B
+    unsigned idesc;      // tcgen05 instruction descriptor
+    int acol;            // first TMEM column of the A buffers (after P and Q)
+    int tmem_cols;       // TMEM columns per block (256 or 512)
+    int ks;              // 16-row K steps per channel (1 or 2)
+    int split;           // 3: BF16 hi/lo products, 1: BF16 only
+    long long budget;    // wait budget, SM clock cycles
+};
 int backproject_tc_tile_x();
 int backproject_tc_tile_y();
-int backproject_tc_window_rows(int R);
-size_t backproject_tc_smem_bytes(int S, int tile_u, int n_chan);
-cudaError_t launch_backproject_tc(const BpDesc &p, const CoefTable &ct, const void *table,
-                                  const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int S,
-                                  int tc_rows, int tc_cols, cudaStream_t st);
+size_t backproject_tc_smem_bytes(const TcArgs &ta);
+cudaError_t launch_backproject_tc(const BpDesc &p, const CoefTable &ct, const TcArgs &ta,
+                                  const CUtensorMap &tm, const TileGeo *tgeo, const float2 *kc_hl,
+                                  float2 *G, int *err, cudaStream_t st);
+// window of every (16 x 8 tile, channel): first row i_lo = the lowest first tap
+// of its 128 pixels; stats[0] = max rows spanned, stats[1] = max i_lo
+cudaError_t launch_setup_tile_geo_tc(const BpDesc &p, const double *ch_xy, TileGeo *tgeo,
+                                     int *stats, cudaStream_t st);
 int backproject_tile_y();
 
 // ---- plan.cu: error reporting for other translation units ----------------------

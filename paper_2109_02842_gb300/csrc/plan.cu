@@ -13,8 +13,28 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "plan_internal.h"
+#include "tc05.cuh"
 
 namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime.
+EncodeTiledFn encode_tiled_fn() {
+    static EncodeTiledFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
 
 thread_local std::string g_err;
 
@@ -207,9 +227,12 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         return fail(PL_ERR_ARG, "nufft_sigma must be in [1.2, 8]");
     if (o.nufft_w < 4 || o.nufft_w > 12 || (o.nufft_w & 1))
         return fail(PL_ERR_ARG, "nufft_w must be even, 4..12");
-    if (o.tile_u != 0 && o.tile_u != 8 && o.tile_u != 16 && o.tile_u != 20 && o.tile_u != 24 &&
-        o.tile_u != 32 && o.tile_u != 40)
-        return fail(PL_ERR_ARG, "tile_u must be 0, 8, 16, 20, 24, 32 or 40");
+    if (o.block_config == 4) {
+        if (o.tile_u != 0 && (o.tile_u % 8 != 0 || o.tile_u < 16 || o.tile_u > 64))
+            return fail(PL_ERR_ARG, "with block_config 4, tile_u must be 0 or a multiple of 8 in 16..64");
+    } else if (o.tile_u != 0 && o.tile_u != 8 && o.tile_u != 16 && o.tile_u != 20 && o.tile_u != 24) {
+        return fail(PL_ERR_ARG, "tile_u must be 0, 8, 16, 20 or 24");
+    }
     if (o.precision != 0 && o.precision != 1) return fail(PL_ERR_ARG, "precision must be 0 or 1");
 
     PL_CUDA(cudaGetDevice(&P->device), "cudaGetDevice");
@@ -226,20 +249,25 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     if (o.block_config < 0 || o.block_config > 4)
         return fail(PL_ERR_ARG, "block_config must be 0..4");
     P->block_config = o.block_config;
-    if (P->block_config == 4 && (o.precision != 0 || (o.nufft_w != 4 && o.nufft_w != 6 && o.nufft_w != 8)))
-        return fail(PL_ERR_UNSUPPORTED, "block_config 4 needs precision 0 and nufft_w 4, 6 or 8");
+    if (P->block_config == 4 && o.nufft_w != 4 && o.nufft_w != 6 && o.nufft_w != 8)
+        return fail(PL_ERR_UNSUPPORTED, "block_config 4 needs nufft_w 4, 6 or 8");
     {
         const int n = s->n_pad ? s->n_pad : s->n;
-        if (P->block_config == 4) {     // tensor-core variant: 32 or 40 bins per block
-            if (P->tile_u != 32 && P->tile_u != 40) {
-                const int w32 = (n + 31) / 32 * 32 - n, w40 = (n + 39) / 40 * 40 - n;
-                P->tile_u = w40 < w32 ? 40 : 32;
+        if (P->block_config == 4) {
+            // tensor-core blocks of UT bins: fewest padded bins, counting ~24
+            // bins' worth of per-channel weight work per block
+            if (P->tile_u == 0) {
+                int best = 0;
+                long long cost = 0;
+                for (int ut = 48; ut >= 16; ut -= 8) {
+                    const long long cst = (long long)((n + ut - 1) / ut) * (ut + 24);
+                    if (best == 0 || cst < cost) { best = ut; cost = cst; }
+                }
+                P->tile_u = best;
             }
         } else if (P->tile_u == 0) {    // fewest padded bins; 20 only when it wastes less than 16
             const int w16 = (n + 15) / 16 * 16 - n, w20 = (n + 19) / 20 * 20 - n;
             P->tile_u = w20 < w16 ? 20 : 16;
-        } else if (P->tile_u > 24) {
-            return fail(PL_ERR_ARG, "tile_u 32 and 40 need block_config 4");
         }
     }
     P->sigma = o.nufft_sigma;
@@ -267,7 +295,9 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     PL_CUDA(cudaMemcpy(P->d_k, k.data(), k.size() * 8, cudaMemcpyHostToDevice), "copy");
 
     cudaStream_t st = 0;
-    PL_CUDA(launch_setup_kz(P->mode, P->Np, P->dzs, P->M, P->d_k, P->d_kc, P->d_kchl,
+    // the tensor-core back-projection shares one band centre per block of bins
+    PL_CUDA(launch_setup_kz(P->mode, P->Np, P->dzs, P->M, P->d_k,
+                            P->block_config == 4 ? P->tile_u : 1, P->d_kc, P->d_kchl,
                             P->d_kspan, st), "setup_kz");
     std::vector<double> kspan(P->Np);
     PL_CUDA(cudaMemcpy(kspan.data(), P->d_kspan, P->Np * 8, cudaMemcpyDeviceToHost), "copy");
@@ -309,37 +339,76 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         amin = std::min(amin, lo + lo2);
         amax = std::max(amax, hi + hi2);
     }
-    // every tile's R-row window [i_lo, i_lo + R), centred on its range, fits:
-    // l0 = amin - ((R+1)/2 + 2) h, L = (amax - amin)/h + R + 6
-    int L = (int)std::ceil((amax - amin) / h) + P->R + 6;
-    L += L & 1;
-    if (L > 4096) return fail(PL_ERR_UNSUPPORTED, "range-profile table too long (grid too large for the band)");
-    int fine = 64, lg = 6;
-    while (fine < 2 * L) { fine <<= 1; ++lg; }
-
     NufftDesc &d = P->nd;
     d.mode = P->mode;
     d.n_chan = P->C;
     d.n_pad = P->Np;
     d.n_f = P->M;
-    d.L = L;
-    d.fine = fine;
-    d.log2_fine = lg;
     d.w = W;
     d.w1 = 7;
     d.beta = (float)(0.97 * M_PI * (1.0 - 0.5 / o.nufft_sigma) * W);
     d.beta1 = (float)(2.30 * d.w1);
     d.h = h;
-    d.l0 = amin - h * (0.5 * (P->R + 1) + 2.0);
+    int L;
+    if (P->block_config == 4) {
+        // tensor-core windows: 16 ks rows from the lowest first tap of each
+        // (16 x 8 tile, channel), found by a pass over the tile's pixels;
+        // l0 leaves w/2 + 2 rows below the nearest range
+        d.l0 = amin - h * (0.5 * W + 2.0);
+        d.L = 0;
+        BpDesc gb = make_bp(P);
+        PL_CUDA(dalloc(&P->d_tgeo, (size_t)ntx * nty * P->C, ws), "cudaMalloc");
+        int *d_stats = nullptr;
+        PL_CUDA(cudaMalloc(&d_stats, 2 * sizeof(int)), "cudaMalloc");
+        int stats[2] = {0, 0};
+        cudaError_t e = cudaMemset(d_stats, 0, 2 * sizeof(int));
+        if (e == cudaSuccess) e = launch_setup_tile_geo_tc(gb, P->d_chxy, P->d_tgeo, d_stats, st);
+        if (e == cudaSuccess) e = cudaMemcpy(stats, d_stats, sizeof(stats), cudaMemcpyDeviceToHost);
+        cudaFree(d_stats);
+        PL_CUDA(e, "setup_tile_geo_tc");
+        const int ks = stats[0] <= 16 ? 1 : (stats[0] <= 32 ? 2 : 0);
+        if (ks == 0)
+            return fail(PL_ERR_UNSUPPORTED,
+                        "a 16 x 8 pixel tile spans more than 32 table rows (grid too coarse for block_config 4)");
+        L = (int)std::ceil((amax - amin) / h) + W + 6 + 16 * ks;
+        L += L & 1;
+        if (stats[1] + 16 * ks > L) return fail(PL_ERR_UNSUPPORTED, "table window past the last row");
+        P->R = 16 * ks;
+        P->tc.ks = ks;
+    } else {
+        // every tile's R-row window [i_lo, i_lo + R), centred on its range, fits:
+        // l0 = amin - ((R+1)/2 + 2) h, L = (amax - amin)/h + R + 6
+        L = (int)std::ceil((amax - amin) / h) + P->R + 6;
+        L += L & 1;
+        d.l0 = amin - h * (0.5 * (P->R + 1) + 2.0);
+    }
+    if (L > 4096) return fail(PL_ERR_UNSUPPORTED, "range-profile table too long (grid too large for the band)");
+    int fine = 64, lg = 6;
+    while (fine < 2 * L) { fine <<= 1; ++lg; }
+    d.L = L;
+    d.fine = fine;
+    d.log2_fine = lg;
     if (range_table_smem_bytes(d) > 200 * 1024)
         return fail(PL_ERR_UNSUPPORTED, "range-profile table too long for shared memory");
     if (P->C > 8192) return fail(PL_ERR_UNSUPPORTED, "more than 8192 channels");
     if (P->block_config == 4) {
-        P->tc_S = backproject_tc_window_rows(P->R);
-        d.tc_rows = (L + P->tc_S + 7) / 8 * 8;
-        d.tc_cols = 2 * ((P->Np + P->tile_u - 1) / P->tile_u * P->tile_u);
-        if (backproject_tc_smem_bytes(P->tc_S, P->tile_u, P->C) > 200 * 1024)
-            return fail(PL_ERR_UNSUPPORTED, "table window too tall for shared memory (grid too coarse)");
+        TcArgs &ta = P->tc;
+        ta.UT = P->tile_u;
+        ta.NG = ta.UT / 4;
+        ta.n_utiles = (P->Np + ta.UT - 1) / ta.UT;
+        ta.split = P->precision == 1 ? 1 : 3;
+        const int planes = ta.split == 3 ? 2 : 1, npl = ta.split == 3 ? 4 : 2;
+        ta.slot_bytes = (unsigned)(planes * ta.NG * 16 * ta.ks * 16);
+        const int N = 2 * ta.UT;
+        const int cols = 2 * N + 2 * npl * ta.ks * 8;
+        if (cols > 512) return fail(PL_ERR_UNSUPPORTED, "tile_u too large for tensor memory");
+        ta.tmem_cols = cols <= 256 ? 256 : 512;
+        ta.acol = 2 * N;
+        const size_t pool = ta.tmem_cols > 256 ? 110 * 1024 : 72 * 1024;
+        ta.nst = (int)std::max<size_t>(2, std::min<size_t>(32, pool / ta.slot_bytes));
+        ta.idesc = tc05::idesc_bf16(128, N, 1);
+        ta.budget = 4ll << 30;
+        d.tc_ngt = ta.n_utiles * ta.UT / 4;
     } else if (backproject_smem_bytes(P->R, P->tile_u, P->C, P->precision, P->block_config) > 200 * 1024)
         return fail(PL_ERR_UNSUPPORTED, "table window too tall for shared memory (grid too coarse)");
     for (int tp = 0; tp < W; ++tp) es_tap_polynomial(W, (double)d.beta, tp, W + 1, P->coef.c[tp]);
@@ -386,7 +455,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
 
     // per (pixel tile, channel) geometry of the back-projection
     P->bp = make_bp(P);
-    {
+    if (P->block_config != 4) {
         const int tpx = P->bp.tile_px, tpy = P->bp.tile_py;
         const size_t ntiles = (size_t)((gr->nx + tpx - 1) / tpx) * ((gr->ny + tpy - 1) / tpy);
         PL_CUDA(dalloc(&P->d_tgeo, ntiles * P->C, ws), "cudaMalloc");
@@ -399,12 +468,34 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     // tensor-core layout [c][hi/lo][column][row] BF16 (zero beyond what the
     // range table writes)
     if (P->block_config == 4)
-        P->table_bytes = (size_t)P->C * 2 * d.tc_cols * d.tc_rows * 2;
+        P->table_bytes = (size_t)P->C * 2 * d.tc_ngt * L * 16;
     else
         P->table_bytes = (size_t)P->C * L * ((P->Np + 1) / 2) * (P->precision == 1 ? 8 : 16);
     ws += P->table_bytes;
     PL_CUDA(cudaMalloc(&P->d_table, P->table_bytes), "cudaMalloc");
-    if (P->block_config == 4) PL_CUDA(cudaMemset(P->d_table, 0, P->table_bytes), "cudaMemset");
+    if (P->block_config == 4) {
+        PL_CUDA(cudaMemset(P->d_table, 0, P->table_bytes), "cudaMemset");
+        // TMA map of the table [c][hi/lo][column group][row][8 BF16]: one box
+        // is a channel's window of 16 ks rows x UT/4 groups (x hi/lo)
+        EncodeTiledFn enc = encode_tiled_fn();
+        if (!enc) return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled not available");
+        const TcArgs &ta = P->tc;
+        const cuuint64_t dims[4] = {8, (cuuint64_t)L, (cuuint64_t)d.tc_ngt, 2 * (cuuint64_t)P->C};
+        const cuuint64_t strides[3] = {16, (cuuint64_t)L * 16, (cuuint64_t)d.tc_ngt * L * 16};
+        const cuuint32_t box[4] = {8, (cuuint32_t)(16 * ta.ks), (cuuint32_t)ta.NG,
+                                   (cuuint32_t)(ta.split == 3 ? 2 : 1)};
+        const cuuint32_t es[4] = {1, 1, 1, 1};
+        const CUresult r = enc(&P->tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, P->d_table, dims,
+                               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        PL_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&P->h_err), sizeof(int), cudaHostAllocMapped),
+                "cudaHostAlloc");
+        *P->h_err = 0;
+        PL_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void **>(&P->d_err), P->h_err, 0),
+                "cudaHostGetDevicePointer");
+    }
     PL_CUDA(dalloc(&P->d_G, (size_t)P->Np * gr->nx * gr->ny, ws), "cudaMalloc");
     PL_CUDA(cudaDeviceSynchronize(), "plan setup");
     return PL_OK;
@@ -423,7 +514,7 @@ pl_status pl_stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st) {
 }
 
 pl_status pl_stage_range_table(pl_plan *P, cudaStream_t st) {
-    const int fmt = P->block_config == 4 ? 2 : (P->precision == 1 ? 1 : 0);
+    const int fmt = P->block_config == 4 ? 3 : (P->precision == 1 ? 1 : 0);
     PL_CUDA(launch_range_table(P->nd, P->fineplan, P->d_S, P->d_alpha, P->d_xg, P->d_dec,
                                P->d_twfine, P->d_table, fmt, st), "range_table");
     return PL_OK;
@@ -431,8 +522,8 @@ pl_status pl_stage_range_table(pl_plan *P, cudaStream_t st) {
 
 pl_status pl_stage_backproject(pl_plan *P, cudaStream_t st) {
     if (P->block_config == 4) {
-        PL_CUDA(launch_backproject_tc(P->bp, P->coef, P->d_table, P->d_tgeo, P->d_kchl, P->d_G,
-                                      P->tc_S, P->nd.tc_rows, P->nd.tc_cols, st),
+        PL_CUDA(launch_backproject_tc(P->bp, P->coef, P->tc, P->tmap, P->d_tgeo, P->d_kchl,
+                                      P->d_G, P->d_err, st),
                 "backproject_tc");
         return PL_OK;
     }
@@ -540,13 +631,27 @@ pl_status pl_plan_destroy(pl_plan *plan) {
     return PL_OK;
 }
 
+// A bounded wait of the tensor-core back-projection that ran out in an
+// earlier execution (flags in mapped host memory: no synchronisation).
+static pl_status take_device_timeout(pl_plan *plan) {
+    if (!plan->h_err || *(volatile int *)plan->h_err == 0) return PL_OK;
+    const int bits = *(volatile int *)plan->h_err;
+    *(volatile int *)plan->h_err = 0;
+    char msg[96];
+    std::snprintf(msg, sizeof msg, "back-projection wait timed out (flags 0x%x)", bits);
+    return fail(PL_ERR_TIMEOUT, msg);
+}
+
 pl_status pl_execute(pl_plan *plan, const void *echo_dev, void *image_dev, void *stream) {
     if (!plan || !echo_dev || !image_dev) return fail(PL_ERR_ARG, "NULL argument");
+    pl_status s = take_device_timeout(plan);
+    if (s != PL_OK) return s;
     return run(plan, (const float2 *)echo_dev, (float2 *)image_dev, (cudaStream_t)stream);
 }
 
 pl_status pl_execute_host(pl_plan *plan, const void *echo_host, void *image_host, void *stream) {
     if (!plan || !echo_host || !image_host) return fail(PL_ERR_ARG, "NULL argument");
+    if (take_device_timeout(plan) != PL_OK) return PL_ERR_TIMEOUT;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t in_bytes = (size_t)plan->C * plan->N * plan->M * sizeof(float2);
     const size_t out_bytes =
@@ -563,7 +668,7 @@ pl_status pl_execute_host(pl_plan *plan, const void *echo_host, void *image_host
     PL_CUDA(cudaMemcpyAsync(image_host, plan->d_img_out, out_bytes, cudaMemcpyDeviceToHost, st),
             "copy image");
     PL_CUDA(cudaStreamSynchronize(st), "execute_host");
-    return PL_OK;
+    return take_device_timeout(plan);
 }
 
 pl_status pl_plan_get_info(const pl_plan *P, pl_info *info) {

@@ -23,7 +23,10 @@ struct pl_plan {
     NufftDesc nd{};
     double sigma = 2.0;
     int R = 0;
-    int tc_S = 0;          // tensor-core variant: window rows staged per channel
+    TcArgs tc{};           // tensor-core variant (block_config 4)
+    CUtensorMap tmap{};    // its TMA map of the range table
+    int *h_err = nullptr;  // its timeout flags (mapped host memory) and device alias
+    int *d_err = nullptr;
     CoefTable coef{};
     BpDesc bp{};
     // transforms
@@ -58,6 +61,7 @@ struct pl_plan {
         for (void *p : ptrs)
             if (p) cudaFree(p);
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+        if (h_err) cudaFreeHost(h_err);
     }
 
     cudaEvent_t next_event() {

@@ -28,9 +28,9 @@ __global__ void __launch_bounds__(256)
 k_range_table(NufftDesc d, FftPlan fp, const float2 *__restrict__ S,
               const float2 *__restrict__ alpha, const float *__restrict__ xg,
               const float *__restrict__ dec, const float2 *__restrict__ tw_g,
-              void *__restrict__ table, int bf16) {
+              void *__restrict__ table, int fmt) {
     extern __shared__ float2 smem[];
-    rt::rt_block<UB>(d, fp, S, alpha, xg, dec, tw_g, table, bf16, blockIdx.y, blockIdx.x, smem);
+    rt::rt_block<UB>(d, fp, S, alpha, xg, dec, tw_g, table, fmt, blockIdx.y, blockIdx.x, smem);
 }
 
 }  // namespace
@@ -42,22 +42,22 @@ size_t range_table_smem_bytes(const NufftDesc &d) {
 template <int UB>
 cudaError_t launch_ub(const NufftDesc &d, const FftPlan &fp, const float2 *S, const float2 *alpha,
                       const float *xg, const float *dec, const float2 *tw_fine, void *table,
-                      int bf16, cudaStream_t st) {
+                      int fmt, cudaStream_t st) {
     const size_t smem = range_table_smem_bytes(d);
     cudaError_t e = cudaFuncSetAttribute(k_range_table<UB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((d.n_pad + UB - 1) / UB, d.n_chan);
-    k_range_table<UB><<<grid, 256, smem, st>>>(d, fp, S, alpha, xg, dec, tw_fine, table, bf16);
+    k_range_table<UB><<<grid, 256, smem, st>>>(d, fp, S, alpha, xg, dec, tw_fine, table, fmt);
     return cudaGetLastError();
 }
 
 cudaError_t launch_range_table(const NufftDesc &d, const FftPlan &fp, const float2 *S,
                                const float2 *alpha, const float *xg, const float *dec,
-                               const float2 *tw_fine, void *table, int bf16, cudaStream_t st) {
+                               const float2 *tw_fine, void *table, int fmt, cudaStream_t st) {
     switch (bins_per_block(d.fine)) {
-        case 16: return launch_ub<16>(d, fp, S, alpha, xg, dec, tw_fine, table, bf16, st);
-        case 8: return launch_ub<8>(d, fp, S, alpha, xg, dec, tw_fine, table, bf16, st);
-        default: return launch_ub<4>(d, fp, S, alpha, xg, dec, tw_fine, table, bf16, st);
+        case 16: return launch_ub<16>(d, fp, S, alpha, xg, dec, tw_fine, table, fmt, st);
+        case 8: return launch_ub<8>(d, fp, S, alpha, xg, dec, tw_fine, table, fmt, st);
+        default: return launch_ub<4>(d, fp, S, alpha, xg, dec, tw_fine, table, fmt, st);
     }
 }

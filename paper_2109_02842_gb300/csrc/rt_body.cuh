@@ -18,7 +18,7 @@ __device__ __forceinline__ void rt_block(const NufftDesc &d, const FftPlan &fp,
                                          const float *__restrict__ xg,
                                          const float *__restrict__ dec,
                                          const float2 *__restrict__ tw_g, void *__restrict__ table,
-                                         int bf16, int c, int ub, float2 *smem) {
+                                         int fmt, int c, int ub, float2 *smem) {
     const int fine = d.fine;
     float2 *tw = smem;                          // [fine]: exp(-2 pi i k / fine)
     float2 *buf0 = tw + fine;                   // [UB][fine]
@@ -56,23 +56,34 @@ __device__ __forceinline__ void rt_block(const NufftDesc &d, const FftPlan &fp,
     const float2 *res = stockham_run<false>(buf0, buf1, tw, fp, +1, UB, fine, 1);
 
     // deconvolve, keep rows j = i - L/2
-    if (bf16 == 2) {
-        // tensor-core layout: [c][plane hi/lo][column 2u + (re, im)][row], BF16 hi and
-        // the BF16 residual lo = x - hi, rows contiguous
-        for (int idx = threadIdx.x; idx < 2 * UB * d.L; idx += blockDim.x) {
-            const int cl = idx / d.L;
-            const int i = idx - cl * d.L;
-            const int ul = cl >> 1;
-            if (u0 + ul >= d.n_pad) continue;
+    if (fmt == 3) {
+        // tensor-core layout [c][plane hi/lo][column group][row][8]: a group
+        // holds bins 4g .. 4g+3 as (re, im) BF16 pairs, hi = BF16(x) and
+        // lo = BF16(x - hi); bins past N_p are zero
+        __nv_bfloat16 *tb = reinterpret_cast<__nv_bfloat16 *>(table);
+        constexpr int NGB = UB / 4;
+        for (int idx = threadIdx.x; idx < NGB * d.L; idx += blockDim.x) {
+            const int gl = idx / d.L;
+            const int i = idx - gl * d.L;
             const int j = (i - d.L / 2) & (fine - 1);
-            const float2 v = cscale(res[ul * fine + j], dec[i]);
-            const float x = (cl & 1) ? v.y : v.x;
-            const __nv_bfloat16 hi = __float2bfloat16(x);
-            const __nv_bfloat16 lo = __float2bfloat16(x - __bfloat162float(hi));
-            const size_t col = 2 * (size_t)u0 + cl;
-            __nv_bfloat16 *tb = reinterpret_cast<__nv_bfloat16 *>(table);
-            tb[(((size_t)c * 2 + 0) * d.tc_cols + col) * d.tc_rows + i] = hi;
-            tb[(((size_t)c * 2 + 1) * d.tc_cols + col) * d.tc_rows + i] = lo;
+            const float s = dec[i];
+            unsigned hi[4], lo[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int ul = 4 * gl + b;
+                const float2 v = u0 + ul < d.n_pad ? cscale(res[ul * fine + j], s)
+                                                   : make_float2(0.f, 0.f);
+                __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+                const float2 hf = __bfloat1622float2(h);
+                __nv_bfloat162 l = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+                hi[b] = *reinterpret_cast<unsigned *>(&h);
+                lo[b] = *reinterpret_cast<unsigned *>(&l);
+            }
+            const size_t g = (size_t)(u0 / 4 + gl);
+            const size_t o0 = (((size_t)c * 2 + 0) * d.tc_ngt + g) * d.L + i;
+            const size_t o1 = (((size_t)c * 2 + 1) * d.tc_ngt + g) * d.L + i;
+            reinterpret_cast<uint4 *>(tb)[o0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            reinterpret_cast<uint4 *>(tb)[o1] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
         return;
     }
@@ -89,7 +100,7 @@ __device__ __forceinline__ void rt_block(const NufftDesc &d, const FftPlan &fp,
         const float2 a = cscale(res[(2 * q) * fine + j], s);
         const float2 e = cscale(res[(2 * q + 1) * fine + j], s);
         const size_t o = ((size_t)c * d.L + i) * np2 + p0 + q;
-        if (!bf16) {
+        if (fmt == 0) {
             reinterpret_cast<float4 *>(table)[o] = make_float4(a.x, e.x, a.y, e.y);
         } else {
             __nv_bfloat162 re = __floats2bfloat162_rn(a.x, e.x);

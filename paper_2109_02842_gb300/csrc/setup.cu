@@ -21,6 +21,7 @@
 // b_i itself is a type-1 transform (nonuniform sources -> uniform rows),
 // computed by spreading onto a fine periodic grid, an FFT, and division by
 // the spreading kernel's transform (range_table.cu).
+#include <climits>
 #include <math.h>
 
 #include "common.cuh"
@@ -37,20 +38,23 @@ __device__ __forceinline__ double kappa_sq(int mode, double k, double kz) {
     return mode == 0 ? 4.0 * k * k - kz * kz : k * k - 0.25 * kz * kz;
 }
 
-__global__ void k_setup_kz(int mode, int n_pad, double dz, int n_f, const double *k, double *kc,
-                           float2 *kc_hl, double *kspan) {
+__global__ void k_setup_kz(int mode, int n_pad, double dz, int n_f, const double *k, int group,
+                           double *kc, float2 *kc_hl, double *kspan) {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n_pad) return;
-    const double kz = kz_of(u, n_pad, dz);
+    const int g0 = u / group * group, g1 = min(g0 + group, n_pad);
     double lo = 0.0, hi = 0.0;
     bool any = false;
-    for (int m = 0; m < n_f; ++m) {
-        const double q = kappa_sq(mode, k[m], kz);
-        if (q <= 0.0) continue;
-        const double kap = sqrt(q);
-        if (!any) { lo = hi = kap; any = true; }
-        lo = fmin(lo, kap);
-        hi = fmax(hi, kap);
+    for (int v = g0; v < g1; ++v) {
+        const double kz = kz_of(v, n_pad, dz);
+        for (int m = 0; m < n_f; ++m) {
+            const double q = kappa_sq(mode, k[m], kz);
+            if (q <= 0.0) continue;
+            const double kap = sqrt(q);
+            if (!any) { lo = hi = kap; any = true; }
+            lo = fmin(lo, kap);
+            hi = fmax(hi, kap);
+        }
     }
     kc[u] = any ? 0.5 * (lo + hi) : 0.0;
     const float kh = (float)kc[u];
@@ -169,13 +173,74 @@ __global__ void k_setup_tile_geo(BpDesc p, int ntx, int nty, const double *ch_xy
     out[idx] = g;
 }
 
+// Window of every (16 x 8 tile, channel) for the tensor-core back-projection:
+// i_lo = the lowest first tap ceil(pos - w/2) over the tile's pixels (pos in
+// table rows, FP64, with a 1e-3-row margin against the kernel's FP32
+// rounding); stats[0] collects the rows the window must span, stats[1] the
+// largest i_lo.
+__global__ void k_setup_tile_geo_tc(BpDesc p, int ntx, int nty, const double *ch_xy, TileGeo *out,
+                                    int *stats) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)ntx * nty * p.n_chan) return;
+    const int c = (int)(idx % p.n_chan);
+    const int tile = (int)(idx / p.n_chan);
+    const int tx = tile % ntx, ty = tile / ntx;
+    const int TX = p.tile_px, TY = p.tile_py;
+    const double xT = ch_xy[4 * c + 0], yT = ch_xy[4 * c + 1];
+    const double xR = ch_xy[4 * c + 2], yR = ch_xy[4 * c + 3];
+    auto range = [&](double x, double y) {
+        double a = sqrt((x - xT) * (x - xT) + (y - yT) * (y - yT));
+        if (p.mode == 1) a += sqrt((x - xR) * (x - xR) + (y - yR) * (y - yR));
+        return a;
+    };
+    const double xc = p.x0 + (tx * TX + 0.5 * (TX - 1)) * p.dx;
+    const double yc = p.y0 + (ty * TY + 0.5 * (TY - 1)) * p.dy;
+    const double half = 0.5 * p.w;
+    long long lo = LLONG_MAX, hi = LLONG_MIN;
+    for (int j = 0; j < TY; ++j)
+        for (int i = 0; i < TX; ++i) {
+            const double pos = (range(p.x0 + (tx * TX + i) * p.dx, p.y0 + (ty * TY + j) * p.dy) -
+                                p.l0) / p.h;
+            lo = min(lo, (long long)ceil(pos - half - 1e-3));
+            hi = max(hi, (long long)ceil(pos - half + 1e-3) + p.w);
+        }
+    const int ilo = (int)max(lo, 0ll);
+    TileGeo g;
+    const double dxt = xc - xT, dyt = yc - yT, rt = sqrt(dxt * dxt + dyt * dyt);
+    double a = rt;
+    g.dxt = (float)dxt; g.dyt = (float)dyt; g.rt = (float)rt;
+    g.dxr = g.dyr = g.rr = 0.f;
+    if (p.mode == 1) {
+        const double dxr = xc - xR, dyr = yc - yR, rr = sqrt(dxr * dxr + dyr * dyr);
+        a += rr;
+        g.dxr = (float)dxr; g.dyr = (float)dyr; g.rr = (float)rr;
+    }
+    g.ilo = ilo;
+    g.off = (float)(a - (p.l0 + ilo * p.h));
+    g.a_hi = (float)a;
+    g.a_lo = (float)(a - (double)g.a_hi);
+    g.pad0 = g.pad1 = 0.f;
+    out[idx] = g;
+    atomicMax(&stats[0], (int)(hi - ilo));
+    atomicMax(&stats[1], ilo);
+}
+
 inline int blocks(long long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
-cudaError_t launch_setup_kz(int mode, int n_pad, double dz, int n_f, const double *k,
+cudaError_t launch_setup_tile_geo_tc(const BpDesc &p, const double *ch_xy, TileGeo *tgeo,
+                                     int *stats, cudaStream_t st) {
+    const int ntx = (p.nx + p.tile_px - 1) / p.tile_px, nty = (p.ny + p.tile_py - 1) / p.tile_py;
+    k_setup_tile_geo_tc<<<blocks((long long)ntx * nty * p.n_chan, 128), 128, 0, st>>>(
+        p, ntx, nty, ch_xy, tgeo, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup_kz(int mode, int n_pad, double dz, int n_f, const double *k, int group,
                             double *kc, float2 *kc_hl, double *kspan, cudaStream_t st) {
-    k_setup_kz<<<blocks(n_pad, 128), 128, 0, st>>>(mode, n_pad, dz, n_f, k, kc, kc_hl, kspan);
+    k_setup_kz<<<blocks(n_pad, 128), 128, 0, st>>>(mode, n_pad, dz, n_f, k, group < 1 ? 1 : group,
+                                                   kc, kc_hl, kspan);
     return cudaGetLastError();
 }
 

@@ -235,29 +235,48 @@ def test_full_size_sampled_columns(binding, which):
     assert report("image %s sampled" % which, got, ref) < TOL_FP32
 
 
-# --- tensor-core interpolation (block_config 4) -----------------------------------
+# --- tensor cores (block_config 4: tcgen05, TMEM accumulators, TMA windows) -------
 
-@pytest.mark.parametrize("case", ["small_mono", "small_multi", "ragged"])
+@pytest.mark.parametrize("case", ["small_mono", "small_multi", "ragged", "tile16", "tile48"])
 def test_tensor_core_variant_small(binding, case):
-    if case == "small_mono":
-        w = wl.small_mono(seed=0)
-    elif case == "small_multi":
+    opts = {}
+    if case == "small_multi":
         w = small_multi()
-    else:
+    elif case == "ragged":
         w = wl.small_mono(seed=3)
         w.grid = dict(w.grid, nx=37, ny=23, nz=7, z0=-0.031, dz=0.0093)
+    else:
+        w = wl.small_mono(seed=0)
+        if case != "small_mono":
+            opts["tile_u"] = int(case[4:])
     echo = scene_echo(w)
-    plan, img = run_gpu(binding, w, echo, block_config=4)
-    assert plan.info["nufft_w"] == 6
+    plan, img = run_gpu(binding, w, echo, block_config=4, **opts)
+    i = plan.info
+    print("%s: tile_u %s, window rows %d, table rows %d" % (case, opts.get("tile_u", "auto"),
+                                                          i["slab_rows"], i["table_len"]))
+    assert i["nufft_w"] == 6 and i["slab_rows"] in (16, 32)
     ref = image_ref(w, echo)
     assert report("image tc %s" % case, img.reshape(w.grid["nz"], -1), ref) < TOL_FP32
+    # a second execution reports any bounded wait of the first that ran out
+    plan.execute(torch.from_numpy(echo).cuda())
+    torch.cuda.synchronize()
+
+
+def test_tensor_core_bf16_only_products(binding):
+    w = wl.small_mono(seed=2)
+    echo = scene_echo(w, 2)
+    _, img = run_gpu(binding, w, echo, block_config=4, precision=1)
+    ref = image_ref(w, echo)
+    assert report("image tc bf16", img.reshape(w.grid["nz"], -1), ref) < TOL_BF16
 
 
 @pytest.mark.parametrize("which", ["full_mono", "multi"])
 def test_tensor_core_variant_full_size_sampled(binding, which):
     w = wl.WORKLOADS[which](seed=0)
     echo = scene_echo(w, 0, n_pts=24)
-    _, img = run_gpu(binding, w, echo, block_config=4)
+    plan, img = run_gpu(binding, w, echo, block_config=4)
+    print("%s: window rows %d, table rows %d" % (which, plan.info["slab_rows"],
+                                                plan.info["table_len"]))
     idx = sampled_columns(w, 48, 1)
     ref = image_ref(w, echo, w.pix_xy()[idx])
     got = img.reshape(w.grid["nz"], -1)[:, idx]
