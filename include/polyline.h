@@ -104,7 +104,7 @@ typedef struct {
  * nufft_sigma: oversampling of the range-profile grid (default 2.0).
  * nufft_w: interpolation taps (even, 4..12; default 6).
  * tile_u: k_z bins per back-projection block (8, 16, 20 or 24; with
- *         block_config 4 a multiple of 8 in 16..64; 0 = chosen from n_pad).
+ *         block_config 4 a multiple of 8 in 16..112; 0 = chosen from n_pad).
  * block_config: back-projection kernel (0 = default: 3 when the x step is
  *         below the table step, else 1; 1 = FP32, one pixel per thread,
  *         8-channel chunks, 3 blocks per SM; 2 = FP32, one pixel per thread,
@@ -113,8 +113,8 @@ typedef struct {
  *         block, the channel sum accumulated in tensor memory, one band centre
  *         per block of bins, BF16 operands split hi + lo (precision 0) or BF16
  *         only (precision 1); needs nufft_w 4, 6 or 8. With 4 the range-table
- *         workspace holds [channel][hi/lo][column group of 4 bins][row][8] BF16:
- *         (re, im) of the group's bins, hi = BF16(x), lo = BF16(x - hi).
+ *         workspace holds [channel][hi/lo][row][column 2u + (re, im)] BF16,
+ *         hi = BF16(x), lo = BF16(x - hi).
  *         A bounded device wait of block_config 4 that runs out makes the next
  *         pl_execute / pl_execute_host call return PL_ERR_TIMEOUT.) */
 typedef struct {

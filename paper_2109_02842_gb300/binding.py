@@ -272,9 +272,9 @@ class Plan:
             # rows of planar bin pairs {re_u, re_u+1, im_u, im_u+1}
             shape = (i["n_chan"], i["table_len"], (i["n_pad"] + 1) // 2, 4)
             if nbytes.value not in (np.prod(shape) * 2, np.prod(shape) * 4):
-                # tensor-core layout [c][hi/lo][column group][row][8] (BF16)
-                ngt = nbytes.value // (i["n_chan"] * 2 * i["table_len"] * 16)
-                shape = (i["n_chan"], 2, ngt, i["table_len"], 8)
+                # tensor-core layout [c][hi/lo][row][column 2u + (re, im)] (BF16)
+                cols = nbytes.value // (i["n_chan"] * 2 * i["table_len"] * 2)
+                shape = (i["n_chan"], 2, i["table_len"], cols)
                 raw = torch.as_tensor(_DevArray(ptr.value, shape, "<i2"), device="cuda")
                 return raw.view(torch.bfloat16)
             if nbytes.value == np.prod(shape) * 2:   # BF16

@@ -18,22 +18,24 @@
 // and the product taken as hi.hi + hi.lo + lo.hi (SPLIT = 3), relative
 // error ~1e-5; SPLIT = 1 takes hi.hi only (~1e-3).
 //
-// Block = 16 x 8 pixels x UT bins, 10 warps:
-//  * warps 0-7 build A: warp w owns TMEM lanes 32 (w % 4) .. +31 (its
-//    pixels) for the channels of parity w / 4. Per channel a thread forms
+// Block = 16 x 8 pixels x UT bins, 4 NPAR + 2 warps (NPAR = 2 with up to 48
+// bins and two blocks per SM, NPAR = 3 with up to 104 bins and one block per
+// SM: 256 or 512 TMEM columns a block):
+//  * warps 0 .. 4 NPAR - 1 build A: warp w owns TMEM lanes 32 (w % 4) .. +31
+//    (its pixels) for the channels c = w / 4 (mod NPAR). Per channel a thread forms
 //    its pixel's range offset, the w tap weights (per-tap polynomials of the
 //    ES kernel), the carrier, the BF16 hi/lo parts, shifts them to the taps'
 //    position in the 16 KS-row window and writes the row to TMEM
-//    (tcgen05.st); one A buffer per parity, so one parity is being written
-//    while the MMAs read the other;
-//  * warp 8 (one thread) issues the tcgen05.mma chain of each channel and
+//    (tcgen05.st); one A buffer per channel class, so NPAR - 1 classes are
+//    being written while the MMAs read the other;
+//  * warp 4 NPAR (one thread) issues the tcgen05.mma chain of each channel and
 //    commits its completion to the barriers that free the A buffer and the
 //    table slot;
-//  * warp 9 (one thread) streams the table windows with TMA: one 4-D box
-//    (8 columns x 16 KS rows x UT/4 column groups x hi/lo) per channel into
-//    a ring of smem slots. The table is stored [c][hi/lo][column group][row][8],
-//    which is the MN-major no-swizzle layout the MMA reads, and a window may
-//    start at any row.
+//  * warp 4 NPAR + 1 (one thread) streams the table windows with TMA into a
+//    ring of smem slots: per channel ceil(2 UT / 64) boxes of 64 columns x
+//    16 KS rows x hi/lo from the row-major table [c][hi/lo][row][column],
+//    written with 128-byte swizzling, which is the MN-major layout the MMA
+//    reads (64-column atoms, rows 128 B apart); a window may start at any row.
 // At the end the accumulators (P, Q: 2 x 2 UT FP32 columns) are read back
 // with tcgen05.ld and written as G[u][y][x].
 //
@@ -50,8 +52,11 @@
 namespace {
 
 constexpr int TCX = 16, TCY = 8;
-constexpr int NCW = 8;                       // A-building warps
-constexpr int NTHREADS = (NCW + 2) * 32;     // + MMA warp + TMA warp
+template <int NPAR>
+struct Warps {
+    static constexpr int compute = 4 * NPAR;          // A-building warps
+    static constexpr int threads = (compute + 2) * 32; // + MMA warp + TMA warp
+};
 
 // Put the NT words t at word offset wo of an NW-word row, zeros elsewhere
 // (a barrel shift over the bits of wo; words pushed past NW are dropped).
@@ -77,21 +82,31 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
     lo = bf2(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xffff0000u));
 }
 
-template <int W, int KS, int SPLIT>
-__global__ void __launch_bounds__(NTHREADS, 2)
+template <int W, int KS, int SPLIT, int NPAR>
+__global__ void __launch_bounds__(Warps<NPAR>::threads, NPAR == 2 ? 2 : 1)
 k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUtensorMap tmap,
                  const TileGeo *__restrict__ tgeo, const float2 *__restrict__ kc_hl,
                  float2 *__restrict__ G, int *err) {
+    constexpr int NCW = Warps<NPAR>::compute;
     constexpr int NPL = SPLIT == 3 ? 4 : 2;     // A planes: (re, im) x (hi[, lo])
     constexpr int NW = 8 * KS;                  // 32-bit words of an A row (16 KS BF16)
     constexpr int NT = W / 2 + 1;               // words of the taps after the parity shift
     constexpr int ND = W + 2;                   // polynomial coefficients per tap
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // swizzled TMA destinations and MMA operands sit on 1024-byte boundaries
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    // Channels go in groups of NPAR (channel c = NPAR g + k, class k); the
+    // slots form NSG slot groups of NPAR. b_full[s]: the windows of the group
+    // in slot group s landed (TMA); done[s]: that group's products completed
+    // (frees the slot group); a_full[k]: A of class k written (its 4 warps);
+    // a_done[k]: the products reading class k's A buffer completed.
+    const int NSG = ta.nst / NPAR;
     uint64_t *b_full = reinterpret_cast<uint64_t *>(smem + (size_t)ta.nst * ta.slot_bytes);
-    uint64_t *b_empty = b_full + ta.nst;
-    uint64_t *a_full = b_empty + ta.nst;        // [2], 4 arrivals (the parity's warps)
-    uint64_t *a_empty = a_full + 2;             // [2], MMA completion
-    uint64_t *acc_full = a_empty + 2;
+    uint64_t *done = b_full + NSG;
+    uint64_t *a_full = done + NSG;
+    uint64_t *a_done = a_full + NPAR;
+    uint64_t *acc_full = a_done + NPAR;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_full + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -102,13 +117,13 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
     const long long budget = ta.budget;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < ta.nst; ++s) {
+        for (int s = 0; s < NSG; ++s) {
             tc05::mbar_init(&b_full[s], 1);
-            tc05::mbar_init(&b_empty[s], 1);
+            tc05::mbar_init(&done[s], 1);
         }
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < NPAR; ++k) {
             tc05::mbar_init(&a_full[k], 4);
-            tc05::mbar_init(&a_empty[k], 1);
+            tc05::mbar_init(&a_done[k], 1);
         }
         tc05::mbar_init(acc_full, 1);
         tc05::fence_mbar_init();
@@ -135,8 +150,12 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
         const float2 kT = kc_hl[u0];
         bool ok = true;
         int it = 0;
-        for (int c = par; c < C; c += 2, ++it) {
-            const TileGeo g = tg[c];
+        // the geometry of the class's next channel is loaded one round ahead
+        TileGeo gn;
+        if (par < C) gn = tg[par];
+        for (int c = par; c < C; c += NPAR, ++it) {
+            const TileGeo g = gn;
+            if (c + NPAR < C) gn = tg[c + NPAR];
             // delta = a - a* from rho^2 - rho*^2 = d (2 D + d): no cancellation
             float ex = g.dxt + ddx, ey = g.dyt + ddy;
             float num = fmaf(ddx, 2.0f * g.dxt + ddx, ddy * (2.0f * g.dyt + ddy));
@@ -193,8 +212,8 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
 #pragma unroll
                 for (int pl = 0; pl < NPL; ++pl) place<NW, NT>(tw[pl], o >> 1, rows[pl]);
             }
-            // the products of channel c - 2 must be done with this buffer
-            if (it > 0) ok = tc05::mbar_wait(&a_empty[par], (it - 1) & 1, budget);
+            // the products of this class's previous channel must be done
+            if (it > 0) ok = tc05::mbar_wait(&a_done[par], (uint32_t)(it - 1) & 1u, budget);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             tc05::fence_after_sync();
@@ -223,7 +242,7 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
             const bool inside = ix < p.nx && iy < p.ny;
             const size_t plane = (size_t)p.nx * p.ny;
             const size_t pofs = (size_t)iy * p.nx + ix;
-            for (int ch = par; ch < (int)(N / 16); ch += 2) {
+            for (int ch = par; ch < (int)(N / 16); ch += NPAR) {
                 uint32_t pv[16], qv[16];
                 tc05::tmem_ld16(lane_base + 16 * ch, pv);
                 tc05::tmem_ld16(lane_base + N + 16 * ch, qv);
@@ -243,61 +262,111 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
         }
     } else if (warp == NCW) {
         // ------------------------------------------------ MMA issue
-        if (lane == 0) {
-            const uint32_t sbase = tc05::smem_addr(smem);
-            const uint32_t plane_bytes = (uint32_t)ta.NG * 16 * KS * 16;
-            const uint32_t sbo = 16 * KS * 16;     // column-group stride; 128 B between 8-row groups
-            bool ok = true;
-            for (int c = 0; c < C; ++c) {
-                const int par = c & 1, it = c >> 1, slot = c % ta.nst, round = c / ta.nst;
-                ok = tc05::mbar_wait(&b_full[slot], round & 1, budget) &&
-                     tc05::mbar_wait(&a_full[par], it & 1, budget);
+        // The whole warp runs the loop on warp-uniform counters (so addresses
+        // and descriptors stay in uniform registers); one lane issues. One
+        // pass per group of NPAR channels: one wait for the group's windows,
+        // then per class a wait for its A, its products and a commit that
+        // frees its A buffer; one commit frees the group's slots.
+        const uint32_t lo16 = (16 * KS * 128) >> 4;       // lo plane, 16-byte units
+        const uint64_t d0 = tc05::smem_desc_sw128(tc05::smem_addr(smem), ta.cb_bytes, 1024);
+        const uint32_t slot16 = ta.slot_bytes >> 4;
+        const uint32_t abase = tmem + ta.acol;
+        const int n_groups = (C + NPAR - 1) / NPAR;
+        bool ok = true;
+        int sg = 0;
+        uint32_t bpar = 0;
+        for (int g = 0; g < n_groups && ok; ++g) {
+            const int nch = min(NPAR, C - g * NPAR);
+            ok = tc05::mbar_wait(&b_full[sg], bpar, budget);
+#pragma unroll
+            for (int k = 0; k < NPAR; ++k) {
+                if (k >= nch) break;
+                ok = ok && tc05::mbar_wait(&a_full[k], (uint32_t)g & 1u, budget);
+                ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 tc05::fence_after_sync();
-                const uint32_t bs = sbase + slot * ta.slot_bytes;
-                const uint32_t a0 = tmem + ta.acol + par * (NPL * KS * 8);
+                if (lane == 0) {
+                    const uint32_t a0 = abase + k * (NPL * KS * 8);
+                    const uint64_t dk = d0 + (uint64_t)((sg * NPAR + k) * slot16);
 #pragma unroll
-                for (int ks = 0; ks < KS; ++ks) {
-                    const uint64_t bh = tc05::smem_desc(bs + ks * 256, 128, sbo);
-                    const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
-                    if (SPLIT == 3) {
-                        const uint64_t bl = tc05::smem_desc(bs + plane_bytes + ks * 256, 128, sbo);
-                        tc05::mma_ts(tmem, a0 + (0 * KS + ks) * 8, bh, ta.idesc, acc);
-                        tc05::mma_ts(tmem, a0 + (0 * KS + ks) * 8, bl, ta.idesc, 1u);
-                        tc05::mma_ts(tmem, a0 + (1 * KS + ks) * 8, bh, ta.idesc, 1u);
-                        tc05::mma_ts(tmem + N, a0 + (2 * KS + ks) * 8, bh, ta.idesc, acc);
-                        tc05::mma_ts(tmem + N, a0 + (2 * KS + ks) * 8, bl, ta.idesc, 1u);
-                        tc05::mma_ts(tmem + N, a0 + (3 * KS + ks) * 8, bh, ta.idesc, 1u);
-                    } else {
-                        tc05::mma_ts(tmem, a0 + ks * 8, bh, ta.idesc, acc);
-                        tc05::mma_ts(tmem + N, a0 + (KS + ks) * 8, bh, ta.idesc, acc);
+                    for (int ks = 0; ks < KS; ++ks) {
+                        const uint64_t bh = dk + (uint64_t)(ks * (2048 >> 4));
+                        const uint32_t acc = (g > 0 || k > 0 || ks > 0) ? 1u : 0u;
+                        if (SPLIT == 3) {
+                            const uint64_t bl = bh + lo16;
+                            tc05::mma_ts(tmem, a0 + (0 * KS + ks) * 8, bh, ta.idesc, acc);
+                            tc05::mma_ts(tmem, a0 + (0 * KS + ks) * 8, bl, ta.idesc, 1u);
+                            tc05::mma_ts(tmem, a0 + (1 * KS + ks) * 8, bh, ta.idesc, 1u);
+                            tc05::mma_ts(tmem + N, a0 + (2 * KS + ks) * 8, bh, ta.idesc, acc);
+                            tc05::mma_ts(tmem + N, a0 + (2 * KS + ks) * 8, bl, ta.idesc, 1u);
+                            tc05::mma_ts(tmem + N, a0 + (3 * KS + ks) * 8, bh, ta.idesc, 1u);
+                        } else {
+                            tc05::mma_ts(tmem, a0 + ks * 8, bh, ta.idesc, acc);
+                            tc05::mma_ts(tmem + N, a0 + (KS + ks) * 8, bh, ta.idesc, acc);
+                        }
                     }
+                    tc05::mma_commit(&a_done[k]);
                 }
-                tc05::mma_commit(&a_empty[par]);
-                tc05::mma_commit(&b_empty[slot]);
+                __syncwarp();
             }
+            if (!ok) break;
+            if (lane == 0) tc05::mma_commit(&done[sg]);
+            __syncwarp();
+            if (++sg == NSG) {
+                sg = 0;
+                bpar ^= 1u;
+            }
+        }
+        if (lane == 0) {
             if (!ok) atomicOr(err, 4);
             tc05::mma_commit(acc_full);
         }
     } else {
         // ------------------------------------------------ TMA producer
-        if (lane == 0) {
-            bool ok = true;
-            int issued = 0;
-            for (int c = 0; c < C; ++c) {
-                const int slot = c % ta.nst, round = c / ta.nst;
-                if (round > 0) ok = tc05::mbar_wait(&b_empty[slot], (round - 1) & 1, budget);
-                if (!ok) break;
-                const int ilo = tg[c].ilo;
-                tc05::mbar_arrive_expect_tx(&b_full[slot], ta.slot_bytes);
-                tc05::tma_load_4d(smem + (size_t)slot * ta.slot_bytes, &tmap, &b_full[slot], 0,
-                                  ilo, u0 / 4, 2 * c);
-                issued = c + 1;
+        // (the whole warp runs the loop; one lane issues the copies)
+        const int n_groups = (C + NPAR - 1) / NPAR;
+        bool ok = true;
+        int issued = 0;          // groups issued
+        int sg = 0;
+        uint32_t dpar = 0;
+        int ilo_next[NPAR];      // first window rows, one group ahead
+#pragma unroll
+        for (int k = 0; k < NPAR; ++k) ilo_next[k] = k < C ? tg[k].ilo : 0;
+        for (int g = 0; g < n_groups; ++g) {
+            const int nch = min(NPAR, C - g * NPAR);
+            int ilo[NPAR];
+#pragma unroll
+            for (int k = 0; k < NPAR; ++k) {
+                ilo[k] = ilo_next[k];
+                const int cn = (g + 1) * NPAR + k;
+                if (cn < C) ilo_next[k] = tg[cn].ilo;
             }
+            // group g reuses the slot group of group g - NSG: phase g / NSG - 1
+            if (g >= NSG) ok = tc05::mbar_wait(&done[sg], dpar, budget);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            if (lane == 0) {
+                tc05::mbar_arrive_expect_tx(&b_full[sg], (uint32_t)nch * ta.slot_bytes);
+#pragma unroll
+                for (int k = 0; k < NPAR; ++k) {
+                    if (k >= nch) break;
+                    unsigned char *dst = smem + (size_t)(sg * NPAR + k) * ta.slot_bytes;
+                    for (int j = 0; j < ta.ncb; ++j)
+                        tc05::tma_load_3d(dst + (size_t)j * ta.cb_bytes, &tmap, &b_full[sg],
+                                          2 * u0 + 64 * j, ilo[k], 2 * (g * NPAR + k));
+                }
+            }
+            issued = g + 1;
+            if (++sg == NSG) {
+                sg = 0;
+                if (g + 1 >= 2 * NSG) dpar ^= 1u;
+            }
+        }
+        // every issued copy has landed before the block can exit
+        if (lane == 0) {
             if (!ok) atomicOr(err, 8);
-            // every issued copy has landed before the block can exit
-            for (int s = 0; s < ta.nst && s < issued; ++s) {
-                const int n_s = (issued - 1 - s) / ta.nst + 1;   // copies into slot s
+            for (int s = 0; s < NSG && s < issued; ++s) {
+                const int n_s = (issued - 1 - s) / NSG + 1;   // groups loaded into slot group s
                 if (!tc05::mbar_wait(&b_full[s], (n_s - 1) & 1, budget)) atomicOr(err, 16);
             }
         }
@@ -307,30 +376,39 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
     if (warp == 0) tc05::tmem_dealloc(tmem, ta.tmem_cols);
 }
 
-template <int W, int KS, int SPLIT>
+template <int W, int KS, int SPLIT, int NPAR>
 cudaError_t launch_t(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
                      const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
                      cudaStream_t st) {
     const size_t smem = backproject_tc_smem_bytes(ta);
-    cudaError_t e = cudaFuncSetAttribute(k_backproject_tc<W, KS, SPLIT>,
+    cudaError_t e = cudaFuncSetAttribute(k_backproject_tc<W, KS, SPLIT, NPAR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((p.nx + TCX - 1) / TCX, (p.ny + TCY - 1) / TCY, ta.n_utiles);
-    k_backproject_tc<W, KS, SPLIT><<<grid, NTHREADS, smem, st>>>(p, ct, ta, tm, tgeo, kc_hl, G,
-                                                                  err);
+    k_backproject_tc<W, KS, SPLIT, NPAR><<<grid, Warps<NPAR>::threads, smem, st>>>(
+        p, ct, ta, tm, tgeo, kc_hl, G, err);
     return cudaGetLastError();
 }
 
-template <int KS, int SPLIT>
+template <int KS, int SPLIT, int NPAR>
 cudaError_t launch_w(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
                      const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
                      cudaStream_t st) {
     switch (p.w) {
-        case 4: return launch_t<4, KS, SPLIT>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
-        case 6: return launch_t<6, KS, SPLIT>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
-        case 8: return launch_t<8, KS, SPLIT>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        case 4: return launch_t<4, KS, SPLIT, NPAR>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        case 6: return launch_t<6, KS, SPLIT, NPAR>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        case 8: return launch_t<8, KS, SPLIT, NPAR>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+template <int KS, int SPLIT>
+cudaError_t launch_p(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
+                     const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
+                     cudaStream_t st) {
+    if (ta.npar == 3) return launch_w<KS, SPLIT, 3>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+    if (ta.npar == 2) return launch_w<KS, SPLIT, 2>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -339,7 +417,8 @@ int backproject_tc_tile_x() { return TCX; }
 int backproject_tc_tile_y() { return TCY; }
 
 size_t backproject_tc_smem_bytes(const TcArgs &ta) {
-    const size_t s = (size_t)ta.nst * ta.slot_bytes + (2 * (size_t)ta.nst + 5) * 8 + 16;
+    const size_t s = 1024 + (size_t)ta.nst * ta.slot_bytes + (2 * (size_t)ta.nst + 2 * 3 + 1) * 8 + 16;
+    // (barriers: 2 per slot group plus the classes' and the accumulator's)
     // at most 2 blocks per SM (256 TMEM columns each), 1 when a block takes 512
     const size_t floor_b = ta.tmem_cols > 256 ? 120 * 1024 : 80 * 1024;
     return s < floor_b ? floor_b : s;
@@ -349,10 +428,10 @@ cudaError_t launch_backproject_tc(const BpDesc &p, const CoefTable &ct, const Tc
                                   const CUtensorMap &tm, const TileGeo *tgeo, const float2 *kc_hl,
                                   float2 *G, int *err, cudaStream_t st) {
     if (ta.ks == 1)
-        return ta.split == 3 ? launch_w<1, 3>(p, ct, ta, tm, tgeo, kc_hl, G, err, st)
-                             : launch_w<1, 1>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        return ta.split == 3 ? launch_p<1, 3>(p, ct, ta, tm, tgeo, kc_hl, G, err, st)
+                             : launch_p<1, 1>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
     if (ta.ks == 2)
-        return ta.split == 3 ? launch_w<2, 3>(p, ct, ta, tm, tgeo, kc_hl, G, err, st)
-                             : launch_w<2, 1>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        return ta.split == 3 ? launch_p<2, 3>(p, ct, ta, tm, tgeo, kc_hl, G, err, st)
+                             : launch_p<2, 1>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
     return cudaErrorInvalidValue;
 }

@@ -52,11 +52,11 @@ struct NufftDesc {
     int mode;          // 0 mono, 1 multi
     int n_chan, n_pad, n_f;
     int L;             // table rows
-    int fine;          // type-1 fine grid length (power of two)
+    int fine;          // type-1 fine grid length (2^a 3^b 5^c)
     int log2_fine;
     int w;             // interpolation taps
     int w1;            // type-1 spreading taps
     float beta, beta1;
     double h, l0;      // table step and origin (m)
-    int tc_ngt;        // tensor-core table layout: column groups (4 bins) per plane
+    int tc_cols;       // tensor-core table layout: columns (2 per bin) per row
 };

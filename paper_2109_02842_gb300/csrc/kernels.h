@@ -88,15 +88,17 @@ int backproject_tile_x(int block_config);
 // tensor-core variant (block_config 4), backproject_tc.cu
 struct TcArgs {
     int UT;              // k_z bins per block (multiple of 8; the MMA's N is 2 UT)
-    int NG;              // column groups per block, UT / 4
+    int ncb;             // 64-column blocks of a block's window, ceil(2 UT / 64)
     int n_utiles;        // blocks along k_z
     int nst;             // table-window slots in shared memory
-    unsigned slot_bytes; // one channel's window: planes x NG x 16 ks rows x 16 B
+    unsigned cb_bytes;   // one column block: planes x 16 ks rows x 128 B
+    unsigned slot_bytes; // one channel's window: ncb x cb_bytes
     unsigned idesc;      // tcgen05 instruction descriptor
     int acol;            // first TMEM column of the A buffers (after P and Q)
     int tmem_cols;       // TMEM columns per block (256 or 512)
     int ks;              // 16-row K steps per channel (1 or 2)
     int split;           // 3: BF16 hi/lo products, 1: BF16 only
+    int npar;            // channel classes of A-building warps (2: 2 blocks/SM, 3: 1 block/SM)
     long long budget;    // wait budget, SM clock cycles
 };
 int backproject_tc_tile_x();

@@ -22,6 +22,25 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// Tensor-core back-projection layout. TMEM columns of a block: the P and Q
+// accumulators (4 UT) and one A buffer (npl planes x ks steps x 8) for each
+// of npar channel classes; 2 classes in 256 columns (2 blocks per SM) or 3
+// in 512 (1 block per SM).
+int tc_cols(int ut, int npar, int npl, int ks) { return 4 * ut + npar * npl * ks * 8; }
+int tc_npar(int ut, int npl, int ks) {
+    if (tc_cols(ut, 2, npl, ks) <= 256) return 2;
+    if (tc_cols(ut, 3, npl, ks) <= 512) return 3;
+    return 0;
+}
+// Bins per block: the fewest blocks that the largest 1-block-per-SM tile
+// allows, split evenly (multiple of 8): N_p = 200 -> 2 x 104, 128 -> 2 x 64.
+int tc_auto_tile(int np, int npl, int ks) {
+    const int ut_max = (512 - 3 * npl * ks * 8) / 4 / 8 * 8;
+    const int n = (np + ut_max - 1) / ut_max;
+    const int ut = ((np + n - 1) / n + 7) / 8 * 8;
+    return std::max(ut, 16);
+}
+
 // The driver's tensor-map encoder, looked up once through the runtime.
 EncodeTiledFn encode_tiled_fn() {
     static EncodeTiledFn fn = [] {
@@ -228,8 +247,8 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     if (o.nufft_w < 4 || o.nufft_w > 12 || (o.nufft_w & 1))
         return fail(PL_ERR_ARG, "nufft_w must be even, 4..12");
     if (o.block_config == 4) {
-        if (o.tile_u != 0 && (o.tile_u % 8 != 0 || o.tile_u < 16 || o.tile_u > 64))
-            return fail(PL_ERR_ARG, "with block_config 4, tile_u must be 0 or a multiple of 8 in 16..64");
+        if (o.tile_u != 0 && (o.tile_u % 8 != 0 || o.tile_u < 16 || o.tile_u > 112))
+            return fail(PL_ERR_ARG, "with block_config 4, tile_u must be 0 or a multiple of 8 in 16..112");
     } else if (o.tile_u != 0 && o.tile_u != 8 && o.tile_u != 16 && o.tile_u != 20 && o.tile_u != 24) {
         return fail(PL_ERR_ARG, "tile_u must be 0, 8, 16, 20 or 24");
     }
@@ -254,17 +273,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     {
         const int n = s->n_pad ? s->n_pad : s->n;
         if (P->block_config == 4) {
-            // tensor-core blocks of UT bins: fewest padded bins, counting ~24
-            // bins' worth of per-channel weight work per block
-            if (P->tile_u == 0) {
-                int best = 0;
-                long long cost = 0;
-                for (int ut = 48; ut >= 16; ut -= 8) {
-                    const long long cst = (long long)((n + ut - 1) / ut) * (ut + 24);
-                    if (best == 0 || cst < cost) { best = ut; cost = cst; }
-                }
-                P->tile_u = best;
-            }
+            if (P->tile_u == 0) P->tile_u = tc_auto_tile(n, o.precision == 1 ? 2 : 4, 1);
         } else if (P->tile_u == 0) {    // fewest padded bins; 20 only when it wastes less than 16
             const int w16 = (n + 15) / 16 * 16 - n, w20 = (n + 19) / 20 * 20 - n;
             P->tile_u = w20 < w16 ? 20 : 16;
@@ -295,27 +304,35 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     PL_CUDA(cudaMemcpy(P->d_k, k.data(), k.size() * 8, cudaMemcpyHostToDevice), "copy");
 
     cudaStream_t st = 0;
-    // the tensor-core back-projection shares one band centre per block of bins
-    PL_CUDA(launch_setup_kz(P->mode, P->Np, P->dzs, P->M, P->d_k,
-                            P->block_config == 4 ? P->tile_u : 1, P->d_kc, P->d_kchl,
-                            P->d_kspan, st), "setup_kz");
-    std::vector<double> kspan(P->Np);
-    PL_CUDA(cudaMemcpy(kspan.data(), P->d_kspan, P->Np * 8, cudaMemcpyDeviceToHost), "copy");
+    // band centre and span of every k_z bin (the tensor-core back-projection
+    // shares one centre per block of `group` bins); kmax = the widest span
     double kmax = 0.0;
-    for (double v : kspan) kmax = std::max(kmax, v);
-    if (!(kmax > 0.0)) {
-        // a single frequency (or all bins evanescent but one): use a nominal band
-        bool alive = false;
-        std::vector<double> kc(P->Np);
-        PL_CUDA(cudaMemcpy(kc.data(), P->d_kc, P->Np * 8, cudaMemcpyDeviceToHost), "copy");
-        for (double v : kc) alive = alive || v > 0.0;
-        if (!alive) return fail(PL_ERR_EVANESCENT, "every (k_z, f) term is evanescent");
-        kmax = 1.0;   // every live bin has one source at kappa'' = 0
+    auto band = [&](int group) -> pl_status {
+        PL_CUDA(launch_setup_kz(P->mode, P->Np, P->dzs, P->M, P->d_k, group, P->d_kc,
+                                P->d_kchl, P->d_kspan, st), "setup_kz");
+        std::vector<double> kspan(P->Np);
+        PL_CUDA(cudaMemcpy(kspan.data(), P->d_kspan, P->Np * 8, cudaMemcpyDeviceToHost), "copy");
+        kmax = 0.0;
+        for (double v : kspan) kmax = std::max(kmax, v);
+        if (!(kmax > 0.0)) {
+            // a single frequency (or all bins evanescent but one): use a nominal band
+            bool alive = false;
+            std::vector<double> kc(P->Np);
+            PL_CUDA(cudaMemcpy(kc.data(), P->d_kc, P->Np * 8, cudaMemcpyDeviceToHost), "copy");
+            for (double v : kc) alive = alive || v > 0.0;
+            if (!alive) return fail(PL_ERR_EVANESCENT, "every (k_z, f) term is evanescent");
+            kmax = 1.0;   // every live bin has one source at kappa'' = 0
+        }
+        return PL_OK;
+    };
+    {
+        const pl_status bs = band(P->block_config == 4 ? P->tile_u : 1);
+        if (bs != PL_OK) return bs;
     }
 
     // NUFFT geometry
     const int W = o.nufft_w;
-    const double h = PL_TWO_PI / (o.nufft_sigma * kmax);
+    double h = PL_TWO_PI / (o.nufft_sigma * kmax);
     // two pixels per thread when x-neighbours are less than one table row
     // apart in range (then their tap windows differ by at most one row)
     const double da_step = (P->mode == 0 ? 1.0 : 2.0) * gr->dx;
@@ -354,25 +371,37 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         // tensor-core windows: 16 ks rows from the lowest first tap of each
         // (16 x 8 tile, channel), found by a pass over the tile's pixels;
         // l0 leaves w/2 + 2 rows below the nearest range
-        d.l0 = amin - h * (0.5 * W + 2.0);
-        d.L = 0;
-        BpDesc gb = make_bp(P);
+        const int npl = P->precision == 1 ? 2 : 4;
         PL_CUDA(dalloc(&P->d_tgeo, (size_t)ntx * nty * P->C, ws), "cudaMalloc");
-        int *d_stats = nullptr;
-        PL_CUDA(cudaMalloc(&d_stats, 2 * sizeof(int)), "cudaMalloc");
-        int stats[2] = {0, 0};
-        cudaError_t e = cudaMemset(d_stats, 0, 2 * sizeof(int));
-        if (e == cudaSuccess) e = launch_setup_tile_geo_tc(gb, P->d_chxy, P->d_tgeo, d_stats, st);
-        if (e == cudaSuccess) e = cudaMemcpy(stats, d_stats, sizeof(stats), cudaMemcpyDeviceToHost);
-        cudaFree(d_stats);
-        PL_CUDA(e, "setup_tile_geo_tc");
-        const int ks = stats[0] <= 16 ? 1 : (stats[0] <= 32 ? 2 : 0);
-        if (ks == 0)
-            return fail(PL_ERR_UNSUPPORTED,
-                        "a 16 x 8 pixel tile spans more than 32 table rows (grid too coarse for block_config 4)");
-        L = (int)std::ceil((amax - amin) / h) + W + 6 + 16 * ks;
+        int stats[2] = {0, 0}, ks = 0;
+        for (int attempt = 0;; ++attempt) {
+            d.h = h;
+            d.l0 = amin - h * (0.5 * W + 2.0);
+            d.L = 0;
+            BpDesc gb = make_bp(P);
+            int *d_stats = nullptr;
+            PL_CUDA(cudaMalloc(&d_stats, 2 * sizeof(int)), "cudaMalloc");
+            cudaError_t e = cudaMemset(d_stats, 0, 2 * sizeof(int));
+            if (e == cudaSuccess) e = launch_setup_tile_geo_tc(gb, P->d_chxy, P->d_tgeo, d_stats, st);
+            if (e == cudaSuccess) e = cudaMemcpy(stats, d_stats, sizeof(stats), cudaMemcpyDeviceToHost);
+            cudaFree(d_stats);
+            PL_CUDA(e, "setup_tile_geo_tc");
+            ks = stats[0] <= 16 ? 1 : (stats[0] <= 32 ? 2 : 0);
+            if (ks == 0)
+                return fail(PL_ERR_UNSUPPORTED,
+                            "a 16 x 8 pixel tile spans more than 32 table rows (grid too coarse for block_config 4)");
+            if (tc_npar(P->tile_u, npl, ks) != 0) break;
+            if (attempt > 0 || o.tile_u != 0)
+                return fail(PL_ERR_UNSUPPORTED, "tile_u too large for tensor memory");
+            // two K steps leave less tensor memory for bins: smaller blocks, new band
+            P->tile_u = tc_auto_tile(P->Np, npl, ks);
+            const pl_status bs = band(P->tile_u);
+            if (bs != PL_OK) return bs;
+            h = PL_TWO_PI / (o.nufft_sigma * kmax);
+        }
+        // rows up to the end of the highest window
+        L = stats[1] + 16 * ks;
         L += L & 1;
-        if (stats[1] + 16 * ks > L) return fail(PL_ERR_UNSUPPORTED, "table window past the last row");
         P->R = 16 * ks;
         P->tc.ks = ks;
     } else {
@@ -383,8 +412,16 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         d.l0 = amin - h * (0.5 * (P->R + 1) + 2.0);
     }
     if (L > 4096) return fail(PL_ERR_UNSUPPORTED, "range-profile table too long (grid too large for the band)");
-    int fine = 64, lg = 6;
-    while (fine < 2 * L) { fine <<= 1; ++lg; }
+    // fine grid: the smallest 2^a 3^b 5^c >= max(2 L, 64) (twice the output rows)
+    int fine = std::max(2 * L, 64);
+    auto smooth5 = [](int n) {
+        for (int r : {2, 3, 5})
+            while (n % r == 0) n /= r;
+        return n == 1;
+    };
+    while (!smooth5(fine)) ++fine;
+    int lg = 0;
+    while ((1 << (lg + 1)) <= fine) ++lg;
     d.L = L;
     d.fine = fine;
     d.log2_fine = lg;
@@ -394,21 +431,26 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     if (P->block_config == 4) {
         TcArgs &ta = P->tc;
         ta.UT = P->tile_u;
-        ta.NG = ta.UT / 4;
+        ta.ncb = (2 * ta.UT + 63) / 64;
         ta.n_utiles = (P->Np + ta.UT - 1) / ta.UT;
         ta.split = P->precision == 1 ? 1 : 3;
         const int planes = ta.split == 3 ? 2 : 1, npl = ta.split == 3 ? 4 : 2;
-        ta.slot_bytes = (unsigned)(planes * ta.NG * 16 * ta.ks * 16);
+        ta.cb_bytes = (unsigned)(planes * 16 * ta.ks * 128);
+        ta.slot_bytes = (unsigned)ta.ncb * ta.cb_bytes;
         const int N = 2 * ta.UT;
-        const int cols = 2 * N + 2 * npl * ta.ks * 8;
-        if (cols > 512) return fail(PL_ERR_UNSUPPORTED, "tile_u too large for tensor memory");
-        ta.tmem_cols = cols <= 256 ? 256 : 512;
+        ta.npar = tc_npar(ta.UT, npl, ta.ks);
+        ta.tmem_cols = ta.npar == 2 ? 256 : 512;
         ta.acol = 2 * N;
-        const size_t pool = ta.tmem_cols > 256 ? 110 * 1024 : 72 * 1024;
-        ta.nst = (int)std::max<size_t>(2, std::min<size_t>(32, pool / ta.slot_bytes));
+        // window slots: whole slot groups of npar (at least 2 groups), within
+        // ~190 KB (one block per SM) or ~100 KB (two)
+        const size_t pool = ta.tmem_cols > 256 ? 190 * 1024 : 100 * 1024;
+        const int nsg = (int)std::max<size_t>(2, std::min<size_t>(16, pool / ((size_t)ta.slot_bytes * ta.npar)));
+        ta.nst = nsg * ta.npar;
+        if (backproject_tc_smem_bytes(ta) > 227 * 1024)
+            return fail(PL_ERR_UNSUPPORTED, "table window slots exceed shared memory");
         ta.idesc = tc05::idesc_bf16(128, N, 1);
         ta.budget = 4ll << 30;
-        d.tc_ngt = ta.n_utiles * ta.UT / 4;
+        d.tc_cols = 2 * ta.n_utiles * ta.UT;
     } else if (backproject_smem_bytes(P->R, P->tile_u, P->C, P->precision, P->block_config) > 200 * 1024)
         return fail(PL_ERR_UNSUPPORTED, "table window too tall for shared memory (grid too coarse)");
     for (int tp = 0; tp < W; ++tp) es_tap_polynomial(W, (double)d.beta, tp, W + 1, P->coef.c[tp]);
@@ -468,26 +510,25 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     // tensor-core layout [c][hi/lo][column][row] BF16 (zero beyond what the
     // range table writes)
     if (P->block_config == 4)
-        P->table_bytes = (size_t)P->C * 2 * d.tc_ngt * L * 16;
+        P->table_bytes = (size_t)P->C * 2 * L * d.tc_cols * 2;
     else
         P->table_bytes = (size_t)P->C * L * ((P->Np + 1) / 2) * (P->precision == 1 ? 8 : 16);
     ws += P->table_bytes;
     PL_CUDA(cudaMalloc(&P->d_table, P->table_bytes), "cudaMalloc");
     if (P->block_config == 4) {
         PL_CUDA(cudaMemset(P->d_table, 0, P->table_bytes), "cudaMemset");
-        // TMA map of the table [c][hi/lo][column group][row][8 BF16]: one box
-        // is a channel's window of 16 ks rows x UT/4 groups (x hi/lo)
+        // TMA map of the table [c][hi/lo][row][column] (BF16): a box is 64
+        // columns x 16 ks rows (x hi/lo), 128-byte swizzled in shared memory
         EncodeTiledFn enc = encode_tiled_fn();
         if (!enc) return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled not available");
         const TcArgs &ta = P->tc;
-        const cuuint64_t dims[4] = {8, (cuuint64_t)L, (cuuint64_t)d.tc_ngt, 2 * (cuuint64_t)P->C};
-        const cuuint64_t strides[3] = {16, (cuuint64_t)L * 16, (cuuint64_t)d.tc_ngt * L * 16};
-        const cuuint32_t box[4] = {8, (cuuint32_t)(16 * ta.ks), (cuuint32_t)ta.NG,
-                                   (cuuint32_t)(ta.split == 3 ? 2 : 1)};
-        const cuuint32_t es[4] = {1, 1, 1, 1};
-        const CUresult r = enc(&P->tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, P->d_table, dims,
+        const cuuint64_t dims[3] = {(cuuint64_t)d.tc_cols, (cuuint64_t)L, 2 * (cuuint64_t)P->C};
+        const cuuint64_t strides[2] = {(cuuint64_t)d.tc_cols * 2, (cuuint64_t)L * d.tc_cols * 2};
+        const cuuint32_t box[3] = {64, (cuuint32_t)(16 * ta.ks), (cuuint32_t)(ta.split == 3 ? 2 : 1)};
+        const cuuint32_t es[3] = {1, 1, 1};
+        const CUresult r = enc(&P->tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, P->d_table, dims,
                                strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled failed");
         PL_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&P->h_err), sizeof(int), cudaHostAllocMapped),
@@ -514,7 +555,7 @@ pl_status pl_stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st) {
 }
 
 pl_status pl_stage_range_table(pl_plan *P, cudaStream_t st) {
-    const int fmt = P->block_config == 4 ? 3 : (P->precision == 1 ? 1 : 0);
+    const int fmt = P->block_config == 4 ? 4 : (P->precision == 1 ? 1 : 0);
     PL_CUDA(launch_range_table(P->nd, P->fineplan, P->d_S, P->d_alpha, P->d_xg, P->d_dec,
                                P->d_twfine, P->d_table, fmt, st), "range_table");
     return PL_OK;

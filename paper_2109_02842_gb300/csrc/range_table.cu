@@ -7,7 +7,7 @@
 // phase) and theta_um = kappa''_um h (see setup.cu). This is a type-1
 // nonuniform FFT: the M sources are spread with an ES kernel onto a periodic
 // fine grid of `fine` points using shared-memory atomics, transformed by a
-// radix-2 FFT in shared memory, and divided by the spreading kernel's
+// mixed-radix FFT in shared memory, and divided by the spreading kernel's
 // transform.
 //
 // A block covers UB consecutive k_z bins of one channel: their fine grids are

@@ -45,7 +45,7 @@ __device__ __forceinline__ void rt_block(const NufftDesc &d, const FftPlan &fp,
         for (int t = 0; t < d.w1; ++t) {
             const int g = g0 + t;
             const float wgt = es_kernel((float)g - x, two_over_w1, d.beta1);
-            float2 *cell = row + (g & (fine - 1));
+            float2 *cell = row + (g < 0 ? g + fine : g);   // |g| < fine: one wrap at most
             atomicAdd(&cell->x, a.x * wgt);
             atomicAdd(&cell->y, a.y * wgt);
         }
@@ -56,34 +56,22 @@ __device__ __forceinline__ void rt_block(const NufftDesc &d, const FftPlan &fp,
     const float2 *res = stockham_run<false>(buf0, buf1, tw, fp, +1, UB, fine, 1);
 
     // deconvolve, keep rows j = i - L/2
-    if (fmt == 3) {
-        // tensor-core layout [c][plane hi/lo][column group][row][8]: a group
-        // holds bins 4g .. 4g+3 as (re, im) BF16 pairs, hi = BF16(x) and
-        // lo = BF16(x - hi); bins past N_p are zero
+    if (fmt == 4) {
+        // tensor-core layout [c][plane hi/lo][row][column 2u + (re, im)], BF16,
+        // hi = BF16(x) and lo = BF16(x - hi); bins past N_p stay zero
         __nv_bfloat16 *tb = reinterpret_cast<__nv_bfloat16 *>(table);
-        constexpr int NGB = UB / 4;
-        for (int idx = threadIdx.x; idx < NGB * d.L; idx += blockDim.x) {
-            const int gl = idx / d.L;
-            const int i = idx - gl * d.L;
-            const int j = (i - d.L / 2) & (fine - 1);
-            const float s = dec[i];
-            unsigned hi[4], lo[4];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int ul = 4 * gl + b;
-                const float2 v = u0 + ul < d.n_pad ? cscale(res[ul * fine + j], s)
-                                                   : make_float2(0.f, 0.f);
-                __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
-                const float2 hf = __bfloat1622float2(h);
-                __nv_bfloat162 l = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
-                hi[b] = *reinterpret_cast<unsigned *>(&h);
-                lo[b] = *reinterpret_cast<unsigned *>(&l);
-            }
-            const size_t g = (size_t)(u0 / 4 + gl);
-            const size_t o0 = (((size_t)c * 2 + 0) * d.tc_ngt + g) * d.L + i;
-            const size_t o1 = (((size_t)c * 2 + 1) * d.tc_ngt + g) * d.L + i;
-            reinterpret_cast<uint4 *>(tb)[o0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            reinterpret_cast<uint4 *>(tb)[o1] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        for (int idx = threadIdx.x; idx < UB * d.L; idx += blockDim.x) {
+            const int i = idx / UB;
+            const int ul = idx - i * UB;
+            if (u0 + ul >= d.n_pad) continue;
+            const int j = i < d.L / 2 ? i - d.L / 2 + fine : i - d.L / 2;
+            const float2 v = cscale(res[ul * fine + j], dec[i]);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+            const size_t o = (((size_t)c * 2) * d.L + i) * d.tc_cols + 2 * (size_t)(u0 + ul);
+            *reinterpret_cast<__nv_bfloat162 *>(tb + o) = h;
+            *reinterpret_cast<__nv_bfloat162 *>(tb + o + (size_t)d.L * d.tc_cols) = l;
         }
         return;
     }
@@ -95,7 +83,7 @@ __device__ __forceinline__ void rt_block(const NufftDesc &d, const FftPlan &fp,
         const int i = idx / NPR;
         const int q = idx - i * NPR;
         if (p0 + q >= np2) continue;
-        const int j = (i - d.L / 2) & (fine - 1);
+        const int j = i < d.L / 2 ? i - d.L / 2 + fine : i - d.L / 2;
         const float s = dec[i];
         const float2 a = cscale(res[(2 * q) * fine + j], s);
         const float2 e = cscale(res[(2 * q + 1) * fine + j], s);
