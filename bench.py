@@ -133,6 +133,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def dtype_of(info: dict, precision: int) -> str:
+    if info["block_config"] == 4:
+        return "bf16x3+f32acc" if precision == 0 else "bf16+f32acc"
+    return "f32" if precision == 0 else "f32+bf16"
+
+
+def tc_flops_per_launch(info: dict, precision: int) -> float:
+    """Dense BF16 flops of one tensor-core back-projection launch: per (pixel,
+    channel, bin) 16 ks window rows x 2 columns (re, im) x 2 accumulators
+    (Re A, Im A) x split products (3 with the hi/lo split, 1 in BF16), over
+    16 x 8 pixel tiles and whole tile_u-bin blocks (the padding is executed)."""
+    ks = max(info["slab_rows"] // 16, 1)
+    split = 3 if precision == 0 else 1
+    ut = info["tile_u"]
+    bins = -(-info["n_pad"] // ut) * ut
+    pix = -(-info["nx"] // 16) * 16 * (-(-info["ny"] // 8) * 8)
+    return 2.0 * pix * info["n_chan"] * bins * 4 * split * 16 * ks
+
+
 def backproject_flops_per_update(w_taps: int) -> int:
     # w complex-by-real MACs (4w flop) + carrier phase product (1) +
     # complex multiply-accumulate (8); the sine/cosine pair is 2 MUFU ops.
@@ -356,18 +375,34 @@ def main():
     bp_ms, bp_n = stage["backproject"]
     bp_avg_s = bp_ms / max(bp_n, 1) * 1e-3
     pix_updates = info["n_chan"] * info["nx"] * info["ny"] * info["n_pad"]
-    flops = pix_updates * backproject_flops_per_update(info["nufft_w"])
+    fp32_flops = pix_updates * backproject_flops_per_update(info["nufft_w"])
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = flops / bp_avg_s / 1e12
-    traffic = kernel_traffic("backproject", w.name)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": traffic,
-                "kernel": "k_backproject", "launch_ms": bp_avg_s * 1e3,
-                "flop_per_launch": flops,
-                "peak_basis": "FP32: 152 SM x 128 lanes x 2 flop x 2070 MHz (recipe unit "
-                              "counts and max clock)",
-                "mufu_frac": (2 * pix_updates / bp_avg_s) /
-                             (N_SM * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6)}
+    peaks, peak_src = measured_peaks()
+    if info["block_config"] == 4:
+        # tensor cores: the dense BF16 contraction of the formulation, per
+        # (pixel, channel, bin): split x (P, Q) x (re, im) x 16 ks window rows
+        # MACs, over the padded 16 x 8 pixel tiles and tile_u-bin blocks
+        flops = tc_flops_per_launch(info, args.precision)
+        peak = float(peaks.get("bf16_tflops", 1900.0))
+        achieved = flops / bp_avg_s / 1e12
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": kernel_traffic("backproject_tc", w.name),
+                    "kernel": "k_backproject_tc", "launch_ms": bp_avg_s * 1e3,
+                    "flop_per_launch": flops,
+                    "peak_basis": "dense BF16 (%s)" % peak_src,
+                    "fp32_equivalent_tflops": fp32_flops / bp_avg_s / 1e12,
+                    "fp32_equivalent_basis": "%d flop per (pixel, channel, bin) update"
+                                             % backproject_flops_per_update(info["nufft_w"])}
+    else:
+        achieved = fp32_flops / bp_avg_s / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp32_peak, "traffic": kernel_traffic("backproject", w.name),
+                    "kernel": "k_backproject", "launch_ms": bp_avg_s * 1e3,
+                    "flop_per_launch": fp32_flops,
+                    "peak_basis": "FP32: 152 SM x 128 lanes x 2 flop x 2070 MHz (recipe unit "
+                                  "counts and max clock)",
+                    "mufu_frac": (2 * pix_updates / bp_avg_s) /
+                                 (N_SM * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6)}
     stage_avg = {k: v[0] / max(v[1], 1) for k, v in stage.items()}
 
     cpu, acc = None, None
@@ -380,12 +415,11 @@ def main():
         img = plan.execute(torch.from_numpy(e_np).to(dev)).cpu().numpy()
         cpu, acc = oracle_baseline(w, e_np, img, n_cols=256)
 
-    peaks, peak_src = measured_peaks()
     line = {
         "metric": "element-voxel-freq updates/s at rel. L2 err <= 1e-3 vs FP64 oracle",
         "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 0 else "f32+bf16",
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(info, args.precision),
         "data": "synthetic",
         "config": {"workload": w.name, "mode": "monostatic" if w.mode == 0 else "multistatic",
                    "n_chan": info["n_chan"],

@@ -105,7 +105,8 @@ typedef struct {
  * nufft_w: interpolation taps (even, 4..12; default 6).
  * tile_u: k_z bins per back-projection block (8, 16, 20 or 24; with
  *         block_config 4 a multiple of 8 in 16..112; 0 = chosen from n_pad).
- * block_config: back-projection kernel (0 = default: 3 when the x step is
+ * block_config: back-projection kernel (0 = default: 4 when nufft_w is 4, 6
+ *         or 8, tile_u is 0 and the grid allows it, else 3 when the x step is
  *         below the table step, else 1; 1 = FP32, one pixel per thread,
  *         8-channel chunks, 3 blocks per SM; 2 = FP32, one pixel per thread,
  *         16-channel chunks; 3 = FP32, two pixels per thread sharing the tap
@@ -143,6 +144,8 @@ typedef struct {
     int launches_per_execute;
     size_t workspace_bytes;
     double updates_per_execute;  /* n_chan * nx * ny * nz * n_f */
+    int block_config;            /* back-projection kernel in use (1..4) */
+    int tile_u;                  /* its k_z bins per block */
 } pl_info;
 
 /* Stage identifiers for timing and workspace access. */

@@ -655,9 +655,27 @@ pl_status pl_plan_create(pl_plan **out, const pl_geometry *geom, const pl_scan *
     *out = nullptr;
     pl_status s = validate(geom, scan, freqs, grid);
     if (s != PL_OK) return s;
+    pl_options o{};
+    if (opt) o = *opt;
+    // default kernel: the tensor-core back-projection where it applies, else
+    // the FP32 kernels (a grid too coarse for its 32-row windows, other w)
+    const int w = o.nufft_w ? o.nufft_w : 6;
+    if (o.block_config == 0 && o.tile_u == 0 && (w == 4 || w == 6 || w == 8)) {
+        pl_options ot = o;
+        ot.block_config = 4;
+        pl_plan *P = new (std::nothrow) pl_plan();
+        if (!P) return fail(PL_ERR_OOM, "host allocation failed");
+        s = build_plan(P, geom, scan, freqs, grid, &ot);
+        if (s == PL_OK) {
+            *out = P;
+            return PL_OK;
+        }
+        delete P;
+        if (s != PL_ERR_UNSUPPORTED) return s;
+    }
     pl_plan *P = new (std::nothrow) pl_plan();
     if (!P) return fail(PL_ERR_OOM, "host allocation failed");
-    s = build_plan(P, geom, scan, freqs, grid, opt);
+    s = build_plan(P, geom, scan, freqs, grid, &o);
     if (s != PL_OK) {
         delete P;
         return s;
@@ -734,6 +752,8 @@ pl_status pl_plan_get_info(const pl_plan *P, pl_info *info) {
     i.launches_per_execute = 4;
     i.workspace_bytes = P->workspace;
     i.updates_per_execute = (double)P->C * P->grid.nx * P->grid.ny * P->grid.nz * P->M;
+    i.block_config = P->block_config;
+    i.tile_u = P->tile_u;
     *info = i;
     return PL_OK;
 }

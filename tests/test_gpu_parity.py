@@ -73,10 +73,12 @@ def test_zfft_stage_matches_dft(binding, n_pad):
     assert report("S n_pad=%d" % n_pad, S, oracle.zdft(echo, n_pad)) < 1e-5
 
 
-def test_kspace_image_matches_exact_sum(binding):
+@pytest.mark.parametrize("bc", [0, 1])
+def test_kspace_image_matches_exact_sum(binding, bc):
     w = wl.small_mono(seed=1)
     echo = scene_echo(w, 1)
-    plan, _ = run_gpu(binding, w, echo)
+    plan, _ = run_gpu(binding, w, echo, block_config=bc)
+    assert plan.info["block_config"] == (4 if bc == 0 else bc)
     G = plan.workspace(binding.PL_STAGE_BACKPROJECT).cpu().numpy().reshape(w.n_pad, -1)
     S = oracle.zdft(echo, w.n_pad)
     ref = oracle.hybrid_spectral(0, w.tx_xy, w.rx_xy, S, w.dz, w.f_hz, w.pix_xy())
@@ -91,39 +93,43 @@ def image_ref(w, echo, pix=None):
                                w.axis("z"))
 
 
-def test_small_mono_image(binding):
+@pytest.mark.parametrize("bc", [0, 1, 3])
+def test_small_mono_image(binding, bc):
     w = wl.small_mono(seed=0)
     echo = scene_echo(w)
-    _, img = run_gpu(binding, w, echo)
+    _, img = run_gpu(binding, w, echo, block_config=bc)
     ref = image_ref(w, echo)
     assert report("image small mono", img.reshape(w.grid["nz"], -1), ref) < TOL_FP32
 
 
-def test_small_multi_image(binding):
+@pytest.mark.parametrize("bc", [0, 1])
+def test_small_multi_image(binding, bc):
     w = small_multi()
     echo = scene_echo(w)
-    _, img = run_gpu(binding, w, echo)
+    _, img = run_gpu(binding, w, echo, block_config=bc)
     ref = image_ref(w, echo)
     assert report("image small multi", img.reshape(w.grid["nz"], -1), ref) < TOL_FP32
 
 
-def test_gpu_mono_equals_multi_colocated(binding):
+@pytest.mark.parametrize("bc", [0, 1])
+def test_gpu_mono_equals_multi_colocated(binding, bc):
     w = wl.small_mono(seed=2)
     echo = scene_echo(w, 2)
-    _, g0 = run_gpu(binding, w, echo)
+    _, g0 = run_gpu(binding, w, echo, block_config=bc)
     w1 = wl.small_mono(seed=2)
     n = w1.elem_xy.shape[0]
     w1.mode, w1.pair_tx, w1.pair_rx = 1, np.arange(n), np.arange(n)
-    _, g1 = run_gpu(binding, w1, echo)
+    _, g1 = run_gpu(binding, w1, echo, block_config=bc)
     assert rel(g1, g0) < 2 * TOL_FP32
 
 
-def test_ragged_grid_and_offgrid_z(binding):
-    # nx, ny not multiples of the 16 x 16 tile; z voxels off the scan grid
+@pytest.mark.parametrize("bc", [0, 1])
+def test_ragged_grid_and_offgrid_z(binding, bc):
+    # nx, ny not multiples of the pixel tile; z voxels off the scan grid
     w = wl.small_mono(seed=3)
     w.grid = dict(w.grid, nx=37, ny=23, nz=7, z0=-0.031, dz=0.0093)
     echo = scene_echo(w, 3)
-    plan, img = run_gpu(binding, w, echo)
+    plan, img = run_gpu(binding, w, echo, block_config=bc)
     assert plan.info["z_transform_fft"] == 0
     assert report("image ragged", img.reshape(7, -1), image_ref(w, echo)) < TOL_FP32
 
@@ -138,20 +144,22 @@ def test_scan_grid_ifft_path_with_offset(binding):
     assert report("image ifft path", img.reshape(20, -1), image_ref(w, echo)) < TOL_FP32
 
 
-def test_single_frequency_and_single_scan(binding):
+@pytest.mark.parametrize("bc", [0, 1])
+def test_single_frequency_and_single_scan(binding, bc):
     w = wl.small_mono(seed=5)
     w.f_hz = w.f_hz[:1]
     w.n_scan, w.n_pad = 1, 1
     w.grid = dict(w.grid, nz=1, z0=w.z0, dz=w.dz)
     echo = scene_echo(w, 5)
-    _, img = run_gpu(binding, w, echo)
+    _, img = run_gpu(binding, w, echo, block_config=bc)
     assert report("image 1 freq 1 scan", img.reshape(1, -1), image_ref(w, echo)) < TOL_FP32
 
 
-def test_bf16_table_variant(binding):
+@pytest.mark.parametrize("bc", [0, 1])
+def test_bf16_table_variant(binding, bc):
     w = wl.small_mono(seed=0)
     echo = scene_echo(w)
-    _, img = run_gpu(binding, w, echo, precision=1)
+    _, img = run_gpu(binding, w, echo, precision=1, block_config=bc)
     assert report("image bf16 table", img.reshape(w.grid["nz"], -1), image_ref(w, echo)) < TOL_BF16
 
 
@@ -196,7 +204,8 @@ def test_invalid_inputs_are_rejected(binding):
     assert ei.value.status == 1
 
 
-def test_evanescent_bins_are_dropped(binding):
+@pytest.mark.parametrize("bc", [0, 1])
+def test_evanescent_bins_are_dropped(binding, bc):
     # dz so coarse that |k_z| > 2k for the outer bins: they contribute nothing,
     # exactly as in the oracle (the k_z = 0 bin always propagates).
     w = wl.small_mono(seed=0)
@@ -205,7 +214,7 @@ def test_evanescent_bins_are_dropped(binding):
     w.f_hz = np.linspace(0.3e9, 0.5e9, 8)
     w.grid = dict(w.grid, nz=8, z0=w.z0, dz=w.dz)
     echo = scene_echo(w, 9)
-    _, img = run_gpu(binding, w, echo)
+    _, img = run_gpu(binding, w, echo, block_config=bc)
     assert report("image evanescent bins", img.reshape(8, -1), image_ref(w, echo)) < TOL_FP32
 
 
@@ -226,9 +235,10 @@ def sampled_columns(w, n, seed):
 
 @pytest.mark.parametrize("which", ["full_mono", "multi"])
 def test_full_size_sampled_columns(binding, which):
+    # the FP32 kernels at full size (the tensor-core kernel: below)
     w = wl.WORKLOADS[which](seed=0)
     echo = scene_echo(w, 0, n_pts=24)
-    _, img = run_gpu(binding, w, echo)
+    _, img = run_gpu(binding, w, echo, block_config=3 if which == "full_mono" else 1)
     idx = sampled_columns(w, 48, 1)
     ref = image_ref(w, echo, w.pix_xy()[idx])
     got = img.reshape(w.grid["nz"], -1)[:, idx]
