@@ -177,6 +177,8 @@ std::map<std::string, std::pair<int, int>> g_tune_cache;   // signature -> (tile
 
 }  // namespace
 
+constexpr int kAuxStreams = 8;
+
 struct pl_batch {
     int n = 0;
     std::vector<pl_plan *> plans;
@@ -190,6 +192,10 @@ struct pl_batch {
     int *h_flag = nullptr;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // scene-parallel streams of the non-persistent path (forked in the graph)
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> aux_ev;
+    std::vector<int> order;          // scenes, largest first
     std::vector<const void *> cap_echo;
     std::vector<void *> cap_img;
     pl_batch_info info{};
@@ -201,6 +207,8 @@ struct pl_batch {
     ~pl_batch() {
         if (exec) cudaGraphExecDestroy(exec);
         if (cap) cudaStreamDestroy(cap);
+        for (cudaStream_t s : aux) cudaStreamDestroy(s);
+        for (cudaEvent_t e : aux_ev) cudaEventDestroy(e);
         if (d_scenes) cudaFree(d_scenes);
         if (d_counters) cudaFree(d_counters);
         if (h_flag) cudaFreeHost(h_flag);
@@ -216,7 +224,7 @@ pl_status make_plans(pl_batch *B, int n, const pl_geometry *g, const pl_scan *s,
     for (int i = 0; i < n; ++i) {
         pl_options o{};
         if (opts) o = opts[i];
-        o.tile_u = tile_u;
+        o.tile_u = block_config == 4 ? 0 : tile_u;     // the tensor-core kernel sizes its own
         o.block_config = block_config;
         pl_plan *p = nullptr;
         pl_status st = pl_plan_create(&p, &g[i], &s[i], &f[i], &gr[i], &o);
@@ -243,6 +251,7 @@ pl_status build_queue(pl_batch *B, int tile_u, double timeout_ms, int debug) {
         return (double)p->C * p->grid.nx * p->grid.ny * p->Np;
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    B->order = order;
     std::vector<BatchScene> hs(n);
     int rt = 0;
     size_t smem = 0;
@@ -271,7 +280,7 @@ pl_status build_queue(pl_batch *B, int tile_u, double timeout_ms, int debug) {
         d.nut = (p->Np + tile_u - 1) / tile_u;
         d.bp_items = d.ntx * d.nty * d.nut;
         d.need = d.rt_items + ((debug && k == 0) ? 1 : 0);
-        smem = std::max(smem, (size_t)(p->nd.fine + 2 * kBatchUB * p->nd.fine) * sizeof(float2));
+        smem = std::max(smem, rt::smem_bytes(p->nd.fine, kBatchUB, p->nd.n_f));
         smem = std::max(smem, backproject_smem_bytes(p->R, tile_u, p->C, p->precision,
                                                      B->block_config));
     }
@@ -302,6 +311,20 @@ pl_status build_queue(pl_batch *B, int tile_u, double timeout_ms, int debug) {
     B->info.persistent = B->persistent ? 1 : 0;
     B->info.persistent_blocks = B->persistent ? B->pblocks : 0;
     B->info.launches_per_execute = B->persistent ? 2 * n + 1 : 4 * n;
+    if (!B->persistent && B->aux.empty()) {
+        // scenes of the per-scene path run on kAuxStreams streams at once
+        for (int k = 0; k < kAuxStreams; ++k) {
+            cudaStream_t s = nullptr;
+            cudaEvent_t e = nullptr;
+            PL_CUDA_RET(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            B->aux.push_back(s);
+            PL_CUDA_RET(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            B->aux_ev.push_back(e);
+        }
+        cudaEvent_t e = nullptr;
+        PL_CUDA_RET(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        B->aux_ev.push_back(e);    // the fork event
+    }
     if (B->exec) cudaGraphExecDestroy(B->exec);
     B->exec = nullptr;
     return PL_OK;
@@ -316,14 +339,28 @@ pl_status enqueue(pl_batch *B, const void *const *echo, void *const *image, cuda
     if (B->persistent) {
         PL_CUDA_RET(launch_batch(B->tile_u, B->block_config, B->bc, B->d_scenes, B->d_counters,
                                  B->smem, &B->pblocks, false, st));
+        for (int i = 0; i < n; ++i)
+            if ((s = pl_stage_zifft(B->plans[i], (float2 *)image[i], st)) != PL_OK) return s;
     } else {
-        for (int i = 0; i < n; ++i) {
-            if ((s = pl_stage_range_table(B->plans[i], st)) != PL_OK) return s;
-            if ((s = pl_stage_backproject(B->plans[i], st)) != PL_OK) return s;
+        // per-scene range table, back-projection and inverse transform, the
+        // scenes (largest first) dealt round-robin to the streams, joined at
+        // the end; the forward transforms above ran on st
+        const int K = (int)B->aux.size();
+        cudaEvent_t fork = B->aux_ev[K];
+        PL_CUDA_RET(cudaEventRecord(fork, st));
+        for (int k = 0; k < K; ++k) PL_CUDA_RET(cudaStreamWaitEvent(B->aux[k], fork, 0));
+        for (int j = 0; j < n; ++j) {
+            const int i = B->order[j];
+            cudaStream_t as = B->aux[j % K];
+            if ((s = pl_stage_range_table(B->plans[i], as)) != PL_OK) return s;
+            if ((s = pl_stage_backproject(B->plans[i], as)) != PL_OK) return s;
+            if ((s = pl_stage_zifft(B->plans[i], (float2 *)image[i], as)) != PL_OK) return s;
+        }
+        for (int k = 0; k < K; ++k) {
+            PL_CUDA_RET(cudaEventRecord(B->aux_ev[k], B->aux[k]));
+            PL_CUDA_RET(cudaStreamWaitEvent(st, B->aux_ev[k], 0));
         }
     }
-    for (int i = 0; i < n; ++i)
-        if ((s = pl_stage_zifft(B->plans[i], (float2 *)image[i], st)) != PL_OK) return s;
     PL_CUDA_RET(cudaMemcpyAsync(B->h_flag, B->d_counters + 1, sizeof(int), cudaMemcpyDeviceToHost,
                                 st));
     return PL_OK;
@@ -362,6 +399,8 @@ pl_status run_batch(pl_batch *B, const void *const *echo, void *const *image, cu
     PL_CUDA_RET(cudaGraphLaunch(B->exec, st));
     PL_CUDA_RET(cudaStreamSynchronize(st));
     if (*B->h_flag) return pl_internal_fail(PL_ERR_TIMEOUT, "a bounded device-side wait expired");
+    for (pl_plan *p : B->plans)
+        if (pl_plan_take_timeout(p) != PL_OK) return PL_ERR_TIMEOUT;
     return PL_OK;
 }
 
@@ -425,8 +464,9 @@ pl_status pl_batch_create(pl_batch **out, int n, const pl_geometry *g, const pl_
     if (e == cudaSuccess) e = cudaMallocHost(&B->h_flag, sizeof(int));
     if (e != cudaSuccess) return bail(pl_internal_cuda_fail(e, "pl_batch_create"));
 
+    // default: the tensor-core kernel, unless an FP32 block shape is asked for
     int tile_u = bo.tile_u ? bo.tile_u : 16;
-    int bcfg = bo.block_config ? bo.block_config : 1;
+    int bcfg = bo.block_config ? bo.block_config : (bo.tile_u ? 1 : 4);
     const bool tune = bo.autotune && !bo.tile_u && !bo.block_config;
     pl_status st;
     if (tune) {
@@ -453,11 +493,13 @@ pl_status pl_batch_create(pl_batch **out, int n, const pl_geometry *g, const pl_
                     e = cudaMalloc(&ibuf[i], sizeof(float2) * (size_t)gr[i].nx * gr[i].ny * gr[i].nz);
             }
             double best = 1e30, dflt = 0.0;
-            const int cfgs[2] = {1, 3};
+            // the tensor-core kernel (per-scene launches, scenes on parallel
+            // streams) and the FP32 persistent kernel in three block shapes
+            const int cfgs[3] = {4, 1, 3};
             const int tus[3] = {8, 16, 20};
-            for (int ci = 0; ci < 2 && e == cudaSuccess; ++ci) {
+            for (int ci = 0; ci < 3 && e == cudaSuccess; ++ci) {
                 if (make_plans(B, n, g, s, f, gr, opts, 16, cfgs[ci]) != PL_OK) continue;
-                for (int ti = 0; ti < 3; ++ti) {
+                for (int ti = 0; ti < (cfgs[ci] == 4 ? 1 : 3); ++ti) {
                     double ms = 0.0;
                     if (build_queue(B, tus[ti], bo.wait_timeout_ms, 0) != PL_OK) continue;
                     if (time_batch(B, ebuf.data(), ibuf.data(), 2, &ms) != PL_OK) continue;

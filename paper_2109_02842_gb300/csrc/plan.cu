@@ -847,3 +847,5 @@ pl_status pl_synth_echo(int n_chan, const double *tx_xy, const double *rx_xy, do
 }
 
 }  // extern "C"
+
+pl_status pl_plan_take_timeout(pl_plan *plan) { return take_device_timeout(plan); }

@@ -81,6 +81,10 @@ struct pl_plan {
         if (e_ != cudaSuccess) return pl_internal_cuda_fail(e_, #call);     \
     } while (0)
 
+// PL_ERR_TIMEOUT (and clear the flags) if a bounded device wait of an earlier
+// execution of the plan ran out, else PL_OK.
+pl_status pl_plan_take_timeout(pl_plan *plan);
+
 // Launch one stage of a plan on `st` (no timing events, no synchronisation).
 pl_status pl_stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st);
 pl_status pl_stage_range_table(pl_plan *P, cudaStream_t st);

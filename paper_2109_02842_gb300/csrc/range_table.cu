@@ -6,17 +6,19 @@
 // evanescent mask, the kernel deconvolution 1/phihat and the range-origin
 // phase) and theta_um = kappa''_um h (see setup.cu). This is a type-1
 // nonuniform FFT: the M sources are spread with an ES kernel onto a periodic
-// fine grid of `fine` points using shared-memory atomics, transformed by a
-// mixed-radix FFT in shared memory, and divided by the spreading kernel's
-// transform.
+// fine grid of `fine` points in shared memory (one 8-lane group per bin, a
+// lane per tap, the sources in a fixed order: no atomics, so the table does
+// not depend on scheduling), transformed by a mixed-radix FFT in shared
+// memory, and divided by the spreading kernel's transform.
 //
 // A block covers UB consecutive k_z bins of one channel: their fine grids are
 // the rows of a [UB][fine] array in shared memory (bin-major, so the atomics
-// of neighbouring sources of one bin hit neighbouring banks), transformed
+// of a bin's row hit neighbouring banks), transformed
 // together by the block-wide mixed-radix Stockham FFT, and the deconvolved
 // rows j = i - L/2 are written as coalesced rows of the table b[c][i][u]
-// (u fastest, in planar pairs {re_u, re_u+1, im_u, im_u+1}, N_p rounded up to
-// even), the layout the back-projection stages.
+// (u fastest; planar pairs {re_u, re_u+1, im_u, im_u+1} for the FP32
+// back-projection, BF16 hi/lo planes of (re_u, im_u) columns for the tensor-core
+// one).
 #include "rt_body.cuh"
 
 namespace {
@@ -36,7 +38,7 @@ k_range_table(NufftDesc d, FftPlan fp, const float2 *__restrict__ S,
 }  // namespace
 
 size_t range_table_smem_bytes(const NufftDesc &d) {
-    return (size_t)(d.fine + 2 * bins_per_block(d.fine) * d.fine) * sizeof(float2);
+    return rt::smem_bytes(d.fine, bins_per_block(d.fine), d.n_f);
 }
 
 template <int UB>

@@ -23,33 +23,63 @@ __device__ __forceinline__ void rt_block(const NufftDesc &d, const FftPlan &fp,
     float2 *tw = smem;                          // [fine]: exp(-2 pi i k / fine)
     float2 *buf0 = tw + fine;                   // [UB][fine]
     float2 *buf1 = buf0 + UB * fine;            // [UB][fine]
+    float2 *src_a = buf1 + UB * fine;           // [UB][M]: S alpha of every source
+    float *src_x = reinterpret_cast<float *>(src_a + UB * d.n_f);   // [UB][M]: position
     const int u0 = ub * UB;
     const float two_over_w1 = 2.0f / d.w1;
     const float half_w1 = 0.5f * d.w1;
 
     for (int k = threadIdx.x; k < fine; k += blockDim.x) tw[k] = tw_g[k];
-    for (int k = threadIdx.x; k < UB * fine; k += blockDim.x) buf0[k] = make_float2(0.f, 0.f);
-    __syncthreads();
-
-    // spread (compensation fused): source m of bin u onto row u of the grid
+    for (int k = threadIdx.x; k < 2 * UB * fine; k += blockDim.x) buf0[k] = make_float2(0.f, 0.f);
+    // compensation fused into the sources: a = S alpha (0 for bins past N_p)
     for (int idx = threadIdx.x; idx < UB * d.n_f; idx += blockDim.x) {
         const int ul = idx / d.n_f;
         const int m = idx - ul * d.n_f;
         const int u = u0 + ul;
-        if (u >= d.n_pad) continue;
-        const float2 a = cmul(S[((size_t)c * d.n_pad + u) * d.n_f + m], alpha[u * d.n_f + m]);
-        if (a.x == 0.f && a.y == 0.f) continue;
-        const float x = xg[u * d.n_f + m];
-        const int g0 = (int)ceilf(x - half_w1);
-        float2 *row = buf0 + ul * fine;
-        for (int t = 0; t < d.w1; ++t) {
-            const int g = g0 + t;
-            const float wgt = es_kernel((float)g - x, two_over_w1, d.beta1);
-            float2 *cell = row + (g < 0 ? g + fine : g);   // |g| < fine: one wrap at most
-            atomicAdd(&cell->x, a.x * wgt);
-            atomicAdd(&cell->y, a.y * wgt);
+        float2 a = make_float2(0.f, 0.f);
+        float x = 0.f;
+        if (u < d.n_pad) {
+            a = cmul(S[((size_t)c * d.n_pad + u) * d.n_f + m], alpha[(size_t)u * d.n_f + m]);
+            x = xg[(size_t)u * d.n_f + m];
+        }
+        src_a[idx] = a;
+        src_x[idx] = x;
+    }
+    __syncthreads();
+
+    // spread: source m of bin u onto row u of the grid. Deterministic: the 8
+    // lanes of a group own one bin and a tap each (the w1 <= 8 taps of one
+    // source hit distinct cells) and add the sources in a fixed order, a
+    // __syncwarp between successive sources; the first half of the sources
+    // goes to buf0 (threads 0 .. 8 UB - 1), the second to buf1 (the next 8 UB),
+    // and the two are added in a fixed order. No atomics: the sums do not
+    // depend on scheduling.
+    if (threadIdx.x < 2 * UB * 8) {
+        const int half = threadIdx.x >= UB * 8;
+        const int lt = threadIdx.x - half * UB * 8;
+        const int ul = lt >> 3;
+        const int t = lt & 7;
+        const bool live = t < d.w1;
+        float2 *row = (half ? buf1 : buf0) + ul * fine;
+        const int mh = (d.n_f + 1) / 2;
+        const int m0 = half ? mh : 0, m1 = half ? d.n_f : mh;
+        const float2 *sa = src_a + ul * d.n_f;
+        const float *sx = src_x + ul * d.n_f;
+        for (int m = m0; m < m1; ++m) {
+            const float2 a = sa[m];
+            if (live && (a.x != 0.f || a.y != 0.f)) {
+                const float x = sx[m];
+                const int g = (int)ceilf(x - half_w1) + t;
+                const float wgt = es_kernel((float)g - x, two_over_w1, d.beta1);
+                float2 *cell = row + (g < 0 ? g + fine : g);   // |g| < fine: one wrap at most
+                cell->x += a.x * wgt;
+                cell->y += a.y * wgt;
+            }
+            __syncwarp();
         }
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < UB * fine; k += blockDim.x) buf0[k] = cadd(buf0[k], buf1[k]);
     __syncthreads();
 
     // inverse transform of every row (exponent +)
@@ -102,5 +132,10 @@ __device__ __forceinline__ void rt_block(const NufftDesc &d, const FftPlan &fp,
 }
 
 inline int bins_per_block(int fine) { return fine <= 512 ? 16 : (fine <= 1024 ? 8 : 4); }
+
+// Shared memory of rt_block<UB>: twiddles, two fine grids per bin, the sources.
+inline size_t smem_bytes(int fine, int ub, int n_f) {
+    return (size_t)(fine + 2 * ub * fine + ub * n_f) * sizeof(float2) + (size_t)ub * n_f * sizeof(float);
+}
 
 }  // namespace rt

@@ -75,14 +75,22 @@ def run_batch(binding, scenes, echo_np, **kw):
     return b, [im.cpu().numpy() for im in imgs]
 
 
-def test_batch_matches_single_scan_path_and_oracle(binding, data):
+@pytest.mark.parametrize("kind", ["tensor_core", "persistent"])
+def test_batch_matches_single_scan_path_and_oracle(binding, data, kind):
+    # default: tensor-core back-projection per scene, scenes on parallel streams;
+    # persistent: the FP32 kernels in one persistent launch over all scenes
     scenes, echo_np = data
-    b, imgs = run_batch(binding, scenes, echo_np)
+    kw = {} if kind == "tensor_core" else dict(tile_u=16, block_config=1)
+    b, imgs = run_batch(binding, scenes, echo_np, **kw)
     info = b.info
-    assert info["persistent"] == 1 and info["n_scenes"] == len(scenes)
+    assert info["persistent"] == (0 if kind == "tensor_core" else 1)
+    assert info["n_scenes"] == len(scenes)
     for i, w in enumerate(scenes):
-        plan = binding.Plan.from_workload(w, tile_u=info["tile_u"],
-                                          block_config=info["block_config"])
+        if kind == "tensor_core":
+            plan = binding.Plan.from_workload(w, block_config=4)
+        else:
+            plan = binding.Plan.from_workload(w, tile_u=info["tile_u"],
+                                              block_config=info["block_config"])
         single = plan.execute(torch.from_numpy(echo_np[i]).cuda()).cpu().numpy()
         assert rel(imgs[i], single) < 1e-6, i
     for i in (0, 2, 3):
@@ -108,7 +116,9 @@ def test_autotuned_batch(binding, data):
     b, imgs = run_batch(binding, scenes, echo_np, autotune=True)
     info = b.info
     assert info["autotuned"] == 1 and info["tune_best_ms"] > 0
-    assert info["tile_u"] in (8, 16, 20) and info["block_config"] in (1, 3)
+    assert info["block_config"] in (1, 3, 4)
+    if info["block_config"] != 4:
+        assert info["tile_u"] in (8, 16, 20)
     w = scenes[0]
     ref = oracle.hybrid_exact(0, w.tx_xy, w.rx_xy, echo_np[0], w.z_scan, w.f_hz, w.n_pad,
                               w.pix_xy(), w.axis("z"))
@@ -130,7 +140,8 @@ def test_per_scene_fallback_when_not_persistent(binding, data):
 
 def test_unsatisfiable_wait_times_out_and_device_stays_usable(binding, data):
     scenes, echo_np = data
-    b = binding.Batch(scenes, debug_unsatisfiable=1, wait_timeout_ms=20.0)
+    b = binding.Batch(scenes, tile_u=16, block_config=1, debug_unsatisfiable=1,
+                      wait_timeout_ms=20.0)
     with pytest.raises(binding.PolylineError) as ei:
         b.execute([torch.from_numpy(e).cuda() for e in echo_np])
     assert ei.value.status == 8
