@@ -83,7 +83,7 @@ __device__ __forceinline__ void rt_block(const NufftDesc &d, const FftPlan &fp,
     __syncthreads();
 
     // inverse transform of every row (exponent +)
-    const float2 *res = stockham_run<false>(buf0, buf1, tw, fp, +1, UB, fine, 1);
+    const float2 *res = stockham_run<false, UB>(buf0, buf1, tw, fp, +1, fine, 1);
 
     // deconvolve, keep rows j = i - L/2
     if (fmt == 4) {

@@ -5,78 +5,118 @@
 //   dst[(j/Ns) Ns R + (j mod Ns) + q Ns] = sum_r v_r W_R^{r q},  q < R
 // for j < N/R. After all stages the data are in natural order. tw holds
 // exp(-2 pi i k / N), k < N; sgn = +1 conjugates it (inverse transform).
+// The small DFTs W_R use the exact values of the R-th roots of unity (R <= 5),
+// and the twiddle index (j mod Ns) r N/(Ns R) is below N (no reduction).
 #pragma once
 
 #include "common.cuh"
 
+namespace stockham_detail {
+
+// v <- DFT_R(v) with exponent sign -1 (sgn < 0) or +1 (sgn > 0)
 template <int R>
-__device__ __forceinline__ void stockham_small_dft(float2 (&v)[5], const float2 *tw, int N,
-                                                   int sgn) {
-    float2 o[R];
-    const int step = N / R;
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-        float2 acc = v[0];
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-            float2 w = tw[((r * q) % R) * step];
-            if (sgn > 0) w.y = -w.y;
-            acc = cadd(acc, cmul(v[r], w));
-        }
-        o[q] = acc;
-    }
-#pragma unroll
-    for (int q = 0; q < R; ++q) v[q] = o[q];
+__device__ __forceinline__ void small_dft(float2 (&v)[5], int sgn);
+
+template <>
+__device__ __forceinline__ void small_dft<2>(float2 (&v)[5], int) {
+    const float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
 }
 
-// COL_FAST: consecutive threads take consecutive columns (use when columns
-// are the contiguous axis); otherwise consecutive j.
-template <int R, bool COL_FAST>
+template <>
+__device__ __forceinline__ void small_dft<4>(float2 (&v)[5], int sgn) {
+    // W_4 = -i (forward) / +i (inverse)
+    const float2 s0 = cadd(v[0], v[2]), d0 = csub(v[0], v[2]);
+    const float2 s1 = cadd(v[1], v[3]), d1 = csub(v[1], v[3]);
+    // d1 * W_4: forward (x, y) -> (y, -x); inverse (x, y) -> (-y, x)
+    const float2 r1 = sgn < 0 ? make_float2(d1.y, -d1.x) : make_float2(-d1.y, d1.x);
+    v[0] = cadd(s0, s1);
+    v[2] = csub(s0, s1);
+    v[1] = cadd(d0, r1);
+    v[3] = csub(d0, r1);
+}
+
+template <>
+__device__ __forceinline__ void small_dft<3>(float2 (&v)[5], int sgn) {
+    // W_3 = -1/2 -+ i sqrt(3)/2
+    const float c = -0.5f, s = (sgn < 0 ? -1.f : 1.f) * 0.866025403784438647f;
+    const float2 t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+    const float2 m = make_float2(v[0].x + c * t.x, v[0].y + c * t.y);
+    const float2 r = make_float2(-s * d.y, s * d.x);    // i s d
+    v[0] = cadd(v[0], t);
+    v[1] = cadd(m, r);
+    v[2] = csub(m, r);
+}
+
+template <>
+__device__ __forceinline__ void small_dft<5>(float2 (&v)[5], int sgn) {
+    // cos / sin of 2 pi / 5 and 4 pi / 5
+    const float c1 = 0.309016994374947424f, c2 = -0.809016994374947424f;
+    const float sg = sgn < 0 ? -1.f : 1.f;
+    const float s1 = sg * 0.951056516295153572f, s2 = sg * 0.587785252292473129f;
+    const float2 t1 = cadd(v[1], v[4]), d1 = csub(v[1], v[4]);
+    const float2 t2 = cadd(v[2], v[3]), d2 = csub(v[2], v[3]);
+    const float2 a1 = make_float2(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+    const float2 a2 = make_float2(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+    // b1 = i (s1 d1 + s2 d2), b2 = i (s2 d1 - s1 d2)
+    const float2 e1 = make_float2(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
+    const float2 e2 = make_float2(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
+    const float2 b1 = make_float2(-e1.y, e1.x), b2 = make_float2(-e2.y, e2.x);
+    v[0] = cadd(v[0], cadd(t1, t2));
+    v[1] = cadd(a1, b1);
+    v[4] = csub(a1, b1);
+    v[2] = cadd(a2, b2);
+    v[3] = csub(a2, b2);
+}
+
+}  // namespace stockham_detail
+
+// NCOL columns (compile time). COL_FAST: consecutive threads take consecutive
+// columns (use when columns are the contiguous axis); otherwise consecutive j.
+template <int R, bool COL_FAST, int NCOL>
 __device__ __forceinline__ void stockham_stage(const float2 *src, float2 *dst, const float2 *tw,
-                                               int N, int Ns, int sgn, int ncol, int cs, int ns) {
+                                               int N, int Ns, int sgn, int cs, int ns) {
     const int nr = N / R;
-    const int items = nr * ncol;
+    const int items = nr * NCOL;
     const int tw_step = N / (Ns * R);
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
         int j, col;
-        if (COL_FAST) { j = it / ncol; col = it - j * ncol; }
+        if (COL_FAST) { j = it / NCOL; col = it - j * NCOL; }
         else { col = it / nr; j = it - col * nr; }
-        const int k = j % Ns;
+        const int jh = j / Ns;
+        const int k = j - jh * Ns;
         const float2 *s = src + col * cs;
         float2 v[5];
+        v[0] = s[j * ns];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            float2 x = s[(j + r * nr) * ns];
-            if (r > 0) {
-                float2 w = tw[(k * r * tw_step) % N];
-                if (sgn > 0) w.y = -w.y;
-                x = cmul(x, w);
-            }
-            v[r] = x;
+        for (int r = 1; r < R; ++r) {
+            float2 w = tw[k * r * tw_step];
+            if (sgn > 0) w.y = -w.y;
+            v[r] = cmul(s[(j + r * nr) * ns], w);
         }
-        stockham_small_dft<R>(v, tw, N, sgn);
+        stockham_detail::small_dft<R>(v, sgn);
         float2 *d = dst + col * cs;
-        const int base = (j / Ns) * Ns * R + k;
+        const int base = jh * Ns * R + k;
 #pragma unroll
         for (int q = 0; q < R; ++q) d[(base + q * Ns) * ns] = v[q];
     }
 }
 
-// Runs every stage of `plan`; returns the buffer holding the result. Ends
-// with a __syncthreads().
-template <bool COL_FAST>
+// Runs every stage of `plan` on NCOL columns; returns the buffer holding the
+// result. Ends with a __syncthreads().
+template <bool COL_FAST, int NCOL>
 __device__ __forceinline__ float2 *stockham_run(float2 *buf0, float2 *buf1, const float2 *tw,
-                                                const FftPlan &plan, int sgn, int ncol, int cs,
-                                                int ns) {
+                                                const FftPlan &plan, int sgn, int cs, int ns) {
     float2 *src = buf0, *dst = buf1;
     int Ns = 1;
     const int N = plan.n;
     for (int s = 0; s < plan.n_stages; ++s) {
         const int R = plan.radix[s];
-        if (R == 4) stockham_stage<4, COL_FAST>(src, dst, tw, N, Ns, sgn, ncol, cs, ns);
-        else if (R == 2) stockham_stage<2, COL_FAST>(src, dst, tw, N, Ns, sgn, ncol, cs, ns);
-        else if (R == 3) stockham_stage<3, COL_FAST>(src, dst, tw, N, Ns, sgn, ncol, cs, ns);
-        else stockham_stage<5, COL_FAST>(src, dst, tw, N, Ns, sgn, ncol, cs, ns);
+        if (R == 4) stockham_stage<4, COL_FAST, NCOL>(src, dst, tw, N, Ns, sgn, cs, ns);
+        else if (R == 2) stockham_stage<2, COL_FAST, NCOL>(src, dst, tw, N, Ns, sgn, cs, ns);
+        else if (R == 3) stockham_stage<3, COL_FAST, NCOL>(src, dst, tw, N, Ns, sgn, cs, ns);
+        else stockham_stage<5, COL_FAST, NCOL>(src, dst, tw, N, Ns, sgn, cs, ns);
         __syncthreads();
         float2 *t = src; src = dst; dst = t;
         Ns *= R;

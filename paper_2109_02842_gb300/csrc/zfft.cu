@@ -40,7 +40,7 @@ k_fft_strided(const float2 *__restrict__ in, float2 *__restrict__ out, int n_in,
     }
     __syncthreads();
 
-    const float2 *src = stockham_run<true>(buf0, buf1, tw, plan, sgn, kFftIB, 1, kFftIB);
+    const float2 *src = stockham_run<true, kFftIB>(buf0, buf1, tw, plan, sgn, 1, kFftIB);
 
     for (int idx = threadIdx.x; idx < out_rows * kFftIB; idx += blockDim.x) {
         const int r = idx / kFftIB;
