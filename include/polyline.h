@@ -175,6 +175,26 @@ pl_status pl_execute(pl_plan *plan, const void *echo_dev, void *image_dev, void 
 pl_status pl_execute_host(pl_plan *plan, const void *echo_host, void *image_host,
                           void *stream);
 
+/* The two comparison algorithms of Sec. III (Table II), on the plan's
+ * geometry, scan, band and voxel grid; same buffers as pl_execute, asynchronous
+ * on `stream`. They exist to time and check the method against; their first
+ * call builds small per-plan tables (synchronously).
+ *
+ * pl_execute_exact: the hybrid method with exact nonuniform sums instead of
+ * the NUFFT ("omega-K-BP" of Sec. III): z-FFT (Eq. 2), then per k_z bin and
+ * pixel G = sum_c sum_m S k_m e^{+j kappa a_c} (Eq. 7 / 19, evanescent terms
+ * dropped), then the inverse transform over k_z (Eq. 9). FP32 with
+ * float-float phases; cost C x M x N_p per pixel.
+ *
+ * pl_execute_bp_direct: direct back-projection (the "BP" of Sec. III), the
+ * matched filter of the echo model Eq. (1) / (10) with the k weight:
+ * g(x,y,z) = sum_c sum_n sum_m s[c][n][m] k_m e^{+j k_m (R_T + R_R)},
+ * R = distance from the element at scan height z'_n to the voxel. FP32 with
+ * float-float ranges and phases; cost C x N x M per voxel. */
+pl_status pl_execute_exact(pl_plan *plan, const void *echo_dev, void *image_dev, void *stream);
+pl_status pl_execute_bp_direct(pl_plan *plan, const void *echo_dev, void *image_dev,
+                               void *stream);
+
 pl_status pl_plan_destroy(pl_plan *plan);
 pl_status pl_plan_get_info(const pl_plan *plan, pl_info *info);
 

@@ -67,7 +67,8 @@ class PlBatchInfo(ctypes.Structure):
                 ("updates_per_execute", _D), ("workspace_bytes", ctypes.c_size_t)]
 
 
-EXPORTED = ("pl_plan_create", "pl_execute", "pl_execute_host", "pl_plan_destroy",
+EXPORTED = ("pl_plan_create", "pl_execute", "pl_execute_host", "pl_execute_exact",
+            "pl_execute_bp_direct", "pl_plan_destroy",
             "pl_plan_get_info", "pl_plan_workspace", "pl_plan_set_timing",
             "pl_plan_stage_times", "pl_synth_echo", "pl_synth_echo_static",
             "pl_batch_create", "pl_execute_batch", "pl_batch_get_info", "pl_batch_destroy",
@@ -98,6 +99,8 @@ def load(path: str = LIB_PATH):
                                    ctypes.POINTER(PlGrid), ctypes.POINTER(PlOptions)]
     lib.pl_execute.argtypes = [_P, _P, _P, _P]
     lib.pl_execute_host.argtypes = [_P, _P, _P, _P]
+    lib.pl_execute_exact.argtypes = [_P, _P, _P, _P]
+    lib.pl_execute_bp_direct.argtypes = [_P, _P, _P, _P]
     lib.pl_plan_destroy.argtypes = [_P]
     lib.pl_plan_get_info.argtypes = [_P, ctypes.POINTER(PlInfo)]
     lib.pl_plan_workspace.argtypes = [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t)]
@@ -257,6 +260,23 @@ class Plan:
         else:
             iptr = image.ctypes.data
         _check(load().pl_execute_host(self._h, _P(eptr), _P(iptr), _stream_handle(stream)))
+        return image
+
+    def execute_exact(self, echo, image=None, stream=None):
+        """The exact-sum hybrid ("omega-K-BP", Sec. III): same buffers as execute."""
+        return self._execute_with(load().pl_execute_exact, echo, image, stream)
+
+    def execute_bp_direct(self, echo, image=None, stream=None):
+        """Direct back-projection (the "BP" of Sec. III): same buffers as execute."""
+        return self._execute_with(load().pl_execute_bp_direct, echo, image, stream)
+
+    def _execute_with(self, fn, echo, image, stream):
+        import torch
+        assert echo.is_cuda and echo.dtype == torch.complex64 and echo.is_contiguous()
+        assert tuple(echo.shape) == self.echo_shape
+        if image is None:
+            image = torch.empty(self.image_shape, dtype=torch.complex64, device=echo.device)
+        _check(fn(self._h, _P(echo.data_ptr()), _P(image.data_ptr()), _stream_handle(stream)))
         return image
 
     def workspace(self, stage):

@@ -113,6 +113,29 @@ cudaError_t launch_setup_tile_geo_tc(const BpDesc &p, const double *ch_xy, TileG
                                      int *stats, cudaStream_t st);
 int backproject_tile_y();
 
+// ---- comparison.cu: exact-sum hybrid and direct back-projection (Sec. III) ------
+struct ExactDesc {
+    int mode, n_chan, n_pad, n_f, nx, ny;
+    double x0, dx, y0, dy;
+};
+struct DirectDesc {
+    int mode, n_chan, n_scan, n_f, nx, ny, nz;
+    int uniform;                    // evenly spaced band: rotation from k_0 by dk
+    double x0, dx, y0, dy, z0, dz;
+    float k0_hi, k0_lo, dk_hi, dk_lo;
+};
+// S [C][N_p][M]; kap [N_p][M] kappa as float pairs; wum [N_p][M] k_m or 0
+// (evanescent); chff [C][2] float4 (xT hi, lo, yT hi, lo), (xR ..); G [N_p][ny][nx]
+cudaError_t launch_exact_sum(const ExactDesc &e, const float2 *S, const float2 *kap,
+                             const float *wum, const float4 *chff, float2 *G, cudaStream_t st);
+// s [C][N][M] echo; zs [N] scan heights and kff [M] wavenumbers as float pairs;
+// img [nz][ny][nx]
+cudaError_t launch_bp_direct(const DirectDesc &e, const float2 *s, const float4 *chff,
+                             const float2 *zs, const float2 *kff, float2 *img, cudaStream_t st);
+// kap / wum of the exact sum, per (k_z bin, frequency)
+cudaError_t launch_setup_exact(int mode, int n_pad, double dz, int n_f, const double *k,
+                               float2 *kap, float *wum, cudaStream_t st);
+
 // ---- plan.cu: error reporting for other translation units ----------------------
 #include "../../include/polyline.h"
 pl_status pl_internal_fail(pl_status s, const char *msg);

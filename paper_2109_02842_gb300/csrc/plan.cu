@@ -293,6 +293,8 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     }
     std::vector<double> k(P->M);
     for (int m = 0; m < P->M; ++m) k[m] = PL_TWO_PI * f->f_hz[m] / PL_C0;
+    P->h_chxy = chxy;
+    P->h_k = k;
 
     size_t &ws = P->workspace;
     PL_CUDA(dalloc(&P->d_chxy, chxy.size(), ws), "cudaMalloc");
@@ -627,6 +629,84 @@ pl_status run(pl_plan *P, const float2 *echo, float2 *image, cudaStream_t st) {
 pl_status pl_internal_fail(pl_status s, const char *msg) { return fail(s, msg); }
 pl_status pl_internal_cuda_fail(cudaError_t e, const char *where) { return cuda_fail(e, where); }
 
+// Tables of the comparison algorithms (first use only): kappa and k weights
+// per (k_z, f), positions, scan heights and wavenumbers as float pairs.
+static pl_status prepare_comparison(pl_plan *P) {
+    if (P->cmp_ready) return PL_OK;
+    auto pair = [](double v) {
+        const float h = (float)v;
+        return std::make_pair(h, (float)(v - (double)h));
+    };
+    std::vector<float4> chff(2 * (size_t)P->C);
+    for (int c = 0; c < P->C; ++c) {
+        const double *q = &P->h_chxy[4 * (size_t)c];
+        auto xt = pair(q[0]), yt = pair(q[1]), xr = pair(q[2]), yr = pair(q[3]);
+        chff[2 * c] = make_float4(xt.first, xt.second, yt.first, yt.second);
+        chff[2 * c + 1] = make_float4(xr.first, xr.second, yr.first, yr.second);
+    }
+    std::vector<float2> zs(P->N), kff(P->M);
+    for (int n = 0; n < P->N; ++n) {
+        auto z = pair(P->z0s + n * P->dzs);
+        zs[n] = make_float2(z.first, z.second);
+    }
+    bool uniform = P->M >= 2;
+    const double dk = P->M >= 2 ? (P->h_k[P->M - 1] - P->h_k[0]) / (P->M - 1) : 0.0;
+    for (int m = 0; m < P->M; ++m) {
+        auto kv = pair(P->h_k[m]);
+        kff[m] = make_float2(kv.first, kv.second);
+        if (std::fabs(P->h_k[m] - (P->h_k[0] + m * dk)) > 1e-9 * P->h_k[m]) uniform = false;
+    }
+    size_t ws = 0;
+    PL_CUDA(dalloc(&P->d_chff, chff.size(), ws), "cudaMalloc");
+    PL_CUDA(dalloc(&P->d_zs, zs.size(), ws), "cudaMalloc");
+    PL_CUDA(dalloc(&P->d_kff, kff.size(), ws), "cudaMalloc");
+    PL_CUDA(dalloc(&P->d_kap, (size_t)P->Np * P->M, ws), "cudaMalloc");
+    PL_CUDA(dalloc(&P->d_wum, (size_t)P->Np * P->M, ws), "cudaMalloc");
+    PL_CUDA(cudaMemcpy(P->d_chff, chff.data(), chff.size() * sizeof(float4), cudaMemcpyHostToDevice),
+            "copy");
+    PL_CUDA(cudaMemcpy(P->d_zs, zs.data(), zs.size() * sizeof(float2), cudaMemcpyHostToDevice),
+            "copy");
+    PL_CUDA(cudaMemcpy(P->d_kff, kff.data(), kff.size() * sizeof(float2), cudaMemcpyHostToDevice),
+            "copy");
+    PL_CUDA(launch_setup_exact(P->mode, P->Np, P->dzs, P->M, P->d_k, P->d_kap, P->d_wum, 0),
+            "setup_exact");
+    PL_CUDA(cudaDeviceSynchronize(), "setup_exact");
+    P->workspace += ws;
+    ExactDesc &e = P->exact;
+    e.mode = P->mode;
+    e.n_chan = P->C;
+    e.n_pad = P->Np;
+    e.n_f = P->M;
+    e.nx = P->grid.nx;
+    e.ny = P->grid.ny;
+    e.x0 = P->grid.x0;
+    e.dx = P->grid.dx;
+    e.y0 = P->grid.y0;
+    e.dy = P->grid.dy;
+    DirectDesc &d = P->direct;
+    d.mode = P->mode;
+    d.n_chan = P->C;
+    d.n_scan = P->N;
+    d.n_f = P->M;
+    d.nx = P->grid.nx;
+    d.ny = P->grid.ny;
+    d.nz = P->grid.nz;
+    d.uniform = uniform ? 1 : 0;
+    d.x0 = P->grid.x0;
+    d.dx = P->grid.dx;
+    d.y0 = P->grid.y0;
+    d.dy = P->grid.dy;
+    d.z0 = P->grid.z0;
+    d.dz = P->grid.dz;
+    auto k0 = pair(P->h_k[0]), dkp = pair(dk);
+    d.k0_hi = k0.first;
+    d.k0_lo = k0.second;
+    d.dk_hi = dkp.first;
+    d.dk_lo = dkp.second;
+    P->cmp_ready = true;
+    return PL_OK;
+}
+
 extern "C" {
 
 const char *pl_status_string(pl_status s) {
@@ -706,6 +786,29 @@ pl_status pl_execute(pl_plan *plan, const void *echo_dev, void *image_dev, void 
     pl_status s = take_device_timeout(plan);
     if (s != PL_OK) return s;
     return run(plan, (const float2 *)echo_dev, (float2 *)image_dev, (cudaStream_t)stream);
+}
+
+pl_status pl_execute_exact(pl_plan *plan, const void *echo_dev, void *image_dev, void *stream) {
+    if (!plan || !echo_dev || !image_dev) return fail(PL_ERR_ARG, "NULL argument");
+    pl_status s = prepare_comparison(plan);
+    if (s != PL_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = pl_stage_zfft(plan, (const float2 *)echo_dev, st)) != PL_OK) return s;
+    PL_CUDA(launch_exact_sum(plan->exact, plan->d_S, plan->d_kap, plan->d_wum, plan->d_chff,
+                             plan->d_G, st),
+            "exact_sum");
+    return pl_stage_zifft(plan, (float2 *)image_dev, st);
+}
+
+pl_status pl_execute_bp_direct(pl_plan *plan, const void *echo_dev, void *image_dev,
+                               void *stream) {
+    if (!plan || !echo_dev || !image_dev) return fail(PL_ERR_ARG, "NULL argument");
+    pl_status s = prepare_comparison(plan);
+    if (s != PL_OK) return s;
+    PL_CUDA(launch_bp_direct(plan->direct, (const float2 *)echo_dev, plan->d_chff, plan->d_zs,
+                             plan->d_kff, (float2 *)image_dev, (cudaStream_t)stream),
+            "bp_direct");
+    return PL_OK;
 }
 
 pl_status pl_execute_host(pl_plan *plan, const void *echo_host, void *image_host, void *stream) {

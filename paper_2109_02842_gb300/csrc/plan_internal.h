@@ -46,6 +46,14 @@ struct pl_plan {
     void *d_table = nullptr;
     size_t table_bytes = 0;
     float2 *d_echo_in = nullptr, *d_img_out = nullptr;   // pl_execute_host staging
+    // comparison algorithms (exact sum, direct BP), set up on first use
+    std::vector<double> h_chxy, h_k;                      // [C][4] positions, [M] k
+    float2 *d_kap = nullptr, *d_zs = nullptr, *d_kff = nullptr;
+    float *d_wum = nullptr;
+    float4 *d_chff = nullptr;
+    bool cmp_ready = false;
+    ExactDesc exact{};
+    DirectDesc direct{};
     size_t workspace = 0;
     int n_gl = 0;
     // timing
@@ -57,7 +65,8 @@ struct pl_plan {
     ~pl_plan() {
         void *ptrs[] = {d_chxy, d_k,    d_kc,   d_kspan, d_glx,  d_glw,     d_kchl, d_tgeo,
                         d_xg,   d_dec,  d_alpha, d_twz,  d_twfine, d_Tfwd, d_Tinv,
-                        d_S,    d_G,    d_table, d_echo_in, d_img_out};
+                        d_S,    d_G,    d_table, d_echo_in, d_img_out, d_kap, d_zs,
+                        d_kff,  d_wum,  d_chff};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);

@@ -225,6 +225,25 @@ __global__ void k_setup_tile_geo_tc(BpDesc p, int ntx, int nty, const double *ch
     atomicMax(&stats[1], ilo);
 }
 
+// kappa (float pair) and the k weight of every (k_z bin, frequency) for the
+// exact sum; both zero where the term is evanescent.
+__global__ void k_setup_exact(int mode, int n_pad, double dz, int n_f, const double *k,
+                              float2 *kap, float *wum) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_pad * n_f) return;
+    const int u = idx / n_f, m = idx - u * n_f;
+    const double q = kappa_sq(mode, k[m], kz_of(u, n_pad, dz));
+    if (q <= 0.0) {
+        kap[idx] = make_float2(0.f, 0.f);
+        wum[idx] = 0.f;
+        return;
+    }
+    const double kp = sqrt(q);
+    const float h = (float)kp;
+    kap[idx] = make_float2(h, (float)(kp - (double)h));
+    wum[idx] = (float)k[m];
+}
+
 inline int blocks(long long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
@@ -234,6 +253,13 @@ cudaError_t launch_setup_tile_geo_tc(const BpDesc &p, const double *ch_xy, TileG
     const int ntx = (p.nx + p.tile_px - 1) / p.tile_px, nty = (p.ny + p.tile_py - 1) / p.tile_py;
     k_setup_tile_geo_tc<<<blocks((long long)ntx * nty * p.n_chan, 128), 128, 0, st>>>(
         p, ntx, nty, ch_xy, tgeo, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup_exact(int mode, int n_pad, double dz, int n_f, const double *k,
+                               float2 *kap, float *wum, cudaStream_t st) {
+    k_setup_exact<<<blocks((long long)n_pad * n_f, 128), 128, 0, st>>>(mode, n_pad, dz, n_f, k,
+                                                                      kap, wum);
     return cudaGetLastError();
 }
 
