@@ -175,6 +175,31 @@ pl_status pl_execute(pl_plan *plan, const void *echo_dev, void *image_dev, void 
 pl_status pl_execute_host(pl_plan *plan, const void *echo_host, void *image_host,
                           void *stream);
 
+/* Sampling and resolution design figures of Sec. II-C/D for an array, scan
+ * and band (host computation, no device work):
+ *   max_rx_spacing   = lambda_min sqrt((L_R + D)^2/4 + R_0^2) / (L_R + D), the
+ *                      multistatic receive spacing limit; max_elem_spacing is
+ *                      that (multistatic) or half of it (monostatic);
+ *   max_scan_step    = lambda_min / (4 sin(theta_z/2));
+ *   res_x = lambda_c / (4 sin(theta_h/2)), res_y = c / (2 B),
+ *   res_z = lambda_c / (4 sin(theta_z/2)).
+ * L_R = chord_len, R_0 = radius cos(half the chord angle) (chord to scene
+ * centre), D = target_dim (largest target dimension, m), theta_h = the arc of
+ * all chords, theta_z = the smaller of the angle the scan length subtends at
+ * the radius and beamwidth_z_deg (0: no beam limit). elem_spacing is the
+ * largest gap between neighbouring (receive) elements of a section;
+ * spacing_ok / scan_step_ok compare the actual values with the limits. */
+typedef struct {
+    double lambda_min, lambda_c, bandwidth;
+    double theta_h_deg, theta_z_deg;
+    double max_rx_spacing, max_elem_spacing, max_scan_step;
+    double res_x, res_y, res_z;
+    double elem_spacing, scan_step;
+    int spacing_ok, scan_step_ok;
+} pl_design_info;
+pl_status pl_design(const pl_geometry *geom, const pl_scan *scan, const pl_freqs *freqs,
+                    double target_dim, double beamwidth_z_deg, pl_design_info *out);
+
 /* The two comparison algorithms of Sec. III (Table II), on the plan's
  * geometry, scan, band and voxel grid; same buffers as pl_execute, asynchronous
  * on `stream`. They exist to time and check the method against; their first

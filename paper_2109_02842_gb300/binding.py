@@ -68,7 +68,7 @@ class PlBatchInfo(ctypes.Structure):
 
 
 EXPORTED = ("pl_plan_create", "pl_execute", "pl_execute_host", "pl_execute_exact",
-            "pl_execute_bp_direct", "pl_plan_destroy",
+            "pl_execute_bp_direct", "pl_design", "pl_plan_destroy",
             "pl_plan_get_info", "pl_plan_workspace", "pl_plan_set_timing",
             "pl_plan_stage_times", "pl_synth_echo", "pl_synth_echo_static",
             "pl_batch_create", "pl_execute_batch", "pl_batch_get_info", "pl_batch_destroy",
@@ -78,6 +78,15 @@ EXPORTED = ("pl_plan_create", "pl_execute", "pl_execute_host", "pl_execute_exact
             "pl_status_string", "pl_last_error", "pl_version")
 
 _lib = None
+
+
+class PlDesignInfo(ctypes.Structure):
+    _fields_ = [("lambda_min", _D), ("lambda_c", _D), ("bandwidth", _D),
+                ("theta_h_deg", _D), ("theta_z_deg", _D),
+                ("max_rx_spacing", _D), ("max_elem_spacing", _D), ("max_scan_step", _D),
+                ("res_x", _D), ("res_y", _D), ("res_z", _D),
+                ("elem_spacing", _D), ("scan_step", _D),
+                ("spacing_ok", _I), ("scan_step_ok", _I)]
 
 
 class PolylineError(RuntimeError):
@@ -326,6 +335,20 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def design(w, target_dim=0.0, beamwidth_z_deg=0.0) -> dict:
+    """Sampling and resolution figures of Sec. II-C/D (pl_design) for a
+    workload's array, scan and band (host computation)."""
+    lib = load()
+    keep = []
+    geom, scan, freqs, _, _ = _descriptors(keep, *_workload_args(w), 0, 0.0, 0, 0, 0)
+    d = PlDesignInfo()
+    lib.pl_design.argtypes = [ctypes.POINTER(PlGeometry), ctypes.POINTER(PlScan),
+                              ctypes.POINTER(PlFreqs), _D, _D, ctypes.POINTER(PlDesignInfo)]
+    _check(lib.pl_design(ctypes.byref(geom), ctypes.byref(scan), ctypes.byref(freqs),
+                         float(target_dim), float(beamwidth_z_deg), ctypes.byref(d)))
+    return {k: getattr(d, k) for k, _ in PlDesignInfo._fields_}
 
 
 def synth_echo(tx_xy, rx_xy, z0, dz, n_scan, f_hz, pts, amp, out=None, stream=None):

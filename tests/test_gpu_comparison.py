@@ -118,3 +118,34 @@ def test_bp_and_hybrid_focus_on_the_same_voxel(binding):
     c = np.corrcoef(g_h.ravel(), g_b.ravel())[0, 1]
     print("|g| correlation hybrid vs BP: %.3f" % c)
     assert c > 0.9
+
+
+def _width_3db(line, step):
+    a = np.abs(line) / np.abs(line).max()
+    i = int(np.argmax(a))
+    lo = hi = i
+    while lo > 0 and a[lo] >= 0.5 ** 0.5:
+        lo -= 1
+    while hi < a.size - 1 and a[hi] >= 0.5 ** 0.5:
+        hi += 1
+    return (hi - lo) * step
+
+
+@pytest.mark.parametrize("axis", ["x", "y", "z"])
+def test_point_spread_widths_match_design(binding, axis):
+    # -3 dB widths of the GPU image of one point at the scene centre against
+    # the Sec. II-D resolutions reported by pl_design (0.5x - 2x, as the
+    # formulas are approximations)
+    w = wl.small_mono(seed=0)
+    step, n = 0.0005, 161
+    t0 = -(n // 2) * step
+    g = dict(x0=0.0, dx=step, nx=1, y0=0.0, dy=step, ny=1, z0=0.0, dz=step, nz=1)
+    g[axis + "0"], g["n" + axis] = t0, n
+    w.grid = g
+    s = oracle.synth_echo(w.tx_xy, w.rx_xy, w.z_scan, w.f_hz, np.zeros((1, 3)), np.ones(1))
+    plan = binding.Plan.from_workload(w)
+    img = plan.execute(torch.from_numpy(s.astype(np.complex64)).cuda()).cpu().numpy().ravel()
+    got = _width_3db(img, step)
+    want = binding.design(w)["res_" + axis]
+    print("point spread %s: -3 dB width %.4f m, Sec. II-D %.4f m" % (axis, got, want))
+    assert 0.5 * want <= got <= 2.0 * want
