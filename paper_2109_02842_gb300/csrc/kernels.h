@@ -113,6 +113,26 @@ cudaError_t launch_setup_tile_geo_tc(const BpDesc &p, const double *ch_xy, TileG
                                      int *stats, cudaStream_t st);
 int backproject_tile_y();
 
+// ---- range_table_tc.cu: the range table as exact sums on the tensor cores ------
+struct RtTcArgs {
+    int C, Np, M;
+    int Kp;              // frequencies rounded up to 64 (the K of the products)
+    int natoms;          // Kp / 64
+    int L, Lp;           // table rows; rounded up to 16 (the N of the products)
+    unsigned idesc;      // tcgen05 instruction descriptor (M 128, N Lp, both K-major)
+    long long budget;    // wait budget, SM clock cycles
+};
+size_t range_table_tc_smem_bytes(const RtTcArgs &ra);
+// E [N_p][re hi, re lo, im hi, im lo][Lp][Kp] BF16: e^{+j theta_um (i - L/2)}
+cudaError_t launch_setup_rt_E(const NufftDesc &d, double dz, const double *k, const double *kc,
+                              int Lp, int Kp, void *E, cudaStream_t st);
+// S, alpha -> A (scratch [N_p][4][C][Kp] BF16) -> prod (scratch [N_p][2][C][Lp]
+// uint32) -> table [C][2][L][row_words uint32]
+cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
+                                  const CUtensorMap &tmB, const float2 *S, const float2 *alpha,
+                                  void *A, void *prod, void *table, int row_words, int *err,
+                                  cudaStream_t st);
+
 // ---- comparison.cu: exact-sum hybrid and direct back-projection (Sec. III) ------
 struct ExactDesc {
     int mode, n_chan, n_pad, n_f, nx, ny;

@@ -538,6 +538,46 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         *P->h_err = 0;
         PL_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void **>(&P->d_err), P->h_err, 0),
                 "cudaHostGetDevicePointer");
+        // the range table as exact sums on the tensor cores (one 64-frequency
+        // step: up to 64 frequencies; table rows up to 256), else the NUFFT
+        RtTcArgs &ra = P->rt;
+        ra.C = P->C;
+        ra.Np = P->Np;
+        ra.M = P->M;
+        ra.Kp = (P->M + 63) / 64 * 64;
+        ra.natoms = ra.Kp / 64;
+        ra.L = L;
+        ra.Lp = (L + 15) / 16 * 16;
+        ra.idesc = tc05::idesc_bf16(128, ra.Lp, 0);
+        ra.budget = 4ll << 30;
+        P->rt_tc = ra.natoms == 1 && ra.Lp <= 256 &&
+                   range_table_tc_smem_bytes(ra) <= 227 * 1024;
+        if (P->rt_tc) {
+            const size_t nE = (size_t)P->Np * 4 * ra.Lp * ra.Kp;
+            const size_t nA = (size_t)P->Np * 4 * P->C * ra.Kp;
+            const size_t nprod = (size_t)P->Np * 2 * P->C * ra.Lp;
+            PL_CUDA(cudaMalloc(&P->d_rtE, nE * 2), "cudaMalloc");
+            PL_CUDA(cudaMalloc(&P->d_rtA, nA * 2), "cudaMalloc");
+            PL_CUDA(cudaMalloc(&P->d_rtprod, nprod * 4), "cudaMalloc");
+            ws += nE * 2 + nA * 2 + nprod * 4;
+            PL_CUDA(launch_setup_rt_E(d, P->dzs, P->d_k, P->d_kc, ra.Lp, ra.Kp, P->d_rtE, st),
+                    "setup_rt_E");
+            const cuuint64_t da[3] = {(cuuint64_t)ra.Kp, (cuuint64_t)P->C, 4 * (cuuint64_t)P->Np};
+            const cuuint64_t sa[2] = {(cuuint64_t)ra.Kp * 2, (cuuint64_t)P->C * ra.Kp * 2};
+            const cuuint32_t ba[3] = {64, 128, 1};
+            const cuuint64_t db[3] = {(cuuint64_t)ra.Kp, (cuuint64_t)ra.Lp, 4 * (cuuint64_t)P->Np};
+            const cuuint64_t sb[2] = {(cuuint64_t)ra.Kp * 2, (cuuint64_t)ra.Lp * ra.Kp * 2};
+            const cuuint32_t bb[3] = {64, (cuuint32_t)ra.Lp, 1};
+            const cuuint32_t e3[3] = {1, 1, 1};
+            CUresult r1 = enc(&P->tmapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, P->d_rtA, da, sa, ba,
+                              e3, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            CUresult r2 = enc(&P->tmapE, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, P->d_rtE, db, sb, bb,
+                              e3, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS)
+                return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled failed (range table)");
+        }
     }
     PL_CUDA(dalloc(&P->d_G, (size_t)P->Np * gr->nx * gr->ny, ws), "cudaMalloc");
     PL_CUDA(cudaDeviceSynchronize(), "plan setup");
@@ -557,6 +597,12 @@ pl_status pl_stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st) {
 }
 
 pl_status pl_stage_range_table(pl_plan *P, cudaStream_t st) {
+    if (P->block_config == 4 && P->rt_tc) {
+        PL_CUDA(launch_range_table_tc(P->rt, P->tmapA, P->tmapE, P->d_S, P->d_alpha, P->d_rtA,
+                                      P->d_rtprod, P->d_table, P->nd.tc_cols / 2, P->d_err, st),
+                "range_table_tc");
+        return PL_OK;
+    }
     const int fmt = P->block_config == 4 ? 4 : (P->precision == 1 ? 1 : 0);
     PL_CUDA(launch_range_table(P->nd, P->fineplan, P->d_S, P->d_alpha, P->d_xg, P->d_dec,
                                P->d_twfine, P->d_table, fmt, st), "range_table");

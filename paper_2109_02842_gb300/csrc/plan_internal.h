@@ -27,6 +27,11 @@ struct pl_plan {
     CUtensorMap tmap{};    // its TMA map of the range table
     int *h_err = nullptr;  // its timeout flags (mapped host memory) and device alias
     int *d_err = nullptr;
+    // its range table as exact sums on the tensor cores (range_table_tc.cu)
+    bool rt_tc = false;
+    RtTcArgs rt{};
+    CUtensorMap tmapA{}, tmapE{};
+    void *d_rtE = nullptr, *d_rtA = nullptr, *d_rtprod = nullptr;
     CoefTable coef{};
     BpDesc bp{};
     // transforms
@@ -66,7 +71,7 @@ struct pl_plan {
         void *ptrs[] = {d_chxy, d_k,    d_kc,   d_kspan, d_glx,  d_glw,     d_kchl, d_tgeo,
                         d_xg,   d_dec,  d_alpha, d_twz,  d_twfine, d_Tfwd, d_Tinv,
                         d_S,    d_G,    d_table, d_echo_in, d_img_out, d_kap, d_zs,
-                        d_kff,  d_wum,  d_chff};
+                        d_kff,  d_wum,  d_chff, d_rtE, d_rtA, d_rtprod};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
