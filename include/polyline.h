@@ -225,10 +225,12 @@ pl_status pl_plan_get_info(const pl_plan *plan, pl_info *info);
 
 /* Device pointer and size of an intermediate buffer, valid until the plan is
  * destroyed (for inspection and tests):
- *  PL_STAGE_ZFFT        -> spectrum S, complex64 [n_chan][n_pad][n_f]
+ *  PL_STAGE_ZFFT        -> spectrum S, complex64 [n_chan][n_pad][n_f] (not written by
+ *                          the tensor-core path with an FFT-length scan: there the
+ *                          z-FFT hands its output straight to the range table)
  *  PL_STAGE_RANGE_TABLE -> table b, [n_chan][L][ceil(n_pad/2)] rows of k_z bin pairs
  *                          {re_u, re_u+1, im_u, im_u+1} (float32, or bfloat16 when
- *                          precision = 1)
+ *                          precision = 1); block_config 4: see pl_options
  *  PL_STAGE_BACKPROJECT -> image spectrum G, complex64 [n_pad][ny][nx] */
 pl_status pl_plan_workspace(pl_plan *plan, int stage, void **dev_ptr, size_t *bytes);
 

@@ -558,6 +558,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
             const size_t nprod = (size_t)P->Np * 2 * P->C * ra.Lp;
             PL_CUDA(cudaMalloc(&P->d_rtE, nE * 2), "cudaMalloc");
             PL_CUDA(cudaMalloc(&P->d_rtA, nA * 2), "cudaMalloc");
+            PL_CUDA(cudaMemset(P->d_rtA, 0, nA * 2), "cudaMemset");   // frequencies >= M stay 0
             PL_CUDA(cudaMalloc(&P->d_rtprod, nprod * 4), "cudaMalloc");
             ws += nE * 2 + nA * 2 + nprod * 4;
             PL_CUDA(launch_setup_rt_E(d, P->dzs, P->d_k, P->d_kc, ra.Lp, ra.Kp, P->d_rtE, st),
@@ -586,8 +587,11 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
 
 }  // namespace
 
-pl_status pl_stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st) {
-    if (P->fwd_fft)
+static pl_status stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st, bool split) {
+    if (P->fwd_fft && split)      // straight into the tensor-core range table's operand
+        PL_CUDA(launch_fft_strided(echo, P->d_S, P->C, P->N, P->M, P->zplan, P->d_twz, -1, 1.0f,
+                                   P->Np, 0, st, P->d_alpha, P->d_rtA, P->rt.Kp), "zfft");
+    else if (P->fwd_fft)
         PL_CUDA(launch_fft_strided(echo, P->d_S, P->C, P->N, P->M, P->zplan, P->d_twz, -1, 1.0f,
                                    P->Np, 0, st), "zfft");
     else
@@ -596,10 +600,15 @@ pl_status pl_stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st) {
     return PL_OK;
 }
 
+pl_status pl_stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st) {
+    return stage_zfft(P, echo, st, P->block_config == 4 && P->rt_tc);
+}
+
 pl_status pl_stage_range_table(pl_plan *P, cudaStream_t st) {
     if (P->block_config == 4 && P->rt_tc) {
         PL_CUDA(launch_range_table_tc(P->rt, P->tmapA, P->tmapE, P->d_S, P->d_alpha, P->d_rtA,
-                                      P->d_rtprod, P->d_table, P->nd.tc_cols / 2, P->d_err, st),
+                                      P->d_rtprod, P->d_table, P->nd.tc_cols / 2, P->d_err,
+                                      P->fwd_fft, st),
                 "range_table_tc");
         return PL_OK;
     }
@@ -839,7 +848,7 @@ pl_status pl_execute_exact(pl_plan *plan, const void *echo_dev, void *image_dev,
     pl_status s = prepare_comparison(plan);
     if (s != PL_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    if ((s = pl_stage_zfft(plan, (const float2 *)echo_dev, st)) != PL_OK) return s;
+    if ((s = stage_zfft(plan, (const float2 *)echo_dev, st, false)) != PL_OK) return s;
     PL_CUDA(launch_exact_sum(plan->exact, plan->d_S, plan->d_kap, plan->d_wum, plan->d_chff,
                              plan->d_G, st),
             "exact_sum");

@@ -226,23 +226,33 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
     if (warp == 0) tc05::tmem_dealloc(tmem, 512);
 }
 
-// prod [u][plane][C][Lp] (uint32 = (re, im) BF16 pair) -> table [c][plane][L][u]
+// prod [u][plane][C][Lp] (uint32 = (re, im) BF16 pair) -> table [c][plane][L][u]:
+// 64 x 64 tiles, 16-byte global accesses on both sides (u beyond N_p written
+// as zeros so the padding columns stay zero)
 __global__ void __launch_bounds__(256)
 k_rt_transpose(const uint32_t *__restrict__ prod, uint32_t *__restrict__ table, int C, int L,
                int Lp, int Np, int row_words) {
-    __shared__ uint32_t t[32][33];
-    const int i0 = blockIdx.x * 32, u0 = blockIdx.y * 32;
+    __shared__ uint32_t s[64][65];
+    const int i0 = blockIdx.x * 64, u0 = blockIdx.y * 64;
     const int cp = blockIdx.z;                 // c * 2 + plane
     const int c = cp >> 1, p = cp & 1;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
-    for (int k = ty; k < 32; k += 8) {
-        const int u = u0 + k, i = i0 + tx;
-        if (u < Np && i < L) t[k][tx] = prod[((size_t)(2 * u + p) * C + c) * Lp + i];
+    const int q = threadIdx.x & 15, r0 = threadIdx.x >> 4;   // 16 x 16
+    for (int k = r0; k < 64; k += 16) {
+        const int u = u0 + k, i = i0 + 4 * q;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (u < Np && i < Lp)
+            v = *reinterpret_cast<const uint4 *>(prod + ((size_t)(2 * u + p) * C + c) * Lp + i);
+        s[k][4 * q + 0] = v.x;
+        s[k][4 * q + 1] = v.y;
+        s[k][4 * q + 2] = v.z;
+        s[k][4 * q + 3] = v.w;
     }
     __syncthreads();
-    for (int k = ty; k < 32; k += 8) {
-        const int i = i0 + k, u = u0 + tx;
-        if (u < Np && i < L) table[((size_t)cp * L + i) * row_words + u] = t[tx][k];
+    for (int k = r0; k < 64; k += 16) {
+        const int i = i0 + k, u = u0 + 4 * q;
+        if (i >= L || u >= row_words) continue;
+        const uint4 v = make_uint4(s[4 * q][k], s[4 * q + 1][k], s[4 * q + 2][k], s[4 * q + 3][k]);
+        *reinterpret_cast<uint4 *>(table + ((size_t)cp * L + i) * row_words + u) = v;
     }
 }
 
@@ -265,12 +275,15 @@ cudaError_t launch_setup_rt_E(const NufftDesc &d, double dz, const double *k, co
 cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
                                   const CUtensorMap &tmB, const float2 *S, const float2 *alpha,
                                   void *A, void *prod, void *table, int row_words, int *err,
-                                  cudaStream_t st) {
-    const long long n = (long long)ra.C * ra.Np * ra.Kp;
-    k_rt_prep<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S, alpha, ra.C, ra.Np, ra.M, ra.Kp,
-                                                           (__nv_bfloat16 *)A);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+                                  bool prepared, cudaStream_t st) {
+    cudaError_t e;
+    if (!prepared) {     // the z transform wrote S, not the split operand
+        const long long n = (long long)ra.C * ra.Np * ra.Kp;
+        k_rt_prep<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S, alpha, ra.C, ra.Np, ra.M,
+                                                               ra.Kp, (__nv_bfloat16 *)A);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     const size_t smem = range_table_tc_smem_bytes(ra);
     e = cudaFuncSetAttribute(k_range_table_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
@@ -279,7 +292,7 @@ cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
     k_range_table_tc<<<grid, 128, smem, st>>>(ra, tmA, tmB, (uint32_t *)prod, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    dim3 tg((ra.L + 31) / 32, (ra.Np + 31) / 32, 2 * ra.C);
+    dim3 tg((ra.L + 63) / 64, (row_words + 63) / 64, 2 * ra.C);
     k_rt_transpose<<<tg, 256, 0, st>>>((const uint32_t *)prod, (uint32_t *)table, ra.C, ra.L,
                                        ra.Lp, ra.Np, row_words);
     return cudaGetLastError();

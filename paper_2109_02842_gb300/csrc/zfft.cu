@@ -8,6 +8,8 @@
 // and writes the requested output rows. Lengths with another prime factor,
 // and inverse transforms onto voxel heights off the scan grid, use the
 // tiled direct DFT kernel below with a precomputed phase matrix.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "stockham.cuh"
@@ -17,11 +19,18 @@ namespace {
 constexpr int kFftIB = 16;   // columns per block (128-byte rows)
 
 // in:  [batch][n_in][I]  (rows n >= n_in are zero padding)
-// out: [batch][out_rows][I], out row r = transform index (r + out_off) mod N
+// out: [batch][out_rows][I], out row r = transform index (r + out_off) mod N;
+// or, with sp.A set, the tensor-core range table's operand instead:
+// A[r][re hi, re lo, im hi, im lo][batch][Kp] = split(X[r][i] alpha[r][i]) (BF16)
+struct SplitOut {
+    const float2 *alpha;     // [out_rows][I]
+    __nv_bfloat16 *A;        // nullptr: plain output
+    int batch, Kp;
+};
 __global__ void __launch_bounds__(256)
 k_fft_strided(const float2 *__restrict__ in, float2 *__restrict__ out, int n_in, int I,
               FftPlan plan, const float2 *__restrict__ tw_g, int sgn, float scale,
-              int out_rows, int out_off) {
+              int out_rows, int out_off, SplitOut sp) {
     extern __shared__ float2 smem[];
     const int N = plan.n;
     float2 *buf0 = smem;
@@ -48,7 +57,19 @@ k_fft_strided(const float2 *__restrict__ in, float2 *__restrict__ out, int n_in,
         if (i0 + col >= I) continue;
         int sr = r + out_off;
         sr %= N;
-        out[(b * out_rows + r) * (size_t)I + i0 + col] = cscale(src[sr * kFftIB + col], scale);
+        const float2 v = cscale(src[sr * kFftIB + col], scale);
+        if (sp.A) {
+            const float2 a = cmul(v, sp.alpha[(size_t)r * I + i0 + col]);
+            const size_t plane = (size_t)sp.batch * sp.Kp;
+            const size_t o = (size_t)r * 4 * plane + b * sp.Kp + i0 + col;
+            const __nv_bfloat16 rh = __float2bfloat16(a.x), ih = __float2bfloat16(a.y);
+            sp.A[o] = rh;
+            sp.A[o + plane] = __float2bfloat16(a.x - __bfloat162float(rh));
+            sp.A[o + 2 * plane] = ih;
+            sp.A[o + 3 * plane] = __float2bfloat16(a.y - __bfloat162float(ih));
+        } else {
+            out[(b * out_rows + r) * (size_t)I + i0 + col] = v;
+        }
     }
 }
 
@@ -105,14 +126,16 @@ size_t fft_strided_smem_bytes(int n) { return (size_t)(2 * n * kFftIB + n) * siz
 
 cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_in, int I,
                                const FftPlan &plan, const float2 *tw, int sgn, float scale,
-                               int out_rows, int out_off, cudaStream_t st) {
+                               int out_rows, int out_off, cudaStream_t st,
+                               const float2 *split_alpha, void *split_A, int split_Kp) {
     const size_t smem = fft_strided_smem_bytes(plan.n);
     cudaError_t e = cudaFuncSetAttribute(k_fft_strided, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((I + kFftIB - 1) / kFftIB, batch);
+    const SplitOut sp{split_alpha, (__nv_bfloat16 *)split_A, batch, split_Kp};
     k_fft_strided<<<grid, 256, smem, st>>>(in, out, n_in, I, plan, tw, sgn, scale, out_rows,
-                                           out_off);
+                                           out_off, sp);
     return cudaGetLastError();
 }
 
