@@ -39,14 +39,23 @@ k_fft_strided(const float2 *__restrict__ in, float2 *__restrict__ out, int n_in,
     const int i0 = blockIdx.x * kFftIB;
     const size_t b = blockIdx.y;
 
+    // the whole panel in flight at once: asynchronous 8-byte copies, zeros
+    // for the padding rows and the columns past I
     for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
     for (int idx = threadIdx.x; idx < N * kFftIB; idx += blockDim.x) {
         const int n = idx / kFftIB;
         const int col = idx - n * kFftIB;
-        float2 v = make_float2(0.f, 0.f);
-        if (n < n_in && i0 + col < I) v = in[(b * n_in + n) * (size_t)I + i0 + col];
-        buf0[idx] = v;
+        if (n < n_in && i0 + col < I) {
+            const float2 *src = in + (b * n_in + n) * (size_t)I + i0 + col;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(
+                             (unsigned)__cvta_generic_to_shared(buf0 + idx)),
+                         "l"(src)
+                         : "memory");
+        } else {
+            buf0[idx] = make_float2(0.f, 0.f);
+        }
     }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
 
     const float2 *src = stockham_run<true, kFftIB>(buf0, buf1, tw, plan, sgn, 1, kFftIB);
