@@ -175,6 +175,18 @@ pl_status pl_execute(pl_plan *plan, const void *echo_dev, void *image_dev, void 
 pl_status pl_execute_host(pl_plan *plan, const void *echo_host, void *image_host,
                           void *stream);
 
+/* A sequence of scans from HOST buffers, pipelined: echo_host[i] (complex64
+ * [n_chan][n_scan][n_f]) -> image_host[i] (complex64 [nz][ny][nx]) for
+ * i < n_scans, with the upload of scan i+1 and the download of scan i-1 on the
+ * copy engines (two internal streams) while scan i is reconstructed on
+ * `stream`. Each image is the one pl_execute gives for its echo. The first
+ * call allocates a second pair of device staging buffers (workspace grows by
+ * the echo and image sizes). Synchronises `stream` before returning; the host
+ * buffers should be pinned (pageable memory gives correct results without the
+ * overlap). n_scans = 0 is a no-op; a NULL array or entry is PL_ERR_ARG. */
+pl_status pl_execute_host_stream(pl_plan *plan, int n_scans, const void *const *echo_host,
+                                 void *const *image_host, void *stream);
+
 /* Sampling and resolution design figures of Sec. II-C/D for an array, scan
  * and band (host computation, no device work):
  *   max_rx_spacing   = lambda_min sqrt((L_R + D)^2/4 + R_0^2) / (L_R + D), the

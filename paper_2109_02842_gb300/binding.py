@@ -67,7 +67,8 @@ class PlBatchInfo(ctypes.Structure):
                 ("updates_per_execute", _D), ("workspace_bytes", ctypes.c_size_t)]
 
 
-EXPORTED = ("pl_plan_create", "pl_execute", "pl_execute_host", "pl_execute_exact",
+EXPORTED = ("pl_plan_create", "pl_execute", "pl_execute_host", "pl_execute_host_stream",
+            "pl_execute_exact",
             "pl_execute_bp_direct", "pl_design", "pl_plan_destroy",
             "pl_plan_get_info", "pl_plan_workspace", "pl_plan_set_timing",
             "pl_plan_stage_times", "pl_synth_echo", "pl_synth_echo_static",
@@ -108,6 +109,7 @@ def load(path: str = LIB_PATH):
                                    ctypes.POINTER(PlGrid), ctypes.POINTER(PlOptions)]
     lib.pl_execute.argtypes = [_P, _P, _P, _P]
     lib.pl_execute_host.argtypes = [_P, _P, _P, _P]
+    lib.pl_execute_host_stream.argtypes = [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _P]
     lib.pl_execute_exact.argtypes = [_P, _P, _P, _P]
     lib.pl_execute_bp_direct.argtypes = [_P, _P, _P, _P]
     lib.pl_plan_destroy.argtypes = [_P]
@@ -128,7 +130,8 @@ def load(path: str = LIB_PATH):
     lib.pl_status_string.argtypes = [_I]
     lib.pl_last_error.restype = ctypes.c_char_p
     lib.pl_version.restype = _I
-    for name in ("pl_plan_create", "pl_execute", "pl_execute_host", "pl_plan_destroy",
+    for name in ("pl_plan_create", "pl_execute", "pl_execute_host", "pl_execute_host_stream",
+                 "pl_plan_destroy",
                  "pl_plan_get_info", "pl_plan_workspace", "pl_plan_set_timing",
                  "pl_plan_stage_times", "pl_synth_echo", "pl_synth_echo_static",
                  "pl_batch_create", "pl_execute_batch", "pl_batch_get_info", "pl_batch_destroy"):
@@ -270,6 +273,28 @@ class Plan:
             iptr = image.ctypes.data
         _check(load().pl_execute_host(self._h, _P(eptr), _P(iptr), _stream_handle(stream)))
         return image
+
+    def execute_host_stream(self, echoes, images=None, stream=None):
+        """A sequence of scans from host buffers with the copies overlapped
+        with the reconstruction; returns the list of host images."""
+        import torch
+        n = len(echoes)
+        if images is None:
+            images = [np.empty(self.image_shape, dtype=np.complex64) for _ in range(n)]
+        assert len(images) == n
+
+        def ptr(a, shape):
+            if isinstance(a, torch.Tensor):
+                assert not a.is_cuda and a.dtype == torch.complex64 and a.is_contiguous()
+                assert tuple(a.shape) == shape
+                return a.data_ptr()
+            assert a.dtype == np.complex64 and a.flags.c_contiguous and a.shape == shape
+            return a.ctypes.data
+
+        ep = (_P * max(n, 1))(*[ptr(e, self.echo_shape) for e in echoes])
+        ip = (_P * max(n, 1))(*[ptr(i, self.image_shape) for i in images])
+        _check(load().pl_execute_host_stream(self._h, n, ep, ip, _stream_handle(stream)))
+        return images
 
     def execute_exact(self, echo, image=None, stream=None):
         """The exact-sum hybrid ("omega-K-BP", Sec. III): same buffers as execute."""

@@ -888,6 +888,67 @@ pl_status pl_execute_host(pl_plan *plan, const void *echo_host, void *image_host
     return take_device_timeout(plan);
 }
 
+pl_status pl_execute_host_stream(pl_plan *plan, int n_scans, const void *const *echo_host,
+                                 void *const *image_host, void *stream) {
+    if (!plan || n_scans < 0 || (n_scans > 0 && (!echo_host || !image_host)))
+        return fail(PL_ERR_ARG, "bad pl_execute_host_stream arguments");
+    for (int i = 0; i < n_scans; ++i)
+        if (!echo_host[i] || !image_host[i]) return fail(PL_ERR_ARG, "NULL scan buffer");
+    if (take_device_timeout(plan) != PL_OK) return PL_ERR_TIMEOUT;
+    if (n_scans == 0) return PL_OK;
+    const size_t in_bytes = (size_t)plan->C * plan->N * plan->M * sizeof(float2);
+    const size_t out_bytes =
+        (size_t)plan->grid.nx * plan->grid.ny * plan->grid.nz * sizeof(float2);
+    if (!plan->d_echo_in) {
+        PL_CUDA(cudaMalloc(&plan->d_echo_in, in_bytes), "cudaMalloc");
+        PL_CUDA(cudaMalloc(&plan->d_img_out, out_bytes), "cudaMalloc");
+        plan->workspace += in_bytes + out_bytes;
+    }
+    if (!plan->d_echo_in2) {
+        PL_CUDA(cudaMalloc(&plan->d_echo_in2, in_bytes), "cudaMalloc");
+        PL_CUDA(cudaMalloc(&plan->d_img_out2, out_bytes), "cudaMalloc");
+        plan->workspace += in_bytes + out_bytes;
+        PL_CUDA(cudaStreamCreateWithFlags(&plan->s_h2d, cudaStreamNonBlocking), "stream");
+        PL_CUDA(cudaStreamCreateWithFlags(&plan->s_d2h, cudaStreamNonBlocking), "stream");
+        for (int b = 0; b < 2; ++b) {
+            PL_CUDA(cudaEventCreateWithFlags(&plan->ev_in[b], cudaEventDisableTiming), "event");
+            PL_CUDA(cudaEventCreateWithFlags(&plan->ev_done[b], cudaEventDisableTiming), "event");
+            PL_CUDA(cudaEventCreateWithFlags(&plan->ev_out[b], cudaEventDisableTiming), "event");
+        }
+        PL_CUDA(cudaEventCreateWithFlags(&plan->ev_start, cudaEventDisableTiming), "event");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    float2 *din[2] = {plan->d_echo_in, plan->d_echo_in2};
+    float2 *dout[2] = {plan->d_img_out, plan->d_img_out2};
+    // the copies start after the caller's earlier work on `stream`
+    PL_CUDA(cudaEventRecord(plan->ev_start, st), "event");
+    PL_CUDA(cudaStreamWaitEvent(plan->s_h2d, plan->ev_start, 0), "wait");
+    PL_CUDA(cudaStreamWaitEvent(plan->s_d2h, plan->ev_start, 0), "wait");
+    // two-deep pipeline: the upload of scan i+1 and the download of scan i-1
+    // run on the copy engines while scan i is reconstructed on `stream`
+    for (int i = 0; i < n_scans; ++i) {
+        const int b = i & 1;
+        if (i >= 2) PL_CUDA(cudaStreamWaitEvent(plan->s_h2d, plan->ev_done[b], 0), "wait");
+        PL_CUDA(cudaMemcpyAsync(din[b], echo_host[i], in_bytes, cudaMemcpyHostToDevice,
+                                plan->s_h2d),
+                "copy echo");
+        PL_CUDA(cudaEventRecord(plan->ev_in[b], plan->s_h2d), "event");
+        PL_CUDA(cudaStreamWaitEvent(st, plan->ev_in[b], 0), "wait");
+        if (i >= 2) PL_CUDA(cudaStreamWaitEvent(st, plan->ev_out[b], 0), "wait");
+        pl_status s = run(plan, din[b], dout[b], st);
+        if (s != PL_OK) return s;
+        PL_CUDA(cudaEventRecord(plan->ev_done[b], st), "event");
+        PL_CUDA(cudaStreamWaitEvent(plan->s_d2h, plan->ev_done[b], 0), "wait");
+        PL_CUDA(cudaMemcpyAsync(image_host[i], dout[b], out_bytes, cudaMemcpyDeviceToHost,
+                                plan->s_d2h),
+                "copy image");
+        PL_CUDA(cudaEventRecord(plan->ev_out[b], plan->s_d2h), "event");
+    }
+    PL_CUDA(cudaStreamWaitEvent(st, plan->ev_out[(n_scans - 1) & 1], 0), "wait");
+    PL_CUDA(cudaStreamSynchronize(st), "execute_host_stream");
+    return take_device_timeout(plan);
+}
+
 pl_status pl_plan_get_info(const pl_plan *P, pl_info *info) {
     if (!P || !info) return fail(PL_ERR_ARG, "NULL argument");
     pl_info i{};

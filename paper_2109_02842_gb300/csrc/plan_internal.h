@@ -51,6 +51,11 @@ struct pl_plan {
     void *d_table = nullptr;
     size_t table_bytes = 0;
     float2 *d_echo_in = nullptr, *d_img_out = nullptr;   // pl_execute_host staging
+    // pl_execute_host_stream: a second staging pair, the copy streams and the
+    // events that order them against the reconstruction
+    float2 *d_echo_in2 = nullptr, *d_img_out2 = nullptr;
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t ev_in[2]{}, ev_done[2]{}, ev_out[2]{}, ev_start = nullptr;
     // comparison algorithms (exact sum, direct BP), set up on first use
     std::vector<double> h_chxy, h_k;                      // [C][4] positions, [M] k
     float2 *d_kap = nullptr, *d_zs = nullptr, *d_kff = nullptr;
@@ -71,9 +76,14 @@ struct pl_plan {
         void *ptrs[] = {d_chxy, d_k,    d_kc,   d_kspan, d_glx,  d_glw,     d_kchl, d_tgeo,
                         d_xg,   d_dec,  d_alpha, d_twz,  d_twfine, d_Tfwd, d_Tinv,
                         d_S,    d_G,    d_table, d_echo_in, d_img_out, d_kap, d_zs,
-                        d_kff,  d_wum,  d_chff, d_rtE, d_rtA, d_rtprod};
+                        d_kff,  d_wum,  d_chff, d_rtE, d_rtA, d_rtprod, d_echo_in2, d_img_out2};
         for (void *p : ptrs)
             if (p) cudaFree(p);
+        for (cudaEvent_t e : {ev_in[0], ev_in[1], ev_done[0], ev_done[1], ev_out[0], ev_out[1],
+                              ev_start})
+            if (e) cudaEventDestroy(e);
+        if (s_h2d) cudaStreamDestroy(s_h2d);
+        if (s_d2h) cudaStreamDestroy(s_d2h);
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         if (h_err) cudaFreeHost(h_err);
     }

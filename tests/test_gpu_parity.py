@@ -173,6 +173,26 @@ def test_execute_host_matches_device(binding):
     assert np.array_equal(img_h, img)
 
 
+def test_execute_host_stream_matches_device(binding):
+    # five different scans through the pipelined host path (two staging pairs,
+    # so buffers are reused twice) against one pl_execute each
+    import ctypes
+    w = wl.small_mono(seed=7)
+    plan = binding.Plan.from_workload(w)
+    echoes = [torch.from_numpy(scene_echo(w, 70 + i)).pin_memory() for i in range(5)]
+    want = [plan.execute(e.cuda()).cpu().numpy() for e in echoes]
+    images = [torch.empty(plan.image_shape, dtype=torch.complex64).pin_memory()
+              for _ in range(5)]
+    plan.execute_host_stream(echoes, images)
+    for a, b in zip(images, want):
+        assert np.array_equal(a.numpy(), b)
+    assert plan.execute_host_stream([]) == []
+    lib = binding.load()
+    null = (ctypes.c_void_p * 1)(None)
+    assert lib.pl_execute_host_stream(plan._h, 1, null, null, None) == 1   # PL_ERR_ARG
+    assert lib.pl_execute_host_stream(plan._h, -1, None, None, None) == 1
+
+
 def test_stage_timing(binding):
     w = wl.small_mono(seed=0)
     plan = binding.Plan.from_workload(w)
