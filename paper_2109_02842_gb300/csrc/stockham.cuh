@@ -80,11 +80,15 @@ __device__ __forceinline__ void stockham_stage(const float2 *src, float2 *dst, c
     const int nr = N / R;
     const int items = nr * NCOL;
     const int tw_step = N / (Ns * R);
+    // j / Ns as floor((j + 1/2) / Ns) in float: exact for j < 2^20 (the
+    // fraction stays at least 1/(2 Ns) away from an integer), and three
+    // instructions instead of an integer division
+    const float inv_ns = 1.0f / (float)Ns;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
         int j, col;
         if (COL_FAST) { j = it / NCOL; col = it - j * NCOL; }
         else { col = it / nr; j = it - col * nr; }
-        const int jh = j / Ns;
+        const int jh = __float2int_rz(((float)j + 0.5f) * inv_ns);
         const int k = j - jh * Ns;
         const float2 *s = src + col * cs;
         float2 v[5];
