@@ -127,3 +127,65 @@ __device__ __forceinline__ float2 *stockham_run(float2 *buf0, float2 *buf1, cons
     }
     return src;
 }
+
+// The same stage on column pairs: NCOL (even) columns stored at n * NCOL +
+// col, one thread item = two adjacent columns as a float4, so the index
+// arithmetic, the twiddle loads and the shared-memory accesses are shared by
+// both columns.
+template <int R, int NCOL>
+__device__ __forceinline__ void stockham_stage_pairs(const float2 *src, float2 *dst,
+                                                     const float2 *tw, int N, int Ns, int sgn) {
+    constexpr int NP = NCOL / 2;
+    const int nr = N / R;
+    const int items = nr * NP;
+    const int tw_step = N / (Ns * R);
+    const float inv_ns = 1.0f / (float)Ns;
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int j = it / NP;
+        const int cp = it - j * NP;
+        const int jh = __float2int_rz(((float)j + 0.5f) * inv_ns);
+        const int k = j - jh * Ns;
+        float2 a[5], b[5];
+        float4 x = s4[j * NP + cp];
+        a[0] = make_float2(x.x, x.y);
+        b[0] = make_float2(x.z, x.w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            float2 w = tw[k * r * tw_step];
+            if (sgn > 0) w.y = -w.y;
+            x = s4[(j + r * nr) * NP + cp];
+            a[r] = cmul(make_float2(x.x, x.y), w);
+            b[r] = cmul(make_float2(x.z, x.w), w);
+        }
+        stockham_detail::small_dft<R>(a, sgn);
+        stockham_detail::small_dft<R>(b, sgn);
+        const int base = jh * Ns * R + k;
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+            d4[(base + q * Ns) * NP + cp] = make_float4(a[q].x, a[q].y, b[q].x, b[q].y);
+    }
+}
+
+// Every stage of `plan` on NCOL columns (column pairs); returns the buffer
+// holding the result. Both buffers 16-byte aligned. Ends with a
+// __syncthreads().
+template <int NCOL>
+__device__ __forceinline__ float2 *stockham_run_pairs(float2 *buf0, float2 *buf1, const float2 *tw,
+                                                      const FftPlan &plan, int sgn) {
+    float2 *src = buf0, *dst = buf1;
+    int Ns = 1;
+    const int N = plan.n;
+    for (int s = 0; s < plan.n_stages; ++s) {
+        const int R = plan.radix[s];
+        if (R == 4) stockham_stage_pairs<4, NCOL>(src, dst, tw, N, Ns, sgn);
+        else if (R == 2) stockham_stage_pairs<2, NCOL>(src, dst, tw, N, Ns, sgn);
+        else if (R == 3) stockham_stage_pairs<3, NCOL>(src, dst, tw, N, Ns, sgn);
+        else stockham_stage_pairs<5, NCOL>(src, dst, tw, N, Ns, sgn);
+        __syncthreads();
+        float2 *t = src; src = dst; dst = t;
+        Ns *= R;
+    }
+    return src;
+}

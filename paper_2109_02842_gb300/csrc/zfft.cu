@@ -27,57 +27,95 @@ struct SplitOut {
     __nv_bfloat16 *A;        // nullptr: plain output
     int batch, Kp;
 };
+// PAIRS (I even): every access moves two adjacent columns (16-byte copies,
+// float4 shared-memory accesses, column pairs through the FFT stages).
+template <bool PAIRS>
 __global__ void __launch_bounds__(256)
 k_fft_strided(const float2 *__restrict__ in, float2 *__restrict__ out, int n_in, int I,
               FftPlan plan, const float2 *__restrict__ tw_g, int sgn, float scale,
               int out_rows, int out_off, SplitOut sp) {
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) float2 smem[];
     const int N = plan.n;
     float2 *buf0 = smem;
     float2 *buf1 = smem + N * kFftIB;
     float2 *tw = smem + 2 * N * kFftIB;
     const int i0 = blockIdx.x * kFftIB;
     const size_t b = blockIdx.y;
+    constexpr int CW = PAIRS ? 2 : 1;          // columns per access
+    constexpr int NG = kFftIB / CW;            // accesses per row
 
-    // the whole panel in flight at once: asynchronous 8-byte copies, zeros
-    // for the padding rows and the columns past I
+    // the whole panel in flight at once: asynchronous copies, zeros for the
+    // padding rows and the columns past I
     for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
-    for (int idx = threadIdx.x; idx < N * kFftIB; idx += blockDim.x) {
-        const int n = idx / kFftIB;
-        const int col = idx - n * kFftIB;
+    for (int idx = threadIdx.x; idx < N * NG; idx += blockDim.x) {
+        const int n = idx / NG;
+        const int col = (idx - n * NG) * CW;
+        float2 *dst = buf0 + n * kFftIB + col;
         if (n < n_in && i0 + col < I) {
             const float2 *src = in + (b * n_in + n) * (size_t)I + i0 + col;
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(
-                             (unsigned)__cvta_generic_to_shared(buf0 + idx)),
-                         "l"(src)
-                         : "memory");
+            if (PAIRS)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(
+                                 (unsigned)__cvta_generic_to_shared(dst)),
+                             "l"(src)
+                             : "memory");
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(
+                                 (unsigned)__cvta_generic_to_shared(dst)),
+                             "l"(src)
+                             : "memory");
+        } else if (PAIRS) {
+            *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
         } else {
-            buf0[idx] = make_float2(0.f, 0.f);
+            *dst = make_float2(0.f, 0.f);
         }
     }
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
 
-    const float2 *src = stockham_run<true, kFftIB>(buf0, buf1, tw, plan, sgn, 1, kFftIB);
+    const float2 *src = PAIRS ? stockham_run_pairs<kFftIB>(buf0, buf1, tw, plan, sgn)
+                              : stockham_run<true, kFftIB>(buf0, buf1, tw, plan, sgn, 1, kFftIB);
 
-    for (int idx = threadIdx.x; idx < out_rows * kFftIB; idx += blockDim.x) {
-        const int r = idx / kFftIB;
-        const int col = idx - r * kFftIB;
+    // out_off < N and r < out_rows <= N: one conditional subtraction wraps
+    for (int idx = threadIdx.x; idx < out_rows * NG; idx += blockDim.x) {
+        const int r = idx / NG;
+        const int col = (idx - r * NG) * CW;
         if (i0 + col >= I) continue;
         int sr = r + out_off;
-        sr %= N;
-        const float2 v = cscale(src[sr * kFftIB + col], scale);
+        if (sr >= N) sr -= N;
+        float2 v[CW];
+        if (PAIRS) {
+            const float4 x = *reinterpret_cast<const float4 *>(src + sr * kFftIB + col);
+            v[0] = cscale(make_float2(x.x, x.y), scale);
+            v[CW - 1] = cscale(make_float2(x.z, x.w), scale);
+        } else {
+            v[0] = cscale(src[sr * kFftIB + col], scale);
+        }
         if (sp.A) {
-            const float2 a = cmul(v, sp.alpha[(size_t)r * I + i0 + col]);
             const size_t plane = (size_t)sp.batch * sp.Kp;
             const size_t o = (size_t)r * 4 * plane + b * sp.Kp + i0 + col;
-            const __nv_bfloat16 rh = __float2bfloat16(a.x), ih = __float2bfloat16(a.y);
-            sp.A[o] = rh;
-            sp.A[o + plane] = __float2bfloat16(a.x - __bfloat162float(rh));
-            sp.A[o + 2 * plane] = ih;
-            sp.A[o + 3 * plane] = __float2bfloat16(a.y - __bfloat162float(ih));
+            const float2 *al = sp.alpha + (size_t)r * I + i0 + col;
+            __nv_bfloat16 h[4][CW];
+#pragma unroll
+            for (int e = 0; e < CW; ++e) {
+                const float2 a = cmul(v[e], al[e]);
+                h[0][e] = __float2bfloat16(a.x);
+                h[1][e] = __float2bfloat16(a.x - __bfloat162float(h[0][e]));
+                h[2][e] = __float2bfloat16(a.y);
+                h[3][e] = __float2bfloat16(a.y - __bfloat162float(h[2][e]));
+            }
+#pragma unroll
+            for (int pl = 0; pl < 4; ++pl) {
+                if (PAIRS)
+                    *reinterpret_cast<__nv_bfloat162 *>(sp.A + o + pl * plane) =
+                        __halves2bfloat162(h[pl][0], h[pl][CW - 1]);
+                else
+                    sp.A[o + pl * plane] = h[pl][0];
+            }
+        } else if (PAIRS) {
+            *reinterpret_cast<float4 *>(out + (b * out_rows + r) * (size_t)I + i0 + col) =
+                make_float4(v[0].x, v[0].y, v[CW - 1].x, v[CW - 1].y);
         } else {
-            out[(b * out_rows + r) * (size_t)I + i0 + col] = v;
+            out[(b * out_rows + r) * (size_t)I + i0 + col] = v[0];
         }
     }
 }
@@ -138,13 +176,19 @@ cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_i
                                int out_rows, int out_off, cudaStream_t st,
                                const float2 *split_alpha, void *split_A, int split_Kp) {
     const size_t smem = fft_strided_smem_bytes(plan.n);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_strided, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // column pairs need 16-byte aligned rows: I even, 16-byte aligned
+    // buffers, and (split output) an even operand row length
+    const bool pairs = (I % 2 == 0) && ((uintptr_t)in % 16 == 0) &&
+                       (split_A ? (split_Kp % 2 == 0 && (uintptr_t)split_A % 4 == 0 &&
+                                   (uintptr_t)split_alpha % 16 == 0)
+                                : (uintptr_t)out % 16 == 0);
+    auto kern = pairs ? k_fft_strided<true> : k_fft_strided<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((I + kFftIB - 1) / kFftIB, batch);
     const SplitOut sp{split_alpha, (__nv_bfloat16 *)split_A, batch, split_Kp};
-    k_fft_strided<<<grid, 256, smem, st>>>(in, out, n_in, I, plan, tw, sgn, scale, out_rows,
-                                           out_off, sp);
+    kern<<<grid, 256, smem, st>>>(in, out, n_in, I, plan, tw, sgn, scale, out_rows, out_off, sp);
     return cudaGetLastError();
 }
 
