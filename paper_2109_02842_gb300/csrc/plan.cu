@@ -133,12 +133,15 @@ void es_tap_polynomial(int W, double beta, int t, int D, float *mono) {
     }
 }
 
-bool smooth_plan(int n, FftPlan &p) {
+// Radix sequence of a 2^a 3^b 5^c length. Radix 8 (fewer passes) pays off
+// in the column-pair z transforms; the fine-grid transform of the range table
+// keeps radices up to 5.
+bool smooth_plan(int n, FftPlan &p, bool radix8) {
     p.n = n;
     p.n_stages = 0;
     int r = n;
-    const int order[4] = {4, 2, 3, 5};
-    for (int oi = 0; oi < 4; ++oi) {
+    const int order[5] = {8, 4, 2, 3, 5};
+    for (int oi = radix8 ? 0 : 1; oi < 5; ++oi) {
         while (r % order[oi] == 0) {
             if (p.n_stages == 16) return false;
             p.radix[p.n_stages++] = order[oi];
@@ -473,10 +476,10 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
                                  P->d_xg, P->d_alpha, st), "setup_sources");
     PL_CUDA(launch_setup_deconv(d, P->d_glx, P->d_glw, P->n_gl, P->d_dec, st), "setup_deconv");
     PL_CUDA(launch_twiddles(fine, fine, -1, P->d_twfine, st), "twiddles");
-    if (!smooth_plan(fine, P->fineplan)) return fail(PL_ERR_UNSUPPORTED, "fine grid length");
+    if (!smooth_plan(fine, P->fineplan, false)) return fail(PL_ERR_UNSUPPORTED, "fine grid length");
 
     // transforms over z
-    const bool smooth = smooth_plan(P->Np, P->zplan) && P->Np <= 512;
+    const bool smooth = smooth_plan(P->Np, P->zplan, true) && P->Np <= 512;
     P->fwd_fft = smooth;
     if (smooth) {
         PL_CUDA(dalloc(&P->d_twz, (size_t)P->Np, ws), "cudaMalloc");

@@ -1,11 +1,11 @@
-// Mixed-radix (2, 3, 4, 5) Stockham autosort FFT stage on a batch of columns
+// Mixed-radix (2, 3, 4, 5, 8) Stockham autosort FFT stage on a batch of columns
 // in shared memory. Element (column col, index n) lives at col*cs + n*ns.
 // One stage of radix R with Ns = product of the previous radices:
 //   v_r = src[j + r N/R] * W_N^{(j mod Ns) r N/(Ns R)},  r < R
 //   dst[(j/Ns) Ns R + (j mod Ns) + q Ns] = sum_r v_r W_R^{r q},  q < R
 // for j < N/R. After all stages the data are in natural order. tw holds
 // exp(-2 pi i k / N), k < N; sgn = +1 conjugates it (inverse transform).
-// The small DFTs W_R use the exact values of the R-th roots of unity (R <= 5),
+// The small DFTs W_R use the exact values of the R-th roots of unity,
 // and the twiddle index (j mod Ns) r N/(Ns R) is below N (no reduction).
 #pragma once
 
@@ -15,17 +15,17 @@ namespace stockham_detail {
 
 // v <- DFT_R(v) with exponent sign -1 (sgn < 0) or +1 (sgn > 0)
 template <int R>
-__device__ __forceinline__ void small_dft(float2 (&v)[5], int sgn);
+__device__ __forceinline__ void small_dft(float2 (&v)[8], int sgn);
 
 template <>
-__device__ __forceinline__ void small_dft<2>(float2 (&v)[5], int) {
+__device__ __forceinline__ void small_dft<2>(float2 (&v)[8], int) {
     const float2 a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
 }
 
 template <>
-__device__ __forceinline__ void small_dft<4>(float2 (&v)[5], int sgn) {
+__device__ __forceinline__ void small_dft<4>(float2 (&v)[8], int sgn) {
     // W_4 = -i (forward) / +i (inverse)
     const float2 s0 = cadd(v[0], v[2]), d0 = csub(v[0], v[2]);
     const float2 s1 = cadd(v[1], v[3]), d1 = csub(v[1], v[3]);
@@ -38,7 +38,7 @@ __device__ __forceinline__ void small_dft<4>(float2 (&v)[5], int sgn) {
 }
 
 template <>
-__device__ __forceinline__ void small_dft<3>(float2 (&v)[5], int sgn) {
+__device__ __forceinline__ void small_dft<3>(float2 (&v)[8], int sgn) {
     // W_3 = -1/2 -+ i sqrt(3)/2
     const float c = -0.5f, s = (sgn < 0 ? -1.f : 1.f) * 0.866025403784438647f;
     const float2 t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
@@ -50,7 +50,7 @@ __device__ __forceinline__ void small_dft<3>(float2 (&v)[5], int sgn) {
 }
 
 template <>
-__device__ __forceinline__ void small_dft<5>(float2 (&v)[5], int sgn) {
+__device__ __forceinline__ void small_dft<5>(float2 (&v)[8], int sgn) {
     // cos / sin of 2 pi / 5 and 4 pi / 5
     const float c1 = 0.309016994374947424f, c2 = -0.809016994374947424f;
     const float sg = sgn < 0 ? -1.f : 1.f;
@@ -68,6 +68,27 @@ __device__ __forceinline__ void small_dft<5>(float2 (&v)[5], int sgn) {
     v[4] = csub(a1, b1);
     v[2] = cadd(a2, b2);
     v[3] = csub(a2, b2);
+}
+
+template <>
+__device__ __forceinline__ void small_dft<8>(float2 (&v)[8], int sgn) {
+    // two DFT_4 on the even and odd entries, combined with W_8^q; W_8 =
+    // (1 -+ i) / sqrt 2, W_8^2 = -+ i, W_8^3 = (-1 -+ i) / sqrt 2
+    float2 e[8] = {v[0], v[2], v[4], v[6]}, o[8] = {v[1], v[3], v[5], v[7]};
+    small_dft<4>(e, sgn);
+    small_dft<4>(o, sgn);
+    const float h = 0.707106781186547524f;
+    const float sg = sgn < 0 ? -1.f : 1.f;
+    float2 t[4];
+    t[0] = o[0];
+    t[1] = make_float2(h * (o[1].x - sg * o[1].y), h * (o[1].y + sg * o[1].x));
+    t[2] = make_float2(-sg * o[2].y, sg * o[2].x);
+    t[3] = make_float2(-h * (o[3].x + sg * o[3].y), h * (sg * o[3].x - o[3].y));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        v[q] = cadd(e[q], t[q]);
+        v[q + 4] = csub(e[q], t[q]);
+    }
 }
 
 }  // namespace stockham_detail
@@ -91,7 +112,7 @@ __device__ __forceinline__ void stockham_stage(const float2 *src, float2 *dst, c
         const int jh = __float2int_rz(((float)j + 0.5f) * inv_ns);
         const int k = j - jh * Ns;
         const float2 *s = src + col * cs;
-        float2 v[5];
+        float2 v[8];
         v[0] = s[j * ns];
 #pragma unroll
         for (int r = 1; r < R; ++r) {
@@ -117,7 +138,8 @@ __device__ __forceinline__ float2 *stockham_run(float2 *buf0, float2 *buf1, cons
     const int N = plan.n;
     for (int s = 0; s < plan.n_stages; ++s) {
         const int R = plan.radix[s];
-        if (R == 4) stockham_stage<4, COL_FAST, NCOL>(src, dst, tw, N, Ns, sgn, cs, ns);
+        if (R == 8) stockham_stage<8, COL_FAST, NCOL>(src, dst, tw, N, Ns, sgn, cs, ns);
+        else if (R == 4) stockham_stage<4, COL_FAST, NCOL>(src, dst, tw, N, Ns, sgn, cs, ns);
         else if (R == 2) stockham_stage<2, COL_FAST, NCOL>(src, dst, tw, N, Ns, sgn, cs, ns);
         else if (R == 3) stockham_stage<3, COL_FAST, NCOL>(src, dst, tw, N, Ns, sgn, cs, ns);
         else stockham_stage<5, COL_FAST, NCOL>(src, dst, tw, N, Ns, sgn, cs, ns);
@@ -147,7 +169,7 @@ __device__ __forceinline__ void stockham_stage_pairs(const float2 *src, float2 *
         const int cp = it - j * NP;
         const int jh = __float2int_rz(((float)j + 0.5f) * inv_ns);
         const int k = j - jh * Ns;
-        float2 a[5], b[5];
+        float2 a[8], b[8];
         float4 x = s4[j * NP + cp];
         a[0] = make_float2(x.x, x.y);
         b[0] = make_float2(x.z, x.w);
@@ -179,7 +201,8 @@ __device__ __forceinline__ float2 *stockham_run_pairs(float2 *buf0, float2 *buf1
     const int N = plan.n;
     for (int s = 0; s < plan.n_stages; ++s) {
         const int R = plan.radix[s];
-        if (R == 4) stockham_stage_pairs<4, NCOL>(src, dst, tw, N, Ns, sgn);
+        if (R == 8) stockham_stage_pairs<8, NCOL>(src, dst, tw, N, Ns, sgn);
+        else if (R == 4) stockham_stage_pairs<4, NCOL>(src, dst, tw, N, Ns, sgn);
         else if (R == 2) stockham_stage_pairs<2, NCOL>(src, dst, tw, N, Ns, sgn);
         else if (R == 3) stockham_stage_pairs<3, NCOL>(src, dst, tw, N, Ns, sgn);
         else stockham_stage_pairs<5, NCOL>(src, dst, tw, N, Ns, sgn);
