@@ -12,15 +12,26 @@
 // p one of the block's 128 pixels (the MMA's M), k one of the 16 KS table rows
 // of the block's window for channel c (starting at i_c, chosen at plan time
 // so that every pixel's w taps fall inside), u the block's UT k_z bins.
-// Complex products are two real ones: with B's columns (re_u, im_u),
-// P = sum Re(A) B and Q = sum Im(A) B give G = (P_re - Q_im, P_im + Q_re).
+// Complex products are real ones in one of two layouts of the table rows:
+//  * planar (PLANAR, the default when it fits): a row holds Re b of every
+//    bin, then Im b; the accumulators are Re G and Im G (UT columns each) and
+//    Re G += Re A Re B - Im A Im B, Im G += Re A Im B + Im A Re B, the minus
+//    through the instruction descriptor's negate-A bit; UT covers every bin,
+//    so a channel is one round of 4 (x3 with hi/lo) products of N = UT;
+//  * interleaved: a row holds (re_u, im_u) pairs, P = sum Re(A) B and
+//    Q = sum Im(A) B (2 UT columns each) give G = (P_re - Q_im, P_im + Q_re),
+//    and the bins go in blocks of UT.
 // Operands are BF16; for FP32-level accuracy each is split into hi + lo
 // and the product taken as hi.hi + hi.lo + lo.hi (SPLIT = 3), relative
-// error ~1e-5; SPLIT = 1 takes hi.hi only (~1e-3).
+// error ~1e-5; SPLIT = 1 takes hi.hi only (~1e-3). In the planar layout a
+// tile's channels go to two blocks (nsplit = 2) that add their sums into G
+// (zeroed first): each accumulator then sums as many products as an
+// interleaved one, and with two addends on zero the result does not depend
+// on their order.
 //
-// Block = 16 x 8 pixels x UT bins, 4 NPAR + 2 warps (NPAR = 2 with up to 48
-// bins and two blocks per SM, NPAR = 3 with up to 104 bins and one block per
-// SM: 256 or 512 TMEM columns a block):
+// Block = 16 x 8 pixels x UT bins, 4 NPAR + 2 warps (NPAR = 2 and two blocks
+// per SM when the accumulators and three A buffers fit in 256 TMEM columns,
+// NPAR = 3 and one block per SM with 512):
 //  * warps 0 .. 4 NPAR - 1 build A: warp w owns TMEM lanes 32 (w % 4) .. +31
 //    (its pixels) for the channels c = w / 4 (mod NPAR). Per channel a thread forms
 //    its pixel's range offset, the w tap weights (per-tap polynomials of the
@@ -32,12 +43,13 @@
 //    commits its completion to the barriers that free the A buffer and the
 //    table slot;
 //  * warp 4 NPAR + 1 (one thread) streams the table windows with TMA into a
-//    ring of smem slots: per channel ceil(2 UT / 64) boxes of 64 columns x
-//    16 KS rows x hi/lo from the row-major table [c][hi/lo][row][column],
+//    ring of smem slots: per channel ceil(N / 64) boxes (twice that planar:
+//    Re and Im columns) of 64 columns x 16 KS rows x hi/lo from the
+//    row-major table [c][hi/lo][row][column],
 //    written with 128-byte swizzling, which is the MN-major layout the MMA
 //    reads (64-column atoms, rows 128 B apart); a window may start at any row.
-// At the end the accumulators (P, Q: 2 x 2 UT FP32 columns) are read back
-// with tcgen05.ld and written as G[u][y][x].
+// At the end the accumulators (2 N FP32 columns) are read back with
+// tcgen05.ld and written (or, with two channel parts, added) as G[u][y][x].
 //
 // Every wait is bounded (a clock budget); a wait that runs out sets a bit in
 // *err, the block skips the rest of its work and still waits (bounded) for
@@ -82,7 +94,7 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
     lo = bf2(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xffff0000u));
 }
 
-template <int W, int KS, int SPLIT, int NPAR>
+template <int W, int KS, int SPLIT, int NPAR, bool PLANAR>
 __global__ void __launch_bounds__(Warps<NPAR>::threads, NPAR == 2 ? 2 : 1)
 k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUtensorMap tmap,
                  const TileGeo *__restrict__ tgeo, const float2 *__restrict__ kc_hl,
@@ -111,8 +123,12 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-    const int u0 = blockIdx.z * ta.UT;
+    // blockIdx.z = bin block x channel part: channels [cb, ce) of the tile
+    const int utile = blockIdx.z / ta.nsplit, part = blockIdx.z - utile * ta.nsplit;
+    const int u0 = utile * ta.UT;
     const int C = p.n_chan;
+    const int cper = (C + ta.nsplit - 1) / ta.nsplit;
+    const int cb = part * cper, ce = min(C, cb + cper);
     const TileGeo *tg = tgeo + (size_t)tile * C;
     const long long budget = ta.budget;
 
@@ -136,7 +152,7 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
     __syncthreads();
     tc05::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t N = 2 * ta.UT;
+    const uint32_t N = PLANAR ? ta.UT : 2 * ta.UT;     // the MMA's N
 
     if (warp < NCW) {
         // ------------------------------------------------ A rows (weights)
@@ -152,10 +168,10 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
         int it = 0;
         // the geometry of the class's next channel is loaded one round ahead
         TileGeo gn;
-        if (par < C) gn = tg[par];
-        for (int c = par; c < C; c += NPAR, ++it) {
+        if (cb + par < ce) gn = tg[cb + par];
+        for (int c = cb + par; c < ce; c += NPAR, ++it) {
             const TileGeo g = gn;
-            if (c + NPAR < C) gn = tg[c + NPAR];
+            if (c + NPAR < ce) gn = tg[c + NPAR];
             // delta = a - a* from rho^2 - rho*^2 = d (2 D + d): no cancellation
             float ex = g.dxt + ddx, ey = g.dyt + ddy;
             float num = fmaf(ddx, 2.0f * g.dxt + ddx, ddy * (2.0f * g.dyt + ddy));
@@ -248,13 +264,21 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
                 tc05::tmem_ld16(lane_base + N + 16 * ch, qv);
                 tc05::tmem_wait_ld();
                 if (!inside) continue;
+                // planar: 16 bins (Re G, Im G columns); interleaved: 8 bins
+                // (re, im pairs of P and Q)
+                constexpr int NB = PLANAR ? 16 : 8;
 #pragma unroll
-                for (int b = 0; b < 8; ++b) {
-                    const int u = u0 + 8 * ch + b;
-                    if (u < p.n_pad)
-                        G[u * plane + pofs] = make_float2(
-                            __uint_as_float(pv[2 * b]) - __uint_as_float(qv[2 * b + 1]),
-                            __uint_as_float(pv[2 * b + 1]) + __uint_as_float(qv[2 * b]));
+                for (int b = 0; b < NB; ++b) {
+                    const int u = u0 + NB * ch + b;
+                    if (u >= p.n_pad) continue;
+                    const float2 v =
+                        PLANAR ? make_float2(__uint_as_float(pv[b]), __uint_as_float(qv[b]))
+                               : make_float2(__uint_as_float(pv[2 * b]) - __uint_as_float(qv[2 * b + 1]),
+                                             __uint_as_float(pv[2 * b + 1]) + __uint_as_float(qv[2 * b]));
+                    if (ta.nsplit > 1)
+                        atomicAdd(reinterpret_cast<float2 *>(G + u * plane + pofs), v);
+                    else
+                        G[u * plane + pofs] = v;
                 }
             }
         } else if (lane == 0) {
@@ -271,12 +295,14 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
         const uint64_t d0 = tc05::smem_desc_sw128(tc05::smem_addr(smem), ta.cb_bytes, 1024);
         const uint32_t slot16 = ta.slot_bytes >> 4;
         const uint32_t abase = tmem + ta.acol;
-        const int n_groups = (C + NPAR - 1) / NPAR;
+        const int n_groups = (ce - cb + NPAR - 1) / NPAR;
+        const uint32_t im16 = ta.im_off >> 4;              // Im B columns (planar)
+        const uint32_t idn = ta.idesc | (1u << 13);        // negated A
         bool ok = true;
         int sg = 0;
         uint32_t bpar = 0;
         for (int g = 0; g < n_groups && ok; ++g) {
-            const int nch = min(NPAR, C - g * NPAR);
+            const int nch = min(NPAR, ce - cb - g * NPAR);
             ok = tc05::mbar_wait(&b_full[sg], bpar, budget);
 #pragma unroll
             for (int k = 0; k < NPAR; ++k) {
@@ -292,7 +318,33 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
                     for (int ks = 0; ks < KS; ++ks) {
                         const uint64_t bh = dk + (uint64_t)(ks * (2048 >> 4));
                         const uint32_t acc = (g > 0 || k > 0 || ks > 0) ? 1u : 0u;
-                        if (SPLIT == 3) {
+                        if (PLANAR) {
+                            // Re G += Re A Re B - Im A Im B, Im G += Re A Im B + Im A Re B
+                            const uint64_t bi = bh + im16;
+                            if (SPLIT == 3) {
+                                const uint64_t bl = bh + lo16, bil = bi + lo16;
+                                const uint32_t ar = a0 + (0 * KS + ks) * 8, arl = a0 + (1 * KS + ks) * 8;
+                                const uint32_t ai = a0 + (2 * KS + ks) * 8, ail = a0 + (3 * KS + ks) * 8;
+                                tc05::mma_ts(tmem, ar, bh, ta.idesc, acc);
+                                tc05::mma_ts(tmem, ar, bl, ta.idesc, 1u);
+                                tc05::mma_ts(tmem, arl, bh, ta.idesc, 1u);
+                                tc05::mma_ts(tmem, ai, bi, idn, 1u);
+                                tc05::mma_ts(tmem, ai, bil, idn, 1u);
+                                tc05::mma_ts(tmem, ail, bi, idn, 1u);
+                                tc05::mma_ts(tmem + N, ar, bi, ta.idesc, acc);
+                                tc05::mma_ts(tmem + N, ar, bil, ta.idesc, 1u);
+                                tc05::mma_ts(tmem + N, arl, bi, ta.idesc, 1u);
+                                tc05::mma_ts(tmem + N, ai, bh, ta.idesc, 1u);
+                                tc05::mma_ts(tmem + N, ai, bl, ta.idesc, 1u);
+                                tc05::mma_ts(tmem + N, ail, bh, ta.idesc, 1u);
+                            } else {
+                                const uint32_t ar = a0 + ks * 8, ai = a0 + (KS + ks) * 8;
+                                tc05::mma_ts(tmem, ar, bh, ta.idesc, acc);
+                                tc05::mma_ts(tmem, ai, bi, idn, 1u);
+                                tc05::mma_ts(tmem + N, ar, bi, ta.idesc, acc);
+                                tc05::mma_ts(tmem + N, ai, bh, ta.idesc, 1u);
+                            }
+                        } else if (SPLIT == 3) {
                             const uint64_t bl = bh + lo16;
                             tc05::mma_ts(tmem, a0 + (0 * KS + ks) * 8, bh, ta.idesc, acc);
                             tc05::mma_ts(tmem, a0 + (0 * KS + ks) * 8, bl, ta.idesc, 1u);
@@ -324,22 +376,22 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
     } else {
         // ------------------------------------------------ TMA producer
         // (the whole warp runs the loop; one lane issues the copies)
-        const int n_groups = (C + NPAR - 1) / NPAR;
+        const int n_groups = (ce - cb + NPAR - 1) / NPAR;
         bool ok = true;
         int issued = 0;          // groups issued
         int sg = 0;
         uint32_t dpar = 0;
         int ilo_next[NPAR];      // first window rows, one group ahead
 #pragma unroll
-        for (int k = 0; k < NPAR; ++k) ilo_next[k] = k < C ? tg[k].ilo : 0;
+        for (int k = 0; k < NPAR; ++k) ilo_next[k] = cb + k < ce ? tg[cb + k].ilo : 0;
         for (int g = 0; g < n_groups; ++g) {
-            const int nch = min(NPAR, C - g * NPAR);
+            const int nch = min(NPAR, ce - cb - g * NPAR);
             int ilo[NPAR];
 #pragma unroll
             for (int k = 0; k < NPAR; ++k) {
                 ilo[k] = ilo_next[k];
-                const int cn = (g + 1) * NPAR + k;
-                if (cn < C) ilo_next[k] = tg[cn].ilo;
+                const int cn = cb + (g + 1) * NPAR + k;
+                if (cn < ce) ilo_next[k] = tg[cn].ilo;
             }
             // group g reuses the slot group of group g - NSG: phase g / NSG - 1
             if (g >= NSG) ok = tc05::mbar_wait(&done[sg], dpar, budget);
@@ -351,9 +403,16 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
                 for (int k = 0; k < NPAR; ++k) {
                     if (k >= nch) break;
                     unsigned char *dst = smem + (size_t)(sg * NPAR + k) * ta.slot_bytes;
-                    for (int j = 0; j < ta.ncb; ++j)
+                    const int cz = 2 * (cb + g * NPAR + k);
+                    for (int j = 0; j < ta.ncb; ++j) {
+                        // planar: the Re columns of the bins, then (im_off bytes
+                        // on) their Im columns; interleaved: (re, im) pairs
                         tc05::tma_load_3d(dst + (size_t)j * ta.cb_bytes, &tmap, &b_full[sg],
-                                          2 * u0 + 64 * j, ilo[k], 2 * (g * NPAR + k));
+                                          (PLANAR ? u0 : 2 * u0) + 64 * j, ilo[k], cz);
+                        if (PLANAR)
+                            tc05::tma_load_3d(dst + ta.im_off + (size_t)j * ta.cb_bytes, &tmap,
+                                              &b_full[sg], ta.im_col + 64 * j, ilo[k], cz);
+                    }
                 }
             }
             issued = g + 1;
@@ -376,18 +435,30 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
     if (warp == 0) tc05::tmem_dealloc(tmem, ta.tmem_cols);
 }
 
-template <int W, int KS, int SPLIT, int NPAR>
+template <int W, int KS, int SPLIT, int NPAR, bool PLANAR>
 cudaError_t launch_t(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
                      const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
                      cudaStream_t st) {
     const size_t smem = backproject_tc_smem_bytes(ta);
-    cudaError_t e = cudaFuncSetAttribute(k_backproject_tc<W, KS, SPLIT, NPAR>,
+    cudaError_t e = cudaFuncSetAttribute(k_backproject_tc<W, KS, SPLIT, NPAR, PLANAR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((p.nx + TCX - 1) / TCX, (p.ny + TCY - 1) / TCY, ta.n_utiles);
-    k_backproject_tc<W, KS, SPLIT, NPAR><<<grid, Warps<NPAR>::threads, smem, st>>>(
+    if (ta.nsplit > 1) {      // the channel parts add into G
+        e = cudaMemsetAsync(G, 0, (size_t)p.n_pad * p.nx * p.ny * sizeof(float2), st);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((p.nx + TCX - 1) / TCX, (p.ny + TCY - 1) / TCY, ta.n_utiles * ta.nsplit);
+    k_backproject_tc<W, KS, SPLIT, NPAR, PLANAR><<<grid, Warps<NPAR>::threads, smem, st>>>(
         p, ct, ta, tm, tgeo, kc_hl, G, err);
     return cudaGetLastError();
+}
+
+template <int W, int KS, int SPLIT, int NPAR>
+cudaError_t launch_pl(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
+                      const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
+                      cudaStream_t st) {
+    return ta.planar ? launch_t<W, KS, SPLIT, NPAR, true>(p, ct, ta, tm, tgeo, kc_hl, G, err, st)
+                     : launch_t<W, KS, SPLIT, NPAR, false>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
 }
 
 template <int KS, int SPLIT, int NPAR>
@@ -395,9 +466,9 @@ cudaError_t launch_w(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, con
                      const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
                      cudaStream_t st) {
     switch (p.w) {
-        case 4: return launch_t<4, KS, SPLIT, NPAR>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
-        case 6: return launch_t<6, KS, SPLIT, NPAR>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
-        case 8: return launch_t<8, KS, SPLIT, NPAR>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        case 4: return launch_pl<4, KS, SPLIT, NPAR>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        case 6: return launch_pl<6, KS, SPLIT, NPAR>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        case 8: return launch_pl<8, KS, SPLIT, NPAR>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
         default: return cudaErrorInvalidValue;
     }
 }

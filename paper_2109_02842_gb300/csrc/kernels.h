@@ -89,12 +89,17 @@ cudaError_t launch_setup_tile_geo(const BpDesc &p, const double *ch_xy, TileGeo 
 int backproject_tile_x(int block_config);
 // tensor-core variant (block_config 4), backproject_tc.cu
 struct TcArgs {
-    int UT;              // k_z bins per block (multiple of 8; the MMA's N is 2 UT)
-    int ncb;             // 64-column blocks of a block's window, ceil(2 UT / 64)
+    int UT;              // k_z bins per block (the MMA's N: UT planar, 2 UT interleaved)
+    int planar;          // 1: table rows [Re of every bin | Im of every bin], accumulators
+                         //    Re G and Im G, 12 products per K step; 0: (re, im) pairs, P and Q
+    int nsplit;          // channel parts per tile (blocks adding into G: 1 or 2)
+    int im_col;          // planar: table column of the first Im entry
+    unsigned im_off;     // planar: smem offset of a window's Im columns (ncb x cb_bytes)
+    int ncb;             // 64-column blocks of a block's window: ceil(N / 64)
     int n_utiles;        // blocks along k_z
     int nst;             // table-window slots in shared memory
     unsigned cb_bytes;   // one column block: planes x 16 ks rows x 128 B
-    unsigned slot_bytes; // one channel's window: ncb x cb_bytes
+    unsigned slot_bytes; // one channel's window: ncb x cb_bytes (x 2 planar)
     unsigned idesc;      // tcgen05 instruction descriptor
     int acol;            // first TMEM column of the A buffers (after P and Q)
     int tmem_cols;       // TMEM columns per block (256 or 512)
@@ -133,7 +138,7 @@ cudaError_t launch_setup_rt_E(const NufftDesc &d, double dz, const double *k, co
 // [C][2][L][row_words uint32]
 cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
                                   const CUtensorMap &tmB, const float2 *S, const float2 *alpha,
-                                  void *A, void *prod, void *table, int row_words, int *err,
+                                  void *A, void *prod, void *table, int row_words, int planar, int *err,
                                   bool prepared, cudaStream_t st);
 
 // ---- comparison.cu: exact-sum hybrid and direct back-projection (Sec. III) ------

@@ -22,14 +22,17 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// Tensor-core back-projection layout. TMEM columns of a block: the P and Q
-// accumulators (4 UT) and one A buffer (npl planes x ks steps x 8) for each
-// of npar channel classes; 2 classes in 256 columns (2 blocks per SM) or 3
-// in 512 (1 block per SM).
-int tc_cols(int ut, int npar, int npl, int ks) { return 4 * ut + npar * npl * ks * 8; }
-int tc_npar(int ut, int npl, int ks) {
-    if (tc_cols(ut, 2, npl, ks) <= 256) return 2;
-    if (tc_cols(ut, 3, npl, ks) <= 512) return 3;
+// Tensor-core back-projection layout. TMEM columns of a block: the
+// accumulators (Re G, Im G: 2 UT planar; P, Q: 4 UT interleaved) and one A
+// buffer (npl planes x ks steps x 8) for each of npar channel classes; 2
+// classes in 256 columns (2 blocks per SM) or 3 in 512 (1 block per SM).
+int tc_cols(int ut, int npar, int npl, int ks, bool planar) {
+    return (planar ? 2 : 4) * ut + npar * npl * ks * 8;
+}
+int tc_npar(int ut, int npl, int ks, bool planar) {
+    if (planar && ut > 256) return 0;          // the MMA's N is at most 256
+    if (tc_cols(ut, 2, npl, ks, planar) <= 256) return 2;
+    if (tc_cols(ut, 3, npl, ks, planar) <= 512) return 3;
     return 0;
 }
 // Bins per block: the fewest blocks that the largest 1-block-per-SM tile
@@ -276,7 +279,12 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     {
         const int n = s->n_pad ? s->n_pad : s->n;
         if (P->block_config == 4) {
-            if (P->tile_u == 0) P->tile_u = tc_auto_tile(n, o.precision == 1 ? 2 : 4, 1);
+            // default: the planar layout with every bin in one block (N = N_p
+            // rounded up to 16); an explicit tile_u asks for interleaved blocks
+            if (P->tile_u == 0) {
+                P->tile_u = (n + 15) / 16 * 16;
+                P->tc.planar = 1;
+            }
         } else if (P->tile_u == 0) {    // fewest padded bins; 20 only when it wastes less than 16
             const int w16 = (n + 15) / 16 * 16 - n, w20 = (n + 19) / 20 * 20 - n;
             P->tile_u = w20 < w16 ? 20 : 16;
@@ -395,10 +403,12 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
             if (ks == 0)
                 return fail(PL_ERR_UNSUPPORTED,
                             "a 16 x 8 pixel tile spans more than 32 table rows (grid too coarse for block_config 4)");
-            if (tc_npar(P->tile_u, npl, ks) != 0) break;
-            if (attempt > 0 || o.tile_u != 0)
+            if (tc_npar(P->tile_u, npl, ks, P->tc.planar != 0) != 0) break;
+            if (attempt > 1 || o.tile_u != 0)
                 return fail(PL_ERR_UNSUPPORTED, "tile_u too large for tensor memory");
-            // two K steps leave less tensor memory for bins: smaller blocks, new band
+            // the planar layout does not fit (too many bins, or two K steps):
+            // interleaved blocks of bins, sized for ks, and their band
+            P->tc.planar = 0;
             P->tile_u = tc_auto_tile(P->Np, npl, ks);
             const pl_status bs = band(P->tile_u);
             if (bs != PL_OK) return bs;
@@ -436,14 +446,16 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     if (P->block_config == 4) {
         TcArgs &ta = P->tc;
         ta.UT = P->tile_u;
-        ta.ncb = (2 * ta.UT + 63) / 64;
+        const int N = ta.planar ? ta.UT : 2 * ta.UT;
+        ta.ncb = (N + 63) / 64;
         ta.n_utiles = (P->Np + ta.UT - 1) / ta.UT;
         ta.split = P->precision == 1 ? 1 : 3;
         const int planes = ta.split == 3 ? 2 : 1, npl = ta.split == 3 ? 4 : 2;
         ta.cb_bytes = (unsigned)(planes * 16 * ta.ks * 128);
-        ta.slot_bytes = (unsigned)ta.ncb * ta.cb_bytes;
-        const int N = 2 * ta.UT;
-        ta.npar = tc_npar(ta.UT, npl, ta.ks);
+        ta.im_off = ta.planar ? (unsigned)ta.ncb * ta.cb_bytes : 0u;
+        ta.im_col = ta.planar ? ta.UT : 0;
+        ta.slot_bytes = (unsigned)(ta.planar ? 2 : 1) * ta.ncb * ta.cb_bytes;
+        ta.npar = tc_npar(ta.UT, npl, ta.ks, ta.planar != 0);
         ta.tmem_cols = ta.npar == 2 ? 256 : 512;
         ta.acol = 2 * N;
         // window slots: whole slot groups of npar (at least 2 groups), within
@@ -455,7 +467,15 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
             return fail(PL_ERR_UNSUPPORTED, "table window slots exceed shared memory");
         ta.idesc = tc05::idesc_bf16(128, N, 1);
         ta.budget = 4ll << 30;
-        d.tc_cols = 2 * ta.n_utiles * ta.UT;
+        d.tc_cols = ta.planar ? 2 * ta.UT : 2 * ta.n_utiles * ta.UT;
+        d.tc_planar = ta.planar;
+        // planar: two channel parts per tile. Each accumulator then takes as
+        // many products as an interleaved P or Q accumulator over all channels
+        // (the planar one takes twice as many per channel, and the
+        // accumulation error measured on the tensor cores grows in
+        // proportion to that count); the parts also fill the SMs' last wave
+        // better than one block per tile.
+        ta.nsplit = ta.planar && P->C >= 2 * ta.npar ? 2 : 1;
     } else if (backproject_smem_bytes(P->R, P->tile_u, P->C, P->precision, P->block_config) > 200 * 1024)
         return fail(PL_ERR_UNSUPPORTED, "table window too tall for shared memory (grid too coarse)");
     for (int tp = 0; tp < W; ++tp) es_tap_polynomial(W, (double)d.beta, tp, W + 1, P->coef.c[tp]);
@@ -610,8 +630,8 @@ pl_status pl_stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st) {
 pl_status pl_stage_range_table(pl_plan *P, cudaStream_t st) {
     if (P->block_config == 4 && P->rt_tc) {
         PL_CUDA(launch_range_table_tc(P->rt, P->tmapA, P->tmapE, P->d_S, P->d_alpha, P->d_rtA,
-                                      P->d_rtprod, P->d_table, P->nd.tc_cols / 2, P->d_err,
-                                      P->fwd_fft, st),
+                                      P->d_rtprod, P->d_table, P->nd.tc_cols / 2,
+                                      P->nd.tc_planar, P->d_err, P->fwd_fft, st),
                 "range_table_tc");
         return PL_OK;
     }

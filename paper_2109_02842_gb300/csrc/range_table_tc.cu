@@ -17,8 +17,9 @@
 //                      tcgen05.ld, BF16 hi/lo, one bulk store per plane into
 //                      prod [u][hi, lo][C][L'] of (re, im) pairs (rows padded
 //                      to L' = L rounded up to 16, so every store is 16-byte aligned)
-//   k_rt_transpose     prod -> table [c][hi, lo][L][column 2u + (re, im)], the
-//                      layout the back-projection streams (u innermost)
+//   k_rt_transpose     prod -> table [c][hi, lo][L][column 2u + (re, im)] (or
+//                      planar: Re at column u, Im at row_words + u), the layout
+//                      the back-projection streams (u innermost)
 //
 // E [u][re hi, re lo, im hi, im lo][L'][K] = e^{+j theta (i - L/2)} is a plan-time table.
 #include <cuda_bf16.h>
@@ -228,7 +229,9 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
 
 // prod [u][plane][C][Lp] (uint32 = (re, im) BF16 pair) -> table [c][plane][L][u]:
 // 64 x 64 tiles, 16-byte global accesses on both sides (u beyond N_p written
-// as zeros so the padding columns stay zero)
+// as zeros so the padding columns stay zero). Interleaved rows hold row_words
+// (re, im) pairs; planar rows hold row_words Re entries, then row_words Im.
+template <bool PLANAR>
 __global__ void __launch_bounds__(256)
 k_rt_transpose(const uint32_t *__restrict__ prod, uint32_t *__restrict__ table, int C, int L,
                int Lp, int Np, int row_words) {
@@ -252,7 +255,17 @@ k_rt_transpose(const uint32_t *__restrict__ prod, uint32_t *__restrict__ table, 
         const int i = i0 + k, u = u0 + 4 * q;
         if (i >= L || u >= row_words) continue;
         const uint4 v = make_uint4(s[4 * q][k], s[4 * q + 1][k], s[4 * q + 2][k], s[4 * q + 3][k]);
-        *reinterpret_cast<uint4 *>(table + ((size_t)cp * L + i) * row_words + u) = v;
+        uint32_t *row = table + ((size_t)cp * L + i) * row_words;
+        if (PLANAR) {
+            // low halves (Re) of four bins, then the high halves (Im)
+            __nv_bfloat16 *rb = reinterpret_cast<__nv_bfloat16 *>(row);
+            const uint2 re = make_uint2(__byte_perm(v.x, v.y, 0x5410), __byte_perm(v.z, v.w, 0x5410));
+            const uint2 im = make_uint2(__byte_perm(v.x, v.y, 0x7632), __byte_perm(v.z, v.w, 0x7632));
+            *reinterpret_cast<uint2 *>(rb + u) = re;
+            *reinterpret_cast<uint2 *>(rb + row_words + u) = im;
+        } else {
+            *reinterpret_cast<uint4 *>(row + u) = v;
+        }
     }
 }
 
@@ -274,8 +287,8 @@ cudaError_t launch_setup_rt_E(const NufftDesc &d, double dz, const double *k, co
 
 cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
                                   const CUtensorMap &tmB, const float2 *S, const float2 *alpha,
-                                  void *A, void *prod, void *table, int row_words, int *err,
-                                  bool prepared, cudaStream_t st) {
+                                  void *A, void *prod, void *table, int row_words, int planar,
+                                  int *err, bool prepared, cudaStream_t st) {
     cudaError_t e;
     if (!prepared) {     // the z transform wrote S, not the split operand
         const long long n = (long long)ra.C * ra.Np * ra.Kp;
@@ -293,7 +306,11 @@ cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 tg((ra.L + 63) / 64, (row_words + 63) / 64, 2 * ra.C);
-    k_rt_transpose<<<tg, 256, 0, st>>>((const uint32_t *)prod, (uint32_t *)table, ra.C, ra.L,
-                                       ra.Lp, ra.Np, row_words);
+    if (planar)
+        k_rt_transpose<true><<<tg, 256, 0, st>>>((const uint32_t *)prod, (uint32_t *)table, ra.C,
+                                                 ra.L, ra.Lp, ra.Np, row_words);
+    else
+        k_rt_transpose<false><<<tg, 256, 0, st>>>((const uint32_t *)prod, (uint32_t *)table, ra.C,
+                                                  ra.L, ra.Lp, ra.Np, row_words);
     return cudaGetLastError();
 }

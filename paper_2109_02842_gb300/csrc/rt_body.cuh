@@ -87,7 +87,8 @@ __device__ __forceinline__ void rt_block(const NufftDesc &d, const FftPlan &fp,
 
     // deconvolve, keep rows j = i - L/2
     if (fmt == 4) {
-        // tensor-core layout [c][plane hi/lo][row][column 2u + (re, im)], BF16,
+        // tensor-core layout [c][plane hi/lo][row][column 2u + (re, im)] (or
+        // planar: Re at column u, Im at tc_cols / 2 + u), BF16,
         // hi = BF16(x) and lo = BF16(x - hi); bins past N_p stay zero
         __nv_bfloat16 *tb = reinterpret_cast<__nv_bfloat16 *>(table);
         for (int idx = threadIdx.x; idx < UB * d.L; idx += blockDim.x) {
@@ -99,9 +100,19 @@ __device__ __forceinline__ void rt_block(const NufftDesc &d, const FftPlan &fp,
             const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
             const float2 hf = __bfloat1622float2(h);
             const __nv_bfloat162 l = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
-            const size_t o = (((size_t)c * 2) * d.L + i) * d.tc_cols + 2 * (size_t)(u0 + ul);
-            *reinterpret_cast<__nv_bfloat162 *>(tb + o) = h;
-            *reinterpret_cast<__nv_bfloat162 *>(tb + o + (size_t)d.L * d.tc_cols) = l;
+            const size_t row = (((size_t)c * 2) * d.L + i) * d.tc_cols;
+            const size_t lo = (size_t)d.L * d.tc_cols;
+            if (d.tc_planar) {       // Re at column u, Im at column tc_cols / 2 + u
+                const size_t o = row + (size_t)(u0 + ul), oi = o + d.tc_cols / 2;
+                tb[o] = __low2bfloat16(h);
+                tb[oi] = __high2bfloat16(h);
+                tb[o + lo] = __low2bfloat16(l);
+                tb[oi + lo] = __high2bfloat16(l);
+            } else {
+                const size_t o = row + 2 * (size_t)(u0 + ul);
+                *reinterpret_cast<__nv_bfloat162 *>(tb + o) = h;
+                *reinterpret_cast<__nv_bfloat162 *>(tb + o + lo) = l;
+            }
         }
         return;
     }
