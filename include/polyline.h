@@ -104,7 +104,8 @@ typedef struct {
  * nufft_sigma: oversampling of the range-profile grid (default 2.0).
  * nufft_w: interpolation taps (even, 4..12; default 6).
  * tile_u: k_z bins per back-projection block (8, 16, 20 or 24; with
- *         block_config 4 a multiple of 8 in 16..112; 0 = chosen from n_pad).
+ *         block_config 4 a multiple of 8 in 16..112, which selects the
+ *         interleaved layout below; 0 = chosen from n_pad).
  * block_config: back-projection kernel (0 = default: 4 when nufft_w is 4, 6
  *         or 8, tile_u is 0 and the grid allows it, else 3 when the x step is
  *         below the table step, else 1; 1 = FP32, one pixel per thread,
@@ -114,8 +115,12 @@ typedef struct {
  *         block, the channel sum accumulated in tensor memory, one band centre
  *         per block of bins, BF16 operands split hi + lo (precision 0) or BF16
  *         only (precision 1); needs nufft_w 4, 6 or 8. With 4 the range-table
- *         workspace holds [channel][hi/lo][row][column 2u + (re, im)] BF16,
- *         hi = BF16(x), lo = BF16(x - hi).
+ *         workspace holds [channel][hi/lo][row][column] BF16, hi = BF16(x),
+ *         lo = BF16(x - hi): by default (tile_u = 0) planar, every bin in one
+ *         block (tile_u = n_pad rounded up to 16), column u = Re b_u and
+ *         column tile_u + u = Im b_u, and each tile's channels in two parts;
+ *         where that does not fit tensor memory, or with an explicit tile_u,
+ *         interleaved, column 2u + (re, im) within blocks of tile_u bins.
  *         A bounded device wait of block_config 4 that runs out makes the next
  *         pl_execute / pl_execute_host call return PL_ERR_TIMEOUT.) */
 typedef struct {
@@ -145,7 +150,8 @@ typedef struct {
     size_t workspace_bytes;
     double updates_per_execute;  /* n_chan * nx * ny * nz * n_f */
     int block_config;            /* back-projection kernel in use (1..4) */
-    int tile_u;                  /* its k_z bins per block */
+    int tile_u;                  /* its k_z bins per block (block_config 4: all
+                                    n_pad, rounded up to 16, in the planar layout) */
 } pl_info;
 
 /* Stage identifiers for timing and workspace access. */
@@ -243,7 +249,10 @@ pl_status pl_plan_get_info(const pl_plan *plan, pl_info *info);
  *  PL_STAGE_RANGE_TABLE -> table b, [n_chan][L][ceil(n_pad/2)] rows of k_z bin pairs
  *                          {re_u, re_u+1, im_u, im_u+1} (float32, or bfloat16 when
  *                          precision = 1); block_config 4: see pl_options
- *  PL_STAGE_BACKPROJECT -> image spectrum G, complex64 [n_pad][ny][nx] */
+ *  PL_STAGE_BACKPROJECT -> image spectrum G, complex64 [parts][n_pad][ny][nx]: the
+ *                          spectrum is the sum over parts (2 parts, one per half
+ *                          of the channels, in the planar block_config 4 layout;
+ *                          else 1) */
 pl_status pl_plan_workspace(pl_plan *plan, int stage, void **dev_ptr, size_t *bytes);
 
 /* Per-stage timing with CUDA events recorded on the execute stream.

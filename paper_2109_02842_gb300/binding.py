@@ -327,7 +327,8 @@ class Plan:
             # rows of planar bin pairs {re_u, re_u+1, im_u, im_u+1}
             shape = (i["n_chan"], i["table_len"], (i["n_pad"] + 1) // 2, 4)
             if nbytes.value not in (np.prod(shape) * 2, np.prod(shape) * 4):
-                # tensor-core layout [c][hi/lo][row][column 2u + (re, im)] (BF16)
+                # tensor-core layout [c][hi/lo][row][column] (BF16; columns
+                # 2u + (re, im), or planar: Re of the bins, then Im)
                 cols = nbytes.value // (i["n_chan"] * 2 * i["table_len"] * 2)
                 shape = (i["n_chan"], 2, i["table_len"], cols)
                 raw = torch.as_tensor(_DevArray(ptr.value, shape, "<i2"), device="cuda")
@@ -337,7 +338,9 @@ class Plan:
                 return raw.view(torch.bfloat16)
             return torch.as_tensor(_DevArray(ptr.value, shape, "<f4"), device="cuda")
         else:
-            shape = (i["n_pad"], i["ny"], i["nx"])
+            # [parts][n_pad][ny][nx]; the spectrum is the sum over parts
+            plane = i["n_pad"] * i["ny"] * i["nx"] * 8
+            shape = (nbytes.value // plane, i["n_pad"], i["ny"], i["nx"])
         return torch.as_tensor(_DevArray(ptr.value, shape, "<c8"), device="cuda")
 
     def set_timing(self, enable: bool = True):

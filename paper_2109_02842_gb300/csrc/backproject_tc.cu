@@ -24,10 +24,9 @@
 // Operands are BF16; for FP32-level accuracy each is split into hi + lo
 // and the product taken as hi.hi + hi.lo + lo.hi (SPLIT = 3), relative
 // error ~1e-5; SPLIT = 1 takes hi.hi only (~1e-3). In the planar layout a
-// tile's channels go to two blocks (nsplit = 2) that add their sums into G
-// (zeroed first): each accumulator then sums as many products as an
-// interleaved one, and with two addends on zero the result does not depend
-// on their order.
+// tile's channels go to two blocks (nsplit = 2) that write their sums to two
+// spectra G[0], G[1] (added by the inverse z transform as it loads them):
+// each accumulator then sums as many products as an interleaved one.
 //
 // Block = 16 x 8 pixels x UT bins, 4 NPAR + 2 warps (NPAR = 2 and two blocks
 // per SM when the accumulators and three A buffers fit in 256 TMEM columns,
@@ -49,7 +48,7 @@
 //    written with 128-byte swizzling, which is the MN-major layout the MMA
 //    reads (64-column atoms, rows 128 B apart); a window may start at any row.
 // At the end the accumulators (2 N FP32 columns) are read back with
-// tcgen05.ld and written (or, with two channel parts, added) as G[u][y][x].
+// tcgen05.ld and written as G[part][u][y][x].
 //
 // Every wait is bounded (a clock budget); a wait that runs out sets a bit in
 // *err, the block skips the rest of its work and still waits (bounded) for
@@ -258,6 +257,7 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
             const bool inside = ix < p.nx && iy < p.ny;
             const size_t plane = (size_t)p.nx * p.ny;
             const size_t pofs = (size_t)iy * p.nx + ix;
+            float2 *Gp = G + (size_t)part * p.n_pad * plane;   // this channel part's spectrum
             for (int ch = par; ch < (int)(N / 16); ch += NPAR) {
                 uint32_t pv[16], qv[16];
                 tc05::tmem_ld16(lane_base + 16 * ch, pv);
@@ -275,10 +275,7 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
                         PLANAR ? make_float2(__uint_as_float(pv[b]), __uint_as_float(qv[b]))
                                : make_float2(__uint_as_float(pv[2 * b]) - __uint_as_float(qv[2 * b + 1]),
                                              __uint_as_float(pv[2 * b + 1]) + __uint_as_float(qv[2 * b]));
-                    if (ta.nsplit > 1)
-                        atomicAdd(reinterpret_cast<float2 *>(G + u * plane + pofs), v);
-                    else
-                        G[u * plane + pofs] = v;
+                    Gp[u * plane + pofs] = v;
                 }
             }
         } else if (lane == 0) {
@@ -443,10 +440,6 @@ cudaError_t launch_t(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, con
     cudaError_t e = cudaFuncSetAttribute(k_backproject_tc<W, KS, SPLIT, NPAR, PLANAR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (ta.nsplit > 1) {      // the channel parts add into G
-        e = cudaMemsetAsync(G, 0, (size_t)p.n_pad * p.nx * p.ny * sizeof(float2), st);
-        if (e != cudaSuccess) return e;
-    }
     dim3 grid((p.nx + TCX - 1) / TCX, (p.ny + TCY - 1) / TCY, ta.n_utiles * ta.nsplit);
     k_backproject_tc<W, KS, SPLIT, NPAR, PLANAR><<<grid, Warps<NPAR>::threads, smem, st>>>(
         p, ct, ta, tm, tgeo, kc_hl, G, err);

@@ -13,9 +13,11 @@ cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_i
                                const FftPlan &plan, const float2 *tw, int sgn, float scale,
                                int out_rows, int out_off, cudaStream_t st,
                                const float2 *split_alpha = nullptr, void *split_A = nullptr,
-                               int split_Kp = 0);
+                               int split_Kp = 0, const float2 *in2 = nullptr);
+// in2 (optional): a second input of the same shape, added to `in` on load
 cudaError_t launch_dft_strided(const float2 *in, float2 *out, int batch, int n_in, int I,
-                               int out_rows, const float2 *T, float scale, cudaStream_t st);
+                               int out_rows, const float2 *T, float scale, cudaStream_t st,
+                               const float2 *in2 = nullptr);
 
 // ---- setup.cu --------------------------------------------------------------
 // Per k_z bin: kappa range over propagating frequencies; kc = centre (double

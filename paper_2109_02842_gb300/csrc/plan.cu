@@ -603,7 +603,10 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
                 return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled failed (range table)");
         }
     }
-    PL_CUDA(dalloc(&P->d_G, (size_t)P->Np * gr->nx * gr->ny, ws), "cudaMalloc");
+    // the spectrum G[part][u][y][x]: two parts when the tensor-core
+    // back-projection splits each tile's channels
+    const int g_parts = P->block_config == 4 ? P->tc.nsplit : 1;
+    PL_CUDA(dalloc(&P->d_G, (size_t)g_parts * P->Np * gr->nx * gr->ny, ws), "cudaMalloc");
     PL_CUDA(cudaDeviceSynchronize(), "plan setup");
     return PL_OK;
 }
@@ -653,15 +656,23 @@ pl_status pl_stage_backproject(pl_plan *P, cudaStream_t st) {
     return PL_OK;
 }
 
-pl_status pl_stage_zifft(pl_plan *P, float2 *image, cudaStream_t st) {
+// The inverse z transform of G; `parts` = 2 adds the second channel part's
+// spectrum as it loads the first.
+static pl_status stage_zifft(pl_plan *P, float2 *image, cudaStream_t st, int parts) {
     const int P2 = P->grid.nx * P->grid.ny;
+    const float2 *G2 = parts > 1 ? P->d_G + (size_t)P->Np * P2 : nullptr;
     if (P->inv_fft)
         PL_CUDA(launch_fft_strided(P->d_G, image, 1, P->Np, P2, P->zplan, P->d_twz, +1,
-                                   1.0f / P->Np, P->grid.nz, P->inv_off, st), "zifft");
+                                   1.0f / P->Np, P->grid.nz, P->inv_off, st, nullptr, nullptr,
+                                   0, G2), "zifft");
     else
         PL_CUDA(launch_dft_strided(P->d_G, image, 1, P->Np, P2, P->grid.nz, P->d_Tinv,
-                                   1.0f / P->Np, st), "zidft");
+                                   1.0f / P->Np, st, G2), "zidft");
     return PL_OK;
+}
+
+pl_status pl_stage_zifft(pl_plan *P, float2 *image, cudaStream_t st) {
+    return stage_zifft(P, image, st, P->block_config == 4 ? P->tc.nsplit : 1);
 }
 
 namespace {
@@ -875,7 +886,7 @@ pl_status pl_execute_exact(pl_plan *plan, const void *echo_dev, void *image_dev,
     PL_CUDA(launch_exact_sum(plan->exact, plan->d_S, plan->d_kap, plan->d_wum, plan->d_chff,
                              plan->d_G, st),
             "exact_sum");
-    return pl_stage_zifft(plan, (float2 *)image_dev, st);
+    return stage_zifft(plan, (float2 *)image_dev, st, 1);     // one whole spectrum
 }
 
 pl_status pl_execute_bp_direct(pl_plan *plan, const void *echo_dev, void *image_dev,
@@ -1013,7 +1024,8 @@ pl_status pl_plan_workspace(pl_plan *P, int stage, void **dev_ptr, size_t *bytes
             return PL_OK;
         case PL_STAGE_BACKPROJECT:
             *dev_ptr = P->d_G;
-            *bytes = (size_t)P->Np * P->grid.nx * P->grid.ny * sizeof(float2);
+            *bytes = (size_t)(P->block_config == 4 ? P->tc.nsplit : 1) * P->Np * P->grid.nx *
+                     P->grid.ny * sizeof(float2);
             return PL_OK;
     }
     return fail(PL_ERR_ARG, "no workspace for this stage");

@@ -31,9 +31,9 @@ struct SplitOut {
 // float4 shared-memory accesses, column pairs through the FFT stages).
 template <bool PAIRS>
 __global__ void __launch_bounds__(256)
-k_fft_strided(const float2 *__restrict__ in, float2 *__restrict__ out, int n_in, int I,
-              FftPlan plan, const float2 *__restrict__ tw_g, int sgn, float scale,
-              int out_rows, int out_off, SplitOut sp) {
+k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, float2 *__restrict__ out,
+              int n_in, int I, FftPlan plan, const float2 *__restrict__ tw_g, int sgn,
+              float scale, int out_rows, int out_off, SplitOut sp) {
     extern __shared__ __align__(16) float2 smem[];
     const int N = plan.n;
     float2 *buf0 = smem;
@@ -47,30 +47,44 @@ k_fft_strided(const float2 *__restrict__ in, float2 *__restrict__ out, int n_in,
     // the whole panel in flight at once: asynchronous copies, zeros for the
     // padding rows and the columns past I
     for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
-    for (int idx = threadIdx.x; idx < N * NG; idx += blockDim.x) {
-        const int n = idx / NG;
-        const int col = (idx - n * NG) * CW;
-        float2 *dst = buf0 + n * kFftIB + col;
-        if (n < n_in && i0 + col < I) {
-            const float2 *src = in + (b * n_in + n) * (size_t)I + i0 + col;
-            if (PAIRS)
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(
-                                 (unsigned)__cvta_generic_to_shared(dst)),
-                             "l"(src)
-                             : "memory");
-            else
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(
-                                 (unsigned)__cvta_generic_to_shared(dst)),
-                             "l"(src)
-                             : "memory");
-        } else if (PAIRS) {
-            *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
-        } else {
-            *dst = make_float2(0.f, 0.f);
+    // in2 (optional): a second array of the same shape, added on load (into
+    // buf1 first, which the transform then reuses)
+    for (int part = 0; part < (in2 ? 2 : 1); ++part) {
+        const float2 *src_arr = part ? in2 : in;
+        float2 *panel = part ? buf1 : buf0;
+        for (int idx = threadIdx.x; idx < N * NG; idx += blockDim.x) {
+            const int n = idx / NG;
+            const int col = (idx - n * NG) * CW;
+            float2 *dst = panel + n * kFftIB + col;
+            if (n < n_in && i0 + col < I) {
+                const float2 *src = src_arr + (b * n_in + n) * (size_t)I + i0 + col;
+                if (PAIRS)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(
+                                     (unsigned)__cvta_generic_to_shared(dst)),
+                                 "l"(src)
+                                 : "memory");
+                else
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(
+                                     (unsigned)__cvta_generic_to_shared(dst)),
+                                 "l"(src)
+                                 : "memory");
+            } else if (PAIRS) {
+                *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                *dst = make_float2(0.f, 0.f);
+            }
         }
     }
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
+    if (in2) {
+        for (int idx = threadIdx.x; idx < N * kFftIB / 2; idx += blockDim.x) {
+            float4 *a = reinterpret_cast<float4 *>(buf0) + idx;
+            const float4 c = reinterpret_cast<const float4 *>(buf1)[idx];
+            *a = make_float4(a->x + c.x, a->y + c.y, a->z + c.z, a->w + c.w);
+        }
+        __syncthreads();
+    }
 
     const float2 *src = PAIRS ? stockham_run_pairs<kFftIB>(buf0, buf1, tw, plan, sgn)
                               : stockham_run<true, kFftIB>(buf0, buf1, tw, plan, sgn, 1, kFftIB);
@@ -124,8 +138,8 @@ k_fft_strided(const float2 *__restrict__ in, float2 *__restrict__ out, int n_in,
 //   out[b][r][i] = scale * sum_{n < n_in} in[b][n][i] * T[r][n]
 // 32 x 32 output tile per block, 256 threads, 4 outputs each.
 __global__ void __launch_bounds__(256)
-k_dft_strided(const float2 *__restrict__ in, float2 *__restrict__ out, int n_in, int I,
-              int out_rows, const float2 *__restrict__ T, float scale) {
+k_dft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, float2 *__restrict__ out,
+              int n_in, int I, int out_rows, const float2 *__restrict__ T, float scale) {
     __shared__ float2 xs[32][33];
     __shared__ float2 ts[32][33];
     const int tx = threadIdx.x & 31;
@@ -140,8 +154,13 @@ k_dft_strided(const float2 *__restrict__ in, float2 *__restrict__ out, int n_in,
         for (int q = 0; q < 4; ++q) {
             const int nn = ty * 4 + q;
             const int n = n0 + nn;
-            xs[nn][tx] = (n < n_in && i < I) ? in[(b * n_in + n) * (size_t)I + i]
-                                             : make_float2(0.f, 0.f);
+            float2 x = make_float2(0.f, 0.f);
+            if (n < n_in && i < I) {
+                const size_t o = (b * n_in + n) * (size_t)I + i;
+                x = in[o];
+                if (in2) x = cadd(x, in2[o]);
+            }
+            xs[nn][tx] = x;
             const int rr = r0 + ty * 4 + q;
             ts[ty * 4 + q][tx] = (rr < out_rows && n0 + tx < n_in)
                                      ? T[(size_t)rr * n_in + n0 + tx] : make_float2(0.f, 0.f);
@@ -174,11 +193,12 @@ size_t fft_strided_smem_bytes(int n) { return (size_t)(2 * n * kFftIB + n) * siz
 cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_in, int I,
                                const FftPlan &plan, const float2 *tw, int sgn, float scale,
                                int out_rows, int out_off, cudaStream_t st,
-                               const float2 *split_alpha, void *split_A, int split_Kp) {
+                               const float2 *split_alpha, void *split_A, int split_Kp,
+                               const float2 *in2) {
     const size_t smem = fft_strided_smem_bytes(plan.n);
     // column pairs need 16-byte aligned rows: I even, 16-byte aligned
     // buffers, and (split output) an even operand row length
-    const bool pairs = (I % 2 == 0) && ((uintptr_t)in % 16 == 0) &&
+    const bool pairs = (I % 2 == 0) && ((uintptr_t)in % 16 == 0) && ((uintptr_t)in2 % 16 == 0) &&
                        (split_A ? (split_Kp % 2 == 0 && (uintptr_t)split_A % 4 == 0 &&
                                    (uintptr_t)split_alpha % 16 == 0)
                                 : (uintptr_t)out % 16 == 0);
@@ -188,13 +208,15 @@ cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_i
     if (e != cudaSuccess) return e;
     dim3 grid((I + kFftIB - 1) / kFftIB, batch);
     const SplitOut sp{split_alpha, (__nv_bfloat16 *)split_A, batch, split_Kp};
-    kern<<<grid, 256, smem, st>>>(in, out, n_in, I, plan, tw, sgn, scale, out_rows, out_off, sp);
+    kern<<<grid, 256, smem, st>>>(in, in2, out, n_in, I, plan, tw, sgn, scale, out_rows, out_off,
+                                  sp);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dft_strided(const float2 *in, float2 *out, int batch, int n_in, int I,
-                               int out_rows, const float2 *T, float scale, cudaStream_t st) {
+                               int out_rows, const float2 *T, float scale, cudaStream_t st,
+                               const float2 *in2) {
     dim3 grid((I + 31) / 32, (out_rows + 31) / 32, batch);
-    k_dft_strided<<<grid, 256, 0, st>>>(in, out, n_in, I, out_rows, T, scale);
+    k_dft_strided<<<grid, 256, 0, st>>>(in, in2, out, n_in, I, out_rows, T, scale);
     return cudaGetLastError();
 }
