@@ -127,8 +127,10 @@ struct RtTcArgs {
     int C, Np, M;
     int Kp;              // frequencies rounded up to 64 (the K of the products)
     int natoms;          // Kp / 64
-    int L, Lp;           // table rows; rounded up to 16 (the N of the products)
-    unsigned idesc;      // tcgen05 instruction descriptor (M 128, N Lp, both K-major)
+    int L, Lp;           // table rows; rounded up to 16
+    int nh, Lh;          // row parts per bin (blocks along the rows) and rows per part,
+                         // a multiple of 16 (the N of the products)
+    unsigned idesc;      // tcgen05 instruction descriptor (M 128, N Lh, both K-major)
     long long budget;    // wait budget, SM clock cycles
 };
 size_t range_table_tc_smem_bytes(const RtTcArgs &ra);
@@ -136,7 +138,7 @@ size_t range_table_tc_smem_bytes(const RtTcArgs &ra);
 cudaError_t launch_setup_rt_E(const NufftDesc &d, double dz, const double *k, const double *kc,
                               int Lp, int Kp, void *E, cudaStream_t st);
 // S, alpha -> A (scratch [N_p][4][C][Kp] BF16; skipped when `prepared`: the
-// z-FFT wrote A) -> prod (scratch [N_p][2][C][Lp] uint32) -> table
+// z-FFT wrote A) -> prod (scratch [N_p][2][nh][C][Lh] uint32) -> table
 // [C][2][L][row_words uint32]
 cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
                                   const CUtensorMap &tmB, const float2 *S, const float2 *alpha,

@@ -571,14 +571,21 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         ra.natoms = ra.Kp / 64;
         ra.L = L;
         ra.Lp = (L + 15) / 16 * 16;
-        ra.idesc = tc05::idesc_bf16(128, ra.Lp, 0);
+        // two row parts when one part would not let two blocks share an SM
+        ra.nh = 1;
+        ra.Lh = ra.Lp;
+        if (2 * ra.Lp > 256 || range_table_tc_smem_bytes(ra) > 110 * 1024) {
+            ra.nh = 2;
+            ra.Lh = ((ra.Lp + 1) / 2 + 15) / 16 * 16;
+        }
+        ra.idesc = tc05::idesc_bf16(128, ra.Lh, 0);
         ra.budget = 4ll << 30;
         P->rt_tc = ra.natoms == 1 && ra.Lp <= 256 &&
                    range_table_tc_smem_bytes(ra) <= 227 * 1024;
         if (P->rt_tc) {
             const size_t nE = (size_t)P->Np * 4 * ra.Lp * ra.Kp;
             const size_t nA = (size_t)P->Np * 4 * P->C * ra.Kp;
-            const size_t nprod = (size_t)P->Np * 2 * P->C * ra.Lp;
+            const size_t nprod = (size_t)P->Np * 2 * ra.nh * P->C * ra.Lh;
             PL_CUDA(cudaMalloc(&P->d_rtE, nE * 2), "cudaMalloc");
             PL_CUDA(cudaMalloc(&P->d_rtA, nA * 2), "cudaMalloc");
             PL_CUDA(cudaMemset(P->d_rtA, 0, nA * 2), "cudaMemset");   // frequencies >= M stay 0
@@ -591,7 +598,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
             const cuuint32_t ba[3] = {64, 128, 1};
             const cuuint64_t db[3] = {(cuuint64_t)ra.Kp, (cuuint64_t)ra.Lp, 4 * (cuuint64_t)P->Np};
             const cuuint64_t sb[2] = {(cuuint64_t)ra.Kp * 2, (cuuint64_t)ra.Lp * ra.Kp * 2};
-            const cuuint32_t bb[3] = {64, (cuuint32_t)ra.Lp, 1};
+            const cuuint32_t bb[3] = {64, (cuuint32_t)ra.Lh, 1};
             const cuuint32_t e3[3] = {1, 1, 1};
             CUresult r1 = enc(&P->tmapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, P->d_rtA, da, sa, ba,
                               e3, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,

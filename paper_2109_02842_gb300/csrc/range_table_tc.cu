@@ -12,11 +12,15 @@
 // instruction descriptor, and the two accumulators (Re, Im) live in TMEM.
 //
 //   k_rt_prep          S [C][N_p][M] x alpha -> A [u][re hi, re lo, im hi, im lo][C][K] BF16
-//   k_range_table_tc   per (128-channel block, bin): TMA (128-byte swizzled,
-//                      K-major) A and E tiles, 12 MMAs per 16-frequency step,
-//                      tcgen05.ld, BF16 hi/lo, one bulk store per plane into
-//                      prod [u][hi, lo][C][L'] of (re, im) pairs (rows padded
-//                      to L' = L rounded up to 16, so every store is 16-byte aligned)
+//   k_range_table_tc   per (128-channel block, bin, row part): TMA (128-byte
+//                      swizzled, K-major) A and E tiles, 12 MMAs per
+//                      16-frequency step, tcgen05.ld, BF16 hi/lo, staged per warp
+//                      and stored as full lines of each channel's consecutive
+//                      rows into prod [u][hi, lo][part][C][Lh] of (re, im) pairs
+//                      (Lh rows per part, a multiple of 16). Two row parts when that lets two
+//                      blocks share an SM (256 TMEM columns, ~107 KB of shared
+//                      memory each), so one block's loads, products and stores
+//                      overlap the other's.
 //   k_rt_transpose     prod -> table [c][hi, lo][L][column 2u + (re, im)] (or
 //                      planar: Re at column u, Im at row_words + u), the layout
 //                      the back-projection streams (u innermost)
@@ -98,9 +102,10 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
     __shared__ __align__(8) uint64_t bar_tma, bar_mma;
     __shared__ uint32_t tmem_slot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c0 = blockIdx.x * 128, u = blockIdx.y;
+    const int c0 = blockIdx.x * 128, u = blockIdx.y, h = blockIdx.z;
     const uint32_t a_tile = 128 * 128;                 // one plane x 64-frequency atom of A
-    const uint32_t b_tile = (uint32_t)ra.Lp * 128;     // of E
+    const uint32_t b_tile = (uint32_t)ra.Lh * 128;     // of E (this part's rows)
+    const uint32_t tcols = 2 * ra.Lh > 256 ? 512 : (2 * ra.Lh > 128 ? 256 : 128);
     unsigned char *As = smem;
     unsigned char *Bs = smem + 4 * ra.natoms * a_tile;
 
@@ -110,7 +115,7 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
         tc05::fence_mbar_init();
     }
     if (warp == 0) {
-        tc05::tmem_alloc(&tmem_slot, 512);
+        tc05::tmem_alloc(&tmem_slot, tcols);
         tc05::tmem_relinquish();
     }
     tc05::fence_before_sync();
@@ -132,7 +137,7 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
                 asm volatile(
                     "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
                     "[%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(tc05::smem_addr(Bs + t * b_tile)),
-                    "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(64 * at), "r"(0), "r"(4 * u + p),
+                    "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(64 * at), "r"(h * ra.Lh), "r"(4 * u + p),
                     "r"(tc05::smem_addr(&bar_tma))
                     : "memory");
             }
@@ -140,7 +145,7 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
         if (ok) {
             tc05::fence_after_sync();
             const uint32_t id = ra.idesc, idn = ra.idesc | (1u << 13);   // negate A
-            const uint32_t dre = tmem, dim = tmem + ra.Lp;
+            const uint32_t dre = tmem, dim = tmem + ra.Lh;
             for (int ks = 0; ks < ra.natoms * 4; ++ks) {
                 const int at = ks >> 2;
                 const uint32_t ko = (ks & 3) * 32;
@@ -177,54 +182,55 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
     __syncwarp();
     bool done = tc05::mbar_wait(&bar_mma, 0, ra.budget);
     done = __all_sync(0xffffffffu, done);
-    // the TMA-written operand tiles are dead now: stage the output there
-    uint32_t *st_hi = reinterpret_cast<uint32_t *>(smem);
-    uint32_t *st_lo = st_hi + 128 * ra.Lp;
-    const int r = 32 * warp + lane;
+    // output in 32-row chunks: each thread (one channel: its TMEM lane)
+    // converts its rows to BF16 hi/lo pairs and puts them in its warp's
+    // staging rows (33 words apart: conflict-free), then the warp writes one
+    // channel's 32 consecutive rows per store instruction (a full 128-byte
+    // line of prod, where a channel's rows are contiguous). The operand tiles
+    // are dead by now and hold the staging.
+    const int rows_here = min(ra.Lh, ra.L - h * ra.Lh);     // table rows of this part
     if (done) {
         tc05::fence_after_sync();
         const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-        for (int i0 = 0; i0 < ra.L; i0 += 16) {
-            uint32_t vr[16], vi[16];
-            tc05::tmem_ld16(lane_base + i0, vr);
-            tc05::tmem_ld16(lane_base + ra.Lp + i0, vi);
-            tc05::tmem_wait_ld();
+        uint32_t *st = reinterpret_cast<uint32_t *>(smem) + warp * (2 * 32 * 33);
+        const int cw = c0 + 32 * warp;                       // the warp's first channel
+        uint32_t *g_hi = prod + ((size_t)(2 * u + 0) * ra.nh + h) * ra.C * ra.Lh;
+        uint32_t *g_lo = prod + ((size_t)(2 * u + 1) * ra.nh + h) * ra.C * ra.Lh;
+        for (int i0 = 0; i0 < rows_here; i0 += 32) {
+            const int nrow = min(32, ra.Lh - i0);            // 16 or 32 columns of the part
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int i = i0 + j;
-                if (i >= ra.L) break;
-                const float re = __uint_as_float(vr[j]), im = __uint_as_float(vi[j]);
-                __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
-                const float2 hf = __bfloat1622float2(h);
-                __nv_bfloat162 l = __floats2bfloat162_rn(re - hf.x, im - hf.y);
-                st_hi[r * ra.Lp + i] = *reinterpret_cast<uint32_t *>(&h);
-                st_lo[r * ra.Lp + i] = *reinterpret_cast<uint32_t *>(&l);
+            for (int half = 0; half < 2; ++half) {
+                if (16 * half >= nrow) break;
+                uint32_t vr[16], vi[16];
+                tc05::tmem_ld16(lane_base + i0 + 16 * half, vr);
+                tc05::tmem_ld16(lane_base + ra.Lh + i0 + 16 * half, vi);
+                tc05::tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float re = __uint_as_float(vr[j]), im = __uint_as_float(vi[j]);
+                    __nv_bfloat162 hv = __floats2bfloat162_rn(re, im);
+                    const float2 hf = __bfloat1622float2(hv);
+                    __nv_bfloat162 l = __floats2bfloat162_rn(re - hf.x, im - hf.y);
+                    st[lane * 33 + 16 * half + j] = *reinterpret_cast<uint32_t *>(&hv);
+                    st[32 * 33 + lane * 33 + 16 * half + j] = *reinterpret_cast<uint32_t *>(&l);
+                }
             }
+            __syncwarp();
+            if (lane < nrow) {
+                for (int rr = 0; rr < 32 && cw + rr < ra.C; ++rr) {
+                    const size_t o = (size_t)(cw + rr) * ra.Lh + i0 + lane;
+                    g_hi[o] = st[rr * 33 + lane];
+                    g_lo[o] = st[32 * 33 + rr * 33 + lane];
+                }
+            }
+            __syncwarp();
         }
     } else if (lane == 0) {
         atomicOr(err, 2);
     }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0 && done) {
-        const int rows = min(128, ra.C - c0);
-        const uint32_t bytes = (uint32_t)rows * ra.Lp * 4;
-        uint32_t *g_hi = prod + ((size_t)(2 * u + 0) * ra.C + c0) * ra.Lp;
-        uint32_t *g_lo = prod + ((size_t)(2 * u + 1) * ra.C + c0) * ra.Lp;
-        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(
-                         reinterpret_cast<uint64_t>(g_hi)),
-                     "r"(tc05::smem_addr(st_hi)), "r"(bytes)
-                     : "memory");
-        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(
-                         reinterpret_cast<uint64_t>(g_lo)),
-                     "r"(tc05::smem_addr(st_lo)), "r"(bytes)
-                     : "memory");
-        asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
-        asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
-    }
     tc05::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc05::tmem_dealloc(tmem, 512);
+    if (warp == 0) tc05::tmem_dealloc(tmem, tcols);
 }
 
 // prod [u][plane][C][Lp] (uint32 = (re, im) BF16 pair) -> table [c][plane][L][u]:
@@ -234,7 +240,7 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
 template <bool PLANAR>
 __global__ void __launch_bounds__(256)
 k_rt_transpose(const uint32_t *__restrict__ prod, uint32_t *__restrict__ table, int C, int L,
-               int Lp, int Np, int row_words) {
+               int nh, int Lh, int Np, int row_words) {
     __shared__ uint32_t s[64][65];
     const int i0 = blockIdx.x * 64, u0 = blockIdx.y * 64;
     const int cp = blockIdx.z;                 // c * 2 + plane
@@ -243,8 +249,12 @@ k_rt_transpose(const uint32_t *__restrict__ prod, uint32_t *__restrict__ table, 
     for (int k = r0; k < 64; k += 16) {
         const int u = u0 + k, i = i0 + 4 * q;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (u < Np && i < Lp)
-            v = *reinterpret_cast<const uint4 *>(prod + ((size_t)(2 * u + p) * C + c) * Lp + i);
+        if (u < Np && i < nh * Lh) {
+            // row i lives in part i / Lh (Lh is a multiple of 4: a uint4 stays in one part)
+            const int hp = i / Lh;
+            v = *reinterpret_cast<const uint4 *>(
+                prod + (((size_t)(2 * u + p) * nh + hp) * C + c) * Lh + (i - hp * Lh));
+        }
         s[k][4 * q + 0] = v.x;
         s[k][4 * q + 1] = v.y;
         s[k][4 * q + 2] = v.z;
@@ -272,9 +282,7 @@ k_rt_transpose(const uint32_t *__restrict__ prod, uint32_t *__restrict__ table, 
 }  // namespace
 
 size_t range_table_tc_smem_bytes(const RtTcArgs &ra) {
-    const size_t ops = (size_t)4 * ra.natoms * (128 * 128 + (size_t)ra.Lp * 128);
-    const size_t stage = (size_t)2 * 128 * ra.Lp * 4;
-    return 1024 + (ops > stage ? ops : stage);
+    return 1024 + (size_t)4 * ra.natoms * (128 * 128 + (size_t)ra.Lh * 128);
 }
 
 cudaError_t launch_setup_rt_E(const NufftDesc &d, double dz, const double *k, const double *kc,
@@ -301,16 +309,16 @@ cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
     e = cudaFuncSetAttribute(k_range_table_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((ra.C + 127) / 128, ra.Np);
+    dim3 grid((ra.C + 127) / 128, ra.Np, ra.nh);
     k_range_table_tc<<<grid, 128, smem, st>>>(ra, tmA, tmB, (uint32_t *)prod, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 tg((ra.L + 63) / 64, (row_words + 63) / 64, 2 * ra.C);
     if (planar)
         k_rt_transpose<true><<<tg, 256, 0, st>>>((const uint32_t *)prod, (uint32_t *)table, ra.C,
-                                                 ra.L, ra.Lp, ra.Np, row_words);
+                                                 ra.L, ra.nh, ra.Lh, ra.Np, row_words);
     else
         k_rt_transpose<false><<<tg, 256, 0, st>>>((const uint32_t *)prod, (uint32_t *)table, ra.C,
-                                                  ra.L, ra.Lp, ra.Np, row_words);
+                                                  ra.L, ra.nh, ra.Lh, ra.Np, row_words);
     return cudaGetLastError();
 }
