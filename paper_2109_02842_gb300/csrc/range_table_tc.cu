@@ -249,7 +249,7 @@ k_rt_transpose(const uint32_t *__restrict__ prod, uint32_t *__restrict__ table, 
     for (int k = r0; k < 64; k += 16) {
         const int u = u0 + k, i = i0 + 4 * q;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (u < Np && i < nh * Lh) {
+        if (u < Np && i < L) {         // padding rows of the parts are never read
             // row i lives in part i / Lh (Lh is a multiple of 4: a uint4 stays in one part)
             const int hp = i / Lh;
             v = *reinterpret_cast<const uint4 *>(
