@@ -35,6 +35,16 @@ int tc_npar(int ut, int npl, int ks, bool planar) {
     if (tc_cols(ut, 3, npl, ks, planar) <= 512) return 3;
     return 0;
 }
+// The layout fits: tensor memory, and two slot groups of table windows in
+// shared memory (npl 4: hi/lo planes).
+bool tc_fits(int ut, int npl, int ks, bool planar) {
+    const int npar = tc_npar(ut, npl, ks, planar);
+    if (npar == 0) return false;
+    const int N = planar ? ut : 2 * ut;
+    const size_t cb = (size_t)(npl == 4 ? 2 : 1) * 16 * ks * 128;
+    const size_t slot = (size_t)(planar ? 2 : 1) * ((N + 63) / 64) * cb;
+    return 1024 + 2 * npar * slot + 512 <= 227 * 1024;
+}
 // Bins per block: the fewest blocks that the largest 1-block-per-SM tile
 // allows, split evenly (multiple of 8): N_p = 200 -> 2 x 104, 128 -> 2 x 64.
 int tc_auto_tile(int np, int npl, int ks) {
@@ -403,11 +413,12 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
             if (ks == 0)
                 return fail(PL_ERR_UNSUPPORTED,
                             "a 16 x 8 pixel tile spans more than 32 table rows (grid too coarse for block_config 4)");
-            if (tc_npar(P->tile_u, npl, ks, P->tc.planar != 0) != 0) break;
+            if (tc_fits(P->tile_u, npl, ks, P->tc.planar != 0)) break;
             if (attempt > 1 || o.tile_u != 0)
                 return fail(PL_ERR_UNSUPPORTED, "tile_u too large for tensor memory");
-            // the planar layout does not fit (too many bins, or two K steps):
-            // interleaved blocks of bins, sized for ks, and their band
+            // the planar layout does not fit (too many bins, or two K steps,
+            // for tensor or shared memory): interleaved blocks of bins, sized
+            // for ks, and their band
             P->tc.planar = 0;
             P->tile_u = tc_auto_tile(P->Np, npl, ks);
             const pl_status bs = band(P->tile_u);
