@@ -271,11 +271,19 @@ def test_full_size_sampled_columns(binding, which):
 
 # --- tensor cores (block_config 4: tcgen05, TMEM accumulators, TMA windows) -------
 
-@pytest.mark.parametrize("case", ["small_mono", "small_multi", "ragged", "tile16", "tile48"])
+@pytest.mark.parametrize("case", ["small_mono", "small_multi", "ragged", "npad45", "tile16",
+                                  "tile48"])
 def test_tensor_core_variant_small(binding, case):
+    # small_mono, small_multi, ragged, npad45: planar layout (all bins in one
+    # block, two channel parts; npad45 pads 45 bins to 48, ragged has voxel
+    # heights off the scan grid: the direct inverse DFT adds the two spectra);
+    # tile16, tile48: interleaved blocks of bins
     opts = {}
     if case == "small_multi":
         w = small_multi()
+    elif case == "npad45":
+        w = wl.small_mono(seed=4)
+        w.n_pad = 45
     elif case == "ragged":
         w = wl.small_mono(seed=3)
         w.grid = dict(w.grid, nx=37, ny=23, nz=7, z0=-0.031, dz=0.0093)
@@ -286,8 +294,10 @@ def test_tensor_core_variant_small(binding, case):
     echo = scene_echo(w)
     plan, img = run_gpu(binding, w, echo, block_config=4, **opts)
     i = plan.info
-    print("%s: tile_u %s, window rows %d, table rows %d" % (case, opts.get("tile_u", "auto"),
+    print("%s: tile_u %d, window rows %d, table rows %d" % (case, i["tile_u"],
                                                           i["slab_rows"], i["table_len"]))
+    if "tile_u" not in opts:                 # planar: one block holds every bin
+        assert i["tile_u"] >= w.n_pad and i["tile_u"] % 16 == 0
     assert i["nufft_w"] == 6 and i["slab_rows"] in (16, 32)
     ref = image_ref(w, echo)
     assert report("image tc %s" % case, img.reshape(w.grid["nz"], -1), ref) < TOL_FP32
