@@ -157,9 +157,10 @@ def tc_flops_per_launch(info: dict, precision: int) -> float:
 
 
 def backproject_flops_per_update(w_taps: int) -> int:
-    # w complex-by-real MACs (4w flop) + carrier phase product (1) +
-    # complex multiply-accumulate (8); the sine/cosine pair is 2 MUFU ops.
-    return 4 * w_taps + 9
+    # w complex-by-real MACs (4w flop) + complex multiply-accumulate by the
+    # carrier (8); the carrier's phase and sine/cosine pair are formed once per
+    # (pixel, channel) and shared by the block's bins.
+    return 4 * w_taps + 8
 
 
 def oracle_baseline(w, echo_np, gpu_image=None, n_cols=256, n_chan=None, seed=1):
@@ -285,7 +286,7 @@ def run_batch64(args, world, rank, local):
             "gpu_launches": best["info"]["launches_per_execute"] * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                         "kernel": "whole batch, FP32-equivalent rate (33 flop per update)"
+                         "kernel": "whole batch, FP32-equivalent rate (32 flop per update)"
                                    + ("; tensor-core back-projection" if tc else
                                       "; persistent FP32 kernel")},
             "batch_info": best["info"]}
@@ -495,7 +496,7 @@ def main():
                     "flop_per_launch": fp32_flops,
                     "peak_basis": "FP32: 152 SM x 128 lanes x 2 flop x 2070 MHz (recipe unit "
                                   "counts and max clock)",
-                    "mufu_frac": (2 * pix_updates / bp_avg_s) /
+                    "mufu_frac": (2 * pix_updates / max(info["tile_u"], 1) / bp_avg_s) /
                                  (N_SM * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6)}
     stage_avg = {k: v[0] / max(v[1], 1) for k, v in stage.items()}
 

@@ -1,11 +1,12 @@
 // Back-projection, step (8b) / (19b) of the paper, with the coherent sum over
 // every channel (all sections) and the k_z tile of one block:
 //
-//   G_u(x,y) = sum_c  e^{j kappa_c,u a_c(x,y)}  sum_{t<w} phi(a_c - l_{i0+t}) b_c[i0+t][u]
+//   G_u(x,y) = sum_c  e^{j kappa_T a_c(x,y)}  sum_{t<w} phi(a_c - l_{i0+t}) b_c[i0+t][u]
 //
 // a_c = rho (monostatic) or rho_T + rho_R (multistatic), phi the ES kernel on
 // the table grid l_i = l0 + i h (setup.cu explains the factorisation; the
-// table already carries the factor h).
+// table already carries the factor h), kappa_T the band centre of the block's
+// UT bins (the range table is built about it for each of them).
 //
 // Block = (16 PX) x 16 pixels x UT consecutive k_z bins; thread = PX
 // x-adjacent pixels with their UT bins in registers. With PX = 2 the two
@@ -18,20 +19,21 @@
 // buffered) while chunk k is computed. Per chunk:
 //  * the plan-time geometry of (tile, channel) gives the range a* of the tile
 //    centre as a float pair and the first row i_lo of the R-row window;
-//  * phi_c,u = kappa_c,u a* mod 2 pi is formed once per (block, channel, bin)
-//    as a float-float product with a two-constant reduction (Dekker /
-//    Cody-Waite; phases reach ~2e3 rad, the result is good to ~3e-7 rad);
+//  * phi_c = kappa_T a* mod 2 pi is formed once per (block, channel) as a
+//    float-float product with a two-constant reduction (Dekker / Cody-Waite;
+//    phases reach ~2e3 rad, the result is good to ~3e-7 rad);
 //  * per pixel: delta = a - a* in FP32 without cancellation (difference of
 //    squares against the tile centre), tap weights from per-tap polynomials
-//    of the ES kernel (fitted at plan time), then for each pair of bins:
-//    w 128-bit shared loads, the interpolation, the carrier
-//    e^{j (kappa_c,u delta + phi_c,u)} (|arg| < ~70 rad, FP32 sin/cos) and
-//    the complex multiply-accumulate, all as packed FP32x2 operations.
+//    of the ES kernel (fitted at plan time), the carrier
+//    e^{j (kappa_T delta + phi_c)} (|arg| < ~70 rad, one FP32 sin/cos pair for
+//    all bins), then for each pair of bins: w 128-bit shared loads, the
+//    interpolation and the complex multiply-accumulate, as packed FP32x2
+//    operations.
 //
 // The table holds bins in planar pairs {re_u, re_u+1, im_u, im_u+1}, so one
 // shared load feeds two bins and the complex multiply-accumulate needs no
 // shuffles: with X = (re_u, re_u+1), Y = (im_u, im_u+1) interpolated and
-// C, S the cosines and sines of the two carriers, Re += X.C - Y.S and
+// C, S the cosine and sine of the carrier, Re += X.C - Y.S and
 // Im += X.S + Y.C as four FP32x2 FMAs into two FP32x2 accumulators.
 #include "bp_body.cuh"
 

@@ -143,16 +143,12 @@ __device__ __forceinline__ void bp_tile(const BpDesc &p, const CoefTable &ct,
             cp_wait<0>();
         }
         __syncthreads();
-        // per (channel, bin pair): kappa and the reference phase
-        for (int idx = threadIdx.x; idx < ncc * NP; idx += blockDim.x) {
-            const int cl = idx / NP;
-            const int q = idx - cl * NP;
+        // per channel: the band centre kappa_T shared by the block's bins
+        // (the table is built about it) and its reference phase at a*
+        const float2 kT = kc_hl[u0];
+        for (int cl = threadIdx.x; cl < ncc; cl += blockDim.x) {
             const TileGeo &g = geo[buf * CC + cl];
-            const int u = u0 + 2 * q;
-            const float2 k0 = u < p.n_pad ? kc_hl[u] : f2(0.f, 0.f);
-            const float2 k1 = u + 1 < p.n_pad ? kc_hl[u + 1] : f2(0.f, 0.f);
-            kphi[cl * NP + q] = make_float4(k0.x, k1.x, phase_ff(k0.x, k0.y, g.a_hi, g.a_lo),
-                                            phase_ff(k1.x, k1.y, g.a_hi, g.a_lo));
+            kphi[cl * NP] = make_float4(kT.x, phase_ff(kT.x, kT.y, g.a_hi, g.a_lo), 0.f, 0.f);
         }
         if (p.bf16) {
             for (int idx = threadIdx.x; idx < ncc * p.R * NP; idx += blockDim.x) {
@@ -219,7 +215,18 @@ __device__ __forceinline__ void bp_tile(const BpDesc &p, const CoefTable &ct,
                 }
             }
             const float4 *row = slab_b + (cl * p.R + base) * RS;
-            const float4 *kp = kphi + cl * NP;
+            // the carrier e^{j kappa_T a} of each pixel: one sin/cos pair per
+            // (pixel, channel), shared by all the block's bins
+            const float4 kk = kphi[cl * NP];
+            float2 C[PX], S[PX], nS[PX];
+#pragma unroll
+            for (int k = 0; k < PX; ++k) {
+                float sv, cv;
+                __sincosf(fmaf(kk.x, delta[k], kk.y), &sv, &cv);
+                C[k] = f2(cv, cv);
+                S[k] = f2(sv, sv);
+                nS[k] = f2(-sv, -sv);
+            }
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
                 float2 X[PX], Y[PX];
@@ -234,17 +241,10 @@ __device__ __forceinline__ void bp_tile(const BpDesc &p, const CoefTable &ct,
                         Y[k] = __ffma2_rn(wt[k][t], f2(b.z, b.w), Y[k]);
                     }
                 }
-                const float4 kk = kp[q];
 #pragma unroll
                 for (int k = 0; k < PX; ++k) {
-                    const float2 arg = __ffma2_rn(f2(kk.x, kk.y), f2(delta[k], delta[k]),
-                                                  f2(kk.z, kk.w));
-                    float s0, c0, s1, c1;
-                    __sincosf(arg.x, &s0, &c0);
-                    __sincosf(arg.y, &s1, &c1);
-                    const float2 C = f2(c0, c1), S = f2(s0, s1), nS = f2(-s0, -s1);
-                    aRe[k][q] = __ffma2_rn(Y[k], nS, __ffma2_rn(X[k], C, aRe[k][q]));
-                    aIm[k][q] = __ffma2_rn(Y[k], C, __ffma2_rn(X[k], S, aIm[k][q]));
+                    aRe[k][q] = __ffma2_rn(Y[k], nS[k], __ffma2_rn(X[k], C[k], aRe[k][q]));
+                    aIm[k][q] = __ffma2_rn(Y[k], C[k], __ffma2_rn(X[k], S[k], aIm[k][q]));
                 }
             }
         }

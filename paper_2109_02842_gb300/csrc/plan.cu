@@ -349,7 +349,9 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         return PL_OK;
     };
     {
-        const pl_status bs = band(P->block_config == 4 ? P->tile_u : 1);
+        // one band centre per block of tile_u bins, for every kernel: the
+        // carrier is then one sin/cos per (pixel, channel), not per bin
+        const pl_status bs = band(P->tile_u);
         if (bs != PL_OK) return bs;
     }
 
