@@ -38,7 +38,7 @@ FP32_LANES_PER_SM = 128
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 MUFU_PER_SM_CLK = 16
-CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+CLOCK_QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -46,7 +46,7 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", type=int, default=0)
@@ -93,7 +93,9 @@ def kernel_traffic(kernel: str, workload: str):
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples during the timed region."""
+    """nvidia-smi clock / throttle samples (every 20 ms) during the timed
+    region: samples stamped outside [t_begin, t_end] (host wall clock) are
+    dropped."""
 
     def __init__(self, index: int, path: str):
         self.path = path
@@ -102,15 +104,18 @@ class ClockSampler:
             self.f = open(path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(index), "--query-gpu=" + CLOCK_QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)          # nvidia-smi is polling before the region starts
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t_begin: float, t_end: float):
+        """Median SM clock and throttle reasons over the samples stamped in
+        [t_begin, t_end] (time.time() values)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        time.sleep(0.25)
+        time.sleep(0.1)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -118,23 +123,30 @@ class ClockSampler:
             self.proc.kill()
         self.f.close()
         sm, smax, reasons = [], [], set()
-        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
-                 "sw_power_cap"]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        total = 0
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
+                stamp = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                stamp += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                clk, clk_max = float(parts[2]), float(parts[3])
+            except (ValueError, IndexError):
                 continue
-            for n, v in zip(names[1:], parts[5:9]):
+            total += 1
+            if not (t_begin - 0.02 <= stamp <= t_end + 0.02):
+                continue
+            sm.append(clk)
+            smax.append(clk_max)
+            for n, v in zip(names, parts[6:10]):
                 if v.lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "samples_outside_region": total - len(sm), "interval_ms": 20}
 
 
 def dtype_of(info: dict, precision: int) -> str:
@@ -417,6 +429,7 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    t_begin = time.time()
     for i in range(args.steps):
         flush.zero_()                       # L2 flush between steps, outside the events
         starts[i].record(stream)
@@ -426,7 +439,7 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     wall = time.perf_counter() - t0
-    clk = clocks.stop()
+    clk = clocks.stop(t_begin, time.time())
     stage = plan.stage_times()
     plan.set_timing(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
