@@ -187,9 +187,14 @@ pl_status pl_execute_host(pl_plan *plan, const void *echo_host, void *image_host
  * copy engines (two internal streams) while scan i is reconstructed on
  * `stream`. Each image is the one pl_execute gives for its echo. The first
  * call allocates a second pair of device staging buffers (workspace grows by
- * the echo and image sizes). Synchronises `stream` before returning; the host
- * buffers should be pinned (pageable memory gives correct results without the
- * overlap). n_scans = 0 is a no-op; a NULL array or entry is PL_ERR_ARG. */
+ * the echo and image sizes); the first call with two or more scans also
+ * builds a second plan from the same inputs (its own workspace, so the
+ * plan's device memory roughly doubles) that takes every other scan on an
+ * internal stream, so that consecutive scans' kernels share the device.
+ * Call it with the plan's device current. Synchronises `stream` before
+ * returning; the host buffers should be pinned (pageable memory gives correct
+ * results without the overlap). n_scans = 0 is a no-op; a NULL array or entry
+ * is PL_ERR_ARG. */
 pl_status pl_execute_host_stream(pl_plan *plan, int n_scans, const void *const *echo_host,
                                  void *const *image_host, void *stream);
 

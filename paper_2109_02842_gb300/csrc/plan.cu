@@ -816,6 +816,32 @@ static pl_status prepare_comparison(pl_plan *P) {
     return PL_OK;
 }
 
+// Deep copy of the creation inputs into P->inputs.
+static void store_inputs(pl_plan *P, const pl_geometry *g, const pl_scan *s, const pl_freqs *f,
+                         const pl_grid *gr, const pl_options *opt) {
+    PlanInputs &in = P->inputs;
+    in.g = *g;
+    in.s = *s;
+    in.f = *f;
+    in.gr = *gr;
+    in.has_opts = opt != nullptr;
+    if (opt) in.o = *opt;
+    in.elem_xy.assign(g->elem_xy, g->elem_xy + 2 * (size_t)g->n_elem);
+    in.g.elem_xy = in.elem_xy.data();
+    if (g->elem_section) {
+        in.elem_section.assign(g->elem_section, g->elem_section + g->n_elem);
+        in.g.elem_section = in.elem_section.data();
+    }
+    if (g->mode == 1 && g->n_pairs > 0) {
+        in.pair_tx.assign(g->pair_tx, g->pair_tx + g->n_pairs);
+        in.pair_rx.assign(g->pair_rx, g->pair_rx + g->n_pairs);
+        in.g.pair_tx = in.pair_tx.data();
+        in.g.pair_rx = in.pair_rx.data();
+    }
+    in.f_hz.assign(f->f_hz, f->f_hz + f->n);
+    in.f.f_hz = in.f_hz.data();
+}
+
 extern "C" {
 
 const char *pl_status_string(pl_status s) {
@@ -856,6 +882,7 @@ pl_status pl_plan_create(pl_plan **out, const pl_geometry *geom, const pl_scan *
         if (!P) return fail(PL_ERR_OOM, "host allocation failed");
         s = build_plan(P, geom, scan, freqs, grid, &ot);
         if (s == PL_OK) {
+            store_inputs(P, geom, scan, freqs, grid, opt);
             *out = P;
             return PL_OK;
         }
@@ -869,6 +896,7 @@ pl_status pl_plan_create(pl_plan **out, const pl_geometry *geom, const pl_scan *
         delete P;
         return s;
     }
+    store_inputs(P, geom, scan, freqs, grid, opt);
     *out = P;
     return PL_OK;
 }
@@ -974,24 +1002,48 @@ pl_status pl_execute_host_stream(pl_plan *plan, int n_scans, const void *const *
     cudaStream_t st = (cudaStream_t)stream;
     float2 *din[2] = {plan->d_echo_in, plan->d_echo_in2};
     float2 *dout[2] = {plan->d_img_out, plan->d_img_out2};
-    // the copies start after the caller's earlier work on `stream`
+    // odd scans go to the twin plan on its own stream, so that consecutive
+    // scans' kernels can share the device (one scan's back-projection leaves
+    // SMs idle in its last wave; the other stages leave the tensor cores idle)
+    pl_plan *pp[2] = {plan, plan};
+    cudaStream_t sc[2] = {st, st};
+    if (n_scans >= 2) {
+        if (!plan->twin) {
+            const PlanInputs &in = plan->inputs;
+            pl_plan *T = nullptr;
+            const pl_status s = pl_plan_create(&T, &in.g, &in.s, &in.f, &in.gr,
+                                               in.has_opts ? &in.o : nullptr);
+            if (s != PL_OK) return s;
+            plan->twin = T;
+            plan->workspace += T->workspace;
+            PL_CUDA(cudaStreamCreateWithFlags(&plan->s_twin, cudaStreamNonBlocking), "stream");
+        }
+        if (take_device_timeout(plan->twin) != PL_OK) return PL_ERR_TIMEOUT;
+        pp[1] = plan->twin;
+        sc[1] = plan->s_twin;
+    }
+    // the copies and the twin's stream start after the caller's earlier work
     PL_CUDA(cudaEventRecord(plan->ev_start, st), "event");
     PL_CUDA(cudaStreamWaitEvent(plan->s_h2d, plan->ev_start, 0), "wait");
     PL_CUDA(cudaStreamWaitEvent(plan->s_d2h, plan->ev_start, 0), "wait");
+    if (sc[1] != st) PL_CUDA(cudaStreamWaitEvent(sc[1], plan->ev_start, 0), "wait");
     // two-deep pipeline: the upload of scan i+1 and the download of scan i-1
-    // run on the copy engines while scan i is reconstructed on `stream`
+    // run on the copy engines while scan i is reconstructed (on the stream of
+    // its parity); scans i and i + 2 share a plan, a stream and the staging
+    // pair, so each waits for the other's copies through events
     for (int i = 0; i < n_scans; ++i) {
         const int b = i & 1;
+        cudaStream_t sb = sc[b];
         if (i >= 2) PL_CUDA(cudaStreamWaitEvent(plan->s_h2d, plan->ev_done[b], 0), "wait");
         PL_CUDA(cudaMemcpyAsync(din[b], echo_host[i], in_bytes, cudaMemcpyHostToDevice,
                                 plan->s_h2d),
                 "copy echo");
         PL_CUDA(cudaEventRecord(plan->ev_in[b], plan->s_h2d), "event");
-        PL_CUDA(cudaStreamWaitEvent(st, plan->ev_in[b], 0), "wait");
-        if (i >= 2) PL_CUDA(cudaStreamWaitEvent(st, plan->ev_out[b], 0), "wait");
-        pl_status s = run(plan, din[b], dout[b], st);
+        PL_CUDA(cudaStreamWaitEvent(sb, plan->ev_in[b], 0), "wait");
+        if (i >= 2) PL_CUDA(cudaStreamWaitEvent(sb, plan->ev_out[b], 0), "wait");
+        pl_status s = run(pp[b], din[b], dout[b], sb);
         if (s != PL_OK) return s;
-        PL_CUDA(cudaEventRecord(plan->ev_done[b], st), "event");
+        PL_CUDA(cudaEventRecord(plan->ev_done[b], sb), "event");
         PL_CUDA(cudaStreamWaitEvent(plan->s_d2h, plan->ev_done[b], 0), "wait");
         PL_CUDA(cudaMemcpyAsync(image_host[i], dout[b], out_bytes, cudaMemcpyDeviceToHost,
                                 plan->s_d2h),
@@ -1000,6 +1052,7 @@ pl_status pl_execute_host_stream(pl_plan *plan, int n_scans, const void *const *
     }
     PL_CUDA(cudaStreamWaitEvent(st, plan->ev_out[(n_scans - 1) & 1], 0), "wait");
     PL_CUDA(cudaStreamSynchronize(st), "execute_host_stream");
+    if (plan->twin && take_device_timeout(plan->twin) != PL_OK) return PL_ERR_TIMEOUT;
     return take_device_timeout(plan);
 }
 

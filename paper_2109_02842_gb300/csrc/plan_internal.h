@@ -10,6 +10,19 @@
 #include "common.cuh"
 #include "kernels.h"
 
+// The inputs a plan was created from (deep copies: the pointers of the
+// structs point into the vectors), so that a second plan can be built alike.
+struct PlanInputs {
+    pl_geometry g{};
+    pl_scan s{};
+    pl_freqs f{};
+    pl_grid gr{};
+    pl_options o{};
+    bool has_opts = false;
+    std::vector<double> elem_xy, f_hz;
+    std::vector<int> elem_section, pair_tx, pair_rx;
+};
+
 struct pl_plan {
     // problem
     int mode = 0, C = 0, N = 0, Np = 0, M = 0;
@@ -56,6 +69,11 @@ struct pl_plan {
     float2 *d_echo_in2 = nullptr, *d_img_out2 = nullptr;
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     cudaEvent_t ev_in[2]{}, ev_done[2]{}, ev_out[2]{}, ev_start = nullptr;
+    // ... and the second plan (same inputs, own workspace) and device stream
+    // that take every other scan, so that consecutive scans overlap
+    PlanInputs inputs;
+    pl_plan *twin = nullptr;
+    cudaStream_t s_twin = nullptr;
     // comparison algorithms (exact sum, direct BP), set up on first use
     std::vector<double> h_chxy, h_k;                      // [C][4] positions, [M] k
     float2 *d_kap = nullptr, *d_zs = nullptr, *d_kff = nullptr;
@@ -84,6 +102,8 @@ struct pl_plan {
             if (e) cudaEventDestroy(e);
         if (s_h2d) cudaStreamDestroy(s_h2d);
         if (s_d2h) cudaStreamDestroy(s_d2h);
+        if (s_twin) cudaStreamDestroy(s_twin);
+        delete twin;
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         if (h_err) cudaFreeHost(h_err);
     }
