@@ -543,7 +543,8 @@ def main():
                 "d2h_bytes_per_step": int(image.numel() * 8),
                 "scans_per_s": world / e2e_s,
                 "api": "pl_execute_host_stream over %d scans (pinned host buffers, "
-                       "copies overlapped with compute)" % args.steps,
+                       "copies overlapped with compute, alternate scans on two "
+                       "plans and streams)" % args.steps,
                 "single_scan_latency_ms": lat_s * 1e3},
         "gpu_launches": info["launches_per_execute"] * args.steps,
         "roofline": roofline,
