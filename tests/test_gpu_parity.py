@@ -271,19 +271,25 @@ def test_full_size_sampled_columns(binding, which):
 
 # --- tensor cores (block_config 4: tcgen05, TMEM accumulators, TMA windows) -------
 
-@pytest.mark.parametrize("case", ["small_mono", "small_multi", "ragged", "npad45", "tile16",
-                                  "tile48"])
+@pytest.mark.parametrize("case", ["small_mono", "small_multi", "ragged", "npad45", "fine128",
+                                  "tile16", "tile48"])
 def test_tensor_core_variant_small(binding, case):
     # small_mono, small_multi, ragged, npad45: planar layout (all bins in one
     # block, two channel parts; npad45 pads 45 bins to 48, ragged has voxel
     # heights off the scan grid: the direct inverse DFT adds the two spectra);
-    # tile16, tile48: interleaved blocks of bins
+    # fine128: a 2 mm grid (one 16-row window step) and 128 bins, one block
+    # per SM with three A buffers; tile16, tile48: interleaved blocks
     opts = {}
     if case == "small_multi":
         w = small_multi()
     elif case == "npad45":
         w = wl.small_mono(seed=4)
         w.n_pad = 45
+    elif case == "fine128":
+        w = wl.small_mono(seed=5)
+        w.n_pad = 128
+        x0, dx = wl.centred_axis(0.128, 64)
+        w.grid = dict(w.grid, x0=x0, dx=dx, nx=64, y0=x0, dy=dx, ny=64, nz=8)
     elif case == "ragged":
         w = wl.small_mono(seed=3)
         w.grid = dict(w.grid, nx=37, ny=23, nz=7, z0=-0.031, dz=0.0093)
@@ -298,6 +304,8 @@ def test_tensor_core_variant_small(binding, case):
                                                           i["slab_rows"], i["table_len"]))
     if "tile_u" not in opts:                 # planar: one block holds every bin
         assert i["tile_u"] >= w.n_pad and i["tile_u"] % 16 == 0
+    if case == "fine128":
+        assert i["tile_u"] == 128 and i["slab_rows"] == 16
     assert i["nufft_w"] == 6 and i["slab_rows"] in (16, 32)
     ref = image_ref(w, echo)
     assert report("image tc %s" % case, img.reshape(w.grid["nz"], -1), ref) < TOL_FP32
