@@ -176,8 +176,8 @@ def test_execute_host_matches_device(binding):
 
 
 def test_execute_host_stream_matches_device(binding):
-    # five different scans through the pipelined host path (two staging pairs,
-    # so buffers are reused twice) against one pl_execute each
+    # five different scans through the pipelined host path (two staging pairs
+    # and two plans, so each is reused) against one pl_execute each
     import ctypes
     w = wl.small_mono(seed=7)
     plan = binding.Plan.from_workload(w)
@@ -188,6 +188,15 @@ def test_execute_host_stream_matches_device(binding):
     plan.execute_host_stream(echoes, images)
     for a, b in zip(images, want):
         assert np.array_equal(a.numpy(), b)
+    # one scan (this plan only) and two scans (one each on this plan and on
+    # the second plan built from the same inputs), on a fresh plan
+    plan2 = binding.Plan.from_workload(w)
+    for n in (1, 2):
+        out = [torch.empty(plan2.image_shape, dtype=torch.complex64).pin_memory()
+               for _ in range(n)]
+        plan2.execute_host_stream(echoes[:n], out)
+        for a, b in zip(out, want[:n]):
+            assert np.array_equal(a.numpy(), b)
     assert plan.execute_host_stream([]) == []
     lib = binding.load()
     null = (ctypes.c_void_p * 1)(None)
