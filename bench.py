@@ -38,6 +38,8 @@ FP32_LANES_PER_SM = 128
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 MUFU_PER_SM_CLK = 16
+# the metric of both arms (the reference arm times the FP64 oracle on it)
+METRIC = "element-voxel-freq updates/s at rel. L2 err <= 1e-3 vs FP64 oracle"
 CLOCK_QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -212,6 +214,17 @@ def oracle_baseline(w, echo_np, gpu_image=None, n_cols=256, n_chan=None, seed=1)
     return out, err
 
 
+def workload_config(w, world, precision, l2):
+    """The `config` of both arms: the workload's name and sizes, the options
+    and how the timing treats the L2 cache."""
+    return {"workload": w.name, "mode": "monostatic" if w.mode == 0 else "multistatic",
+            "n_chan": int(w.n_chan), "n_scan": int(w.n_scan), "n_f": int(w.n_f),
+            "grid": [w.grid["nx"], w.grid["ny"], w.grid["nz"]], "n_pad": int(w.n_pad),
+            "precision": "fp32" if precision == 0 else "bf16-table",
+            "nufft_w": 6, "nufft_sigma": 2.0,
+            "parallelism": "replicas%d" % world, "l2": l2}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -233,11 +246,13 @@ def run_reference(args, world, rank):
     v = statistics.mean(vals)
     base = b
     base["value"] = v
-    line = {"impl": "reference", "metric": "element-voxel-freq updates/s (FP64 CPU oracle)",
+    line = {"impl": "reference", "metric": METRIC,
             "value": v, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name},
+            "data": "synthetic",
+            "config": workload_config(w, world, args.precision,
+                                      "CPU oracle on host cores (no GPU cache involved)"),
             "cpu_baseline": base,
             "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -282,7 +297,7 @@ def run_batch64(args, world, rank, local):
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     achieved = pix_upd * backproject_flops_per_update(6) / (best["ms_per_batch"] * 1e-3) / 1e12
     tc = best["info"]["block_config"] == 4
-    line = {"metric": "element-voxel-freq updates/s at rel. L2 err <= 1e-3 vs FP64 oracle",
+    line = {"metric": METRIC,
             "value": best["value"], "unit": "updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": best["ms_per_batch"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f32acc" if tc else "f32",
@@ -364,7 +379,7 @@ def run_table2(args, world, rank, local):
                      "block_config": plan.info["block_config"]}
         plan.close()
     m = out["mono"]
-    line = {"metric": "element-voxel-freq updates/s at rel. L2 err <= 1e-3 vs FP64 oracle",
+    line = {"metric": METRIC,
             "value": m["updates_per_s"], "unit": "updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": m["omegaK_NUFFT_BP_ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -524,19 +539,14 @@ def main():
         cpu, acc = oracle_baseline(w, e_np, img, n_cols=256)
 
     line = {
-        "metric": "element-voxel-freq updates/s at rel. L2 err <= 1e-3 vs FP64 oracle",
+        "metric": METRIC,
         "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(info, args.precision),
         "data": "synthetic",
-        "config": {"workload": w.name, "mode": "monostatic" if w.mode == 0 else "multistatic",
-                   "n_chan": info["n_chan"],
-                   "n_scan": info["n_scan"], "n_f": info["n_f"],
-                   "grid": [info["nx"], info["ny"], info["nz"]], "n_pad": info["n_pad"],
-                   "precision": "fp32" if args.precision == 0 else "bf16-table",
-                   "nufft_w": info["nufft_w"], "nufft_sigma": info["nufft_sigma"],
-                   "parallelism": "replicas%d" % world,
-                   "l2": "flushed before every step (256 MiB write, outside the step events)"},
+        "config": workload_config(w, world, args.precision,
+                                  "flushed before every step (256 MiB write, outside the "
+                                  "step events)"),
         "scans_per_s": world / (ms * 1e-3),
         "e2e": {"value": world * upd / e2e_s, "unit": "updates/s",
                 "h2d_bytes_per_step": int(echo.numel() * 8),
