@@ -93,7 +93,7 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
     lo = bf2(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xffff0000u));
 }
 
-template <int W, int KS, int SPLIT, int NPAR, bool PLANAR>
+template <int W, int KS, int SPLIT, int NPAR, bool PLANAR, int CPR>
 __global__ void __launch_bounds__(Warps<NPAR>::threads, NPAR == 2 ? 2 : 1)
 k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUtensorMap tmap,
                  const TileGeo *__restrict__ tgeo, const float2 *__restrict__ kc_hl,
@@ -112,7 +112,7 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
     // in slot group s landed (TMA); done[s]: that group's products completed
     // (frees the slot group); a_full[k]: A of class k written (its 4 warps);
     // a_done[k]: the products reading class k's A buffer completed.
-    const int NSG = ta.nst / NPAR;
+    const int NSG = ta.nst / (NPAR * CPR);
     uint64_t *b_full = reinterpret_cast<uint64_t *>(smem + (size_t)ta.nst * ta.slot_bytes);
     uint64_t *done = b_full + NSG;
     uint64_t *a_full = done + NSG;
@@ -161,16 +161,19 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
         const float ddx = ((float)px - 0.5f * (TCX - 1)) * p.dxf;
         const float ddy = ((float)py - 0.5f * (TCY - 1)) * p.dyf;
         const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
-        const uint32_t abuf = lane_base + ta.acol + par * (NPL * KS * 8);
+        // class par's round `it` takes channels cb + (it NPAR + par) CPR + j,
+        // j < CPR, into its A buffer (CPR channel slots)
+        const uint32_t abuf = lane_base + ta.acol + par * (CPR * NPL * KS * 8);
         const float2 kT = kc_hl[u0];
         bool ok = true;
-        int it = 0;
-        // the geometry of the class's next channel is loaded one round ahead
+        int it = 0, jc = 0;
+        // the geometry of the class's next channel is loaded one channel ahead
         TileGeo gn;
-        if (cb + par < ce) gn = tg[cb + par];
-        for (int c = cb + par; c < ce; c += NPAR, ++it) {
+        if (cb + par * CPR < ce) gn = tg[cb + par * CPR];
+        for (int c = cb + par * CPR; c < ce;) {
             const TileGeo g = gn;
-            if (c + NPAR < ce) gn = tg[c + NPAR];
+            const int cnext = jc + 1 < CPR ? c + 1 : c + 1 + (NPAR - 1) * CPR;
+            if (cnext < ce) gn = tg[cnext];
             // delta = a - a* from rho^2 - rho*^2 = d (2 D + d): no cancellation
             float ex = g.dxt + ddx, ey = g.dyt + ddy;
             float num = fmaf(ddx, 2.0f * g.dxt + ddx, ddy * (2.0f * g.dyt + ddy));
@@ -227,11 +230,15 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
 #pragma unroll
                 for (int pl = 0; pl < NPL; ++pl) place<NW, NT>(tw[pl], o >> 1, rows[pl]);
             }
-            // the products of this class's previous channel must be done
-            if (it > 0) ok = tc05::mbar_wait(&a_done[par], (uint32_t)(it - 1) & 1u, budget);
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) break;
-            tc05::fence_after_sync();
+            // before a round's first channel: the products of the class's
+            // previous round must be done
+            if (CPR == 1 || jc == 0) {
+                if (it > 0) ok = tc05::mbar_wait(&a_done[par], (uint32_t)(it - 1) & 1u, budget);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                tc05::fence_after_sync();
+            }
+            const int jslot = CPR == 1 ? 0 : jc;
 #pragma unroll
             for (int pl = 0; pl < NPL; ++pl)
 #pragma unroll
@@ -239,12 +246,21 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
                     uint32_t v[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) v[j] = rows[pl][8 * ks + j];
-                    tc05::tmem_st8(abuf + (pl * KS + ks) * 8, v);
+                    tc05::tmem_st8(abuf + ((jslot * NPL + pl) * KS + ks) * 8, v);
                 }
-            tc05::tmem_wait_st();
-            tc05::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) tc05::mbar_arrive(&a_full[par]);
+            // after the round's last channel its A is complete
+            const bool round_end = CPR == 1 || jc + 1 == CPR || cnext >= ce;
+            if (round_end) {
+                tc05::tmem_wait_st();
+                tc05::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc05::mbar_arrive(&a_full[par]);
+                jc = 0;
+                ++it;
+            } else {
+                ++jc;
+            }
+            c = cnext;
         }
         if (!ok && lane == 0) atomicOr(err, 1);
 
@@ -292,29 +308,33 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
         const uint64_t d0 = tc05::smem_desc_sw128(tc05::smem_addr(smem), ta.cb_bytes, 1024);
         const uint32_t slot16 = ta.slot_bytes >> 4;
         const uint32_t abase = tmem + ta.acol;
-        const int n_groups = (ce - cb + NPAR - 1) / NPAR;
+        constexpr int PG = NPAR * CPR;                       // channels per slot group
+        const int n_groups = (ce - cb + PG - 1) / PG;
         const uint32_t im16 = ta.im_off >> 4;              // Im B columns (planar)
         const uint32_t idn = ta.idesc | (1u << 13);        // negated A
         bool ok = true;
         int sg = 0;
         uint32_t bpar = 0;
         for (int g = 0; g < n_groups && ok; ++g) {
-            const int nch = min(NPAR, ce - cb - g * NPAR);
+            const int nleft = ce - cb - g * PG;              // channels of the group
             ok = tc05::mbar_wait(&b_full[sg], bpar, budget);
 #pragma unroll
             for (int k = 0; k < NPAR; ++k) {
-                if (k >= nch) break;
+                if (k * CPR >= nleft) break;
                 ok = ok && tc05::mbar_wait(&a_full[k], (uint32_t)g & 1u, budget);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 tc05::fence_after_sync();
                 if (lane == 0) {
-                    const uint32_t a0 = abase + k * (NPL * KS * 8);
-                    const uint64_t dk = d0 + (uint64_t)((sg * NPAR + k) * slot16);
+#pragma unroll
+                  for (int j = 0; j < CPR; ++j) {
+                    if (k * CPR + j >= nleft) break;
+                    const uint32_t a0 = abase + (k * CPR + j) * (NPL * KS * 8);
+                    const uint64_t dk = d0 + (uint64_t)(((sg * NPAR + k) * CPR + j) * slot16);
 #pragma unroll
                     for (int ks = 0; ks < KS; ++ks) {
                         const uint64_t bh = dk + (uint64_t)(ks * (2048 >> 4));
-                        const uint32_t acc = (g > 0 || k > 0 || ks > 0) ? 1u : 0u;
+                        const uint32_t acc = (g > 0 || k > 0 || j > 0 || ks > 0) ? 1u : 0u;
                         if (PLANAR) {
                             // Re G += Re A Re B - Im A Im B, Im G += Re A Im B + Im A Re B
                             const uint64_t bi = bh + im16;
@@ -354,6 +374,7 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
                             tc05::mma_ts(tmem + N, a0 + (KS + ks) * 8, bh, ta.idesc, acc);
                         }
                     }
+                  }
                     tc05::mma_commit(&a_done[k]);
                 }
                 __syncwarp();
@@ -373,21 +394,22 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
     } else {
         // ------------------------------------------------ TMA producer
         // (the whole warp runs the loop; one lane issues the copies)
-        const int n_groups = (ce - cb + NPAR - 1) / NPAR;
+        constexpr int PG = NPAR * CPR;                       // channels per slot group
+        const int n_groups = (ce - cb + PG - 1) / PG;
         bool ok = true;
         int issued = 0;          // groups issued
         int sg = 0;
         uint32_t dpar = 0;
-        int ilo_next[NPAR];      // first window rows, one group ahead
+        int ilo_next[PG];        // first window rows, one group ahead
 #pragma unroll
-        for (int k = 0; k < NPAR; ++k) ilo_next[k] = cb + k < ce ? tg[cb + k].ilo : 0;
+        for (int k = 0; k < PG; ++k) ilo_next[k] = cb + k < ce ? tg[cb + k].ilo : 0;
         for (int g = 0; g < n_groups; ++g) {
-            const int nch = min(NPAR, ce - cb - g * NPAR);
-            int ilo[NPAR];
+            const int nch = min(PG, ce - cb - g * PG);
+            int ilo[PG];
 #pragma unroll
-            for (int k = 0; k < NPAR; ++k) {
+            for (int k = 0; k < PG; ++k) {
                 ilo[k] = ilo_next[k];
-                const int cn = cb + (g + 1) * NPAR + k;
+                const int cn = cb + (g + 1) * PG + k;
                 if (cn < ce) ilo_next[k] = tg[cn].ilo;
             }
             // group g reuses the slot group of group g - NSG: phase g / NSG - 1
@@ -397,10 +419,10 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
             if (lane == 0) {
                 tc05::mbar_arrive_expect_tx(&b_full[sg], (uint32_t)nch * ta.slot_bytes);
 #pragma unroll
-                for (int k = 0; k < NPAR; ++k) {
+                for (int k = 0; k < PG; ++k) {
                     if (k >= nch) break;
-                    unsigned char *dst = smem + (size_t)(sg * NPAR + k) * ta.slot_bytes;
-                    const int cz = 2 * (cb + g * NPAR + k);
+                    unsigned char *dst = smem + (size_t)(sg * PG + k) * ta.slot_bytes;
+                    const int cz = 2 * (cb + g * PG + k);
                     for (int j = 0; j < ta.ncb; ++j) {
                         // planar: the Re columns of the bins, then (im_off bytes
                         // on) their Im columns; interleaved: (re, im) pairs
@@ -432,16 +454,16 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
     if (warp == 0) tc05::tmem_dealloc(tmem, ta.tmem_cols);
 }
 
-template <int W, int KS, int SPLIT, int NPAR, bool PLANAR>
+template <int W, int KS, int SPLIT, int NPAR, bool PLANAR, int CPR>
 cudaError_t launch_t(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
                      const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
                      cudaStream_t st) {
     const size_t smem = backproject_tc_smem_bytes(ta);
-    cudaError_t e = cudaFuncSetAttribute(k_backproject_tc<W, KS, SPLIT, NPAR, PLANAR>,
+    cudaError_t e = cudaFuncSetAttribute(k_backproject_tc<W, KS, SPLIT, NPAR, PLANAR, CPR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((p.nx + TCX - 1) / TCX, (p.ny + TCY - 1) / TCY, ta.n_utiles * ta.nsplit);
-    k_backproject_tc<W, KS, SPLIT, NPAR, PLANAR><<<grid, Warps<NPAR>::threads, smem, st>>>(
+    k_backproject_tc<W, KS, SPLIT, NPAR, PLANAR, CPR><<<grid, Warps<NPAR>::threads, smem, st>>>(
         p, ct, ta, tm, tgeo, kc_hl, G, err);
     return cudaGetLastError();
 }
@@ -450,8 +472,14 @@ template <int W, int KS, int SPLIT, int NPAR>
 cudaError_t launch_pl(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
                       const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
                       cudaStream_t st) {
-    return ta.planar ? launch_t<W, KS, SPLIT, NPAR, true>(p, ct, ta, tm, tgeo, kc_hl, G, err, st)
-                     : launch_t<W, KS, SPLIT, NPAR, false>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+    if constexpr (NPAR == 3) {           // two channels per round: one block per SM only
+        if (ta.cpr == 2)
+            return ta.planar
+                       ? launch_t<W, KS, SPLIT, NPAR, true, 2>(p, ct, ta, tm, tgeo, kc_hl, G, err, st)
+                       : launch_t<W, KS, SPLIT, NPAR, false, 2>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+    }
+    return ta.planar ? launch_t<W, KS, SPLIT, NPAR, true, 1>(p, ct, ta, tm, tgeo, kc_hl, G, err, st)
+                     : launch_t<W, KS, SPLIT, NPAR, false, 1>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
 }
 
 template <int KS, int SPLIT, int NPAR>

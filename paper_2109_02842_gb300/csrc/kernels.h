@@ -99,7 +99,7 @@ struct TcArgs {
     unsigned im_off;     // planar: smem offset of a window's Im columns (ncb x cb_bytes)
     int ncb;             // 64-column blocks of a block's window: ceil(N / 64)
     int n_utiles;        // blocks along k_z
-    int nst;             // table-window slots in shared memory
+    int nst;             // table-window slots in shared memory (groups of npar x cpr)
     unsigned cb_bytes;   // one column block: planes x 16 ks rows x 128 B
     unsigned slot_bytes; // one channel's window: ncb x cb_bytes (x 2 planar)
     unsigned idesc;      // tcgen05 instruction descriptor
@@ -108,6 +108,8 @@ struct TcArgs {
     int ks;              // 16-row K steps per channel (1 or 2)
     int split;           // 3: BF16 hi/lo products, 1: BF16 only
     int npar;            // channel classes of A-building warps (2: 2 blocks/SM, 3: 1 block/SM)
+    int cpr;             // channels per class round (1, or 2 with npar 3): A buffers of cpr
+                         // channels, one A-ready wait and one release per round
     long long budget;    // wait budget, SM clock cycles
 };
 int backproject_tc_tile_x();

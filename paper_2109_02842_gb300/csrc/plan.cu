@@ -471,11 +471,20 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         ta.npar = tc_npar(ta.UT, npl, ta.ks, ta.planar != 0);
         ta.tmem_cols = ta.npar == 2 ? 256 : 512;
         ta.acol = 2 * N;
-        // window slots: whole slot groups of npar (at least 2 groups), within
-        // ~190 KB (one block per SM) or ~100 KB (two)
+        // two channels per class round (twice the products per A wait and
+        // release) where three classes of two-channel A buffers fit next to
+        // the accumulators and two slot groups of six windows fit in shared
+        // memory
+        ta.cpr = 1;
+        if (ta.npar == 3 && 2 * N + 3 * 2 * npl * ta.ks * 8 <= 512 &&
+            1024 + 2 * (size_t)3 * 2 * ta.slot_bytes + 512 <= 227 * 1024)
+            ta.cpr = 2;
+        // window slots: whole slot groups of npar x cpr (at least 2 groups),
+        // within ~190 KB (one block per SM) or ~100 KB (two)
         const size_t pool = ta.tmem_cols > 256 ? 190 * 1024 : 100 * 1024;
-        const int nsg = (int)std::max<size_t>(2, std::min<size_t>(16, pool / ((size_t)ta.slot_bytes * ta.npar)));
-        ta.nst = nsg * ta.npar;
+        const size_t group_bytes = (size_t)ta.slot_bytes * ta.npar * ta.cpr;
+        const int nsg = (int)std::max<size_t>(2, std::min<size_t>(16, pool / group_bytes));
+        ta.nst = nsg * ta.npar * ta.cpr;
         if (backproject_tc_smem_bytes(ta) > 227 * 1024)
             return fail(PL_ERR_UNSUPPORTED, "table window slots exceed shared memory");
         ta.idesc = tc05::idesc_bf16(128, N, 1);
