@@ -323,6 +323,26 @@ def test_tensor_core_variant_small(binding, case):
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("taps", [4, 8])
+@pytest.mark.parametrize("grid", ["coarse", "fine128"])
+def test_tensor_core_other_tap_counts(binding, taps, grid):
+    # the 4- and 8-tap kernels (planar layout; fine128: one 16-row window
+    # step and 128 bins, two channels per class round). Four taps at
+    # sigma 2 resolve the table only to ~1e-3 (the interpolation error of
+    # the ES kernel), eight to the FP32 bar
+    w = wl.small_mono(seed=6)
+    if grid == "fine128":
+        w.n_pad = 128
+        x0, dx = wl.centred_axis(0.128, 64)
+        w.grid = dict(w.grid, x0=x0, dx=dx, nx=64, y0=x0, dy=dx, ny=64, nz=8)
+    echo = scene_echo(w, 6)
+    plan, img = run_gpu(binding, w, echo, block_config=4, nufft_w=taps)
+    assert plan.info["nufft_w"] == taps and plan.info["block_config"] == 4
+    err = report("image tc %d taps %s" % (taps, grid), img.reshape(w.grid["nz"], -1),
+                 image_ref(w, echo))
+    assert err < (2e-3 if taps == 4 else TOL_FP32)
+
+
 def test_tensor_core_bf16_only_products(binding):
     w = wl.small_mono(seed=2)
     echo = scene_echo(w, 2)
