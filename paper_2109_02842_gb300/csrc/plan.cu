@@ -45,8 +45,9 @@ bool tc_fits(int ut, int npl, int ks, bool planar) {
     const size_t slot = (size_t)(planar ? 2 : 1) * ((N + 63) / 64) * cb;
     return 1024 + 2 * npar * slot + 512 <= 227 * 1024;
 }
-// Bins per block: the fewest blocks that the largest 1-block-per-SM tile
-// allows, split evenly (multiple of 8): N_p = 200 -> 2 x 104, 128 -> 2 x 64.
+// Bins per block of the interleaved layout (used where the planar one does
+// not fit): the fewest blocks that the largest 1-block-per-SM tile allows,
+// split evenly (multiple of 8), e.g. N_p = 200 -> 2 x 104, 128 -> 2 x 64.
 int tc_auto_tile(int np, int npl, int ks) {
     const int ut_max = (512 - 3 * npl * ks * 8) / 4 / 8 * 8;
     const int n = (np + ut_max - 1) / ut_max;
