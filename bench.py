@@ -214,6 +214,23 @@ def oracle_baseline(w, echo_np, gpu_image=None, n_cols=256, n_chan=None, seed=1)
     return out, err
 
 
+def max_over_ranks(values, world: int, device):
+    """The per-rank floats reduced to their maximum over all ranks (the
+    slowest rank's times); unchanged for one rank."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank processes its own units)."""
+    return world * units_per_rank / seconds
+
+
 def workload_config(w, world, precision, l2):
     """The `config` of both arms: the workload's name and sizes, the options
     and how the timing treats the L2 cache."""
@@ -458,13 +475,9 @@ def main():
     stage = plan.stage_times()
     plan.set_timing(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks([statistics.mean(step_ms)], world, dev)[0]
     upd = w.updates_per_scan()
-    value = world * upd / (ms * 1e-3)
+    value = whole_job_rate(upd, world, ms * 1e-3)
 
     # end to end through the C ABI with pinned host buffers: a stream of K
     # scans through pl_execute_host_stream (every scan's echo uploaded and
@@ -488,11 +501,7 @@ def main():
         ta = time.perf_counter()
         plan.execute_host(echo_h[0], image_h[0])
         lat.append(time.perf_counter() - ta)
-    lat_s = statistics.mean(lat)
-    if world > 1:
-        t = torch.tensor([e2e_s, lat_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s, lat_s = (float(x) for x in t.tolist())
+    e2e_s, lat_s = max_over_ranks([e2e_s, statistics.mean(lat)], world, dev)
 
     # roofline of the dominant kernel (back-projection), live CUDA-event times
     bp_ms, bp_n = stage["backproject"]
@@ -548,7 +557,7 @@ def main():
                                   "flushed before every step (256 MiB write, outside the "
                                   "step events)"),
         "scans_per_s": world / (ms * 1e-3),
-        "e2e": {"value": world * upd / e2e_s, "unit": "updates/s",
+        "e2e": {"value": whole_job_rate(upd, world, e2e_s), "unit": "updates/s",
                 "h2d_bytes_per_step": int(echo.numel() * 8),
                 "d2h_bytes_per_step": int(image.numel() * 8),
                 "scans_per_s": world / e2e_s,
