@@ -310,7 +310,16 @@ pl_status build_queue(pl_batch *B, int tile_u, double timeout_ms, int debug) {
     B->info.work_items = total;
     B->info.persistent = B->persistent ? 1 : 0;
     B->info.persistent_blocks = B->persistent ? B->pblocks : 0;
-    B->info.launches_per_execute = B->persistent ? 2 * n + 1 : 4 * n;
+    if (B->persistent) {
+        B->info.launches_per_execute = 2 * n + 1;
+    } else {        // each scene's own kernels (pl_plan_get_info counts them)
+        int total = 0;
+        for (pl_plan *p : B->plans) {
+            pl_info pi{};
+            if (pl_plan_get_info(p, &pi) == PL_OK) total += pi.launches_per_execute;
+        }
+        B->info.launches_per_execute = total;
+    }
     if (!B->persistent && B->aux.empty()) {
         // scenes of the per-scene path run on kAuxStreams streams at once
         for (int k = 0; k < kAuxStreams; ++k) {

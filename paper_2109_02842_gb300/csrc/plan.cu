@@ -1085,7 +1085,10 @@ pl_status pl_plan_get_info(const pl_plan *P, pl_info *info) {
     i.table_h = P->nd.h;
     i.table_l0 = P->nd.l0;
     i.z_transform_fft = P->inv_fft ? 1 : 0;
-    i.launches_per_execute = 4;
+    // z transform, range table (tensor cores: the products and the transpose,
+    // plus the operand's preparation when the z transform is a DFT), the
+    // back-projection, the inverse z transform
+    i.launches_per_execute = (P->block_config == 4 && P->rt_tc) ? (P->fwd_fft ? 5 : 6) : 4;
     i.workspace_bytes = P->workspace;
     i.updates_per_execute = (double)P->C * P->grid.nx * P->grid.ny * P->grid.nz * P->M;
     i.block_config = P->block_config;
