@@ -1,6 +1,6 @@
 """Learned fast path: a 3-D convolutional encoder-decoder that maps a cheap
 reconstruction to the full one (the paper has no learned component; the plain
-hybrid method stays the fallback and the judge of the network's error).
+hybrid method stays the fallback and the yardstick for the network's error).
 
 Cheap reconstruction: every other frequency and a coarse range table (NUFFT
 oversampling 1.25, 4 taps). Full reconstruction: all frequencies, sigma = 2,
