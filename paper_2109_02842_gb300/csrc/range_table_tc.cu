@@ -233,48 +233,53 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
     if (warp == 0) tc05::tmem_dealloc(tmem, tcols);
 }
 
-// prod [u][plane][C][Lp] (uint32 = (re, im) BF16 pair) -> table [c][plane][L][u]:
-// 64 x 64 tiles, 16-byte global accesses on both sides (u beyond N_p written
-// as zeros so the padding columns stay zero). Interleaved rows hold row_words
-// (re, im) pairs; planar rows hold row_words Re entries, then row_words Im.
+// prod [u][plane][part][C][Lh] (uint32 = (re, im) BF16 pair) -> table
+// [c][plane][L][u], u beyond N_p written as zeros so the padding columns stay
+// zero. Interleaved rows hold row_words (re, im) pairs; planar rows hold
+// row_words Re entries, then row_words Im. A block covers 64 rows x 64 bins;
+// each thread transposes a 4 x 4 block in registers: four independent 16-byte
+// loads (4 rows i of one bin each) and four row stores, so a warp (16 rows x
+// 32 bins) reads and writes 64-byte runs with no shared memory or barrier.
+__device__ __forceinline__ uint32_t word_of(const uint4 &v, int e) {
+    return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+
 template <bool PLANAR>
 __global__ void __launch_bounds__(256)
 k_rt_transpose(const uint32_t *__restrict__ prod, uint32_t *__restrict__ table, int C, int L,
                int nh, int Lh, int Np, int row_words) {
-    __shared__ uint32_t s[64][65];
-    const int i0 = blockIdx.x * 64, u0 = blockIdx.y * 64;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 64 + 16 * (warp & 3) + 4 * (lane & 3);
+    const int u = blockIdx.y * 64 + 32 * (warp >> 2) + 4 * (lane >> 2);
     const int cp = blockIdx.z;                 // c * 2 + plane
     const int c = cp >> 1, p = cp & 1;
-    const int q = threadIdx.x & 15, r0 = threadIdx.x >> 4;   // 16 x 16
-    for (int k = r0; k < 64; k += 16) {
-        const int u = u0 + k, i = i0 + 4 * q;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (u < Np && i < L) {         // padding rows of the parts are never read
-            // row i lives in part i / Lh (Lh is a multiple of 4: a uint4 stays in one part)
-            const int hp = i / Lh;
-            v = *reinterpret_cast<const uint4 *>(
-                prod + (((size_t)(2 * u + p) * nh + hp) * C + c) * Lh + (i - hp * Lh));
-        }
-        s[k][4 * q + 0] = v.x;
-        s[k][4 * q + 1] = v.y;
-        s[k][4 * q + 2] = v.z;
-        s[k][4 * q + 3] = v.w;
-    }
-    __syncthreads();
-    for (int k = r0; k < 64; k += 16) {
-        const int i = i0 + k, u = u0 + 4 * q;
-        if (i >= L || u >= row_words) continue;
-        const uint4 v = make_uint4(s[4 * q][k], s[4 * q + 1][k], s[4 * q + 2][k], s[4 * q + 3][k]);
-        uint32_t *row = table + ((size_t)cp * L + i) * row_words;
+    if (i >= L || u >= row_words) return;      // row_words is a multiple of 4
+    // row i lives in part i / Lh (Lh is a multiple of 16: rows i..i+3 stay in
+    // one part; those at L and beyond are padding, loaded but never stored)
+    const int hp = i / Lh;
+    const uint32_t *src = prod + ((size_t)hp * C + c) * Lh + (i - hp * Lh);
+    const size_t bin_stride = (size_t)2 * nh * C * Lh;
+    uint4 v[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        v[r] = u + r < Np ? *reinterpret_cast<const uint4 *>(src + (size_t)(u + r) * bin_stride +
+                                                              (size_t)p * nh * C * Lh)
+                          : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (i + e >= L) break;
+        const uint32_t w0 = word_of(v[0], e), w1 = word_of(v[1], e);
+        const uint32_t w2 = word_of(v[2], e), w3 = word_of(v[3], e);
+        uint32_t *row = table + ((size_t)cp * L + i + e) * row_words;
         if (PLANAR) {
-            // low halves (Re) of four bins, then the high halves (Im)
+            // low halves (Re) of the four bins, then the high halves (Im)
             __nv_bfloat16 *rb = reinterpret_cast<__nv_bfloat16 *>(row);
-            const uint2 re = make_uint2(__byte_perm(v.x, v.y, 0x5410), __byte_perm(v.z, v.w, 0x5410));
-            const uint2 im = make_uint2(__byte_perm(v.x, v.y, 0x7632), __byte_perm(v.z, v.w, 0x7632));
-            *reinterpret_cast<uint2 *>(rb + u) = re;
-            *reinterpret_cast<uint2 *>(rb + row_words + u) = im;
+            *reinterpret_cast<uint2 *>(rb + u) =
+                make_uint2(__byte_perm(w0, w1, 0x5410), __byte_perm(w2, w3, 0x5410));
+            *reinterpret_cast<uint2 *>(rb + row_words + u) =
+                make_uint2(__byte_perm(w0, w1, 0x7632), __byte_perm(w2, w3, 0x7632));
         } else {
-            *reinterpret_cast<uint4 *>(row + u) = v;
+            *reinterpret_cast<uint4 *>(row + u) = make_uint4(w0, w1, w2, w3);
         }
     }
 }
@@ -313,6 +318,7 @@ cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
     k_range_table_tc<<<grid, 128, smem, st>>>(ra, tmA, tmB, (uint32_t *)prod, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (row_words % 4 != 0 || ra.Lh % 16 != 0) return cudaErrorInvalidValue;
     dim3 tg((ra.L + 63) / 64, (row_words + 63) / 64, 2 * ra.C);
     if (planar)
         k_rt_transpose<true><<<tg, 256, 0, st>>>((const uint32_t *)prod, (uint32_t *)table, ra.C,

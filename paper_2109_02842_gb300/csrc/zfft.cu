@@ -16,7 +16,8 @@
 
 namespace {
 
-constexpr int kFftIB = 16;   // columns per block (128-byte rows)
+constexpr int kFftIB = 16;        // columns per block (128-byte rows)
+constexpr int kFftThreads = 256;  // threads per block
 
 // in:  [batch][n_in][I]  (rows n >= n_in are zero padding)
 // out: [batch][out_rows][I], out row r = transform index (r + out_off) mod N;
@@ -30,7 +31,7 @@ struct SplitOut {
 // PAIRS (I even): every access moves two adjacent columns (16-byte copies,
 // float4 shared-memory accesses, column pairs through the FFT stages).
 template <bool PAIRS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kFftThreads)
 k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, float2 *__restrict__ out,
               int n_in, int I, FftPlan plan, const float2 *__restrict__ tw_g, int sgn,
               float scale, int out_rows, int out_off, SplitOut sp) {
@@ -45,19 +46,21 @@ k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, flo
     constexpr int NG = kFftIB / CW;            // accesses per row
 
     // the whole panel in flight at once: asynchronous copies, zeros for the
-    // padding rows and the columns past I
-    for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
+    // padding rows and the columns past I. Each thread keeps one column group
+    // (CW columns) and walks the rows RPS apart with running pointers.
+    constexpr int RPS = kFftThreads / NG;      // rows per sweep of the block
+    const int col = (threadIdx.x % NG) * CW;
+    const int n_first = threadIdx.x / NG;
+    const bool col_ok = i0 + col < I;
+    for (int k = threadIdx.x; k < N; k += kFftThreads) tw[k] = tw_g[k];
     // in2 (optional): a second array of the same shape, added on load (into
     // buf1 first, which the transform then reuses)
     for (int part = 0; part < (in2 ? 2 : 1); ++part) {
-        const float2 *src_arr = part ? in2 : in;
-        float2 *panel = part ? buf1 : buf0;
-        for (int idx = threadIdx.x; idx < N * NG; idx += blockDim.x) {
-            const int n = idx / NG;
-            const int col = (idx - n * NG) * CW;
-            float2 *dst = panel + n * kFftIB + col;
-            if (n < n_in && i0 + col < I) {
-                const float2 *src = src_arr + (b * n_in + n) * (size_t)I + i0 + col;
+        const float2 *src = (part ? in2 : in) + (b * n_in + n_first) * (size_t)I + i0 + col;
+        float2 *dst = (part ? buf1 : buf0) + n_first * kFftIB + col;
+        const size_t src_step = (size_t)RPS * I;
+        for (int n = n_first; n < N; n += RPS, src += src_step, dst += RPS * kFftIB) {
+            if (col_ok && n < n_in) {
                 if (PAIRS)
                     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(
                                      (unsigned)__cvta_generic_to_shared(dst)),
@@ -78,7 +81,7 @@ k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, flo
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     if (in2) {
-        for (int idx = threadIdx.x; idx < N * kFftIB / 2; idx += blockDim.x) {
+        for (int idx = threadIdx.x; idx < N * kFftIB / 2; idx += kFftThreads) {
             float4 *a = reinterpret_cast<float4 *>(buf0) + idx;
             const float4 c = reinterpret_cast<const float4 *>(buf1)[idx];
             *a = make_float4(a->x + c.x, a->y + c.y, a->z + c.z, a->w + c.w);
@@ -90,46 +93,57 @@ k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, flo
                               : stockham_run<true, kFftIB>(buf0, buf1, tw, plan, sgn, 1, kFftIB);
 
     // out_off < N and r < out_rows <= N: one conditional subtraction wraps
-    for (int idx = threadIdx.x; idx < out_rows * NG; idx += blockDim.x) {
-        const int r = idx / NG;
-        const int col = (idx - r * NG) * CW;
-        if (i0 + col >= I) continue;
-        int sr = r + out_off;
-        if (sr >= N) sr -= N;
-        float2 v[CW];
-        if (PAIRS) {
-            const float4 x = *reinterpret_cast<const float4 *>(src + sr * kFftIB + col);
-            v[0] = cscale(make_float2(x.x, x.y), scale);
-            v[CW - 1] = cscale(make_float2(x.z, x.w), scale);
-        } else {
-            v[0] = cscale(src[sr * kFftIB + col], scale);
-        }
-        if (sp.A) {
-            const size_t plane = (size_t)sp.batch * sp.Kp;
-            const size_t o = (size_t)r * 4 * plane + b * sp.Kp + i0 + col;
-            const float2 *al = sp.alpha + (size_t)r * I + i0 + col;
+    if (!col_ok) return;
+    if (sp.A) {
+        const size_t plane = (size_t)sp.batch * sp.Kp;
+        __nv_bfloat16 *o = sp.A + (size_t)n_first * 4 * plane + b * sp.Kp + i0 + col;
+        const float2 *al = sp.alpha + (size_t)n_first * I + i0 + col;
+        for (int r = n_first; r < out_rows; r += RPS, o += (size_t)RPS * 4 * plane,
+                 al += (size_t)RPS * I) {
+            int sr = r + out_off;
+            if (sr >= N) sr -= N;
+            float2 v[CW], a[CW];
+            if (PAIRS) {
+                const float4 x = *reinterpret_cast<const float4 *>(src + sr * kFftIB + col);
+                const float4 w = *reinterpret_cast<const float4 *>(al);
+                v[0] = make_float2(x.x, x.y);
+                v[CW - 1] = make_float2(x.z, x.w);
+                a[0] = make_float2(w.x, w.y);
+                a[CW - 1] = make_float2(w.z, w.w);
+            } else {
+                v[0] = src[sr * kFftIB + col];
+                a[0] = al[0];
+            }
             __nv_bfloat16 h[4][CW];
 #pragma unroll
             for (int e = 0; e < CW; ++e) {
-                const float2 a = cmul(v[e], al[e]);
-                h[0][e] = __float2bfloat16(a.x);
-                h[1][e] = __float2bfloat16(a.x - __bfloat162float(h[0][e]));
-                h[2][e] = __float2bfloat16(a.y);
-                h[3][e] = __float2bfloat16(a.y - __bfloat162float(h[2][e]));
+                const float2 t = cmul(cscale(v[e], scale), a[e]);
+                h[0][e] = __float2bfloat16(t.x);
+                h[1][e] = __float2bfloat16(t.x - __bfloat162float(h[0][e]));
+                h[2][e] = __float2bfloat16(t.y);
+                h[3][e] = __float2bfloat16(t.y - __bfloat162float(h[2][e]));
             }
 #pragma unroll
             for (int pl = 0; pl < 4; ++pl) {
                 if (PAIRS)
-                    *reinterpret_cast<__nv_bfloat162 *>(sp.A + o + pl * plane) =
+                    *reinterpret_cast<__nv_bfloat162 *>(o + pl * plane) =
                         __halves2bfloat162(h[pl][0], h[pl][CW - 1]);
                 else
-                    sp.A[o + pl * plane] = h[pl][0];
+                    o[pl * plane] = h[pl][0];
             }
-        } else if (PAIRS) {
-            *reinterpret_cast<float4 *>(out + (b * out_rows + r) * (size_t)I + i0 + col) =
-                make_float4(v[0].x, v[0].y, v[CW - 1].x, v[CW - 1].y);
+        }
+        return;
+    }
+    float2 *o = out + (b * out_rows + n_first) * (size_t)I + i0 + col;
+    for (int r = n_first; r < out_rows; r += RPS, o += (size_t)RPS * I) {
+        int sr = r + out_off;
+        if (sr >= N) sr -= N;
+        if (PAIRS) {
+            const float4 x = *reinterpret_cast<const float4 *>(src + sr * kFftIB + col);
+            *reinterpret_cast<float4 *>(o) =
+                make_float4(scale * x.x, scale * x.y, scale * x.z, scale * x.w);
         } else {
-            out[(b * out_rows + r) * (size_t)I + i0 + col] = v[0];
+            *o = cscale(src[sr * kFftIB + col], scale);
         }
     }
 }
@@ -208,7 +222,7 @@ cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_i
     if (e != cudaSuccess) return e;
     dim3 grid((I + kFftIB - 1) / kFftIB, batch);
     const SplitOut sp{split_alpha, (__nv_bfloat16 *)split_A, batch, split_Kp};
-    kern<<<grid, 256, smem, st>>>(in, in2, out, n_in, I, plan, tw, sgn, scale, out_rows, out_off,
+    kern<<<grid, kFftThreads, smem, st>>>(in, in2, out, n_in, I, plan, tw, sgn, scale, out_rows, out_off,
                                   sp);
     return cudaGetLastError();
 }
