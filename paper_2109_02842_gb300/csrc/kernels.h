@@ -134,13 +134,14 @@ struct RtTcArgs {
                          // a multiple of 16 (the N of the products)
     unsigned idesc;      // tcgen05 instruction descriptor (M 128, N Lh, both K-major)
     long long budget;    // wait budget, SM clock cycles
+    int grid;            // persistent blocks (one per SM)
 };
 size_t range_table_tc_smem_bytes(const RtTcArgs &ra);
 // E [N_p][re hi, re lo, im hi, im lo][Lp][Kp] BF16: e^{+j theta_um (i - L/2)}
 cudaError_t launch_setup_rt_E(const NufftDesc &d, double dz, const double *k, const double *kc,
                               int Lp, int Kp, void *E, cudaStream_t st);
 // S, alpha -> A (scratch [N_p][4][C][Kp] BF16; skipped when `prepared`: the
-// z-FFT wrote A) -> prod (scratch [N_p][2][nh][C][Lh] uint32) -> table
+// z-FFT wrote A) -> prod (scratch [N_p][2][nh * Lh][C rounded up to 128] uint32) -> table
 // [C][2][L][row_words uint32]
 cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
                                   const CUtensorMap &tmB, const float2 *S, const float2 *alpha,

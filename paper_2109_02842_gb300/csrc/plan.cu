@@ -594,21 +594,29 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         ra.natoms = ra.Kp / 64;
         ra.L = L;
         ra.Lp = (L + 15) / 16 * 16;
-        // two row parts when one part would not let two blocks share an SM
-        ra.nh = 1;
-        ra.Lh = ra.Lp;
-        if (2 * ra.Lp > 256 || range_table_tc_smem_bytes(ra) > 110 * 1024) {
-            ra.nh = 2;
-            ra.Lh = ((ra.Lp + 1) / 2 + 15) / 16 * 16;
+        // the fewest row parts whose two operand buffers (the persistent
+        // kernel's double buffering) fit in shared memory, and whose two
+        // accumulator pairs fit in TMEM
+        for (ra.nh = 1;; ++ra.nh) {
+            ra.Lh = ((ra.Lp + ra.nh - 1) / ra.nh + 15) / 16 * 16;
+            if ((range_table_tc_smem_bytes(ra) <= 227 * 1024 && 4 * ra.Lh <= 512) || ra.Lh <= 16)
+                break;
         }
         ra.idesc = tc05::idesc_bf16(128, ra.Lh, 0);
         ra.budget = 4ll << 30;
-        P->rt_tc = ra.natoms == 1 && ra.Lp <= 256 &&
+        {
+            int dev = 0, sms = 0;
+            PL_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+            PL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev),
+                    "cudaDeviceGetAttribute");
+            ra.grid = sms;
+        }
+        P->rt_tc = ra.natoms == 1 && ra.Lp <= 256 && 4 * ra.Lh <= 512 &&
                    range_table_tc_smem_bytes(ra) <= 227 * 1024;
         if (P->rt_tc) {
             const size_t nE = (size_t)P->Np * 4 * ra.Lp * ra.Kp;
             const size_t nA = (size_t)P->Np * 4 * P->C * ra.Kp;
-            const size_t nprod = (size_t)P->Np * 2 * ra.nh * P->C * ra.Lh;
+            const size_t nprod = (size_t)P->Np * 2 * ra.nh * ra.Lh * ((P->C + 127) / 128 * 128);
             PL_CUDA(cudaMalloc(&P->d_rtE, nE * 2), "cudaMalloc");
             PL_CUDA(cudaMalloc(&P->d_rtA, nA * 2), "cudaMalloc");
             PL_CUDA(cudaMemset(P->d_rtA, 0, nA * 2), "cudaMemset");   // frequencies >= M stay 0

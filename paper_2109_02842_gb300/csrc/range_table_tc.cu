@@ -12,15 +12,16 @@
 // instruction descriptor, and the two accumulators (Re, Im) live in TMEM.
 //
 //   k_rt_prep          S [C][N_p][M] x alpha -> A [u][re hi, re lo, im hi, im lo][C][K] BF16
-//   k_range_table_tc   per (128-channel block, bin, row part): TMA (128-byte
-//                      swizzled, K-major) A and E tiles, 12 MMAs per
-//                      16-frequency step, tcgen05.ld, BF16 hi/lo, staged per warp
-//                      and stored as full lines of each channel's consecutive
-//                      rows into prod [u][hi, lo][part][C][Lh] of (re, im) pairs
-//                      (Lh rows per part, a multiple of 16). Two row parts when that lets two
-//                      blocks share an SM (256 TMEM columns, ~107 KB of shared
-//                      memory each), so one block's loads, products and stores
-//                      overlap the other's.
+//   k_range_table_tc   persistent, one block per SM, over the items (128-channel
+//                      block, bin, row part): TMA (128-byte swizzled, K-major) A
+//                      and E tiles, 12 MMAs per 16-frequency step, tcgen05.ld,
+//                      BF16 hi/lo, stored straight from the registers into
+//                      prod [u][hi, lo][row][Cp] of (re, im) pairs, channels
+//                      innermost (full 128-byte lines). Row parts of Lh rows
+//                      (a multiple of 16, at most 96 so that two items'
+//                      operands fit in shared memory). Double-buffered: one
+//                      item's conversion and stores overlap the next item's
+//                      products and the copies of the one after.
 //   k_rt_transpose     prod -> table [c][hi, lo][L][column 2u + (re, im)] (or
 //                      planar: Re at column u, Im at row_words + u), the layout
 //                      the back-projection streams (u innermost)
@@ -93,69 +94,62 @@ __global__ void k_rt_prep(const float2 *__restrict__ S, const float2 *__restrict
     A[base + 3 * plane] = l;
 }
 
-__global__ void __launch_bounds__(128, 1)
+// One block per SM (persistent, 8 warps) walks the work items (128-channel
+// block, bin, row part) gridDim.x apart, with two operand buffers and two
+// accumulator pairs: while the warps convert and store item k, the operands
+// of item k + 1 are already in shared memory and its products run on the
+// tensor cores, and the copies of item k + 2 are issued as soon as item k's
+// buffer is free again.
+__global__ void __launch_bounds__(256, 1)
 k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
                  const __grid_constant__ CUtensorMap tmB, uint32_t *__restrict__ prod, int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t bar_tma, bar_mma;
+    __shared__ __align__(8) uint64_t bar_tma[2], bar_mma[2];
     __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c0 = blockIdx.x * 128, u = blockIdx.y, h = blockIdx.z;
     const uint32_t a_tile = 128 * 128;                 // one plane x 64-frequency atom of A
-    const uint32_t b_tile = (uint32_t)ra.Lh * 128;     // of E (this part's rows)
-    const uint32_t tcols = 2 * ra.Lh > 256 ? 512 : (2 * ra.Lh > 128 ? 256 : 128);
-    unsigned char *As = smem;
-    unsigned char *Bs = smem + 4 * ra.natoms * a_tile;
-
-    if (threadIdx.x == 0) {
-        tc05::mbar_init(&bar_tma, 1);
-        tc05::mbar_init(&bar_mma, 1);
-        tc05::fence_mbar_init();
-    }
-    if (warp == 0) {
-        tc05::tmem_alloc(&tmem_slot, tcols);
-        tc05::tmem_relinquish();
-    }
-    tc05::fence_before_sync();
-    __syncthreads();
-    tc05::fence_after_sync();
-    const uint32_t tmem = tmem_slot;
-
-    if (threadIdx.x == 0) {
-        tc05::mbar_arrive_expect_tx(&bar_tma, 4 * ra.natoms * (a_tile + b_tile));
-        for (int p = 0; p < 4; ++p)
-            for (int at = 0; at < ra.natoms; ++at) {
-                const int t = p * ra.natoms + at;
-                asm volatile(
-                    "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-                    "[%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(tc05::smem_addr(As + t * a_tile)),
-                    "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(64 * at), "r"(c0), "r"(4 * u + p),
-                    "r"(tc05::smem_addr(&bar_tma))
-                    : "memory");
-                asm volatile(
-                    "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-                    "[%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(tc05::smem_addr(Bs + t * b_tile)),
-                    "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(64 * at), "r"(h * ra.Lh), "r"(4 * u + p),
-                    "r"(tc05::smem_addr(&bar_tma))
-                    : "memory");
-            }
-        bool ok = tc05::mbar_wait(&bar_tma, 0, ra.budget);
-        if (ok) {
+    const uint32_t b_tile = (uint32_t)ra.Lh * 128;     // of E (one row part)
+    const uint32_t buf_bytes = 4 * (a_tile + b_tile);  // one item's operands (natoms == 1)
+    const int ncb = (ra.C + 127) / 128;
+    const int items = ncb * ra.Np * ra.nh;
+    const int nmine = (items - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    // item -> (first channel, bin, row part); channel blocks vary fastest so
+    // the blocks running together share each bin's E tile in L2
+    auto coords = [&](int k, int &c0, int &u, int &h) {
+        const int it = (int)blockIdx.x + k * (int)gridDim.x;
+        const int cb = it % ncb, r = it / ncb;
+        c0 = 128 * cb;
+        u = r % ra.Np;
+        h = r / ra.Np;
+    };
+    auto issue_tma = [&](int k, int b) {
+        int c0, u, h;
+        coords(k, c0, u, h);
+        unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
+        tc05::mbar_arrive_expect_tx(&bar_tma[b], buf_bytes);
+        for (int p = 0; p < 4; ++p) {
+            tc05::tma_load_3d(As + p * a_tile, &tmA, &bar_tma[b], 0, c0, 4 * u + p);
+            tc05::tma_load_3d(Bs + p * b_tile, &tmB, &bar_tma[b], 0, h * ra.Lh, 4 * u + p);
+        }
+    };
+    // the products of the item in buffer b, once its operands landed; the
+    // commit always follows so that the epilogue's wait ends
+    auto issue_mma = [&](int k, int b) {
+        if (tc05::mbar_wait(&bar_tma[b], (k >> 1) & 1, ra.budget)) {
             tc05::fence_after_sync();
+            const unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
             const uint32_t id = ra.idesc, idn = ra.idesc | (1u << 13);   // negate A
-            const uint32_t dre = tmem, dim = tmem + ra.Lh;
-            for (int ks = 0; ks < ra.natoms * 4; ++ks) {
-                const int at = ks >> 2;
-                const uint32_t ko = (ks & 3) * 32;
+            const uint32_t dre = tmem_slot + (uint32_t)(b * 2 * ra.Lh), dim = dre + ra.Lh;
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint32_t ko = ks * 32;
                 auto da = [&](int p) {
-                    return tc05::smem_desc_sw128(tc05::smem_addr(As + (p * ra.natoms + at) * a_tile) + ko,
-                                                 16, 1024);
+                    return tc05::smem_desc_sw128(tc05::smem_addr(As + p * a_tile) + ko, 16, 1024);
                 };
                 auto db = [&](int p) {
-                    return tc05::smem_desc_sw128(tc05::smem_addr(Bs + (p * ra.natoms + at) * b_tile) + ko,
-                                                 16, 1024);
+                    return tc05::smem_desc_sw128(tc05::smem_addr(Bs + p * b_tile) + ko, 16, 1024);
                 };
                 const uint32_t acc = ks > 0 ? 1u : 0u;
                 // planes: 0 re hi, 1 re lo, 2 im hi, 3 im lo
@@ -176,101 +170,145 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
             }
         } else {
             atomicOr(err, 1);
+            abort_flag = 1;
         }
-        tc05::mma_commit(&bar_mma);   // arrives once every issued MMA completed
+        tc05::mma_commit(&bar_mma[b]);   // arrives once every issued MMA completed
+    };
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b) {
+            tc05::mbar_init(&bar_tma[b], 1);
+            tc05::mbar_init(&bar_mma[b], 1);
+        }
+        tc05::fence_mbar_init();
+        abort_flag = 0;
     }
-    __syncwarp();
-    bool done = tc05::mbar_wait(&bar_mma, 0, ra.budget);
-    done = __all_sync(0xffffffffu, done);
-    // output in 32-row chunks: each thread (one channel: its TMEM lane)
-    // converts its rows to BF16 hi/lo pairs and puts them in its warp's
-    // staging rows (33 words apart: conflict-free), then the warp writes one
-    // channel's 32 consecutive rows per store instruction (a full 128-byte
-    // line of prod, where a channel's rows are contiguous). The operand tiles
-    // are dead by now and hold the staging.
-    const int rows_here = min(ra.Lh, ra.L - h * ra.Lh);     // table rows of this part
-    if (done) {
-        tc05::fence_after_sync();
-        const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-        uint32_t *st = reinterpret_cast<uint32_t *>(smem) + warp * (2 * 32 * 33);
-        const int cw = c0 + 32 * warp;                       // the warp's first channel
-        uint32_t *g_hi = prod + ((size_t)(2 * u + 0) * ra.nh + h) * ra.C * ra.Lh;
-        uint32_t *g_lo = prod + ((size_t)(2 * u + 1) * ra.nh + h) * ra.C * ra.Lh;
-        for (int i0 = 0; i0 < rows_here; i0 += 32) {
-            const int nrow = min(32, ra.Lh - i0);            // 16 or 32 columns of the part
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                if (16 * half >= nrow) break;
-                uint32_t vr[16], vi[16];
-                tc05::tmem_ld16(lane_base + i0 + 16 * half, vr);
-                tc05::tmem_ld16(lane_base + ra.Lh + i0 + 16 * half, vi);
-                tc05::tmem_wait_ld();
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float re = __uint_as_float(vr[j]), im = __uint_as_float(vi[j]);
-                    __nv_bfloat162 hv = __floats2bfloat162_rn(re, im);
-                    const float2 hf = __bfloat1622float2(hv);
-                    __nv_bfloat162 l = __floats2bfloat162_rn(re - hf.x, im - hf.y);
-                    st[lane * 33 + 16 * half + j] = *reinterpret_cast<uint32_t *>(&hv);
-                    st[32 * 33 + lane * 33 + 16 * half + j] = *reinterpret_cast<uint32_t *>(&l);
-                }
-            }
-            __syncwarp();
-            if (lane < nrow) {
-                for (int rr = 0; rr < 32 && cw + rr < ra.C; ++rr) {
-                    const size_t o = (size_t)(cw + rr) * ra.Lh + i0 + lane;
-                    g_hi[o] = st[rr * 33 + lane];
-                    g_lo[o] = st[32 * 33 + rr * 33 + lane];
-                }
-            }
-            __syncwarp();
-        }
-    } else if (lane == 0) {
-        atomicOr(err, 2);
+    if (warp == 0) {
+        tc05::tmem_alloc(&tmem_slot, 512);
+        tc05::tmem_relinquish();
     }
     tc05::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc05::tmem_dealloc(tmem, tcols);
+    tc05::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+
+    if (threadIdx.x == 0) {
+        issue_tma(0, 0);
+        if (nmine > 1) issue_tma(1, 1);
+    }
+    int pending_tma = -1;      // an item whose copies were issued but not waited for
+    if (threadIdx.x == 0) {
+        issue_mma(0, 0);
+        if (abort_flag) pending_tma = 0;
+    }
+    const int Cp = ncb * 128;                // channel stride of prod
+    const int R = ra.nh * ra.Lh;             // rows of prod per (bin, plane)
+    for (int k = 0; k < nmine; ++k) {
+        const int b = k & 1;
+        // the next item's products, before this item's epilogue
+        if (threadIdx.x == 0 && k + 1 < nmine) {
+            issue_mma(k + 1, b ^ 1);
+            if (abort_flag) pending_tma = k + 1;
+        }
+        __syncwarp();
+        bool done = tc05::mbar_wait(&bar_mma[b], (k >> 1) & 1, ra.budget);
+        done = __all_sync(0xffffffffu, done);
+        // this item's operands are consumed: the copies of item k + 2 go
+        // into its buffer now and overlap this epilogue and the next products
+        if (threadIdx.x == 0 && done && !abort_flag && k + 2 < nmine) issue_tma(k + 2, b);
+        int c0, u, h;
+        coords(k, c0, u, h);
+        // output: each thread (one channel: its TMEM lane) converts 16 rows at
+        // a time to BF16 hi/lo (re, im) pairs and stores them into
+        // prod [u][hi, lo][row][Cp], channels innermost, so each store
+        // instruction of a warp writes 32 consecutive channels (a full
+        // 128-byte line). Warps 0-3 and 4-7 take alternate 16-row chunks of
+        // their TMEM lane quarter.
+        const int rows_here = min(ra.Lh, ra.L - h * ra.Lh);     // table rows of this part
+        if (done) {
+            tc05::fence_after_sync();
+            const int q = warp & 3;
+            const uint32_t lane_base = tmem + (uint32_t)(b * 2 * ra.Lh) + ((uint32_t)(32 * q) << 16);
+            const int c = c0 + 32 * q + lane;
+            uint32_t *g_hi = prod + ((size_t)(2 * u + 0) * R + h * ra.Lh) * Cp + c;
+            uint32_t *g_lo = prod + ((size_t)(2 * u + 1) * R + h * ra.Lh) * Cp + c;
+            for (int i0 = 16 * (warp >> 2); i0 < rows_here; i0 += 32) {
+                uint32_t vr[16], vi[16];
+                tc05::tmem_ld16(lane_base + i0, vr);
+                tc05::tmem_ld16(lane_base + ra.Lh + i0, vi);
+                tc05::tmem_wait_ld();
+                const int n = min(16, rows_here - i0);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if (j < n) {
+                        const float re = __uint_as_float(vr[j]), im = __uint_as_float(vi[j]);
+                        __nv_bfloat162 hv = __floats2bfloat162_rn(re, im);
+                        const float2 hf = __bfloat1622float2(hv);
+                        __nv_bfloat162 l = __floats2bfloat162_rn(re - hf.x, im - hf.y);
+                        g_hi[(size_t)(i0 + j) * Cp] = *reinterpret_cast<uint32_t *>(&hv);
+                        g_lo[(size_t)(i0 + j) * Cp] = *reinterpret_cast<uint32_t *>(&l);
+                    }
+                }
+            }
+        } else {
+            if (lane == 0) atomicOr(err, 2);
+            abort_flag = 1;
+        }
+        // the TMEM reads finish before the accumulators take new products
+        tc05::fence_before_sync();
+        __syncthreads();
+        tc05::fence_after_sync();
+        if (abort_flag) {
+            // copies of item k + 2 may have been issued above
+            if (threadIdx.x == 0 && done && k + 2 < nmine && pending_tma < 0) pending_tma = k + 2;
+            break;
+        }
+    }
+    // after a timed-out wait: give copies still in flight one more budget
+    // before the shared memory is released
+    if (threadIdx.x == 0 && pending_tma >= 0)
+        tc05::mbar_wait(&bar_tma[pending_tma & 1], (pending_tma >> 1) & 1, ra.budget);
+    tc05::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc05::tmem_dealloc(tmem, 512);
 }
 
-// prod [u][plane][part][C][Lh] (uint32 = (re, im) BF16 pair) -> table
+// prod [u][plane][row][Cp] (uint32 = (re, im) BF16 pair) -> table
 // [c][plane][L][u], u beyond N_p written as zeros so the padding columns stay
 // zero. Interleaved rows hold row_words (re, im) pairs; planar rows hold
-// row_words Re entries, then row_words Im. A block covers 64 rows x 64 bins;
-// each thread transposes a 4 x 4 block in registers: four independent 16-byte
-// loads (4 rows i of one bin each) and four row stores, so a warp (16 rows x
-// 32 bins) reads and writes 64-byte runs with no shared memory or barrier.
+// row_words Re entries, then row_words Im. A block covers 64 channels x 64
+// bins of one (plane, row); each thread transposes a 4 x 4 block in
+// registers: four independent 16-byte loads (4 channels of one bin each) and
+// four row stores (4 bins of one channel), so a warp (16 channels x 32 bins)
+// reads and writes 64-byte runs with no shared memory or barrier.
 __device__ __forceinline__ uint32_t word_of(const uint4 &v, int e) {
     return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
 }
 
 template <bool PLANAR>
 __global__ void __launch_bounds__(256)
-k_rt_transpose(const uint32_t *__restrict__ prod, uint32_t *__restrict__ table, int C, int L,
-               int nh, int Lh, int Np, int row_words) {
+k_rt_transpose(const uint32_t *__restrict__ prod, uint32_t *__restrict__ table, int C, int Cp,
+               int L, int R, int Np, int row_words) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = blockIdx.x * 64 + 16 * (warp & 3) + 4 * (lane & 3);
+    const int c = blockIdx.x * 64 + 16 * (warp & 3) + 4 * (lane & 3);
     const int u = blockIdx.y * 64 + 32 * (warp >> 2) + 4 * (lane >> 2);
-    const int cp = blockIdx.z;                 // c * 2 + plane
-    const int c = cp >> 1, p = cp & 1;
-    if (i >= L || u >= row_words) return;      // row_words is a multiple of 4
-    // row i lives in part i / Lh (Lh is a multiple of 16: rows i..i+3 stay in
-    // one part; those at L and beyond are padding, loaded but never stored)
-    const int hp = i / Lh;
-    const uint32_t *src = prod + ((size_t)hp * C + c) * Lh + (i - hp * Lh);
-    const size_t bin_stride = (size_t)2 * nh * C * Lh;
+    const int p = blockIdx.z / L, i = blockIdx.z - p * L;
+    if (c >= C || u >= row_words) return;      // row_words is a multiple of 4
+    // channels c..c+3 are below Cp (a multiple of 128); those at C and beyond
+    // are loaded but never stored
+    const uint32_t *src = prod + ((size_t)p * R + i) * Cp + c;
+    const size_t bin_stride = (size_t)2 * R * Cp;
     uint4 v[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
-        v[r] = u + r < Np ? *reinterpret_cast<const uint4 *>(src + (size_t)(u + r) * bin_stride +
-                                                              (size_t)p * nh * C * Lh)
+        v[r] = u + r < Np ? *reinterpret_cast<const uint4 *>(src + (size_t)(u + r) * bin_stride)
                           : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-        if (i + e >= L) break;
+        if (c + e >= C) break;
         const uint32_t w0 = word_of(v[0], e), w1 = word_of(v[1], e);
         const uint32_t w2 = word_of(v[2], e), w3 = word_of(v[3], e);
-        uint32_t *row = table + ((size_t)cp * L + i + e) * row_words;
+        uint32_t *row = table + (((size_t)(c + e) * 2 + p) * L + i) * row_words;
         if (PLANAR) {
             // low halves (Re) of the four bins, then the high halves (Im)
             __nv_bfloat16 *rb = reinterpret_cast<__nv_bfloat16 *>(row);
@@ -287,7 +325,7 @@ k_rt_transpose(const uint32_t *__restrict__ prod, uint32_t *__restrict__ table, 
 }  // namespace
 
 size_t range_table_tc_smem_bytes(const RtTcArgs &ra) {
-    return 1024 + (size_t)4 * ra.natoms * (128 * 128 + (size_t)ra.Lh * 128);
+    return 1024 + (size_t)2 * 4 * ra.natoms * (128 * 128 + (size_t)ra.Lh * 128);
 }
 
 cudaError_t launch_setup_rt_E(const NufftDesc &d, double dz, const double *k, const double *kc,
@@ -302,6 +340,9 @@ cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
                                   const CUtensorMap &tmB, const float2 *S, const float2 *alpha,
                                   void *A, void *prod, void *table, int row_words, int planar,
                                   int *err, bool prepared, cudaStream_t st) {
+    if (ra.natoms != 1 || 4 * ra.Lh > 512 || ra.grid < 1 || row_words % 4 != 0 ||
+        2 * ra.L > 65535)
+        return cudaErrorInvalidValue;
     cudaError_t e;
     if (!prepared) {     // the z transform wrote S, not the split operand
         const long long n = (long long)ra.C * ra.Np * ra.Kp;
@@ -314,17 +355,17 @@ cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
     e = cudaFuncSetAttribute(k_range_table_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((ra.C + 127) / 128, ra.Np, ra.nh);
-    k_range_table_tc<<<grid, 128, smem, st>>>(ra, tmA, tmB, (uint32_t *)prod, err);
+    const int items = (ra.C + 127) / 128 * ra.Np * ra.nh;
+    k_range_table_tc<<<min(items, ra.grid), 256, smem, st>>>(ra, tmA, tmB, (uint32_t *)prod, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (row_words % 4 != 0 || ra.Lh % 16 != 0) return cudaErrorInvalidValue;
-    dim3 tg((ra.L + 63) / 64, (row_words + 63) / 64, 2 * ra.C);
+    const int Cp = (ra.C + 127) / 128 * 128, R = ra.nh * ra.Lh;
+    dim3 tg((ra.C + 63) / 64, (row_words + 63) / 64, 2 * ra.L);
     if (planar)
         k_rt_transpose<true><<<tg, 256, 0, st>>>((const uint32_t *)prod, (uint32_t *)table, ra.C,
-                                                 ra.L, ra.nh, ra.Lh, ra.Np, row_words);
+                                                 Cp, ra.L, R, ra.Np, row_words);
     else
         k_rt_transpose<false><<<tg, 256, 0, st>>>((const uint32_t *)prod, (uint32_t *)table, ra.C,
-                                                  ra.L, ra.nh, ra.Lh, ra.Np, row_words);
+                                                  Cp, ra.L, R, ra.Np, row_words);
     return cudaGetLastError();
 }
