@@ -212,3 +212,123 @@ __device__ __forceinline__ float2 *stockham_run_pairs(float2 *buf0, float2 *buf1
     }
     return src;
 }
+
+// First stage (N_s = 1, so every twiddle is 1) on column pairs when the
+// input is the sum of two panels: reads a + b, and after a barrier writes the
+// stage's output over b. Needs (N / R) * NCOL / 2 <= blockDim.x (one item per
+// thread), so that every read precedes every write.
+template <int R, int NCOL>
+__device__ __forceinline__ void stockham_first_stage_sum_pairs(const float2 *a_buf, float2 *b_buf,
+                                                               int N, int sgn) {
+    constexpr int NP = NCOL / 2;
+    const int nr = N / R;
+    const int it = threadIdx.x;
+    const bool act = it < nr * NP;
+    const int j = it / NP;
+    const int cp = it - j * NP;
+    float2 a[8], b[8];
+    if (act) {
+        const float4 *s4 = reinterpret_cast<const float4 *>(a_buf);
+        const float4 *t4 = reinterpret_cast<const float4 *>(b_buf);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float4 x = s4[(j + r * nr) * NP + cp], y = t4[(j + r * nr) * NP + cp];
+            a[r] = make_float2(x.x + y.x, x.y + y.y);
+            b[r] = make_float2(x.z + y.z, x.w + y.w);
+        }
+        stockham_detail::small_dft<R>(a, sgn);
+        stockham_detail::small_dft<R>(b, sgn);
+    }
+    __syncthreads();
+    if (act) {
+        float4 *d4 = reinterpret_cast<float4 *>(b_buf);
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+            d4[(j * R + q) * NP + cp] = make_float4(a[q].x, a[q].y, b[q].x, b[q].y);
+    }
+}
+
+// Last stage (N_s = N / R: every output row is j + q N_s, twiddle step 1) on
+// column pairs, handing each output row to emit(row, column pair, first
+// column, second column) instead of writing shared memory.
+template <int R, int NCOL, class Emit>
+__device__ __forceinline__ void stockham_last_stage_pairs(const float2 *src, const float2 *tw,
+                                                          int N, int sgn, const Emit &emit) {
+    constexpr int NP = NCOL / 2;
+    const int nr = N / R;
+    const int items = nr * NP;
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int j = it / NP;
+        const int cp = it - j * NP;
+        float2 a[8], b[8];
+        float4 x = s4[j * NP + cp];
+        a[0] = make_float2(x.x, x.y);
+        b[0] = make_float2(x.z, x.w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            float2 w = tw[j * r];
+            if (sgn > 0) w.y = -w.y;
+            x = s4[(j + r * nr) * NP + cp];
+            a[r] = cmul(make_float2(x.x, x.y), w);
+            b[r] = cmul(make_float2(x.z, x.w), w);
+        }
+        stockham_detail::small_dft<R>(a, sgn);
+        stockham_detail::small_dft<R>(b, sgn);
+#pragma unroll
+        for (int q = 0; q < R; ++q) emit(j + q * nr, cp, a[q], b[q]);
+    }
+}
+
+// Every stage of `plan` on NCOL columns (column pairs), the input the sum of
+// buf0 and buf1 when `sum2` (else buf0 alone), the last stage's rows handed
+// to `emit`. Both buffers 16-byte aligned.
+template <int NCOL, class Emit>
+__device__ __forceinline__ void stockham_run_pairs_emit(float2 *buf0, float2 *buf1, const float2 *tw,
+                                                        const FftPlan &plan, int sgn, bool sum2,
+                                                        const Emit &emit) {
+    const int N = plan.n;
+    const int S = plan.n_stages;
+    float2 *src = buf0, *dst = buf1;
+    int Ns = 1;
+    int s = 0;
+    if (sum2) {
+        const int R = plan.radix[0];
+        if (S >= 2 && (N / R) * (NCOL / 2) <= (int)blockDim.x) {
+            if (R == 8) stockham_first_stage_sum_pairs<8, NCOL>(buf0, buf1, N, sgn);
+            else if (R == 4) stockham_first_stage_sum_pairs<4, NCOL>(buf0, buf1, N, sgn);
+            else if (R == 2) stockham_first_stage_sum_pairs<2, NCOL>(buf0, buf1, N, sgn);
+            else if (R == 3) stockham_first_stage_sum_pairs<3, NCOL>(buf0, buf1, N, sgn);
+            else stockham_first_stage_sum_pairs<5, NCOL>(buf0, buf1, N, sgn);
+            __syncthreads();
+            src = buf1;
+            dst = buf0;
+            Ns = R;
+            s = 1;
+        } else {     // a separate pass: buf0 += buf1
+            for (int idx = threadIdx.x; idx < N * NCOL / 2; idx += blockDim.x) {
+                float4 *p = reinterpret_cast<float4 *>(buf0) + idx;
+                const float4 c = reinterpret_cast<const float4 *>(buf1)[idx];
+                *p = make_float4(p->x + c.x, p->y + c.y, p->z + c.z, p->w + c.w);
+            }
+            __syncthreads();
+        }
+    }
+    for (; s < S - 1; ++s) {
+        const int R = plan.radix[s];
+        if (R == 8) stockham_stage_pairs<8, NCOL>(src, dst, tw, N, Ns, sgn);
+        else if (R == 4) stockham_stage_pairs<4, NCOL>(src, dst, tw, N, Ns, sgn);
+        else if (R == 2) stockham_stage_pairs<2, NCOL>(src, dst, tw, N, Ns, sgn);
+        else if (R == 3) stockham_stage_pairs<3, NCOL>(src, dst, tw, N, Ns, sgn);
+        else stockham_stage_pairs<5, NCOL>(src, dst, tw, N, Ns, sgn);
+        __syncthreads();
+        float2 *t = src; src = dst; dst = t;
+        Ns *= R;
+    }
+    const int R = plan.radix[S - 1];
+    if (R == 8) stockham_last_stage_pairs<8, NCOL>(src, tw, N, sgn, emit);
+    else if (R == 4) stockham_last_stage_pairs<4, NCOL>(src, tw, N, sgn, emit);
+    else if (R == 2) stockham_last_stage_pairs<2, NCOL>(src, tw, N, sgn, emit);
+    else if (R == 3) stockham_last_stage_pairs<3, NCOL>(src, tw, N, sgn, emit);
+    else stockham_last_stage_pairs<5, NCOL>(src, tw, N, sgn, emit);
+}

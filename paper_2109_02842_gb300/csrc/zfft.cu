@@ -30,7 +30,8 @@ struct SplitOut {
 };
 // PAIRS (I even): every access moves two adjacent columns (16-byte copies,
 // float4 shared-memory accesses, column pairs through the FFT stages).
-template <bool PAIRS>
+// SPLIT: the output is the range table's operand (sp.A), else `out`.
+template <bool PAIRS, bool SPLIT>
 __global__ void __launch_bounds__(kFftThreads)
 k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, float2 *__restrict__ out,
               int n_in, int I, FftPlan plan, const float2 *__restrict__ tw_g, int sgn,
@@ -80,6 +81,26 @@ k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, flo
     }
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
+
+    if constexpr (PAIRS) {
+        // plain output: the last FFT stage writes the output rows itself
+        // (transform index t to output row (t - out_off) mod N when that is
+        // below out_rows). The split operand keeps its own pass below, where
+        // the loads of alpha overlap better.
+        if constexpr (!SPLIT) {
+            float2 *o0 = out + b * out_rows * (size_t)I + i0;
+            auto emit = [&](int t, int cp, float2 x0, float2 x1) {
+                int r = t - out_off;
+                if (r < 0) r += N;
+                if (r >= out_rows || i0 + 2 * cp >= I) return;
+                *reinterpret_cast<float4 *>(o0 + (size_t)r * I + 2 * cp) =
+                    make_float4(scale * x0.x, scale * x0.y, scale * x1.x, scale * x1.y);
+            };
+            stockham_run_pairs_emit<kFftIB>(buf0, buf1, tw, plan, sgn, in2 != nullptr, emit);
+            return;
+        }
+    }
+
     if (in2) {
         for (int idx = threadIdx.x; idx < N * kFftIB / 2; idx += kFftThreads) {
             float4 *a = reinterpret_cast<float4 *>(buf0) + idx;
@@ -88,13 +109,12 @@ k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, flo
         }
         __syncthreads();
     }
-
     const float2 *src = PAIRS ? stockham_run_pairs<kFftIB>(buf0, buf1, tw, plan, sgn)
                               : stockham_run<true, kFftIB>(buf0, buf1, tw, plan, sgn, 1, kFftIB);
 
     // out_off < N and r < out_rows <= N: one conditional subtraction wraps
     if (!col_ok) return;
-    if (sp.A) {
+    if constexpr (SPLIT) {
         const size_t plane = (size_t)sp.batch * sp.Kp;
         __nv_bfloat16 *o = sp.A + (size_t)n_first * 4 * plane + b * sp.Kp + i0 + col;
         const float2 *al = sp.alpha + (size_t)n_first * I + i0 + col;
@@ -216,7 +236,8 @@ cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_i
                        (split_A ? (split_Kp % 2 == 0 && (uintptr_t)split_A % 4 == 0 &&
                                    (uintptr_t)split_alpha % 16 == 0)
                                 : (uintptr_t)out % 16 == 0);
-    auto kern = pairs ? k_fft_strided<true> : k_fft_strided<false>;
+    auto kern = split_A ? (pairs ? k_fft_strided<true, true> : k_fft_strided<false, true>)
+                        : (pairs ? k_fft_strided<true, false> : k_fft_strided<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
