@@ -12,8 +12,8 @@ size_t fft_strided_smem_bytes(int n);
 cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_in, int I,
                                const FftPlan &plan, const float2 *tw, int sgn, float scale,
                                int out_rows, int out_off, cudaStream_t st,
-                               const float2 *split_alpha = nullptr, void *split_A = nullptr,
-                               int split_Kp = 0, const float2 *in2 = nullptr);
+                               void *split_A = nullptr, int split_Kp = 0,
+                               const float2 *in2 = nullptr);
 // in2 (optional): a second input of the same shape, added to `in` on load
 cudaError_t launch_dft_strided(const float2 *in, float2 *out, int batch, int n_in, int I,
                                int out_rows, const float2 *T, float scale, cudaStream_t st,
@@ -137,14 +137,14 @@ struct RtTcArgs {
     int grid;            // persistent blocks (one per SM)
 };
 size_t range_table_tc_smem_bytes(const RtTcArgs &ra);
-// E [N_p][re hi, re lo, im hi, im lo][Lp][Kp] BF16: e^{+j theta_um (i - L/2)}
+// E [N_p][re hi, re lo, im hi, im lo][Lp][Kp] BF16: alpha_um e^{+j theta_um (i - L/2)}
 cudaError_t launch_setup_rt_E(const NufftDesc &d, double dz, const double *k, const double *kc,
-                              int Lp, int Kp, void *E, cudaStream_t st);
-// S, alpha -> A (scratch [N_p][4][C][Kp] BF16; skipped when `prepared`: the
+                              const float2 *alpha, int Lp, int Kp, void *E, cudaStream_t st);
+// S -> A (scratch [N_p][4][C][Kp] BF16; skipped when `prepared`: the
 // z-FFT wrote A) -> prod (scratch [N_p][2][nh * Lh][C rounded up to 128] uint32) -> table
 // [C][2][L][row_words uint32]
 cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
-                                  const CUtensorMap &tmB, const float2 *S, const float2 *alpha,
+                                  const CUtensorMap &tmB, const float2 *S,
                                   void *A, void *prod, void *table, int row_words, int planar, int *err,
                                   bool prepared, cudaStream_t st);
 

@@ -622,7 +622,8 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
             PL_CUDA(cudaMemset(P->d_rtA, 0, nA * 2), "cudaMemset");   // frequencies >= M stay 0
             PL_CUDA(cudaMalloc(&P->d_rtprod, nprod * 4), "cudaMalloc");
             ws += nE * 2 + nA * 2 + nprod * 4;
-            PL_CUDA(launch_setup_rt_E(d, P->dzs, P->d_k, P->d_kc, ra.Lp, ra.Kp, P->d_rtE, st),
+            PL_CUDA(launch_setup_rt_E(d, P->dzs, P->d_k, P->d_kc, P->d_alpha, ra.Lp, ra.Kp,
+                                      P->d_rtE, st),
                     "setup_rt_E");
             const cuuint64_t da[3] = {(cuuint64_t)ra.Kp, (cuuint64_t)P->C, 4 * (cuuint64_t)P->Np};
             const cuuint64_t sa[2] = {(cuuint64_t)ra.Kp * 2, (cuuint64_t)P->C * ra.Kp * 2};
@@ -654,7 +655,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
 static pl_status stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st, bool split) {
     if (P->fwd_fft && split)      // straight into the tensor-core range table's operand
         PL_CUDA(launch_fft_strided(echo, P->d_S, P->C, P->N, P->M, P->zplan, P->d_twz, -1, 1.0f,
-                                   P->Np, 0, st, P->d_alpha, P->d_rtA, P->rt.Kp), "zfft");
+                                   P->Np, 0, st, P->d_rtA, P->rt.Kp), "zfft");
     else if (P->fwd_fft)
         PL_CUDA(launch_fft_strided(echo, P->d_S, P->C, P->N, P->M, P->zplan, P->d_twz, -1, 1.0f,
                                    P->Np, 0, st), "zfft");
@@ -670,7 +671,7 @@ pl_status pl_stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st) {
 
 pl_status pl_stage_range_table(pl_plan *P, cudaStream_t st) {
     if (P->block_config == 4 && P->rt_tc) {
-        PL_CUDA(launch_range_table_tc(P->rt, P->tmapA, P->tmapE, P->d_S, P->d_alpha, P->d_rtA,
+        PL_CUDA(launch_range_table_tc(P->rt, P->tmapA, P->tmapE, P->d_S, P->d_rtA,
                                       P->d_rtprod, P->d_table, P->nd.tc_cols / 2,
                                       P->nd.tc_planar, P->d_err, P->fwd_fft, st),
                 "range_table_tc");
@@ -701,8 +702,8 @@ static pl_status stage_zifft(pl_plan *P, float2 *image, cudaStream_t st, int par
     const float2 *G2 = parts > 1 ? P->d_G + (size_t)P->Np * P2 : nullptr;
     if (P->inv_fft)
         PL_CUDA(launch_fft_strided(P->d_G, image, 1, P->Np, P2, P->zplan, P->d_twz, +1,
-                                   1.0f / P->Np, P->grid.nz, P->inv_off, st, nullptr, nullptr,
-                                   0, G2), "zifft");
+                                   1.0f / P->Np, P->grid.nz, P->inv_off, st, nullptr, 0, G2),
+                "zifft");
     else
         PL_CUDA(launch_dft_strided(P->d_G, image, 1, P->Np, P2, P->grid.nz, P->d_Tinv,
                                    1.0f / P->Np, st, G2), "zidft");

@@ -1,7 +1,7 @@
 // Range-profile table of step (8a) / (19a) for the tensor-core back-projection,
 // evaluated as exact sums on the tensor cores instead of a type-1 NUFFT:
 //
-//   b[c][i][u] = sum_m a[c][u][m] e^{+j theta_um (i - L/2)},   a = S alpha,
+//   b[c][i][u] = sum_m S[c][u][m] E[u][i][m],   E = alpha e^{+j theta_um (i - L/2)},
 //
 // theta_um = kappa''_um h and alpha as in setup.cu (k weight, 1/phihat of the
 // interpolation kernel, range-origin phase). For one k_z bin u this is a
@@ -11,7 +11,7 @@
 // four real ones with the imaginary-by-imaginary term negated through the
 // instruction descriptor, and the two accumulators (Re, Im) live in TMEM.
 //
-//   k_rt_prep          S [C][N_p][M] x alpha -> A [u][re hi, re lo, im hi, im lo][C][K] BF16
+//   k_rt_prep          S [C][N_p][M] -> A [u][re hi, re lo, im hi, im lo][C][K] BF16
 //   k_range_table_tc   persistent, one block per SM, over the items (128-channel
 //                      block, bin, row part): TMA (128-byte swizzled, K-major) A
 //                      and E tiles, 12 MMAs per 16-frequency step, tcgen05.ld,
@@ -26,7 +26,8 @@
 //                      planar: Re at column u, Im at row_words + u), the layout
 //                      the back-projection streams (u innermost)
 //
-// E [u][re hi, re lo, im hi, im lo][L'][K] = e^{+j theta (i - L/2)} is a plan-time table.
+// E [u][re hi, re lo, im hi, im lo][L'][K] = alpha_um e^{+j theta_um (i - L/2)} is a
+// plan-time table (the per-(k_z, f) factor on the side of the smaller operand).
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -45,8 +46,8 @@ __device__ __forceinline__ double kz_at(int u, int n_pad, double dz) {
     return PL_TWO_PI * (double)ut / ((double)n_pad * dz);
 }
 
-__global__ void k_setup_rt_E(NufftDesc d, double dz, const double *k, const double *kc, int Lp,
-                             int Kp, __nv_bfloat16 *E) {
+__global__ void k_setup_rt_E(NufftDesc d, double dz, const double *k, const double *kc,
+                             const float2 *alpha, int Lp, int Kp, __nv_bfloat16 *E) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)d.n_pad * Lp * Kp) return;
     const int m = (int)(idx % Kp);
@@ -57,9 +58,13 @@ __global__ void k_setup_rt_E(NufftDesc d, double dz, const double *k, const doub
         const double kz = kz_at(u, d.n_pad, dz);
         const double q = d.mode == 0 ? 4.0 * k[m] * k[m] - kz * kz : k[m] * k[m] - 0.25 * kz * kz;
         if (q > 0.0) {
+            // the source factor alpha_um (k weight, 1 / phihat, range-origin
+            // phase) rides on E, so the operand A is the plain spectrum
             const double ph = (sqrt(q) - kc[u]) * d.h * (double)(i - d.L / 2);
-            re = cos(ph);
-            im = sin(ph);
+            const float2 al = alpha[(size_t)u * d.n_f + m];
+            const double c = cos(ph), sn = sin(ph);
+            re = (double)al.x * c - (double)al.y * sn;
+            im = (double)al.x * sn + (double)al.y * c;
         }
     }
     __nv_bfloat16 h, l;
@@ -73,16 +78,16 @@ __global__ void k_setup_rt_E(NufftDesc d, double dz, const double *k, const doub
     E[base + 3 * plane] = l;
 }
 
-// A[u][plane][c][m] = split(S[c][u][m] alpha[u][m]) (zero for m >= M)
-__global__ void k_rt_prep(const float2 *__restrict__ S, const float2 *__restrict__ alpha, int C,
-                          int Np, int M, int Kp, __nv_bfloat16 *__restrict__ A) {
+// A[u][plane][c][m] = split(S[c][u][m]) (zero for m >= M)
+__global__ void k_rt_prep(const float2 *__restrict__ S, int C, int Np, int M, int Kp,
+                          __nv_bfloat16 *__restrict__ A) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)C * Np * Kp) return;
     const int m = (int)(idx % Kp);
     const int u = (int)((idx / Kp) % Np);
     const int c = (int)(idx / ((long long)Kp * Np));
     float2 a = make_float2(0.f, 0.f);
-    if (m < M) a = cmul(S[((size_t)c * Np + u) * M + m], alpha[(size_t)u * M + m]);
+    if (m < M) a = S[((size_t)c * Np + u) * M + m];
     __nv_bfloat16 h, l;
     const size_t plane = (size_t)C * Kp;
     const size_t base = (size_t)u * 4 * plane + (size_t)c * Kp + m;
@@ -329,15 +334,15 @@ size_t range_table_tc_smem_bytes(const RtTcArgs &ra) {
 }
 
 cudaError_t launch_setup_rt_E(const NufftDesc &d, double dz, const double *k, const double *kc,
-                              int Lp, int Kp, void *E, cudaStream_t st) {
+                              const float2 *alpha, int Lp, int Kp, void *E, cudaStream_t st) {
     const long long n = (long long)d.n_pad * Lp * Kp;
-    k_setup_rt_E<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d, dz, k, kc, Lp, Kp,
+    k_setup_rt_E<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d, dz, k, kc, alpha, Lp, Kp,
                                                               (__nv_bfloat16 *)E);
     return cudaGetLastError();
 }
 
 cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
-                                  const CUtensorMap &tmB, const float2 *S, const float2 *alpha,
+                                  const CUtensorMap &tmB, const float2 *S,
                                   void *A, void *prod, void *table, int row_words, int planar,
                                   int *err, bool prepared, cudaStream_t st) {
     if (ra.natoms != 1 || 4 * ra.Lh > 512 || ra.grid < 1 || row_words % 4 != 0 ||
@@ -346,8 +351,8 @@ cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
     cudaError_t e;
     if (!prepared) {     // the z transform wrote S, not the split operand
         const long long n = (long long)ra.C * ra.Np * ra.Kp;
-        k_rt_prep<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S, alpha, ra.C, ra.Np, ra.M,
-                                                               ra.Kp, (__nv_bfloat16 *)A);
+        k_rt_prep<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S, ra.C, ra.Np, ra.M, ra.Kp,
+                                                               (__nv_bfloat16 *)A);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -22,9 +22,8 @@ constexpr int kFftThreads = 256;  // threads per block
 // in:  [batch][n_in][I]  (rows n >= n_in are zero padding)
 // out: [batch][out_rows][I], out row r = transform index (r + out_off) mod N;
 // or, with sp.A set, the tensor-core range table's operand instead:
-// A[r][re hi, re lo, im hi, im lo][batch][Kp] = split(X[r][i] alpha[r][i]) (BF16)
+// A[r][re hi, re lo, im hi, im lo][batch][Kp] = split(X[r][i]) (BF16)
 struct SplitOut {
-    const float2 *alpha;     // [out_rows][I]
     __nv_bfloat16 *A;        // nullptr: plain output
     int batch, Kp;
 };
@@ -83,11 +82,30 @@ k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, flo
     __syncthreads();
 
     if constexpr (PAIRS) {
-        // plain output: the last FFT stage writes the output rows itself
-        // (transform index t to output row (t - out_off) mod N when that is
-        // below out_rows). The split operand keeps its own pass below, where
-        // the loads of alpha overlap better.
-        if constexpr (!SPLIT) {
+        // the last FFT stage writes the output rows itself: transform index t
+        // goes to output row (t - out_off) mod N when that is below out_rows
+        if constexpr (SPLIT) {
+            const size_t plane = (size_t)sp.batch * sp.Kp;
+            __nv_bfloat16 *A = sp.A + b * sp.Kp + i0;
+            auto emit = [&](int t, int cp, float2 x0, float2 x1) {
+                int r = t - out_off;
+                if (r < 0) r += N;
+                if (r >= out_rows || i0 + 2 * cp >= I) return;
+                const float2 v0 = cscale(x0, scale), v1 = cscale(x1, scale);
+                const __nv_bfloat16 h0 = __float2bfloat16(v0.x), h1 = __float2bfloat16(v1.x);
+                const __nv_bfloat16 g0 = __float2bfloat16(v0.y), g1 = __float2bfloat16(v1.y);
+                __nv_bfloat16 *o = A + (size_t)r * 4 * plane + 2 * cp;
+                *reinterpret_cast<__nv_bfloat162 *>(o) = __halves2bfloat162(h0, h1);
+                *reinterpret_cast<__nv_bfloat162 *>(o + plane) = __halves2bfloat162(
+                    __float2bfloat16(v0.x - __bfloat162float(h0)),
+                    __float2bfloat16(v1.x - __bfloat162float(h1)));
+                *reinterpret_cast<__nv_bfloat162 *>(o + 2 * plane) = __halves2bfloat162(g0, g1);
+                *reinterpret_cast<__nv_bfloat162 *>(o + 3 * plane) = __halves2bfloat162(
+                    __float2bfloat16(v0.y - __bfloat162float(g0)),
+                    __float2bfloat16(v1.y - __bfloat162float(g1)));
+            };
+            stockham_run_pairs_emit<kFftIB>(buf0, buf1, tw, plan, sgn, in2 != nullptr, emit);
+        } else {
             float2 *o0 = out + b * out_rows * (size_t)I + i0;
             auto emit = [&](int t, int cp, float2 x0, float2 x1) {
                 int r = t - out_off;
@@ -97,8 +115,8 @@ k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, flo
                     make_float4(scale * x0.x, scale * x0.y, scale * x1.x, scale * x1.y);
             };
             stockham_run_pairs_emit<kFftIB>(buf0, buf1, tw, plan, sgn, in2 != nullptr, emit);
-            return;
         }
+        return;
     }
 
     if (in2) {
@@ -109,60 +127,28 @@ k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, flo
         }
         __syncthreads();
     }
-    const float2 *src = PAIRS ? stockham_run_pairs<kFftIB>(buf0, buf1, tw, plan, sgn)
-                              : stockham_run<true, kFftIB>(buf0, buf1, tw, plan, sgn, 1, kFftIB);
-
+    // single columns (I odd or unaligned buffers)
+    const float2 *src = stockham_run<true, kFftIB>(buf0, buf1, tw, plan, sgn, 1, kFftIB);
     // out_off < N and r < out_rows <= N: one conditional subtraction wraps
     if (!col_ok) return;
     if constexpr (SPLIT) {
         const size_t plane = (size_t)sp.batch * sp.Kp;
         __nv_bfloat16 *o = sp.A + (size_t)n_first * 4 * plane + b * sp.Kp + i0 + col;
-        const float2 *al = sp.alpha + (size_t)n_first * I + i0 + col;
-        for (int r = n_first; r < out_rows; r += RPS, o += (size_t)RPS * 4 * plane,
-                 al += (size_t)RPS * I) {
+        for (int r = n_first; r < out_rows; r += RPS, o += (size_t)RPS * 4 * plane) {
             int sr = r + out_off;
             if (sr >= N) sr -= N;
-            float2 v[CW], a[CW];
-            if (PAIRS) {
-                const float4 x = *reinterpret_cast<const float4 *>(src + sr * kFftIB + col);
-                const float4 w = *reinterpret_cast<const float4 *>(al);
-                v[0] = make_float2(x.x, x.y);
-                v[CW - 1] = make_float2(x.z, x.w);
-                a[0] = make_float2(w.x, w.y);
-                a[CW - 1] = make_float2(w.z, w.w);
-            } else {
-                v[0] = src[sr * kFftIB + col];
-                a[0] = al[0];
-            }
-            __nv_bfloat16 h[4][CW];
-#pragma unroll
-            for (int e = 0; e < CW; ++e) {
-                const float2 t = cmul(cscale(v[e], scale), a[e]);
-                h[0][e] = __float2bfloat16(t.x);
-                h[1][e] = __float2bfloat16(t.x - __bfloat162float(h[0][e]));
-                h[2][e] = __float2bfloat16(t.y);
-                h[3][e] = __float2bfloat16(t.y - __bfloat162float(h[2][e]));
-            }
-#pragma unroll
-            for (int pl = 0; pl < 4; ++pl) {
-                if (PAIRS)
-                    *reinterpret_cast<__nv_bfloat162 *>(o + pl * plane) =
-                        __halves2bfloat162(h[pl][0], h[pl][CW - 1]);
-                else
-                    o[pl * plane] = h[pl][0];
-            }
+            const float2 t = cscale(src[sr * kFftIB + col], scale);
+            const __nv_bfloat16 h = __float2bfloat16(t.x), g = __float2bfloat16(t.y);
+            o[0] = h;
+            o[plane] = __float2bfloat16(t.x - __bfloat162float(h));
+            o[2 * plane] = g;
+            o[3 * plane] = __float2bfloat16(t.y - __bfloat162float(g));
         }
-        return;
-    }
-    float2 *o = out + (b * out_rows + n_first) * (size_t)I + i0 + col;
-    for (int r = n_first; r < out_rows; r += RPS, o += (size_t)RPS * I) {
-        int sr = r + out_off;
-        if (sr >= N) sr -= N;
-        if (PAIRS) {
-            const float4 x = *reinterpret_cast<const float4 *>(src + sr * kFftIB + col);
-            *reinterpret_cast<float4 *>(o) =
-                make_float4(scale * x.x, scale * x.y, scale * x.z, scale * x.w);
-        } else {
+    } else {
+        float2 *o = out + (b * out_rows + n_first) * (size_t)I + i0 + col;
+        for (int r = n_first; r < out_rows; r += RPS, o += (size_t)RPS * I) {
+            int sr = r + out_off;
+            if (sr >= N) sr -= N;
             *o = cscale(src[sr * kFftIB + col], scale);
         }
     }
@@ -227,14 +213,12 @@ size_t fft_strided_smem_bytes(int n) { return (size_t)(2 * n * kFftIB + n) * siz
 cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_in, int I,
                                const FftPlan &plan, const float2 *tw, int sgn, float scale,
                                int out_rows, int out_off, cudaStream_t st,
-                               const float2 *split_alpha, void *split_A, int split_Kp,
-                               const float2 *in2) {
+                               void *split_A, int split_Kp, const float2 *in2) {
     const size_t smem = fft_strided_smem_bytes(plan.n);
     // column pairs need 16-byte aligned rows: I even, 16-byte aligned
     // buffers, and (split output) an even operand row length
     const bool pairs = (I % 2 == 0) && ((uintptr_t)in % 16 == 0) && ((uintptr_t)in2 % 16 == 0) &&
-                       (split_A ? (split_Kp % 2 == 0 && (uintptr_t)split_A % 4 == 0 &&
-                                   (uintptr_t)split_alpha % 16 == 0)
+                       (split_A ? (split_Kp % 2 == 0 && (uintptr_t)split_A % 4 == 0)
                                 : (uintptr_t)out % 16 == 0);
     auto kern = split_A ? (pairs ? k_fft_strided<true, true> : k_fft_strided<false, true>)
                         : (pairs ? k_fft_strided<true, false> : k_fft_strided<false, false>);
@@ -242,7 +226,7 @@ cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_i
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((I + kFftIB - 1) / kFftIB, batch);
-    const SplitOut sp{split_alpha, (__nv_bfloat16 *)split_A, batch, split_Kp};
+    const SplitOut sp{(__nv_bfloat16 *)split_A, batch, split_Kp};
     kern<<<grid, kFftThreads, smem, st>>>(in, in2, out, n_in, I, plan, tw, sgn, scale, out_rows, out_off,
                                   sp);
     return cudaGetLastError();
