@@ -121,9 +121,14 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_full + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-    // blockIdx.z = bin block x channel part: channels [cb, ce) of the tile
-    const int utile = blockIdx.z / ta.nsplit, part = blockIdx.z - utile * ta.nsplit;
+    // linear block index (tile x fastest, then tile y, then bin block x
+    // channel part), from ta.blk0 on: a launch may cover a range of blocks
+    const int nbx = (p.nx + TCX - 1) / TCX, nby = (p.ny + TCY - 1) / TCY;
+    const int lin = (int)blockIdx.x + ta.blk0;
+    const int bx = lin % nbx, by = (lin / nbx) % nby, bz = lin / (nbx * nby);
+    const int tile = by * nbx + bx;
+    // bz = bin block x channel part: channels [cb, ce) of the tile
+    const int utile = bz / ta.nsplit, part = bz - utile * ta.nsplit;
     const int u0 = utile * ta.UT;
     const int C = p.n_chan;
     const int cper = (C + ta.nsplit - 1) / ta.nsplit;
@@ -269,7 +274,7 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
         done = __all_sync(0xffffffffu, done);
         if (done) {
             tc05::fence_after_sync();
-            const int ix = blockIdx.x * TCX + px, iy = blockIdx.y * TCY + py;
+            const int ix = bx * TCX + px, iy = by * TCY + py;
             const bool inside = ix < p.nx && iy < p.ny;
             const size_t plane = (size_t)p.nx * p.ny;
             const size_t pofs = (size_t)iy * p.nx + ix;
@@ -462,8 +467,10 @@ cudaError_t launch_t(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, con
     cudaError_t e = cudaFuncSetAttribute(k_backproject_tc<W, KS, SPLIT, NPAR, PLANAR, CPR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((p.nx + TCX - 1) / TCX, (p.ny + TCY - 1) / TCY, ta.n_utiles * ta.nsplit);
-    k_backproject_tc<W, KS, SPLIT, NPAR, PLANAR, CPR><<<grid, Warps<NPAR>::threads, smem, st>>>(
+    const int total = backproject_tc_blocks(p, ta);
+    const int nblk = ta.nblk > 0 ? ta.nblk : total - ta.blk0;
+    if (ta.blk0 < 0 || nblk <= 0 || ta.blk0 + nblk > total) return cudaErrorInvalidValue;
+    k_backproject_tc<W, KS, SPLIT, NPAR, PLANAR, CPR><<<nblk, Warps<NPAR>::threads, smem, st>>>(
         p, ct, ta, tm, tgeo, kc_hl, G, err);
     return cudaGetLastError();
 }
@@ -504,6 +511,10 @@ cudaError_t launch_p(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, con
 }
 
 }  // namespace
+
+int backproject_tc_blocks(const BpDesc &p, const TcArgs &ta) {
+    return (p.nx + TCX - 1) / TCX * ((p.ny + TCY - 1) / TCY) * ta.n_utiles * ta.nsplit;
+}
 
 int backproject_tc_tile_x() { return TCX; }
 int backproject_tc_tile_y() { return TCY; }

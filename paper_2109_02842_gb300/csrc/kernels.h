@@ -13,7 +13,9 @@ cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_i
                                const FftPlan &plan, const float2 *tw, int sgn, float scale,
                                int out_rows, int out_off, cudaStream_t st,
                                void *split_A = nullptr, int split_Kp = 0,
-                               const float2 *in2 = nullptr);
+                               const float2 *in2 = nullptr, int ld = 0);
+// (ld: row stride in elements, 0 = I; a launch may cover columns [0, I) of
+// wider rows, the pointers offset by the first column)
 // in2 (optional): a second input of the same shape, added to `in` on load
 cudaError_t launch_dft_strided(const float2 *in, float2 *out, int batch, int n_in, int I,
                                int out_rows, const float2 *T, float scale, cudaStream_t st,
@@ -111,7 +113,11 @@ struct TcArgs {
     int cpr;             // channels per class round (1, or 2 with npar 3): A buffers of cpr
                          // channels, one A-ready wait and one release per round
     long long budget;    // wait budget, SM clock cycles
+    int blk0, nblk;      // the launch's blocks: linear indices [blk0, blk0 + nblk) of
+                         // (tile x, tile y, bin block x part), x fastest; nblk 0: to the end
 };
+// blocks of a whole back-projection
+int backproject_tc_blocks(const BpDesc &p, const TcArgs &ta);
 int backproject_tc_tile_x();
 int backproject_tc_tile_y();
 size_t backproject_tc_smem_bytes(const TcArgs &ta);

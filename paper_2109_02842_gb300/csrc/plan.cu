@@ -646,6 +646,33 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     // back-projection splits each tile's channels
     const int g_parts = P->block_config == 4 ? P->tc.nsplit : 1;
     PL_CUDA(dalloc(&P->d_G, (size_t)g_parts * P->Np * gr->nx * gr->ny, ws), "cudaMalloc");
+    // blocks of the back-projection's full waves, and the pixels whose every
+    // channel part they cover: with one bin block, tile t's last part is
+    // block (nsplit - 1) T + t, so the first bp_full - (nsplit - 1) T tiles
+    // (whole rows of tiles of them) are done when the full waves are
+    if (P->block_config == 4 && P->tc.planar && P->tc.n_utiles == 1 && P->inv_fft) {
+        int dev = 0, sms = 0;
+        PL_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+        PL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev),
+                "cudaDeviceGetAttribute");
+        const size_t smem = backproject_tc_smem_bytes(P->tc) + 1024;
+        const int per_sm = std::max(1, std::min(512 / P->tc.tmem_cols, (int)((228 * 1024) / smem)));
+        const int wave = sms * per_sm;
+        const int total = backproject_tc_blocks(P->bp, P->tc);
+        const int full = total / wave * wave;
+        const int T = total / P->tc.nsplit;
+        const int nbx = (gr->nx + backproject_tc_tile_x() - 1) / backproject_tc_tile_x();
+        const int tiles_done = std::max(0, full - (P->tc.nsplit - 1) * T);
+        const int rows = std::min(gr->ny, tiles_done / nbx * backproject_tc_tile_y());
+        if (full > 0 && full < total && rows > 0) {
+            PL_CUDA(cudaStreamCreateWithFlags(&P->s_bp, cudaStreamNonBlocking),
+                    "cudaStreamCreateWithFlags");
+            PL_CUDA(cudaEventCreateWithFlags(&P->ev_bpA, cudaEventDisableTiming), "cudaEventCreate");
+            PL_CUDA(cudaEventCreateWithFlags(&P->ev_bpB, cudaEventDisableTiming), "cudaEventCreate");
+            P->bp_full = full;
+            P->zi_cols = rows * gr->nx;
+        }
+    }
     PL_CUDA(cudaDeviceSynchronize(), "plan setup");
     return PL_OK;
 }
@@ -714,6 +741,47 @@ pl_status pl_stage_zifft(pl_plan *P, float2 *image, cudaStream_t st) {
     return stage_zifft(P, image, st, P->block_config == 4 ? P->tc.nsplit : 1);
 }
 
+// a5 + a6 with the back-projection's last partial wave beside the z-IFFT of
+// the pixels the full waves finished (P->bp_full > 0). The last wave follows
+// the full waves on the caller's stream, so its blocks are dispatched as soon
+// as SMs free up; the transform of the finished pixels waits on an event on
+// s_bp and takes the SMs the last wave leaves idle. Timing events (may be
+// null): t[0], t[1] around the back-projection, t[2], t[3] around the z-IFFT
+// left after it (the rest of the pixels, and the join).
+static pl_status stage_bp_zifft_overlapped(pl_plan *P, float2 *image, cudaStream_t st,
+                                           const cudaEvent_t (&t)[4]) {
+    const int P2 = P->grid.nx * P->grid.ny;
+    const int parts = P->tc.nsplit;
+    const float2 *G2 = parts > 1 ? P->d_G + (size_t)P->Np * P2 : nullptr;
+    TcArgs a = P->tc;
+    if (t[0]) PL_CUDA(cudaEventRecord(t[0], st), "event");
+    a.blk0 = 0;
+    a.nblk = P->bp_full;
+    PL_CUDA(launch_backproject_tc(P->bp, P->coef, a, P->tmap, P->d_tgeo, P->d_kchl, P->d_G,
+                                  P->d_err, st), "backproject_tc (full waves)");
+    PL_CUDA(cudaEventRecord(P->ev_bpA, st), "event");
+    // Eq. (9) on the finished pixels [0, zi_cols), beside the last wave
+    PL_CUDA(cudaStreamWaitEvent(P->s_bp, P->ev_bpA, 0), "cudaStreamWaitEvent");
+    PL_CUDA(launch_fft_strided(P->d_G, image, 1, P->Np, P->zi_cols, P->zplan, P->d_twz, +1,
+                               1.0f / P->Np, P->grid.nz, P->inv_off, P->s_bp, nullptr, 0, G2, P2),
+            "zifft (finished pixels)");
+    PL_CUDA(cudaEventRecord(P->ev_bpB, P->s_bp), "event");
+    a.blk0 = P->bp_full;
+    a.nblk = 0;
+    PL_CUDA(launch_backproject_tc(P->bp, P->coef, a, P->tmap, P->d_tgeo, P->d_kchl, P->d_G,
+                                  P->d_err, st), "backproject_tc (last wave)");
+    if (t[1]) PL_CUDA(cudaEventRecord(t[1], st), "event");
+    if (t[2]) PL_CUDA(cudaEventRecord(t[2], st), "event");
+    const size_t c0 = (size_t)P->zi_cols;
+    PL_CUDA(launch_fft_strided(P->d_G + c0, image + c0, 1, P->Np, P2 - P->zi_cols, P->zplan,
+                               P->d_twz, +1, 1.0f / P->Np, P->grid.nz, P->inv_off, st, nullptr, 0,
+                               G2 ? G2 + c0 : nullptr, P2),
+            "zifft (rest)");
+    PL_CUDA(cudaStreamWaitEvent(st, P->ev_bpB, 0), "cudaStreamWaitEvent");
+    if (t[3]) PL_CUDA(cudaEventRecord(t[3], st), "event");
+    return PL_OK;
+}
+
 namespace {
 
 pl_status run(pl_plan *P, const float2 *echo, float2 *image, cudaStream_t st) {
@@ -738,14 +806,21 @@ pl_status run(pl_plan *P, const float2 *echo, float2 *image, cudaStream_t st) {
     PL_CUDA(mark(1, 0), "event");
     if ((s = pl_stage_range_table(P, st)) != PL_OK) return s;
     PL_CUDA(mark(1, 1), "event");
-    // a5: back-projection with the coherent channel sum, Eq. (8b)
-    PL_CUDA(mark(2, 0), "event");
-    if ((s = pl_stage_backproject(P, st)) != PL_OK) return s;
-    PL_CUDA(mark(2, 1), "event");
-    // a6: inverse transform over k_z, Eq. (9)
-    PL_CUDA(mark(3, 0), "event");
-    if ((s = pl_stage_zifft(P, image, st)) != PL_OK) return s;
-    PL_CUDA(mark(3, 1), "event");
+    if (P->bp_full > 0) {
+        // a5 + a6, the back-projection's last wave beside part of the z-IFFT
+        const cudaEvent_t t[4] = {P->timing ? ev[2][0] : nullptr, P->timing ? ev[2][1] : nullptr,
+                                  P->timing ? ev[3][0] : nullptr, P->timing ? ev[3][1] : nullptr};
+        if ((s = stage_bp_zifft_overlapped(P, image, st, t)) != PL_OK) return s;
+    } else {
+        // a5: back-projection with the coherent channel sum, Eq. (8b)
+        PL_CUDA(mark(2, 0), "event");
+        if ((s = pl_stage_backproject(P, st)) != PL_OK) return s;
+        PL_CUDA(mark(2, 1), "event");
+        // a6: inverse transform over k_z, Eq. (9)
+        PL_CUDA(mark(3, 0), "event");
+        if ((s = pl_stage_zifft(P, image, st)) != PL_OK) return s;
+        PL_CUDA(mark(3, 1), "event");
+    }
     if (P->timing)
         for (int sidx = 0; sidx < PL_NUM_STAGES; ++sidx)
             P->recorded.push_back({sidx, {ev[sidx][0], ev[sidx][1]}});
@@ -1098,6 +1173,7 @@ pl_status pl_plan_get_info(const pl_plan *P, pl_info *info) {
     // plus the operand's preparation when the z transform is a DFT), the
     // back-projection, the inverse z transform
     i.launches_per_execute = (P->block_config == 4 && P->rt_tc) ? (P->fwd_fft ? 5 : 6) : 4;
+    if (P->bp_full > 0) i.launches_per_execute += 2;   // a second back-projection and z-IFFT launch
     i.workspace_bytes = P->workspace;
     i.updates_per_execute = (double)P->C * P->grid.nx * P->grid.ny * P->grid.nz * P->M;
     i.block_config = P->block_config;

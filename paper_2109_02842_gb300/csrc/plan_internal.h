@@ -47,6 +47,14 @@ struct pl_plan {
     void *d_rtE = nullptr, *d_rtA = nullptr, *d_rtprod = nullptr;
     CoefTable coef{};
     BpDesc bp{};
+    // the tensor-core back-projection's last partial wave: an execution
+    // launches the blocks of the full waves (bp_full), then the rest, on its
+    // stream, and meanwhile, on s_bp, the z-IFFT of the first zi_cols pixels,
+    // whose channel parts all finished in the full waves, on the SMs the last
+    // wave leaves idle (bp_full 0: one launch each)
+    int bp_full = 0, zi_cols = 0;
+    cudaStream_t s_bp = nullptr;
+    cudaEvent_t ev_bpA = nullptr, ev_bpB = nullptr;
     // transforms
     bool fwd_fft = true, inv_fft = true;
     int inv_off = 0;
@@ -103,6 +111,9 @@ struct pl_plan {
         if (s_h2d) cudaStreamDestroy(s_h2d);
         if (s_d2h) cudaStreamDestroy(s_d2h);
         if (s_twin) cudaStreamDestroy(s_twin);
+        if (s_bp) cudaStreamDestroy(s_bp);
+        for (cudaEvent_t e : {ev_bpA, ev_bpB})
+            if (e) cudaEventDestroy(e);
         delete twin;
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         if (h_err) cudaFreeHost(h_err);

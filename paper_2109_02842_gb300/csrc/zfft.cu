@@ -19,8 +19,8 @@ namespace {
 constexpr int kFftIB = 16;        // columns per block (128-byte rows)
 constexpr int kFftThreads = 256;  // threads per block
 
-// in:  [batch][n_in][I]  (rows n >= n_in are zero padding)
-// out: [batch][out_rows][I], out row r = transform index (r + out_off) mod N;
+// in:  [batch][n_in][ld], columns i < I  (rows n >= n_in are zero padding)
+// out: [batch][out_rows][ld], out row r = transform index (r + out_off) mod N;
 // or, with sp.A set, the tensor-core range table's operand instead:
 // A[r][re hi, re lo, im hi, im lo][batch][Kp] = split(X[r][i]) (BF16)
 struct SplitOut {
@@ -33,7 +33,7 @@ struct SplitOut {
 template <bool PAIRS, bool SPLIT>
 __global__ void __launch_bounds__(kFftThreads)
 k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, float2 *__restrict__ out,
-              int n_in, int I, FftPlan plan, const float2 *__restrict__ tw_g, int sgn,
+              int n_in, int I, int ld, FftPlan plan, const float2 *__restrict__ tw_g, int sgn,
               float scale, int out_rows, int out_off, SplitOut sp) {
     extern __shared__ __align__(16) float2 smem[];
     const int N = plan.n;
@@ -56,9 +56,9 @@ k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, flo
     // in2 (optional): a second array of the same shape, added on load (into
     // buf1 first, which the transform then reuses)
     for (int part = 0; part < (in2 ? 2 : 1); ++part) {
-        const float2 *src = (part ? in2 : in) + (b * n_in + n_first) * (size_t)I + i0 + col;
+        const float2 *src = (part ? in2 : in) + (b * n_in + n_first) * (size_t)ld + i0 + col;
         float2 *dst = (part ? buf1 : buf0) + n_first * kFftIB + col;
-        const size_t src_step = (size_t)RPS * I;
+        const size_t src_step = (size_t)RPS * ld;
         for (int n = n_first; n < N; n += RPS, src += src_step, dst += RPS * kFftIB) {
             if (col_ok && n < n_in) {
                 if (PAIRS)
@@ -106,12 +106,12 @@ k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, flo
             };
             stockham_run_pairs_emit<kFftIB>(buf0, buf1, tw, plan, sgn, in2 != nullptr, emit);
         } else {
-            float2 *o0 = out + b * out_rows * (size_t)I + i0;
+            float2 *o0 = out + b * out_rows * (size_t)ld + i0;
             auto emit = [&](int t, int cp, float2 x0, float2 x1) {
                 int r = t - out_off;
                 if (r < 0) r += N;
                 if (r >= out_rows || i0 + 2 * cp >= I) return;
-                *reinterpret_cast<float4 *>(o0 + (size_t)r * I + 2 * cp) =
+                *reinterpret_cast<float4 *>(o0 + (size_t)r * ld + 2 * cp) =
                     make_float4(scale * x0.x, scale * x0.y, scale * x1.x, scale * x1.y);
             };
             stockham_run_pairs_emit<kFftIB>(buf0, buf1, tw, plan, sgn, in2 != nullptr, emit);
@@ -145,8 +145,8 @@ k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, flo
             o[3 * plane] = __float2bfloat16(t.y - __bfloat162float(g));
         }
     } else {
-        float2 *o = out + (b * out_rows + n_first) * (size_t)I + i0 + col;
-        for (int r = n_first; r < out_rows; r += RPS, o += (size_t)RPS * I) {
+        float2 *o = out + (b * out_rows + n_first) * (size_t)ld + i0 + col;
+        for (int r = n_first; r < out_rows; r += RPS, o += (size_t)RPS * ld) {
             int sr = r + out_off;
             if (sr >= N) sr -= N;
             *o = cscale(src[sr * kFftIB + col], scale);
@@ -213,11 +213,14 @@ size_t fft_strided_smem_bytes(int n) { return (size_t)(2 * n * kFftIB + n) * siz
 cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_in, int I,
                                const FftPlan &plan, const float2 *tw, int sgn, float scale,
                                int out_rows, int out_off, cudaStream_t st,
-                               void *split_A, int split_Kp, const float2 *in2) {
+                               void *split_A, int split_Kp, const float2 *in2, int ld) {
     const size_t smem = fft_strided_smem_bytes(plan.n);
     // column pairs need 16-byte aligned rows: I even, 16-byte aligned
     // buffers, and (split output) an even operand row length
-    const bool pairs = (I % 2 == 0) && ((uintptr_t)in % 16 == 0) && ((uintptr_t)in2 % 16 == 0) &&
+    if (ld <= 0) ld = I;
+    if (ld < I) return cudaErrorInvalidValue;
+    const bool pairs = (I % 2 == 0) && (ld % 2 == 0) && ((uintptr_t)in % 16 == 0) &&
+                       ((uintptr_t)in2 % 16 == 0) &&
                        (split_A ? (split_Kp % 2 == 0 && (uintptr_t)split_A % 4 == 0)
                                 : (uintptr_t)out % 16 == 0);
     auto kern = split_A ? (pairs ? k_fft_strided<true, true> : k_fft_strided<false, true>)
@@ -227,7 +230,7 @@ cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_i
     if (e != cudaSuccess) return e;
     dim3 grid((I + kFftIB - 1) / kFftIB, batch);
     const SplitOut sp{(__nv_bfloat16 *)split_A, batch, split_Kp};
-    kern<<<grid, kFftThreads, smem, st>>>(in, in2, out, n_in, I, plan, tw, sgn, scale, out_rows, out_off,
+    kern<<<grid, kFftThreads, smem, st>>>(in, in2, out, n_in, I, ld, plan, tw, sgn, scale, out_rows, out_off,
                                   sp);
     return cudaGetLastError();
 }
