@@ -521,6 +521,9 @@ def main():
                     "frac": achieved / peak, "traffic": kernel_traffic("backproject_tc", w.name),
                     "kernel": "k_backproject_tc", "launch_ms": bp_avg_s * 1e3,
                     "flop_per_launch": flops,
+                    "launches_per_pass": info.get("bp_launches", 1),
+                    "pass": "launch_ms, flop_per_launch and traffic are per back-projection "
+                            "pass: from the start of its first launch to the end of its last",
                     "peak_basis": "dense BF16 (%s)" % peak_src,
                     "fp32_equivalent_tflops": fp32_flops / bp_avg_s / 1e12,
                     "fp32_equivalent_basis": "%d flop per (pixel, channel, bin) update"

@@ -152,6 +152,11 @@ typedef struct {
     int block_config;            /* back-projection kernel in use (1..4) */
     int tile_u;                  /* its k_z bins per block (block_config 4: all
                                     n_pad, rounded up to 16, in the planar layout) */
+    int bp_launches;             /* launches of the back-projection per execution:
+                                    2 when its full waves and its last partial wave
+                                    are separate launches (block_config 4, the
+                                    z-IFFT of the pixels the full waves finished
+                                    running beside the last wave), else 1 */
 } pl_info;
 
 /* Stage identifiers for timing and workspace access. */

@@ -52,7 +52,7 @@ class PlInfo(ctypes.Structure):
                 ("slab_rows", _I), ("nufft_w", _I), ("nufft_sigma", _D), ("table_h", _D),
                 ("table_l0", _D), ("z_transform_fft", _I), ("launches_per_execute", _I),
                 ("workspace_bytes", ctypes.c_size_t), ("updates_per_execute", _D),
-                ("block_config", _I), ("tile_u", _I)]
+                ("block_config", _I), ("tile_u", _I), ("bp_launches", _I)]
 
 
 class PlBatchOptions(ctypes.Structure):

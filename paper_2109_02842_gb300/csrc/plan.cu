@@ -1174,6 +1174,7 @@ pl_status pl_plan_get_info(const pl_plan *P, pl_info *info) {
     // back-projection, the inverse z transform
     i.launches_per_execute = (P->block_config == 4 && P->rt_tc) ? (P->fwd_fft ? 5 : 6) : 4;
     if (P->bp_full > 0) i.launches_per_execute += 2;   // a second back-projection and z-IFFT launch
+    i.bp_launches = P->bp_full > 0 ? 2 : 1;
     i.workspace_bytes = P->workspace;
     i.updates_per_execute = (double)P->C * P->grid.nx * P->grid.ny * P->grid.nz * P->M;
     i.block_config = P->block_config;
