@@ -92,7 +92,14 @@ def test_batch_matches_single_scan_path_and_oracle(binding, data, kind):
             plan = binding.Plan.from_workload(w, tile_u=info["tile_u"],
                                               block_config=info["block_config"])
         single = plan.execute(torch.from_numpy(echo_np[i]).cuda()).cpu().numpy()
-        assert rel(imgs[i], single) < 1e-6, i
+        if kind == "tensor_core":
+            # the batch runs each scene's stages one launch each; a plan's own
+            # execution splits the back-projection into its full waves and
+            # its last wave with part of the z-IFFT beside it (scene 0): the
+            # same arithmetic per output, so the images agree bit for bit
+            assert np.array_equal(imgs[i], single), i
+        else:
+            assert rel(imgs[i], single) < 1e-6, i
     for i in (0, 2, 3):
         w = scenes[i]
         ref = oracle.hybrid_exact(w.mode, w.tx_xy, w.rx_xy, echo_np[i], w.z_scan, w.f_hz,

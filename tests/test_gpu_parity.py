@@ -356,8 +356,13 @@ def test_tensor_core_variant_full_size_sampled(binding, which):
     w = wl.WORKLOADS[which](seed=0)
     echo = scene_echo(w, 0, n_pts=24)
     plan, img = run_gpu(binding, w, echo, block_config=4)
-    print("%s: window rows %d, table rows %d" % (which, plan.info["slab_rows"],
-                                                plan.info["table_len"]))
+    print("%s: window rows %d, table rows %d, back-projection launches %d"
+          % (which, plan.info["slab_rows"], plan.info["table_len"], plan.info["bp_launches"]))
+    if which == "full_mono":
+        # 1024 blocks on 152 SMs: the full waves, then the last wave beside the
+        # z-IFFT of the pixels they finished (the sampled columns span both)
+        assert plan.info["bp_launches"] == 2
+        assert plan.info["launches_per_execute"] == 7
     idx = sampled_columns(w, 48, 1)
     ref = image_ref(w, echo, w.pix_xy()[idx])
     got = img.reshape(w.grid["nz"], -1)[:, idx]
