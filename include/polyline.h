@@ -177,7 +177,11 @@ pl_status pl_plan_create(pl_plan **out, const pl_geometry *geom, const pl_scan *
 /* Reconstruct one scan. echo_dev: device complex64 [n_chan][n_scan][n_f]
  * (channel-major, frequency fastest); image_dev: device complex64
  * [nz][ny][nx]. Asynchronous on `stream`; the buffers must stay valid until
- * the stream reaches the end of this call's work. */
+ * the stream reaches the end of this call's work. When the tensor-core
+ * back-projection has a partial last wave (pl_info.bp_launches == 2), part of
+ * the inverse z transform runs on a plan-owned stream beside it, forked from
+ * and joined back into `stream` by events: the call's work stays ordered on
+ * `stream` (also under stream capture). */
 pl_status pl_execute(pl_plan *plan, const void *echo_dev, void *image_dev, void *stream);
 
 /* Same reconstruction from HOST buffers: copies the echo to the device,
@@ -268,7 +272,10 @@ pl_status pl_plan_workspace(pl_plan *plan, int stage, void **dev_ptr, size_t *by
 /* Per-stage timing with CUDA events recorded on the execute stream.
  * enable != 0 starts recording (and clears the sums). pl_plan_stage_times
  * waits for the recorded events and returns, per stage, the summed
- * milliseconds and the number of launches timed since the last clear. */
+ * milliseconds and the number of executions timed since the last clear.
+ * With pl_info.bp_launches == 2 the back-projection stage spans both of its
+ * launches (with the inverse transform of the finished pixels beside the
+ * second) and the inverse-transform stage is the part left after it. */
 pl_status pl_plan_set_timing(pl_plan *plan, int enable);
 pl_status pl_plan_stage_times(pl_plan *plan, double ms[PL_NUM_STAGES],
                               int launches[PL_NUM_STAGES]);
