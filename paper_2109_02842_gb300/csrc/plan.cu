@@ -14,6 +14,7 @@
 #include "kernels.h"
 #include "plan_internal.h"
 #include "tc05.cuh"
+#include "wave_split.h"
 
 namespace {
 
@@ -657,20 +658,17 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
                 "cudaDeviceGetAttribute");
         const size_t smem = backproject_tc_smem_bytes(P->tc) + 1024;
         const int per_sm = std::max(1, std::min(512 / P->tc.tmem_cols, (int)((228 * 1024) / smem)));
-        const int wave = sms * per_sm;
-        const int total = backproject_tc_blocks(P->bp, P->tc);
-        const int full = total / wave * wave;
-        const int T = total / P->tc.nsplit;
         const int nbx = (gr->nx + backproject_tc_tile_x() - 1) / backproject_tc_tile_x();
-        const int tiles_done = std::max(0, full - (P->tc.nsplit - 1) * T);
-        const int rows = std::min(gr->ny, tiles_done / nbx * backproject_tc_tile_y());
-        if (full > 0 && full < total && rows > 0) {
+        const WaveSplit wsplit =
+            bp_wave_split(backproject_tc_blocks(P->bp, P->tc), sms * per_sm, P->tc.nsplit, nbx,
+                          backproject_tc_tile_y(), gr->nx, gr->ny);
+        if (wsplit.full > 0) {
             PL_CUDA(cudaStreamCreateWithFlags(&P->s_bp, cudaStreamNonBlocking),
                     "cudaStreamCreateWithFlags");
             PL_CUDA(cudaEventCreateWithFlags(&P->ev_bpA, cudaEventDisableTiming), "cudaEventCreate");
             PL_CUDA(cudaEventCreateWithFlags(&P->ev_bpB, cudaEventDisableTiming), "cudaEventCreate");
-            P->bp_full = full;
-            P->zi_cols = rows * gr->nx;
+            P->bp_full = wsplit.full;
+            P->zi_cols = wsplit.cols;
         }
     }
     PL_CUDA(cudaDeviceSynchronize(), "plan setup");
