@@ -2,12 +2,16 @@
 //
 // Both act on the middle axis of a [batch][n][inner] complex64 array whose
 // inner axis is contiguous: the echo s[c][n][m] (forward, zero-padded to N_p)
-// and the image spectrum G[u][pixel] (inverse). One block stages a
+// and the image spectrum G[u][pixel] (inverse; the sum of the two channel
+// parts' spectra, added as the first stage reads them). One block stages a
 // [n][IB] column panel in shared memory (coalesced row segments), runs a
-// mixed-radix (2, 3, 4, 5) Stockham autosort FFT on all IB columns at once
-// and writes the requested output rows. Lengths with another prime factor,
-// and inverse transforms onto voxel heights off the scan grid, use the
-// tiled direct DFT kernel below with a precomputed phase matrix.
+// mixed-radix (2, 3, 4, 5, 8) Stockham autosort FFT on all IB columns at once
+// (column pairs), and its last stage writes the requested output rows to
+// global memory (complex64 rows, or the range table's BF16 hi/lo operand). A
+// launch may cover a range of columns of wider rows (row stride ld). Lengths
+// with another prime factor, and inverse transforms onto voxel heights off
+// the scan grid, use the tiled direct DFT kernel below with a precomputed
+// phase matrix.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
