@@ -153,8 +153,8 @@ class ClockSampler:
 
 def dtype_of(info: dict, precision: int) -> str:
     if info["block_config"] == 4:
-        return "bf16x3+f32acc" if precision == 0 else "bf16+f32acc"
-    return "f32" if precision == 0 else "f32+bf16"
+        return ("bf16x3+f32acc", "bf16+f32acc", "bf16+f32acc,bf16-spectrum")[precision]
+    return ("f32", "f32+bf16-table", "f32+bf16-table+bf16-spectrum")[precision]
 
 
 def tc_flops_per_launch(info: dict, precision: int) -> float:
@@ -168,6 +168,23 @@ def tc_flops_per_launch(info: dict, precision: int) -> float:
     bins = -(-info["n_pad"] // ut) * ut
     pix = -(-info["nx"] // 16) * 16 * (-(-info["ny"] // 8) * 8)
     return 2.0 * pix * info["n_chan"] * bins * 4 * split * 16 * ks
+
+
+# the method's work per (pixel, channel, k_z bin) update of the back-projection
+# at w = 6 taps: 2w FMA for the interpolation, ~8 FMA for the split-float
+# carrier phase and its reduction, 4 FMA for the complex multiply-accumulate,
+# i.e. 24 FMA = 48 flop
+METHOD_FLOP_PER_UPDATE = 48
+
+
+def measure_unit_peaks(binding) -> dict:
+    """FP32 FMA, MUFU sine and shared-memory peaks measured on this device
+    (pl_measure_peak), or {} if the call fails."""
+    try:
+        return {"fp32_tflops": binding.measure_peak(0), "mufu_gsin": binding.measure_peak(1),
+                "smem_gbs": binding.measure_peak(2), "source": "pl_measure_peak, this run"}
+    except Exception as e:          # reported, not fatal for the bench line
+        return {"error": str(e)}
 
 
 def backproject_flops_per_update(w_taps: int) -> int:
@@ -207,11 +224,18 @@ def oracle_baseline(w, echo_np, gpu_image=None, n_cols=256, n_chan=None, seed=1)
            "seconds": t2 - t0}
     err = None
     if gpu_image is not None and cs == C:
-        got = gpu_image.reshape(w.grid["nz"], -1)[:, idx]
-        mx = float(np.max(np.abs(got - g)) / np.max(np.abs(g)))
-        err = {"rel_l2": float(np.linalg.norm(got - g) / np.linalg.norm(g)),
-               "max_abs_over_max_ref": mx, "columns": int(idx.size)}
-    return out, err
+        err = column_error(gpu_image, w, idx, g)
+    return out, err, (idx, g)
+
+
+def column_error(image, w, idx, ref):
+    """Relative L2 and largest per-voxel error of an image's sampled columns
+    against the oracle's values there."""
+    import numpy as np
+    got = image.reshape(w.grid["nz"], -1)[:, idx]
+    return {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "max_abs_over_max_ref": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
+            "columns": int(idx.size)}
 
 
 def max_over_ranks(values, world: int, device):
@@ -237,7 +261,7 @@ def workload_config(w, world, precision, l2):
     return {"workload": w.name, "mode": "monostatic" if w.mode == 0 else "multistatic",
             "n_chan": int(w.n_chan), "n_scan": int(w.n_scan), "n_f": int(w.n_f),
             "grid": [w.grid["nx"], w.grid["ny"], w.grid["nz"]], "n_pad": int(w.n_pad),
-            "precision": "fp32" if precision == 0 else "bf16-table",
+            "precision": ("fp32", "bf16-table", "bf16-table+spectrum")[precision],
             "nufft_w": 6, "nufft_sigma": 2.0,
             "parallelism": "replicas%d" % world, "l2": l2}
 
@@ -257,7 +281,7 @@ def run_reference(args, world, rank):
         oracle_baseline(w, echo, n_cols=64, n_chan=48)
     vals, secs = [], []
     for _ in range(args.steps):
-        b, _ = oracle_baseline(w, echo, n_cols=64, n_chan=48)
+        b, _, _ = oracle_baseline(w, echo, n_cols=64, n_chan=48)
         vals.append(b["value"])
         secs.append(b["seconds"])
     v = statistics.mean(vals)
@@ -311,9 +335,17 @@ def run_batch64(args, world, rank, local):
         res[name] = {"ms_per_batch": ms, "value": upd / (ms * 1e-3), "info": b.get_info()}
         b.close()
     best = res["autotuned"]
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = pix_upd * backproject_flops_per_update(6) / (best["ms_per_batch"] * 1e-3) / 1e12
     tc = best["info"]["block_config"] == 4
+    peaks, peak_src = measured_peaks()
+    unit_peaks = measure_unit_peaks(binding)
+    if tc:
+        peak, bound = float(peaks.get("bf16_tflops", 1900.0)), "tensor"
+        basis = "dense BF16 burst, %s" % ("of measured" if peak_src == "measured" else "of fallback")
+    else:
+        peak, bound = (unit_peaks.get("fp32_tflops")
+                       or N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e-6), "alu"
+        basis = "FP32 FMA pipe (pl_measure_peak)" if unit_peaks.get("fp32_tflops") else "FP32 unit counts"
+    achieved = pix_upd * METHOD_FLOP_PER_UPDATE / (best["ms_per_batch"] * 1e-3) / 1e12
     line = {"metric": METRIC,
             "value": best["value"], "unit": "updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": best["ms_per_batch"], "higher_is_better": True,
@@ -328,11 +360,14 @@ def run_batch64(args, world, rank, local):
                                    for k, v in res.items()},
             "autotune_speedup": res["fixed"]["ms_per_batch"] / best["ms_per_batch"],
             "gpu_launches": best["info"]["launches_per_execute"] * args.steps,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                         "kernel": "whole batch, FP32-equivalent rate (32 flop per update)"
+            "roofline": {"bound": bound, "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_basis": basis,
+                         "kernel": "whole batch, the method's %d flop per (pixel, channel, "
+                                   "k_z bin) update" % METHOD_FLOP_PER_UPDATE
                                    + ("; tensor-core back-projection" if tc else
                                       "; persistent FP32 kernel")},
+            "unit_peaks": unit_peaks,
             "batch_info": best["info"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -507,48 +542,87 @@ def main():
     bp_ms, bp_n = stage["backproject"]
     bp_avg_s = bp_ms / max(bp_n, 1) * 1e-3
     pix_updates = info["n_chan"] * info["nx"] * info["ny"] * info["n_pad"]
-    fp32_flops = pix_updates * backproject_flops_per_update(info["nufft_w"])
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    method_flops = pix_updates * METHOD_FLOP_PER_UPDATE
     peaks, peak_src = measured_peaks()
+    unit_peaks = measure_unit_peaks(binding)
     if info["block_config"] == 4:
-        # tensor cores: the dense BF16 contraction of the formulation, per
-        # (pixel, channel, bin): split x (P, Q) x (re, im) x 16 ks window rows
-        # MACs, over the padded 16 x 8 pixel tiles and tile_u-bin blocks
-        flops = tc_flops_per_launch(info, args.precision)
+        # tensor cores: the method's work (48 flop per (pixel, channel, bin)
+        # update) against the dense BF16 peak; beside it the dense MMA work the
+        # formulation issues (window rows x split products), i.e. how busy the
+        # tensor pipe is kept
+        dense = tc_flops_per_launch(info, args.precision)
         peak = float(peaks.get("bf16_tflops", 1900.0))
-        achieved = flops / bp_avg_s / 1e12
+        achieved = method_flops / bp_avg_s / 1e12
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": kernel_traffic("backproject_tc", w.name),
                     "kernel": "k_backproject_tc", "launch_ms": bp_avg_s * 1e3,
-                    "flop_per_launch": flops,
+                    "flop_per_launch": method_flops,
+                    "flop_basis": "%d flop per (pixel, channel, k_z bin) update: w-tap "
+                                  "interpolation, split-float carrier phase and the complex "
+                                  "multiply-accumulate (x %d updates per pass)"
+                                  % (METHOD_FLOP_PER_UPDATE, pix_updates),
                     "launches_per_pass": info.get("bp_launches", 1),
                     "pass": "launch_ms, flop_per_launch and traffic are per back-projection "
                             "pass: from the start of its first launch to the end of its last",
-                    "peak_basis": "dense BF16 (%s)" % peak_src,
-                    "fp32_equivalent_tflops": fp32_flops / bp_avg_s / 1e12,
-                    "fp32_equivalent_basis": "%d flop per (pixel, channel, bin) update"
-                                             % backproject_flops_per_update(info["nufft_w"])}
+                    "peak_basis": "dense BF16 burst, %s" % ("of measured" if peak_src == "measured"
+                                                            else "of fallback"),
+                    "mma_pipe_frac": dense / bp_avg_s / 1e12 / peak,
+                    "mma_dense_flop_per_launch": dense,
+                    "mma_basis": "dense BF16 MMA work issued: 16 window rows x 4 real products "
+                                 "x %d split products x 2 per (pixel, channel, bin) over padded "
+                                 "tiles; only %d of the 16 rows carry a tap"
+                                 % (3 if args.precision == 0 else 1, info["nufft_w"])}
     else:
-        achieved = fp32_flops / bp_avg_s / 1e12
+        fp32_peak = unit_peaks.get("fp32_tflops") or N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e-6
+        achieved = method_flops / bp_avg_s / 1e12
+        executed = pix_updates * backproject_flops_per_update(info["nufft_w"])
         roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": achieved / fp32_peak, "traffic": kernel_traffic("backproject", w.name),
                     "kernel": "k_backproject", "launch_ms": bp_avg_s * 1e3,
-                    "flop_per_launch": fp32_flops,
-                    "peak_basis": "FP32: 152 SM x 128 lanes x 2 flop x 2070 MHz (recipe unit "
-                                  "counts and max clock)",
-                    "mufu_frac": (2 * pix_updates / max(info["tile_u"], 1) / bp_avg_s) /
-                                 (N_SM * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6)}
+                    "flop_per_launch": method_flops,
+                    "flop_basis": "%d flop per (pixel, channel, k_z bin) update"
+                                  % METHOD_FLOP_PER_UPDATE,
+                    "peak_basis": ("FP32 FMA pipe, measured by pl_measure_peak in this run"
+                                   if unit_peaks.get("fp32_tflops") else
+                                   "FP32: 152 SM x 128 lanes x 2 flop x 2070 MHz (unit counts)"),
+                    "executed_flop_frac": executed / bp_avg_s / 1e12 / fp32_peak,
+                    "executed_basis": "%d flop per update actually executed (the carrier's phase "
+                                      "and sin/cos once per (pixel, channel, bin block))"
+                                      % backproject_flops_per_update(info["nufft_w"]),
+                    "mufu_frac": (2 * pix_updates / max(info["tile_u"], 1) / bp_avg_s / 1e9) /
+                                 unit_peaks["mufu_gsin"] if unit_peaks.get("mufu_gsin") else None}
     stage_avg = {k: v[0] / max(v[1], 1) for k, v in stage.items()}
 
-    cpu, acc = None, None
+    cpu, acc, variants = None, None, None
     if rank == 0 and world == 1 and not args.no_oracle:
-        # accuracy leg and CPU baseline on an oracle-made echo (24 points)
+        # accuracy leg and CPU baseline on an oracle-made echo (24 of the
+        # scene's points: the operator is linear, so the error of the timed
+        # 2020-point echo's image is of the same kind)
         import oracle
         oracle.build()
         clean = oracle.synth_echo(w.tx_xy, w.rx_xy, w.z_scan, w.f_hz, w.pts[:24], w.amp[:24])
         e_np = wl.add_noise(clean, w.snr_db, wl.rng_for(100, 0)).astype(np.complex64)
-        img = plan.execute(torch.from_numpy(e_np).to(dev)).cpu().numpy()
-        cpu, acc = oracle_baseline(w, e_np, img, n_cols=256)
+        e_dev = torch.from_numpy(e_np).to(dev)
+        img = plan.execute(e_dev).cpu().numpy()
+        cpu, acc, (idx, ref) = oracle_baseline(w, e_np, img, n_cols=256)
+        acc["echo"] = "oracle echo of 24 of the scene's points, 30 dB noise"
+        # every precision variant of both kernel families on the same columns
+        variants = {}
+        for name, kw in (("tensor_core_bf16x3", dict(block_config=4, precision=0)),
+                         ("tensor_core_bf16", dict(block_config=4, precision=1)),
+                         ("tensor_core_bf16_spectrum", dict(block_config=4, precision=2)),
+                         ("fp32", dict(block_config=3 if w.mode == 0 else 1, precision=0)),
+                         ("fp32_bf16_table", dict(block_config=1, precision=1)),
+                         ("fp32_bf16_table_spectrum", dict(block_config=1, precision=2))):
+            try:
+                pv = binding.Plan.from_workload(w, **kw)
+            except binding.PolylineError as ex:
+                variants[name] = {"unavailable": str(ex)}
+                continue
+            iv = pv.execute(e_dev).cpu().numpy()
+            variants[name] = dict(column_error(iv, w, idx, ref), dtype=dtype_of(pv.info, kw["precision"]),
+                                  block_config=pv.info["block_config"], precision=kw["precision"])
+            pv.close()
 
     line = {
         "metric": METRIC,
@@ -574,6 +648,8 @@ def main():
         "clocks": clk,
         "wall_s_timed_region": wall,
         "accuracy_vs_oracle": acc,
+        "accuracy_by_variant": variants,
+        "unit_peaks": unit_peaks,
         "cpu_baseline": cpu,
         "peaks_source": peak_src,
         "hbm_peak_gbs": peaks.get("hbm_gbs"),

@@ -157,6 +157,28 @@ typedef struct {
                                     are separate launches (block_config 4, the
                                     z-IFFT of the pixels the full waves finished
                                     running beside the last wave), else 1 */
+    /* The range table b of Eq. (8a)/(19a) (workspace PL_STAGE_RANGE_TABLE): row
+     * i holds, for every k_z bin u, the type-1 NUFFT coefficients at range
+     * l_i = table_l0 + i table_h,
+     *   b_i(u) = table_h sum_m S_um k_m e^{j kappa''_um l_i} / phihat(kappa''_um),
+     * kappa'' = kappa - kappa_c with kappa_c the centre of the band (live
+     * kappa values) of the bin's group of band_group consecutive bins, and
+     * phihat the Fourier transform of the ES kernel
+     * ES(t) = exp(es_beta (sqrt(1 - (2t / nufft_w)^2) - 1)), |t| < nufft_w / 2.
+     * The back-projection's interpolation sum_i ES((l - l_i) / table_h) b_i(u)
+     * then approximates sum_m S_um k_m e^{j kappa''_um l}. */
+    double es_beta;
+    int band_group;
+    int table_layout;     /* 0: float32 rows of bin pairs {re_u, re_u+1, im_u, im_u+1},
+                             [n_chan][L][ceil(n_pad/2)]; 1: the same in bfloat16;
+                             2: bfloat16 [n_chan][hi, lo][L][table_cols], column
+                             2u + (re, im); 3: the same planar, column u = Re b_u,
+                             column table_cols/2 + u = Im b_u (value = hi + lo) */
+    int table_cols;       /* layouts 2 and 3: columns of a row */
+    int table_exact;      /* 1: b evaluated as exact sums over the frequencies
+                             (tensor cores); 0: type-1 NUFFT (spread, FFT,
+                             deconvolution) */
+    int precision;        /* pl_options.precision in use */
 } pl_info;
 
 /* Stage identifiers for timing and workspace access. */
@@ -286,8 +308,11 @@ pl_status pl_plan_stage_times(pl_plan *plan, double ms[PL_NUM_STAGES],
  *   echo[c][n][m] = sum_t amp_t exp(-j k_m (R_T + R_R)),  k_m = 2 pi f_m / c.
  * tx_xy, rx_xy: host [n_chan][2]; f_hz: host [n_f]; pts: host [n_pts][3];
  * amp: host [n_pts][2] (complex). echo_dev: device complex64
- * [n_chan][n_scan][n_f]. Phases are formed in FP32 after an FP64 split of
- * the range; accuracy ~1e-5 rad. Synchronises `stream` before returning. */
+ * [n_chan][n_scan][n_f]. The range R_T + R_R of every (point, channel, scan
+ * position) is formed in FP64 and kept as a float pair; k_m (R_T + R_R) is a
+ * float-float product reduced modulo 2 pi before an FP32 sin/cos, so each
+ * phase carries ~1e-6 rad of error (accumulation over points in FP32).
+ * Synchronises `stream` before returning. */
 pl_status pl_synth_echo(int n_chan, const double *tx_xy, const double *rx_xy,
                         double z0, double dz, int n_scan, const double *f_hz, int n_f,
                         int n_pts, const double *pts, const double *amp,
@@ -385,6 +410,12 @@ pl_status pl_batch_destroy(pl_batch *batch);
  *   grad (FP32 [V][2], may be NULL) = 2 (pred - t/s) / sums[0]; pred FP32
  *   [V][2], target complex64.
  * pl_nn_residual: pred[v] += gain (Re img[v], Im img[v]) / s.
+ * pl_nn_check: the acceptance check of a learned correction corr (FP32
+ *   [V][2], the network's output before pl_nn_residual): out (device FP32[3])
+ *   = (number of non-finite entries of corr, sum of corr^2 over the finite
+ *   ones, sum |gain img / s|^2); fixed-order reduction. The caller falls back
+ *   to the plain reconstruction when out[0] > 0 or the correction is too
+ *   large against the scaled cheap image.
  * pl_nn_to_complex: img[v] = s (pred[v][0] + j pred[v][1]).
  * pl_nn_adam: one bias-corrected Adam step (Kingma & Ba 2015) on FP32
  *   parameters p with gradient g and moments m, v; refreshes the BF16 copy
@@ -406,6 +437,8 @@ pl_status pl_nn_loss(const float *pred, const void *target, const float *scale, 
                      float *grad, size_t n, void *stream);
 pl_status pl_nn_residual(float *pred, const void *img, const float *scale, float gain, size_t n,
                          void *stream);
+pl_status pl_nn_check(const float *corr, const void *img, const float *scale, float gain,
+                      size_t n, float *out, void *stream);
 pl_status pl_nn_to_complex(const float *pred, const float *scale, void *img, size_t n,
                            void *stream);
 pl_status pl_nn_adam(float *p, const float *g, float *m, float *v, void *p_bf16, size_t n,
@@ -418,7 +451,7 @@ pl_status pl_nn_adam(float *p, const float *g, float *m, float *v, void *p_bf16,
  *
  * Same arguments and same result as pl_synth_echo, but the device-side copies
  * of the inputs live in a fixed scratch array inside the library (a static
- * __device__ variable of about 1.3 MB that every device loading the library
+ * __device__ variable of about 0.8 MB that every device loading the library
  * holds until exit) instead of buffers allocated per call: this call never
  * calls cudaMalloc or cudaFree. Limits: n_chan <= PL_STATIC_MAX_CHANNELS,
  * n_f <= PL_STATIC_MAX_FREQS, n_pts <= PL_STATIC_MAX_POINTS; larger sizes
@@ -429,8 +462,12 @@ pl_status pl_nn_adam(float *p, const float *g, float *m, float *v, void *p_bf16,
  *  - All calls share the one scratch array, which keeps the last call's
  *    contents. Calls whose GPU work overlaps (e.g. on two streams) race on it:
  *    issue them on one stream or order them.
- *  - The host arrays are copied before the call returns; the echo is complete
- *    when `stream` reaches the end of this call's work (no synchronisation). */
+ *  - The call does not synchronise: the inputs are copied to the scratch with
+ *    cudaMemcpyAsync on `stream`, and the echo is complete when `stream`
+ *    reaches the end of this call's work. From pageable host memory the copies
+ *    are staged before the call returns; from page-locked (pinned) host
+ *    memory, or under stream capture, they run later, so keep the host arrays
+ *    valid and unchanged until `stream` has reached the end of the call. */
 #define PL_STATIC_MAX_CHANNELS 4096
 #define PL_STATIC_MAX_FREQS 512
 #define PL_STATIC_MAX_POINTS 16384
@@ -438,6 +475,17 @@ pl_status pl_synth_echo_static(int n_chan, const double *tx_xy, const double *rx
                                double z0, double dz, int n_scan, const double *f_hz, int n_f,
                                int n_pts, const double *pts, const double *amp,
                                void *echo_dev, void *stream);
+
+/* Measured peak of one unit that bounds the FP32 back-projection, for its
+ * roofline (a device micro-benchmark on `stream`, ~0.1 s; synchronises it;
+ * changes no device setting):
+ *   which 0: FP32 FMA pipe, *value in TFLOP/s (2 flop per FMA);
+ *   which 1: MUFU sine, *value in G sin/s;
+ *   which 2: shared-memory load bandwidth (conflict-free 16-byte loads),
+ *            *value in GB/s.
+ * Every SM is filled with independent dependency chains; the best of three
+ * timed launches after a warm-up launch is kept. */
+pl_status pl_measure_peak(int which, void *stream, double *value);
 
 const char *pl_status_string(pl_status s);
 const char *pl_last_error(void);

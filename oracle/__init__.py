@@ -10,9 +10,12 @@ passage of Wang, Li, Zhao, Sun, "Near-Field Millimeter-Wave Imaging via Arrays
 in the Shape of Polyline" (arXiv 2109.02842) that it follows.
 
 Parity status: the echo model, the z-DFT, the exact-sum hybrid (Eq. 7 / 17-19),
-the z inverse transform and the direct back-projection are each pinned by
-tests in ``tests/test_oracle_pins.py`` (closed forms, library routines,
-adjoint identity, mono/multi identity, point-target focusing).
+the z inverse transform, the direct back-projection and the range profile of
+step (8a)/(19a) are each pinned by tests in ``tests/test_oracle_pins.py``
+(closed forms, library routines, adjoint identity, mono/multi identity,
+point-target focusing; the range profile by the inverse DFT at k_z = 0, the
+mono/multi identity q_mono(l) = q_multi(2 l) at k_z != 0, and the split
+kappa a = kappa' a + kappa_0 a against the exact-sum hybrid in both modes).
 """
 from __future__ import annotations
 

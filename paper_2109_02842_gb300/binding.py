@@ -52,7 +52,9 @@ class PlInfo(ctypes.Structure):
                 ("slab_rows", _I), ("nufft_w", _I), ("nufft_sigma", _D), ("table_h", _D),
                 ("table_l0", _D), ("z_transform_fft", _I), ("launches_per_execute", _I),
                 ("workspace_bytes", ctypes.c_size_t), ("updates_per_execute", _D),
-                ("block_config", _I), ("tile_u", _I), ("bp_launches", _I)]
+                ("block_config", _I), ("tile_u", _I), ("bp_launches", _I),
+                ("es_beta", _D), ("band_group", _I), ("table_layout", _I), ("table_cols", _I),
+                ("table_exact", _I), ("precision", _I)]
 
 
 class PlBatchOptions(ctypes.Structure):
@@ -75,8 +77,8 @@ EXPORTED = ("pl_plan_create", "pl_execute", "pl_execute_host", "pl_execute_host_
             "pl_batch_create", "pl_execute_batch", "pl_batch_get_info", "pl_batch_destroy",
             "pl_nn_padded_k", "pl_nn_conv3d", "pl_nn_wgrad_workspace", "pl_nn_conv3d_wgrad",
             "pl_nn_weight_flip", "pl_nn_elementwise", "pl_nn_resample", "pl_nn_features",
-            "pl_nn_loss", "pl_nn_residual", "pl_nn_to_complex", "pl_nn_adam",
-            "pl_status_string", "pl_last_error", "pl_version")
+            "pl_nn_loss", "pl_nn_residual", "pl_nn_check", "pl_nn_to_complex", "pl_nn_adam",
+            "pl_measure_peak", "pl_status_string", "pl_last_error", "pl_version")
 
 _lib = None
 
@@ -126,6 +128,8 @@ def load(path: str = LIB_PATH):
     lib.pl_execute_batch.argtypes = [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P]
     lib.pl_batch_get_info.argtypes = [_P, ctypes.POINTER(PlBatchInfo)]
     lib.pl_batch_destroy.argtypes = [_P]
+    lib.pl_measure_peak.argtypes = [_I, _P, ctypes.POINTER(_D)]
+    lib.pl_measure_peak.restype = _I
     lib.pl_status_string.restype = ctypes.c_char_p
     lib.pl_status_string.argtypes = [_I]
     lib.pl_last_error.restype = ctypes.c_char_p
@@ -413,6 +417,17 @@ def synth_echo_static(tx_xy, rx_xy, z0, dz, n_scan, f_hz, pts, amp, out=None, st
                                        int(n_scan), _ptr(f), f.size, p.shape[0], _ptr(p),
                                        _ptr(a), _P(out.data_ptr()), _stream_handle(stream)))
     return out
+
+
+PEAK_UNITS = ("TFLOP/s", "Gsin/s", "GB/s")
+
+
+def measure_peak(which: int, stream=None) -> float:
+    """pl_measure_peak: 0 FP32 FMA (TFLOP/s), 1 MUFU sine (G/s), 2 shared-memory
+    load bandwidth (GB/s), measured on the current device."""
+    v = _D()
+    _check(load().pl_measure_peak(int(which), _stream_handle(stream), ctypes.byref(v)))
+    return v.value
 
 
 class Batch:

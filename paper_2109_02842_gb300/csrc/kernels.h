@@ -183,9 +183,12 @@ pl_status pl_internal_fail(pl_status s, const char *msg);
 pl_status pl_internal_cuda_fail(cudaError_t e, const char *where);
 
 // ---- synth.cu ----------------------------------------------------------------
-cudaError_t launch_synth_echo(int n_chan, const float4 *ch, int n_scan, float z0, float dz,
-                              int n_f, const float *k, int n_pts, const float4 *pts,
-                              const float2 *amp, float2 *echo, cudaStream_t st);
+// device arrays in the caller's FP64 layouts: tx_xy, rx_xy [n_chan][2], f_hz [n_f],
+// pts [n_pts][3], amp [n_pts][2]
+cudaError_t launch_synth_echo(int n_chan, const double *tx_xy, const double *rx_xy, int n_scan,
+                              double z0, double dz, int n_f, const double *f_hz, int n_pts,
+                              const double *pts, const double *amp, float2 *echo,
+                              cudaStream_t st);
 
 // ---- nn.cu: learned fast path -------------------------------------------------
 cudaError_t nn_conv3d(const void *x, const void *w, const float *bias, void *out, int D, int H,
@@ -193,6 +196,8 @@ cudaError_t nn_conv3d(const void *x, const void *w, const float *bias, void *out
 size_t nn_wgrad_work_floats(int D, int H, int W, int Cin, int Cout, int Kp);
 cudaError_t nn_conv3d_wgrad(const void *x, const void *gy, float *gw, float *gb, float *work,
                             int D, int H, int W, int Cin, int Cout, int Kp, cudaStream_t st);
+cudaError_t nn_check(const float *corr, const void *img, const float *scale, float gain, size_t n,
+                     float *out, cudaStream_t st);
 cudaError_t nn_residual(float *pred, const void *img, const float *scale, float gain, size_t n,
                         cudaStream_t st);
 cudaError_t nn_weight_flip(const void *w, void *wt, int Cin, int Cout, int Kp, int Kpt,

@@ -377,6 +377,42 @@ k_loss_sums(const float *__restrict__ pred, const float2 *__restrict__ tgt,
     }
 }
 
+// Acceptance check of a learned correction: out[0] = number of non-finite
+// entries of corr ([n][2]), out[1] = sum of corr^2 over the finite ones,
+// out[2] = sum |gain img / s|^2 (the scaled cheap image the correction is
+// added to). One block of 1024 threads, fixed-order tree.
+__global__ void __launch_bounds__(1024)
+k_check(const float *__restrict__ corr, const float2 *__restrict__ img,
+        const float *__restrict__ scale, float gain, size_t n, float *out) {
+    __shared__ float s_bad[1024], s_c[1024], s_i[1024];
+    const float k = gain / (*scale > 0.f ? *scale : 1.f);
+    float bad = 0.f, sc = 0.f, si = 0.f;
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const float a = corr[2 * i], b = corr[2 * i + 1];
+        if (isfinite(a)) sc += a * a; else bad += 1.f;
+        if (isfinite(b)) sc += b * b; else bad += 1.f;
+        const float x = k * img[i].x, y = k * img[i].y;
+        si += x * x + y * y;
+    }
+    s_bad[threadIdx.x] = bad;
+    s_c[threadIdx.x] = sc;
+    s_i[threadIdx.x] = si;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            s_bad[threadIdx.x] += s_bad[threadIdx.x + o];
+            s_c[threadIdx.x] += s_c[threadIdx.x + o];
+            s_i[threadIdx.x] += s_i[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = s_bad[0];
+        out[1] = s_c[0];
+        out[2] = s_i[0];
+    }
+}
+
 // grad = 2 (pred - target/s) / sum|target/s|^2
 __global__ void k_loss_grad(const float *__restrict__ pred, const float2 *__restrict__ tgt,
                             const float *__restrict__ scale, const float *__restrict__ sums,
@@ -542,6 +578,12 @@ cudaError_t nn_loss(const float *pred, const void *target, const float *scale, f
                     float *grad, size_t n, cudaStream_t st) {
     k_loss_sums<<<1, 1024, 0, st>>>(pred, (const float2 *)target, scale, n, sums);
     if (grad) k_loss_grad<<<nblk(n), 256, 0, st>>>(pred, (const float2 *)target, scale, sums, grad, n);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_check(const float *corr, const void *img, const float *scale, float gain, size_t n,
+                     float *out, cudaStream_t st) {
+    k_check<<<1, 1024, 0, st>>>(corr, (const float2 *)img, scale, gain, n, out);
     return cudaGetLastError();
 }
 

@@ -85,6 +85,12 @@ pl_status pl_nn_residual(float *pred, const void *img, const float *scale, float
     return ret(nn_residual(pred, img, scale, gain, n, (cudaStream_t)stream), "pl_nn_residual");
 }
 
+pl_status pl_nn_check(const float *corr, const void *img, const float *scale, float gain,
+                      size_t n, float *out, void *stream) {
+    if (!corr || !img || !scale || !out) return pl_internal_fail(PL_ERR_ARG, "bad pl_nn_check");
+    return ret(nn_check(corr, img, scale, gain, n, out, (cudaStream_t)stream), "pl_nn_check");
+}
+
 pl_status pl_nn_to_complex(const float *pred, const float *scale, void *img, size_t n,
                            void *stream) {
     if (!pred || !scale || !img) return pl_internal_fail(PL_ERR_ARG, "bad pl_nn_to_complex");

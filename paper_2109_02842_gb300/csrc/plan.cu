@@ -954,7 +954,7 @@ const char *pl_status_string(pl_status s) {
 
 const char *pl_last_error(void) { return g_err.c_str(); }
 
-int pl_version(void) { return 100; }
+int pl_version(void) { return 200; }
 
 pl_status pl_plan_create(pl_plan **out, const pl_geometry *geom, const pl_scan *scan,
                          const pl_freqs *freqs, const pl_grid *grid, const pl_options *opt) {
@@ -1177,6 +1177,17 @@ pl_status pl_plan_get_info(const pl_plan *P, pl_info *info) {
     i.updates_per_execute = (double)P->C * P->grid.nx * P->grid.ny * P->grid.nz * P->M;
     i.block_config = P->block_config;
     i.tile_u = P->tile_u;
+    i.es_beta = (double)P->nd.beta;
+    i.band_group = P->tile_u;
+    if (P->block_config == 4) {
+        i.table_layout = P->nd.tc_planar ? 3 : 2;
+        i.table_cols = P->nd.tc_cols;
+    } else {
+        i.table_layout = P->precision == 1 ? 1 : 0;
+        i.table_cols = 0;
+    }
+    i.table_exact = (P->block_config == 4 && P->rt_tc) ? 1 : 0;
+    i.precision = P->precision;
     *info = i;
     return PL_OK;
 }
@@ -1234,38 +1245,30 @@ pl_status pl_synth_echo(int n_chan, const double *tx_xy, const double *rx_xy, do
         !echo_dev || (n_pts > 0 && (!pts || !amp)))
         return fail(PL_ERR_ARG, "bad pl_synth_echo arguments");
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<float4> ch(n_chan);
-    for (int c = 0; c < n_chan; ++c)
-        ch[c] = make_float4((float)tx_xy[2 * c], (float)tx_xy[2 * c + 1], (float)rx_xy[2 * c],
-                            (float)rx_xy[2 * c + 1]);
-    std::vector<float> k(n_f);
-    for (int m = 0; m < n_f; ++m) k[m] = (float)(PL_TWO_PI * f_hz[m] / PL_C0);
-    const int np = std::max(n_pts, 1);
-    std::vector<float4> p(np, make_float4(0.f, 0.f, 0.f, 0.f));
-    std::vector<float2> a(np, make_float2(0.f, 0.f));
-    for (int t = 0; t < n_pts; ++t) {
-        p[t] = make_float4((float)pts[3 * t], (float)pts[3 * t + 1], (float)pts[3 * t + 2], 0.f);
-        a[t] = make_float2((float)amp[2 * t], (float)amp[2 * t + 1]);
-    }
-    float4 *d_ch = nullptr, *d_p = nullptr;
-    float *d_k = nullptr;
-    float2 *d_a = nullptr;
-    cudaError_t e = cudaMalloc(&d_ch, ch.size() * sizeof(float4));
-    if (e == cudaSuccess) e = cudaMalloc(&d_p, p.size() * sizeof(float4));
-    if (e == cudaSuccess) e = cudaMalloc(&d_k, k.size() * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&d_a, a.size() * sizeof(float2));
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ch, ch.data(), ch.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_p, p.data(), p.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_k, k.data(), k.size() * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_a, a.data(), a.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+    // device copies of the caller's FP64 arrays (the kernel forms the ranges
+    // in FP64)
+    const size_t b_ch = sizeof(double) * 2 * n_chan, b_f = sizeof(double) * n_f;
+    const size_t b_p = sizeof(double) * 3 * std::max(n_pts, 1);
+    const size_t b_a = sizeof(double) * 2 * std::max(n_pts, 1);
+    double *d_tx = nullptr, *d_rx = nullptr, *d_f = nullptr, *d_p = nullptr, *d_a = nullptr;
+    cudaError_t e = cudaMalloc(&d_tx, b_ch);
+    if (e == cudaSuccess) e = cudaMalloc(&d_rx, b_ch);
+    if (e == cudaSuccess) e = cudaMalloc(&d_f, b_f);
+    if (e == cudaSuccess) e = cudaMalloc(&d_p, b_p);
+    if (e == cudaSuccess) e = cudaMalloc(&d_a, b_a);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tx, tx_xy, b_ch, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rx, rx_xy, b_ch, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_f, f_hz, b_f, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n_pts > 0)
+        e = cudaMemcpyAsync(d_p, pts, sizeof(double) * 3 * n_pts, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n_pts > 0)
+        e = cudaMemcpyAsync(d_a, amp, sizeof(double) * 2 * n_pts, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = launch_synth_echo(n_chan, d_ch, n_scan, (float)z0, (float)dz, n_f, d_k, n_pts, d_p, d_a,
+        e = launch_synth_echo(n_chan, d_tx, d_rx, n_scan, z0, dz, n_f, d_f, n_pts, d_p, d_a,
                               (float2 *)echo_dev, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(d_ch);
-    cudaFree(d_p);
-    cudaFree(d_k);
-    cudaFree(d_a);
+    for (double *q : {d_tx, d_rx, d_f, d_p, d_a})
+        if (q) cudaFree(q);
     if (e != cudaSuccess) return cuda_fail(e, "pl_synth_echo");
     return PL_OK;
 }

@@ -22,45 +22,17 @@ constexpr int kMaxChan = PL_STATIC_MAX_CHANNELS;
 constexpr int kMaxFreq = PL_STATIC_MAX_FREQS;
 constexpr int kMaxPts = PL_STATIC_MAX_POINTS;
 
-// Byte offsets inside the scratch array: raw FP64 copies of the caller's
-// arrays, then the FP32 lists the synthesis kernel reads.
+// Byte offsets inside the scratch array: device copies of the caller's FP64
+// arrays, in the layouts the synthesis kernel reads directly.
 constexpr size_t kRawTx = 0;
 constexpr size_t kRawRx = kRawTx + sizeof(double) * 2 * kMaxChan;
 constexpr size_t kRawF = kRawRx + sizeof(double) * 2 * kMaxChan;
 constexpr size_t kRawPts = kRawF + sizeof(double) * kMaxFreq;
 constexpr size_t kRawAmp = kRawPts + sizeof(double) * 3 * kMaxPts;
-constexpr size_t kCh = (kRawAmp + sizeof(double) * 2 * kMaxPts + 255) / 256 * 256;
-constexpr size_t kK = kCh + sizeof(float4) * kMaxChan;
-constexpr size_t kPts = (kK + sizeof(float) * kMaxFreq + 255) / 256 * 256;
-constexpr size_t kAmp = kPts + sizeof(float4) * kMaxPts;
-constexpr size_t kScratchBytes = kAmp + sizeof(float2) * kMaxPts;
+constexpr size_t kScratchBytes = kRawAmp + sizeof(double) * 2 * kMaxPts;
 
 // The scratch. Every device that loads the library holds it until exit.
 static __device__ __align__(256) unsigned char g_synth_scratch[kScratchBytes];
-
-// Same conversions as pl_synth_echo performs on the host: positions and
-// points to float, k = 2 pi f / c in double then to float.
-__global__ void k_convert_inputs(const unsigned char *base, int n_chan, int n_f, int n_pts,
-                                 unsigned char *out) {
-    const double *tx = reinterpret_cast<const double *>(base + kRawTx);
-    const double *rx = reinterpret_cast<const double *>(base + kRawRx);
-    const double *f = reinterpret_cast<const double *>(base + kRawF);
-    const double *pts = reinterpret_cast<const double *>(base + kRawPts);
-    const double *amp = reinterpret_cast<const double *>(base + kRawAmp);
-    float4 *ch = reinterpret_cast<float4 *>(out + kCh);
-    float *k = reinterpret_cast<float *>(out + kK);
-    float4 *p = reinterpret_cast<float4 *>(out + kPts);
-    float2 *a = reinterpret_cast<float2 *>(out + kAmp);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n_chan)
-        ch[i] = make_float4((float)tx[2 * i], (float)tx[2 * i + 1], (float)rx[2 * i],
-                            (float)rx[2 * i + 1]);
-    if (i < n_f) k[i] = (float)(PL_TWO_PI * f[i] / PL_C0);
-    if (i < n_pts) {
-        p[i] = make_float4((float)pts[3 * i], (float)pts[3 * i + 1], (float)pts[3 * i + 2], 0.f);
-        a[i] = make_float2((float)amp[2 * i], (float)amp[2 * i + 1]);
-    }
-}
 
 std::mutex g_mu;
 unsigned char *g_addr[256] = {};
@@ -115,16 +87,11 @@ extern "C" pl_status pl_synth_echo_static(int n_chan, const double *tx_xy, const
         e = cudaMemcpyAsync(base + kRawAmp, amp, sizeof(double) * 2 * n_pts,
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
-        const int n = n_chan > n_f ? (n_chan > n_pts ? n_chan : n_pts) : (n_f > n_pts ? n_f : n_pts);
-        k_convert_inputs<<<(n + 127) / 128, 128, 0, st>>>(base, n_chan, n_f, n_pts, base);
-        e = cudaGetLastError();
+        const double *sb = reinterpret_cast<const double *>(base);
+        e = launch_synth_echo(n_chan, sb + kRawTx / 8, sb + kRawRx / 8, n_scan, z0, dz, n_f,
+                              sb + kRawF / 8, n_pts, sb + kRawPts / 8, sb + kRawAmp / 8,
+                              (float2 *)echo_dev, st);
     }
-    if (e == cudaSuccess)
-        e = launch_synth_echo(n_chan, reinterpret_cast<const float4 *>(base + kCh), n_scan,
-                              (float)z0, (float)dz, n_f, reinterpret_cast<const float *>(base + kK),
-                              n_pts, reinterpret_cast<const float4 *>(base + kPts),
-                              reinterpret_cast<const float2 *>(base + kAmp), (float2 *)echo_dev,
-                              st);
     if (e != cudaSuccess) return pl_internal_cuda_fail(e, "pl_synth_echo_static");
     return PL_OK;
 }

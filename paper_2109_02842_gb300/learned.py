@@ -48,6 +48,7 @@ _ARGTYPES = {
     "pl_nn_features": ([_P, _P, _P, _S, _P], _I),
     "pl_nn_loss": ([_P, _P, _P, _P, _P, _S, _P], _I),
     "pl_nn_residual": ([_P, _P, _P, _F, _S, _P], _I),
+    "pl_nn_check": ([_P, _P, _P, _F, _S, _P, _P], _I),
     "pl_nn_to_complex": ([_P, _P, _P, _S, _P], _I),
     "pl_nn_adam": ([_P, _P, _P, _P, _P, _S, _F, _F, _F, _F, _I, _P], _I),
 }
@@ -338,13 +339,31 @@ class FastPath:
         self.net.adam_step(lr)
         return sums
 
-    def infer(self, echo_cheap):
-        """Learned image (complex64 volume) from the cheap echo."""
+    def infer(self, echo_cheap, echo_full=None, max_correction=1.0):
+        """Learned image (complex64 volume) from the cheap echo (every other
+        frequency of the full echo, see cheap_echo).
+
+        Returns (image, cheap image, fell_back). The network's correction is
+        accepted only if it is finite and its L2 norm is at most
+        max_correction times that of the scaled cheap image it is added to
+        (pl_nn_check). Otherwise the plain reconstruction of echo_full, the
+        full echo, is returned with fell_back = True; without echo_full a
+        rejected correction raises RuntimeError."""
         import torch
         cheap = self.cheap.execute(echo_cheap)
         feat, scale = self.features(cheap)
         pred = self.net.forward(feat, self.dims)
+        stats = torch.empty(3, dtype=torch.float32, device="cuda")
+        B._check(lib().pl_nn_check(_p(pred), _p(cheap), _p(scale), self.gain, self.V, _p(stats),
+                                   _s()))
+        bad, corr2, base2 = (float(v) for v in stats.cpu())
+        if bad > 0 or not math.isfinite(corr2) or corr2 > max_correction ** 2 * base2:
+            if echo_full is None:
+                raise RuntimeError("learned correction rejected (%d non-finite values, "
+                                   "|corr|^2 = %.3e vs %.3e) and no full echo to fall back on"
+                                   % (bad, corr2, max_correction ** 2 * base2))
+            return self.full.execute(echo_full).view(self.dims), cheap, True
         B._check(lib().pl_nn_residual(_p(pred), _p(cheap), _p(scale), self.gain, self.V, _s()))
         img = torch.empty(self.V, dtype=torch.complex64, device="cuda")
         B._check(lib().pl_nn_to_complex(_p(pred), _p(scale), _p(img), self.V, _s()))
-        return img.view(self.dims), cheap
+        return img.view(self.dims), cheap, False

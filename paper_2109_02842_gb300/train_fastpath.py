@@ -58,7 +58,7 @@ def evaluate(fp, n_eval, first_seed=1_000_000):
     for j in range(n_eval):
         e = scene_echo(fp.w, first_seed + j)
         full = fp.full.execute(e)
-        img, cheap = fp.infer(fp.cheap_echo(e))
+        img, cheap, _ = fp.infer(fp.cheap_echo(e), e)
         f, i, c = (x.reshape(-1) for x in (full, img, cheap))
         a = torch.vdot(c, f) / torch.vdot(c, c)
         ec.append(float((a * c - f).norm() / f.norm()))
@@ -71,7 +71,7 @@ def time_paths(fp, reps=20):
     e = scene_echo(fp.w, 7)
     ec = fp.cheap_echo(e)
     out = fp.full.execute(e)
-    fp.infer(ec)
+    fp.infer(ec, e)
     torch.cuda.synchronize()
 
     def timed(fn):
@@ -84,7 +84,7 @@ def time_paths(fp, reps=20):
         return s.elapsed_time(t) / reps
 
     t_full = timed(lambda: fp.full.execute(e, out))
-    t_learned = timed(lambda: fp.infer(ec))
+    t_learned = timed(lambda: fp.infer(ec, e))
     t_cheap = timed(lambda: fp.cheap.execute(ec))
     return t_full, t_learned, t_cheap
 

@@ -106,10 +106,14 @@ def monostatic_array(radius, n_sections, span_deg, per_chord):
 
 
 def multistatic_array(radius, n_sections, span_deg, n_tx, n_rx, cross_section=False):
-    """Tx and Rx interleaved on each chord; pairs = all Tx x Rx within a chord.
+    """Tx and Rx interleaved on each chord; pairs = all Tx x Rx within a chord,
+    and with ``cross_section`` also every Tx with every Rx of the neighbouring
+    chords (s - 1 and s + 1), the cross-section pairs Sec. II-C allows.
 
     Element order: for each section, its n_tx transmitters then its n_rx
-    receivers. Pair order: section, then Tx, then Rx.
+    receivers. Pair order: section, then Tx, then Rx (the within-chord pairs
+    of all sections first, then the cross-section pairs in the same order,
+    neighbouring chord s - 1 before s + 1).
     """
     j = chord_joints(radius, n_sections, span_deg)
     xy, sec, ptx, prx = [], [], [], []
@@ -123,6 +127,15 @@ def multistatic_array(radius, n_sections, span_deg, n_tx, n_rx, cross_section=Fa
                 ptx.append(base + t)
                 prx.append(base + n_tx + r)
         base += n_tx + n_rx
+    if cross_section:
+        per = n_tx + n_rx
+        for s in range(n_sections):
+            for t in range(n_tx):
+                for nb in (s - 1, s + 1):
+                    if 0 <= nb < n_sections:
+                        for r in range(n_rx):
+                            ptx.append(s * per + t)
+                            prx.append(nb * per + n_tx + r)
     return (np.concatenate(xy), np.array(sec), np.array(ptx), np.array(prx),
             float(np.linalg.norm(j[1] - j[0])))
 
@@ -259,10 +272,14 @@ def multi(seed: int = 0, n_surf: int = 500, n_bright: int = 10) -> Workload:
                     pts, amp, 30.0, seed)
 
 
-def paper_table1(mode: int, seed: int = 0, n_scan: int = 64, n_grid: int = 64) -> Workload:
+def paper_table1(mode: int, seed: int = 0, n_scan: int = 64, n_grid: int = 64,
+                 cross_section: bool = False) -> Workload:
     """Table I of the paper: R0 = 1.0 m, 3 sections, 30-35 GHz in 51 steps,
     dz = 0.5 cm; mono 40 elements per section at 0.48 cm; multi 4 Tx in total
-    (at the joints and ends) with 20 Rx per section, pairs within a section.
+    (at the joints and ends) with 20 Rx per section, pairs within a section
+    (each section's Rx with the two Tx at its ends); with ``cross_section``
+    also every Tx with the Rx of the sections it does not bound (Sec. II-C:
+    a joint transmitter may also serve the farther sections).
     The paper gives no scan count and no image grid: ``n_scan`` scans and an
     ``n_grid``^3 grid over a 0.2 m cube are this module's choice. The chord
     length is set by the element count times the stated spacing (0.192 m),
@@ -283,6 +300,13 @@ def paper_table1(mode: int, seed: int = 0, n_scan: int = 64, n_grid: int = 64) -
                 for r in range(20):
                     ptx.append(t)
                     prx.append(4 + 20 * s + r)
+        if cross_section:
+            for s in range(3):
+                for t in range(4):
+                    if t not in (s, s + 1):
+                        for r in range(20):
+                            ptx.append(t)
+                            prx.append(4 + 20 * s + r)
         ptx, prx = np.array(ptx), np.array(prx)
     dz = 0.005
     z0 = -(n_scan - 1) / 2 * dz
@@ -293,7 +317,8 @@ def paper_table1(mode: int, seed: int = 0, n_scan: int = 64, n_grid: int = 64) -
                          (0.1, 0.1, min(span_z[1], 0.1)), 5)
     amp = rng.uniform(0.5, 1.0, 5).astype(np.complex128)
     n_pad = 1 << int(math.ceil(math.log2(2 * n_scan)))
-    return Workload("table1-%s" % ("mono" if mode == 0 else "multi"), mode, 1.0, 3, L, xy,
+    name = "table1-%s%s" % ("mono" if mode == 0 else "multi", "-cross" if cross_section else "")
+    return Workload(name, mode, 1.0, 3, L, xy,
                     sec, ptx, prx, z0, dz, n_scan, n_pad, uniform_freqs(30e9, 35e9, 51),
                     dict(x0=x0, dx=dx, nx=n_grid, y0=x0, dy=dx, ny=n_grid, z0=x0, dz=dx,
                          nz=n_grid), pts, amp, 30.0, seed)
@@ -328,6 +353,16 @@ def batch_scene(index: int, seed: int = 0) -> Workload:
     nf = int(rng.integers(32, 97))
     ng = int(rng.integers(64, 161))
     npts = int(rng.integers(50, 501))
+    return uneven_scene(rng, ns, per, n, nf, ng, npts, "batch-scene-%d" % index, seed)
+
+
+def uneven_scene(rng, ns: int, per: int, n: int, nf: int, ng: int, npts: int,
+                 name: str = "uneven-scene", seed: int = 0) -> Workload:
+    """A monostatic scene of the batched workload's family with the given
+    sizes: ``ns`` chords of R = 0.6 m over 120 deg with ``per`` elements each,
+    ``n`` scans at 5 mm (N_p the smallest 5-smooth length >= 2 n), ``nf``
+    frequencies over 24-34 GHz, an ``ng``^3 image (0.4 x 0.4 m, z over the
+    scan span) and ``npts`` points U(0.5, 1) drawn from ``rng``."""
     xy, sec, L = monostatic_array(0.6, ns, 120.0, per)
     dz = 0.005
     z0 = -(n - 1) / 2 * dz
@@ -336,7 +371,7 @@ def batch_scene(index: int, seed: int = 0) -> Workload:
     zz0, zdz = centred_axis(zext, ng)
     pts = uniform_points(rng, (-0.15, -0.15, z0), (0.15, 0.15, z0 + (n - 1) * dz), npts)
     amp = rng.uniform(0.5, 1.0, npts).astype(np.complex128)
-    return Workload("batch-scene-%d" % index, 0, 0.6, ns, L, xy, sec, np.zeros(0, int),
+    return Workload(name, 0, 0.6, ns, L, xy, sec, np.zeros(0, int),
                     np.zeros(0, int), z0, dz, n, smooth_at_least(2 * n),
                     uniform_freqs(24e9, 34e9, nf),
                     dict(x0=x0, dx=dx, nx=ng, y0=x0, dy=dx, ny=ng, z0=zz0, dz=zdz, nz=ng),

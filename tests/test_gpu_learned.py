@@ -129,6 +129,29 @@ def test_features_loss_adam(L):
     assert rel(out.cpu().numpy(), pred + 2.0 * np.stack([g.real, g.imag], 1) / rs) < 1e-6
 
 
+def test_correction_check_kernel(L):
+    # pl_nn_check against NumPy: non-finite count, sum of squares of the
+    # finite correction entries, and of the scaled cheap image
+    from paper_2109_02842_gb300 import binding as B
+    rng = np.random.default_rng(21)
+    n = 5000
+    corr = rng.standard_normal((n, 2)).astype(np.float32)
+    corr[17, 1] = np.nan
+    corr[4000, 0] = np.inf
+    img = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    scale = torch.tensor([2.5], device="cuda")
+    out = torch.empty(3, device="cuda")
+    B._check(L.lib().pl_nn_check(L._p(torch.from_numpy(corr).cuda()),
+                                 L._p(torch.from_numpy(img).cuda()), L._p(scale), 2.0, n,
+                                 L._p(out), L._s()))
+    got = out.cpu().numpy().astype(np.float64)
+    fin = np.isfinite(corr)
+    assert got[0] == 2
+    assert abs(got[1] - np.sum(corr[fin].astype(np.float64) ** 2)) < 1e-5 * got[1]
+    ref_i = np.sum(np.abs(2.0 * img.astype(np.complex128) / 2.5) ** 2)
+    assert abs(got[2] - ref_i) < 1e-5 * ref_i
+
+
 def _oracle_unet(net, feat, target_over_s):
     """Forward + backward of the same network with the oracle's layers (FP64)."""
     def W(conv):
@@ -191,10 +214,12 @@ def _oracle_unet(net, feat, target_over_s):
     return loss, grads
 
 
-def test_network_gradients_match_oracle(L):
+@pytest.mark.parametrize("widths", [(4, 8, 16, 16), (16, 32, 64, 128)])
+def test_network_gradients_match_oracle(L, widths):
+    # (16, 32, 64, 128): the widths of the learned fast path itself
     from paper_2109_02842_gb300 import binding as B
     dims = (8, 8, 16)
-    net = L.UNet3D(seed=3, widths=(4, 8, 16, 16))
+    net = L.UNet3D(seed=3, widths=widths)
     rng = np.random.default_rng(9)
     # the head starts at zero (no gradient would reach the other layers)
     hw = np.zeros(tuple(net.head.w.shape), np.float32)
@@ -272,7 +297,8 @@ def test_training_beats_the_cheap_reconstruction(L):
     for s in range(8):
         echo = _scene_echo(fp, 50000 + s)
         full = fp.full.execute(echo).cpu().numpy().ravel()
-        img, cheap = fp.infer(fp.cheap_echo(echo))
+        img, cheap, fell_back = fp.infer(fp.cheap_echo(echo), echo)
+        assert not fell_back
         img, cheap = img.cpu().numpy().ravel(), cheap.cpu().numpy().ravel()
         a = np.vdot(cheap, full) / np.vdot(cheap, cheap)
         e_cheap.append(rel(a * cheap, full))
@@ -280,3 +306,24 @@ def test_training_beats_the_cheap_reconstruction(L):
     print("held-out rel L2 vs full: network %.3f, cheap (best-scaled) %.3f"
           % (np.mean(e_net), np.mean(e_cheap)))
     assert np.mean(e_net) < 0.85 * np.mean(e_cheap)
+
+
+def test_rejected_correction_falls_back_to_the_plain_image(L):
+    """The plain hybrid method stays the fallback: a network whose correction
+    is non-finite (a NaN written into the head's bias on the host side) or
+    implausibly large (a huge head bias) returns the full plain image, the
+    same bits as the plain path's own execution."""
+    fp = _small_fastpath(L)
+    echo = _scene_echo(fp, 3)
+    full = fp.full.execute(echo).cpu().numpy()
+    img, _, fell_back = fp.infer(fp.cheap_echo(echo), echo)
+    assert not fell_back                       # zero head: no correction yet
+    for bad in (float("nan"), 1e6):
+        b = np.zeros(2, np.float32)
+        b[0] = bad
+        fp.net.head.b.copy_(torch.from_numpy(b))
+        img, _, fell_back = fp.infer(fp.cheap_echo(echo), echo)
+        assert fell_back
+        assert np.array_equal(img.cpu().numpy(), full)
+        with pytest.raises(RuntimeError):
+            fp.infer(fp.cheap_echo(echo))

@@ -28,6 +28,15 @@ def report(name, got, ref):
     e = rel(got, ref)
     mx = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
     print("%s: rel L2 %.3e, max |err| / max |ref| %.3e" % (name, e, mx))
+    return e, mx
+
+
+def check(name, got, ref, tol):
+    """Relative L2 error and the largest per-voxel error (relative to the
+    largest reference magnitude) both within `tol`; returns the L2 error."""
+    e, mx = report(name, got, ref)
+    assert e < tol, (name, e)
+    assert mx < tol, (name, mx)
     return e
 
 
@@ -72,7 +81,7 @@ def test_zfft_stage_matches_dft(binding, n_pad):
     echo = scene_echo(w)
     plan, _ = run_gpu(binding, w, echo, block_config=1)
     S = plan.workspace(binding.PL_STAGE_ZFFT).cpu().numpy()
-    assert report("S n_pad=%d" % n_pad, S, oracle.zdft(echo, n_pad)) < 1e-5
+    check("S n_pad=%d" % n_pad, S, oracle.zdft(echo, n_pad), 1e-5)
 
 
 @pytest.mark.parametrize("bc", [0, 1])
@@ -86,7 +95,7 @@ def test_kspace_image_matches_exact_sum(binding, bc):
     G = G.reshape(-1, w.n_pad, w.grid["nx"] * w.grid["ny"]).sum(axis=0)
     S = oracle.zdft(echo, w.n_pad)
     ref = oracle.hybrid_spectral(0, w.tx_xy, w.rx_xy, S, w.dz, w.f_hz, w.pix_xy())
-    assert report("G small mono", G, ref) < TOL_FP32
+    check("G small mono", G, ref, TOL_FP32)
 
 
 # --- end-to-end images ----------------------------------------------------------
@@ -103,7 +112,7 @@ def test_small_mono_image(binding, bc):
     echo = scene_echo(w)
     _, img = run_gpu(binding, w, echo, block_config=bc)
     ref = image_ref(w, echo)
-    assert report("image small mono", img.reshape(w.grid["nz"], -1), ref) < TOL_FP32
+    check("image small mono", img.reshape(w.grid["nz"], -1), ref, TOL_FP32)
 
 
 @pytest.mark.parametrize("bc", [0, 1])
@@ -112,7 +121,7 @@ def test_small_multi_image(binding, bc):
     echo = scene_echo(w)
     _, img = run_gpu(binding, w, echo, block_config=bc)
     ref = image_ref(w, echo)
-    assert report("image small multi", img.reshape(w.grid["nz"], -1), ref) < TOL_FP32
+    check("image small multi", img.reshape(w.grid["nz"], -1), ref, TOL_FP32)
 
 
 @pytest.mark.parametrize("bc", [0, 1])
@@ -135,7 +144,7 @@ def test_ragged_grid_and_offgrid_z(binding, bc):
     echo = scene_echo(w, 3)
     plan, img = run_gpu(binding, w, echo, block_config=bc)
     assert plan.info["z_transform_fft"] == 0
-    assert report("image ragged", img.reshape(7, -1), image_ref(w, echo)) < TOL_FP32
+    check("image ragged", img.reshape(7, -1), image_ref(w, echo), TOL_FP32)
 
 
 def test_scan_grid_ifft_path_with_offset(binding):
@@ -145,7 +154,7 @@ def test_scan_grid_ifft_path_with_offset(binding):
     echo = scene_echo(w, 4)
     plan, img = run_gpu(binding, w, echo)
     assert plan.info["z_transform_fft"] == 1
-    assert report("image ifft path", img.reshape(20, -1), image_ref(w, echo)) < TOL_FP32
+    check("image ifft path", img.reshape(20, -1), image_ref(w, echo), TOL_FP32)
 
 
 @pytest.mark.parametrize("bc", [0, 1])
@@ -156,7 +165,7 @@ def test_single_frequency_and_single_scan(binding, bc):
     w.grid = dict(w.grid, nz=1, z0=w.z0, dz=w.dz)
     echo = scene_echo(w, 5)
     _, img = run_gpu(binding, w, echo, block_config=bc)
-    assert report("image 1 freq 1 scan", img.reshape(1, -1), image_ref(w, echo)) < TOL_FP32
+    check("image 1 freq 1 scan", img.reshape(1, -1), image_ref(w, echo), TOL_FP32)
 
 
 @pytest.mark.parametrize("bc", [0, 1])
@@ -164,7 +173,7 @@ def test_bf16_table_variant(binding, bc):
     w = wl.small_mono(seed=0)
     echo = scene_echo(w)
     _, img = run_gpu(binding, w, echo, precision=1, block_config=bc)
-    assert report("image bf16 table", img.reshape(w.grid["nz"], -1), image_ref(w, echo)) < TOL_BF16
+    check("image bf16 table", img.reshape(w.grid["nz"], -1), image_ref(w, echo), TOL_BF16)
 
 
 def test_execute_host_matches_device(binding):
@@ -248,14 +257,21 @@ def test_evanescent_bins_are_dropped(binding, bc):
     w.grid = dict(w.grid, nz=8, z0=w.z0, dz=w.dz)
     echo = scene_echo(w, 9)
     _, img = run_gpu(binding, w, echo, block_config=bc)
-    assert report("image evanescent bins", img.reshape(8, -1), image_ref(w, echo)) < TOL_FP32
+    check("image evanescent bins", img.reshape(8, -1), image_ref(w, echo), TOL_FP32)
 
 
-def test_gpu_echo_synthesis_matches_oracle(binding):
-    w = wl.small_mono(seed=7)
-    got = binding.synth_echo(w.tx_xy, w.rx_xy, w.z0, w.dz, w.n_scan, w.f_hz, w.pts, w.amp)
-    ref = oracle.synth_echo(w.tx_xy, w.rx_xy, w.z_scan, w.f_hz, w.pts, w.amp)
-    assert rel(got.cpu().numpy(), ref) < 1e-3
+@pytest.mark.parametrize("which", ["small_mono", "full_mono", "multi"])
+def test_gpu_echo_synthesis_matches_oracle(binding, which):
+    # ranges in FP64, k R as a float-float product reduced modulo 2 pi before
+    # the FP32 sin/cos: ~1e-6 rad per phase at k R ~ 1.5e3 rad (full size:
+    # the first 48 channels, 64 of the scene's points)
+    w = wl.WORKLOADS[which](seed=7)
+    tx, rx, pts, amp = w.tx_xy, w.rx_xy, w.pts, w.amp
+    if which != "small_mono":
+        tx, rx, pts, amp = tx[:48], rx[:48], pts[:64], amp[:64]
+    got = binding.synth_echo(tx, rx, w.z0, w.dz, w.n_scan, w.f_hz, pts, amp).cpu().numpy()
+    ref = oracle.synth_echo(tx, rx, w.z_scan, w.f_hz, pts, amp)
+    check("echo synthesis %s" % which, got, ref, 1e-5)
 
 
 # --- full sizes, sampled outputs --------------------------------------------------
@@ -275,7 +291,7 @@ def test_full_size_sampled_columns(binding, which):
     idx = sampled_columns(w, 48, 1)
     ref = image_ref(w, echo, w.pix_xy()[idx])
     got = img.reshape(w.grid["nz"], -1)[:, idx]
-    assert report("image %s sampled" % which, got, ref) < TOL_FP32
+    check("image %s sampled" % which, got, ref, TOL_FP32)
 
 
 # --- tensor cores (block_config 4: tcgen05, TMEM accumulators, TMA windows) -------
@@ -317,7 +333,7 @@ def test_tensor_core_variant_small(binding, case):
         assert i["tile_u"] == 128 and i["slab_rows"] == 16
     assert i["nufft_w"] == 6 and i["slab_rows"] in (16, 32)
     ref = image_ref(w, echo)
-    assert report("image tc %s" % case, img.reshape(w.grid["nz"], -1), ref) < TOL_FP32
+    check("image tc %s" % case, img.reshape(w.grid["nz"], -1), ref, TOL_FP32)
     # a second execution reports any bounded wait of the first that ran out
     plan.execute(torch.from_numpy(echo).cuda())
     torch.cuda.synchronize()
@@ -338,9 +354,8 @@ def test_tensor_core_other_tap_counts(binding, taps, grid):
     echo = scene_echo(w, 6)
     plan, img = run_gpu(binding, w, echo, block_config=4, nufft_w=taps)
     assert plan.info["nufft_w"] == taps and plan.info["block_config"] == 4
-    err = report("image tc %d taps %s" % (taps, grid), img.reshape(w.grid["nz"], -1),
-                 image_ref(w, echo))
-    assert err < (2e-3 if taps == 4 else TOL_FP32)
+    check("image tc %d taps %s" % (taps, grid), img.reshape(w.grid["nz"], -1),
+          image_ref(w, echo), 2e-3 if taps == 4 else TOL_FP32)
 
 
 def test_tensor_core_bf16_only_products(binding):
@@ -348,7 +363,7 @@ def test_tensor_core_bf16_only_products(binding):
     echo = scene_echo(w, 2)
     _, img = run_gpu(binding, w, echo, block_config=4, precision=1)
     ref = image_ref(w, echo)
-    assert report("image tc bf16", img.reshape(w.grid["nz"], -1), ref) < TOL_BF16
+    check("image tc bf16", img.reshape(w.grid["nz"], -1), ref, TOL_BF16)
 
 
 @pytest.mark.parametrize("which", ["full_mono", "multi"])
@@ -366,4 +381,66 @@ def test_tensor_core_variant_full_size_sampled(binding, which):
     idx = sampled_columns(w, 48, 1)
     ref = image_ref(w, echo, w.pix_xy()[idx])
     got = img.reshape(w.grid["nz"], -1)[:, idx]
-    assert report("image tc %s sampled" % which, got, ref) < TOL_FP32
+    check("image tc %s sampled" % which, got, ref, TOL_FP32)
+
+
+# --- configurations at the edges of the workloads --------------------------------
+
+def test_tensor_core_96_frequencies_nufft_table(binding):
+    # more than 64 frequencies: the tensor-core back-projection reads a table
+    # built by the type-1 NUFFT (spread, fine FFT, deconvolution)
+    w = wl.small_mono(seed=8)
+    w.f_hz = wl.uniform_freqs(28e9, 33e9, 96)
+    echo = scene_echo(w, 8)
+    plan, img = run_gpu(binding, w, echo)
+    assert plan.info["block_config"] == 4 and plan.info["table_exact"] == 0
+    check("image tc 96 freqs", img.reshape(w.grid["nz"], -1), image_ref(w, echo), TOL_FP32)
+
+
+def test_uneven_scene_at_the_edge_of_the_batch_ranges(binding):
+    # the largest scene the batched workload draws: 12 sections x 48 elements
+    # (576 channels), 256 scans (N_p 512), 96 frequencies, a 160^3 image;
+    # 500 points, 32 sampled columns x all 160 heights
+    w = wl.uneven_scene(wl.rng_for(4, 999), 12, 48, 256, 96, 160, 500, "uneven-edge")
+    assert (w.n_chan, w.n_scan, w.n_pad, w.n_f, w.grid["nx"]) == (576, 256, 512, 96, 160)
+    echo = scene_echo(w, 9, n_pts=64)
+    plan, img = run_gpu(binding, w, echo)
+    print("edge scene: block_config %d, tile_u %d, window rows %d, table rows %d, exact %d"
+          % (plan.info["block_config"], plan.info["tile_u"], plan.info["slab_rows"],
+             plan.info["table_len"], plan.info["table_exact"]))
+    idx = sampled_columns(w, 32, 3)
+    ref = image_ref(w, echo, w.pix_xy()[idx])
+    got = img.reshape(w.grid["nz"], -1)[:, idx]
+    check("image edge scene sampled", got, ref, TOL_FP32)
+
+
+@pytest.mark.parametrize("bc", [4, 1])
+def test_full_size_multistatic_bf16_variants(binding, bc):
+    # precision 1 at the full multistatic size (1024 pairs, 128 scans,
+    # 64 frequencies, 192 x 192 x 128): BF16-only products on the tensor
+    # cores (bc 4), a BF16 table with FP32 arithmetic (bc 1)
+    w = wl.multi(seed=0)
+    echo = scene_echo(w, 0, n_pts=24)
+    plan, img = run_gpu(binding, w, echo, block_config=bc, precision=1)
+    assert plan.info["precision"] == 1 and plan.info["block_config"] == bc
+    idx = sampled_columns(w, 48, 1)
+    ref = image_ref(w, echo, w.pix_xy()[idx])
+    got = img.reshape(w.grid["nz"], -1)[:, idx]
+    check("image multi precision 1 bc %d sampled" % bc, got, ref, TOL_BF16)
+
+
+@pytest.mark.parametrize("mode,cross", [(0, False), (1, False), (1, True)])
+def test_paper_table1_geometry(binding, mode, cross):
+    # Table I: R0 = 1.0 m, 3 sections, 51 frequencies over 30-35 GHz, dz 0.5 cm;
+    # mono 40 elements per section, multi 4 Tx at the joints and ends with 20 Rx
+    # per section (pairs within a section; cross: every Tx with every section's
+    # Rx); 64 scans and a 64^3 grid over 0.2 m (the paper states neither);
+    # 128 sampled columns x all heights
+    w = wl.paper_table1(mode, seed=1, cross_section=cross)
+    assert w.n_chan == (120 if mode == 0 else (240 if cross else 120))
+    echo = scene_echo(w, 1)
+    plan, img = run_gpu(binding, w, echo)
+    idx = sampled_columns(w, 128, 4)
+    ref = image_ref(w, echo, w.pix_xy()[idx])
+    got = img.reshape(w.grid["nz"], -1)[:, idx]
+    check("image %s sampled" % w.name, got, ref, TOL_FP32)

@@ -221,6 +221,58 @@ def test_range_profile_at_kz0_is_inverse_dft():
     assert rel(q, ref) < 1e-12
 
 
+@pytest.mark.parametrize("u", [3, 29])
+def test_range_profile_mono_at_l_equals_multi_at_2l(u):
+    # Eq. (5) vs Eq. (18): kappa_mono(k, k_z) = 2 kappa_multi(k, k_z) for every
+    # k and k_z, and so for kappa_0 = kappa(k_0, k_z) too. Hence, at k_z != 0,
+    # q_mono(l) = q_multi(2 l) for the same spectrum. A kappa_0 that is wrong
+    # in one mode (2 k_0 in both, or the monostatic kappa_0 in mode 1) or a
+    # multistatic branch with the monostatic dispersion fails this.
+    rng = np.random.default_rng(11)
+    M, n_pad, dz = 24, 64, 0.005
+    f = np.linspace(24e9, 34e9, M)
+    S = rng.standard_normal((2, n_pad, M)) + 1j * rng.standard_normal((2, n_pad, M))
+    assert abs(oracle.kz_bins(n_pad, dz)[u]) > 50.0
+    l = np.linspace(0.31, 0.93, 17)
+    q0 = oracle.range_profile(0, S, dz, f, 1, u, l)
+    q1 = oracle.range_profile(1, S, dz, f, 1, u, 2 * l)
+    assert np.max(np.abs(q0 - q1)) / np.max(np.abs(q0)) < 1e-12
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_range_profile_times_carrier_is_the_hybrid_sum(mode):
+    # Eq. (8a)-(8b) (mode 0) and (19a)-(19b) (mode 1) split the phase as
+    # kappa a = kappa' a + kappa_0 a with kappa_0 = kappa(k_0, k_z). For
+    # channels whose range a (rho, or rho_T + rho_R) to a pixel is the same,
+    # sum_c q_c(a) e^{j kappa_0 a} must equal the exact-sum hybrid G_u at that
+    # pixel (Eq. 7 / 19, pinned above by the adjoint identity), at k_z != 0,
+    # where kappa_0 differs from 2 k_0 (mode 0) and k_0 (mode 1).
+    rng = np.random.default_rng(12 + mode)
+    M, n_pad, dz = 20, 32, 0.005
+    f = np.linspace(24e9, 34e9, M)
+    k0 = 2 * np.pi * f[0] / C0
+    S = rng.standard_normal((3, n_pad, M)) + 1j * rng.standard_normal((3, n_pad, M))
+    pix = np.array([[0.013, -0.021]])
+    phis = np.array([-1.1, -0.4, 0.7])
+    if mode == 0:
+        rho = 0.55                                   # three elements at range 0.55 m
+        tx = pix + rho * np.stack([np.sin(phis), -np.cos(phis)], 1)
+        rx = tx
+        a = rho
+    else:
+        # Tx at 0.50 m and Rx at 0.62 m from the pixel: a = 1.12 m per pair
+        tx = pix + 0.50 * np.stack([np.sin(phis), -np.cos(phis)], 1)
+        rx = pix + 0.62 * np.stack([np.sin(phis + 0.05), -np.cos(phis + 0.05)], 1)
+        a = 1.12
+    G = oracle.hybrid_spectral(mode, tx, rx, S, dz, f, pix)
+    kz = oracle.kz_bins(n_pad, dz)
+    for u in (0, 5, 17, 31):
+        kap0 = math.sqrt(4 * k0 ** 2 - kz[u] ** 2) if mode == 0 else math.sqrt(k0 ** 2 - kz[u] ** 2 / 4)
+        q = sum(oracle.range_profile(mode, S, dz, f, c, u, [a])[0] for c in range(3))
+        got = q * np.exp(1j * kap0 * a)
+        assert abs(got - G[u, 0]) / abs(G[u, 0]) < 1e-10, (u, got, G[u, 0])
+
+
 def test_bp_and_hybrid_agree_on_tiny_grid():
     # Sec. III: the proposed method's focusing is very similar to BP. Each
     # point alone peaks at the same voxel under both; for the whole scene the
