@@ -100,7 +100,11 @@ typedef struct {
 
 /* Numerical options. Zero-initialise and set what you need.
  * precision: 0 = FP32 everywhere (default);
- *            1 = range-profile table stored as BF16 pairs (FP32 accumulate).
+ *            1 = range-profile table stored as BF16 pairs (FP32 accumulate);
+ *            2 = as 1, and the spectrum S of Eq. (2) stored in BF16 as well
+ *                (FP32 kernels: S as bfloat16 (re, im) pairs; block_config 4:
+ *                the exact-sum range table takes the spectrum's BF16 part
+ *                only, two products per real product instead of three).
  * nufft_sigma: oversampling of the range-profile grid (default 2.0).
  * nufft_w: interpolation taps (even, 4..12; default 6).
  * tile_u: k_z bins per back-projection block (8, 16, 20 or 24; with
@@ -279,12 +283,13 @@ pl_status pl_plan_get_info(const pl_plan *plan, pl_info *info);
 
 /* Device pointer and size of an intermediate buffer, valid until the plan is
  * destroyed (for inspection and tests):
- *  PL_STAGE_ZFFT        -> spectrum S, complex64 [n_chan][n_pad][n_f] (not written by
+ *  PL_STAGE_ZFFT        -> spectrum S, complex64 [n_chan][n_pad][n_f] (bfloat16 (re, im)
+ *                          pairs with precision 2 on the NUFFT paths; not written by
  *                          the tensor-core path with an FFT-length scan: there the
  *                          z-FFT hands its output straight to the range table)
  *  PL_STAGE_RANGE_TABLE -> table b, [n_chan][L][ceil(n_pad/2)] rows of k_z bin pairs
  *                          {re_u, re_u+1, im_u, im_u+1} (float32, or bfloat16 when
- *                          precision = 1); block_config 4: see pl_options
+ *                          precision >= 1); block_config 4: see pl_options
  *  PL_STAGE_BACKPROJECT -> image spectrum G, complex64 [parts][n_pad][ny][nx]: the
  *                          spectrum is the sum over parts (2 parts, one per half
  *                          of the channels, in the planar block_config 4 layout;

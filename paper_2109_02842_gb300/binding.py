@@ -327,17 +327,21 @@ class Plan:
         i = self.info
         if stage == PL_STAGE_ZFFT:
             shape = (i["n_chan"], i["n_pad"], i["n_f"])
+            if nbytes.value == np.prod(shape) * 4:        # BF16 spectrum (precision 2)
+                raw = torch.as_tensor(_DevArray(ptr.value, shape + (2,), "<i2"), device="cuda")
+                return raw.view(torch.bfloat16)
         elif stage == PL_STAGE_RANGE_TABLE:
-            # rows of planar bin pairs {re_u, re_u+1, im_u, im_u+1}
-            shape = (i["n_chan"], i["table_len"], (i["n_pad"] + 1) // 2, 4)
-            if nbytes.value not in (np.prod(shape) * 2, np.prod(shape) * 4):
+            lay = i["table_layout"]
+            if lay in (2, 3):
                 # tensor-core layout [c][hi/lo][row][column] (BF16; columns
                 # 2u + (re, im), or planar: Re of the bins, then Im)
-                cols = nbytes.value // (i["n_chan"] * 2 * i["table_len"] * 2)
-                shape = (i["n_chan"], 2, i["table_len"], cols)
-                raw = torch.as_tensor(_DevArray(ptr.value, shape, "<i2"), device="cuda")
-                return raw.view(torch.bfloat16)
-            if nbytes.value == np.prod(shape) * 2:   # BF16
+                shape = (i["n_chan"], 2, i["table_len"], i["table_cols"])
+            else:
+                # rows of planar bin pairs {re_u, re_u+1, im_u, im_u+1}
+                shape = (i["n_chan"], i["table_len"], (i["n_pad"] + 1) // 2, 4)
+            esize = 4 if lay == 0 else 2
+            assert nbytes.value == np.prod(shape) * esize, (nbytes.value, shape, lay)
+            if esize == 2:
                 raw = torch.as_tensor(_DevArray(ptr.value, shape, "<i2"), device="cuda")
                 return raw.view(torch.bfloat16)
             return torch.as_tensor(_DevArray(ptr.value, shape, "<f4"), device="cuda")

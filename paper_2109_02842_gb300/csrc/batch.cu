@@ -281,7 +281,7 @@ pl_status build_queue(pl_batch *B, int tile_u, double timeout_ms, int debug) {
         d.bp_items = d.ntx * d.nty * d.nut;
         d.need = d.rt_items + ((debug && k == 0) ? 1 : 0);
         smem = std::max(smem, rt::smem_bytes(p->nd.fine, kBatchUB, p->nd.n_f));
-        smem = std::max(smem, backproject_smem_bytes(p->R, tile_u, p->C, p->precision,
+        smem = std::max(smem, backproject_smem_bytes(p->R, tile_u, p->C, p->precision >= 1,
                                                      B->block_config));
     }
     int total = rt;

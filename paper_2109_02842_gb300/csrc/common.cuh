@@ -60,4 +60,5 @@ struct NufftDesc {
     double h, l0;      // table step and origin (m)
     int tc_cols;       // tensor-core table layout: columns (2 per bin) per row
     int tc_planar;     // 1: [Re of the bins | Im of the bins] per row, 0: (re, im) pairs
+    int s_bf16;        // 1: the spectrum S is stored as bfloat16 (re, im) pairs
 };

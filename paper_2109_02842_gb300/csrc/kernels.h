@@ -13,13 +13,13 @@ cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_i
                                const FftPlan &plan, const float2 *tw, int sgn, float scale,
                                int out_rows, int out_off, cudaStream_t st,
                                void *split_A = nullptr, int split_Kp = 0,
-                               const float2 *in2 = nullptr, int ld = 0);
+                               const float2 *in2 = nullptr, int ld = 0, int bf16_out = 0);
 // (ld: row stride in elements, 0 = I; a launch may cover columns [0, I) of
 // wider rows, the pointers offset by the first column)
 // in2 (optional): a second input of the same shape, added to `in` on load
 cudaError_t launch_dft_strided(const float2 *in, float2 *out, int batch, int n_in, int I,
                                int out_rows, const float2 *T, float scale, cudaStream_t st,
-                               const float2 *in2 = nullptr);
+                               const float2 *in2 = nullptr, int bf16_out = 0);
 
 // ---- setup.cu --------------------------------------------------------------
 // Per k_z bin: kappa range over propagating frequencies; kc = centre (double
@@ -141,6 +141,8 @@ struct RtTcArgs {
     unsigned idesc;      // tcgen05 instruction descriptor (M 128, N Lh, both K-major)
     long long budget;    // wait budget, SM clock cycles
     int grid;            // persistent blocks (one per SM)
+    int a_hi_only;       // 1: the spectrum operand is BF16 (hi planes only): 8 products
+                         // per K step instead of 12
 };
 size_t range_table_tc_smem_bytes(const RtTcArgs &ra);
 // E [N_p][re hi, re lo, im hi, im lo][Lp][Kp] BF16: alpha_um e^{+j theta_um (i - L/2)}

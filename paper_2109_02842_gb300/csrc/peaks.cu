@@ -63,12 +63,12 @@ __global__ void __launch_bounds__(kThreads) k_peak_smem(int iters) {
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            // an asm volatile load, so the compiler cannot keep the
-            // (repeating) values in registers instead of reading them again
+            // a volatile load, so neither compiler can keep the (repeating)
+            // values in registers instead of reading them again
             float4 v;
             const unsigned a = (unsigned)__cvta_generic_to_shared(
                 &buf[(idx + k * kThreads) & (kThreads * 4 - 1)]);
-            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+            asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                          : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                          : "r"(a));
             acc.x += v.x;

@@ -249,7 +249,7 @@ BpDesc make_bp(const pl_plan *P) {
     bp.block_config = P->block_config;
     bp.tile_px = P->block_config == 4 ? backproject_tc_tile_x() : backproject_tile_x(P->block_config);
     bp.tile_py = P->block_config == 4 ? backproject_tc_tile_y() : backproject_tile_y();
-    bp.bf16 = P->precision == 1;
+    bp.bf16 = P->precision >= 1;
     return bp;
 }
 
@@ -270,7 +270,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     } else if (o.tile_u != 0 && o.tile_u != 8 && o.tile_u != 16 && o.tile_u != 20 && o.tile_u != 24) {
         return fail(PL_ERR_ARG, "tile_u must be 0, 8, 16, 20 or 24");
     }
-    if (o.precision != 0 && o.precision != 1) return fail(PL_ERR_ARG, "precision must be 0 or 1");
+    if (o.precision < 0 || o.precision > 2) return fail(PL_ERR_ARG, "precision must be 0, 1 or 2");
 
     PL_CUDA(cudaGetDevice(&P->device), "cudaGetDevice");
     P->mode = g->mode;
@@ -398,7 +398,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         // tensor-core windows: 16 ks rows from the lowest first tap of each
         // (16 x 8 tile, channel), found by a pass over the tile's pixels;
         // l0 leaves w/2 + 2 rows below the nearest range
-        const int npl = P->precision == 1 ? 2 : 4;
+        const int npl = P->precision >= 1 ? 2 : 4;
         PL_CUDA(dalloc(&P->d_tgeo, (size_t)ntx * nty * P->C, ws), "cudaMalloc");
         int stats[2] = {0, 0}, ks = 0;
         for (int attempt = 0;; ++attempt) {
@@ -464,7 +464,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         const int N = ta.planar ? ta.UT : 2 * ta.UT;
         ta.ncb = (N + 63) / 64;
         ta.n_utiles = (P->Np + ta.UT - 1) / ta.UT;
-        ta.split = P->precision == 1 ? 1 : 3;
+        ta.split = P->precision >= 1 ? 1 : 3;
         const int planes = ta.split == 3 ? 2 : 1, npl = ta.split == 3 ? 4 : 2;
         ta.cb_bytes = (unsigned)(planes * 16 * ta.ks * 128);
         ta.im_off = ta.planar ? (unsigned)ta.ncb * ta.cb_bytes : 0u;
@@ -500,7 +500,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         // proportion to that count); the parts also fill the SMs' last wave
         // better than one block per tile.
         ta.nsplit = ta.planar && P->C >= 2 * ta.npar ? 2 : 1;
-    } else if (backproject_smem_bytes(P->R, P->tile_u, P->C, P->precision, P->block_config) > 200 * 1024)
+    } else if (backproject_smem_bytes(P->R, P->tile_u, P->C, P->precision >= 1, P->block_config) > 200 * 1024)
         return fail(PL_ERR_UNSUPPORTED, "table window too tall for shared memory (grid too coarse)");
     for (int tp = 0; tp < W; ++tp) es_tap_polynomial(W, (double)d.beta, tp, W + 1, P->coef.c[tp]);
 
@@ -561,7 +561,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     if (P->block_config == 4)
         P->table_bytes = (size_t)P->C * 2 * L * d.tc_cols * 2;
     else
-        P->table_bytes = (size_t)P->C * L * ((P->Np + 1) / 2) * (P->precision == 1 ? 8 : 16);
+        P->table_bytes = (size_t)P->C * L * ((P->Np + 1) / 2) * (P->precision >= 1 ? 8 : 16);
     ws += P->table_bytes;
     PL_CUDA(cudaMalloc(&P->d_table, P->table_bytes), "cudaMalloc");
     if (P->block_config == 4) {
@@ -605,6 +605,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         }
         ra.idesc = tc05::idesc_bf16(128, ra.Lh, 0);
         ra.budget = 4ll << 30;
+        ra.a_hi_only = P->precision == 2 ? 1 : 0;
         {
             int dev = 0, sms = 0;
             PL_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
@@ -671,27 +672,36 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
             P->zi_cols = wsplit.cols;
         }
     }
+    // precision 2: the spectrum S is stored in BF16 (the NUFFT paths read
+    // bfloat16 (re, im) pairs; the tensor-core exact-sum table takes the hi
+    // planes of its operand only)
+    d.s_bf16 = (P->precision == 2 && !(P->block_config == 4 && P->rt_tc)) ? 1 : 0;
     PL_CUDA(cudaDeviceSynchronize(), "plan setup");
     return PL_OK;
 }
 
 }  // namespace
 
-static pl_status stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st, bool split) {
+// split: straight into the tensor-core range table's operand; s_bf16: S as
+// bfloat16 (re, im) rows (precision 2 on the NUFFT paths)
+static pl_status stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st, bool split,
+                            int s_bf16) {
+    // precision 2: a BF16 spectrum (the hi planes of the split operand only)
+    const int bf16 = P->precision == 2 ? 1 : 0;
     if (P->fwd_fft && split)      // straight into the tensor-core range table's operand
         PL_CUDA(launch_fft_strided(echo, P->d_S, P->C, P->N, P->M, P->zplan, P->d_twz, -1, 1.0f,
-                                   P->Np, 0, st, P->d_rtA, P->rt.Kp), "zfft");
+                                   P->Np, 0, st, P->d_rtA, P->rt.Kp, nullptr, 0, bf16), "zfft");
     else if (P->fwd_fft)
         PL_CUDA(launch_fft_strided(echo, P->d_S, P->C, P->N, P->M, P->zplan, P->d_twz, -1, 1.0f,
-                                   P->Np, 0, st), "zfft");
-    else
-        PL_CUDA(launch_dft_strided(echo, P->d_S, P->C, P->N, P->M, P->Np, P->d_Tfwd, 1.0f, st),
-                "zdft");
+                                   P->Np, 0, st, nullptr, 0, nullptr, 0, s_bf16), "zfft");
+    else   // the tensor-core table's operand is split from an FP32 S (k_rt_prep)
+        PL_CUDA(launch_dft_strided(echo, P->d_S, P->C, P->N, P->M, P->Np, P->d_Tfwd, 1.0f, st,
+                                   nullptr, s_bf16), "zdft");
     return PL_OK;
 }
 
 pl_status pl_stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st) {
-    return stage_zfft(P, echo, st, P->block_config == 4 && P->rt_tc);
+    return stage_zfft(P, echo, st, P->block_config == 4 && P->rt_tc, P->nd.s_bf16);
 }
 
 pl_status pl_stage_range_table(pl_plan *P, cudaStream_t st) {
@@ -702,7 +712,7 @@ pl_status pl_stage_range_table(pl_plan *P, cudaStream_t st) {
                 "range_table_tc");
         return PL_OK;
     }
-    const int fmt = P->block_config == 4 ? 4 : (P->precision == 1 ? 1 : 0);
+    const int fmt = P->block_config == 4 ? 4 : (P->precision >= 1 ? 1 : 0);
     PL_CUDA(launch_range_table(P->nd, P->fineplan, P->d_S, P->d_alpha, P->d_xg, P->d_dec,
                                P->d_twfine, P->d_table, fmt, st), "range_table");
     return PL_OK;
@@ -1022,7 +1032,8 @@ pl_status pl_execute_exact(pl_plan *plan, const void *echo_dev, void *image_dev,
     pl_status s = prepare_comparison(plan);
     if (s != PL_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    if ((s = stage_zfft(plan, (const float2 *)echo_dev, st, false)) != PL_OK) return s;
+    // the exact sum reads an FP32 spectrum whatever the plan's precision
+    if ((s = stage_zfft(plan, (const float2 *)echo_dev, st, false, 0)) != PL_OK) return s;
     PL_CUDA(launch_exact_sum(plan->exact, plan->d_S, plan->d_kap, plan->d_wum, plan->d_chff,
                              plan->d_G, st),
             "exact_sum");
@@ -1183,7 +1194,7 @@ pl_status pl_plan_get_info(const pl_plan *P, pl_info *info) {
         i.table_layout = P->nd.tc_planar ? 3 : 2;
         i.table_cols = P->nd.tc_cols;
     } else {
-        i.table_layout = P->precision == 1 ? 1 : 0;
+        i.table_layout = P->precision >= 1 ? 1 : 0;
         i.table_cols = 0;
     }
     i.table_exact = (P->block_config == 4 && P->rt_tc) ? 1 : 0;
@@ -1197,7 +1208,7 @@ pl_status pl_plan_workspace(pl_plan *P, int stage, void **dev_ptr, size_t *bytes
     switch (stage) {
         case PL_STAGE_ZFFT:
             *dev_ptr = P->d_S;
-            *bytes = (size_t)P->C * P->Np * P->M * sizeof(float2);
+            *bytes = (size_t)P->C * P->Np * P->M * (P->nd.s_bf16 ? 4 : sizeof(float2));
             return PL_OK;
         case PL_STAGE_RANGE_TABLE:
             *dev_ptr = P->d_table;

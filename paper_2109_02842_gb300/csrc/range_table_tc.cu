@@ -7,7 +7,8 @@
 // interpolation kernel, range-origin phase). For one k_z bin u this is a
 // complex matrix product over the frequencies: channels (M = 128 per block) x
 // table rows (N = L rounded up to 16) x frequencies (K). Operands are BF16
-// split hi + lo (three products per real product), the complex product is
+// split hi + lo (three products per real product; with a BF16 spectrum, two:
+// A hi times E hi and E lo), the complex product is
 // four real ones with the imaginary-by-imaginary term negated through the
 // instruction descriptor, and the two accumulators (Re, Im) live in TMEM.
 //
@@ -80,7 +81,7 @@ __global__ void k_setup_rt_E(NufftDesc d, double dz, const double *k, const doub
 
 // A[u][plane][c][m] = split(S[c][u][m]) (zero for m >= M)
 __global__ void k_rt_prep(const float2 *__restrict__ S, int C, int Np, int M, int Kp,
-                          __nv_bfloat16 *__restrict__ A) {
+                          int hi_only, __nv_bfloat16 *__restrict__ A) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)C * Np * Kp) return;
     const int m = (int)(idx % Kp);
@@ -93,10 +94,10 @@ __global__ void k_rt_prep(const float2 *__restrict__ S, int C, int Np, int M, in
     const size_t base = (size_t)u * 4 * plane + (size_t)c * Kp + m;
     split_bf16(a.x, h, l);
     A[base] = h;
-    A[base + plane] = l;
+    if (!hi_only) A[base + plane] = l;
     split_bf16(a.y, h, l);
     A[base + 2 * plane] = h;
-    A[base + 3 * plane] = l;
+    if (!hi_only) A[base + 3 * plane] = l;
 }
 
 // One block per SM (persistent, 8 warps) walks the work items (128-channel
@@ -134,9 +135,11 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
         int c0, u, h;
         coords(k, c0, u, h);
         unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
-        tc05::mbar_arrive_expect_tx(&bar_tma[b], buf_bytes);
+        // with a BF16 spectrum only A's hi planes (0 and 2) are loaded
+        tc05::mbar_arrive_expect_tx(&bar_tma[b], buf_bytes - (ra.a_hi_only ? 2 * a_tile : 0u));
         for (int p = 0; p < 4; ++p) {
-            tc05::tma_load_3d(As + p * a_tile, &tmA, &bar_tma[b], 0, c0, 4 * u + p);
+            if (!ra.a_hi_only || (p & 1) == 0)
+                tc05::tma_load_3d(As + p * a_tile, &tmA, &bar_tma[b], 0, c0, 4 * u + p);
             tc05::tma_load_3d(Bs + p * b_tile, &tmB, &bar_tma[b], 0, h * ra.Lh, 4 * u + p);
         }
     };
@@ -161,17 +164,17 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
                 // Re += a_r b_r - a_i b_i
                 tc05::mma_ss(dre, da(0), db(0), id, acc);
                 tc05::mma_ss(dre, da(0), db(1), id, 1u);
-                tc05::mma_ss(dre, da(1), db(0), id, 1u);
+                if (!ra.a_hi_only) tc05::mma_ss(dre, da(1), db(0), id, 1u);
                 tc05::mma_ss(dre, da(2), db(2), idn, 1u);
                 tc05::mma_ss(dre, da(2), db(3), idn, 1u);
-                tc05::mma_ss(dre, da(3), db(2), idn, 1u);
+                if (!ra.a_hi_only) tc05::mma_ss(dre, da(3), db(2), idn, 1u);
                 // Im += a_r b_i + a_i b_r
                 tc05::mma_ss(dim, da(0), db(2), id, acc);
                 tc05::mma_ss(dim, da(0), db(3), id, 1u);
-                tc05::mma_ss(dim, da(1), db(2), id, 1u);
+                if (!ra.a_hi_only) tc05::mma_ss(dim, da(1), db(2), id, 1u);
                 tc05::mma_ss(dim, da(2), db(0), id, 1u);
                 tc05::mma_ss(dim, da(2), db(1), id, 1u);
-                tc05::mma_ss(dim, da(3), db(0), id, 1u);
+                if (!ra.a_hi_only) tc05::mma_ss(dim, da(3), db(0), id, 1u);
             }
         } else {
             atomicOr(err, 1);
@@ -352,7 +355,7 @@ cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
     if (!prepared) {     // the z transform wrote S, not the split operand
         const long long n = (long long)ra.C * ra.Np * ra.Kp;
         k_rt_prep<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S, ra.C, ra.Np, ra.M, ra.Kp,
-                                                               (__nv_bfloat16 *)A);
+                                                               ra.a_hi_only, (__nv_bfloat16 *)A);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -39,7 +39,11 @@ __device__ __forceinline__ void rt_block(const NufftDesc &d, const FftPlan &fp,
         float2 a = make_float2(0.f, 0.f);
         float x = 0.f;
         if (u < d.n_pad) {
-            a = cmul(S[((size_t)c * d.n_pad + u) * d.n_f + m], alpha[(size_t)u * d.n_f + m]);
+            const size_t si = ((size_t)c * d.n_pad + u) * d.n_f + m;
+            const float2 sv = d.s_bf16
+                                  ? __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(S)[si])
+                                  : S[si];
+            a = cmul(sv, alpha[(size_t)u * d.n_f + m]);
             x = xg[(size_t)u * d.n_f + m];
         }
         src_a[idx] = a;

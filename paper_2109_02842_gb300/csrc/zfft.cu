@@ -24,12 +24,16 @@ constexpr int kFftIB = 16;        // columns per block (128-byte rows)
 constexpr int kFftThreads = 256;  // threads per block
 
 // in:  [batch][n_in][ld], columns i < I  (rows n >= n_in are zero padding)
-// out: [batch][out_rows][ld], out row r = transform index (r + out_off) mod N;
-// or, with sp.A set, the tensor-core range table's operand instead:
-// A[r][re hi, re lo, im hi, im lo][batch][Kp] = split(X[r][i]) (BF16)
+// out: [batch][out_rows][ld], out row r = transform index (r + out_off) mod N
+// (complex64, or with sp.bf16_rows set bfloat16 (re, im) pairs in the same
+// layout); or, with sp.A set, the tensor-core range table's operand instead:
+// A[r][re hi, re lo, im hi, im lo][batch][Kp] = split(X[r][i]) (BF16; with
+// sp.hi_only only the hi planes are written)
 struct SplitOut {
     __nv_bfloat16 *A;        // nullptr: plain output
     int batch, Kp;
+    int hi_only;             // split output: hi planes only (BF16 spectrum)
+    int bf16_rows;           // plain output as bfloat16 (re, im) pairs
 };
 // PAIRS (I even): every access moves two adjacent columns (16-byte copies,
 // float4 shared-memory accesses, column pairs through the FFT stages).
@@ -100,10 +104,11 @@ k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, flo
                 const __nv_bfloat16 g0 = __float2bfloat16(v0.y), g1 = __float2bfloat16(v1.y);
                 __nv_bfloat16 *o = A + (size_t)r * 4 * plane + 2 * cp;
                 *reinterpret_cast<__nv_bfloat162 *>(o) = __halves2bfloat162(h0, h1);
+                *reinterpret_cast<__nv_bfloat162 *>(o + 2 * plane) = __halves2bfloat162(g0, g1);
+                if (sp.hi_only) return;
                 *reinterpret_cast<__nv_bfloat162 *>(o + plane) = __halves2bfloat162(
                     __float2bfloat16(v0.x - __bfloat162float(h0)),
                     __float2bfloat16(v1.x - __bfloat162float(h1)));
-                *reinterpret_cast<__nv_bfloat162 *>(o + 2 * plane) = __halves2bfloat162(g0, g1);
                 *reinterpret_cast<__nv_bfloat162 *>(o + 3 * plane) = __halves2bfloat162(
                     __float2bfloat16(v0.y - __bfloat162float(g0)),
                     __float2bfloat16(v1.y - __bfloat162float(g1)));
@@ -111,10 +116,18 @@ k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, flo
             stockham_run_pairs_emit<kFftIB>(buf0, buf1, tw, plan, sgn, in2 != nullptr, emit);
         } else {
             float2 *o0 = out + b * out_rows * (size_t)ld + i0;
+            __nv_bfloat162 *ob = reinterpret_cast<__nv_bfloat162 *>(out) + b * out_rows * (size_t)ld + i0;
             auto emit = [&](int t, int cp, float2 x0, float2 x1) {
                 int r = t - out_off;
                 if (r < 0) r += N;
                 if (r >= out_rows || i0 + 2 * cp >= I) return;
+                if (sp.bf16_rows) {
+                    __nv_bfloat162 q[2] = {__floats2bfloat162_rn(scale * x0.x, scale * x0.y),
+                                           __floats2bfloat162_rn(scale * x1.x, scale * x1.y)};
+                    *reinterpret_cast<uint2 *>(ob + (size_t)r * ld + 2 * cp) =
+                        *reinterpret_cast<const uint2 *>(q);
+                    return;
+                }
                 *reinterpret_cast<float4 *>(o0 + (size_t)r * ld + 2 * cp) =
                     make_float4(scale * x0.x, scale * x0.y, scale * x1.x, scale * x1.y);
             };
@@ -144,9 +157,20 @@ k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, flo
             const float2 t = cscale(src[sr * kFftIB + col], scale);
             const __nv_bfloat16 h = __float2bfloat16(t.x), g = __float2bfloat16(t.y);
             o[0] = h;
-            o[plane] = __float2bfloat16(t.x - __bfloat162float(h));
             o[2 * plane] = g;
-            o[3 * plane] = __float2bfloat16(t.y - __bfloat162float(g));
+            if (!sp.hi_only) {
+                o[plane] = __float2bfloat16(t.x - __bfloat162float(h));
+                o[3 * plane] = __float2bfloat16(t.y - __bfloat162float(g));
+            }
+        }
+    } else if (sp.bf16_rows) {
+        __nv_bfloat162 *o = reinterpret_cast<__nv_bfloat162 *>(out) +
+                            (b * out_rows + n_first) * (size_t)ld + i0 + col;
+        for (int r = n_first; r < out_rows; r += RPS, o += (size_t)RPS * ld) {
+            int sr = r + out_off;
+            if (sr >= N) sr -= N;
+            const float2 t = cscale(src[sr * kFftIB + col], scale);
+            *o = __floats2bfloat162_rn(t.x, t.y);
         }
     } else {
         float2 *o = out + (b * out_rows + n_first) * (size_t)ld + i0 + col;
@@ -163,7 +187,8 @@ k_fft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, flo
 // 32 x 32 output tile per block, 256 threads, 4 outputs each.
 __global__ void __launch_bounds__(256)
 k_dft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, float2 *__restrict__ out,
-              int n_in, int I, int out_rows, const float2 *__restrict__ T, float scale) {
+              int n_in, int I, int out_rows, const float2 *__restrict__ T, float scale,
+              int out_bf16) {
     __shared__ float2 xs[32][33];
     __shared__ float2 ts[32][33];
     const int tx = threadIdx.x & 31;
@@ -205,7 +230,13 @@ k_dft_strided(const float2 *__restrict__ in, const float2 *__restrict__ in2, flo
     if (i < I) {
         for (int q = 0; q < 4; ++q) {
             const int r = r0 + ty * 4 + q;
-            if (r < out_rows) out[(b * out_rows + r) * (size_t)I + i] = cscale(acc[q], scale);
+            if (r >= out_rows) continue;
+            const float2 v = cscale(acc[q], scale);
+            const size_t o = (b * out_rows + r) * (size_t)I + i;
+            if (out_bf16)
+                reinterpret_cast<__nv_bfloat162 *>(out)[o] = __floats2bfloat162_rn(v.x, v.y);
+            else
+                out[o] = v;
         }
     }
 }
@@ -217,7 +248,8 @@ size_t fft_strided_smem_bytes(int n) { return (size_t)(2 * n * kFftIB + n) * siz
 cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_in, int I,
                                const FftPlan &plan, const float2 *tw, int sgn, float scale,
                                int out_rows, int out_off, cudaStream_t st,
-                               void *split_A, int split_Kp, const float2 *in2, int ld) {
+                               void *split_A, int split_Kp, const float2 *in2, int ld,
+                               int bf16_out) {
     const size_t smem = fft_strided_smem_bytes(plan.n);
     // column pairs need 16-byte aligned rows: I even, 16-byte aligned
     // buffers, and (split output) an even operand row length
@@ -233,7 +265,9 @@ cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_i
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((I + kFftIB - 1) / kFftIB, batch);
-    const SplitOut sp{(__nv_bfloat16 *)split_A, batch, split_Kp};
+    // bf16_out: with split_A, the hi planes only; else bfloat16 (re, im) rows
+    const SplitOut sp{(__nv_bfloat16 *)split_A, batch, split_Kp, split_A ? bf16_out : 0,
+                      split_A ? 0 : bf16_out};
     kern<<<grid, kFftThreads, smem, st>>>(in, in2, out, n_in, I, ld, plan, tw, sgn, scale, out_rows, out_off,
                                   sp);
     return cudaGetLastError();
@@ -241,8 +275,8 @@ cudaError_t launch_fft_strided(const float2 *in, float2 *out, int batch, int n_i
 
 cudaError_t launch_dft_strided(const float2 *in, float2 *out, int batch, int n_in, int I,
                                int out_rows, const float2 *T, float scale, cudaStream_t st,
-                               const float2 *in2) {
+                               const float2 *in2, int bf16_out) {
     dim3 grid((I + 31) / 32, (out_rows + 31) / 32, batch);
-    k_dft_strided<<<grid, 256, 0, st>>>(in, in2, out, n_in, I, out_rows, T, scale);
+    k_dft_strided<<<grid, 256, 0, st>>>(in, in2, out, n_in, I, out_rows, T, scale, bf16_out);
     return cudaGetLastError();
 }

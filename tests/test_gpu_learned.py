@@ -141,9 +141,9 @@ def test_correction_check_kernel(L):
     img = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
     scale = torch.tensor([2.5], device="cuda")
     out = torch.empty(3, device="cuda")
-    B._check(L.lib().pl_nn_check(L._p(torch.from_numpy(corr).cuda()),
-                                 L._p(torch.from_numpy(img).cuda()), L._p(scale), 2.0, n,
-                                 L._p(out), L._s()))
+    corr_d, img_d = torch.from_numpy(corr).cuda(), torch.from_numpy(img).cuda()
+    B._check(L.lib().pl_nn_check(L._p(corr_d), L._p(img_d), L._p(scale), 2.0, n, L._p(out),
+                                 L._s()))
     got = out.cpu().numpy().astype(np.float64)
     fin = np.isfinite(corr)
     assert got[0] == 2

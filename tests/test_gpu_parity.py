@@ -168,12 +168,29 @@ def test_single_frequency_and_single_scan(binding, bc):
     check("image 1 freq 1 scan", img.reshape(1, -1), image_ref(w, echo), TOL_FP32)
 
 
+@pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("bc", [0, 1])
-def test_bf16_table_variant(binding, bc):
+def test_bf16_table_variant(binding, bc, precision):
+    # precision 1: BF16 table; 2: BF16 table and BF16 spectrum
     w = wl.small_mono(seed=0)
     echo = scene_echo(w)
-    _, img = run_gpu(binding, w, echo, precision=1, block_config=bc)
-    check("image bf16 table", img.reshape(w.grid["nz"], -1), image_ref(w, echo), TOL_BF16)
+    plan, img = run_gpu(binding, w, echo, precision=precision, block_config=bc)
+    assert plan.info["precision"] == precision
+    check("image bf16 precision %d" % precision, img.reshape(w.grid["nz"], -1),
+          image_ref(w, echo), TOL_BF16)
+
+
+@pytest.mark.parametrize("n_pad", [64, 67])
+def test_bf16_spectrum_stage(binding, n_pad):
+    # precision 2 on the FP32 kernels' path: S stored as bfloat16 (re, im)
+    # pairs (64: Stockham FFT; 67: direct DFT), within BF16 rounding of the DFT
+    w = wl.small_mono(seed=0)
+    w.n_pad = n_pad
+    echo = scene_echo(w)
+    plan, _ = run_gpu(binding, w, echo, block_config=1, precision=2)
+    S = plan.workspace(binding.PL_STAGE_ZFFT).float().cpu().numpy()
+    S = S[..., 0] + 1j * S[..., 1]
+    check("S bf16 n_pad=%d" % n_pad, S, oracle.zdft(echo, n_pad), 8e-3)
 
 
 def test_execute_host_matches_device(binding):
@@ -414,19 +431,21 @@ def test_uneven_scene_at_the_edge_of_the_batch_ranges(binding):
     check("image edge scene sampled", got, ref, TOL_FP32)
 
 
+@pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("bc", [4, 1])
-def test_full_size_multistatic_bf16_variants(binding, bc):
-    # precision 1 at the full multistatic size (1024 pairs, 128 scans,
-    # 64 frequencies, 192 x 192 x 128): BF16-only products on the tensor
-    # cores (bc 4), a BF16 table with FP32 arithmetic (bc 1)
+def test_full_size_multistatic_bf16_variants(binding, bc, precision):
+    # the BF16 variants at the full multistatic size (1024 pairs, 128 scans,
+    # 64 frequencies, 192 x 192 x 128): precision 1, BF16-only products on
+    # the tensor cores (bc 4) or a BF16 table with FP32 arithmetic (bc 1);
+    # precision 2, the spectrum in BF16 as well
     w = wl.multi(seed=0)
     echo = scene_echo(w, 0, n_pts=24)
-    plan, img = run_gpu(binding, w, echo, block_config=bc, precision=1)
-    assert plan.info["precision"] == 1 and plan.info["block_config"] == bc
+    plan, img = run_gpu(binding, w, echo, block_config=bc, precision=precision)
+    assert plan.info["precision"] == precision and plan.info["block_config"] == bc
     idx = sampled_columns(w, 48, 1)
     ref = image_ref(w, echo, w.pix_xy()[idx])
     got = img.reshape(w.grid["nz"], -1)[:, idx]
-    check("image multi precision 1 bc %d sampled" % bc, got, ref, TOL_BF16)
+    check("image multi precision %d bc %d sampled" % (precision, bc), got, ref, TOL_BF16)
 
 
 @pytest.mark.parametrize("mode,cross", [(0, False), (1, False), (1, True)])

@@ -147,6 +147,10 @@ CASES = {
     "fp32_table_multi": (small_multi, dict(block_config=1), (0, 0), 1e-4),
     "bf16_table": (lambda: wl.small_mono(seed=1), dict(block_config=1, precision=1), (1, 0),
                    1e-2),
+    "tc_bf16_spectrum": (lambda: wl.small_mono(seed=1), dict(block_config=4, precision=2),
+                         (3, 1), 1e-2),
+    "bf16_table_spectrum": (lambda: wl.small_mono(seed=1), dict(block_config=1, precision=2),
+                            (1, 0), 1e-2),
 }
 
 
@@ -158,11 +162,13 @@ def test_range_table_matches_oracle_profile(binding, case):
     assert (i["table_layout"], i["table_exact"]) == (layout, exact)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_nufft_built_tensor_core_table_above_64_frequencies(binding, mode):
+@pytest.mark.parametrize("mode,precision", [(0, 0), (1, 0), (0, 2)])
+def test_nufft_built_tensor_core_table_above_64_frequencies(binding, mode, precision):
     # more than 64 frequencies: the tensor-core back-projection's table comes
     # from the type-1 NUFFT (spread, FFT, deconvolution), not the exact sums
+    # (precision 2: from a BF16 spectrum)
     w = wl.small_mono(seed=2) if mode == 0 else small_multi()
     w.f_hz = wl.uniform_freqs(28e9, 33e9, 96)
-    i = check_table(binding, w, echo_of(w, 2), 1e-4, block_config=4)
+    i = check_table(binding, w, echo_of(w, 2), 1e-4 if precision == 0 else 1e-2,
+                    block_config=4, precision=precision)
     assert i["table_exact"] == 0 and i["table_layout"] in (2, 3) and i["n_f"] == 96
