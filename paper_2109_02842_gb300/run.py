@@ -4,6 +4,8 @@ captured with.
 
     python -m paper_2109_02842_gb300.run --workload full_mono [--block-config 4]
         [--precision 0] [--tile-u 0] [--repeat 4]
+    python -m paper_2109_02842_gb300.run --workload batch64 [--repeat 2]
+        (the 64 uneven scenes of the batched workload, default batch options)
 """
 from __future__ import annotations
 
@@ -24,6 +26,49 @@ def main(argv=None):
     from . import binding, build, workloads as wl
     build.build()
     binding.load()
+    if a.workload == "batch64-stages":
+        # the 64 scenes one after another through their own plans, with the
+        # per-stage CUDA-event times summed over the scenes
+        tot, rows = {}, []
+        for i in range(64):
+            w = wl.batch_scene(i)
+            e = binding.synth_echo(w.tx_xy, w.rx_xy, w.z0, w.dz, w.n_scan, w.f_hz, w.pts, w.amp)
+            plan = binding.Plan.from_workload(w, block_config=a.block_config,
+                                              precision=a.precision)
+            img = plan.execute(e)
+            plan.set_timing(True)
+            for _ in range(a.repeat):
+                plan.execute(e, img)
+            torch.cuda.synchronize()
+            t = {k: v[0] / max(v[1], 1) for k, v in plan.stage_times().items()}
+            for k, v in t.items():
+                tot[k] = tot.get(k, 0.0) + v
+            inf = plan.info
+            rows.append({"scene": i, "C": w.n_chan, "Np": w.n_pad, "M": w.n_f,
+                         "grid": w.grid["nx"], "exact": inf["table_exact"],
+                         "tile_u": inf["tile_u"], "rows": inf["slab_rows"],
+                         "layout": inf["table_layout"], "zfft_inv": inf["z_transform_fft"],
+                         "ms": t})
+            plan.close()
+        print(json.dumps({"workload": "batch64-stages", "total_ms": tot, "scenes": rows}))
+        return
+    if a.workload == "batch64":
+        scenes = [wl.batch_scene(i) for i in range(64)]
+        echos = [binding.synth_echo(w.tx_xy, w.rx_xy, w.z0, w.dz, w.n_scan, w.f_hz, w.pts, w.amp)
+                 for w in scenes]
+        b = binding.Batch(scenes, block_config=a.block_config, tile_u=a.tile_u,
+                          precision=a.precision)
+        imgs = b.execute(echos)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(max(a.repeat - 1, 0)):
+            b.execute(echos, imgs)
+        ev[1].record()
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": "batch64", "info": b.get_info(),
+                          "ms_per_batch": ev[0].elapsed_time(ev[1]) / max(a.repeat - 1, 1)}))
+        b.close()
+        return
     w = wl.WORKLOADS[a.workload](seed=0)
     echo = binding.synth_echo(w.tx_xy, w.rx_xy, w.z0, w.dz, w.n_scan, w.f_hz, w.pts, w.amp)
     plan = binding.Plan.from_workload(w, block_config=a.block_config, precision=a.precision,
