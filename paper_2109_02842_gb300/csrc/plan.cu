@@ -585,8 +585,9 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         *P->h_err = 0;
         PL_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void **>(&P->d_err), P->h_err, 0),
                 "cudaHostGetDevicePointer");
-        // the range table as exact sums on the tensor cores (one 64-frequency
-        // step: up to 64 frequencies; table rows up to 256), else the NUFFT
+        // the range table as exact sums on the tensor cores (one or two
+        // 64-frequency atoms: up to 128 frequencies; table rows up to 256),
+        // else the NUFFT
         RtTcArgs &ra = P->rt;
         ra.C = P->C;
         ra.Np = P->Np;
@@ -613,7 +614,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
                     "cudaDeviceGetAttribute");
             ra.grid = sms;
         }
-        P->rt_tc = ra.natoms == 1 && ra.Lp <= 256 && 4 * ra.Lh <= 512 &&
+        P->rt_tc = ra.natoms <= 2 && ra.Lp <= 256 && 4 * ra.Lh <= 512 &&
                    range_table_tc_smem_bytes(ra) <= 227 * 1024;
         if (P->rt_tc) {
             const size_t nE = (size_t)P->Np * 4 * ra.Lp * ra.Kp;

@@ -1,5 +1,6 @@
 // Range-profile table of step (8a) / (19a) for the tensor-core back-projection,
-// evaluated as exact sums on the tensor cores instead of a type-1 NUFFT:
+// evaluated as exact sums on the tensor cores instead of a type-1 NUFFT (up to
+// 128 frequencies):
 //
 //   b[c][i][u] = sum_m S[c][u][m] E[u][i][m],   E = alpha e^{+j theta_um (i - L/2)},
 //
@@ -15,7 +16,8 @@
 //   k_rt_prep          S [C][N_p][M] -> A [u][re hi, re lo, im hi, im lo][C][K] BF16
 //   k_range_table_tc   persistent, one block per SM, over the items (128-channel
 //                      block, bin, row part): TMA (128-byte swizzled, K-major) A
-//                      and E tiles, 12 MMAs per 16-frequency step, tcgen05.ld,
+//                      and E tiles, 12 MMAs per 16-frequency step (up to two
+//                      64-frequency atoms per item), tcgen05.ld,
 //                      BF16 hi/lo, stored straight from the registers into
 //                      prod [u][hi, lo][row][Cp] of (re, im) pairs, channels
 //                      innermost (full 128-byte lines). Row parts of Lh rows
@@ -102,10 +104,15 @@ __global__ void k_rt_prep(const float2 *__restrict__ S, int C, int Np, int M, in
 
 // One block per SM (persistent, 8 warps) walks the work items (128-channel
 // block, bin, row part) gridDim.x apart, with two operand buffers and two
-// accumulator pairs: while the warps convert and store item k, the operands
-// of item k + 1 are already in shared memory and its products run on the
-// tensor cores, and the copies of item k + 2 are issued as soon as item k's
-// buffer is free again.
+// accumulator pairs.
+//  * One 64-frequency atom (M <= 64): while the warps convert and store item
+//    k, the operands of item k + 1 are already in shared memory and its
+//    products run on the tensor cores, and the copies of item k + 2 are
+//    issued as soon as item k's buffer is free again.
+//  * Two atoms (64 < M <= 128): an item's two atoms fill the two buffers
+//    (atom a in buffer a, its products accumulated over both); the copies and
+//    products of item k + 1 are issued once item k's products completed, and
+//    overlap item k's conversion and stores.
 __global__ void __launch_bounds__(256, 1)
 k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
                  const __grid_constant__ CUtensorMap tmB, uint32_t *__restrict__ prod, int *err) {
@@ -118,7 +125,8 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t a_tile = 128 * 128;                 // one plane x 64-frequency atom of A
     const uint32_t b_tile = (uint32_t)ra.Lh * 128;     // of E (one row part)
-    const uint32_t buf_bytes = 4 * (a_tile + b_tile);  // one item's operands (natoms == 1)
+    const uint32_t buf_bytes = 4 * (a_tile + b_tile);  // one atom's operands
+    const bool two = ra.natoms == 2;
     const int ncb = (ra.C + 127) / 128;
     const int items = ncb * ra.Np * ra.nh;
     const int nmine = (items - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -131,7 +139,8 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
         u = r % ra.Np;
         h = r / ra.Np;
     };
-    auto issue_tma = [&](int k, int b) {
+    // the copies of atom `at` of item k into buffer b
+    auto issue_tma = [&](int k, int b, int at) {
         int c0, u, h;
         coords(k, c0, u, h);
         unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
@@ -139,48 +148,65 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
         tc05::mbar_arrive_expect_tx(&bar_tma[b], buf_bytes - (ra.a_hi_only ? 2 * a_tile : 0u));
         for (int p = 0; p < 4; ++p) {
             if (!ra.a_hi_only || (p & 1) == 0)
-                tc05::tma_load_3d(As + p * a_tile, &tmA, &bar_tma[b], 0, c0, 4 * u + p);
-            tc05::tma_load_3d(Bs + p * b_tile, &tmB, &bar_tma[b], 0, h * ra.Lh, 4 * u + p);
+                tc05::tma_load_3d(As + p * a_tile, &tmA, &bar_tma[b], 64 * at, c0, 4 * u + p);
+            tc05::tma_load_3d(Bs + p * b_tile, &tmB, &bar_tma[b], 64 * at, h * ra.Lh, 4 * u + p);
         }
     };
-    // the products of the item in buffer b, once its operands landed; the
-    // commit always follows so that the epilogue's wait ends
+    // the products of the atom in buffer b (copies of phase `ph`) into the
+    // accumulator pair `acc_pair`; false if the copies did not land in time
+    auto mma_atom = [&](int b, uint32_t ph, int acc_pair, bool first) -> bool {
+        if (!tc05::mbar_wait(&bar_tma[b], ph, ra.budget)) return false;
+        tc05::fence_after_sync();
+        const unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
+        const uint32_t id = ra.idesc, idn = ra.idesc | (1u << 13);   // negate A
+        const uint32_t dre = tmem_slot + (uint32_t)(acc_pair * 2 * ra.Lh), dim = dre + ra.Lh;
+        for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t ko = ks * 32;
+            auto da = [&](int p) {
+                return tc05::smem_desc_sw128(tc05::smem_addr(As + p * a_tile) + ko, 16, 1024);
+            };
+            auto db = [&](int p) {
+                return tc05::smem_desc_sw128(tc05::smem_addr(Bs + p * b_tile) + ko, 16, 1024);
+            };
+            const uint32_t acc = (!first || ks > 0) ? 1u : 0u;
+            // planes: 0 re hi, 1 re lo, 2 im hi, 3 im lo
+            // Re += a_r b_r - a_i b_i
+            tc05::mma_ss(dre, da(0), db(0), id, acc);
+            tc05::mma_ss(dre, da(0), db(1), id, 1u);
+            if (!ra.a_hi_only) tc05::mma_ss(dre, da(1), db(0), id, 1u);
+            tc05::mma_ss(dre, da(2), db(2), idn, 1u);
+            tc05::mma_ss(dre, da(2), db(3), idn, 1u);
+            if (!ra.a_hi_only) tc05::mma_ss(dre, da(3), db(2), idn, 1u);
+            // Im += a_r b_i + a_i b_r
+            tc05::mma_ss(dim, da(0), db(2), id, acc);
+            tc05::mma_ss(dim, da(0), db(3), id, 1u);
+            if (!ra.a_hi_only) tc05::mma_ss(dim, da(1), db(2), id, 1u);
+            tc05::mma_ss(dim, da(2), db(0), id, 1u);
+            tc05::mma_ss(dim, da(2), db(1), id, 1u);
+            if (!ra.a_hi_only) tc05::mma_ss(dim, da(3), db(0), id, 1u);
+        }
+        return true;
+    };
+    // one atom: the products of the item in buffer b, once its operands
+    // landed; the commit always follows so that the epilogue's wait ends
     auto issue_mma = [&](int k, int b) {
-        if (tc05::mbar_wait(&bar_tma[b], (k >> 1) & 1, ra.budget)) {
-            tc05::fence_after_sync();
-            const unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
-            const uint32_t id = ra.idesc, idn = ra.idesc | (1u << 13);   // negate A
-            const uint32_t dre = tmem_slot + (uint32_t)(b * 2 * ra.Lh), dim = dre + ra.Lh;
-            for (int ks = 0; ks < 4; ++ks) {
-                const uint32_t ko = ks * 32;
-                auto da = [&](int p) {
-                    return tc05::smem_desc_sw128(tc05::smem_addr(As + p * a_tile) + ko, 16, 1024);
-                };
-                auto db = [&](int p) {
-                    return tc05::smem_desc_sw128(tc05::smem_addr(Bs + p * b_tile) + ko, 16, 1024);
-                };
-                const uint32_t acc = ks > 0 ? 1u : 0u;
-                // planes: 0 re hi, 1 re lo, 2 im hi, 3 im lo
-                // Re += a_r b_r - a_i b_i
-                tc05::mma_ss(dre, da(0), db(0), id, acc);
-                tc05::mma_ss(dre, da(0), db(1), id, 1u);
-                if (!ra.a_hi_only) tc05::mma_ss(dre, da(1), db(0), id, 1u);
-                tc05::mma_ss(dre, da(2), db(2), idn, 1u);
-                tc05::mma_ss(dre, da(2), db(3), idn, 1u);
-                if (!ra.a_hi_only) tc05::mma_ss(dre, da(3), db(2), idn, 1u);
-                // Im += a_r b_i + a_i b_r
-                tc05::mma_ss(dim, da(0), db(2), id, acc);
-                tc05::mma_ss(dim, da(0), db(3), id, 1u);
-                if (!ra.a_hi_only) tc05::mma_ss(dim, da(1), db(2), id, 1u);
-                tc05::mma_ss(dim, da(2), db(0), id, 1u);
-                tc05::mma_ss(dim, da(2), db(1), id, 1u);
-                if (!ra.a_hi_only) tc05::mma_ss(dim, da(3), db(0), id, 1u);
-            }
-        } else {
+        if (!mma_atom(b, (k >> 1) & 1, b, true)) {
             atomicOr(err, 1);
             abort_flag = 1;
         }
         tc05::mma_commit(&bar_mma[b]);   // arrives once every issued MMA completed
+    };
+    // two atoms: copies of both (buffers 0 and 1, phase k & 1), the products
+    // into accumulator pair k & 1, one commit
+    auto issue_item2 = [&](int k) {
+        issue_tma(k, 0, 0);
+        issue_tma(k, 1, 1);
+        const uint32_t ph = (uint32_t)k & 1u;
+        if (!mma_atom(0, ph, k & 1, true) || !mma_atom(1, ph, k & 1, false)) {
+            atomicOr(err, 1);
+            abort_flag = 1;
+        }
+        tc05::mma_commit(&bar_mma[k & 1]);
     };
 
     if (threadIdx.x == 0) {
@@ -200,30 +226,46 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
     tc05::fence_after_sync();
     const uint32_t tmem = tmem_slot;
 
-    if (threadIdx.x == 0) {
-        issue_tma(0, 0);
-        if (nmine > 1) issue_tma(1, 1);
-    }
     int pending_tma = -1;      // an item whose copies were issued but not waited for
     if (threadIdx.x == 0) {
-        issue_mma(0, 0);
-        if (abort_flag) pending_tma = 0;
+        if (two) {
+            issue_item2(0);
+            if (abort_flag) pending_tma = 0;
+        } else {
+            issue_tma(0, 0, 0);
+            if (nmine > 1) issue_tma(1, 1, 0);
+            issue_mma(0, 0);
+            if (abort_flag) pending_tma = 0;
+        }
     }
     const int Cp = ncb * 128;                // channel stride of prod
     const int R = ra.nh * ra.Lh;             // rows of prod per (bin, plane)
     for (int k = 0; k < nmine; ++k) {
-        const int b = k & 1;
-        // the next item's products, before this item's epilogue
-        if (threadIdx.x == 0 && k + 1 < nmine) {
-            issue_mma(k + 1, b ^ 1);
-            if (abort_flag) pending_tma = k + 1;
+        const int b = k & 1;                 // accumulator pair (and buffer, one atom)
+        bool done;
+        if (two) {
+            // item k's products done: its buffers are free for item k + 1,
+            // whose copies and products go ahead of item k's epilogue
+            done = tc05::mbar_wait(&bar_mma[b], (k >> 1) & 1, ra.budget);
+            done = __all_sync(0xffffffffu, done);
+            if (threadIdx.x == 0 && done && !abort_flag && k + 1 < nmine) {
+                issue_item2(k + 1);
+                if (abort_flag) pending_tma = k + 1;
+            }
+            __syncwarp();
+        } else {
+            // the next item's products, before this item's epilogue
+            if (threadIdx.x == 0 && k + 1 < nmine) {
+                issue_mma(k + 1, b ^ 1);
+                if (abort_flag) pending_tma = k + 1;
+            }
+            __syncwarp();
+            done = tc05::mbar_wait(&bar_mma[b], (k >> 1) & 1, ra.budget);
+            done = __all_sync(0xffffffffu, done);
+            // this item's operands are consumed: the copies of item k + 2 go
+            // into its buffer now and overlap this epilogue and the next products
+            if (threadIdx.x == 0 && done && !abort_flag && k + 2 < nmine) issue_tma(k + 2, b, 0);
         }
-        __syncwarp();
-        bool done = tc05::mbar_wait(&bar_mma[b], (k >> 1) & 1, ra.budget);
-        done = __all_sync(0xffffffffu, done);
-        // this item's operands are consumed: the copies of item k + 2 go
-        // into its buffer now and overlap this epilogue and the next products
-        if (threadIdx.x == 0 && done && !abort_flag && k + 2 < nmine) issue_tma(k + 2, b);
         int c0, u, h;
         coords(k, c0, u, h);
         // output: each thread (one channel: its TMEM lane) converts 16 rows at
@@ -267,15 +309,22 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
         __syncthreads();
         tc05::fence_after_sync();
         if (abort_flag) {
-            // copies of item k + 2 may have been issued above
-            if (threadIdx.x == 0 && done && k + 2 < nmine && pending_tma < 0) pending_tma = k + 2;
+            // one atom: copies of item k + 2 may have been issued above
+            if (threadIdx.x == 0 && !two && done && k + 2 < nmine && pending_tma < 0)
+                pending_tma = k + 2;
             break;
         }
     }
     // after a timed-out wait: give copies still in flight one more budget
-    // before the shared memory is released
-    if (threadIdx.x == 0 && pending_tma >= 0)
-        tc05::mbar_wait(&bar_tma[pending_tma & 1], (pending_tma >> 1) & 1, ra.budget);
+    // before the shared memory is released (two atoms: both buffers)
+    if (threadIdx.x == 0 && pending_tma >= 0) {
+        if (two) {
+            for (int bb = 0; bb < 2; ++bb)
+                tc05::mbar_wait(&bar_tma[bb], (uint32_t)pending_tma & 1u, ra.budget);
+        } else {
+            tc05::mbar_wait(&bar_tma[pending_tma & 1], (pending_tma >> 1) & 1, ra.budget);
+        }
+    }
     tc05::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc05::tmem_dealloc(tmem, 512);
@@ -333,7 +382,8 @@ k_rt_transpose(const uint32_t *__restrict__ prod, uint32_t *__restrict__ table, 
 }  // namespace
 
 size_t range_table_tc_smem_bytes(const RtTcArgs &ra) {
-    return 1024 + (size_t)2 * 4 * ra.natoms * (128 * 128 + (size_t)ra.Lh * 128);
+    // two operand buffers of one 64-frequency atom each (whatever natoms)
+    return 1024 + (size_t)2 * 4 * (128 * 128 + (size_t)ra.Lh * 128);
 }
 
 cudaError_t launch_setup_rt_E(const NufftDesc &d, double dz, const double *k, const double *kc,
@@ -348,7 +398,7 @@ cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
                                   const CUtensorMap &tmB, const float2 *S,
                                   void *A, void *prod, void *table, int row_words, int planar,
                                   int *err, bool prepared, cudaStream_t st) {
-    if (ra.natoms != 1 || 4 * ra.Lh > 512 || ra.grid < 1 || row_words % 4 != 0 ||
+    if (ra.natoms < 1 || ra.natoms > 2 || 4 * ra.Lh > 512 || ra.grid < 1 || row_words % 4 != 0 ||
         2 * ra.L > 65535)
         return cudaErrorInvalidValue;
     cudaError_t e;

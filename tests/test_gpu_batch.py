@@ -55,12 +55,13 @@ def uneven_scenes():
     w = wl.small_mono(seed=4)
     w.grid = dict(w.grid, nx=17, ny=33, nz=9)
     out.append(w)
-    # more than 64 frequencies: the tensor-core path builds this scene's
-    # table with the NUFFT instead of the exact sums
-    w = wl.small_mono(seed=5)
-    w.f_hz = np.linspace(26e9, 34e9, 80)
-    w.grid = dict(w.grid, nz=16)
-    out.append(w)
+    # more than 64 frequencies: the tensor-core path sums this scene's table
+    # over two 64-frequency atoms; more than 128: it builds it with the NUFFT
+    for seed, n_f in ((5, 80), (6, 136)):
+        w = wl.small_mono(seed=seed)
+        w.f_hz = np.linspace(26e9, 34e9, n_f)
+        w.grid = dict(w.grid, nz=16)
+        out.append(w)
     return out
 
 
@@ -110,7 +111,7 @@ def test_batch_matches_single_scan_path_and_oracle(binding, data, kind):
             assert np.array_equal(imgs[i], single), i
         else:
             assert rel(imgs[i], single) < 1e-6, i
-    for i in (0, 2, 3, 5):
+    for i in (0, 2, 3, 5, 6):
         w = scenes[i]
         ref = oracle.hybrid_exact(w.mode, w.tx_xy, w.rx_xy, echo_np[i], w.z_scan, w.f_hz,
                                   w.n_pad, w.pix_xy(), w.axis("z"))

@@ -403,15 +403,17 @@ def test_tensor_core_variant_full_size_sampled(binding, which):
 
 # --- configurations at the edges of the workloads --------------------------------
 
-def test_tensor_core_96_frequencies_nufft_table(binding):
-    # more than 64 frequencies: the tensor-core back-projection reads a table
-    # built by the type-1 NUFFT (spread, fine FFT, deconvolution)
+@pytest.mark.parametrize("n_f,exact", [(96, 1), (160, 0)])
+def test_tensor_core_many_frequencies(binding, n_f, exact):
+    # 96 frequencies: the exact-sum table over two 64-frequency atoms; 160:
+    # the tensor-core back-projection reads a table built by the type-1 NUFFT
+    # (spread, fine FFT, deconvolution)
     w = wl.small_mono(seed=8)
-    w.f_hz = wl.uniform_freqs(28e9, 33e9, 96)
+    w.f_hz = wl.uniform_freqs(28e9, 33e9, n_f)
     echo = scene_echo(w, 8)
     plan, img = run_gpu(binding, w, echo)
-    assert plan.info["block_config"] == 4 and plan.info["table_exact"] == 0
-    check("image tc 96 freqs", img.reshape(w.grid["nz"], -1), image_ref(w, echo), TOL_FP32)
+    assert plan.info["block_config"] == 4 and plan.info["table_exact"] == exact
+    check("image tc %d freqs" % n_f, img.reshape(w.grid["nz"], -1), image_ref(w, echo), TOL_FP32)
 
 
 def test_uneven_scene_at_the_edge_of_the_batch_ranges(binding):

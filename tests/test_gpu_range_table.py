@@ -9,7 +9,8 @@ q_{c,u}(l) = sum_m S k_m e^{j (kappa - kappa_0) l} up to the change of
 reference from kappa_0 = kappa(k_0, k_z) to the band centre kappa_c:
     sum_i ES(...) b_i(u) = q_{c,u}(l) e^{j (kappa_0 - kappa_c) l}.
 Every table format is covered: exact sums on the tensor cores (planar and
-interleaved), the NUFFT-built tensor-core table (more than 64 frequencies),
+interleaved; one and two 64-frequency atoms), the NUFFT-built tensor-core
+table (more than 128 frequencies),
 the FP32 kernels' float32 and bfloat16 tables, monostatic and multistatic.
 The spectrum S fed to the oracle is its own FP64 z-DFT of the same echo.
 """
@@ -163,12 +164,23 @@ def test_range_table_matches_oracle_profile(binding, case):
 
 
 @pytest.mark.parametrize("mode,precision", [(0, 0), (1, 0), (0, 2)])
-def test_nufft_built_tensor_core_table_above_64_frequencies(binding, mode, precision):
-    # more than 64 frequencies: the tensor-core back-projection's table comes
-    # from the type-1 NUFFT (spread, FFT, deconvolution), not the exact sums
-    # (precision 2: from a BF16 spectrum)
+def test_two_atom_exact_table(binding, mode, precision):
+    # 65 to 128 frequencies: the exact sums over two 64-frequency atoms
+    # accumulated in tensor memory (precision 2: the spectrum's BF16 part)
     w = wl.small_mono(seed=2) if mode == 0 else small_multi()
     w.f_hz = wl.uniform_freqs(28e9, 33e9, 96)
     i = check_table(binding, w, echo_of(w, 2), 1e-4 if precision == 0 else 1e-2,
                     block_config=4, precision=precision)
-    assert i["table_exact"] == 0 and i["table_layout"] in (2, 3) and i["n_f"] == 96
+    assert i["table_exact"] == 1 and i["table_layout"] in (2, 3) and i["n_f"] == 96
+
+
+@pytest.mark.parametrize("mode,precision", [(0, 0), (1, 0), (0, 2)])
+def test_nufft_built_tensor_core_table_above_128_frequencies(binding, mode, precision):
+    # more than 128 frequencies: the tensor-core back-projection's table comes
+    # from the type-1 NUFFT (spread, FFT, deconvolution), not the exact sums
+    # (precision 2: from a BF16 spectrum)
+    w = wl.small_mono(seed=2) if mode == 0 else small_multi()
+    w.f_hz = wl.uniform_freqs(28e9, 33e9, 160)
+    i = check_table(binding, w, echo_of(w, 2), 1e-4 if precision == 0 else 1e-2,
+                    block_config=4, precision=precision)
+    assert i["table_exact"] == 0 and i["table_layout"] in (2, 3) and i["n_f"] == 160
