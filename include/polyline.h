@@ -193,6 +193,17 @@ enum {
     PL_STAGE_ZIFFT = 3,       /* Eq. (9): inverse transform over k_z */
     PL_NUM_STAGES = 4
 };
+/* Further workspace identifiers for pl_plan_workspace (inspection only) of a
+ * plan whose range table is evaluated as exact sums on the tensor cores
+ * (pl_info.table_exact = 1), with Kp = n_f rounded up to 64 and Lp =
+ * table_len rounded up to 16, all bfloat16:
+ *  PL_WS_RT_OPERAND_A -> the spectrum operand [n_pad][re hi, re lo, im hi,
+ *                        im lo][n_chan][Kp], S split as hi = BF16(S),
+ *                        lo = BF16(S - hi) (lo planes unused with precision 2)
+ *  PL_WS_RT_OPERAND_E -> the plan-time factor [n_pad][re hi, re lo, im hi,
+ *                        im lo][Lp][Kp], E[u][i][m] = alpha_um
+ *                        e^{j theta_um (i - L/2)}, b[c][i][u] = sum_m S E */
+enum { PL_WS_RT_OPERAND_A = 16, PL_WS_RT_OPERAND_E = 17 };
 
 /* Create a plan: validates the inputs, allocates device workspace on the
  * current device and precomputes the per-(k_z, f) tables on the GPU.

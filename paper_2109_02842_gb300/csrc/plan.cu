@@ -1215,6 +1215,17 @@ pl_status pl_plan_workspace(pl_plan *P, int stage, void **dev_ptr, size_t *bytes
             *dev_ptr = P->d_table;
             *bytes = P->table_bytes;
             return PL_OK;
+        case PL_WS_RT_OPERAND_A:
+        case PL_WS_RT_OPERAND_E:
+            if (!(P->block_config == 4 && P->rt_tc)) break;
+            if (stage == PL_WS_RT_OPERAND_A) {
+                *dev_ptr = P->d_rtA;
+                *bytes = (size_t)P->Np * 4 * P->C * P->rt.Kp * 2;
+            } else {
+                *dev_ptr = P->d_rtE;
+                *bytes = (size_t)P->Np * 4 * P->rt.Lp * P->rt.Kp * 2;
+            }
+            return PL_OK;
         case PL_STAGE_BACKPROJECT:
             *dev_ptr = P->d_G;
             *bytes = (size_t)(P->block_config == 4 ? P->tc.nsplit : 1) * P->Np * P->grid.nx *

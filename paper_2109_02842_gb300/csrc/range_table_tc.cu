@@ -103,16 +103,14 @@ __global__ void k_rt_prep(const float2 *__restrict__ S, int C, int Np, int M, in
 }
 
 // One block per SM (persistent, 8 warps) walks the work items (128-channel
-// block, bin, row part) gridDim.x apart, with two operand buffers and two
-// accumulator pairs.
-//  * One 64-frequency atom (M <= 64): while the warps convert and store item
-//    k, the operands of item k + 1 are already in shared memory and its
-//    products run on the tensor cores, and the copies of item k + 2 are
-//    issued as soon as item k's buffer is free again.
-//  * Two atoms (64 < M <= 128): an item's two atoms fill the two buffers
-//    (atom a in buffer a, its products accumulated over both); the copies and
-//    products of item k + 1 are issued once item k's products completed, and
-//    overlap item k's conversion and stores.
+// block, bin, row part) gridDim.x apart as a pipeline of stages, one stage
+// per 64-frequency atom of an item (natoms = 1 or 2): stage s is atom
+// s % natoms of the block's item s / natoms, its operands go to buffer s & 1,
+// its products accumulate into the item's accumulator pair (item & 1). While
+// the warps convert and store item k (after its last stage), the operands of
+// the next stage are already in shared memory and its products run on the
+// tensor cores, and the copies of the stage after it are issued as soon as
+// their buffer is free again.
 __global__ void __launch_bounds__(256, 1)
 k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
                  const __grid_constant__ CUtensorMap tmB, uint32_t *__restrict__ prod, int *err) {
@@ -125,11 +123,12 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t a_tile = 128 * 128;                 // one plane x 64-frequency atom of A
     const uint32_t b_tile = (uint32_t)ra.Lh * 128;     // of E (one row part)
-    const uint32_t buf_bytes = 4 * (a_tile + b_tile);  // one atom's operands
-    const bool two = ra.natoms == 2;
+    const uint32_t buf_bytes = 4 * (a_tile + b_tile);  // one stage's operands
+    const int NA = ra.natoms;
     const int ncb = (ra.C + 127) / 128;
     const int items = ncb * ra.Np * ra.nh;
     const int nmine = (items - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int nstages = nmine * NA;
     // item -> (first channel, bin, row part); channel blocks vary fastest so
     // the blocks running together share each bin's E tile in L2
     auto coords = [&](int k, int &c0, int &u, int &h) {
@@ -139,10 +138,11 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
         u = r % ra.Np;
         h = r / ra.Np;
     };
-    // the copies of atom `at` of item k into buffer b
-    auto issue_tma = [&](int k, int b, int at) {
+    // the copies of stage st into buffer st & 1
+    auto issue_tma = [&](int st) {
         int c0, u, h;
-        coords(k, c0, u, h);
+        coords(st / NA, c0, u, h);
+        const int at = st % NA, b = st & 1;
         unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
         // with a BF16 spectrum only A's hi planes (0 and 2) are loaded
         tc05::mbar_arrive_expect_tx(&bar_tma[b], buf_bytes - (ra.a_hi_only ? 2 * a_tile : 0u));
@@ -152,61 +152,46 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
             tc05::tma_load_3d(Bs + p * b_tile, &tmB, &bar_tma[b], 64 * at, h * ra.Lh, 4 * u + p);
         }
     };
-    // the products of the atom in buffer b (copies of phase `ph`) into the
-    // accumulator pair `acc_pair`; false if the copies did not land in time
-    auto mma_atom = [&](int b, uint32_t ph, int acc_pair, bool first) -> bool {
-        if (!tc05::mbar_wait(&bar_tma[b], ph, ra.budget)) return false;
-        tc05::fence_after_sync();
-        const unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
-        const uint32_t id = ra.idesc, idn = ra.idesc | (1u << 13);   // negate A
-        const uint32_t dre = tmem_slot + (uint32_t)(acc_pair * 2 * ra.Lh), dim = dre + ra.Lh;
-        for (int ks = 0; ks < 4; ++ks) {
-            const uint32_t ko = ks * 32;
-            auto da = [&](int p) {
-                return tc05::smem_desc_sw128(tc05::smem_addr(As + p * a_tile) + ko, 16, 1024);
-            };
-            auto db = [&](int p) {
-                return tc05::smem_desc_sw128(tc05::smem_addr(Bs + p * b_tile) + ko, 16, 1024);
-            };
-            const uint32_t acc = (!first || ks > 0) ? 1u : 0u;
-            // planes: 0 re hi, 1 re lo, 2 im hi, 3 im lo
-            // Re += a_r b_r - a_i b_i
-            tc05::mma_ss(dre, da(0), db(0), id, acc);
-            tc05::mma_ss(dre, da(0), db(1), id, 1u);
-            if (!ra.a_hi_only) tc05::mma_ss(dre, da(1), db(0), id, 1u);
-            tc05::mma_ss(dre, da(2), db(2), idn, 1u);
-            tc05::mma_ss(dre, da(2), db(3), idn, 1u);
-            if (!ra.a_hi_only) tc05::mma_ss(dre, da(3), db(2), idn, 1u);
-            // Im += a_r b_i + a_i b_r
-            tc05::mma_ss(dim, da(0), db(2), id, acc);
-            tc05::mma_ss(dim, da(0), db(3), id, 1u);
-            if (!ra.a_hi_only) tc05::mma_ss(dim, da(1), db(2), id, 1u);
-            tc05::mma_ss(dim, da(2), db(0), id, 1u);
-            tc05::mma_ss(dim, da(2), db(1), id, 1u);
-            if (!ra.a_hi_only) tc05::mma_ss(dim, da(3), db(0), id, 1u);
-        }
-        return true;
-    };
-    // one atom: the products of the item in buffer b, once its operands
-    // landed; the commit always follows so that the epilogue's wait ends
-    auto issue_mma = [&](int k, int b) {
-        if (!mma_atom(b, (k >> 1) & 1, b, true)) {
+    // the products of stage st, once its operands landed, into the
+    // accumulator pair of its item (overwriting at the item's first atom);
+    // the commit always follows so that the waits on bar_mma end
+    auto issue_mma = [&](int st) {
+        const int b = st & 1, k = st / NA, at = st % NA;
+        if (tc05::mbar_wait(&bar_tma[b], (st >> 1) & 1, ra.budget)) {
+            tc05::fence_after_sync();
+            const unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
+            const uint32_t id = ra.idesc, idn = ra.idesc | (1u << 13);   // negate A
+            const uint32_t dre = tmem_slot + (uint32_t)((k & 1) * 2 * ra.Lh), dim = dre + ra.Lh;
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint32_t ko = ks * 32;
+                auto da = [&](int p) {
+                    return tc05::smem_desc_sw128(tc05::smem_addr(As + p * a_tile) + ko, 16, 1024);
+                };
+                auto db = [&](int p) {
+                    return tc05::smem_desc_sw128(tc05::smem_addr(Bs + p * b_tile) + ko, 16, 1024);
+                };
+                const uint32_t acc = (at > 0 || ks > 0) ? 1u : 0u;
+                // planes: 0 re hi, 1 re lo, 2 im hi, 3 im lo
+                // Re += a_r b_r - a_i b_i
+                tc05::mma_ss(dre, da(0), db(0), id, acc);
+                tc05::mma_ss(dre, da(0), db(1), id, 1u);
+                if (!ra.a_hi_only) tc05::mma_ss(dre, da(1), db(0), id, 1u);
+                tc05::mma_ss(dre, da(2), db(2), idn, 1u);
+                tc05::mma_ss(dre, da(2), db(3), idn, 1u);
+                if (!ra.a_hi_only) tc05::mma_ss(dre, da(3), db(2), idn, 1u);
+                // Im += a_r b_i + a_i b_r
+                tc05::mma_ss(dim, da(0), db(2), id, acc);
+                tc05::mma_ss(dim, da(0), db(3), id, 1u);
+                if (!ra.a_hi_only) tc05::mma_ss(dim, da(1), db(2), id, 1u);
+                tc05::mma_ss(dim, da(2), db(0), id, 1u);
+                tc05::mma_ss(dim, da(2), db(1), id, 1u);
+                if (!ra.a_hi_only) tc05::mma_ss(dim, da(3), db(0), id, 1u);
+            }
+        } else {
             atomicOr(err, 1);
             abort_flag = 1;
         }
         tc05::mma_commit(&bar_mma[b]);   // arrives once every issued MMA completed
-    };
-    // two atoms: copies of both (buffers 0 and 1, phase k & 1), the products
-    // into accumulator pair k & 1, one commit
-    auto issue_item2 = [&](int k) {
-        issue_tma(k, 0, 0);
-        issue_tma(k, 1, 1);
-        const uint32_t ph = (uint32_t)k & 1u;
-        if (!mma_atom(0, ph, k & 1, true) || !mma_atom(1, ph, k & 1, false)) {
-            atomicOr(err, 1);
-            abort_flag = 1;
-        }
-        tc05::mma_commit(&bar_mma[k & 1]);
     };
 
     if (threadIdx.x == 0) {
@@ -226,59 +211,45 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
     tc05::fence_after_sync();
     const uint32_t tmem = tmem_slot;
 
-    int pending_tma = -1;      // an item whose copies were issued but not waited for
     if (threadIdx.x == 0) {
-        if (two) {
-            issue_item2(0);
-            if (abort_flag) pending_tma = 0;
-        } else {
-            issue_tma(0, 0, 0);
-            if (nmine > 1) issue_tma(1, 1, 0);
-            issue_mma(0, 0);
-            if (abort_flag) pending_tma = 0;
-        }
+        issue_tma(0);
+        if (nstages > 1) issue_tma(1);
+    }
+    int pending_tma = -1;      // a stage whose copies were issued but not waited for
+    if (threadIdx.x == 0) {
+        issue_mma(0);
+        if (abort_flag) pending_tma = 0;
     }
     const int Cp = ncb * 128;                // channel stride of prod
     const int R = ra.nh * ra.Lh;             // rows of prod per (bin, plane)
-    for (int k = 0; k < nmine; ++k) {
-        const int b = k & 1;                 // accumulator pair (and buffer, one atom)
-        bool done;
-        if (two) {
-            // item k's products done: its buffers are free for item k + 1,
-            // whose copies and products go ahead of item k's epilogue
-            done = tc05::mbar_wait(&bar_mma[b], (k >> 1) & 1, ra.budget);
-            done = __all_sync(0xffffffffu, done);
-            if (threadIdx.x == 0 && done && !abort_flag && k + 1 < nmine) {
-                issue_item2(k + 1);
-                if (abort_flag) pending_tma = k + 1;
-            }
-            __syncwarp();
-        } else {
-            // the next item's products, before this item's epilogue
-            if (threadIdx.x == 0 && k + 1 < nmine) {
-                issue_mma(k + 1, b ^ 1);
-                if (abort_flag) pending_tma = k + 1;
-            }
-            __syncwarp();
-            done = tc05::mbar_wait(&bar_mma[b], (k >> 1) & 1, ra.budget);
-            done = __all_sync(0xffffffffu, done);
-            // this item's operands are consumed: the copies of item k + 2 go
-            // into its buffer now and overlap this epilogue and the next products
-            if (threadIdx.x == 0 && done && !abort_flag && k + 2 < nmine) issue_tma(k + 2, b, 0);
+    for (int st = 0; st < nstages; ++st) {
+        const int b = st & 1;
+        const int k = st / NA;
+        // the next stage's products, before this stage's completion and
+        // (at an item's last stage) its epilogue
+        if (threadIdx.x == 0 && st + 1 < nstages) {
+            issue_mma(st + 1);
+            if (abort_flag && pending_tma < 0) pending_tma = st + 1;
         }
-        int c0, u, h;
-        coords(k, c0, u, h);
-        // output: each thread (one channel: its TMEM lane) converts 16 rows at
-        // a time to BF16 hi/lo (re, im) pairs and stores them into
-        // prod [u][hi, lo][row][Cp], channels innermost, so each store
-        // instruction of a warp writes 32 consecutive channels (a full
-        // 128-byte line). Warps 0-3 and 4-7 take alternate 16-row chunks of
-        // their TMEM lane quarter.
-        const int rows_here = min(ra.Lh, ra.L - h * ra.Lh);     // table rows of this part
-        if (done) {
+        __syncwarp();
+        bool done = tc05::mbar_wait(&bar_mma[b], (st >> 1) & 1, ra.budget);
+        done = __all_sync(0xffffffffu, done);
+        // this stage's operands are consumed: the copies of stage st + 2 go
+        // into its buffer now and overlap the next products and the epilogue
+        if (threadIdx.x == 0 && done && !abort_flag && st + 2 < nstages) issue_tma(st + 2);
+        if (done && st % NA == NA - 1) {
+            int c0, u, h;
+            coords(k, c0, u, h);
+            // output: each thread (one channel: its TMEM lane) converts 16
+            // rows at a time to BF16 hi/lo (re, im) pairs and stores them
+            // into prod [u][hi, lo][row][Cp], channels innermost, so each
+            // store instruction of a warp writes 32 consecutive channels (a
+            // full 128-byte line). Warps 0-3 and 4-7 take alternate 16-row
+            // chunks of their TMEM lane quarter.
+            const int rows_here = min(ra.Lh, ra.L - h * ra.Lh);     // table rows of this part
             tc05::fence_after_sync();
             const int q = warp & 3;
-            const uint32_t lane_base = tmem + (uint32_t)(b * 2 * ra.Lh) + ((uint32_t)(32 * q) << 16);
+            const uint32_t lane_base = tmem + (uint32_t)((k & 1) * 2 * ra.Lh) + ((uint32_t)(32 * q) << 16);
             const int c = c0 + 32 * q + lane;
             uint32_t *g_hi = prod + ((size_t)(2 * u + 0) * R + h * ra.Lh) * Cp + c;
             uint32_t *g_lo = prod + ((size_t)(2 * u + 1) * R + h * ra.Lh) * Cp + c;
@@ -300,7 +271,7 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
                     }
                 }
             }
-        } else {
+        } else if (!done) {
             if (lane == 0) atomicOr(err, 2);
             abort_flag = 1;
         }
@@ -309,22 +280,16 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
         __syncthreads();
         tc05::fence_after_sync();
         if (abort_flag) {
-            // one atom: copies of item k + 2 may have been issued above
-            if (threadIdx.x == 0 && !two && done && k + 2 < nmine && pending_tma < 0)
-                pending_tma = k + 2;
+            // copies of stage st + 2 may have been issued above
+            if (threadIdx.x == 0 && done && st + 2 < nstages && pending_tma < 0)
+                pending_tma = st + 2;
             break;
         }
     }
     // after a timed-out wait: give copies still in flight one more budget
-    // before the shared memory is released (two atoms: both buffers)
-    if (threadIdx.x == 0 && pending_tma >= 0) {
-        if (two) {
-            for (int bb = 0; bb < 2; ++bb)
-                tc05::mbar_wait(&bar_tma[bb], (uint32_t)pending_tma & 1u, ra.budget);
-        } else {
-            tc05::mbar_wait(&bar_tma[pending_tma & 1], (pending_tma >> 1) & 1, ra.budget);
-        }
-    }
+    // before the shared memory is released
+    if (threadIdx.x == 0 && pending_tma >= 0)
+        tc05::mbar_wait(&bar_tma[pending_tma & 1], (pending_tma >> 1) & 1, ra.budget);
     tc05::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc05::tmem_dealloc(tmem, 512);
