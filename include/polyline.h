@@ -133,7 +133,16 @@ typedef struct {
     int nufft_w;
     int tile_u;
     int block_config;
-    int reserved[7];
+    /* Bounded waits of the tensor-core kernels (block_config 4):
+     * wait_timeout_us = how long one wait may last before it gives up
+     * (0 = about 2 s); debug_unsatisfiable (a test hook) = 1 makes the
+     * back-projection's MMA warp, 2 the range-table kernel's first stage,
+     * wait first on a barrier nothing completes, so that the wait runs out
+     * and the kernel takes its exit path (the next pl_execute returns
+     * PL_ERR_TIMEOUT; no device fault, the context stays usable). */
+    int debug_unsatisfiable;
+    int wait_timeout_us;
+    int reserved[5];
 } pl_options;
 
 typedef struct pl_plan pl_plan;

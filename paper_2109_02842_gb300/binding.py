@@ -43,7 +43,8 @@ class PlGrid(ctypes.Structure):
 
 class PlOptions(ctypes.Structure):
     _fields_ = [("precision", _I), ("nufft_sigma", _D), ("nufft_w", _I), ("tile_u", _I),
-                ("block_config", _I), ("reserved", _I * 7)]
+                ("block_config", _I), ("debug_unsatisfiable", _I), ("wait_timeout_us", _I),
+                ("reserved", _I * 5)]
 
 
 class PlInfo(ctypes.Structure):
@@ -182,7 +183,7 @@ class _DevArray:
 
 def _descriptors(keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad, pair_tx,
                  pair_rx, radius, n_sections, chord_len, elem_section, precision, nufft_sigma,
-                 nufft_w, tile_u, block_config):
+                 nufft_w, tile_u, block_config, debug_unsatisfiable=0, wait_timeout_us=0):
     exy = _f64(elem_xy).reshape(-1, 2)
     sec = None if elem_section is None else _i32(elem_section)
     ptx = None if pair_tx is None else _i32(pair_tx)
@@ -198,7 +199,7 @@ def _descriptors(keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pa
                float(grid["z0"]), float(grid["dz"]), int(grid["nx"]), int(grid["ny"]),
                int(grid["nz"]))
     opt = PlOptions(int(precision), float(nufft_sigma), int(nufft_w), int(tile_u),
-                    int(block_config))
+                    int(block_config), int(debug_unsatisfiable), int(wait_timeout_us))
     return geom, scan, freqs, g, opt
 
 
@@ -214,13 +215,13 @@ class Plan:
     def __init__(self, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad=0,
                  pair_tx=None, pair_rx=None, radius=0.0, n_sections=0, chord_len=0.0,
                  elem_section=None, precision=0, nufft_sigma=0.0, nufft_w=0, tile_u=0,
-                 block_config=0):
+                 block_config=0, debug_unsatisfiable=0, wait_timeout_us=0):
         lib = load()
         self._keep = []
         geom, scan, freqs, g, opt = _descriptors(
             self._keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad, pair_tx,
             pair_rx, radius, n_sections, chord_len, elem_section, precision, nufft_sigma,
-            nufft_w, tile_u, block_config)
+            nufft_w, tile_u, block_config, debug_unsatisfiable, wait_timeout_us)
         h = _P()
         _check(lib.pl_plan_create(ctypes.byref(h), geom, scan, freqs, g, opt))
         self._h = h

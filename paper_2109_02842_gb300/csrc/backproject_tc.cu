@@ -52,7 +52,9 @@
 //
 // Every wait is bounded (a clock budget); a wait that runs out sets a bit in
 // *err, the block skips the rest of its work and still waits (bounded) for
-// its own copies and products before releasing tensor memory.
+// its own copies and products before releasing tensor memory. (ta.dbg_wait
+// makes the MMA warp wait first on a barrier nothing completes, so that
+// tests can run these exit paths.)
 #include <cuda_bf16.h>
 
 #include "bp_body.cuh"
@@ -135,8 +137,10 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
     const int cb = part * cper, ce = min(C, cb + cper);
     const TileGeo *tg = tgeo + (size_t)tile * C;
     const long long budget = ta.budget;
+    __shared__ __align__(8) uint64_t dbg_bar;    // test hook: never completed
 
     if (threadIdx.x == 0) {
+        tc05::mbar_init(&dbg_bar, 1);
         for (int s = 0; s < NSG; ++s) {
             tc05::mbar_init(&b_full[s], 1);
             tc05::mbar_init(&done[s], 1);
@@ -318,6 +322,7 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
         const uint32_t im16 = ta.im_off >> 4;              // Im B columns (planar)
         const uint32_t idn = ta.idesc | (1u << 13);        // negated A
         bool ok = true;
+        if (ta.dbg_wait) ok = __all_sync(0xffffffffu, tc05::mbar_wait(&dbg_bar, 0, budget));
         int sg = 0;
         uint32_t bpar = 0;
         for (int g = 0; g < n_groups && ok; ++g) {

@@ -113,6 +113,8 @@ struct TcArgs {
     int cpr;             // channels per class round (1, or 2 with npar 3): A buffers of cpr
                          // channels, one A-ready wait and one release per round
     long long budget;    // wait budget, SM clock cycles
+    int dbg_wait;        // test hook: the MMA warp first waits on a barrier nothing
+                         // completes, so the bounded-wait exit paths run
     int blk0, nblk;      // the launch's blocks: linear indices [blk0, blk0 + nblk) of
                          // (tile x, tile y, bin block x part), x fastest; nblk 0: to the end
 };
@@ -143,6 +145,8 @@ struct RtTcArgs {
     int grid;            // persistent blocks (one per SM)
     int a_hi_only;       // 1: the spectrum operand is BF16 (hi planes only): 8 products
                          // per K step instead of 12
+    int dbg_wait;        // test hook: the first stage's operand wait is replaced by a
+                         // wait on a barrier nothing completes
 };
 size_t range_table_tc_smem_bytes(const RtTcArgs &ra);
 // E [N_p][re hi, re lo, im hi, im lo][Lp][Kp] BF16: alpha_um e^{+j theta_um (i - L/2)}

@@ -178,6 +178,17 @@ void rect_dist(double px, double py, double x0, double x1, double y0, double y1,
         for (double yy : ys) dmax = std::max(dmax, std::hypot(px - xx, py - yy));
 }
 
+// SM clock cycles of a bounded device-side wait: about 2 s by default, else
+// the requested microseconds at the device's clock rate.
+long long wait_budget_cycles(int us) {
+    if (us <= 0) return 4ll << 30;
+    int dev = 0, khz = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0)
+        khz = 2000000;
+    return (long long)us * khz / 1000;
+}
+
 template <typename T>
 cudaError_t dalloc(T **p, size_t count, size_t &total) {
     total += count * sizeof(T);
@@ -271,6 +282,8 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         return fail(PL_ERR_ARG, "tile_u must be 0, 8, 16, 20 or 24");
     }
     if (o.precision < 0 || o.precision > 2) return fail(PL_ERR_ARG, "precision must be 0, 1 or 2");
+    if (o.debug_unsatisfiable < 0 || o.debug_unsatisfiable > 2 || o.wait_timeout_us < 0)
+        return fail(PL_ERR_ARG, "debug_unsatisfiable must be 0..2, wait_timeout_us >= 0");
 
     PL_CUDA(cudaGetDevice(&P->device), "cudaGetDevice");
     P->mode = g->mode;
@@ -490,7 +503,8 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         if (backproject_tc_smem_bytes(ta) > 227 * 1024)
             return fail(PL_ERR_UNSUPPORTED, "table window slots exceed shared memory");
         ta.idesc = tc05::idesc_bf16(128, N, 1);
-        ta.budget = 4ll << 30;
+        ta.budget = wait_budget_cycles(o.wait_timeout_us);
+        ta.dbg_wait = o.debug_unsatisfiable == 1 ? 1 : 0;
         d.tc_cols = ta.planar ? 2 * ta.UT : 2 * ta.n_utiles * ta.UT;
         d.tc_planar = ta.planar;
         // planar: two channel parts per tile. Each accumulator then takes as
@@ -605,7 +619,8 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
                 break;
         }
         ra.idesc = tc05::idesc_bf16(128, ra.Lh, 0);
-        ra.budget = 4ll << 30;
+        ra.budget = wait_budget_cycles(o.wait_timeout_us);
+        ra.dbg_wait = o.debug_unsatisfiable == 2 ? 1 : 0;
         ra.a_hi_only = P->precision == 2 ? 1 : 0;
         {
             int dev = 0, sms = 0;
@@ -1017,7 +1032,8 @@ static pl_status take_device_timeout(pl_plan *plan) {
     const int bits = *(volatile int *)plan->h_err;
     *(volatile int *)plan->h_err = 0;
     char msg[96];
-    std::snprintf(msg, sizeof msg, "back-projection wait timed out (flags 0x%x)", bits);
+    std::snprintf(msg, sizeof msg,
+                  "a bounded wait of the tensor-core kernels timed out (flags 0x%x)", bits);
     return fail(PL_ERR_TIMEOUT, msg);
 }
 

@@ -117,13 +117,14 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t bar_tma[2], bar_mma[2];
+    __shared__ __align__(8) uint64_t bar_tma[2], bar_mma[2], dbg_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t a_tile = 128 * 128;                 // one plane x 64-frequency atom of A
     const uint32_t b_tile = (uint32_t)ra.Lh * 128;     // of E (one row part)
     const uint32_t buf_bytes = 4 * (a_tile + b_tile);  // one stage's operands
+    int n_tma = 0, n_mma = 0;    // stages whose copies / products thread 0 issued
     const int NA = ra.natoms;
     const int ncb = (ra.C + 127) / 128;
     const int items = ncb * ra.Np * ra.nh;
@@ -144,6 +145,7 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
         coords(st / NA, c0, u, h);
         const int at = st % NA, b = st & 1;
         unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
+        n_tma = st + 1;
         // with a BF16 spectrum only A's hi planes (0 and 2) are loaded
         tc05::mbar_arrive_expect_tx(&bar_tma[b], buf_bytes - (ra.a_hi_only ? 2 * a_tile : 0u));
         for (int p = 0; p < 4; ++p) {
@@ -157,7 +159,11 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
     // the commit always follows so that the waits on bar_mma end
     auto issue_mma = [&](int st) {
         const int b = st & 1, k = st / NA, at = st % NA;
-        if (tc05::mbar_wait(&bar_tma[b], (st >> 1) & 1, ra.budget)) {
+        // (test hook: the first stage waits on a barrier nothing completes)
+        const bool landed = (ra.dbg_wait && st == 0)
+                                ? tc05::mbar_wait(&dbg_bar, 0, ra.budget)
+                                : tc05::mbar_wait(&bar_tma[b], (st >> 1) & 1, ra.budget);
+        if (landed) {
             tc05::fence_after_sync();
             const unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
             const uint32_t id = ra.idesc, idn = ra.idesc | (1u << 13);   // negate A
@@ -192,9 +198,11 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
             abort_flag = 1;
         }
         tc05::mma_commit(&bar_mma[b]);   // arrives once every issued MMA completed
+        n_mma = st + 1;
     };
 
     if (threadIdx.x == 0) {
+        tc05::mbar_init(&dbg_bar, 1);
         for (int b = 0; b < 2; ++b) {
             tc05::mbar_init(&bar_tma[b], 1);
             tc05::mbar_init(&bar_mma[b], 1);
@@ -214,11 +222,7 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
     if (threadIdx.x == 0) {
         issue_tma(0);
         if (nstages > 1) issue_tma(1);
-    }
-    int pending_tma = -1;      // a stage whose copies were issued but not waited for
-    if (threadIdx.x == 0) {
         issue_mma(0);
-        if (abort_flag) pending_tma = 0;
     }
     const int Cp = ncb * 128;                // channel stride of prod
     const int R = ra.nh * ra.Lh;             // rows of prod per (bin, plane)
@@ -227,10 +231,7 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
         const int k = st / NA;
         // the next stage's products, before this stage's completion and
         // (at an item's last stage) its epilogue
-        if (threadIdx.x == 0 && st + 1 < nstages) {
-            issue_mma(st + 1);
-            if (abort_flag && pending_tma < 0) pending_tma = st + 1;
-        }
+        if (threadIdx.x == 0 && st + 1 < nstages) issue_mma(st + 1);
         __syncwarp();
         bool done = tc05::mbar_wait(&bar_mma[b], (st >> 1) & 1, ra.budget);
         done = __all_sync(0xffffffffu, done);
@@ -279,17 +280,18 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
         tc05::fence_before_sync();
         __syncthreads();
         tc05::fence_after_sync();
-        if (abort_flag) {
-            // copies of stage st + 2 may have been issued above
-            if (threadIdx.x == 0 && done && st + 2 < nstages && pending_tma < 0)
-                pending_tma = st + 2;
-            break;
-        }
+        if (abort_flag) break;
     }
-    // after a timed-out wait: give copies still in flight one more budget
-    // before the shared memory is released
-    if (threadIdx.x == 0 && pending_tma >= 0)
-        tc05::mbar_wait(&bar_tma[pending_tma & 1], (pending_tma >> 1) & 1, ra.budget);
+    // before shared and tensor memory are released, the copies and products
+    // thread 0 issued have completed: only the last stage on each buffer can
+    // still be outstanding (after a timed-out wait), and waiting again on a
+    // completed phase returns at once
+    if (threadIdx.x == 0) {
+        for (int st = n_tma > 2 ? n_tma - 2 : 0; st < n_tma; ++st)
+            tc05::mbar_wait(&bar_tma[st & 1], (st >> 1) & 1, ra.budget);
+        for (int st = n_mma > 2 ? n_mma - 2 : 0; st < n_mma; ++st)
+            tc05::mbar_wait(&bar_mma[st & 1], (st >> 1) & 1, ra.budget);
+    }
     tc05::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc05::tmem_dealloc(tmem, 512);
