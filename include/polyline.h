@@ -142,7 +142,12 @@ typedef struct {
      * PL_ERR_TIMEOUT; no device fault, the context stays usable). */
     int debug_unsatisfiable;
     int wait_timeout_us;
-    int reserved[5];
+    /* block_config 4: 1 = the one-block-per-SM layout (three channel classes,
+     * one channel per round, 512 TMEM columns) whatever fits, the layout a
+     * batch's persistent back-projection runs every scene in; 0 = chosen by
+     * size (default). */
+    int one_block_per_sm;
+    int reserved[4];
 } pl_options;
 
 typedef struct pl_plan pl_plan;
@@ -345,21 +350,35 @@ pl_status pl_synth_echo(int n_chan, const double *tx_xy, const double *rx_xy,
 
 /* ---- Batches of uneven scans (one persistent launch) --------------------
  * A batch reconstructs n_scenes independent scans whose geometry, scan,
- * band and grid may all differ. pl_execute_batch replays one CUDA graph:
- * the per-scene transforms over z (Eq. 2), then ONE persistent kernel that
- * pulls work items from a device queue -- every scene's range-table blocks
- * (Eq. 8a/19a) first, then every scene's back-projection tiles (Eq. 8b/19b),
- * largest scenes first -- and finally the per-scene inverse transforms
- * (Eq. 9). A back-projection item waits for its scene's range table through a
- * per-scene counter; the wait is bounded (wait_timeout_ms) and gives up with
+ * band and grid may all differ. pl_execute_batch replays one CUDA graph.
+ *
+ * Tensor cores (block_config 4, the default): the per-scene transforms over z
+ * (Eq. 2) and range tables (Eq. 8a/19a), the scenes spread over parallel
+ * streams, then ONE persistent tensor-core back-projection (Eq. 8b/19b), one
+ * block per SM pulling every scene's back-projection blocks from a device
+ * queue (largest scenes first; each scene in the one-block-per-SM layout,
+ * K steps and planar or interleaved rows per scene), then the per-scene
+ * inverse transforms (Eq. 9). tc_launch = 2 runs each scene's own
+ * back-projection launch instead (on the parallel streams).
+ *
+ * FP32 kernels (block_config 1-3): the per-scene transforms over z, then ONE
+ * persistent kernel that pulls work items from a device queue -- every
+ * scene's range-table blocks first, then every scene's back-projection tiles,
+ * largest scenes first -- and finally the per-scene inverse transforms. A
+ * back-projection item waits for its scene's range table through a per-scene
+ * counter.
+ *
+ * Every device-side wait is bounded (wait_timeout_ms) and gives up with
  * PL_ERR_TIMEOUT instead of hanging.
  *
- * Block shape: all scenes share one (tile_u, block_config). With autotune = 1
- * (and tile_u = block_config = 0) pl_batch_create times the candidate shapes
- * on this batch and keeps the fastest; the choice is cached per batch
- * signature for the life of the process. The persistent path needs
- * nufft_w = 6 and a fine grid <= 512 points in every scene; otherwise the
- * batch falls back to per-scene launches inside the same graph (see
+ * Block shape: with autotune = 1 (and tile_u = block_config = 0)
+ * pl_batch_create times the candidates on this batch -- the persistent
+ * tensor-core back-projection, the per-scene tensor-core launches, and the
+ * FP32 persistent kernel with tile_u 8, 16 and 20 -- and keeps the fastest;
+ * the choice is cached per batch signature for the life of the process. The
+ * persistent paths need nufft_w = 6 in every scene (FP32: and a fine grid
+ * <= 512 points; tensor cores: at most 96 scenes, one precision); otherwise
+ * the batch falls back to per-scene launches inside the same graph (see
  * pl_batch_info.persistent). */
 typedef struct pl_batch pl_batch;
 
@@ -369,15 +388,21 @@ typedef struct {
     int autotune;            /* 1: choose tile_u / block_config by timing */
     double wait_timeout_ms;  /* bound of a device-side wait (0 = 2000 ms) */
     int debug_unsatisfiable; /* test hook: scene 0's tiles wait for one more range-table
-                              * block than exists, so the bounded wait must expire */
-    int reserved[7];
+                              * block than exists, so the bounded wait must expire (FP32
+                              * persistent kernel; for the tensor-core kernels see
+                              * pl_options.debug_unsatisfiable) */
+    int tc_launch;           /* block_config 4: 0 = one persistent back-projection when every
+                              * scene allows it (default), 1 = persistent (PL_ERR_UNSUPPORTED
+                              * if a scene does not allow it), 2 = each scene's own launch */
+    int reserved[6];
 } pl_batch_options;
 
 typedef struct {
     int n_scenes;
     int tile_u, block_config;
     int autotuned;             /* 1 if the shape came from timing (or its cache) */
-    int persistent;            /* 1: one persistent launch; 0: per-scene launches */
+    int persistent;            /* 1: one persistent launch (block_config 4: of the
+                                  back-projection); 0: per-scene launches */
     int persistent_blocks;     /* resident blocks of the persistent launch */
     int work_items;            /* range-table + back-projection items */
     int launches_per_execute;  /* kernel launches in the graph */

@@ -44,7 +44,7 @@ class PlGrid(ctypes.Structure):
 class PlOptions(ctypes.Structure):
     _fields_ = [("precision", _I), ("nufft_sigma", _D), ("nufft_w", _I), ("tile_u", _I),
                 ("block_config", _I), ("debug_unsatisfiable", _I), ("wait_timeout_us", _I),
-                ("reserved", _I * 5)]
+                ("one_block_per_sm", _I), ("reserved", _I * 4)]
 
 
 class PlInfo(ctypes.Structure):
@@ -60,7 +60,8 @@ class PlInfo(ctypes.Structure):
 
 class PlBatchOptions(ctypes.Structure):
     _fields_ = [("tile_u", _I), ("block_config", _I), ("autotune", _I),
-                ("wait_timeout_ms", _D), ("debug_unsatisfiable", _I), ("reserved", _I * 7)]
+                ("wait_timeout_ms", _D), ("debug_unsatisfiable", _I), ("tc_launch", _I),
+                ("reserved", _I * 6)]
 
 
 class PlBatchInfo(ctypes.Structure):
@@ -183,7 +184,8 @@ class _DevArray:
 
 def _descriptors(keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad, pair_tx,
                  pair_rx, radius, n_sections, chord_len, elem_section, precision, nufft_sigma,
-                 nufft_w, tile_u, block_config, debug_unsatisfiable=0, wait_timeout_us=0):
+                 nufft_w, tile_u, block_config, debug_unsatisfiable=0, wait_timeout_us=0,
+                 one_block_per_sm=0):
     exy = _f64(elem_xy).reshape(-1, 2)
     sec = None if elem_section is None else _i32(elem_section)
     ptx = None if pair_tx is None else _i32(pair_tx)
@@ -199,7 +201,8 @@ def _descriptors(keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pa
                float(grid["z0"]), float(grid["dz"]), int(grid["nx"]), int(grid["ny"]),
                int(grid["nz"]))
     opt = PlOptions(int(precision), float(nufft_sigma), int(nufft_w), int(tile_u),
-                    int(block_config), int(debug_unsatisfiable), int(wait_timeout_us))
+                    int(block_config), int(debug_unsatisfiable), int(wait_timeout_us),
+                    int(one_block_per_sm))
     return geom, scan, freqs, g, opt
 
 
@@ -215,13 +218,14 @@ class Plan:
     def __init__(self, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad=0,
                  pair_tx=None, pair_rx=None, radius=0.0, n_sections=0, chord_len=0.0,
                  elem_section=None, precision=0, nufft_sigma=0.0, nufft_w=0, tile_u=0,
-                 block_config=0, debug_unsatisfiable=0, wait_timeout_us=0):
+                 block_config=0, debug_unsatisfiable=0, wait_timeout_us=0, one_block_per_sm=0):
         lib = load()
         self._keep = []
         geom, scan, freqs, g, opt = _descriptors(
             self._keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad, pair_tx,
             pair_rx, radius, n_sections, chord_len, elem_section, precision, nufft_sigma,
-            nufft_w, tile_u, block_config, debug_unsatisfiable, wait_timeout_us)
+            nufft_w, tile_u, block_config, debug_unsatisfiable, wait_timeout_us,
+            one_block_per_sm)
         h = _P()
         _check(lib.pl_plan_create(ctypes.byref(h), geom, scan, freqs, g, opt))
         self._h = h
@@ -441,7 +445,8 @@ class Batch:
     launch, replayed as a CUDA graph."""
 
     def __init__(self, workloads, precision=0, nufft_sigma=0.0, nufft_w=0, tile_u=0,
-                 block_config=0, autotune=False, wait_timeout_ms=0.0, debug_unsatisfiable=0):
+                 block_config=0, autotune=False, wait_timeout_ms=0.0, debug_unsatisfiable=0,
+                 tc_launch=0, tc_debug_unsatisfiable=0, tc_wait_timeout_us=0):
         lib = load()
         self._keep = []
         n = len(workloads)
@@ -449,9 +454,10 @@ class Batch:
                          (PlOptions * n)())
         for i, w in enumerate(workloads):
             G[i], S[i], F[i], R[i], O[i] = _descriptors(
-                self._keep, *_workload_args(w), precision, nufft_sigma, nufft_w, 0, 0)
+                self._keep, *_workload_args(w), precision, nufft_sigma, nufft_w, 0, 0,
+                tc_debug_unsatisfiable, tc_wait_timeout_us)
         bo = PlBatchOptions(int(tile_u), int(block_config), 1 if autotune else 0,
-                            float(wait_timeout_ms), int(debug_unsatisfiable))
+                            float(wait_timeout_ms), int(debug_unsatisfiable), int(tc_launch))
         h = _P()
         _check(lib.pl_batch_create(ctypes.byref(h), n, G, S, F, R, O, ctypes.byref(bo)))
         self._h = h

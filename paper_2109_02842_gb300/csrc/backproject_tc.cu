@@ -95,38 +95,44 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
     lo = bf2(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xffff0000u));
 }
 
+// Barriers of one block's item: b_full[NSG], done[NSG], a_full[NPAR],
+// a_done[NPAR], acc_full (NSG = nst / (NPAR CPR) slot groups).
+__host__ __device__ constexpr int tc_barriers(int nsg, int npar) { return 2 * nsg + 2 * npar + 1; }
+
+// One block of the back-projection: 16 x 8 pixel tile, bin block and channel
+// part decoded from the linear block index `lin`. The caller has allocated
+// tensor memory (`tmem`, tmem_cols columns) and initialised the barriers
+// `bars` (layout above: arrival counts 1, 1, 4, 1, 1); on return every copy
+// and product the block issued has completed and no arrival on `bars` is
+// outstanding, so the caller may re-initialise them for another item.
 template <int W, int KS, int SPLIT, int NPAR, bool PLANAR, int CPR>
-__global__ void __launch_bounds__(Warps<NPAR>::threads, NPAR == 2 ? 2 : 1)
-k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUtensorMap tmap,
-                 const TileGeo *__restrict__ tgeo, const float2 *__restrict__ kc_hl,
-                 float2 *__restrict__ G, int *err) {
+__device__ __forceinline__ void bp_tc_item(const BpDesc &p, const CoefTable &ct, const TcArgs &ta,
+                                           const CUtensorMap *tmap, const TileGeo *__restrict__ tgeo,
+                                           const float2 *__restrict__ kc_hl,
+                                           float2 *__restrict__ G, int *err, int lin,
+                                           unsigned char *smem, uint64_t *bars, uint32_t tmem,
+                                           uint64_t *dbg_bar) {
     constexpr int NCW = Warps<NPAR>::compute;
     constexpr int NPL = SPLIT == 3 ? 4 : 2;     // A planes: (re, im) x (hi[, lo])
     constexpr int NW = 8 * KS;                  // 32-bit words of an A row (16 KS BF16)
     constexpr int NT = W / 2 + 1;               // words of the taps after the parity shift
     constexpr int ND = W + 2;                   // polynomial coefficients per tap
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // swizzled TMA destinations and MMA operands sit on 1024-byte boundaries
-    unsigned char *smem = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     // Channels go in groups of NPAR (channel c = NPAR g + k, class k); the
     // slots form NSG slot groups of NPAR. b_full[s]: the windows of the group
     // in slot group s landed (TMA); done[s]: that group's products completed
     // (frees the slot group); a_full[k]: A of class k written (its 4 warps);
     // a_done[k]: the products reading class k's A buffer completed.
     const int NSG = ta.nst / (NPAR * CPR);
-    uint64_t *b_full = reinterpret_cast<uint64_t *>(smem + (size_t)ta.nst * ta.slot_bytes);
+    uint64_t *b_full = bars;
     uint64_t *done = b_full + NSG;
     uint64_t *a_full = done + NSG;
     uint64_t *a_done = a_full + NPAR;
     uint64_t *acc_full = a_done + NPAR;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_full + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // linear block index (tile x fastest, then tile y, then bin block x
-    // channel part), from ta.blk0 on: a launch may cover a range of blocks
+    // linear block index: tile x fastest, then tile y, then bin block x
+    // channel part
     const int nbx = (p.nx + TCX - 1) / TCX, nby = (p.ny + TCY - 1) / TCY;
-    const int lin = (int)blockIdx.x + ta.blk0;
     const int bx = lin % nbx, by = (lin / nbx) % nby, bz = lin / (nbx * nby);
     const int tile = by * nbx + bx;
     // bz = bin block x channel part: channels [cb, ce) of the tile
@@ -137,29 +143,6 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
     const int cb = part * cper, ce = min(C, cb + cper);
     const TileGeo *tg = tgeo + (size_t)tile * C;
     const long long budget = ta.budget;
-    __shared__ __align__(8) uint64_t dbg_bar;    // test hook: never completed
-
-    if (threadIdx.x == 0) {
-        tc05::mbar_init(&dbg_bar, 1);
-        for (int s = 0; s < NSG; ++s) {
-            tc05::mbar_init(&b_full[s], 1);
-            tc05::mbar_init(&done[s], 1);
-        }
-        for (int k = 0; k < NPAR; ++k) {
-            tc05::mbar_init(&a_full[k], 4);
-            tc05::mbar_init(&a_done[k], 1);
-        }
-        tc05::mbar_init(acc_full, 1);
-        tc05::fence_mbar_init();
-    }
-    if (warp == 0) {
-        tc05::tmem_alloc(tmem_slot, ta.tmem_cols);
-        tc05::tmem_relinquish();
-    }
-    tc05::fence_before_sync();
-    __syncthreads();
-    tc05::fence_after_sync();
-    const uint32_t tmem = *tmem_slot;
     const uint32_t N = PLANAR ? ta.UT : 2 * ta.UT;     // the MMA's N
 
     if (warp < NCW) {
@@ -271,6 +254,9 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
             }
             c = cnext;
         }
+        // the release of the class's last round has arrived (no arrival on
+        // a_done outstanding when the block returns)
+        if (ok && it > 0) ok = __all_sync(0xffffffffu, tc05::mbar_wait(&a_done[par], (uint32_t)(it - 1) & 1u, budget));
         if (!ok && lane == 0) atomicOr(err, 1);
 
         // ------------------------------------------------ epilogue
@@ -322,7 +308,7 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
         const uint32_t im16 = ta.im_off >> 4;              // Im B columns (planar)
         const uint32_t idn = ta.idesc | (1u << 13);        // negated A
         bool ok = true;
-        if (ta.dbg_wait) ok = __all_sync(0xffffffffu, tc05::mbar_wait(&dbg_bar, 0, budget));
+        if (ta.dbg_wait) ok = __all_sync(0xffffffffu, tc05::mbar_wait(dbg_bar, 0, budget));
         int sg = 0;
         uint32_t bpar = 0;
         for (int g = 0; g < n_groups && ok; ++g) {
@@ -436,10 +422,10 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
                     for (int j = 0; j < ta.ncb; ++j) {
                         // planar: the Re columns of the bins, then (im_off bytes
                         // on) their Im columns; interleaved: (re, im) pairs
-                        tc05::tma_load_3d(dst + (size_t)j * ta.cb_bytes, &tmap, &b_full[sg],
+                        tc05::tma_load_3d(dst + (size_t)j * ta.cb_bytes, tmap, &b_full[sg],
                                           (PLANAR ? u0 : 2 * u0) + 64 * j, ilo[k], cz);
                         if (PLANAR)
-                            tc05::tma_load_3d(dst + ta.im_off + (size_t)j * ta.cb_bytes, &tmap,
+                            tc05::tma_load_3d(dst + ta.im_off + (size_t)j * ta.cb_bytes, tmap,
                                               &b_full[sg], ta.im_col + 64 * j, ilo[k], cz);
                     }
                 }
@@ -450,18 +436,156 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
                 if (g + 1 >= 2 * NSG) dpar ^= 1u;
             }
         }
-        // every issued copy has landed before the block can exit
+        // every issued copy has landed before the block can exit, and the
+        // products of every issued group have released its slot group (no
+        // arrival on b_full or done outstanding)
         if (lane == 0) {
             if (!ok) atomicOr(err, 8);
             for (int s = 0; s < NSG && s < issued; ++s) {
                 const int n_s = (issued - 1 - s) / NSG + 1;   // groups loaded into slot group s
                 if (!tc05::mbar_wait(&b_full[s], (n_s - 1) & 1, budget)) atomicOr(err, 16);
+                if (ok && !tc05::mbar_wait(&done[s], (n_s - 1) & 1, budget)) atomicOr(err, 32);
             }
         }
     }
+}
+
+// The per-scan kernel: one block per (tile, bin block, channel part) from
+// ta.blk0 on (a launch may cover a range of blocks); the barriers follow the
+// window slots in shared memory.
+template <int W, int KS, int SPLIT, int NPAR, bool PLANAR, int CPR>
+__global__ void __launch_bounds__(Warps<NPAR>::threads, NPAR == 2 ? 2 : 1)
+k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUtensorMap tmap,
+                 const TileGeo *__restrict__ tgeo, const float2 *__restrict__ kc_hl,
+                 float2 *__restrict__ G, int *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // swizzled TMA destinations and MMA operands sit on 1024-byte boundaries
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int NSG = ta.nst / (NPAR * CPR);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)ta.nst * ta.slot_bytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + tc_barriers(NSG, NPAR));
+    __shared__ __align__(8) uint64_t dbg_bar;    // test hook: never completed
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        tc05::mbar_init(&dbg_bar, 1);
+        for (int s = 0; s < NSG; ++s) {
+            tc05::mbar_init(&bars[s], 1);
+            tc05::mbar_init(&bars[NSG + s], 1);
+        }
+        for (int k = 0; k < NPAR; ++k) {
+            tc05::mbar_init(&bars[2 * NSG + k], 4);
+            tc05::mbar_init(&bars[2 * NSG + NPAR + k], 1);
+        }
+        tc05::mbar_init(&bars[2 * NSG + 2 * NPAR], 1);
+        tc05::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc05::tmem_alloc(tmem_slot, ta.tmem_cols);
+        tc05::tmem_relinquish();
+    }
+    tc05::fence_before_sync();
+    __syncthreads();
+    tc05::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    bp_tc_item<W, KS, SPLIT, NPAR, PLANAR, CPR>(p, ct, ta, &tmap, tgeo, kc_hl, G, err,
+                                               (int)blockIdx.x + ta.blk0, smem, bars, tmem,
+                                               &dbg_bar);
     tc05::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc05::tmem_dealloc(tmem, ta.tmem_cols);
+}
+
+// The batch: ONE persistent launch, one block per SM, over a device work
+// queue of every scene's back-projection blocks (scenes in decreasing cost,
+// a scene's blocks in their linear order). Per item the block copies the
+// scene's descriptors into shared memory, (re-)initialises the barriers and
+// runs the item in that scene's layout (K steps and planar or interleaved
+// picked at run time; all scenes in the one-block-per-SM layout). Tensor
+// memory is allocated once for the block's life. An expired wait anywhere
+// stops every block from taking further items.
+template <int W, int SPLIT>
+__global__ void __launch_bounds__(Warps<3>::threads, 1)
+k_backproject_tc_batch(const __grid_constant__ TcBatchMaps maps, CoefTable ct,
+                       const TcScene *__restrict__ scenes, int n_scenes, int total,
+                       int *counters, int *err) {
+    constexpr int kMaxBars = tc_barriers(16, 3);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t bars[kMaxBars];
+    __shared__ __align__(8) uint64_t dbg_bar;     // test hook: never completed
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_item, s_scene;
+    __shared__ BpDesc s_bp;
+    __shared__ TcArgs s_ta;
+    const int warp = threadIdx.x >> 5;
+    int n_bars = 0;          // barriers initialised for the last item (thread 0)
+    if (threadIdx.x == 0) tc05::mbar_init(&dbg_bar, 1);
+    if (warp == 0) {
+        tc05::tmem_alloc(&tmem_slot, 512);
+        tc05::tmem_relinquish();
+    }
+    tc05::fence_before_sync();
+    __syncthreads();
+    tc05::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int item = total;
+            if (*(volatile int *)err == 0) item = atomicAdd(&counters[0], 1);
+            int sc = 0;
+            if (item < total) {
+                sc = n_scenes - 1;
+                while (sc > 0 && scenes[sc].begin > item) --sc;
+                s_bp = scenes[sc].bp;
+                s_ta = scenes[sc].ta;
+                // the previous item left every barrier with its phases
+                // complete and no arrival outstanding
+                for (int i = 0; i < n_bars; ++i) tc05::mbar_inval(&bars[i]);
+                const int NSG = s_ta.nst / 3;
+                for (int i = 0; i < 2 * NSG; ++i) tc05::mbar_init(&bars[i], 1);
+                for (int k = 0; k < 3; ++k) {
+                    tc05::mbar_init(&bars[2 * NSG + k], 4);
+                    tc05::mbar_init(&bars[2 * NSG + 3 + k], 1);
+                }
+                tc05::mbar_init(&bars[2 * NSG + 6], 1);
+                n_bars = tc_barriers(NSG, 3);
+                tc05::fence_mbar_init();
+            }
+            s_item = item;
+            s_scene = sc;
+        }
+        tc05::fence_before_sync();
+        __syncthreads();
+        tc05::fence_after_sync();
+        const int item = s_item;
+        if (item >= total) break;
+        const TcScene &sd = scenes[s_scene];
+        const CUtensorMap *tm = &maps.m[s_scene];
+        const int lin = item - sd.begin;
+        if (s_ta.ks == 1) {
+            if (s_ta.planar)
+                bp_tc_item<W, 1, SPLIT, 3, true, 1>(s_bp, ct, s_ta, tm, sd.tgeo, sd.kc_hl, sd.G,
+                                                    err, lin, smem, bars, tmem, &dbg_bar);
+            else
+                bp_tc_item<W, 1, SPLIT, 3, false, 1>(s_bp, ct, s_ta, tm, sd.tgeo, sd.kc_hl, sd.G,
+                                                     err, lin, smem, bars, tmem, &dbg_bar);
+        } else {
+            if (s_ta.planar)
+                bp_tc_item<W, 2, SPLIT, 3, true, 1>(s_bp, ct, s_ta, tm, sd.tgeo, sd.kc_hl, sd.G,
+                                                    err, lin, smem, bars, tmem, &dbg_bar);
+            else
+                bp_tc_item<W, 2, SPLIT, 3, false, 1>(s_bp, ct, s_ta, tm, sd.tgeo, sd.kc_hl, sd.G,
+                                                     err, lin, smem, bars, tmem, &dbg_bar);
+        }
+        tc05::fence_before_sync();
+        __syncthreads();
+        tc05::fence_after_sync();
+    }
+    tc05::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc05::tmem_dealloc(tmem, 512);
 }
 
 template <int W, int KS, int SPLIT, int NPAR, bool PLANAR, int CPR>
@@ -530,6 +654,24 @@ size_t backproject_tc_smem_bytes(const TcArgs &ta) {
     // at most 2 blocks per SM (256 TMEM columns each), 1 when a block takes 512
     const size_t floor_b = ta.tmem_cols > 256 ? 120 * 1024 : 80 * 1024;
     return s < floor_b ? floor_b : s;
+}
+
+size_t backproject_tc_batch_smem_bytes(const TcArgs &ta) {
+    return 1024 + (size_t)ta.nst * ta.slot_bytes;     // alignment slack + window slots
+}
+
+cudaError_t launch_backproject_tc_batch(const TcBatchMaps &maps, const CoefTable &ct,
+                                        const TcScene *scenes, int n_scenes, int total, int split,
+                                        int *counters, int *err, int grid, size_t smem,
+                                        cudaStream_t st) {
+    if (n_scenes < 1 || n_scenes > kTcBatchMaxScenes || grid < 1 || smem > 227 * 1024)
+        return cudaErrorInvalidValue;
+    auto kern = split == 3 ? k_backproject_tc_batch<6, 3> : k_backproject_tc_batch<6, 1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, Warps<3>::threads, smem, st>>>(maps, ct, scenes, n_scenes, total, counters, err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_backproject_tc(const BpDesc &p, const CoefTable &ct, const TcArgs &ta,

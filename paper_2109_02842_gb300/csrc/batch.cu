@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <numeric>
@@ -174,6 +175,7 @@ cudaError_t launch_batch(int tile_u, int block_config, const BatchConst &bc,
 
 std::mutex g_tune_mu;
 std::map<std::string, std::pair<int, int>> g_tune_cache;   // signature -> (tile_u, block_config)
+std::map<std::string, int> g_tune_tc_cache;                // signature -> tc_launch
 
 }  // namespace
 
@@ -199,6 +201,15 @@ struct pl_batch {
     std::vector<const void *> cap_echo;
     std::vector<void *> cap_img;
     pl_batch_info info{};
+    // the persistent tensor-core back-projection: requested mode (0 auto,
+    // 1 persistent, 2 per-scene launches), and when in use the scenes'
+    // descriptors (device), table maps (a kernel parameter), items, launch shape
+    int tc_mode = 0;
+    bool tc_persistent = false;
+    TcBatchMaps *h_maps = nullptr;
+    TcScene *d_tcscenes = nullptr;
+    int tc_total = 0, tc_split = 3, tc_grid = 0;
+    size_t tc_smem = 0;
 
     void free_plans() {
         for (pl_plan *p : plans) pl_plan_destroy(p);
@@ -210,6 +221,8 @@ struct pl_batch {
         for (cudaStream_t s : aux) cudaStreamDestroy(s);
         for (cudaEvent_t e : aux_ev) cudaEventDestroy(e);
         if (d_scenes) cudaFree(d_scenes);
+        if (d_tcscenes) cudaFree(d_tcscenes);
+        delete h_maps;
         if (d_counters) cudaFree(d_counters);
         if (h_flag) cudaFreeHost(h_flag);
         free_plans();
@@ -218,14 +231,19 @@ struct pl_batch {
 
 namespace {
 
+// tc_mode (block_config 4): 2 = per-scene launches in the layout each scene
+// picks; otherwise every scene in the one-block-per-SM layout of the
+// persistent back-projection
 pl_status make_plans(pl_batch *B, int n, const pl_geometry *g, const pl_scan *s, const pl_freqs *f,
-                     const pl_grid *gr, const pl_options *opts, int tile_u, int block_config) {
+                     const pl_grid *gr, const pl_options *opts, int tile_u, int block_config,
+                     int tc_mode) {
     B->free_plans();
     for (int i = 0; i < n; ++i) {
         pl_options o{};
         if (opts) o = opts[i];
         o.tile_u = block_config == 4 ? 0 : tile_u;     // the tensor-core kernel sizes its own
         o.block_config = block_config;
+        o.one_block_per_sm = (block_config == 4 && tc_mode != 2) ? 1 : 0;
         pl_plan *p = nullptr;
         pl_status st = pl_plan_create(&p, &g[i], &s[i], &f[i], &gr[i], &o);
         if (st != PL_OK) return st;
@@ -291,6 +309,59 @@ pl_status build_queue(pl_batch *B, int tile_u, double timeout_ms, int debug) {
     }
     if (smem > 200 * 1024) B->persistent = false;
     B->smem = smem;
+    // the tensor-core scenes' back-projections as one persistent launch: every
+    // scene in the one-block-per-SM layout with 6 taps, one split, the same tap
+    // polynomials, and the largest window pool within shared memory
+    B->tc_persistent = false;
+    if (B->block_config == 4 && B->tc_mode != 2) {
+        const pl_plan *p0 = B->plans[0];
+        bool ok = n <= kTcBatchMaxScenes;
+        size_t tsm = 0;
+        for (const pl_plan *p : B->plans) {
+            ok = ok && p->block_config == 4 && p->nd.w == 6 && p->tc.npar == 3 && p->tc.cpr == 1 &&
+                 p->tc.split == p0->tc.split &&
+                 std::memcmp(&p->coef, &p0->coef, sizeof(CoefTable)) == 0;
+            tsm = std::max(tsm, backproject_tc_batch_smem_bytes(p->tc));
+        }
+        ok = ok && tsm + 1024 <= 227 * 1024;      // + the kernel's static shared memory
+        if (!ok && B->tc_mode == 1)
+            return pl_internal_fail(PL_ERR_UNSUPPORTED,
+                                    "a scene does not allow the persistent tensor-core launch");
+        if (ok) {
+            std::vector<TcScene> ts(n);
+            if (!B->h_maps) B->h_maps = new (std::nothrow) TcBatchMaps();
+            if (!B->h_maps) return pl_internal_fail(PL_ERR_OOM, "host allocation failed");
+            int total_tc = 0;
+            for (int k = 0; k < n; ++k) {
+                const pl_plan *p = B->plans[order[k]];
+                TcScene &t = ts[k];
+                t.bp = p->bp;
+                t.ta = p->tc;
+                t.ta.blk0 = 0;
+                t.ta.nblk = 0;
+                t.tgeo = p->d_tgeo;
+                t.kc_hl = p->d_kchl;
+                t.G = p->d_G;
+                t.begin = total_tc;
+                t.nblk = backproject_tc_blocks(p->bp, p->tc);
+                total_tc += t.nblk;
+                B->h_maps->m[k] = p->tmap;
+            }
+            if (B->d_tcscenes) cudaFree(B->d_tcscenes);
+            B->d_tcscenes = nullptr;
+            PL_CUDA_RET(cudaMalloc(&B->d_tcscenes, sizeof(TcScene) * n));
+            PL_CUDA_RET(cudaMemcpy(B->d_tcscenes, ts.data(), sizeof(TcScene) * n,
+                                   cudaMemcpyHostToDevice));
+            int dev = 0, sms = 0;
+            PL_CUDA_RET(cudaGetDevice(&dev));
+            PL_CUDA_RET(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            B->tc_total = total_tc;
+            B->tc_split = p0->tc.split;
+            B->tc_grid = sms;
+            B->tc_smem = tsm;
+            B->tc_persistent = true;
+        }
+    }
     B->bc = BatchConst{};
     B->bc.ct = B->plans[0]->coef;
     B->bc.n_scenes = n;
@@ -307,11 +378,18 @@ pl_status build_queue(pl_batch *B, int tile_u, double timeout_ms, int debug) {
     if (B->persistent)
         PL_CUDA_RET(launch_batch(tile_u, B->block_config, B->bc, B->d_scenes, B->d_counters,
                                  B->smem, &B->pblocks, true, nullptr));
-    B->info.work_items = total;
-    B->info.persistent = B->persistent ? 1 : 0;
-    B->info.persistent_blocks = B->persistent ? B->pblocks : 0;
+    B->info.work_items = B->tc_persistent ? B->tc_total : total;
+    B->info.persistent = (B->persistent || B->tc_persistent) ? 1 : 0;
+    B->info.persistent_blocks = B->persistent ? B->pblocks : (B->tc_persistent ? B->tc_grid : 0);
     if (B->persistent) {
         B->info.launches_per_execute = 2 * n + 1;
+    } else if (B->tc_persistent) {
+        // per scene: the z transform, its range-table launches and the
+        // inverse transform; one back-projection launch for all
+        int total = 1;
+        for (const pl_plan *p : B->plans)
+            total += 2 + ((p->block_config == 4 && p->rt_tc) ? (p->fwd_fft ? 2 : 3) : 1);
+        B->info.launches_per_execute = total;
     } else {        // each scene's own kernels (pl_plan_get_info counts them)
         int total = 0;
         for (pl_plan *p : B->plans) {
@@ -320,7 +398,7 @@ pl_status build_queue(pl_batch *B, int tile_u, double timeout_ms, int debug) {
         }
         B->info.launches_per_execute = total;
     }
-    if (!B->persistent && B->aux.empty()) {
+    if ((!B->persistent || B->tc_persistent) && B->aux.empty()) {
         // scenes of the per-scene path run on kAuxStreams streams at once
         for (int k = 0; k < kAuxStreams; ++k) {
             cudaStream_t s = nullptr;
@@ -350,6 +428,32 @@ pl_status enqueue(pl_batch *B, const void *const *echo, void *const *image, cuda
                                  B->smem, &B->pblocks, false, st));
         for (int i = 0; i < n; ++i)
             if ((s = pl_stage_zifft(B->plans[i], (float2 *)image[i], st)) != PL_OK) return s;
+    } else if (B->tc_persistent) {
+        // the scenes' range tables on the parallel streams, then one
+        // persistent back-projection for every scene, then the inverse
+        // transforms on the parallel streams again
+        const int K = (int)B->aux.size();
+        cudaEvent_t fork = B->aux_ev[K];
+        for (int phase = 0; phase < 2; ++phase) {
+            PL_CUDA_RET(cudaEventRecord(fork, st));
+            for (int k = 0; k < K; ++k) PL_CUDA_RET(cudaStreamWaitEvent(B->aux[k], fork, 0));
+            for (int j = 0; j < n; ++j) {
+                const int i = B->order[j];
+                cudaStream_t as = B->aux[j % K];
+                s = phase == 0 ? pl_stage_range_table(B->plans[i], as)
+                               : pl_stage_zifft(B->plans[i], (float2 *)image[i], as);
+                if (s != PL_OK) return s;
+            }
+            for (int k = 0; k < K; ++k) {
+                PL_CUDA_RET(cudaEventRecord(B->aux_ev[k], B->aux[k]));
+                PL_CUDA_RET(cudaStreamWaitEvent(st, B->aux_ev[k], 0));
+            }
+            if (phase == 0)
+                PL_CUDA_RET(launch_backproject_tc_batch(*B->h_maps, B->plans[0]->coef,
+                                                        B->d_tcscenes, n, B->tc_total, B->tc_split,
+                                                        B->d_counters, B->d_counters + 1,
+                                                        B->tc_grid, B->tc_smem, st));
+        }
     } else {
         // per-scene range table, back-projection and inverse transform, the
         // scenes (largest first) dealt round-robin to the streams, joined at
@@ -464,9 +568,11 @@ pl_status pl_batch_create(pl_batch **out, int n, const pl_geometry *g, const pl_
     pl_batch_options bo{};
     if (bopt) bo = *bopt;
     if (bo.wait_timeout_ms <= 0) bo.wait_timeout_ms = 2000.0;
+    if (bo.tc_launch < 0 || bo.tc_launch > 2) return pl_internal_fail(PL_ERR_ARG, "tc_launch must be 0..2");
     pl_batch *B = new (std::nothrow) pl_batch();
     if (!B) return pl_internal_fail(PL_ERR_OOM, "host allocation failed");
     B->n = n;
+    B->tc_mode = bo.tc_launch;
     auto bail = [&](pl_status st) { delete B; return st; };
     cudaError_t e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&B->d_counters, sizeof(int) * (2 + n));
@@ -487,6 +593,7 @@ pl_status pl_batch_create(pl_batch **out, int n, const pl_geometry *g, const pl_
             if (it != g_tune_cache.end()) {
                 tile_u = it->second.first;
                 bcfg = it->second.second;
+                B->tc_mode = g_tune_tc_cache[sig];
                 cached = true;
             }
         }
@@ -502,12 +609,16 @@ pl_status pl_batch_create(pl_batch **out, int n, const pl_geometry *g, const pl_
                     e = cudaMalloc(&ibuf[i], sizeof(float2) * (size_t)gr[i].nx * gr[i].ny * gr[i].nz);
             }
             double best = 1e30, dflt = 0.0;
-            // the tensor-core kernel (per-scene launches, scenes on parallel
-            // streams) and the FP32 persistent kernel in three block shapes
-            const int cfgs[3] = {4, 1, 3};
+            int best_tc = 0;
+            // the tensor-core kernels (one persistent back-projection; each
+            // scene's own launches, scenes on parallel streams) and the FP32
+            // persistent kernel in three block shapes
+            const int cfgs[4] = {4, 4, 1, 3};
+            const int tcm[4] = {1, 2, 0, 0};
             const int tus[3] = {8, 16, 20};
-            for (int ci = 0; ci < 3 && e == cudaSuccess; ++ci) {
-                if (make_plans(B, n, g, s, f, gr, opts, 16, cfgs[ci]) != PL_OK) continue;
+            for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
+                B->tc_mode = tcm[ci];
+                if (make_plans(B, n, g, s, f, gr, opts, 16, cfgs[ci], tcm[ci]) != PL_OK) continue;
                 for (int ti = 0; ti < (cfgs[ci] == 4 ? 1 : 3); ++ti) {
                     double ms = 0.0;
                     if (build_queue(B, tus[ti], bo.wait_timeout_ms, 0) != PL_OK) continue;
@@ -517,9 +628,11 @@ pl_status pl_batch_create(pl_batch **out, int n, const pl_geometry *g, const pl_
                         best = ms;
                         tile_u = tus[ti];
                         bcfg = cfgs[ci];
+                        best_tc = tcm[ci];
                     }
                 }
             }
+            B->tc_mode = best_tc;
             for (int i = 0; i < n; ++i) {
                 if (ebuf[i]) cudaFree(ebuf[i]);
                 if (ibuf[i]) cudaFree(ibuf[i]);
@@ -529,12 +642,21 @@ pl_status pl_batch_create(pl_batch **out, int n, const pl_geometry *g, const pl_
             B->info.tune_default_ms = dflt;
             std::lock_guard<std::mutex> lock(g_tune_mu);
             g_tune_cache[sig] = {tile_u, bcfg};
+            g_tune_tc_cache[sig] = best_tc;
         }
         B->info.autotuned = 1;
     }
-    if ((st = make_plans(B, n, g, s, f, gr, opts, tile_u, bcfg)) != PL_OK) return bail(st);
+    if ((st = make_plans(B, n, g, s, f, gr, opts, tile_u, bcfg, B->tc_mode)) != PL_OK)
+        return bail(st);
     if ((st = build_queue(B, tile_u, bo.wait_timeout_ms, bo.debug_unsatisfiable)) != PL_OK)
         return bail(st);
+    if (B->block_config == 4 && B->tc_mode == 0 && !B->tc_persistent) {
+        // a scene rules out the persistent launch: each scene in its own layout
+        B->tc_mode = 2;
+        if ((st = make_plans(B, n, g, s, f, gr, opts, tile_u, bcfg, 2)) != PL_OK) return bail(st);
+        if ((st = build_queue(B, tile_u, bo.wait_timeout_ms, bo.debug_unsatisfiable)) != PL_OK)
+            return bail(st);
+    }
     B->info.n_scenes = n;
     B->info.tile_u = tile_u;
     B->info.block_config = B->block_config;

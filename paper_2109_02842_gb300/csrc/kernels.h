@@ -120,6 +120,30 @@ struct TcArgs {
 };
 // blocks of a whole back-projection
 int backproject_tc_blocks(const BpDesc &p, const TcArgs &ta);
+// One scene of a batch whose back-projections run as ONE persistent launch
+// (every scene in the one-block-per-SM layout: npar 3, cpr 1, 512 TMEM
+// columns; w = 6; one precision; the same tap polynomials).
+struct TcScene {
+    BpDesc bp;
+    TcArgs ta;
+    const TileGeo *tgeo;
+    const float2 *kc_hl;
+    float2 *G;
+    int begin;           // the scene's first item in the work queue
+    int nblk;            // its items (back-projection blocks)
+};
+constexpr int kTcBatchMaxScenes = 96;
+// the scenes' table maps, a kernel parameter (TMA reads them from there)
+struct TcBatchMaps {
+    CUtensorMap m[kTcBatchMaxScenes];
+};
+// counters[0]: next item (zeroed before the launch); err: wait-expired bits
+// (any set bit also stops the blocks from taking further items)
+cudaError_t launch_backproject_tc_batch(const TcBatchMaps &maps, const CoefTable &ct,
+                                        const TcScene *scenes, int n_scenes, int total, int split,
+                                        int *counters, int *err, int grid, size_t smem,
+                                        cudaStream_t st);
+size_t backproject_tc_batch_smem_bytes(const TcArgs &ta);
 int backproject_tc_tile_x();
 int backproject_tc_tile_y();
 size_t backproject_tc_smem_bytes(const TcArgs &ta);

@@ -30,16 +30,17 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 int tc_cols(int ut, int npar, int npl, int ks, bool planar) {
     return (planar ? 2 : 4) * ut + npar * npl * ks * 8;
 }
-int tc_npar(int ut, int npl, int ks, bool planar) {
+// (force3: the one-block-per-SM layout of three classes whatever fits)
+int tc_npar(int ut, int npl, int ks, bool planar, bool force3 = false) {
     if (planar && ut > 256) return 0;          // the MMA's N is at most 256
-    if (tc_cols(ut, 2, npl, ks, planar) <= 256) return 2;
+    if (!force3 && tc_cols(ut, 2, npl, ks, planar) <= 256) return 2;
     if (tc_cols(ut, 3, npl, ks, planar) <= 512) return 3;
     return 0;
 }
 // The layout fits: tensor memory, and two slot groups of table windows in
 // shared memory (npl 4: hi/lo planes).
-bool tc_fits(int ut, int npl, int ks, bool planar) {
-    const int npar = tc_npar(ut, npl, ks, planar);
+bool tc_fits(int ut, int npl, int ks, bool planar, bool force3 = false) {
+    const int npar = tc_npar(ut, npl, ks, planar, force3);
     if (npar == 0) return false;
     const int N = planar ? ut : 2 * ut;
     const size_t cb = (size_t)(npl == 4 ? 2 : 1) * 16 * ks * 128;
@@ -430,7 +431,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
             if (ks == 0)
                 return fail(PL_ERR_UNSUPPORTED,
                             "a 16 x 8 pixel tile spans more than 32 table rows (grid too coarse for block_config 4)");
-            if (tc_fits(P->tile_u, npl, ks, P->tc.planar != 0)) break;
+            if (tc_fits(P->tile_u, npl, ks, P->tc.planar != 0, o.one_block_per_sm != 0)) break;
             if (attempt > 1 || o.tile_u != 0)
                 return fail(PL_ERR_UNSUPPORTED, "tile_u too large for tensor memory");
             // the planar layout does not fit (too many bins, or two K steps,
@@ -483,7 +484,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         ta.im_off = ta.planar ? (unsigned)ta.ncb * ta.cb_bytes : 0u;
         ta.im_col = ta.planar ? ta.UT : 0;
         ta.slot_bytes = (unsigned)(ta.planar ? 2 : 1) * ta.ncb * ta.cb_bytes;
-        ta.npar = tc_npar(ta.UT, npl, ta.ks, ta.planar != 0);
+        ta.npar = tc_npar(ta.UT, npl, ta.ks, ta.planar != 0, o.one_block_per_sm != 0);
         ta.tmem_cols = ta.npar == 2 ? 256 : 512;
         ta.acol = 2 * N;
         // two channels per class round (twice the products per A wait and
@@ -491,7 +492,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         // the accumulators and two slot groups of six windows fit in shared
         // memory
         ta.cpr = 1;
-        if (ta.npar == 3 && 2 * N + 3 * 2 * npl * ta.ks * 8 <= 512 &&
+        if (!o.one_block_per_sm && ta.npar == 3 && 2 * N + 3 * 2 * npl * ta.ks * 8 <= 512 &&
             1024 + 2 * (size_t)3 * 2 * ta.slot_bytes + 512 <= 227 * 1024)
             ta.cpr = 2;
         // window slots: whole slot groups of npar x cpr (at least 2 groups),

@@ -86,28 +86,37 @@ def run_batch(binding, scenes, echo_np, **kw):
     return b, [im.cpu().numpy() for im in imgs]
 
 
-@pytest.mark.parametrize("kind", ["tensor_core", "persistent"])
+@pytest.mark.parametrize("kind", ["tensor_core", "tensor_core_per_scene", "persistent"])
 def test_batch_matches_single_scan_path_and_oracle(binding, data, kind):
-    # default: tensor-core back-projection per scene, scenes on parallel streams;
-    # persistent: the FP32 kernels in one persistent launch over all scenes
+    # default: the scenes' range tables on parallel streams, then ONE
+    # persistent tensor-core back-projection over every scene's blocks;
+    # tensor_core_per_scene: each scene's own tensor-core launches on parallel
+    # streams; persistent: the FP32 kernels in one persistent launch over all
+    # scenes (range tables and back-projections)
     scenes, echo_np = data
-    kw = {} if kind == "tensor_core" else dict(tile_u=16, block_config=1)
+    kw = {"tensor_core": {}, "tensor_core_per_scene": dict(tc_launch=2),
+          "persistent": dict(tile_u=16, block_config=1)}[kind]
     b, imgs = run_batch(binding, scenes, echo_np, **kw)
     info = b.info
-    assert info["persistent"] == (0 if kind == "tensor_core" else 1)
+    assert info["persistent"] == (0 if kind == "tensor_core_per_scene" else 1)
     assert info["n_scenes"] == len(scenes)
+    if kind == "tensor_core":
+        assert info["block_config"] == 4 and info["persistent_blocks"] > 0
     for i, w in enumerate(scenes):
         if kind == "tensor_core":
+            plan = binding.Plan.from_workload(w, block_config=4, one_block_per_sm=1)
+        elif kind == "tensor_core_per_scene":
             plan = binding.Plan.from_workload(w, block_config=4)
         else:
             plan = binding.Plan.from_workload(w, tile_u=info["tile_u"],
                                               block_config=info["block_config"])
         single = plan.execute(torch.from_numpy(echo_np[i]).cuda()).cpu().numpy()
-        if kind == "tensor_core":
-            # the batch runs each scene's stages one launch each; a plan's own
-            # execution splits the back-projection into its full waves and
-            # its last wave with part of the z-IFFT beside it (scene 0): the
-            # same arithmetic per output, so the images agree bit for bit
+        if kind != "persistent":
+            # the batch runs each scene's blocks (one persistent launch for
+            # all scenes, or one launch per scene); a plan's own execution
+            # may split its back-projection into its full waves and its last
+            # wave with part of the z-IFFT beside it: the same arithmetic per
+            # output, so the images agree bit for bit
             assert np.array_equal(imgs[i], single), i
         else:
             assert rel(imgs[i], single) < 1e-6, i
@@ -165,6 +174,23 @@ def test_unsatisfiable_wait_times_out_and_device_stays_usable(binding, data):
         b.execute([torch.from_numpy(e).cuda() for e in echo_np])
     assert ei.value.status == 8
     # the context is still good: a normal batch runs and matches
+    _, imgs = run_batch(binding, scenes[:1], echo_np[:1])
+    w = scenes[0]
+    ref = oracle.hybrid_exact(0, w.tx_xy, w.rx_xy, echo_np[0], w.z_scan, w.f_hz, w.n_pad,
+                              w.pix_xy(), w.axis("z"))
+    assert rel(imgs[0].reshape(w.grid["nz"], -1), ref) < TOL_FP32
+
+
+def test_persistent_tensor_core_wait_times_out(binding, data):
+    # the persistent tensor-core back-projection with a wait nothing completes
+    # (the test hook of pl_options) and a 2 ms budget: PL_ERR_TIMEOUT, the
+    # blocks stop taking items, and the device stays usable
+    scenes, echo_np = data
+    b = binding.Batch(scenes[:3], tc_debug_unsatisfiable=1, tc_wait_timeout_us=2000)
+    assert b.info["persistent"] == 1 and b.info["block_config"] == 4
+    with pytest.raises(binding.PolylineError) as ei:
+        b.execute([torch.from_numpy(e).cuda() for e in echo_np[:3]])
+    assert ei.value.status == 8
     _, imgs = run_batch(binding, scenes[:1], echo_np[:1])
     w = scenes[0]
     ref = oracle.hybrid_exact(0, w.tx_xy, w.rx_xy, echo_np[0], w.z_scan, w.f_hz, w.n_pad,
