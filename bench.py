@@ -317,7 +317,7 @@ def run_batch64(args, world, rank, local):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     res = {}
     for name, kw in (("fixed", dict(tile_u=16, block_config=1)), ("default", {}),
-                     ("autotuned", dict(autotune=True))):
+                     ("persistent_tc", dict(tc_launch=1)), ("autotuned", dict(autotune=True))):
         b = binding.Batch(scenes, **kw)
         imgs = b.execute(echos)
         for _ in range(max(0, args.warmup - 1)):
@@ -356,7 +356,8 @@ def run_batch64(args, world, rank, local):
             "scans_per_s": 64 / (best["ms_per_batch"] * 1e-3),
             "fixed_vs_autotuned": {k: {"ms_per_batch": v["ms_per_batch"], "value": v["value"],
                                        "tile_u": v["info"]["tile_u"],
-                                       "block_config": v["info"]["block_config"]}
+                                       "block_config": v["info"]["block_config"],
+                                       "persistent": v["info"]["persistent"]}
                                    for k, v in res.items()},
             "autotune_speedup": res["fixed"]["ms_per_batch"] / best["ms_per_batch"],
             "gpu_launches": best["info"]["launches_per_execute"] * args.steps,

@@ -352,14 +352,15 @@ pl_status pl_synth_echo(int n_chan, const double *tx_xy, const double *rx_xy,
  * A batch reconstructs n_scenes independent scans whose geometry, scan,
  * band and grid may all differ. pl_execute_batch replays one CUDA graph.
  *
- * Tensor cores (block_config 4, the default): the per-scene transforms over z
- * (Eq. 2) and range tables (Eq. 8a/19a), the scenes spread over parallel
- * streams, then ONE persistent tensor-core back-projection (Eq. 8b/19b), one
- * block per SM pulling every scene's back-projection blocks from a device
- * queue (largest scenes first; each scene in the one-block-per-SM layout,
- * K steps and planar or interleaved rows per scene), then the per-scene
- * inverse transforms (Eq. 9). tc_launch = 2 runs each scene's own
- * back-projection launch instead (on the parallel streams).
+ * Tensor cores (block_config 4, the default): each scene's chain -- transform
+ * over z (Eq. 2), range table (Eq. 8a/19a), back-projection (Eq. 8b/19b),
+ * inverse transform (Eq. 9) -- with the scenes spread over parallel streams,
+ * largest first. With tc_launch = 1 the back-projections are ONE persistent
+ * launch instead: the scenes' transforms and range tables on the parallel
+ * streams, then one block per SM pulling every scene's back-projection blocks
+ * from a device queue (largest scenes first; each scene in the
+ * one-block-per-SM layout, K steps and planar or interleaved rows per scene),
+ * then the inverse transforms on the parallel streams.
  *
  * FP32 kernels (block_config 1-3): the per-scene transforms over z, then ONE
  * persistent kernel that pulls work items from a device queue -- every
@@ -391,9 +392,10 @@ typedef struct {
                               * block than exists, so the bounded wait must expire (FP32
                               * persistent kernel; for the tensor-core kernels see
                               * pl_options.debug_unsatisfiable) */
-    int tc_launch;           /* block_config 4: 0 = one persistent back-projection when every
-                              * scene allows it (default), 1 = persistent (PL_ERR_UNSUPPORTED
-                              * if a scene does not allow it), 2 = each scene's own launch */
+    int tc_launch;           /* block_config 4: 1 = one persistent back-projection for every
+                              * scene (PL_ERR_UNSUPPORTED if a scene does not allow it);
+                              * 0 or 2 = each scene's own launches on the parallel streams
+                              * (default); with autotune both are timed */
     int reserved[6];
 } pl_batch_options;
 

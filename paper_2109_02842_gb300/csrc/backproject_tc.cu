@@ -517,10 +517,12 @@ k_backproject_tc_batch(const __grid_constant__ TcBatchMaps maps, CoefTable ct,
     __shared__ __align__(8) uint64_t dbg_bar;     // test hook: never completed
     __shared__ uint32_t tmem_slot;
     __shared__ int s_item, s_scene;
-    __shared__ BpDesc s_bp;
-    __shared__ TcArgs s_ta;
-    const int warp = threadIdx.x >> 5;
+    __shared__ int s_begin[kTcBatchMaxScenes];    // the scenes' first items
+    __shared__ __align__(16) BpDesc s_bp;
+    __shared__ __align__(16) TcArgs s_ta;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int n_bars = 0;          // barriers initialised for the last item (thread 0)
+    for (int i = threadIdx.x; i < n_scenes; i += blockDim.x) s_begin[i] = scenes[i].begin;
     if (threadIdx.x == 0) tc05::mbar_init(&dbg_bar, 1);
     if (warp == 0) {
         tc05::tmem_alloc(&tmem_slot, 512);
@@ -531,15 +533,31 @@ k_backproject_tc_batch(const __grid_constant__ TcBatchMaps maps, CoefTable ct,
     tc05::fence_after_sync();
     const uint32_t tmem = tmem_slot;
     for (;;) {
+        // the next item and its scene (binary search over the scenes' first
+        // items), then warp 0 copies the scene's descriptors
         if (threadIdx.x == 0) {
             int item = total;
             if (*(volatile int *)err == 0) item = atomicAdd(&counters[0], 1);
-            int sc = 0;
-            if (item < total) {
-                sc = n_scenes - 1;
-                while (sc > 0 && scenes[sc].begin > item) --sc;
-                s_bp = scenes[sc].bp;
-                s_ta = scenes[sc].ta;
+            int lo = 0, hi = n_scenes - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_begin[mid] <= item) lo = mid; else hi = mid - 1;
+            }
+            s_item = item;
+            s_scene = lo;
+        }
+        __syncthreads();
+        if (warp == 0 && s_item < total) {
+            const uint32_t *src_b = reinterpret_cast<const uint32_t *>(&scenes[s_scene].bp);
+            const uint32_t *src_t = reinterpret_cast<const uint32_t *>(&scenes[s_scene].ta);
+            uint32_t *dst_b = reinterpret_cast<uint32_t *>(&s_bp);
+            uint32_t *dst_t = reinterpret_cast<uint32_t *>(&s_ta);
+            for (int i = lane; i < (int)(sizeof(BpDesc) / 4); i += 32) dst_b[i] = src_b[i];
+            for (int i = lane; i < (int)(sizeof(TcArgs) / 4); i += 32) dst_t[i] = src_t[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s_item < total) {
                 // the previous item left every barrier with its phases
                 // complete and no arrival outstanding
                 for (int i = 0; i < n_bars; ++i) tc05::mbar_inval(&bars[i]);
@@ -553,8 +571,6 @@ k_backproject_tc_batch(const __grid_constant__ TcBatchMaps maps, CoefTable ct,
                 n_bars = tc_barriers(NSG, 3);
                 tc05::fence_mbar_init();
             }
-            s_item = item;
-            s_scene = sc;
         }
         tc05::fence_before_sync();
         __syncthreads();

@@ -421,8 +421,12 @@ pl_status enqueue(pl_batch *B, const void *const *echo, void *const *image, cuda
     const int n = (int)B->plans.size();
     pl_status s;
     PL_CUDA_RET(cudaMemsetAsync(B->d_counters, 0, sizeof(int) * (2 + n), st));
-    for (int i = 0; i < n; ++i)
-        if ((s = pl_stage_zfft(B->plans[i], (const float2 *)echo[i], st)) != PL_OK) return s;
+    // the FP32 persistent kernel: the z transforms first, on `st`; the
+    // tensor-core paths run each scene's z transform at the head of its chain
+    // on the parallel streams
+    if (B->persistent)
+        for (int i = 0; i < n; ++i)
+            if ((s = pl_stage_zfft(B->plans[i], (const float2 *)echo[i], st)) != PL_OK) return s;
     if (B->persistent) {
         PL_CUDA_RET(launch_batch(B->tile_u, B->block_config, B->bc, B->d_scenes, B->d_counters,
                                  B->smem, &B->pblocks, false, st));
@@ -440,8 +444,13 @@ pl_status enqueue(pl_batch *B, const void *const *echo, void *const *image, cuda
             for (int j = 0; j < n; ++j) {
                 const int i = B->order[j];
                 cudaStream_t as = B->aux[j % K];
-                s = phase == 0 ? pl_stage_range_table(B->plans[i], as)
-                               : pl_stage_zifft(B->plans[i], (float2 *)image[i], as);
+                if (phase == 0) {
+                    if ((s = pl_stage_zfft(B->plans[i], (const float2 *)echo[i], as)) != PL_OK)
+                        return s;
+                    s = pl_stage_range_table(B->plans[i], as);
+                } else {
+                    s = pl_stage_zifft(B->plans[i], (float2 *)image[i], as);
+                }
                 if (s != PL_OK) return s;
             }
             for (int k = 0; k < K; ++k) {
@@ -465,6 +474,7 @@ pl_status enqueue(pl_batch *B, const void *const *echo, void *const *image, cuda
         for (int j = 0; j < n; ++j) {
             const int i = B->order[j];
             cudaStream_t as = B->aux[j % K];
+            if ((s = pl_stage_zfft(B->plans[i], (const float2 *)echo[i], as)) != PL_OK) return s;
             if ((s = pl_stage_range_table(B->plans[i], as)) != PL_OK) return s;
             if ((s = pl_stage_backproject(B->plans[i], as)) != PL_OK) return s;
             if ((s = pl_stage_zifft(B->plans[i], (float2 *)image[i], as)) != PL_OK) return s;
@@ -572,7 +582,9 @@ pl_status pl_batch_create(pl_batch **out, int n, const pl_geometry *g, const pl_
     pl_batch *B = new (std::nothrow) pl_batch();
     if (!B) return pl_internal_fail(PL_ERR_OOM, "host allocation failed");
     B->n = n;
-    B->tc_mode = bo.tc_launch;
+    // tensor cores without autotuning: each scene's own launches unless the
+    // persistent launch is asked for (tc_launch 1); the autotuner times both
+    B->tc_mode = bo.tc_launch == 1 ? 1 : 2;
     auto bail = [&](pl_status st) { delete B; return st; };
     cudaError_t e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&B->d_counters, sizeof(int) * (2 + n));

@@ -88,13 +88,13 @@ def run_batch(binding, scenes, echo_np, **kw):
 
 @pytest.mark.parametrize("kind", ["tensor_core", "tensor_core_per_scene", "persistent"])
 def test_batch_matches_single_scan_path_and_oracle(binding, data, kind):
-    # default: the scenes' range tables on parallel streams, then ONE
+    # tensor_core: the scenes' range tables on parallel streams, then ONE
     # persistent tensor-core back-projection over every scene's blocks;
-    # tensor_core_per_scene: each scene's own tensor-core launches on parallel
-    # streams; persistent: the FP32 kernels in one persistent launch over all
-    # scenes (range tables and back-projections)
+    # tensor_core_per_scene (the default): each scene's own tensor-core
+    # launches on parallel streams; persistent: the FP32 kernels in one
+    # persistent launch over all scenes (range tables and back-projections)
     scenes, echo_np = data
-    kw = {"tensor_core": {}, "tensor_core_per_scene": dict(tc_launch=2),
+    kw = {"tensor_core": dict(tc_launch=1), "tensor_core_per_scene": {},
           "persistent": dict(tile_u=16, block_config=1)}[kind]
     b, imgs = run_batch(binding, scenes, echo_np, **kw)
     info = b.info
@@ -186,7 +186,7 @@ def test_persistent_tensor_core_wait_times_out(binding, data):
     # (the test hook of pl_options) and a 2 ms budget: PL_ERR_TIMEOUT, the
     # blocks stop taking items, and the device stays usable
     scenes, echo_np = data
-    b = binding.Batch(scenes[:3], tc_debug_unsatisfiable=1, tc_wait_timeout_us=2000)
+    b = binding.Batch(scenes[:3], tc_launch=1, tc_debug_unsatisfiable=1, tc_wait_timeout_us=2000)
     assert b.info["persistent"] == 1 and b.info["block_config"] == 4
     with pytest.raises(binding.PolylineError) as ei:
         b.execute([torch.from_numpy(e).cuda() for e in echo_np[:3]])
