@@ -220,6 +220,13 @@ cudaError_t launch_synth_echo(int n_chan, const double *tx_xy, const double *rx_
                               const double *pts, const double *amp, float2 *echo,
                               cudaStream_t st);
 
+// ---- nn_tc.cu: the convolution on the tensor cores (tcgen05) -------------------
+bool nn_conv3d_tc_supported(int D, int H, int W, int Cin, int Cout, const void *x, const void *w,
+                            const void *out);
+cudaError_t nn_conv3d_tc(const void *x, const void *w, const float *bias, void *out, int D, int H,
+                         int W, int Cin, int Cout, int Kp, int relu, int out_bf16,
+                         cudaStream_t st);
+
 // ---- nn.cu: learned fast path -------------------------------------------------
 cudaError_t nn_conv3d(const void *x, const void *w, const float *bias, void *out, int D, int H,
                       int W, int Cin, int Cout, int Kp, int relu, int out_bf16, cudaStream_t st);

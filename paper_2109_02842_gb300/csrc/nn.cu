@@ -10,7 +10,11 @@
 //
 // The convolution is an implicit GEMM on the tensor cores: out[v][co] =
 // sum_k A[v][k] B[k][co] with A the (never materialised) im2col matrix and B
-// the weights, as BF16 mma.sync m16n8k16 with FP32 accumulation. A block of 4
+// the weights. The shapes the network runs at full size (Cin a multiple of
+// 16, Cout 16..128, rows of 16..128 voxels) take the tcgen05 kernel of
+// nn_tc.cu; the others (the 3-channel input layer, the 2-channel head, small
+// or odd test volumes) the kernel below, BF16 mma.sync m16n8k16 with FP32
+// accumulation. A block of 4
 // warps owns 64 voxels x (8 NT) output channels; per 16-wide K chunk it
 // stages the A tile (one 32-byte row per voxel when Cin is a multiple of 16,
 // an element gather otherwise) and the B tile in shared memory.
@@ -469,6 +473,9 @@ inline unsigned nblk(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t)
 // ---------------------------------------------------------------------------
 cudaError_t nn_conv3d(const void *x, const void *w, const float *bias, void *out, int D, int H,
                       int W, int Cin, int Cout, int Kp, int relu, int out_bf16, cudaStream_t st) {
+    // the shapes the network runs at full size go to the tcgen05 kernel
+    if (nn_conv3d_tc_supported(D, H, W, Cin, Cout, x, w, out))
+        return nn_conv3d_tc(x, w, bias, out, D, H, W, Cin, Cout, Kp, relu, out_bf16, st);
     const int V = D * H * W;
     Vol vol{D, H, W};
     const auto *xb = (const __nv_bfloat16 *)x;

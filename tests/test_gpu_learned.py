@@ -44,9 +44,16 @@ def pack_w(w, kp):
     return out
 
 
+# the mma.sync kernel (odd sizes, 3 input or 2 output channels) and the
+# tcgen05 kernel (Cin a multiple of 16, Cout 16..128, rows of 16..128 voxels
+# with 128 / W dividing H: the shapes of the network at full size; their input
+# gradients, convolutions with swapped channel roles, take it too)
 @pytest.mark.parametrize("dims,cin,cout", [((5, 6, 7), 3, 16), ((4, 5, 9), 16, 2),
                                            ((8, 8, 8), 16, 32), ((6, 4, 4), 32, 64),
-                                           ((4, 4, 4), 64, 128), ((16, 16, 17), 16, 16)])
+                                           ((4, 4, 4), 64, 128), ((16, 16, 17), 16, 16),
+                                           ((4, 8, 16), 16, 16), ((3, 4, 32), 32, 64),
+                                           ((2, 2, 64), 64, 128), ((2, 1, 128), 128, 64),
+                                           ((5, 16, 16), 16, 32), ((2, 8, 16), 128, 32)])
 def test_conv3d_forward_and_gradients(L, dims, cin, cout):
     rng = np.random.default_rng(cin * 1000 + cout)
     x = bf16_round(rng.standard_normal(dims + (cin,)))
