@@ -465,9 +465,10 @@ pl_status pl_batch_destroy(pl_batch *batch);
  * pl_nn_check: the acceptance check of a learned correction corr (FP32
  *   [V][2], the network's output before pl_nn_residual): out (device FP32[3])
  *   = (number of non-finite entries of corr, sum of corr^2 over the finite
- *   ones, sum |gain img / s|^2); fixed-order reduction. The caller falls back
- *   to the plain reconstruction when out[0] > 0 or the correction is too
- *   large against the scaled cheap image.
+ *   ones, sum |gain img / s|^2); fixed-order reduction through a partial-sum
+ *   array inside the library, so two checks must not run at the same time on
+ *   different streams. The caller falls back to the plain reconstruction when
+ *   out[0] > 0 or the correction is too large against the scaled cheap image.
  * pl_nn_to_complex: img[v] = s (pred[v][0] + j pred[v][1]).
  * pl_nn_adam: one bias-corrected Adam step (Kingma & Ba 2015) on FP32
  *   parameters p with gradient g and moments m, v; refreshes the BF16 copy

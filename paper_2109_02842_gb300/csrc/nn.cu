@@ -311,6 +311,19 @@ __global__ void k_upsample2(const __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *
     y[i] = x[(((size_t)(zz / 2) * H + yy / 2) * W + xx / 2) * C + c];
 }
 
+// the same with 8 channels (16 bytes) per thread, for C a multiple of 8
+__global__ void k_upsample2_v8(const uint4 *__restrict__ x, uint4 *__restrict__ y, int D, int H,
+                               int W, int C8) {
+    const size_t n = (size_t)8 * D * H * W * C8;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % C8);
+    const size_t v = i / C8;
+    const int W2 = 2 * W, H2 = 2 * H;
+    const int xx = (int)(v % W2), yy = (int)((v / W2) % H2), zz = (int)(v / ((size_t)W2 * H2));
+    y[i] = x[(((size_t)(zz / 2) * H + yy / 2) * W + xx / 2) * C8 + c];
+}
+
 // gx[Z][Y][X] = sum of gy over the 8 children (gx has the small size D x H x W)
 __global__ void k_upsample2_bwd(const float *__restrict__ gy, float *__restrict__ gx, int D, int H,
                                 int W, int C) {
@@ -384,14 +397,20 @@ k_loss_sums(const float *__restrict__ pred, const float2 *__restrict__ tgt,
 // Acceptance check of a learned correction: out[0] = number of non-finite
 // entries of corr ([n][2]), out[1] = sum of corr^2 over the finite ones,
 // out[2] = sum |gain img / s|^2 (the scaled cheap image the correction is
-// added to). One block of 1024 threads, fixed-order tree.
-__global__ void __launch_bounds__(1024)
-k_check(const float *__restrict__ corr, const float2 *__restrict__ img,
-        const float *__restrict__ scale, float gain, size_t n, float *out) {
-    __shared__ float s_bad[1024], s_c[1024], s_i[1024];
+// added to). Two passes with fixed orders (reproducible sums): 256 blocks of
+// 256 threads write partial sums (block b takes the entries b, b + 256, ...
+// in tree order), one block adds the partials in block order.
+constexpr int kCheckBlocks = 256;
+// the partial sums: a file-scope device array (the check allocates nothing;
+// two checks running at the same time on different streams would race on it)
+__device__ float g_check_part[3 * kCheckBlocks];
+__global__ void __launch_bounds__(256)
+k_check_part(const float *__restrict__ corr, const float2 *__restrict__ img,
+             const float *__restrict__ scale, float gain, size_t n, float *part) {
+    __shared__ float s_bad[256], s_c[256], s_i[256];
     const float k = gain / (*scale > 0.f ? *scale : 1.f);
     float bad = 0.f, sc = 0.f, si = 0.f;
-    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+    for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (size_t)kCheckBlocks * 256) {
         const float a = corr[2 * i], b = corr[2 * i + 1];
         if (isfinite(a)) sc += a * a; else bad += 1.f;
         if (isfinite(b)) sc += b * b; else bad += 1.f;
@@ -402,7 +421,7 @@ k_check(const float *__restrict__ corr, const float2 *__restrict__ img,
     s_c[threadIdx.x] = sc;
     s_i[threadIdx.x] = si;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    for (int o = 128; o > 0; o >>= 1) {
         if ((int)threadIdx.x < o) {
             s_bad[threadIdx.x] += s_bad[threadIdx.x + o];
             s_c[threadIdx.x] += s_c[threadIdx.x + o];
@@ -411,10 +430,22 @@ k_check(const float *__restrict__ corr, const float2 *__restrict__ img,
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        out[0] = s_bad[0];
-        out[1] = s_c[0];
-        out[2] = s_i[0];
+        part[3 * blockIdx.x + 0] = s_bad[0];
+        part[3 * blockIdx.x + 1] = s_c[0];
+        part[3 * blockIdx.x + 2] = s_i[0];
     }
+}
+
+__global__ void __launch_bounds__(256) k_check_sum(const float *__restrict__ part, float *out) {
+    __shared__ float s[3][kCheckBlocks];
+    for (int q = 0; q < 3; ++q) s[q][threadIdx.x] = part[3 * threadIdx.x + q];
+    __syncthreads();
+    for (int o = kCheckBlocks / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int q = 0; q < 3; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) out[threadIdx.x] = s[threadIdx.x][0];
 }
 
 // grad = 2 (pred - target/s) / sum|target/s|^2
@@ -564,8 +595,14 @@ cudaError_t nn_resample(int op, const void *x, void *y, int D, int H, int W, int
                     (const __nv_bfloat16 *)x, (__nv_bfloat16 *)y, D, H, W, C); break;
         case 1: k_avgpool2_bwd<<<nblk((size_t)D * H * W * C), 256, 0, st>>>(
                     (const float *)x, (float *)y, D, H, W, C); break;
-        case 2: k_upsample2<<<nblk((size_t)8 * D * H * W * C), 256, 0, st>>>(
-                    (const __nv_bfloat16 *)x, (__nv_bfloat16 *)y, D, H, W, C); break;
+        case 2:
+            if (C % 8 == 0 && (uintptr_t)x % 16 == 0 && (uintptr_t)y % 16 == 0)
+                k_upsample2_v8<<<nblk((size_t)D * H * W * C), 256, 0, st>>>(
+                    (const uint4 *)x, (uint4 *)y, D, H, W, C / 8);
+            else
+                k_upsample2<<<nblk((size_t)8 * D * H * W * C), 256, 0, st>>>(
+                    (const __nv_bfloat16 *)x, (__nv_bfloat16 *)y, D, H, W, C);
+            break;
         case 3: k_upsample2_bwd<<<nblk((size_t)D * H * W * C), 256, 0, st>>>(
                     (const float *)x, (float *)y, D, H, W, C); break;
         default: return cudaErrorInvalidValue;
@@ -590,7 +627,11 @@ cudaError_t nn_loss(const float *pred, const void *target, const float *scale, f
 
 cudaError_t nn_check(const float *corr, const void *img, const float *scale, float gain, size_t n,
                      float *out, cudaStream_t st) {
-    k_check<<<1, 1024, 0, st>>>(corr, (const float2 *)img, scale, gain, n, out);
+    float *part = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void **)&part, g_check_part);
+    if (e != cudaSuccess) return e;
+    k_check_part<<<kCheckBlocks, 256, 0, st>>>(corr, (const float2 *)img, scale, gain, n, part);
+    k_check_sum<<<1, kCheckBlocks, 0, st>>>(part, out);
     return cudaGetLastError();
 }
 

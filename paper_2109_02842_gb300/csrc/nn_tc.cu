@@ -1,8 +1,8 @@
 // The learned path's 3 x 3 x 3 convolution on the fifth-generation tensor
 // cores (tcgen05), for the shapes the network runs at full size: Cin a
-// multiple of 16, Cout in {16, 32, 64, 128}, rows of W in {16, 32, 64, 128}
-// voxels with 128 / W dividing H. Other shapes (the 3-channel input layer,
-// the 2-channel head, odd sizes) keep the mma.sync kernel of nn.cu.
+// multiple of 16, Cout in 1..16 (the MMA's N = 16) or {32, 64, 128}, rows of W
+// in {16, 32, 64, 128} voxels with 128 / W dividing H. Other shapes (the
+// 3-channel input layer, odd sizes) keep the mma.sync kernel of nn.cu.
 //
 // Implicit GEMM: out[v][co] = act(bias[co] + sum_{tap, ci} x[v + off(tap)][ci]
 // w[co][tap Cin + ci]). A tile is 128 consecutive voxels (the MMA's M: 128 / W
@@ -82,7 +82,7 @@ k_conv3d_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
         tc05::fence_mbar_init();
         abort_flag = 0;
     }
-    for (int i = threadIdx.x; i < N; i += kThreads) s_bias[i] = bias ? bias[i] : 0.f;
+    for (int i = threadIdx.x; i < N; i += kThreads) s_bias[i] = (bias && i < a.Cout) ? bias[i] : 0.f;
     if (warp == 0) {
         tc05::tmem_alloc(&tmem_slot, kTmemCols);
         tc05::tmem_relinquish();
@@ -182,7 +182,17 @@ k_conv3d_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
                     f[i] = __uint_as_float(r[i]) + s_bias[c0 + i];
                     if (a.relu) f[i] = fmaxf(f[i], 0.f);
                 }
-                if (OUT_BF16) {
+                if (a.Cout < N) {
+                    // fewer real output channels than the MMA's N (the head):
+                    // the weight rows past Cout were zero-filled by the copy
+                    for (int i = 0; i < 16 && c0 + i < a.Cout; ++i) {
+                        if (OUT_BF16)
+                            reinterpret_cast<__nv_bfloat16 *>(out)[v * a.Cout + c0 + i] =
+                                __float2bfloat16(f[i]);
+                        else
+                            reinterpret_cast<float *>(out)[v * a.Cout + c0 + i] = f[i];
+                    }
+                } else if (OUT_BF16) {
                     uint32_t p[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -248,15 +258,27 @@ cudaError_t launch_n(const CUtensorMap &tx, const CUtensorMap &tw, const float *
     const size_t smem = 1024 + (size_t)kStages * (kABytes + N * 32);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+    // all of the unified L1 / shared storage as shared memory, so that several
+    // blocks share an SM (their copies and products overlap)
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0, per_sm = 0, smem_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     if (e != cudaSuccess) return e;
-    // tensor memory: at most 512 columns per SM across resident blocks
+    // blocks per SM: the occupancy limit, at least what shared memory allows
+    // (1 KB of static shared memory and 1 KB the system reserves per block),
+    // and at most what tensor memory allows (512 columns per SM)
     const int cols = 2 * N < 32 ? 32 : 2 * N;
+    const int by_smem = smem_sm / (int)(smem + 2048);
+    per_sm = per_sm < by_smem ? by_smem : per_sm;
     per_sm = per_sm < 1 ? 1 : per_sm;
+    if (per_sm > 2048 / kThreads) per_sm = 2048 / kThreads;
     if (per_sm * cols > 512) per_sm = 512 / cols;
     const int grid = a.tiles < sms * per_sm ? a.tiles : sms * per_sm;
     kern<<<grid, kThreads, smem, st>>>(tx, tw, bias, out, a);
@@ -268,7 +290,7 @@ cudaError_t launch_n(const CUtensorMap &tx, const CUtensorMap &tw, const float *
 bool nn_conv3d_tc_supported(int D, int H, int W, int Cin, int Cout, const void *x, const void *w,
                             const void *out) {
     const bool w_ok = W == 16 || W == 32 || W == 64 || W == 128;
-    return Cin % 16 == 0 && Cin >= 16 && (Cout == 16 || Cout == 32 || Cout == 64 || Cout == 128) &&
+    return Cin % 16 == 0 && Cin >= 16 && ((Cout >= 1 && Cout <= 16) || Cout == 32 || Cout == 64 || Cout == 128) &&
            w_ok && H % (128 / W) == 0 && D >= 1 && ((uintptr_t)x % 16) == 0 &&
            ((uintptr_t)w % 16) == 0 && ((uintptr_t)out % 16) == 0 && encode_fn() != nullptr;
 }
@@ -291,9 +313,11 @@ cudaError_t nn_conv3d_tc(const void *x, const void *w, const float *bias, void *
             return cudaErrorInvalidValue;
     }
     {
+        // a box of N rows (N = Cout, or 16 for fewer channels: the rows past
+        // Cout are out of bounds and land as zeros)
         const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)Cout};
         const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
-        const cuuint32_t box[2] = {16, (cuuint32_t)Cout};
+        const cuuint32_t box[2] = {16, (cuuint32_t)(Cout < 16 ? 16 : Cout)};
         const cuuint32_t es[2] = {1, 1};
         if (enc(&tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(w), dims, strides, box,
                 es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
@@ -308,7 +332,7 @@ cudaError_t nn_conv3d_tc(const void *x, const void *w, const float *bias, void *
     a.relu = relu;
     a.Cout = Cout;
     a.budget = 4ll << 30;
-    switch (Cout) {
+    switch (Cout < 16 ? 16 : Cout) {
         case 16: return out_bf16 ? launch_n<16, true>(tx, tw, bias, out, a, st)
                                  : launch_n<16, false>(tx, tw, bias, out, a, st);
         case 32: return out_bf16 ? launch_n<32, true>(tx, tw, bias, out, a, st)

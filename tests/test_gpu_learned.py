@@ -53,7 +53,8 @@ def pack_w(w, kp):
                                            ((4, 4, 4), 64, 128), ((16, 16, 17), 16, 16),
                                            ((4, 8, 16), 16, 16), ((3, 4, 32), 32, 64),
                                            ((2, 2, 64), 64, 128), ((2, 1, 128), 128, 64),
-                                           ((5, 16, 16), 16, 32), ((2, 8, 16), 128, 32)])
+                                           ((5, 16, 16), 16, 32), ((2, 8, 16), 128, 32),
+                                           ((4, 8, 16), 16, 2), ((2, 4, 32), 32, 5)])
 def test_conv3d_forward_and_gradients(L, dims, cin, cout):
     rng = np.random.default_rng(cin * 1000 + cout)
     x = bf16_round(rng.standard_normal(dims + (cin,)))
