@@ -6,6 +6,8 @@ captured with.
         [--precision 0] [--tile-u 0] [--repeat 4]
     python -m paper_2109_02842_gb300.run --workload batch64 [--repeat 2]
         (the 64 uneven scenes of the batched workload, default batch options)
+    python -m paper_2109_02842_gb300.run --workload conv:CIN:COUT [--repeat 10]
+        (one learned-path convolution on 96 x 128 x 128 voxels)
 """
 from __future__ import annotations
 
@@ -26,6 +28,30 @@ def main(argv=None):
     from . import binding, build, workloads as wl
     build.build()
     binding.load()
+    if a.workload.startswith("conv"):
+        # one learned-path convolution layer on 96 x 128 x 128 voxels:
+        # --workload conv:CIN:COUT
+        from . import learned as L
+        _, cin, cout = a.workload.split(":")
+        cin, cout = int(cin), int(cout)
+        D, H, W = 96, 128, 128
+        L.lib()
+        x = torch.randn(D * H * W, cin, device="cuda").to(torch.bfloat16)
+        kp = L.lib().pl_nn_padded_k(cin)
+        wt = (torch.randn(cout, kp, device="cuda") * 0.05).to(torch.bfloat16)
+        bias = torch.zeros(cout, device="cuda")
+        for _ in range(3):
+            L.conv3d(x, wt, bias, (D, H, W), cin, cout, True, True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(a.repeat):
+            L.conv3d(x, wt, bias, (D, H, W), cin, cout, True, True)
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / a.repeat
+        print(json.dumps({"workload": a.workload, "ms": ms,
+                          "tflops": 2 * D * H * W * 27 * cin * cout / ms / 1e9}))
+        return
     if a.workload == "batch64-stages":
         # the 64 scenes one after another through their own plans, with the
         # per-stage CUDA-event times summed over the scenes
