@@ -147,7 +147,21 @@ typedef struct {
      * batch's persistent back-projection runs every scene in; 0 = chosen by
      * size (default). */
     int one_block_per_sm;
-    int reserved[4];
+    /* check_nonfinite = 1: every execution first scans its echo for NaN or
+     * Inf (one read of the echo on the device, a flag in mapped host memory).
+     * pl_execute_host and pl_execute_host_stream then return
+     * PL_ERR_NONFINITE from the call itself; pl_execute, which does not
+     * synchronise, returns it from the next pl_execute / pl_execute_host call
+     * on the plan (after pl_execute, synchronise the stream before relying on
+     * that report). The image of an echo with such values is not defined.
+     * 0 = no scan (default). */
+    int check_nonfinite;
+    /* debug_fail_alloc (a test hook) = n > 0: the n-th device allocation that
+     * pl_plan_create makes for this plan fails as if the device were out of
+     * memory, so that the call returns PL_ERR_OOM and frees what it had
+     * allocated. 0 = off (default). */
+    int debug_fail_alloc;
+    int reserved[2];
 } pl_options;
 
 typedef struct pl_plan pl_plan;
@@ -414,14 +428,16 @@ typedef struct {
 } pl_batch_info;
 
 /* geoms, scans, freqs, grids: arrays of n_scenes host descriptors; opts may
- * be NULL or an array of n_scenes (precision and NUFFT fields are used; the
- * block shape comes from bopt). bopt may be NULL. */
+ * be NULL or an array of n_scenes (precision, NUFFT, wait and check_nonfinite
+ * fields are used; the block shape comes from bopt). bopt may be NULL. */
 pl_status pl_batch_create(pl_batch **out, int n_scenes, const pl_geometry *geoms,
                           const pl_scan *scans, const pl_freqs *freqs, const pl_grid *grids,
                           const pl_options *opts, const pl_batch_options *bopt);
 /* echo_dev[i], image_dev[i]: device buffers of scene i (layouts as in
  * pl_execute). The pointer arrays are host memory. Runs on `stream` and
- * synchronises it before returning (the wait status is read back). */
+ * synchronises it before returning (the status is read back: PL_ERR_TIMEOUT
+ * for an expired wait, PL_ERR_NONFINITE when a scene built with
+ * check_nonfinite had NaN or Inf in its echo). */
 pl_status pl_execute_batch(pl_batch *batch, const void *const *echo_dev,
                            void *const *image_dev, void *stream);
 pl_status pl_batch_get_info(const pl_batch *batch, pl_batch_info *info);

@@ -44,7 +44,8 @@ class PlGrid(ctypes.Structure):
 class PlOptions(ctypes.Structure):
     _fields_ = [("precision", _I), ("nufft_sigma", _D), ("nufft_w", _I), ("tile_u", _I),
                 ("block_config", _I), ("debug_unsatisfiable", _I), ("wait_timeout_us", _I),
-                ("one_block_per_sm", _I), ("reserved", _I * 4)]
+                ("one_block_per_sm", _I), ("check_nonfinite", _I), ("debug_fail_alloc", _I),
+                ("reserved", _I * 2)]
 
 
 class PlInfo(ctypes.Structure):
@@ -185,7 +186,7 @@ class _DevArray:
 def _descriptors(keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad, pair_tx,
                  pair_rx, radius, n_sections, chord_len, elem_section, precision, nufft_sigma,
                  nufft_w, tile_u, block_config, debug_unsatisfiable=0, wait_timeout_us=0,
-                 one_block_per_sm=0):
+                 one_block_per_sm=0, check_nonfinite=0, debug_fail_alloc=0):
     exy = _f64(elem_xy).reshape(-1, 2)
     sec = None if elem_section is None else _i32(elem_section)
     ptx = None if pair_tx is None else _i32(pair_tx)
@@ -202,7 +203,7 @@ def _descriptors(keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pa
                int(grid["nz"]))
     opt = PlOptions(int(precision), float(nufft_sigma), int(nufft_w), int(tile_u),
                     int(block_config), int(debug_unsatisfiable), int(wait_timeout_us),
-                    int(one_block_per_sm))
+                    int(one_block_per_sm), 1 if check_nonfinite else 0, int(debug_fail_alloc))
     return geom, scan, freqs, g, opt
 
 
@@ -218,14 +219,15 @@ class Plan:
     def __init__(self, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad=0,
                  pair_tx=None, pair_rx=None, radius=0.0, n_sections=0, chord_len=0.0,
                  elem_section=None, precision=0, nufft_sigma=0.0, nufft_w=0, tile_u=0,
-                 block_config=0, debug_unsatisfiable=0, wait_timeout_us=0, one_block_per_sm=0):
+                 block_config=0, debug_unsatisfiable=0, wait_timeout_us=0, one_block_per_sm=0,
+                 check_nonfinite=False, debug_fail_alloc=0):
         lib = load()
         self._keep = []
         geom, scan, freqs, g, opt = _descriptors(
             self._keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad, pair_tx,
             pair_rx, radius, n_sections, chord_len, elem_section, precision, nufft_sigma,
             nufft_w, tile_u, block_config, debug_unsatisfiable, wait_timeout_us,
-            one_block_per_sm)
+            one_block_per_sm, check_nonfinite, debug_fail_alloc)
         h = _P()
         _check(lib.pl_plan_create(ctypes.byref(h), geom, scan, freqs, g, opt))
         self._h = h
@@ -446,7 +448,8 @@ class Batch:
 
     def __init__(self, workloads, precision=0, nufft_sigma=0.0, nufft_w=0, tile_u=0,
                  block_config=0, autotune=False, wait_timeout_ms=0.0, debug_unsatisfiable=0,
-                 tc_launch=0, tc_debug_unsatisfiable=0, tc_wait_timeout_us=0):
+                 tc_launch=0, tc_debug_unsatisfiable=0, tc_wait_timeout_us=0,
+                 check_nonfinite=False):
         lib = load()
         self._keep = []
         n = len(workloads)
@@ -455,7 +458,7 @@ class Batch:
         for i, w in enumerate(workloads):
             G[i], S[i], F[i], R[i], O[i] = _descriptors(
                 self._keep, *_workload_args(w), precision, nufft_sigma, nufft_w, 0, 0,
-                tc_debug_unsatisfiable, tc_wait_timeout_us)
+                tc_debug_unsatisfiable, tc_wait_timeout_us, 0, check_nonfinite)
         bo = PlBatchOptions(int(tile_u), int(block_config), 1 if autotune else 0,
                             float(wait_timeout_ms), int(debug_unsatisfiable), int(tc_launch))
         h = _P()

@@ -522,9 +522,12 @@ pl_status run_batch(pl_batch *B, const void *const *echo, void *const *image, cu
     PL_CUDA_RET(cudaGraphLaunch(B->exec, st));
     PL_CUDA_RET(cudaStreamSynchronize(st));
     if (*B->h_flag) return pl_internal_fail(PL_ERR_TIMEOUT, "a bounded device-side wait expired");
-    for (pl_plan *p : B->plans)
-        if (pl_plan_take_timeout(p) != PL_OK) return PL_ERR_TIMEOUT;
-    return PL_OK;
+    pl_status first = PL_OK;
+    for (pl_plan *p : B->plans) {                // every plan's flags are taken
+        const pl_status ps = pl_plan_take_timeout(p);
+        if (first == PL_OK) first = ps;
+    }
+    return first;
 }
 
 // Time one batch execution (ms), best of `reps` after one warm-up.

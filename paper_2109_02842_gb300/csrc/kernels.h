@@ -21,14 +21,23 @@ cudaError_t launch_dft_strided(const float2 *in, float2 *out, int batch, int n_i
                                int out_rows, const float2 *T, float scale, cudaStream_t st,
                                const float2 *in2 = nullptr, int bf16_out = 0);
 
+// Status bit a kernel sets in the plan's mapped status word when the echo
+// holds NaN or Inf (the tensor-core kernels' expired waits use bits 0..5).
+constexpr int PL_FLAG_NONFINITE = 1 << 20;
+// Sets PL_FLAG_NONFINITE in *flag if any of the n complex values is NaN or Inf
+// (a test of the exponent bits; one read of the buffer).
+cudaError_t launch_check_finite(const float2 *x, size_t n, int *flag, cudaStream_t st);
+
 // ---- setup.cu --------------------------------------------------------------
 // Per k_z bin: kappa range over propagating frequencies; kc = centre (double
 // and as a float pair hi + lo), kspan = kappa_max - kappa_min (0 when every
 // frequency is evanescent). With group > 1 the range is taken over the group
 // of bins [group floor(u / group), + group) and every bin of it gets the
-// group's centre and span.
+// group's centre and span. band: scratch of 2 n_pad doubles (each bin's own
+// kappa range, the first pass).
 cudaError_t launch_setup_kz(int mode, int n_pad, double dz, int n_f, const double *k, int group,
-                            double *kc, float2 *kc_hl, double *kspan, cudaStream_t st);
+                            double *band, double *kc, float2 *kc_hl, double *kspan,
+                            cudaStream_t st);
 // Per (k_z, f): spreading position (fine cells) and source factor alpha.
 cudaError_t launch_setup_sources(const NufftDesc &d, double dz, const double *k,
                                  const double *kc, const double *gl_x, const double *gl_w,

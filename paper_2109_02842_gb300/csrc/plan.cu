@@ -190,10 +190,23 @@ long long wait_budget_cycles(int us) {
     return (long long)us * khz / 1000;
 }
 
+// Plan-time device allocations go through here: pl_options.debug_fail_alloc
+// = n makes the n-th one of the plan being built fail as if the device were
+// out of memory (a test hook for the PL_ERR_OOM path; nothing is allocated).
+thread_local int g_fail_alloc_countdown = 0;
+
+cudaError_t plan_malloc(void **p, size_t bytes) {
+    if (g_fail_alloc_countdown > 0 && --g_fail_alloc_countdown == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 template <typename T>
 cudaError_t dalloc(T **p, size_t count, size_t &total) {
     total += count * sizeof(T);
-    return cudaMalloc((void **)p, std::max<size_t>(count, 1) * sizeof(T));
+    return plan_malloc((void **)p, std::max<size_t>(count, 1) * sizeof(T));
 }
 
 }  // namespace
@@ -285,6 +298,17 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     if (o.precision < 0 || o.precision > 2) return fail(PL_ERR_ARG, "precision must be 0, 1 or 2");
     if (o.debug_unsatisfiable < 0 || o.debug_unsatisfiable > 2 || o.wait_timeout_us < 0)
         return fail(PL_ERR_ARG, "debug_unsatisfiable must be 0..2, wait_timeout_us >= 0");
+    if (o.check_nonfinite < 0 || o.check_nonfinite > 1 || o.debug_fail_alloc < 0)
+        return fail(PL_ERR_ARG, "check_nonfinite must be 0 or 1, debug_fail_alloc >= 0");
+    g_fail_alloc_countdown = o.debug_fail_alloc;
+    P->check_nonfinite = o.check_nonfinite != 0;
+    // the device-side status word (mapped host memory): expired waits of the
+    // tensor-core kernels, non-finite echo values
+    PL_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&P->h_err), sizeof(int), cudaHostAllocMapped),
+            "cudaHostAlloc");
+    *P->h_err = 0;
+    PL_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void **>(&P->d_err), P->h_err, 0),
+            "cudaHostGetDevicePointer");
 
     PL_CUDA(cudaGetDevice(&P->device), "cudaGetDevice");
     P->mode = g->mode;
@@ -339,6 +363,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     PL_CUDA(dalloc(&P->d_kc, P->Np, ws), "cudaMalloc");
     PL_CUDA(dalloc(&P->d_kchl, P->Np, ws), "cudaMalloc");
     PL_CUDA(dalloc(&P->d_kspan, P->Np, ws), "cudaMalloc");
+    PL_CUDA(dalloc(&P->d_kband, 2 * (size_t)P->Np, ws), "cudaMalloc");
     PL_CUDA(cudaMemcpy(P->d_chxy, chxy.data(), chxy.size() * 8, cudaMemcpyHostToDevice), "copy");
     PL_CUDA(cudaMemcpy(P->d_k, k.data(), k.size() * 8, cudaMemcpyHostToDevice), "copy");
 
@@ -347,8 +372,8 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     // shares one centre per block of `group` bins); kmax = the widest span
     double kmax = 0.0;
     auto band = [&](int group) -> pl_status {
-        PL_CUDA(launch_setup_kz(P->mode, P->Np, P->dzs, P->M, P->d_k, group, P->d_kc,
-                                P->d_kchl, P->d_kspan, st), "setup_kz");
+        PL_CUDA(launch_setup_kz(P->mode, P->Np, P->dzs, P->M, P->d_k, group, P->d_kband,
+                                P->d_kc, P->d_kchl, P->d_kspan, st), "setup_kz");
         std::vector<double> kspan(P->Np);
         PL_CUDA(cudaMemcpy(kspan.data(), P->d_kspan, P->Np * 8, cudaMemcpyDeviceToHost), "copy");
         kmax = 0.0;
@@ -421,7 +446,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
             d.L = 0;
             BpDesc gb = make_bp(P);
             int *d_stats = nullptr;
-            PL_CUDA(cudaMalloc(&d_stats, 2 * sizeof(int)), "cudaMalloc");
+            PL_CUDA(plan_malloc(reinterpret_cast<void **>(&d_stats), 2 * sizeof(int)), "cudaMalloc");
             cudaError_t e = cudaMemset(d_stats, 0, 2 * sizeof(int));
             if (e == cudaSuccess) e = launch_setup_tile_geo_tc(gb, P->d_chxy, P->d_tgeo, d_stats, st);
             if (e == cudaSuccess) e = cudaMemcpy(stats, d_stats, sizeof(stats), cudaMemcpyDeviceToHost);
@@ -578,7 +603,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     else
         P->table_bytes = (size_t)P->C * L * ((P->Np + 1) / 2) * (P->precision >= 1 ? 8 : 16);
     ws += P->table_bytes;
-    PL_CUDA(cudaMalloc(&P->d_table, P->table_bytes), "cudaMalloc");
+    PL_CUDA(plan_malloc(&P->d_table, P->table_bytes), "cudaMalloc");
     if (P->block_config == 4) {
         PL_CUDA(cudaMemset(P->d_table, 0, P->table_bytes), "cudaMemset");
         // TMA map of the table [c][hi/lo][row][column] (BF16): a box is 64
@@ -595,11 +620,6 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
                                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-        PL_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&P->h_err), sizeof(int), cudaHostAllocMapped),
-                "cudaHostAlloc");
-        *P->h_err = 0;
-        PL_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void **>(&P->d_err), P->h_err, 0),
-                "cudaHostGetDevicePointer");
         // the range table as exact sums on the tensor cores (one or two
         // 64-frequency atoms: up to 128 frequencies; table rows up to 256),
         // else the NUFFT
@@ -636,10 +656,10 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
             const size_t nE = (size_t)P->Np * 4 * ra.Lp * ra.Kp;
             const size_t nA = (size_t)P->Np * 4 * P->C * ra.Kp;
             const size_t nprod = (size_t)P->Np * 2 * ra.nh * ra.Lh * ((P->C + 127) / 128 * 128);
-            PL_CUDA(cudaMalloc(&P->d_rtE, nE * 2), "cudaMalloc");
-            PL_CUDA(cudaMalloc(&P->d_rtA, nA * 2), "cudaMalloc");
+            PL_CUDA(plan_malloc(&P->d_rtE, nE * 2), "cudaMalloc");
+            PL_CUDA(plan_malloc(&P->d_rtA, nA * 2), "cudaMalloc");
             PL_CUDA(cudaMemset(P->d_rtA, 0, nA * 2), "cudaMemset");   // frequencies >= M stay 0
-            PL_CUDA(cudaMalloc(&P->d_rtprod, nprod * 4), "cudaMalloc");
+            PL_CUDA(plan_malloc(&P->d_rtprod, nprod * 4), "cudaMalloc");
             ws += nE * 2 + nA * 2 + nprod * 4;
             PL_CUDA(launch_setup_rt_E(d, P->dzs, P->d_k, P->d_kc, P->d_alpha, ra.Lp, ra.Kp,
                                       P->d_rtE, st),
@@ -718,6 +738,9 @@ static pl_status stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st, boo
 }
 
 pl_status pl_stage_zfft(pl_plan *P, const float2 *echo, cudaStream_t st) {
+    if (P->check_nonfinite)
+        PL_CUDA(launch_check_finite(echo, (size_t)P->C * P->N * P->M, P->d_err, st),
+                "check_finite");
     return stage_zfft(P, echo, st, P->block_config == 4 && P->rt_tc, P->nd.s_bf16);
 }
 
@@ -1000,6 +1023,7 @@ pl_status pl_plan_create(pl_plan **out, const pl_geometry *geom, const pl_scan *
         pl_plan *P = new (std::nothrow) pl_plan();
         if (!P) return fail(PL_ERR_OOM, "host allocation failed");
         s = build_plan(P, geom, scan, freqs, grid, &ot);
+        g_fail_alloc_countdown = 0;
         if (s == PL_OK) {
             store_inputs(P, geom, scan, freqs, grid, opt);
             *out = P;
@@ -1011,6 +1035,7 @@ pl_status pl_plan_create(pl_plan **out, const pl_geometry *geom, const pl_scan *
     pl_plan *P = new (std::nothrow) pl_plan();
     if (!P) return fail(PL_ERR_OOM, "host allocation failed");
     s = build_plan(P, geom, scan, freqs, grid, &o);
+    g_fail_alloc_countdown = 0;
     if (s != PL_OK) {
         delete P;
         return s;
@@ -1032,6 +1057,8 @@ static pl_status take_device_timeout(pl_plan *plan) {
     if (!plan->h_err || *(volatile int *)plan->h_err == 0) return PL_OK;
     const int bits = *(volatile int *)plan->h_err;
     *(volatile int *)plan->h_err = 0;
+    if (bits & PL_FLAG_NONFINITE)
+        return fail(PL_ERR_NONFINITE, "the echo held NaN or Inf values (check_nonfinite)");
     char msg[96];
     std::snprintf(msg, sizeof msg,
                   "a bounded wait of the tensor-core kernels timed out (flags 0x%x)", bits);
@@ -1071,7 +1098,8 @@ pl_status pl_execute_bp_direct(pl_plan *plan, const void *echo_dev, void *image_
 
 pl_status pl_execute_host(pl_plan *plan, const void *echo_host, void *image_host, void *stream) {
     if (!plan || !echo_host || !image_host) return fail(PL_ERR_ARG, "NULL argument");
-    if (take_device_timeout(plan) != PL_OK) return PL_ERR_TIMEOUT;
+    pl_status s0 = take_device_timeout(plan);
+    if (s0 != PL_OK) return s0;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t in_bytes = (size_t)plan->C * plan->N * plan->M * sizeof(float2);
     const size_t out_bytes =
@@ -1097,7 +1125,8 @@ pl_status pl_execute_host_stream(pl_plan *plan, int n_scans, const void *const *
         return fail(PL_ERR_ARG, "bad pl_execute_host_stream arguments");
     for (int i = 0; i < n_scans; ++i)
         if (!echo_host[i] || !image_host[i]) return fail(PL_ERR_ARG, "NULL scan buffer");
-    if (take_device_timeout(plan) != PL_OK) return PL_ERR_TIMEOUT;
+    pl_status s0 = take_device_timeout(plan);
+    if (s0 != PL_OK) return s0;
     if (n_scans == 0) return PL_OK;
     const size_t in_bytes = (size_t)plan->C * plan->N * plan->M * sizeof(float2);
     const size_t out_bytes =
@@ -1131,15 +1160,17 @@ pl_status pl_execute_host_stream(pl_plan *plan, int n_scans, const void *const *
     if (n_scans >= 2) {
         if (!plan->twin) {
             const PlanInputs &in = plan->inputs;
+            pl_options to = in.o;
+            to.debug_fail_alloc = 0;            // the test hook covers the caller's plan only
             pl_plan *T = nullptr;
             const pl_status s = pl_plan_create(&T, &in.g, &in.s, &in.f, &in.gr,
-                                               in.has_opts ? &in.o : nullptr);
+                                               in.has_opts ? &to : nullptr);
             if (s != PL_OK) return s;
             plan->twin = T;
             plan->workspace += T->workspace;
             PL_CUDA(cudaStreamCreateWithFlags(&plan->s_twin, cudaStreamNonBlocking), "stream");
         }
-        if (take_device_timeout(plan->twin) != PL_OK) return PL_ERR_TIMEOUT;
+        if ((s0 = take_device_timeout(plan->twin)) != PL_OK) return s0;
         pp[1] = plan->twin;
         sc[1] = plan->s_twin;
     }
@@ -1173,7 +1204,10 @@ pl_status pl_execute_host_stream(pl_plan *plan, int n_scans, const void *const *
     }
     PL_CUDA(cudaStreamWaitEvent(st, plan->ev_out[(n_scans - 1) & 1], 0), "wait");
     PL_CUDA(cudaStreamSynchronize(st), "execute_host_stream");
-    if (plan->twin && take_device_timeout(plan->twin) != PL_OK) return PL_ERR_TIMEOUT;
+    if (plan->twin && (s0 = take_device_timeout(plan->twin)) != PL_OK) {
+        take_device_timeout(plan);                  // both plans' flags are taken
+        return s0;
+    }
     return take_device_timeout(plan);
 }
 

@@ -38,8 +38,11 @@ struct pl_plan {
     int R = 0;
     TcArgs tc{};           // tensor-core variant (block_config 4)
     CUtensorMap tmap{};    // its TMA map of the range table
-    int *h_err = nullptr;  // its timeout flags (mapped host memory) and device alias
+    // status word in mapped host memory and its device alias: expired waits of
+    // the tensor-core kernels, PL_FLAG_NONFINITE from the echo scan
+    int *h_err = nullptr;
     int *d_err = nullptr;
+    bool check_nonfinite = false;   // scan every echo for NaN / Inf first
     // its range table as exact sums on the tensor cores (range_table_tc.cu)
     bool rt_tc = false;
     RtTcArgs rt{};
@@ -62,6 +65,7 @@ struct pl_plan {
     FftPlan fineplan{};
     // device memory
     double *d_chxy = nullptr, *d_k = nullptr, *d_kc = nullptr, *d_kspan = nullptr;
+    double *d_kband = nullptr;
     double *d_glx = nullptr, *d_glw = nullptr;
     float *d_xg = nullptr, *d_dec = nullptr;
     float2 *d_kchl = nullptr;
@@ -99,7 +103,7 @@ struct pl_plan {
     size_t ev_next = 0;
 
     ~pl_plan() {
-        void *ptrs[] = {d_chxy, d_k,    d_kc,   d_kspan, d_glx,  d_glw,     d_kchl, d_tgeo,
+        void *ptrs[] = {d_chxy, d_k,    d_kc,   d_kspan, d_kband, d_glx,  d_glw,     d_kchl, d_tgeo,
                         d_xg,   d_dec,  d_alpha, d_twz,  d_twfine, d_Tfwd, d_Tinv,
                         d_S,    d_G,    d_table, d_echo_in, d_img_out, d_kap, d_zs,
                         d_kff,  d_wum,  d_chff, d_rtE, d_rtA, d_rtprod, d_echo_in2, d_img_out2};
@@ -136,8 +140,9 @@ struct pl_plan {
         if (e_ != cudaSuccess) return pl_internal_cuda_fail(e_, #call);     \
     } while (0)
 
-// PL_ERR_TIMEOUT (and clear the flags) if a bounded device wait of an earlier
-// execution of the plan ran out, else PL_OK.
+// PL_ERR_NONFINITE if the echo scan of an earlier execution of the plan found
+// NaN / Inf, else PL_ERR_TIMEOUT if one of its bounded device waits ran out,
+// else PL_OK; the flags are cleared.
 pl_status pl_plan_take_timeout(pl_plan *plan);
 
 // Launch one stage of a plan on `st` (no timing events, no synchronisation).

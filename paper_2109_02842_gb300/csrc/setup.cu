@@ -38,23 +38,38 @@ __device__ __forceinline__ double kappa_sq(int mode, double k, double kz) {
     return mode == 0 ? 4.0 * k * k - kz * kz : k * k - 0.25 * kz * kz;
 }
 
-__global__ void k_setup_kz(int mode, int n_pad, double dz, int n_f, const double *k, int group,
-                           double *kc, float2 *kc_hl, double *kspan) {
+// Pass 1: the live kappa band [lo, hi] of every bin (lo < 0: no live term).
+__global__ void k_setup_kz_bins(int mode, int n_pad, double dz, int n_f, const double *k,
+                                double *band) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n_pad) return;
+    const double kz = kz_of(u, n_pad, dz);
+    double lo = -1.0, hi = -1.0;
+    for (int m = 0; m < n_f; ++m) {
+        const double q = kappa_sq(mode, k[m], kz);
+        if (q <= 0.0) continue;
+        const double kap = sqrt(q);
+        if (lo < 0.0) { lo = hi = kap; }
+        lo = fmin(lo, kap);
+        hi = fmax(hi, kap);
+    }
+    band[2 * u] = lo;
+    band[2 * u + 1] = hi;
+}
+
+// Pass 2: centre and span of the band of every bin's group of `group` bins.
+__global__ void k_setup_kz(int n_pad, int group, const double *band, double *kc, float2 *kc_hl,
+                           double *kspan) {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n_pad) return;
     const int g0 = u / group * group, g1 = min(g0 + group, n_pad);
     double lo = 0.0, hi = 0.0;
     bool any = false;
     for (int v = g0; v < g1; ++v) {
-        const double kz = kz_of(v, n_pad, dz);
-        for (int m = 0; m < n_f; ++m) {
-            const double q = kappa_sq(mode, k[m], kz);
-            if (q <= 0.0) continue;
-            const double kap = sqrt(q);
-            if (!any) { lo = hi = kap; any = true; }
-            lo = fmin(lo, kap);
-            hi = fmax(hi, kap);
-        }
+        if (band[2 * v] < 0.0) continue;
+        if (!any) { lo = band[2 * v]; hi = band[2 * v + 1]; any = true; }
+        lo = fmin(lo, band[2 * v]);
+        hi = fmax(hi, band[2 * v + 1]);
     }
     kc[u] = any ? 0.5 * (lo + hi) : 0.0;
     const float kh = (float)kc[u];
@@ -264,9 +279,11 @@ cudaError_t launch_setup_exact(int mode, int n_pad, double dz, int n_f, const do
 }
 
 cudaError_t launch_setup_kz(int mode, int n_pad, double dz, int n_f, const double *k, int group,
-                            double *kc, float2 *kc_hl, double *kspan, cudaStream_t st) {
-    k_setup_kz<<<blocks(n_pad, 128), 128, 0, st>>>(mode, n_pad, dz, n_f, k, group < 1 ? 1 : group,
-                                                   kc, kc_hl, kspan);
+                            double *band, double *kc, float2 *kc_hl, double *kspan,
+                            cudaStream_t st) {
+    k_setup_kz_bins<<<blocks(n_pad, 128), 128, 0, st>>>(mode, n_pad, dz, n_f, k, band);
+    k_setup_kz<<<blocks(n_pad, 128), 128, 0, st>>>(n_pad, group < 1 ? 1 : group, band, kc, kc_hl,
+                                                   kspan);
     return cudaGetLastError();
 }
 

@@ -14,6 +14,10 @@
 // phase matrix.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <cstdint>
+
+
 #include "common.cuh"
 #include "kernels.h"
 #include "stockham.cuh"
@@ -278,5 +282,58 @@ cudaError_t launch_dft_strided(const float2 *in, float2 *out, int batch, int n_i
                                const float2 *in2, int bf16_out) {
     dim3 grid((I + 31) / 32, (out_rows + 31) / 32, batch);
     k_dft_strided<<<grid, 256, 0, st>>>(in, in2, out, n_in, I, out_rows, T, scale, bf16_out);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// Exponent all ones <=> NaN or Inf, decided on the bits (no float compare).
+__device__ __forceinline__ bool nonfinite_bits(float v) {
+    return (__float_as_uint(v) & 0x7f800000u) == 0x7f800000u;
+}
+
+__global__ void __launch_bounds__(256) k_check_finite(const float4 *__restrict__ x4, size_t n4,
+                                                     const float2 *__restrict__ tail, int n_tail,
+                                                     int *flag) {
+    bool bad = false;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float4 v = __ldg(&x4[i]);
+        bad |= nonfinite_bits(v.x) | nonfinite_bits(v.y) | nonfinite_bits(v.z) |
+               nonfinite_bits(v.w);
+    }
+    if (blockIdx.x == 0 && (int)threadIdx.x < n_tail) {
+        const float2 v = tail[threadIdx.x];
+        bad |= nonfinite_bits(v.x) | nonfinite_bits(v.y);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, PL_FLAG_NONFINITE);
+}
+
+}  // namespace
+
+cudaError_t launch_check_finite(const float2 *x, size_t n, int *flag, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    if (!x || !flag) return cudaErrorInvalidValue;
+    // float4 body from the first 16-byte boundary; the rest (at most two
+    // leading or one trailing complex value) read as float2
+    const size_t lead = ((uintptr_t)x % 16) ? 1 : 0;       // x is 8-byte aligned
+    if (lead && n == 1) {
+        k_check_finite<<<1, 32, 0, st>>>(nullptr, 0, x, 1, flag);
+        return cudaGetLastError();
+    }
+    const size_t body = (n - lead) / 2;                      // float4 = two complex values
+    const size_t rest = n - lead - 2 * body;                 // 0 or 1
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const size_t want = (body + 255) / 256;
+    const int blocks = (int)std::max<size_t>(1, std::min<size_t>(want, (size_t)sms * 8));
+    if (lead) {
+        k_check_finite<<<1, 32, 0, st>>>(nullptr, 0, x, 1, flag);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_check_finite<<<blocks, 256, 0, st>>>(reinterpret_cast<const float4 *>(x + lead), body,
+                                           x + lead + 2 * body, (int)rest, flag);
     return cudaGetLastError();
 }

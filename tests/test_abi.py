@@ -73,3 +73,34 @@ def test_product_path_does_not_import_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "liboracle" not in txt, f
+
+
+STRUCTS = {"PlGeometry": "pl_geometry", "PlScan": "pl_scan", "PlFreqs": "pl_freqs",
+           "PlGrid": "pl_grid", "PlOptions": "pl_options", "PlInfo": "pl_info",
+           "PlBatchOptions": "pl_batch_options", "PlBatchInfo": "pl_batch_info",
+           "PlDesignInfo": "pl_design_info"}
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    # a C program compiled against the header prints sizeof and offsetof of
+    # every field the ctypes mirror declares; both must agree byte for byte
+    from paper_2109_02842_gb300 import binding
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "polyline.h"',
+             "int main(void) {"]
+    expect = []
+    for py, c in STRUCTS.items():
+        cls = getattr(binding, py)
+        lines.append('printf("%%zu\\n", sizeof(%s));' % c)
+        expect.append(ctypes.sizeof(cls))
+        for name, _ in cls._fields_:
+            lines.append('printf("%%zu\\n", offsetof(%s, %s));' % (c, name))
+            expect.append(getattr(cls, name).offset)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert got == expect
