@@ -136,8 +136,9 @@ typedef struct {
     /* Bounded waits of the tensor-core kernels (block_config 4):
      * wait_timeout_us = how long one wait may last before it gives up
      * (0 = about 2 s); debug_unsatisfiable (a test hook) = 1 makes the
-     * back-projection's MMA warp, 2 the range-table kernel's first stage,
-     * wait first on a barrier nothing completes, so that the wait runs out
+     * back-projection's MMA warp, 2 the range-table kernel's first stage, 3
+     * the MMA warp of the inverse z transform at off-grid heights, wait first
+     * on a barrier nothing completes, so that the wait runs out
      * and the kernel takes its exit path (the next pl_execute returns
      * PL_ERR_TIMEOUT; no device fault, the context stays usable). */
     int debug_unsatisfiable;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 
@@ -27,6 +28,36 @@ constexpr int PL_FLAG_NONFINITE = 1 << 20;
 // Sets PL_FLAG_NONFINITE in *flag if any of the n complex values is NaN or Inf
 // (a test of the exponent bits; one read of the buffer).
 cudaError_t launch_check_finite(const float2 *x, size_t n, int *flag, cudaStream_t st);
+
+// ---- zidft_tc.cu -----------------------------------------------------------
+// Inverse z transform at off-grid heights on the tensor cores: image[z][p] =
+// sum_u T[z][u] (G[u][p] + G2[u][p]), T from a BF16 hi/lo table (scale folded in).
+struct ZidftTcArgs {
+    int n_in;          // N_p: rows (bins) of G
+    int ksteps;        // ceil(n_in / 16)
+    int n_cols;        // columns (pixels) of G and of the image
+    int ld, out_ld;    // row strides of G and of the image, elements
+    int nz;            // output heights
+    int nzc;           // heights per block (the MMA's N, multiple of 16, <= 96)
+    int zchunks;       // ceil(nz / nzc)
+    int nzp;           // table rows per plane (zchunks nzc)
+    int plane_bytes;   // shared memory of one plane of a stage
+    long long budget;  // wait budget, SM clock cycles
+    int dbg_wait;      // test hook: the MMA warp first waits on a barrier nothing completes
+};
+typedef CUresult (*TmapEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+ZidftTcArgs zidft_tc_shape(int n_in, int n_cols, int nz);
+size_t zidft_tc_table_elems(const ZidftTcArgs &a);       // BF16 elements of the table
+cudaError_t launch_zidft_tc_table(const ZidftTcArgs &a, const float2 *T, float scale,
+                                  __nv_bfloat16 *tb, cudaStream_t st);
+bool zidft_tc_make_map(const ZidftTcArgs &a, const __nv_bfloat16 *tb, CUtensorMap *map,
+                       TmapEncodeFn enc);
+size_t zidft_tc_smem_bytes(const ZidftTcArgs &a);
+cudaError_t launch_zidft_tc(const ZidftTcArgs &a, const CUtensorMap *map, const float2 *G,
+                            const float2 *G2, float2 *out, int *err, cudaStream_t st);
 
 // ---- setup.cu --------------------------------------------------------------
 // Per k_z bin: kappa range over propagating frequencies; kc = centre (double

@@ -296,8 +296,8 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         return fail(PL_ERR_ARG, "tile_u must be 0, 8, 16, 20 or 24");
     }
     if (o.precision < 0 || o.precision > 2) return fail(PL_ERR_ARG, "precision must be 0, 1 or 2");
-    if (o.debug_unsatisfiable < 0 || o.debug_unsatisfiable > 2 || o.wait_timeout_us < 0)
-        return fail(PL_ERR_ARG, "debug_unsatisfiable must be 0..2, wait_timeout_us >= 0");
+    if (o.debug_unsatisfiable < 0 || o.debug_unsatisfiable > 3 || o.wait_timeout_us < 0)
+        return fail(PL_ERR_ARG, "debug_unsatisfiable must be 0..3, wait_timeout_us >= 0");
     if (o.check_nonfinite < 0 || o.check_nonfinite > 1 || o.debug_fail_alloc < 0)
         return fail(PL_ERR_ARG, "check_nonfinite must be 0 or 1, debug_fail_alloc >= 0");
     g_fail_alloc_countdown = o.debug_fail_alloc;
@@ -582,6 +582,24 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         PL_CUDA(dalloc(&P->d_Tinv, (size_t)gr->nz * P->Np, ws), "cudaMalloc");
         PL_CUDA(launch_dft_matrix_inv(P->Np, P->dzs, P->z0s, gr->nz, gr->z0, gr->dz, P->d_Tinv, st),
                 "dft_matrix_inv");
+        if (P->block_config == 4 && encode_tiled_fn()) {
+            // tensor-core plans: the transform's products on the tensor cores
+            // too (BF16 hi/lo table of T / N_p)
+            ZidftTcArgs &zt = P->zt;
+            zt = zidft_tc_shape(P->Np, gr->nx * gr->ny, gr->nz);
+            zt.budget = wait_budget_cycles(o.wait_timeout_us);
+            zt.dbg_wait = o.debug_unsatisfiable == 3 ? 1 : 0;
+            const size_t nb = zidft_tc_table_elems(zt) * 2;
+            PL_CUDA(plan_malloc(&P->d_TinvB, nb), "cudaMalloc");
+            ws += nb;
+            PL_CUDA(launch_zidft_tc_table(zt, P->d_Tinv, (float)(1.0 / P->Np),
+                                          (__nv_bfloat16 *)P->d_TinvB, st),
+                    "zidft_tc_table");
+            if (!zidft_tc_make_map(zt, (const __nv_bfloat16 *)P->d_TinvB, &P->tmapZ,
+                                   encode_tiled_fn()))
+                return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled failed (z transform table)");
+            P->zidft_tc = true;
+        }
     }
 
     // per (pixel tile, channel) geometry of the back-projection
@@ -779,6 +797,8 @@ static pl_status stage_zifft(pl_plan *P, float2 *image, cudaStream_t st, int par
         PL_CUDA(launch_fft_strided(P->d_G, image, 1, P->Np, P2, P->zplan, P->d_twz, +1,
                                    1.0f / P->Np, P->grid.nz, P->inv_off, st, nullptr, 0, G2),
                 "zifft");
+    else if (P->zidft_tc)
+        PL_CUDA(launch_zidft_tc(P->zt, &P->tmapZ, P->d_G, G2, image, P->d_err, st), "zidft_tc");
     else
         PL_CUDA(launch_dft_strided(P->d_G, image, 1, P->Np, P2, P->grid.nz, P->d_Tinv,
                                    1.0f / P->Np, st, G2), "zidft");

@@ -72,6 +72,12 @@ struct pl_plan {
     TileGeo *d_tgeo = nullptr;
     float2 *d_alpha = nullptr, *d_twz = nullptr, *d_twfine = nullptr;
     float2 *d_Tfwd = nullptr, *d_Tinv = nullptr;
+    // the inverse transform at off-grid heights on the tensor cores (tensor-core
+    // plans): its shape, BF16 table and TMA map
+    bool zidft_tc = false;
+    ZidftTcArgs zt{};
+    void *d_TinvB = nullptr;
+    CUtensorMap tmapZ{};
     float2 *d_S = nullptr, *d_G = nullptr;
     void *d_table = nullptr;
     size_t table_bytes = 0;
@@ -106,7 +112,8 @@ struct pl_plan {
         void *ptrs[] = {d_chxy, d_k,    d_kc,   d_kspan, d_kband, d_glx,  d_glw,     d_kchl, d_tgeo,
                         d_xg,   d_dec,  d_alpha, d_twz,  d_twfine, d_Tfwd, d_Tinv,
                         d_S,    d_G,    d_table, d_echo_in, d_img_out, d_kap, d_zs,
-                        d_kff,  d_wum,  d_chff, d_rtE, d_rtA, d_rtprod, d_echo_in2, d_img_out2};
+                        d_kff,  d_wum,  d_chff, d_rtE, d_rtA, d_rtprod, d_echo_in2, d_img_out2,
+                        d_TinvB};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         for (cudaEvent_t e : {ev_in[0], ev_in[1], ev_done[0], ev_done[1], ev_out[0], ev_out[1],

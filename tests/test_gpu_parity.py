@@ -147,6 +147,26 @@ def test_ragged_grid_and_offgrid_z(binding, bc):
     check("image ragged", img.reshape(7, -1), image_ref(w, echo), TOL_FP32)
 
 
+@pytest.mark.parametrize("nz,nx,ny,tile_u", [(7, 37, 23, 0), (50, 32, 32, 0), (50, 32, 32, 16),
+                                            (100, 40, 33, 0), (200, 24, 24, 0)])
+def test_tensor_core_zidft_stage(binding, nz, nx, ny, tile_u):
+    # Eq. (9) at voxel heights off the scan grid on the tensor cores, against
+    # the oracle's inverse transform of the plan's own k-space image G: one,
+    # two and three blocks of heights, pixel counts that are not multiples of
+    # the 128-pixel block, two channel parts (planar) and one (tile_u 16)
+    w = wl.small_mono(seed=5)
+    zext = w.n_scan * w.dz
+    w.grid = dict(w.grid, nx=nx, ny=ny, nz=nz, z0=-0.5 * zext + 0.0013, dz=zext / nz)
+    echo = scene_echo(w, 5)
+    plan, img = run_gpu(binding, w, echo, block_config=4, tile_u=tile_u)
+    assert plan.info["block_config"] == 4 and plan.info["z_transform_fft"] == 0
+    G = plan.workspace(binding.PL_STAGE_BACKPROJECT).cpu().numpy()
+    G = G.reshape(-1, w.n_pad, nx * ny).sum(axis=0)
+    ref = oracle.zidft(G, w.dz, w.z0, w.axis("z"))
+    check("tensor-core z-IDFT nz=%d %dx%d tile_u=%d" % (nz, nx, ny, tile_u),
+          img.reshape(nz, -1), ref, 3e-5)
+
+
 def test_scan_grid_ifft_path_with_offset(binding):
     # voxel heights on the scan grid, shifted by 5 scan steps: inverse FFT path
     w = wl.small_mono(seed=4)

@@ -3,8 +3,9 @@
 Every wait of the tcgen05 back-projection and of the tensor-core range
 table is bounded by a clock budget. A test hook (pl_options
 debug_unsatisfiable) makes one wait depend on a barrier that nothing
-completes -- the back-projection's MMA warp (1) or the range table's first
-stage (2) -- with a short budget (wait_timeout_us). The kernel must then give
+completes -- the back-projection's MMA warp (1), the range table's first
+stage (2) or the MMA warp of the inverse z transform at off-grid heights (3)
+-- with a short budget (wait_timeout_us). The kernel must then give
 up, drain its own copies and products, release tensor memory and return: the
 next pl_execute reports PL_ERR_TIMEOUT, no CUDA error is raised, and the same
 device goes on to produce a correct image. Nothing here faults, traps or
@@ -36,13 +37,17 @@ def echo_of(w):
     return wl.add_noise(clean, w.snr_db, wl.rng_for(130, 0)).astype(np.complex64)
 
 
-@pytest.mark.parametrize("hook", [1, 2])
+@pytest.mark.parametrize("hook", [1, 2, 3])
 def test_unsatisfiable_wait_times_out_and_device_stays_usable(binding, hook):
     w = wl.small_mono(seed=0)
+    if hook == 3:
+        # voxel heights off the scan grid: the tensor-core inverse DFT
+        w.grid = dict(w.grid, nz=24, z0=-0.071, dz=0.0061)
     echo = torch.from_numpy(echo_of(w)).cuda()
     plan = binding.Plan.from_workload(w, block_config=4, debug_unsatisfiable=hook,
                                       wait_timeout_us=2000)
     assert plan.info["block_config"] == 4 and plan.info["table_exact"] == 1
+    assert plan.info["z_transform_fft"] == (0 if hook == 3 else 1)
     plan.execute(echo)
     torch.cuda.synchronize()            # the kernels returned: no CUDA error
     with pytest.raises(binding.PolylineError) as ei:
@@ -64,7 +69,7 @@ def test_unsatisfiable_wait_times_out_and_device_stays_usable(binding, hook):
 def test_debug_hook_is_validated(binding):
     w = wl.small_mono(seed=0)
     with pytest.raises(binding.PolylineError) as ei:
-        binding.Plan.from_workload(w, block_config=4, debug_unsatisfiable=3)
+        binding.Plan.from_workload(w, block_config=4, debug_unsatisfiable=4)
     assert ei.value.status == 1
     with pytest.raises(binding.PolylineError) as ei:
         binding.Plan.from_workload(w, block_config=4, wait_timeout_us=-1)
