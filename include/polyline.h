@@ -162,7 +162,16 @@ typedef struct {
      * memory, so that the call returns PL_ERR_OOM and frees what it had
      * allocated. 0 = off (default). */
     int debug_fail_alloc;
-    int reserved[2];
+    /* block_config 4, planar layout with 16-row windows: by default the
+     * back-projection's products are 2:4 sparse (tcgen05.mma.sp). A window's
+     * rows are taken in residue order (K index 4 j + e <-> row j + 4 e), in
+     * which a pixel's w consecutive taps leave at most two nonzeros in every
+     * group of four; with the K operand [Re rows; Im rows] of the table a
+     * channel takes six sparse products instead of twelve dense ones. The
+     * sums are the same up to rounding order. dense_products = 1 keeps the
+     * dense products. */
+    int dense_products;
+    int reserved[1];
 } pl_options;
 
 typedef struct pl_plan pl_plan;
@@ -212,6 +221,8 @@ typedef struct {
                              (tensor cores); 0: type-1 NUFFT (spread, FFT,
                              deconvolution) */
     int precision;        /* pl_options.precision in use */
+    int sparse_products;  /* 1: the tensor-core back-projection takes 2:4-sparse
+                             products (see pl_options.dense_products) */
 } pl_info;
 
 /* Stage identifiers for timing and workspace access. */

@@ -45,7 +45,7 @@ class PlOptions(ctypes.Structure):
     _fields_ = [("precision", _I), ("nufft_sigma", _D), ("nufft_w", _I), ("tile_u", _I),
                 ("block_config", _I), ("debug_unsatisfiable", _I), ("wait_timeout_us", _I),
                 ("one_block_per_sm", _I), ("check_nonfinite", _I), ("debug_fail_alloc", _I),
-                ("reserved", _I * 2)]
+                ("dense_products", _I), ("reserved", _I * 1)]
 
 
 class PlInfo(ctypes.Structure):
@@ -56,7 +56,7 @@ class PlInfo(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t), ("updates_per_execute", _D),
                 ("block_config", _I), ("tile_u", _I), ("bp_launches", _I),
                 ("es_beta", _D), ("band_group", _I), ("table_layout", _I), ("table_cols", _I),
-                ("table_exact", _I), ("precision", _I)]
+                ("table_exact", _I), ("precision", _I), ("sparse_products", _I)]
 
 
 class PlBatchOptions(ctypes.Structure):
@@ -186,7 +186,7 @@ class _DevArray:
 def _descriptors(keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad, pair_tx,
                  pair_rx, radius, n_sections, chord_len, elem_section, precision, nufft_sigma,
                  nufft_w, tile_u, block_config, debug_unsatisfiable=0, wait_timeout_us=0,
-                 one_block_per_sm=0, check_nonfinite=0, debug_fail_alloc=0):
+                 one_block_per_sm=0, check_nonfinite=0, debug_fail_alloc=0, dense_products=0):
     exy = _f64(elem_xy).reshape(-1, 2)
     sec = None if elem_section is None else _i32(elem_section)
     ptx = None if pair_tx is None else _i32(pair_tx)
@@ -203,7 +203,8 @@ def _descriptors(keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pa
                int(grid["nz"]))
     opt = PlOptions(int(precision), float(nufft_sigma), int(nufft_w), int(tile_u),
                     int(block_config), int(debug_unsatisfiable), int(wait_timeout_us),
-                    int(one_block_per_sm), 1 if check_nonfinite else 0, int(debug_fail_alloc))
+                    int(one_block_per_sm), 1 if check_nonfinite else 0, int(debug_fail_alloc),
+                    1 if dense_products else 0)
     return geom, scan, freqs, g, opt
 
 
@@ -220,14 +221,14 @@ class Plan:
                  pair_tx=None, pair_rx=None, radius=0.0, n_sections=0, chord_len=0.0,
                  elem_section=None, precision=0, nufft_sigma=0.0, nufft_w=0, tile_u=0,
                  block_config=0, debug_unsatisfiable=0, wait_timeout_us=0, one_block_per_sm=0,
-                 check_nonfinite=False, debug_fail_alloc=0):
+                 check_nonfinite=False, debug_fail_alloc=0, dense_products=False):
         lib = load()
         self._keep = []
         geom, scan, freqs, g, opt = _descriptors(
             self._keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad, pair_tx,
             pair_rx, radius, n_sections, chord_len, elem_section, precision, nufft_sigma,
             nufft_w, tile_u, block_config, debug_unsatisfiable, wait_timeout_us,
-            one_block_per_sm, check_nonfinite, debug_fail_alloc)
+            one_block_per_sm, check_nonfinite, debug_fail_alloc, dense_products)
         h = _P()
         _check(lib.pl_plan_create(ctypes.byref(h), geom, scan, freqs, g, opt))
         self._h = h

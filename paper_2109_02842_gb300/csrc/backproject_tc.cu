@@ -95,6 +95,44 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
     lo = bf2(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xffff0000u));
 }
 
+// One (pixel, channel) of a tile: the window row o of the first of the w taps
+// (0 <= o <= 16 KS - w), the tap weights and the carrier e^{j kappa_T a}
+// (sin, cos). The pixel sits (ddx, ddy) from the tile centre; g holds the
+// channel's geometry relative to that centre.
+template <int W, int KS>
+__device__ __forceinline__ void channel_taps(const BpDesc &p, const CoefTable &ct, const TileGeo &g,
+                                             float ddx, float ddy, float2 kT, int &o,
+                                             float (&w)[W], float &sn, float &cs) {
+    constexpr int ND = W + 2;                   // polynomial coefficients per tap
+    // delta = a - a* from rho^2 - rho*^2 = d (2 D + d): no cancellation
+    float ex = g.dxt + ddx, ey = g.dyt + ddy;
+    float num = fmaf(ddx, 2.0f * g.dxt + ddx, ddy * (2.0f * g.dyt + ddy));
+    float r2 = fmaf(ex, ex, ey * ey);
+    float dl = num * __frcp_rn(fmaf(r2, rsqrtf(r2), g.rt));
+    if (p.mode == 1) {
+        ex = g.dxr + ddx;
+        ey = g.dyr + ddy;
+        num = fmaf(ddx, 2.0f * g.dxr + ddx, ddy * (2.0f * g.dyr + ddy));
+        r2 = fmaf(ex, ex, ey * ey);
+        dl += num * __frcp_rn(fmaf(r2, rsqrtf(r2), g.rr));
+    }
+    // taps: rows o .. o + w - 1 of the window, weights from the per-tap
+    // polynomials in s = 2 (pos - o) - (w - 1)
+    const float pos = (dl + g.off) * p.inv_h;
+    o = min(max((int)ceilf(pos - 0.5f * W), 0), 16 * KS - W);
+    const float s = fmaf(2.0f, pos - (float)o, -(float)(W - 1));
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+        float acc = ct.c[t][ND - 1];
+#pragma unroll
+        for (int d = ND - 2; d >= 0; --d) acc = fmaf(acc, s, ct.c[t][d]);
+        w[t] = acc;
+    }
+    // carrier e^{j kappa_T a} = e^{j (kappa_T delta + (kappa_T a* mod 2 pi))}
+    const float th = fmaf(kT.x, dl, bp::phase_ff(kT.x, kT.y, g.a_hi, g.a_lo));
+    __sincosf(th, &sn, &cs);
+}
+
 // Barriers of one block's item: b_full[NSG], done[NSG], a_full[NPAR],
 // a_done[NPAR], acc_full (NSG = nst / (NPAR CPR) slot groups).
 __host__ __device__ constexpr int tc_barriers(int nsg, int npar) { return 2 * nsg + 2 * npar + 1; }
@@ -116,7 +154,6 @@ __device__ __forceinline__ void bp_tc_item(const BpDesc &p, const CoefTable &ct,
     constexpr int NPL = SPLIT == 3 ? 4 : 2;     // A planes: (re, im) x (hi[, lo])
     constexpr int NW = 8 * KS;                  // 32-bit words of an A row (16 KS BF16)
     constexpr int NT = W / 2 + 1;               // words of the taps after the parity shift
-    constexpr int ND = W + 2;                   // polynomial coefficients per tap
     // Channels go in groups of NPAR (channel c = NPAR g + k, class k); the
     // slots form NSG slot groups of NPAR. b_full[s]: the windows of the group
     // in slot group s landed (TMA); done[s]: that group's products completed
@@ -166,35 +203,9 @@ __device__ __forceinline__ void bp_tc_item(const BpDesc &p, const CoefTable &ct,
             const TileGeo g = gn;
             const int cnext = jc + 1 < CPR ? c + 1 : c + 1 + (NPAR - 1) * CPR;
             if (cnext < ce) gn = tg[cnext];
-            // delta = a - a* from rho^2 - rho*^2 = d (2 D + d): no cancellation
-            float ex = g.dxt + ddx, ey = g.dyt + ddy;
-            float num = fmaf(ddx, 2.0f * g.dxt + ddx, ddy * (2.0f * g.dyt + ddy));
-            float r2 = fmaf(ex, ex, ey * ey);
-            float dl = num * __frcp_rn(fmaf(r2, rsqrtf(r2), g.rt));
-            if (p.mode == 1) {
-                ex = g.dxr + ddx;
-                ey = g.dyr + ddy;
-                num = fmaf(ddx, 2.0f * g.dxr + ddx, ddy * (2.0f * g.dyr + ddy));
-                r2 = fmaf(ex, ex, ey * ey);
-                dl += num * __frcp_rn(fmaf(r2, rsqrtf(r2), g.rr));
-            }
-            // taps: rows o .. o + w - 1 of the window, weights from the per-tap
-            // polynomials in s = 2 (pos - o) - (w - 1)
-            const float pos = (dl + g.off) * p.inv_h;
-            const int o = min(max((int)ceilf(pos - 0.5f * W), 0), 16 * KS - W);
-            const float s = fmaf(2.0f, pos - (float)o, -(float)(W - 1));
-            float w[W];
-#pragma unroll
-            for (int t = 0; t < W; ++t) {
-                float acc = ct.c[t][ND - 1];
-#pragma unroll
-                for (int d = ND - 2; d >= 0; --d) acc = fmaf(acc, s, ct.c[t][d]);
-                w[t] = acc;
-            }
-            // carrier e^{j kappa_T a} = e^{j (kappa_T delta + (kappa_T a* mod 2 pi))}
-            const float th = fmaf(kT.x, dl, bp::phase_ff(kT.x, kT.y, g.a_hi, g.a_lo));
-            float sn, cs;
-            __sincosf(th, &sn, &cs);
+            int o;
+            float w[W], sn, cs;
+            channel_taps<W, KS>(p, ct, g, ddx, ddy, kT, o, w, sn, cs);
             // element o of the row starts word o / 2; an odd o puts a zero first
             const bool odd = (o & 1) != 0;
             float e[W + 2];
@@ -450,6 +461,292 @@ __device__ __forceinline__ void bp_tc_item(const BpDesc &p, const CoefTable &ct,
     }
 }
 
+// The same block with 2:4-sparse products (planar layout, one 16-row window
+// per channel, one channel per class round). The window's rows are taken in
+// residue order, K index 4 j + e <-> window row j + 4 e (j, e < 4): a pixel's
+// w <= 8 taps, consecutive rows o .. o + w - 1, put at most two in each
+// group of four K indices, so each A row is 2:4 sparse. The B operand of one
+// sparse product (K = 32) is the window's Re rows followed by its Im rows,
+// S = [Re b; Im b] (a 5-D TMA box: 64 columns x 4 x 4 rows x Re / Im x hi /
+// lo), and the complex product becomes
+//   Re G += [Re A | -Im A] S,   Im G += [Im A | Re A] S,
+// so a channel takes six sparse products (hi/lo split: A_hi S_hi, A_hi S_lo,
+// A_lo S_hi for each accumulator) instead of twelve dense ones. Each class
+// buffer holds the four compressed A matrices (8 columns each: 8 kept values
+// per K half); the kept positions, the same in both K halves, go to the
+// class's metadata column.
+template <int W, int SPLIT, int NPAR>
+__device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &ct,
+                                              const TcArgs &ta, const CUtensorMap *tmap,
+                                              const TileGeo *__restrict__ tgeo,
+                                              const float2 *__restrict__ kc_hl,
+                                              float2 *__restrict__ G, int *err, int lin,
+                                              unsigned char *smem, uint64_t *bars, uint32_t tmem,
+                                              uint64_t *dbg_bar) {
+    static_assert(W == 4 || W == 6 || W == 8, "taps");
+    constexpr int NCW = Warps<NPAR>::compute;
+    constexpr int NMAT = SPLIT == 3 ? 4 : 2;    // compressed A matrices per channel
+    const int NSG = ta.nst / NPAR;
+    uint64_t *b_full = bars;
+    uint64_t *done = b_full + NSG;
+    uint64_t *a_full = done + NSG;
+    uint64_t *a_done = a_full + NPAR;
+    uint64_t *acc_full = a_done + NPAR;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nbx = (p.nx + TCX - 1) / TCX, nby = (p.ny + TCY - 1) / TCY;
+    const int bx = lin % nbx, by = (lin / nbx) % nby, bz = lin / (nbx * nby);
+    const int tile = by * nbx + bx;
+    const int part = bz % ta.nsplit;             // planar: one bin block, bz = part
+    const int C = p.n_chan;
+    const int cper = (C + ta.nsplit - 1) / ta.nsplit;
+    const int cb = part * cper, ce = min(C, cb + cper);
+    const TileGeo *tg = tgeo + (size_t)tile * C;
+    const long long budget = ta.budget;
+    const uint32_t N = ta.UT;                    // the MMA's N (Re G, Im G columns)
+
+    if (warp < NCW) {
+        // ------------------------------------------------ A rows (compressed)
+        const int q = warp & 3, par = warp >> 2;
+        const int pix = 32 * q + lane;
+        const int px = pix % TCX, py = pix / TCX;
+        const float ddx = ((float)px - 0.5f * (TCX - 1)) * p.dxf;
+        const float ddy = ((float)py - 0.5f * (TCY - 1)) * p.dyf;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+        const uint32_t abuf = lane_base + ta.acol + par * (NMAT * 8);
+        const uint32_t mbuf = lane_base + ta.mcol + par * 8;
+        const float2 kT = kc_hl[0];
+        bool ok = true;
+        int it = 0;
+        TileGeo gn;
+        if (cb + par < ce) gn = tg[cb + par];
+        for (int c = cb + par; c < ce; c += NPAR, ++it) {
+            const TileGeo g = gn;
+            if (c + NPAR < ce) gn = tg[c + NPAR];
+            int o;
+            float w[W], sn, cs;
+            channel_taps<W, 1>(p, ct, g, ddx, ddy, kT, o, w, sn, cs);
+            // taps t < 4 fall in distinct groups j = (o + t) mod 4 at position
+            // e = (o + t) / 4; tap t + 4 (< w) in the same group at e + 1. Kept
+            // pair of group j: (e, e + 1) with values (w_t, w_{t+4} or 0), or
+            // (2, 3) with (0, w_t) when a lone tap sits at e = 3.
+            const int r = o & 3, ob = o >> 2;
+            float kv0[4], kv1[4];
+            uint32_t nib[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int e = ob + ((r + t) >> 2);
+                const bool two = t + 4 < W;
+                const float first = w[t];
+                const float second = two ? w[t + 4 < W ? t + 4 : t] : 0.f;
+                const bool top = !two && e == 3;
+                kv0[t] = top ? 0.f : first;
+                kv1[t] = top ? first : second;
+                const uint32_t i0 = top ? 2u : (uint32_t)e;
+                nib[t] = i0 | ((i0 + 1u) << 2);
+            }
+            // rotate from tap order t to group order j = (t + r) mod 4
+#pragma unroll
+            for (int b = 1; b < 4; b <<= 1) {
+                if (r & b) {
+                    float a0[4], a1[4];
+                    uint32_t n0[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        a0[j] = kv0[(j - b) & 3];
+                        a1[j] = kv1[(j - b) & 3];
+                        n0[j] = nib[(j - b) & 3];
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        kv0[j] = a0[j];
+                        kv1[j] = a1[j];
+                        nib[j] = n0[j];
+                    }
+                }
+            }
+            const uint32_t m16 = nib[0] | (nib[1] << 4) | (nib[2] << 8) | (nib[3] << 12);
+            // kept values times the carrier: Re / Im, BF16 hi (and lo), two
+            // kept values (one group) per 32-bit word
+            uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float r0 = kv0[j] * cs, r1 = kv1[j] * cs;
+                const float i0 = kv0[j] * sn, i1 = kv1[j] * sn;
+                if (SPLIT == 3) {
+                    split2(r0, r1, rh[j], rl[j]);
+                    split2(i0, i1, ih[j], il[j]);
+                } else {
+                    rh[j] = bf2(r0, r1);
+                    ih[j] = bf2(i0, i1);
+                    rl[j] = il[j] = 0u;
+                }
+            }
+            // metadata word of this lane: rows (r, r + 8) of its 16-lane block,
+            // K 0..15 in lanes r < 8 and K 16..31 in lanes r + 8 (equal halves)
+            const uint32_t other = __shfl_xor_sync(0xffffffffu, m16, 8);
+            const uint32_t mword = (lane & 8) ? (other | (m16 << 16)) : (m16 | (other << 16));
+            if (it > 0) ok = tc05::mbar_wait(&a_done[par], (uint32_t)(it - 1) & 1u, budget);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            tc05::fence_after_sync();
+            constexpr uint32_t NEG = 0x80008000u;
+            {
+                uint32_t v[8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) { v[j] = rh[j]; v[4 + j] = ih[j] ^ NEG; }
+                tc05::tmem_st8(abuf, v);                       // [Re A | -Im A] hi
+#pragma unroll
+                for (int j = 0; j < 4; ++j) { v[j] = ih[j]; v[4 + j] = rh[j]; }
+                tc05::tmem_st8(abuf + 8, v);                   // [Im A | Re A] hi
+                if (SPLIT == 3) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) { v[j] = rl[j]; v[4 + j] = il[j] ^ NEG; }
+                    tc05::tmem_st8(abuf + 16, v);              // [Re A | -Im A] lo
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) { v[j] = il[j]; v[4 + j] = rl[j]; }
+                    tc05::tmem_st8(abuf + 24, v);              // [Im A | Re A] lo
+                }
+            }
+            tc05::tmem_st1(mbuf, mword);
+            tc05::tmem_wait_st();
+            tc05::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc05::mbar_arrive(&a_full[par]);
+        }
+        if (ok && it > 0)
+            ok = __all_sync(0xffffffffu, tc05::mbar_wait(&a_done[par], (uint32_t)(it - 1) & 1u, budget));
+        if (!ok && lane == 0) atomicOr(err, 1);
+
+        // ------------------------------------------------ epilogue
+        bool fin = __all_sync(0xffffffffu, tc05::mbar_wait(acc_full, 0, budget));
+        if (fin) {
+            tc05::fence_after_sync();
+            const int ix = bx * TCX + px, iy = by * TCY + py;
+            const bool inside = ix < p.nx && iy < p.ny;
+            const size_t plane = (size_t)p.nx * p.ny;
+            const size_t pofs = (size_t)iy * p.nx + ix;
+            float2 *Gp = G + (size_t)part * p.n_pad * plane;
+            for (int ch = par; ch < (int)(N / 16); ch += NPAR) {
+                uint32_t pv[16], qv[16];
+                tc05::tmem_ld16(lane_base + 16 * ch, pv);
+                tc05::tmem_ld16(lane_base + N + 16 * ch, qv);
+                tc05::tmem_wait_ld();
+                if (!inside) continue;
+#pragma unroll
+                for (int b = 0; b < 16; ++b) {
+                    const int u = 16 * ch + b;
+                    if (u >= p.n_pad) continue;
+                    Gp[u * plane + pofs] = make_float2(__uint_as_float(pv[b]), __uint_as_float(qv[b]));
+                }
+            }
+        } else if (lane == 0) {
+            atomicOr(err, 2);
+        }
+    } else if (warp == NCW) {
+        // ------------------------------------------------ MMA issue
+        const uint64_t d0 = tc05::smem_desc_sw128(tc05::smem_addr(smem), ta.cb_bytes, 1024);
+        const uint32_t slot16 = ta.slot_bytes >> 4;
+        const uint32_t lo16 = 4096u >> 4;                  // S_lo after S_hi
+        const uint32_t idsp = ta.idesc | (1u << 2);        // 2:4 sparse A
+        const int n_groups = (ce - cb + NPAR - 1) / NPAR;
+        bool ok = true;
+        if (ta.dbg_wait) ok = __all_sync(0xffffffffu, tc05::mbar_wait(dbg_bar, 0, budget));
+        int sg = 0;
+        uint32_t bpar = 0;
+        for (int g = 0; g < n_groups && ok; ++g) {
+            const int nleft = ce - cb - g * NPAR;
+            ok = tc05::mbar_wait(&b_full[sg], bpar, budget);
+#pragma unroll
+            for (int k = 0; k < NPAR; ++k) {
+                if (k >= nleft) break;
+                ok = ok && tc05::mbar_wait(&a_full[k], (uint32_t)g & 1u, budget);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                tc05::fence_after_sync();
+                if (lane == 0) {
+                    const uint32_t a1 = tmem + ta.acol + k * (NMAT * 8);
+                    const uint32_t meta = tmem + ta.mcol + k * 8;
+                    const uint64_t sh = d0 + (uint64_t)((sg * NPAR + k) * slot16);
+                    const uint32_t acc = (g > 0 || k > 0) ? 1u : 0u;
+                    // Re G += [Re A | -Im A] S, Im G += [Im A | Re A] S
+                    tc05::mma_sp_ts(tmem, a1, sh, meta, idsp, acc);
+                    tc05::mma_sp_ts(tmem + N, a1 + 8, sh, meta, idsp, acc);
+                    if (SPLIT == 3) {
+                        const uint64_t sl = sh + lo16;
+                        tc05::mma_sp_ts(tmem, a1, sl, meta, idsp, 1u);
+                        tc05::mma_sp_ts(tmem, a1 + 16, sh, meta, idsp, 1u);
+                        tc05::mma_sp_ts(tmem + N, a1 + 8, sl, meta, idsp, 1u);
+                        tc05::mma_sp_ts(tmem + N, a1 + 24, sh, meta, idsp, 1u);
+                    }
+                    tc05::mma_commit(&a_done[k]);
+                }
+                __syncwarp();
+            }
+            if (!ok) break;
+            if (lane == 0) tc05::mma_commit(&done[sg]);
+            __syncwarp();
+            if (++sg == NSG) {
+                sg = 0;
+                bpar ^= 1u;
+            }
+        }
+        if (lane == 0) {
+            if (!ok) atomicOr(err, 4);
+            tc05::mma_commit(acc_full);
+        }
+    } else {
+        // ------------------------------------------------ TMA producer
+        const int n_groups = (ce - cb + NPAR - 1) / NPAR;
+        bool ok = true;
+        int issued = 0;
+        int sg = 0;
+        uint32_t dpar = 0;
+        int ilo_next[NPAR];
+#pragma unroll
+        for (int k = 0; k < NPAR; ++k) ilo_next[k] = cb + k < ce ? tg[cb + k].ilo : 0;
+        for (int g = 0; g < n_groups; ++g) {
+            const int nch = min(NPAR, ce - cb - g * NPAR);
+            int ilo[NPAR];
+#pragma unroll
+            for (int k = 0; k < NPAR; ++k) {
+                ilo[k] = ilo_next[k];
+                const int cn = cb + (g + 1) * NPAR + k;
+                if (cn < ce) ilo_next[k] = tg[cn].ilo;
+            }
+            if (g >= NSG) ok = tc05::mbar_wait(&done[sg], dpar, budget);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            if (lane == 0) {
+                tc05::mbar_arrive_expect_tx(&b_full[sg], (uint32_t)nch * ta.slot_bytes);
+#pragma unroll
+                for (int k = 0; k < NPAR; ++k) {
+                    if (k >= nch) break;
+                    unsigned char *dst = smem + (size_t)(sg * NPAR + k) * ta.slot_bytes;
+                    const int cz = 2 * (cb + g * NPAR + k);
+                    // rows ilo + j + 4 e: quad ilo / 4 + e, row-in-quad ilo % 4 + j
+                    for (int j = 0; j < ta.ncb; ++j)
+                        tc05::tma_load_5d(dst + (size_t)j * ta.cb_bytes, tmap, &b_full[sg], 64 * j,
+                                          ilo[k] >> 2, ilo[k] & 3, 0, cz);
+                }
+            }
+            issued = g + 1;
+            if (++sg == NSG) {
+                sg = 0;
+                if (g + 1 >= 2 * NSG) dpar ^= 1u;
+            }
+        }
+        if (lane == 0) {
+            if (!ok) atomicOr(err, 8);
+            for (int s = 0; s < NSG && s < issued; ++s) {
+                const int n_s = (issued - 1 - s) / NSG + 1;
+                if (!tc05::mbar_wait(&b_full[s], (n_s - 1) & 1, budget)) atomicOr(err, 16);
+                if (ok && !tc05::mbar_wait(&done[s], (n_s - 1) & 1, budget)) atomicOr(err, 32);
+            }
+        }
+    }
+}
+
 // The per-scan kernel: one block per (tile, bin block, channel part) from
 // ta.blk0 on (a launch may cover a range of blocks); the barriers follow the
 // window slots in shared memory.
@@ -491,6 +788,49 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
     bp_tc_item<W, KS, SPLIT, NPAR, PLANAR, CPR>(p, ct, ta, &tmap, tgeo, kc_hl, G, err,
                                                (int)blockIdx.x + ta.blk0, smem, bars, tmem,
                                                &dbg_bar);
+    tc05::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc05::tmem_dealloc(tmem, ta.tmem_cols);
+}
+
+// The per-scan kernel of the sparse products (planar, 16-row windows, one
+// channel per class round).
+template <int W, int SPLIT, int NPAR>
+__global__ void __launch_bounds__(Warps<NPAR>::threads, 1)
+k_backproject_tc_sp(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUtensorMap tmap,
+                    const TileGeo *__restrict__ tgeo, const float2 *__restrict__ kc_hl,
+                    float2 *__restrict__ G, int *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int NSG = ta.nst / NPAR;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)ta.nst * ta.slot_bytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + tc_barriers(NSG, NPAR));
+    __shared__ __align__(8) uint64_t dbg_bar;    // test hook: never completed
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        tc05::mbar_init(&dbg_bar, 1);
+        for (int s = 0; s < NSG; ++s) {
+            tc05::mbar_init(&bars[s], 1);
+            tc05::mbar_init(&bars[NSG + s], 1);
+        }
+        for (int k = 0; k < NPAR; ++k) {
+            tc05::mbar_init(&bars[2 * NSG + k], 4);
+            tc05::mbar_init(&bars[2 * NSG + NPAR + k], 1);
+        }
+        tc05::mbar_init(&bars[2 * NSG + 2 * NPAR], 1);
+        tc05::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc05::tmem_alloc(tmem_slot, ta.tmem_cols);
+        tc05::tmem_relinquish();
+    }
+    tc05::fence_before_sync();
+    __syncthreads();
+    tc05::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    bp_tc_item_sp<W, SPLIT, NPAR>(p, ct, ta, &tmap, tgeo, kc_hl, G, err, (int)blockIdx.x + ta.blk0,
+                                  smem, bars, tmem, &dbg_bar);
     tc05::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc05::tmem_dealloc(tmem, ta.tmem_cols);
@@ -634,6 +974,34 @@ cudaError_t launch_pl(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, co
                      : launch_t<W, KS, SPLIT, NPAR, false, 1>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
 }
 
+template <int W, int SPLIT, int NPAR>
+cudaError_t launch_sp(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
+                      const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
+                      cudaStream_t st) {
+    const size_t smem = backproject_tc_smem_bytes(ta);
+    cudaError_t e = cudaFuncSetAttribute(k_backproject_tc_sp<W, SPLIT, NPAR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int total = backproject_tc_blocks(p, ta);
+    const int nblk = ta.nblk > 0 ? ta.nblk : total - ta.blk0;
+    if (ta.blk0 < 0 || nblk <= 0 || ta.blk0 + nblk > total) return cudaErrorInvalidValue;
+    k_backproject_tc_sp<W, SPLIT, NPAR><<<nblk, Warps<NPAR>::threads, smem, st>>>(
+        p, ct, ta, tm, tgeo, kc_hl, G, err);
+    return cudaGetLastError();
+}
+
+template <int SPLIT, int NPAR>
+cudaError_t launch_spw(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
+                       const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
+                       cudaStream_t st) {
+    switch (p.w) {
+        case 4: return launch_sp<4, SPLIT, NPAR>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        case 6: return launch_sp<6, SPLIT, NPAR>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        case 8: return launch_sp<8, SPLIT, NPAR>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int KS, int SPLIT, int NPAR>
 cudaError_t launch_w(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
                      const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
@@ -693,6 +1061,16 @@ cudaError_t launch_backproject_tc_batch(const TcBatchMaps &maps, const CoefTable
 cudaError_t launch_backproject_tc(const BpDesc &p, const CoefTable &ct, const TcArgs &ta,
                                   const CUtensorMap &tm, const TileGeo *tgeo, const float2 *kc_hl,
                                   float2 *G, int *err, cudaStream_t st) {
+    if (ta.sparse) {
+        if (ta.ks != 1 || !ta.planar || ta.cpr != 1) return cudaErrorInvalidValue;
+        if (ta.npar == 3)
+            return ta.split == 3 ? launch_spw<3, 3>(p, ct, ta, tm, tgeo, kc_hl, G, err, st)
+                                 : launch_spw<1, 3>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        if (ta.npar == 2)
+            return ta.split == 3 ? launch_spw<3, 2>(p, ct, ta, tm, tgeo, kc_hl, G, err, st)
+                                 : launch_spw<1, 2>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        return cudaErrorInvalidValue;
+    }
     if (ta.ks == 1)
         return ta.split == 3 ? launch_p<1, 3>(p, ct, ta, tm, tgeo, kc_hl, G, err, st)
                              : launch_p<1, 1>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);

@@ -157,6 +157,10 @@ struct TcArgs {
                          // completes, so the bounded-wait exit paths run
     int blk0, nblk;      // the launch's blocks: linear indices [blk0, blk0 + nblk) of
                          // (tile x, tile y, bin block x part), x fastest; nblk 0: to the end
+    int sparse;          // 1: 2:4-sparse products (planar, 16-row windows, cpr 1): window rows
+                         // taken in residue order, K = [Re rows; Im rows] of the table, six
+                         // sparse products per channel (split 3); 5-D table map
+    int mcol;            // sparse: first TMEM column of the classes' metadata (8 apart)
 };
 // blocks of a whole back-projection
 int backproject_tc_blocks(const BpDesc &p, const TcArgs &ta);

@@ -47,6 +47,19 @@ bool tc_fits(int ut, int npl, int ks, bool planar, bool force3 = false) {
     const size_t slot = (size_t)(planar ? 2 : 1) * ((N + 63) / 64) * cb;
     return 1024 + 2 * npar * slot + 512 <= 227 * 1024;
 }
+// The 2:4-sparse products (planar layout, 16-row windows): TMEM columns of
+// the accumulators, each class's compressed A matrices (nmat x 8 columns) and
+// its metadata column (8 apart); classes: 2 in 256 columns (two blocks per
+// SM), else 3, else 2 in 512.
+int tc_cols_sp(int ut, int npar, int nmat) { return 2 * ut + npar * nmat * 8 + npar * 8; }
+int tc_npar_sp(int ut, int nmat) {
+    if (ut > 256) return 0;
+    if (tc_cols_sp(ut, 2, nmat) <= 256) return 2;
+    if (tc_cols_sp(ut, 3, nmat) <= 512) return 3;
+    if (tc_cols_sp(ut, 2, nmat) <= 512) return 2;
+    return 0;
+}
+
 // Bins per block of the interleaved layout (used where the planar one does
 // not fit): the fewest blocks that the largest 1-block-per-SM tile allows,
 // split evenly (multiple of 8), e.g. N_p = 200 -> 2 x 104, 128 -> 2 x 64.
@@ -58,6 +71,30 @@ int tc_auto_tile(int np, int npl, int ks) {
 }
 
 // The driver's tensor-map encoder, looked up once through the runtime.
+EncodeTiledFn encode_tiled_fn();
+
+// TMA map of the planar table [c][hi/lo][row][Re | Im columns] (BF16, `part`
+// columns per half) for the sparse products: a box is 64 columns x 4 row
+// quads x 4 rows in a quad x (Re, Im) x `planes` (hi[, lo]), so that a box at
+// (quad i / 4, row-in-quad i % 4) holds rows i + j + 4 e in the order
+// [plane][Re / Im][j][e]. The row-in-quad dimension has 7 entries over
+// overlapping rows, so any first row i is reachable; the last quad ends
+// inside the channel's plane (rows 4 (nq - 1) + 6 < L).
+bool encode_sparse_map(CUtensorMap *m, void *table, int part, int L, int C, int planes) {
+    EncodeTiledFn enc = encode_tiled_fn();
+    if (!enc || L < 7) return false;
+    const cuuint64_t pitch = (cuuint64_t)part * 2 * 2;
+    const cuuint64_t nq = (cuuint64_t)((L - 7) / 4 + 1);
+    const cuuint64_t dims[5] = {(cuuint64_t)part, nq, 7, 2, 2 * (cuuint64_t)C};
+    const cuuint64_t strides[4] = {4 * pitch, pitch, (cuuint64_t)part * 2, (cuuint64_t)L * pitch};
+    const cuuint32_t box[5] = {64, 4, 4, 2, (cuuint32_t)planes};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, table, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
 EncodeTiledFn encode_tiled_fn() {
     static EncodeTiledFn fn = [] {
         void *f = nullptr;
@@ -298,8 +335,9 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     if (o.precision < 0 || o.precision > 2) return fail(PL_ERR_ARG, "precision must be 0, 1 or 2");
     if (o.debug_unsatisfiable < 0 || o.debug_unsatisfiable > 3 || o.wait_timeout_us < 0)
         return fail(PL_ERR_ARG, "debug_unsatisfiable must be 0..3, wait_timeout_us >= 0");
-    if (o.check_nonfinite < 0 || o.check_nonfinite > 1 || o.debug_fail_alloc < 0)
-        return fail(PL_ERR_ARG, "check_nonfinite must be 0 or 1, debug_fail_alloc >= 0");
+    if (o.check_nonfinite < 0 || o.check_nonfinite > 1 || o.debug_fail_alloc < 0 ||
+        o.dense_products < 0 || o.dense_products > 1)
+        return fail(PL_ERR_ARG, "check_nonfinite and dense_products must be 0 or 1, debug_fail_alloc >= 0");
     g_fail_alloc_countdown = o.debug_fail_alloc;
     P->check_nonfinite = o.check_nonfinite != 0;
     // the device-side status word (mapped host memory): expired waits of the
@@ -473,6 +511,21 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         L += L & 1;
         P->R = 16 * ks;
         P->tc.ks = ks;
+        // 2:4-sparse products where the layout allows them (four more table
+        // rows: the last row quad of the sparse map must hold every window)
+        P->tc.sparse = 0;
+        if (!o.dense_products && P->tc.planar && ks == 1 && !o.one_block_per_sm &&
+            (W == 4 || W == 6 || W == 8) && tc_npar_sp(P->tile_u, npl) > 0) {
+            CUtensorMap trial{};
+            alignas(64) static unsigned char probe_buf[64];
+            // the encoder only checks the layout (the address is not read)
+            const uintptr_t fake = (reinterpret_cast<uintptr_t>(probe_buf) + 63) & ~(uintptr_t)63;
+            if (encode_sparse_map(&trial, reinterpret_cast<void *>(fake), P->tile_u, L + 4, P->C,
+                                  P->precision >= 1 ? 1 : 2)) {
+                P->tc.sparse = 1;
+                L += 4;
+            }
+        }
     } else {
         // every tile's R-row window [i_lo, i_lo + R), centred on its range, fits:
         // l0 = amin - ((R+1)/2 + 2) h, L = (amax - amin)/h + R + 6
@@ -512,12 +565,21 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         ta.npar = tc_npar(ta.UT, npl, ta.ks, ta.planar != 0, o.one_block_per_sm != 0);
         ta.tmem_cols = ta.npar == 2 ? 256 : 512;
         ta.acol = 2 * N;
+        if (ta.sparse) {
+            // per 64-column block: [hi: Re rows, Im rows][lo: Re rows, Im rows]
+            ta.cb_bytes = (unsigned)planes * 4096u;
+            ta.im_off = 0;
+            ta.slot_bytes = (unsigned)ta.ncb * ta.cb_bytes;
+            ta.npar = tc_npar_sp(ta.UT, npl);
+            ta.tmem_cols = tc_cols_sp(ta.UT, ta.npar, npl) <= 256 ? 256 : 512;
+            ta.mcol = ta.acol + ta.npar * npl * 8;
+        }
         // two channels per class round (twice the products per A wait and
         // release) where three classes of two-channel A buffers fit next to
         // the accumulators and two slot groups of six windows fit in shared
         // memory
         ta.cpr = 1;
-        if (!o.one_block_per_sm && ta.npar == 3 && 2 * N + 3 * 2 * npl * ta.ks * 8 <= 512 &&
+        if (!ta.sparse && !o.one_block_per_sm && ta.npar == 3 && 2 * N + 3 * 2 * npl * ta.ks * 8 <= 512 &&
             1024 + 2 * (size_t)3 * 2 * ta.slot_bytes + 512 <= 227 * 1024)
             ta.cpr = 2;
         // window slots: whole slot groups of npar x cpr (at least 2 groups),
@@ -629,15 +691,20 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         EncodeTiledFn enc = encode_tiled_fn();
         if (!enc) return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled not available");
         const TcArgs &ta = P->tc;
-        const cuuint64_t dims[3] = {(cuuint64_t)d.tc_cols, (cuuint64_t)L, 2 * (cuuint64_t)P->C};
-        const cuuint64_t strides[2] = {(cuuint64_t)d.tc_cols * 2, (cuuint64_t)L * d.tc_cols * 2};
-        const cuuint32_t box[3] = {64, (cuuint32_t)(16 * ta.ks), (cuuint32_t)(ta.split == 3 ? 2 : 1)};
-        const cuuint32_t es[3] = {1, 1, 1};
-        const CUresult r = enc(&P->tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, P->d_table, dims,
-                               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        if (ta.sparse) {
+            if (!encode_sparse_map(&P->tmap, P->d_table, ta.UT, L, P->C, ta.split == 3 ? 2 : 1))
+                return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled failed (sparse table map)");
+        } else {
+            const cuuint64_t dims[3] = {(cuuint64_t)d.tc_cols, (cuuint64_t)L, 2 * (cuuint64_t)P->C};
+            const cuuint64_t strides[2] = {(cuuint64_t)d.tc_cols * 2, (cuuint64_t)L * d.tc_cols * 2};
+            const cuuint32_t box[3] = {64, (cuuint32_t)(16 * ta.ks), (cuuint32_t)(ta.split == 3 ? 2 : 1)};
+            const cuuint32_t es[3] = {1, 1, 1};
+            const CUresult r = enc(&P->tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, P->d_table, dims,
+                                   strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        }
         // the range table as exact sums on the tensor cores (one or two
         // 64-frequency atoms: up to 128 frequencies; table rows up to 256),
         // else the NUFFT
@@ -1271,6 +1338,7 @@ pl_status pl_plan_get_info(const pl_plan *P, pl_info *info) {
     }
     i.table_exact = (P->block_config == 4 && P->rt_tc) ? 1 : 0;
     i.precision = P->precision;
+    i.sparse_products = (P->block_config == 4 && P->tc.sparse) ? 1 : 0;
     *info = i;
     return PL_OK;
 }

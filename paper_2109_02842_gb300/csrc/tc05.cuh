@@ -1,6 +1,6 @@
 // Thin inline-PTX wrappers for the Blackwell (sm_100a / sm_103a) asynchronous
 // units: mbarriers, TMA tensor loads, tensor memory (TMEM) and the tcgen05
-// matrix-multiply instructions. Only what the back-projection uses.
+// matrix-multiply instructions (dense and 2:4 sparse).
 #pragma once
 
 #include <cuda.h>
@@ -84,6 +84,17 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// 5-D tiled tensor load into shared memory, completion counted on `bar`.
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1, int c2, int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+        "r"(smem_addr(bar))
+        : "memory");
+}
+
 // ---------------------------------------------------------------- TMEM
 // Allocation and release are warp-wide (.sync.aligned); the allocated base
 // address is written to shared memory.
@@ -114,6 +125,11 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
             taddr),
         "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
         : "memory");
+}
+// Each thread of the warp writes one 32-bit column of its own lane.
+__device__ __forceinline__ void tmem_st1(uint32_t taddr, uint32_t v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};\n" ::"r"(taddr), "r"(v)
+                 : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() {
     asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
@@ -174,6 +190,24 @@ __device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a_desc, uint64_
         "setp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// D[tmem] (+)= A[tmem] x B[smem] with A 2:4 sparse along K (K = 32 BF16: A
+// holds the 16 kept values of a row, 8 columns; the 2-bit positions of the
+// kept values in their groups of four are read from the metadata column at
+// meta_tmem), issued by one thread; idesc has the sparsity bit set. Metadata
+// layout (M = 128): in each block of 16 lanes, lane r < 8 holds row r's
+// positions for K 0..15 in bits 0..15 and row r + 8's in bits 16..31, lane
+// r + 8 the same rows' positions for K 16..31; nibble g of a 16-bit half =
+// group g (first kept position in bits 0-1, the second in bits 2-3).
+__device__ __forceinline__ void mma_sp_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                          uint32_t meta_tmem, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "setp.ne.b32 p, %5, 0;\n"
+        "tcgen05.mma.sp.cta_group::1.kind::f16 [%0], [%1], %2, [%3], %4, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(meta_tmem), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 // Arrive on `bar` once every tcgen05 operation this thread issued has completed.

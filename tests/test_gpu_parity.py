@@ -395,6 +395,59 @@ def test_tensor_core_other_tap_counts(binding, taps, grid):
           image_ref(w, echo), 2e-3 if taps == 4 else TOL_FP32)
 
 
+@pytest.mark.parametrize("case", ["mono", "multi", "ragged", "npad45", "offgrid", "taps4",
+                                  "taps8", "bf16"])
+def test_sparse_products_match_dense_and_oracle(binding, case):
+    # the 2:4-sparse products (window rows in residue order, K = [Re; Im]
+    # rows of the table) against the dense products of the same plan layout
+    # and against the oracle, on 2 mm grids (16-row windows): monostatic and
+    # multistatic, a ragged pixel grid, 45 bins padded to 48, heights off the
+    # scan grid, 4, 6 and 8 taps, BF16-only products
+    opts = {}
+    tol = TOL_FP32
+    w = small_multi() if case == "multi" else wl.small_mono(seed=7)
+    nx, ny = (37, 23) if case == "ragged" else (64, 64)
+    x0, dx = wl.centred_axis(0.128, 64)
+    w.grid = dict(w.grid, x0=x0, dx=dx, nx=nx, y0=x0, dy=dx, ny=ny, nz=8)
+    if case == "npad45":
+        w.n_pad = 45
+    elif case == "offgrid":
+        w.grid = dict(w.grid, nz=11, z0=-0.047, dz=0.0087)
+    elif case.startswith("taps"):
+        opts["nufft_w"] = int(case[4:])
+        tol = 2e-3 if case == "taps4" else TOL_FP32
+    elif case == "bf16":
+        opts["precision"] = 1
+        tol = TOL_BF16
+    echo = scene_echo(w, 7)
+    sp, img = run_gpu(binding, w, echo, block_config=4, **opts)
+    de, img_d = run_gpu(binding, w, echo, block_config=4, dense_products=True, **opts)
+    print("%s: window rows %d, table rows %d, bins %d" % (case, sp.info["slab_rows"],
+                                                         sp.info["table_len"], sp.info["tile_u"]))
+    assert sp.info["sparse_products"] == 1 and de.info["sparse_products"] == 0
+    nz = w.grid["nz"]
+    d = float(np.linalg.norm(img - img_d) / np.linalg.norm(img_d))
+    print("%s: sparse vs dense rel L2 %.3e" % (case, d))
+    assert d < (1e-3 if case == "bf16" else 3e-5)
+    check("image tc sparse %s" % case, img.reshape(nz, -1), image_ref(w, echo), tol)
+
+
+@pytest.mark.parametrize("which", ["full_mono", "multi"])
+def test_sparse_products_full_size(binding, which):
+    w = wl.WORKLOADS[which](seed=0)
+    echo = scene_echo(w, 0, n_pts=24)
+    sp, img = run_gpu(binding, w, echo, block_config=4)
+    de, img_d = run_gpu(binding, w, echo, block_config=4, dense_products=True)
+    assert sp.info["sparse_products"] == 1
+    d = float(np.linalg.norm(img - img_d) / np.linalg.norm(img_d))
+    print("%s: sparse vs dense rel L2 %.3e" % (which, d))
+    assert d < 3e-5
+    idx = sampled_columns(w, 48, 2)
+    ref = image_ref(w, echo, w.pix_xy()[idx])
+    check("image tc sparse %s sampled" % which, img.reshape(w.grid["nz"], -1)[:, idx], ref,
+          TOL_FP32)
+
+
 def test_tensor_core_bf16_only_products(binding):
     w = wl.small_mono(seed=2)
     echo = scene_echo(w, 2)
