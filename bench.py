@@ -556,7 +556,7 @@ def main():
         achieved = method_flops / bp_avg_s / 1e12
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": kernel_traffic("backproject_tc", w.name),
-                    "kernel": "k_backproject_tc", "launch_ms": bp_avg_s * 1e3,
+                    "launch_ms": bp_avg_s * 1e3,
                     "flop_per_launch": method_flops,
                     "flop_basis": "%d flop per (pixel, channel, k_z bin) update: w-tap "
                                   "interpolation, split-float carrier phase and the complex "
@@ -567,12 +567,21 @@ def main():
                             "pass: from the start of its first launch to the end of its last",
                     "peak_basis": "dense BF16 burst, %s" % ("of measured" if peak_src == "measured"
                                                             else "of fallback"),
-                    "mma_pipe_frac": dense / bp_avg_s / 1e12 / peak,
+                    "kernel": "k_backproject_tc_sp" if info.get("sparse_products") else
+                              "k_backproject_tc",
+                    # the 2:4-sparse products issue the same logical MMA work
+                    # (K = 32 per sparse product over [Re; Im] rows) at twice
+                    # the dense rate: their pipe fraction is taken against 2x
+                    # the dense peak
+                    "mma_pipe_frac": dense / bp_avg_s / 1e12 / (peak * (2 if info.get(
+                        "sparse_products") else 1)),
                     "mma_dense_flop_per_launch": dense,
-                    "mma_basis": "dense BF16 MMA work issued: 16 window rows x 4 real products "
-                                 "x %d split products x 2 per (pixel, channel, bin) over padded "
-                                 "tiles; only %d of the 16 rows carry a tap"
-                                 % (3 if args.precision == 0 else 1, info["nufft_w"])}
+                    "mma_basis": "BF16 MMA work issued (logical, dense-equivalent): 16 window "
+                                 "rows x 4 real products x %d split products x 2 per (pixel, "
+                                 "channel, bin) over padded tiles; only %d of the 16 rows carry "
+                                 "a tap%s" % (3 if args.precision == 0 else 1, info["nufft_w"],
+                                              "; 2:4-sparse products, against 2x the dense "
+                                              "peak" if info.get("sparse_products") else "")}
     else:
         fp32_peak = unit_peaks.get("fp32_tflops") or N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e-6
         achieved = method_flops / bp_avg_s / 1e12

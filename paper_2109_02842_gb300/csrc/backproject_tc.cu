@@ -474,8 +474,15 @@ __device__ __forceinline__ void bp_tc_item(const BpDesc &p, const CoefTable &ct,
 // A_lo S_hi for each accumulator) instead of twelve dense ones. Each class
 // buffer holds the four compressed A matrices (8 columns each: 8 kept values
 // per K half); the kept positions, the same in both K halves, go to the
-// class's metadata column.
-template <int W, int SPLIT, int NPAR>
+// class's metadata column. Each class buffer is filled by NSET sets of four
+// warps in turn (set s takes the class's rounds r = s mod NSET), so that one
+// set computes its next channel while another's is stored and multiplied.
+// A set may overwrite the buffer for round r only when round r - 1 (stored
+// by another set) has been consumed. The products of round r release it on
+// a_done[class][r mod NSET], so that each release barrier runs through the
+// rounds of one set: a waiter never falls two phases behind the barrier it
+// tests (the parity of a phase test would not tell them apart).
+template <int W, int SPLIT, int NPAR, int NSET>
 __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &ct,
                                               const TcArgs &ta, const CUtensorMap *tmap,
                                               const TileGeo *__restrict__ tgeo,
@@ -484,14 +491,14 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
                                               unsigned char *smem, uint64_t *bars, uint32_t tmem,
                                               uint64_t *dbg_bar) {
     static_assert(W == 4 || W == 6 || W == 8, "taps");
-    constexpr int NCW = Warps<NPAR>::compute;
+    constexpr int NCW = 4 * NPAR * NSET;         // A-building warps
     constexpr int NMAT = SPLIT == 3 ? 4 : 2;    // compressed A matrices per channel
     const int NSG = ta.nst / NPAR;
     uint64_t *b_full = bars;
     uint64_t *done = b_full + NSG;
     uint64_t *a_full = done + NSG;
-    uint64_t *a_done = a_full + NPAR;
-    uint64_t *acc_full = a_done + NPAR;
+    uint64_t *a_done = a_full + NPAR;            // [class][set]
+    uint64_t *acc_full = a_done + NPAR * NSET;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nbx = (p.nx + TCX - 1) / TCX, nby = (p.ny + TCY - 1) / TCY;
@@ -507,7 +514,7 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
 
     if (warp < NCW) {
         // ------------------------------------------------ A rows (compressed)
-        const int q = warp & 3, par = warp >> 2;
+        const int q = warp & 3, par = (warp >> 2) % NPAR, set = (warp >> 2) / NPAR;
         const int pix = 32 * q + lane;
         const int px = pix % TCX, py = pix / TCX;
         const float ddx = ((float)px - 0.5f * (TCX - 1)) * p.dxf;
@@ -517,12 +524,19 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
         const uint32_t mbuf = lane_base + ta.mcol + par * 8;
         const float2 kT = kc_hl[0];
         bool ok = true;
-        int it = 0;
+        const int rounds = ce - cb > par ? (ce - cb - par + NPAR - 1) / NPAR : 0;
+        // round r's release: barrier a_done[par][r mod NSET], its phase r / NSET
+        auto released = [&](int r) {
+            return tc05::mbar_wait(&a_done[par * NSET + r % NSET], (uint32_t)(r / NSET) & 1u,
+                                   budget);
+        };
+        constexpr int STEP = NPAR * NSET;
         TileGeo gn;
-        if (cb + par < ce) gn = tg[cb + par];
-        for (int c = cb + par; c < ce; c += NPAR, ++it) {
+        if (cb + par + NPAR * set < ce) gn = tg[cb + par + NPAR * set];
+        for (int it = set; it < rounds; it += NSET) {
+            const int c = cb + par + NPAR * it;
             const TileGeo g = gn;
-            if (c + NPAR < ce) gn = tg[c + NPAR];
+            if (c + STEP < ce) gn = tg[c + STEP];
             int o;
             float w[W], sn, cs;
             channel_taps<W, 1>(p, ct, g, ddx, ddy, kT, o, w, sn, cs);
@@ -586,7 +600,8 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
             // K 0..15 in lanes r < 8 and K 16..31 in lanes r + 8 (equal halves)
             const uint32_t other = __shfl_xor_sync(0xffffffffu, m16, 8);
             const uint32_t mword = (lane & 8) ? (other | (m16 << 16)) : (m16 | (other << 16));
-            if (it > 0) ok = tc05::mbar_wait(&a_done[par], (uint32_t)(it - 1) & 1u, budget);
+            // round it - 1 consumed (and with it every earlier round)
+            if (it > 0) ok = released(it - 1);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             tc05::fence_after_sync();
@@ -614,8 +629,10 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
             __syncwarp();
             if (lane == 0) tc05::mbar_arrive(&a_full[par]);
         }
-        if (ok && it > 0)
-            ok = __all_sync(0xffffffffu, tc05::mbar_wait(&a_done[par], (uint32_t)(it - 1) & 1u, budget));
+        // the class's last round released: every release has arrived (none
+        // outstanding on exit)
+        if (ok && rounds > 0) ok = released(rounds - 1);
+        ok = __all_sync(0xffffffffu, ok);
         if (!ok && lane == 0) atomicOr(err, 1);
 
         // ------------------------------------------------ epilogue
@@ -627,7 +644,7 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
             const size_t plane = (size_t)p.nx * p.ny;
             const size_t pofs = (size_t)iy * p.nx + ix;
             float2 *Gp = G + (size_t)part * p.n_pad * plane;
-            for (int ch = par; ch < (int)(N / 16); ch += NPAR) {
+            for (int ch = warp >> 2; ch < (int)(N / 16); ch += NPAR * NSET) {
                 uint32_t pv[16], qv[16];
                 tc05::tmem_ld16(lane_base + 16 * ch, pv);
                 tc05::tmem_ld16(lane_base + N + 16 * ch, qv);
@@ -679,7 +696,7 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
                         tc05::mma_sp_ts(tmem + N, a1 + 8, sl, meta, idsp, 1u);
                         tc05::mma_sp_ts(tmem + N, a1 + 24, sh, meta, idsp, 1u);
                     }
-                    tc05::mma_commit(&a_done[k]);
+                    tc05::mma_commit(&a_done[k * NSET + g % NSET]);
                 }
                 __syncwarp();
             }
@@ -795,8 +812,13 @@ k_backproject_tc(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUte
 
 // The per-scan kernel of the sparse products (planar, 16-row windows, one
 // channel per class round).
-template <int W, int SPLIT, int NPAR>
-__global__ void __launch_bounds__(Warps<NPAR>::threads, 1)
+template <int NPAR, int NSET>
+struct SpWarps {
+    static constexpr int threads = (4 * NPAR * NSET + 2) * 32;   // + MMA warp + TMA warp
+};
+
+template <int W, int SPLIT, int NPAR, int NSET>
+__global__ void __launch_bounds__(SpWarps<NPAR, NSET>::threads, 1)
 k_backproject_tc_sp(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUtensorMap tmap,
                     const TileGeo *__restrict__ tgeo, const float2 *__restrict__ kc_hl,
                     float2 *__restrict__ G, int *err) {
@@ -805,20 +827,15 @@ k_backproject_tc_sp(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ C
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int NSG = ta.nst / NPAR;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)ta.nst * ta.slot_bytes);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + tc_barriers(NSG, NPAR));
+    // b_full[NSG], done[NSG], a_full[NPAR], a_done[NPAR][NSET], acc_full
+    const int nbars = 2 * NSG + NPAR + NPAR * NSET + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + nbars);
     __shared__ __align__(8) uint64_t dbg_bar;    // test hook: never completed
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         tc05::mbar_init(&dbg_bar, 1);
-        for (int s = 0; s < NSG; ++s) {
-            tc05::mbar_init(&bars[s], 1);
-            tc05::mbar_init(&bars[NSG + s], 1);
-        }
-        for (int k = 0; k < NPAR; ++k) {
-            tc05::mbar_init(&bars[2 * NSG + k], 4);
-            tc05::mbar_init(&bars[2 * NSG + NPAR + k], 1);
-        }
-        tc05::mbar_init(&bars[2 * NSG + 2 * NPAR], 1);
+        for (int i = 0; i < nbars; ++i)
+            tc05::mbar_init(&bars[i], (i >= 2 * NSG && i < 2 * NSG + NPAR) ? 4u : 1u);
         tc05::fence_mbar_init();
     }
     if (warp == 0) {
@@ -829,8 +846,8 @@ k_backproject_tc_sp(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ C
     __syncthreads();
     tc05::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    bp_tc_item_sp<W, SPLIT, NPAR>(p, ct, ta, &tmap, tgeo, kc_hl, G, err, (int)blockIdx.x + ta.blk0,
-                                  smem, bars, tmem, &dbg_bar);
+    bp_tc_item_sp<W, SPLIT, NPAR, NSET>(p, ct, ta, &tmap, tgeo, kc_hl, G, err,
+                                        (int)blockIdx.x + ta.blk0, smem, bars, tmem, &dbg_bar);
     tc05::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc05::tmem_dealloc(tmem, ta.tmem_cols);
@@ -979,13 +996,14 @@ cudaError_t launch_sp(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, co
                       const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
                       cudaStream_t st) {
     const size_t smem = backproject_tc_smem_bytes(ta);
-    cudaError_t e = cudaFuncSetAttribute(k_backproject_tc_sp<W, SPLIT, NPAR>,
+    constexpr int NSET = 2;
+    cudaError_t e = cudaFuncSetAttribute(k_backproject_tc_sp<W, SPLIT, NPAR, NSET>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int total = backproject_tc_blocks(p, ta);
     const int nblk = ta.nblk > 0 ? ta.nblk : total - ta.blk0;
     if (ta.blk0 < 0 || nblk <= 0 || ta.blk0 + nblk > total) return cudaErrorInvalidValue;
-    k_backproject_tc_sp<W, SPLIT, NPAR><<<nblk, Warps<NPAR>::threads, smem, st>>>(
+    k_backproject_tc_sp<W, SPLIT, NPAR, NSET><<<nblk, SpWarps<NPAR, NSET>::threads, smem, st>>>(
         p, ct, ta, tm, tgeo, kc_hl, G, err);
     return cudaGetLastError();
 }

@@ -584,7 +584,9 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
             ta.cpr = 2;
         // window slots: whole slot groups of npar x cpr (at least 2 groups),
         // within ~190 KB (one block per SM) or ~100 KB (two)
-        const size_t pool = ta.tmem_cols > 256 ? 190 * 1024 : 100 * 1024;
+        // (the sparse products consume a window twice as fast: one more slot
+        // group where it fits keeps the copies ahead of them)
+        const size_t pool = ta.tmem_cols > 256 ? (ta.sparse ? 200 : 190) * 1024 : 100 * 1024;
         const size_t group_bytes = (size_t)ta.slot_bytes * ta.npar * ta.cpr;
         const int nsg = (int)std::max<size_t>(2, std::min<size_t>(16, pool / group_bytes));
         ta.nst = nsg * ta.npar * ta.cpr;

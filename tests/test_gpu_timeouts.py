@@ -37,18 +37,23 @@ def echo_of(w):
     return wl.add_noise(clean, w.snr_db, wl.rng_for(130, 0)).astype(np.complex64)
 
 
-@pytest.mark.parametrize("hook", [1, 2, 3])
-def test_unsatisfiable_wait_times_out_and_device_stays_usable(binding, hook):
+@pytest.mark.parametrize("hook,fine", [(1, False), (1, True), (2, False), (3, False)])
+def test_unsatisfiable_wait_times_out_and_device_stays_usable(binding, hook, fine):
     w = wl.small_mono(seed=0)
     if hook == 3:
         # 24 voxel heights off the scan grid: the tensor-core inverse DFT
         w.grid = dict(w.grid, nz=24, z0=-0.071, dz=0.0061)
+    if fine:
+        # a 2 mm grid: 16-row windows, the back-projection's sparse products
+        x0, dx = wl.centred_axis(0.128, 64)
+        w.grid = dict(w.grid, x0=x0, dx=dx, nx=64, y0=x0, dy=dx, ny=64, nz=8)
     echo = torch.from_numpy(echo_of(w)).cuda()
     plan = binding.Plan.from_workload(w, block_config=4, debug_unsatisfiable=hook,
                                       wait_timeout_us=2000)
     assert plan.info["block_config"] == 4 and plan.info["table_exact"] == 1
     if hook == 3:
         assert plan.info["z_transform_fft"] == 0
+    assert plan.info["sparse_products"] == (1 if fine else 0)
     plan.execute(echo)
     torch.cuda.synchronize()            # the kernels returned: no CUDA error
     with pytest.raises(binding.PolylineError) as ei:
