@@ -171,6 +171,11 @@ typedef struct {
      * sums are the same up to rounding order. dense_products = 1 keeps the
      * dense products. */
     int dense_products;
+    /* The sparse products' window: 0 = 16 rows (default); 12 = 12 rows
+     * (residues mod 3) where every tile's taps span at most 12 rows and
+     * nufft_w <= 6, else 16. (12-row windows copy a quarter fewer table
+     * bytes; on the full-size monostatic workload they are not faster.) */
+    int sparse_window_rows;
     int reserved[1];
 } pl_options;
 

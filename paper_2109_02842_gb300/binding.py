@@ -45,7 +45,7 @@ class PlOptions(ctypes.Structure):
     _fields_ = [("precision", _I), ("nufft_sigma", _D), ("nufft_w", _I), ("tile_u", _I),
                 ("block_config", _I), ("debug_unsatisfiable", _I), ("wait_timeout_us", _I),
                 ("one_block_per_sm", _I), ("check_nonfinite", _I), ("debug_fail_alloc", _I),
-                ("dense_products", _I), ("reserved", _I * 1)]
+                ("dense_products", _I), ("sparse_window_rows", _I), ("reserved", _I * 1)]
 
 
 class PlInfo(ctypes.Structure):
@@ -186,7 +186,8 @@ class _DevArray:
 def _descriptors(keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad, pair_tx,
                  pair_rx, radius, n_sections, chord_len, elem_section, precision, nufft_sigma,
                  nufft_w, tile_u, block_config, debug_unsatisfiable=0, wait_timeout_us=0,
-                 one_block_per_sm=0, check_nonfinite=0, debug_fail_alloc=0, dense_products=0):
+                 one_block_per_sm=0, check_nonfinite=0, debug_fail_alloc=0, dense_products=0,
+                 sparse_window_rows=0):
     exy = _f64(elem_xy).reshape(-1, 2)
     sec = None if elem_section is None else _i32(elem_section)
     ptx = None if pair_tx is None else _i32(pair_tx)
@@ -204,7 +205,7 @@ def _descriptors(keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pa
     opt = PlOptions(int(precision), float(nufft_sigma), int(nufft_w), int(tile_u),
                     int(block_config), int(debug_unsatisfiable), int(wait_timeout_us),
                     int(one_block_per_sm), 1 if check_nonfinite else 0, int(debug_fail_alloc),
-                    1 if dense_products else 0)
+                    1 if dense_products else 0, int(sparse_window_rows))
     return geom, scan, freqs, g, opt
 
 
@@ -221,14 +222,16 @@ class Plan:
                  pair_tx=None, pair_rx=None, radius=0.0, n_sections=0, chord_len=0.0,
                  elem_section=None, precision=0, nufft_sigma=0.0, nufft_w=0, tile_u=0,
                  block_config=0, debug_unsatisfiable=0, wait_timeout_us=0, one_block_per_sm=0,
-                 check_nonfinite=False, debug_fail_alloc=0, dense_products=False):
+                 check_nonfinite=False, debug_fail_alloc=0, dense_products=False,
+                 sparse_window_rows=0):
         lib = load()
         self._keep = []
         geom, scan, freqs, g, opt = _descriptors(
             self._keep, mode, elem_xy, scan_z0, scan_dz, n_scan, f_hz, grid, n_pad, pair_tx,
             pair_rx, radius, n_sections, chord_len, elem_section, precision, nufft_sigma,
             nufft_w, tile_u, block_config, debug_unsatisfiable, wait_timeout_us,
-            one_block_per_sm, check_nonfinite, debug_fail_alloc, dense_products)
+            one_block_per_sm, check_nonfinite, debug_fail_alloc, dense_products,
+            sparse_window_rows)
         h = _P()
         _check(lib.pl_plan_create(ctypes.byref(h), geom, scan, freqs, g, opt))
         self._h = h

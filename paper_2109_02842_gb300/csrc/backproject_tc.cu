@@ -96,10 +96,10 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
 }
 
 // One (pixel, channel) of a tile: the window row o of the first of the w taps
-// (0 <= o <= 16 KS - w), the tap weights and the carrier e^{j kappa_T a}
-// (sin, cos). The pixel sits (ddx, ddy) from the tile centre; g holds the
-// channel's geometry relative to that centre.
-template <int W, int KS>
+// (0 <= o <= ROWS - w for a window of ROWS rows), the tap weights and the
+// carrier e^{j kappa_T a} (sin, cos). The pixel sits (ddx, ddy) from the tile
+// centre; g holds the channel's geometry relative to that centre.
+template <int W, int ROWS>
 __device__ __forceinline__ void channel_taps(const BpDesc &p, const CoefTable &ct, const TileGeo &g,
                                              float ddx, float ddy, float2 kT, int &o,
                                              float (&w)[W], float &sn, float &cs) {
@@ -119,7 +119,7 @@ __device__ __forceinline__ void channel_taps(const BpDesc &p, const CoefTable &c
     // taps: rows o .. o + w - 1 of the window, weights from the per-tap
     // polynomials in s = 2 (pos - o) - (w - 1)
     const float pos = (dl + g.off) * p.inv_h;
-    o = min(max((int)ceilf(pos - 0.5f * W), 0), 16 * KS - W);
+    o = min(max((int)ceilf(pos - 0.5f * W), 0), ROWS - W);
     const float s = fmaf(2.0f, pos - (float)o, -(float)(W - 1));
 #pragma unroll
     for (int t = 0; t < W; ++t) {
@@ -205,7 +205,7 @@ __device__ __forceinline__ void bp_tc_item(const BpDesc &p, const CoefTable &ct,
             if (cnext < ce) gn = tg[cnext];
             int o;
             float w[W], sn, cs;
-            channel_taps<W, KS>(p, ct, g, ddx, ddy, kT, o, w, sn, cs);
+            channel_taps<W, 16 * KS>(p, ct, g, ddx, ddy, kT, o, w, sn, cs);
             // element o of the row starts word o / 2; an odd o puts a zero first
             const bool odd = (o & 1) != 0;
             float e[W + 2];
@@ -461,6 +461,92 @@ __device__ __forceinline__ void bp_tc_item(const BpDesc &p, const CoefTable &ct,
     }
 }
 
+// Compressed 2:4-sparse A rows of one (pixel, channel) for a window of RW
+// rows taken in residue order: NG = RW / 4 residue classes j of four rows
+// each (row j + NG e at K position 4 j + e, e < 4). Taps t < NG fall in
+// distinct classes j = (o + t) mod NG at e = (o + t) / NG, tap t + NG (< w)
+// in the same class at e + 1, so each class holds at most two taps (w <=
+// 2 NG). Kept pair of class j: positions (e, e + 1) with values (w_t, w_{t+NG}
+// or 0), or (2, 3) with (0, w_t) when a lone tap sits at e = 3. The K = 32
+// operand is [Re rows | Im rows] (classes 0 .. NG - 1 of each, then zero
+// groups when NG = 3), so the rows are a1 = [Re A | -Im A] and a3 = [Im A |
+// Re A] (BF16 hi, and lo for SPLIT 3; word k = the kept pair of K group k)
+// and mA, mB the metadata of K 0..15 and 16..31.
+template <int W, int RW, int SPLIT>
+__device__ __forceinline__ void sparse_rows(int o, const float (&w)[W], float sn, float cs,
+                                            uint32_t (&a1h)[8], uint32_t (&a3h)[8],
+                                            uint32_t (&a1l)[8], uint32_t (&a3l)[8],
+                                            uint32_t &mA, uint32_t &mB) {
+    constexpr int NG = RW / 4;
+    static_assert(RW == 16 || RW == 12, "window rows");
+    static_assert(W <= 2 * NG, "at most two taps per residue class");
+    const int r = o % NG, ob = o / NG;
+    float kv0[NG], kv1[NG];
+    uint32_t nib[NG];
+#pragma unroll
+    for (int t = 0; t < NG; ++t) {
+        const int e = ob + ((r + t) >= NG ? 1 : 0);
+        const bool two = t + NG < W;
+        const float first = w[t];
+        const float second = two ? w[t + NG < W ? t + NG : t] : 0.f;
+        const bool top = !two && e == 3;
+        kv0[t] = top ? 0.f : first;
+        kv1[t] = top ? first : second;
+        const uint32_t i0 = top ? 2u : (uint32_t)e;
+        nib[t] = i0 | ((i0 + 1u) << 2);
+    }
+    // rotate from tap order t to class order j = (t + r) mod NG, one step at
+    // a time
+#pragma unroll
+    for (int step = 1; step < NG; ++step) {
+        if (step <= r) {
+            const float l0 = kv0[NG - 1], l1 = kv1[NG - 1];
+            const uint32_t ln = nib[NG - 1];
+#pragma unroll
+            for (int j = NG - 1; j > 0; --j) {
+                kv0[j] = kv0[j - 1];
+                kv1[j] = kv1[j - 1];
+                nib[j] = nib[j - 1];
+            }
+            kv0[0] = l0;
+            kv1[0] = l1;
+            nib[0] = ln;
+        }
+    }
+    constexpr uint32_t NEG = 0x80008000u;
+    constexpr uint32_t PAD = 0x4u;                  // kept positions (0, 1), values zero
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a1h[k] = a3h[k] = a1l[k] = a3l[k] = 0u;
+    uint32_t nb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) nb[k] = PAD;
+#pragma unroll
+    for (int j = 0; j < NG; ++j) {
+        const float r0 = kv0[j] * cs, r1 = kv1[j] * cs;
+        const float i0 = kv0[j] * sn, i1 = kv1[j] * sn;
+        uint32_t rh, rl, ih, il;
+        if (SPLIT == 3) {
+            split2(r0, r1, rh, rl);
+            split2(i0, i1, ih, il);
+        } else {
+            rh = bf2(r0, r1);
+            ih = bf2(i0, i1);
+            rl = il = 0u;
+        }
+        a1h[j] = rh;
+        a1h[NG + j] = ih ^ NEG;
+        a3h[j] = ih;
+        a3h[NG + j] = rh;
+        a1l[j] = rl;
+        a1l[NG + j] = il ^ NEG;
+        a3l[j] = il;
+        a3l[NG + j] = rl;
+        nb[j] = nb[NG + j] = nib[j];
+    }
+    mA = nb[0] | (nb[1] << 4) | (nb[2] << 8) | (nb[3] << 12);
+    mB = nb[4] | (nb[5] << 4) | (nb[6] << 8) | (nb[7] << 12);
+}
+
 // The same block with 2:4-sparse products (planar layout, one 16-row window
 // per channel, one channel per class round). The window's rows are taken in
 // residue order, K index 4 j + e <-> window row j + 4 e (j, e < 4): a pixel's
@@ -482,7 +568,7 @@ __device__ __forceinline__ void bp_tc_item(const BpDesc &p, const CoefTable &ct,
 // a_done[class][r mod NSET], so that each release barrier runs through the
 // rounds of one set: a waiter never falls two phases behind the barrier it
 // tests (the parity of a phase test would not tell them apart).
-template <int W, int SPLIT, int NPAR, int NSET>
+template <int W, int SPLIT, int NPAR, int NSET, int RW>
 __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &ct,
                                               const TcArgs &ta, const CUtensorMap *tmap,
                                               const TileGeo *__restrict__ tgeo,
@@ -539,89 +625,24 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
             if (c + STEP < ce) gn = tg[c + STEP];
             int o;
             float w[W], sn, cs;
-            channel_taps<W, 1>(p, ct, g, ddx, ddy, kT, o, w, sn, cs);
-            // taps t < 4 fall in distinct groups j = (o + t) mod 4 at position
-            // e = (o + t) / 4; tap t + 4 (< w) in the same group at e + 1. Kept
-            // pair of group j: (e, e + 1) with values (w_t, w_{t+4} or 0), or
-            // (2, 3) with (0, w_t) when a lone tap sits at e = 3.
-            const int r = o & 3, ob = o >> 2;
-            float kv0[4], kv1[4];
-            uint32_t nib[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int e = ob + ((r + t) >> 2);
-                const bool two = t + 4 < W;
-                const float first = w[t];
-                const float second = two ? w[t + 4 < W ? t + 4 : t] : 0.f;
-                const bool top = !two && e == 3;
-                kv0[t] = top ? 0.f : first;
-                kv1[t] = top ? first : second;
-                const uint32_t i0 = top ? 2u : (uint32_t)e;
-                nib[t] = i0 | ((i0 + 1u) << 2);
-            }
-            // rotate from tap order t to group order j = (t + r) mod 4
-#pragma unroll
-            for (int b = 1; b < 4; b <<= 1) {
-                if (r & b) {
-                    float a0[4], a1[4];
-                    uint32_t n0[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        a0[j] = kv0[(j - b) & 3];
-                        a1[j] = kv1[(j - b) & 3];
-                        n0[j] = nib[(j - b) & 3];
-                    }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        kv0[j] = a0[j];
-                        kv1[j] = a1[j];
-                        nib[j] = n0[j];
-                    }
-                }
-            }
-            const uint32_t m16 = nib[0] | (nib[1] << 4) | (nib[2] << 8) | (nib[3] << 12);
-            // kept values times the carrier: Re / Im, BF16 hi (and lo), two
-            // kept values (one group) per 32-bit word
-            uint32_t rh[4], rl[4], ih[4], il[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float r0 = kv0[j] * cs, r1 = kv1[j] * cs;
-                const float i0 = kv0[j] * sn, i1 = kv1[j] * sn;
-                if (SPLIT == 3) {
-                    split2(r0, r1, rh[j], rl[j]);
-                    split2(i0, i1, ih[j], il[j]);
-                } else {
-                    rh[j] = bf2(r0, r1);
-                    ih[j] = bf2(i0, i1);
-                    rl[j] = il[j] = 0u;
-                }
-            }
+            channel_taps<W, RW>(p, ct, g, ddx, ddy, kT, o, w, sn, cs);
+            uint32_t a1h[8], a3h[8], a1l[8], a3l[8], mA, mB;
+            sparse_rows<W, RW, SPLIT>(o, w, sn, cs, a1h, a3h, a1l, a3l, mA, mB);
             // metadata word of this lane: rows (r, r + 8) of its 16-lane block,
-            // K 0..15 in lanes r < 8 and K 16..31 in lanes r + 8 (equal halves)
-            const uint32_t other = __shfl_xor_sync(0xffffffffu, m16, 8);
-            const uint32_t mword = (lane & 8) ? (other | (m16 << 16)) : (m16 | (other << 16));
+            // K 0..15 in lanes r < 8 and K 16..31 in lanes r + 8
+            const uint32_t oA = __shfl_xor_sync(0xffffffffu, mA, 8);
+            const uint32_t oB = __shfl_xor_sync(0xffffffffu, mB, 8);
+            const uint32_t mword = (lane & 8) ? (oB | (mB << 16)) : (mA | (oA << 16));
             // round it - 1 consumed (and with it every earlier round)
             if (it > 0) ok = released(it - 1);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             tc05::fence_after_sync();
-            constexpr uint32_t NEG = 0x80008000u;
-            {
-                uint32_t v[8];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) { v[j] = rh[j]; v[4 + j] = ih[j] ^ NEG; }
-                tc05::tmem_st8(abuf, v);                       // [Re A | -Im A] hi
-#pragma unroll
-                for (int j = 0; j < 4; ++j) { v[j] = ih[j]; v[4 + j] = rh[j]; }
-                tc05::tmem_st8(abuf + 8, v);                   // [Im A | Re A] hi
-                if (SPLIT == 3) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) { v[j] = rl[j]; v[4 + j] = il[j] ^ NEG; }
-                    tc05::tmem_st8(abuf + 16, v);              // [Re A | -Im A] lo
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) { v[j] = il[j]; v[4 + j] = rl[j]; }
-                    tc05::tmem_st8(abuf + 24, v);              // [Im A | Re A] lo
-                }
+            tc05::tmem_st8(abuf, a1h);                         // [Re A | -Im A] hi
+            tc05::tmem_st8(abuf + 8, a3h);                     // [Im A | Re A] hi
+            if (SPLIT == 3) {
+                tc05::tmem_st8(abuf + 16, a1l);                // [Re A | -Im A] lo
+                tc05::tmem_st8(abuf + 24, a3l);                // [Im A | Re A] lo
             }
             tc05::tmem_st1(mbuf, mword);
             tc05::tmem_wait_st();
@@ -664,7 +685,7 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
         // ------------------------------------------------ MMA issue
         const uint64_t d0 = tc05::smem_desc_sw128(tc05::smem_addr(smem), ta.cb_bytes, 1024);
         const uint32_t slot16 = ta.slot_bytes >> 4;
-        const uint32_t lo16 = 4096u >> 4;                  // S_lo after S_hi
+        const uint32_t lo16 = (uint32_t)(RW * 2 * 128) >> 4;   // S_lo after S_hi
         const uint32_t idsp = ta.idesc | (1u << 2);        // 2:4 sparse A
         const int n_groups = (ce - cb + NPAR - 1) / NPAR;
         bool ok = true;
@@ -735,16 +756,20 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             if (lane == 0) {
-                tc05::mbar_arrive_expect_tx(&b_full[sg], (uint32_t)nch * ta.slot_bytes);
+                // the bytes the copies deliver (a 12-row window's pad is not copied)
+                tc05::mbar_arrive_expect_tx(&b_full[sg],
+                                            (uint32_t)(nch * ta.ncb) * ta.cb_bytes);
 #pragma unroll
                 for (int k = 0; k < NPAR; ++k) {
                     if (k >= nch) break;
                     unsigned char *dst = smem + (size_t)(sg * NPAR + k) * ta.slot_bytes;
                     const int cz = 2 * (cb + g * NPAR + k);
-                    // rows ilo + j + 4 e: quad ilo / 4 + e, row-in-quad ilo % 4 + j
+                    // rows ilo + j + NG e: group ilo / NG + e, row-in-group
+                    // ilo % NG + j (NG = RW / 4)
+                    const int a0 = ilo[k] / (RW / 4), g0 = ilo[k] - a0 * (RW / 4);
                     for (int j = 0; j < ta.ncb; ++j)
                         tc05::tma_load_5d(dst + (size_t)j * ta.cb_bytes, tmap, &b_full[sg], 64 * j,
-                                          ilo[k] >> 2, ilo[k] & 3, 0, cz);
+                                          a0, g0, 0, cz);
                 }
             }
             issued = g + 1;
@@ -817,7 +842,7 @@ struct SpWarps {
     static constexpr int threads = (4 * NPAR * NSET + 2) * 32;   // + MMA warp + TMA warp
 };
 
-template <int W, int SPLIT, int NPAR, int NSET>
+template <int W, int SPLIT, int NPAR, int NSET, int RW>
 __global__ void __launch_bounds__(SpWarps<NPAR, NSET>::threads, 1)
 k_backproject_tc_sp(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUtensorMap tmap,
                     const TileGeo *__restrict__ tgeo, const float2 *__restrict__ kc_hl,
@@ -842,12 +867,25 @@ k_backproject_tc_sp(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ C
         tc05::tmem_alloc(tmem_slot, ta.tmem_cols);
         tc05::tmem_relinquish();
     }
+    if (RW == 12) {
+        // 12-row windows: the last two K groups of an operand (zero weights)
+        // read 8 rows past its data, into the next column block of the same
+        // window (copied with it) or the window slot's 1 KB pad, which no
+        // copy writes: zero the pads so that those rows are finite, and order
+        // these writes before the products
+        const size_t pad0 = (size_t)ta.ncb * ta.cb_bytes;
+        for (int i = threadIdx.x; i < ta.nst * 64; i += blockDim.x) {
+            uint4 *z = reinterpret_cast<uint4 *>(smem + (size_t)(i >> 6) * ta.slot_bytes + pad0);
+            z[i & 63] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
     tc05::fence_before_sync();
     __syncthreads();
     tc05::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    bp_tc_item_sp<W, SPLIT, NPAR, NSET>(p, ct, ta, &tmap, tgeo, kc_hl, G, err,
-                                        (int)blockIdx.x + ta.blk0, smem, bars, tmem, &dbg_bar);
+    bp_tc_item_sp<W, SPLIT, NPAR, NSET, RW>(p, ct, ta, &tmap, tgeo, kc_hl, G, err,
+                                            (int)blockIdx.x + ta.blk0, smem, bars, tmem, &dbg_bar);
     tc05::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc05::tmem_dealloc(tmem, ta.tmem_cols);
@@ -991,20 +1029,20 @@ cudaError_t launch_pl(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, co
                      : launch_t<W, KS, SPLIT, NPAR, false, 1>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
 }
 
-template <int W, int SPLIT, int NPAR>
+template <int W, int SPLIT, int NPAR, int RW>
 cudaError_t launch_sp(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
                       const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
                       cudaStream_t st) {
     const size_t smem = backproject_tc_smem_bytes(ta);
     constexpr int NSET = 2;
-    cudaError_t e = cudaFuncSetAttribute(k_backproject_tc_sp<W, SPLIT, NPAR, NSET>,
+    cudaError_t e = cudaFuncSetAttribute(k_backproject_tc_sp<W, SPLIT, NPAR, NSET, RW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int total = backproject_tc_blocks(p, ta);
     const int nblk = ta.nblk > 0 ? ta.nblk : total - ta.blk0;
     if (ta.blk0 < 0 || nblk <= 0 || ta.blk0 + nblk > total) return cudaErrorInvalidValue;
-    k_backproject_tc_sp<W, SPLIT, NPAR, NSET><<<nblk, SpWarps<NPAR, NSET>::threads, smem, st>>>(
-        p, ct, ta, tm, tgeo, kc_hl, G, err);
+    k_backproject_tc_sp<W, SPLIT, NPAR, NSET, RW>
+        <<<nblk, SpWarps<NPAR, NSET>::threads, smem, st>>>(p, ct, ta, tm, tgeo, kc_hl, G, err);
     return cudaGetLastError();
 }
 
@@ -1012,10 +1050,17 @@ template <int SPLIT, int NPAR>
 cudaError_t launch_spw(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
                        const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
                        cudaStream_t st) {
+    if (ta.rw == 12) {                  // 12-row windows: w <= 6
+        switch (p.w) {
+            case 4: return launch_sp<4, SPLIT, NPAR, 12>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+            case 6: return launch_sp<6, SPLIT, NPAR, 12>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (p.w) {
-        case 4: return launch_sp<4, SPLIT, NPAR>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
-        case 6: return launch_sp<6, SPLIT, NPAR>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
-        case 8: return launch_sp<8, SPLIT, NPAR>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        case 4: return launch_sp<4, SPLIT, NPAR, 16>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        case 6: return launch_sp<6, SPLIT, NPAR, 16>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+        case 8: return launch_sp<8, SPLIT, NPAR, 16>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -161,6 +161,8 @@ struct TcArgs {
                          // taken in residue order, K = [Re rows; Im rows] of the table, six
                          // sparse products per channel (split 3); 5-D table map
     int mcol;            // sparse: first TMEM column of the classes' metadata (8 apart)
+    int rw;              // sparse: window rows, 16 (residues mod 4) or 12 (mod 3, w <= 6;
+                         // each window slot then ends in a 1 KB zero pad)
 };
 // blocks of a whole back-projection
 int backproject_tc_blocks(const BpDesc &p, const TcArgs &ta);

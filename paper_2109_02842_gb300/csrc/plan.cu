@@ -74,20 +74,25 @@ int tc_auto_tile(int np, int npl, int ks) {
 EncodeTiledFn encode_tiled_fn();
 
 // TMA map of the planar table [c][hi/lo][row][Re | Im columns] (BF16, `part`
-// columns per half) for the sparse products: a box is 64 columns x 4 row
-// quads x 4 rows in a quad x (Re, Im) x `planes` (hi[, lo]), so that a box at
-// (quad i / 4, row-in-quad i % 4) holds rows i + j + 4 e in the order
-// [plane][Re / Im][j][e]. The row-in-quad dimension has 7 entries over
-// overlapping rows, so any first row i is reachable; the last quad ends
-// inside the channel's plane (rows 4 (nq - 1) + 6 < L).
-bool encode_sparse_map(CUtensorMap *m, void *table, int part, int L, int C, int planes) {
+// columns per half) for the sparse products with windows of rw = 4 NG rows
+// (NG = 4 or 3 residue classes): a box is 64 columns x 4 row groups (NG rows
+// apart) x NG rows in a group x (Re, Im) x `planes` (hi[, lo]), so that a box
+// at (group i / NG, row-in-group i % NG) holds rows i + j + NG e in the order
+// [plane][Re / Im][j][e]. The row-in-group dimension has 2 NG - 1 entries
+// over overlapping rows, so any first row i is reachable; the last group
+// ends inside the channel's plane (rows NG (ng - 1) + 2 NG - 2 < L).
+bool encode_sparse_map(CUtensorMap *m, void *table, int part, int L, int C, int planes,
+                       int rw) {
     EncodeTiledFn enc = encode_tiled_fn();
-    if (!enc || L < 7) return false;
+    const int NG = rw / 4;
+    if (!enc || (rw != 16 && rw != 12) || L < 2 * NG) return false;
     const cuuint64_t pitch = (cuuint64_t)part * 2 * 2;
-    const cuuint64_t nq = (cuuint64_t)((L - 7) / 4 + 1);
-    const cuuint64_t dims[5] = {(cuuint64_t)part, nq, 7, 2, 2 * (cuuint64_t)C};
-    const cuuint64_t strides[4] = {4 * pitch, pitch, (cuuint64_t)part * 2, (cuuint64_t)L * pitch};
-    const cuuint32_t box[5] = {64, 4, 4, 2, (cuuint32_t)planes};
+    const cuuint64_t ng = (cuuint64_t)((L - (2 * NG - 1)) / NG + 1);
+    const cuuint64_t dims[5] = {(cuuint64_t)part, ng, (cuuint64_t)(2 * NG - 1), 2,
+                                2 * (cuuint64_t)C};
+    const cuuint64_t strides[4] = {(cuuint64_t)NG * pitch, pitch, (cuuint64_t)part * 2,
+                                   (cuuint64_t)L * pitch};
+    const cuuint32_t box[5] = {64, 4, (cuuint32_t)NG, 2, (cuuint32_t)planes};
     const cuuint32_t es[5] = {1, 1, 1, 1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, table, dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -336,8 +341,10 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
     if (o.debug_unsatisfiable < 0 || o.debug_unsatisfiable > 3 || o.wait_timeout_us < 0)
         return fail(PL_ERR_ARG, "debug_unsatisfiable must be 0..3, wait_timeout_us >= 0");
     if (o.check_nonfinite < 0 || o.check_nonfinite > 1 || o.debug_fail_alloc < 0 ||
-        o.dense_products < 0 || o.dense_products > 1)
-        return fail(PL_ERR_ARG, "check_nonfinite and dense_products must be 0 or 1, debug_fail_alloc >= 0");
+        o.dense_products < 0 || o.dense_products > 1 ||
+        (o.sparse_window_rows != 0 && o.sparse_window_rows != 12))
+        return fail(PL_ERR_ARG, "check_nonfinite and dense_products must be 0 or 1, "
+                                "sparse_window_rows 0 or 12, debug_fail_alloc >= 0");
     g_fail_alloc_countdown = o.debug_fail_alloc;
     P->check_nonfinite = o.check_nonfinite != 0;
     // the device-side status word (mapped host memory): expired waits of the
@@ -513,16 +520,23 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         P->tc.ks = ks;
         // 2:4-sparse products where the layout allows them (four more table
         // rows: the last row quad of the sparse map must hold every window)
+        // (on request, windows of 12 rows, residues mod 3, where every
+        // tile's taps span at most 12 rows and w <= 6: a quarter fewer bytes
+        // per copy)
         P->tc.sparse = 0;
+        P->tc.rw = 16;
         if (!o.dense_products && P->tc.planar && ks == 1 && !o.one_block_per_sm &&
             (W == 4 || W == 6 || W == 8) && tc_npar_sp(P->tile_u, npl) > 0) {
+            const int rw = (stats[0] <= 12 && W <= 6 && o.sparse_window_rows == 12) ? 12 : 16;
             CUtensorMap trial{};
             alignas(64) static unsigned char probe_buf[64];
             // the encoder only checks the layout (the address is not read)
             const uintptr_t fake = (reinterpret_cast<uintptr_t>(probe_buf) + 63) & ~(uintptr_t)63;
             if (encode_sparse_map(&trial, reinterpret_cast<void *>(fake), P->tile_u, L + 4, P->C,
-                                  P->precision >= 1 ? 1 : 2)) {
+                                  P->precision >= 1 ? 1 : 2, rw)) {
                 P->tc.sparse = 1;
+                P->tc.rw = rw;
+                P->R = rw;
                 L += 4;
             }
         }
@@ -567,9 +581,10 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         ta.acol = 2 * N;
         if (ta.sparse) {
             // per 64-column block: [hi: Re rows, Im rows][lo: Re rows, Im rows]
-            ta.cb_bytes = (unsigned)planes * 4096u;
+            // (rw rows each); 12-row windows end in a 1 KB zero pad
+            ta.cb_bytes = (unsigned)(planes * 2 * ta.rw * 128);
             ta.im_off = 0;
-            ta.slot_bytes = (unsigned)ta.ncb * ta.cb_bytes;
+            ta.slot_bytes = (unsigned)ta.ncb * ta.cb_bytes + (ta.rw == 12 ? 1024u : 0u);
             ta.npar = tc_npar_sp(ta.UT, npl);
             ta.tmem_cols = tc_cols_sp(ta.UT, ta.npar, npl) <= 256 ? 256 : 512;
             ta.mcol = ta.acol + ta.npar * npl * 8;
@@ -694,7 +709,8 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         if (!enc) return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled not available");
         const TcArgs &ta = P->tc;
         if (ta.sparse) {
-            if (!encode_sparse_map(&P->tmap, P->d_table, ta.UT, L, P->C, ta.split == 3 ? 2 : 1))
+            if (!encode_sparse_map(&P->tmap, P->d_table, ta.UT, L, P->C, ta.split == 3 ? 2 : 1,
+                                   ta.rw))
                 return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled failed (sparse table map)");
         } else {
             const cuuint64_t dims[3] = {(cuuint64_t)d.tc_cols, (cuuint64_t)L, 2 * (cuuint64_t)P->C};

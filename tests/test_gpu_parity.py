@@ -395,15 +395,18 @@ def test_tensor_core_other_tap_counts(binding, taps, grid):
           image_ref(w, echo), 2e-3 if taps == 4 else TOL_FP32)
 
 
+@pytest.mark.parametrize("rows", [0, 12])
 @pytest.mark.parametrize("case", ["mono", "multi", "ragged", "npad45", "offgrid", "taps4",
                                   "taps8", "bf16"])
-def test_sparse_products_match_dense_and_oracle(binding, case):
+def test_sparse_products_match_dense_and_oracle(binding, case, rows):
     # the 2:4-sparse products (window rows in residue order, K = [Re; Im]
     # rows of the table) against the dense products of the same plan layout
     # and against the oracle, on 2 mm grids (16-row windows): monostatic and
     # multistatic, a ragged pixel grid, 45 bins padded to 48, heights off the
-    # scan grid, 4, 6 and 8 taps, BF16-only products
-    opts = {}
+    # scan grid, 4, 6 and 8 taps, BF16-only products; windows of 16 rows, or
+    # on request (rows = 12) of 12 rows (residues mod 3) where the taps of
+    # every tile span at most 12 rows and w <= 6
+    opts = {"sparse_window_rows": rows}
     tol = TOL_FP32
     w = small_multi() if case == "multi" else wl.small_mono(seed=7)
     nx, ny = (37, 23) if case == "ragged" else (64, 64)
@@ -425,6 +428,7 @@ def test_sparse_products_match_dense_and_oracle(binding, case):
     print("%s: window rows %d, table rows %d, bins %d" % (case, sp.info["slab_rows"],
                                                          sp.info["table_len"], sp.info["tile_u"]))
     assert sp.info["sparse_products"] == 1 and de.info["sparse_products"] == 0
+    assert sp.info["slab_rows"] == (12 if rows == 12 and case != "taps8" else 16)
     nz = w.grid["nz"]
     d = float(np.linalg.norm(img - img_d) / np.linalg.norm(img_d))
     print("%s: sparse vs dense rel L2 %.3e" % (case, d))
@@ -432,11 +436,15 @@ def test_sparse_products_match_dense_and_oracle(binding, case):
     check("image tc sparse %s" % case, img.reshape(nz, -1), image_ref(w, echo), tol)
 
 
+@pytest.mark.parametrize("rows", [0, 12])
 @pytest.mark.parametrize("which", ["full_mono", "multi"])
-def test_sparse_products_full_size(binding, which):
+def test_sparse_products_full_size(binding, which, rows):
+    # full_mono: every tile's taps span at most 12 rows, so 12-row windows
+    # apply on request; multi (spans up to 14 rows) keeps 16
     w = wl.WORKLOADS[which](seed=0)
     echo = scene_echo(w, 0, n_pts=24)
-    sp, img = run_gpu(binding, w, echo, block_config=4)
+    sp, img = run_gpu(binding, w, echo, block_config=4, sparse_window_rows=rows)
+    assert sp.info["slab_rows"] == (12 if which == "full_mono" and rows == 12 else 16)
     de, img_d = run_gpu(binding, w, echo, block_config=4, dense_products=True)
     assert sp.info["sparse_products"] == 1
     d = float(np.linalg.norm(img - img_d) / np.linalg.norm(img_d))
