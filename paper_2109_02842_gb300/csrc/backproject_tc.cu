@@ -547,6 +547,107 @@ __device__ __forceinline__ void sparse_rows(int o, const float (&w)[W], float sn
     mB = nb[4] | (nb[5] << 4) | (nb[6] << 8) | (nb[7] << 12);
 }
 
+// Compressed 2:4-sparse A rows of one (pixel, channel) for a 32-row window
+// (the interleaved layout, K = the window's 32 rows): residue classes j of
+// the rows mod 4, row j + 4 e at K position 8 j + e (e < 8), so class j
+// spans the K groups 2 j and 2 j + 1. Taps t < 4 fall in distinct classes j
+// = (o + t) mod 4 at e = (o + t) / 4, tap t + 4 (< w) at e + 1: at most two
+// taps per class, in one group or straddling the two (e = 3, e + 1 = 4).
+// Each group keeps a pair of positions; a group without a tap keeps (0, 1)
+// with zero values. Rows re = Re A, im = Im A (BF16 hi, and lo for SPLIT 3;
+// word k = the kept pair of K group k); mA, mB the metadata of K 0..15 and
+// 16..31.
+template <int W, int SPLIT>
+__device__ __forceinline__ void sparse_rows32(int o, const float (&w)[W], float sn, float cs,
+                                              uint32_t (&reh)[8], uint32_t (&imh)[8],
+                                              uint32_t (&rel)[8], uint32_t (&iml)[8],
+                                              uint32_t &mA, uint32_t &mB) {
+    static_assert(W <= 8, "at most two taps per residue class");
+    constexpr uint32_t PAD = 0x4u;                  // kept positions (0, 1)
+    const int r = o & 3, ob = o >> 2;
+    // per tap t < 4 (its class): the kept pairs of the class's two groups
+    float v0[4][2], v1[4][2];
+    uint32_t nb[4][2];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int e = ob + ((r + t) >> 2);           // 0 .. 7
+        const int hi = e >> 2, pos = e & 3;
+        const bool two = t + 4 < W;
+        const float first = w[t];
+        const float second = two ? w[t + 4 < W ? t + 4 : t] : 0.f;
+        const bool straddle = two && pos == 3;       // e = 3: second tap at e = 4
+        // the group holding the (first) tap
+        float a0, a1;
+        uint32_t n;
+        if (pos <= 2) {
+            a0 = first;
+            a1 = second;
+            n = (uint32_t)pos | ((uint32_t)(pos + 1) << 2);
+        } else {
+            a0 = 0.f;
+            a1 = first;
+            n = 2u | (3u << 2);
+        }
+        // the other group keeps (0, 1) with zeros, except when straddling
+        // (then hi = 0): group 1 keeps (0, 1) = (w_{t+4}, 0)
+        const bool h1 = hi != 0;
+        v0[t][0] = h1 ? 0.f : a0;
+        v1[t][0] = h1 ? 0.f : a1;
+        nb[t][0] = h1 ? PAD : n;
+        v0[t][1] = h1 ? a0 : (straddle ? second : 0.f);
+        v1[t][1] = h1 ? a1 : 0.f;
+        nb[t][1] = h1 ? n : PAD;
+    }
+    // rotate from tap order t to class order j = (t + r) mod 4
+#pragma unroll
+    for (int step = 1; step < 4; ++step) {
+        if (step <= r) {
+            float l0[2], l1[2];
+            uint32_t ln[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                l0[h] = v0[3][h];
+                l1[h] = v1[3][h];
+                ln[h] = nb[3][h];
+            }
+#pragma unroll
+            for (int j = 3; j > 0; --j)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    v0[j][h] = v0[j - 1][h];
+                    v1[j][h] = v1[j - 1][h];
+                    nb[j][h] = nb[j - 1][h];
+                }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                v0[0][h] = l0[h];
+                v1[0][h] = l1[h];
+                nb[0][h] = ln[h];
+            }
+        }
+    }
+    uint32_t g[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 2 * j + h;
+            const float r0 = v0[j][h] * cs, r1 = v1[j][h] * cs;
+            const float i0 = v0[j][h] * sn, i1 = v1[j][h] * sn;
+            if (SPLIT == 3) {
+                split2(r0, r1, reh[k], rel[k]);
+                split2(i0, i1, imh[k], iml[k]);
+            } else {
+                reh[k] = bf2(r0, r1);
+                imh[k] = bf2(i0, i1);
+                rel[k] = iml[k] = 0u;
+            }
+            g[k] = nb[j][h];
+        }
+    mA = g[0] | (g[1] << 4) | (g[2] << 8) | (g[3] << 12);
+    mB = g[4] | (g[5] << 4) | (g[6] << 8) | (g[7] << 12);
+}
+
 // The same block with 2:4-sparse products (planar layout, one 16-row window
 // per channel, one channel per class round). The window's rows are taken in
 // residue order, K index 4 j + e <-> window row j + 4 e (j, e < 4): a pixel's
@@ -568,7 +669,7 @@ __device__ __forceinline__ void sparse_rows(int o, const float (&w)[W], float sn
 // a_done[class][r mod NSET], so that each release barrier runs through the
 // rounds of one set: a waiter never falls two phases behind the barrier it
 // tests (the parity of a phase test would not tell them apart).
-template <int W, int SPLIT, int NPAR, int NSET, int RW>
+template <int W, int SPLIT, int NPAR, int NSET, int RW, bool PLANAR>
 __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &ct,
                                               const TcArgs &ta, const CUtensorMap *tmap,
                                               const TileGeo *__restrict__ tgeo,
@@ -590,13 +691,15 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
     const int nbx = (p.nx + TCX - 1) / TCX, nby = (p.ny + TCY - 1) / TCY;
     const int bx = lin % nbx, by = (lin / nbx) % nby, bz = lin / (nbx * nby);
     const int tile = by * nbx + bx;
-    const int part = bz % ta.nsplit;             // planar: one bin block, bz = part
+    const int utile = bz / ta.nsplit, part = bz - utile * ta.nsplit;
+    const int u0 = utile * ta.UT;
     const int C = p.n_chan;
     const int cper = (C + ta.nsplit - 1) / ta.nsplit;
     const int cb = part * cper, ce = min(C, cb + cper);
     const TileGeo *tg = tgeo + (size_t)tile * C;
     const long long budget = ta.budget;
-    const uint32_t N = ta.UT;                    // the MMA's N (Re G, Im G columns)
+    // the MMA's N: planar Re G, Im G (UT columns each); interleaved P, Q (2 UT)
+    const uint32_t N = PLANAR ? ta.UT : 2 * ta.UT;
 
     if (warp < NCW) {
         // ------------------------------------------------ A rows (compressed)
@@ -608,7 +711,7 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
         const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
         const uint32_t abuf = lane_base + ta.acol + par * (NMAT * 8);
         const uint32_t mbuf = lane_base + ta.mcol + par * 8;
-        const float2 kT = kc_hl[0];
+        const float2 kT = kc_hl[u0];
         bool ok = true;
         const int rounds = ce - cb > par ? (ce - cb - par + NPAR - 1) / NPAR : 0;
         // round r's release: barrier a_done[par][r mod NSET], its phase r / NSET
@@ -626,8 +729,13 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
             int o;
             float w[W], sn, cs;
             channel_taps<W, RW>(p, ct, g, ddx, ddy, kT, o, w, sn, cs);
+            // planar: a1 = [Re A | -Im A], a3 = [Im A | Re A] over [Re rows |
+            // Im rows]; interleaved (32 rows): a1 = Re A, a3 = Im A
             uint32_t a1h[8], a3h[8], a1l[8], a3l[8], mA, mB;
-            sparse_rows<W, RW, SPLIT>(o, w, sn, cs, a1h, a3h, a1l, a3l, mA, mB);
+            if constexpr (RW == 32)
+                sparse_rows32<W, SPLIT>(o, w, sn, cs, a1h, a3h, a1l, a3l, mA, mB);
+            else
+                sparse_rows<W, RW, SPLIT>(o, w, sn, cs, a1h, a3h, a1l, a3l, mA, mB);
             // metadata word of this lane: rows (r, r + 8) of its 16-lane block,
             // K 0..15 in lanes r < 8 and K 16..31 in lanes r + 8
             const uint32_t oA = __shfl_xor_sync(0xffffffffu, mA, 8);
@@ -638,11 +746,11 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             tc05::fence_after_sync();
-            tc05::tmem_st8(abuf, a1h);                         // [Re A | -Im A] hi
-            tc05::tmem_st8(abuf + 8, a3h);                     // [Im A | Re A] hi
+            tc05::tmem_st8(abuf, a1h);                         // a1 hi
+            tc05::tmem_st8(abuf + 8, a3h);                     // a3 hi
             if (SPLIT == 3) {
-                tc05::tmem_st8(abuf + 16, a1l);                // [Re A | -Im A] lo
-                tc05::tmem_st8(abuf + 24, a3l);                // [Im A | Re A] lo
+                tc05::tmem_st8(abuf + 16, a1l);                // a1 lo
+                tc05::tmem_st8(abuf + 24, a3l);                // a3 lo
             }
             tc05::tmem_st1(mbuf, mword);
             tc05::tmem_wait_st();
@@ -671,11 +779,18 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
                 tc05::tmem_ld16(lane_base + N + 16 * ch, qv);
                 tc05::tmem_wait_ld();
                 if (!inside) continue;
+                // planar: 16 bins (Re G, Im G columns); interleaved: 8 bins
+                // ((re, im) pairs of P and Q: G = (P_re - Q_im, P_im + Q_re))
+                constexpr int NB = PLANAR ? 16 : 8;
 #pragma unroll
-                for (int b = 0; b < 16; ++b) {
-                    const int u = 16 * ch + b;
+                for (int b = 0; b < NB; ++b) {
+                    const int u = u0 + NB * ch + b;
                     if (u >= p.n_pad) continue;
-                    Gp[u * plane + pofs] = make_float2(__uint_as_float(pv[b]), __uint_as_float(qv[b]));
+                    const float2 v =
+                        PLANAR ? make_float2(__uint_as_float(pv[b]), __uint_as_float(qv[b]))
+                               : make_float2(__uint_as_float(pv[2 * b]) - __uint_as_float(qv[2 * b + 1]),
+                                             __uint_as_float(pv[2 * b + 1]) + __uint_as_float(qv[2 * b]));
+                    Gp[u * plane + pofs] = v;
                 }
             }
         } else if (lane == 0) {
@@ -685,7 +800,8 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
         // ------------------------------------------------ MMA issue
         const uint64_t d0 = tc05::smem_desc_sw128(tc05::smem_addr(smem), ta.cb_bytes, 1024);
         const uint32_t slot16 = ta.slot_bytes >> 4;
-        const uint32_t lo16 = (uint32_t)(RW * 2 * 128) >> 4;   // S_lo after S_hi
+        // S_lo after S_hi: planar [Re rows; Im rows], interleaved the rows
+        const uint32_t lo16 = (uint32_t)(RW * (PLANAR ? 2 : 1) * 128) >> 4;
         const uint32_t idsp = ta.idesc | (1u << 2);        // 2:4 sparse A
         const int n_groups = (ce - cb + NPAR - 1) / NPAR;
         bool ok = true;
@@ -707,7 +823,8 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
                     const uint32_t meta = tmem + ta.mcol + k * 8;
                     const uint64_t sh = d0 + (uint64_t)((sg * NPAR + k) * slot16);
                     const uint32_t acc = (g > 0 || k > 0) ? 1u : 0u;
-                    // Re G += [Re A | -Im A] S, Im G += [Im A | Re A] S
+                    // planar: Re G += [Re A | -Im A] S, Im G += [Im A | Re A] S;
+                    // interleaved: P += Re A B, Q += Im A B
                     tc05::mma_sp_ts(tmem, a1, sh, meta, idsp, acc);
                     tc05::mma_sp_ts(tmem + N, a1 + 8, sh, meta, idsp, acc);
                     if (SPLIT == 3) {
@@ -766,10 +883,12 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
                     const int cz = 2 * (cb + g * NPAR + k);
                     // rows ilo + j + NG e: group ilo / NG + e, row-in-group
                     // ilo % NG + j (NG = RW / 4)
-                    const int a0 = ilo[k] / (RW / 4), g0 = ilo[k] - a0 * (RW / 4);
+                    constexpr int NG = RW == 12 ? 3 : 4;
+                    const int a0 = ilo[k] / NG, g0 = ilo[k] - a0 * NG;
+                    const int x0 = PLANAR ? 0 : 2 * u0;
                     for (int j = 0; j < ta.ncb; ++j)
-                        tc05::tma_load_5d(dst + (size_t)j * ta.cb_bytes, tmap, &b_full[sg], 64 * j,
-                                          a0, g0, 0, cz);
+                        tc05::tma_load_5d(dst + (size_t)j * ta.cb_bytes, tmap, &b_full[sg],
+                                          x0 + 64 * j, a0, g0, 0, cz);
                 }
             }
             issued = g + 1;
@@ -842,7 +961,7 @@ struct SpWarps {
     static constexpr int threads = (4 * NPAR * NSET + 2) * 32;   // + MMA warp + TMA warp
 };
 
-template <int W, int SPLIT, int NPAR, int NSET, int RW>
+template <int W, int SPLIT, int NPAR, int NSET, int RW, bool PLANAR>
 __global__ void __launch_bounds__(SpWarps<NPAR, NSET>::threads, 1)
 k_backproject_tc_sp(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ CUtensorMap tmap,
                     const TileGeo *__restrict__ tgeo, const float2 *__restrict__ kc_hl,
@@ -884,7 +1003,7 @@ k_backproject_tc_sp(BpDesc p, CoefTable ct, TcArgs ta, const __grid_constant__ C
     __syncthreads();
     tc05::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    bp_tc_item_sp<W, SPLIT, NPAR, NSET, RW>(p, ct, ta, &tmap, tgeo, kc_hl, G, err,
+    bp_tc_item_sp<W, SPLIT, NPAR, NSET, RW, PLANAR>(p, ct, ta, &tmap, tgeo, kc_hl, G, err,
                                             (int)blockIdx.x + ta.blk0, smem, bars, tmem, &dbg_bar);
     tc05::fence_before_sync();
     __syncthreads();
@@ -1029,19 +1148,19 @@ cudaError_t launch_pl(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, co
                      : launch_t<W, KS, SPLIT, NPAR, false, 1>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
 }
 
-template <int W, int SPLIT, int NPAR, int RW>
+template <int W, int SPLIT, int NPAR, int RW, bool PLANAR = true>
 cudaError_t launch_sp(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
                       const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
                       cudaStream_t st) {
     const size_t smem = backproject_tc_smem_bytes(ta);
     constexpr int NSET = 2;
-    cudaError_t e = cudaFuncSetAttribute(k_backproject_tc_sp<W, SPLIT, NPAR, NSET, RW>,
+    cudaError_t e = cudaFuncSetAttribute(k_backproject_tc_sp<W, SPLIT, NPAR, NSET, RW, PLANAR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int total = backproject_tc_blocks(p, ta);
     const int nblk = ta.nblk > 0 ? ta.nblk : total - ta.blk0;
     if (ta.blk0 < 0 || nblk <= 0 || ta.blk0 + nblk > total) return cudaErrorInvalidValue;
-    k_backproject_tc_sp<W, SPLIT, NPAR, NSET, RW>
+    k_backproject_tc_sp<W, SPLIT, NPAR, NSET, RW, PLANAR>
         <<<nblk, SpWarps<NPAR, NSET>::threads, smem, st>>>(p, ct, ta, tm, tgeo, kc_hl, G, err);
     return cudaGetLastError();
 }
@@ -1050,6 +1169,14 @@ template <int SPLIT, int NPAR>
 cudaError_t launch_spw(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
                        const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
                        cudaStream_t st) {
+    if (ta.rw == 32) {                  // interleaved layout, 32-row windows
+        switch (p.w) {
+            case 4: return launch_sp<4, SPLIT, NPAR, 32, false>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+            case 6: return launch_sp<6, SPLIT, NPAR, 32, false>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+            case 8: return launch_sp<8, SPLIT, NPAR, 32, false>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (ta.rw == 12) {                  // 12-row windows: w <= 6
         switch (p.w) {
             case 4: return launch_sp<4, SPLIT, NPAR, 12>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
@@ -1125,7 +1252,9 @@ cudaError_t launch_backproject_tc(const BpDesc &p, const CoefTable &ct, const Tc
                                   const CUtensorMap &tm, const TileGeo *tgeo, const float2 *kc_hl,
                                   float2 *G, int *err, cudaStream_t st) {
     if (ta.sparse) {
-        if (ta.ks != 1 || !ta.planar || ta.cpr != 1) return cudaErrorInvalidValue;
+        const bool ok = ta.cpr == 1 && ((ta.planar && ta.ks == 1 && ta.rw != 32) ||
+                                        (!ta.planar && ta.ks == 2 && ta.rw == 32));
+        if (!ok) return cudaErrorInvalidValue;
         if (ta.npar == 3)
             return ta.split == 3 ? launch_spw<3, 3>(p, ct, ta, tm, tgeo, kc_hl, G, err, st)
                                  : launch_spw<1, 3>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);

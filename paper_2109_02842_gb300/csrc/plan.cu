@@ -81,18 +81,24 @@ EncodeTiledFn encode_tiled_fn();
 // [plane][Re / Im][j][e]. The row-in-group dimension has 2 NG - 1 entries
 // over overlapping rows, so any first row i is reachable; the last group
 // ends inside the channel's plane (rows NG (ng - 1) + 2 NG - 2 < L).
+// The interleaved table [c][hi/lo][row][tc_cols columns of (re, im) pairs]
+// with 32-row windows (rw = 32, `part` = tc_cols): no Re / Im dimension
+// (extent 1), 8 row groups of 4 rows, a box holding rows i + j + 4 e in the
+// order [plane][j][e] (j < 4, e < 8).
 bool encode_sparse_map(CUtensorMap *m, void *table, int part, int L, int C, int planes,
                        int rw) {
     EncodeTiledFn enc = encode_tiled_fn();
-    const int NG = rw / 4;
-    if (!enc || (rw != 16 && rw != 12) || L < 2 * NG) return false;
-    const cuuint64_t pitch = (cuuint64_t)part * 2 * 2;
+    const int NG = rw == 12 ? 3 : 4;
+    const bool planar = rw != 32;
+    if (!enc || (rw != 16 && rw != 12 && rw != 32) || L < 2 * NG) return false;
+    const cuuint64_t pitch = (cuuint64_t)part * 2 * (planar ? 2 : 1);
     const cuuint64_t ng = (cuuint64_t)((L - (2 * NG - 1)) / NG + 1);
-    const cuuint64_t dims[5] = {(cuuint64_t)part, ng, (cuuint64_t)(2 * NG - 1), 2,
-                                2 * (cuuint64_t)C};
-    const cuuint64_t strides[4] = {(cuuint64_t)NG * pitch, pitch, (cuuint64_t)part * 2,
-                                   (cuuint64_t)L * pitch};
-    const cuuint32_t box[5] = {64, 4, (cuuint32_t)NG, 2, (cuuint32_t)planes};
+    const cuuint64_t dims[5] = {(cuuint64_t)part, ng, (cuuint64_t)(2 * NG - 1),
+                                (cuuint64_t)(planar ? 2 : 1), 2 * (cuuint64_t)C};
+    const cuuint64_t strides[4] = {(cuuint64_t)NG * pitch, pitch,
+                                   planar ? (cuuint64_t)part * 2 : pitch, (cuuint64_t)L * pitch};
+    const cuuint32_t box[5] = {64, (cuuint32_t)(rw / NG), (cuuint32_t)NG,
+                               (cuuint32_t)(planar ? 2 : 1), (cuuint32_t)planes};
     const cuuint32_t es[5] = {1, 1, 1, 1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, table, dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -523,16 +529,24 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         // (on request, windows of 12 rows, residues mod 3, where every
         // tile's taps span at most 12 rows and w <= 6: a quarter fewer bytes
         // per copy)
+        // The interleaved layout with 32-row windows takes them too (one
+        // sparse product per real product covers the whole window).
         P->tc.sparse = 0;
         P->tc.rw = 16;
-        if (!o.dense_products && P->tc.planar && ks == 1 && !o.one_block_per_sm &&
-            (W == 4 || W == 6 || W == 8) && tc_npar_sp(P->tile_u, npl) > 0) {
-            const int rw = (stats[0] <= 12 && W <= 6 && o.sparse_window_rows == 12) ? 12 : 16;
+        const bool sp_planar = P->tc.planar && ks == 1 && tc_npar_sp(P->tile_u, npl) > 0;
+        const bool sp_inter = !P->tc.planar && ks == 2 && tc_npar_sp(2 * P->tile_u, npl) > 0;
+        if (!o.dense_products && (sp_planar || sp_inter) && !o.one_block_per_sm &&
+            (W == 4 || W == 6 || W == 8)) {
+            const int rw = sp_inter ? 32
+                                    : (stats[0] <= 12 && W <= 6 && o.sparse_window_rows == 12) ? 12
+                                                                                               : 16;
+            const int part = sp_inter ? 2 * P->tile_u * ((P->Np + P->tile_u - 1) / P->tile_u)
+                                      : P->tile_u;
             CUtensorMap trial{};
             alignas(64) static unsigned char probe_buf[64];
             // the encoder only checks the layout (the address is not read)
             const uintptr_t fake = (reinterpret_cast<uintptr_t>(probe_buf) + 63) & ~(uintptr_t)63;
-            if (encode_sparse_map(&trial, reinterpret_cast<void *>(fake), P->tile_u, L + 4, P->C,
+            if (encode_sparse_map(&trial, reinterpret_cast<void *>(fake), part, L + 4, P->C,
                                   P->precision >= 1 ? 1 : 2, rw)) {
                 P->tc.sparse = 1;
                 P->tc.rw = rw;
@@ -580,13 +594,14 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         ta.tmem_cols = ta.npar == 2 ? 256 : 512;
         ta.acol = 2 * N;
         if (ta.sparse) {
-            // per 64-column block: [hi: Re rows, Im rows][lo: Re rows, Im rows]
-            // (rw rows each); 12-row windows end in a 1 KB zero pad
-            ta.cb_bytes = (unsigned)(planes * 2 * ta.rw * 128);
+            // per 64-column block: planar [hi: Re rows, Im rows][lo: Re rows,
+            // Im rows] (rw rows each; 12-row windows end in a 1 KB zero pad),
+            // interleaved [hi rows][lo rows] (32 each)
+            ta.cb_bytes = (unsigned)(planes * (ta.planar ? 2 : 1) * ta.rw * 128);
             ta.im_off = 0;
             ta.slot_bytes = (unsigned)ta.ncb * ta.cb_bytes + (ta.rw == 12 ? 1024u : 0u);
-            ta.npar = tc_npar_sp(ta.UT, npl);
-            ta.tmem_cols = tc_cols_sp(ta.UT, ta.npar, npl) <= 256 ? 256 : 512;
+            ta.npar = tc_npar_sp(N, npl);
+            ta.tmem_cols = tc_cols_sp(N, ta.npar, npl) <= 256 ? 256 : 512;
             ta.mcol = ta.acol + ta.npar * npl * 8;
         }
         // two channels per class round (twice the products per A wait and
@@ -709,8 +724,8 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         if (!enc) return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled not available");
         const TcArgs &ta = P->tc;
         if (ta.sparse) {
-            if (!encode_sparse_map(&P->tmap, P->d_table, ta.UT, L, P->C, ta.split == 3 ? 2 : 1,
-                                   ta.rw))
+            if (!encode_sparse_map(&P->tmap, P->d_table, ta.planar ? ta.UT : d.tc_cols, L, P->C,
+                                   ta.split == 3 ? 2 : 1, ta.rw))
                 return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled failed (sparse table map)");
         } else {
             const cuuint64_t dims[3] = {(cuuint64_t)d.tc_cols, (cuuint64_t)L, 2 * (cuuint64_t)P->C};

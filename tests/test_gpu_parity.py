@@ -436,6 +436,38 @@ def test_sparse_products_match_dense_and_oracle(binding, case, rows):
     check("image tc sparse %s" % case, img.reshape(nz, -1), image_ref(w, echo), tol)
 
 
+@pytest.mark.parametrize("case", ["tile16", "tile48", "multi", "ragged", "taps8", "bf16"])
+def test_sparse_products_interleaved_32_row_windows(binding, case):
+    # the interleaved layout (blocks of tile_u bins, accumulators P and Q)
+    # with 32-row windows (the 6.25 mm grid of small_mono): one sparse product
+    # per real product covers the whole window, rows in residue order mod 4
+    # (K position 8 j + e <-> row j + 4 e)
+    opts = {"tile_u": 48 if case == "tile48" else 16}
+    tol = TOL_FP32
+    w = small_multi() if case == "multi" else wl.small_mono(seed=8)
+    if case == "ragged":
+        # pixel counts off the tile and heights off the scan grid
+        w.grid = dict(w.grid, nx=37, ny=23, nz=7, z0=-0.031, dz=0.0093)
+    elif case.startswith("taps"):
+        opts["nufft_w"] = int(case[4:])
+        tol = 2e-3 if case == "taps4" else TOL_FP32
+    elif case == "bf16":
+        opts["precision"] = 1
+        tol = TOL_BF16
+    echo = scene_echo(w, 8)
+    sp, img = run_gpu(binding, w, echo, block_config=4, **opts)
+    de, img_d = run_gpu(binding, w, echo, block_config=4, dense_products=True, **opts)
+    print("%s: window rows %d, bins per block %d, table rows %d" % (
+        case, sp.info["slab_rows"], sp.info["tile_u"], sp.info["table_len"]))
+    assert sp.info["slab_rows"] == 32 and sp.info["table_layout"] == 2
+    assert sp.info["sparse_products"] == 1 and de.info["sparse_products"] == 0
+    d = float(np.linalg.norm(img - img_d) / np.linalg.norm(img_d))
+    print("%s: sparse vs dense rel L2 %.3e" % (case, d))
+    assert d < (1e-3 if case == "bf16" else 3e-5)
+    check("image tc sparse interleaved %s" % case, img.reshape(w.grid["nz"], -1),
+          image_ref(w, echo), tol)
+
+
 @pytest.mark.parametrize("rows", [0, 12])
 @pytest.mark.parametrize("which", ["full_mono", "multi"])
 def test_sparse_products_full_size(binding, which, rows):
