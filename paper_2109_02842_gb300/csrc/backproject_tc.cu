@@ -472,7 +472,11 @@ __device__ __forceinline__ void bp_tc_item(const BpDesc &p, const CoefTable &ct,
 // groups when NG = 3), so the rows are a1 = [Re A | -Im A] and a3 = [Im A |
 // Re A] (BF16 hi, and lo for SPLIT 3; word k = the kept pair of K group k)
 // and mA, mB the metadata of K 0..15 and 16..31.
-template <int W, int RW, int SPLIT>
+// INTER (interleaved layout, RW = 16, SPLIT = 3): the K = 32 operand is
+// instead the window's [hi rows | lo rows] and the rows are a1 = [Re A_hi |
+// Re A_hi], a3 = [Im A_hi | Im A_hi] (products A_hi b_hi + A_hi b_lo) and
+// a1l = [Re A_lo | 0], a3l = [Im A_lo | 0] (A_lo b_hi).
+template <int W, int RW, int SPLIT, bool INTER = false>
 __device__ __forceinline__ void sparse_rows(int o, const float (&w)[W], float sn, float cs,
                                             uint32_t (&a1h)[8], uint32_t (&a3h)[8],
                                             uint32_t (&a1l)[8], uint32_t (&a3l)[8],
@@ -533,14 +537,21 @@ __device__ __forceinline__ void sparse_rows(int o, const float (&w)[W], float sn
             ih = bf2(i0, i1);
             rl = il = 0u;
         }
-        a1h[j] = rh;
-        a1h[NG + j] = ih ^ NEG;
-        a3h[j] = ih;
-        a3h[NG + j] = rh;
-        a1l[j] = rl;
-        a1l[NG + j] = il ^ NEG;
-        a3l[j] = il;
-        a3l[NG + j] = rl;
+        if (INTER) {
+            a1h[j] = a1h[NG + j] = rh;
+            a3h[j] = a3h[NG + j] = ih;
+            a1l[j] = rl;
+            a3l[j] = il;
+        } else {
+            a1h[j] = rh;
+            a1h[NG + j] = ih ^ NEG;
+            a3h[j] = ih;
+            a3h[NG + j] = rh;
+            a1l[j] = rl;
+            a1l[NG + j] = il ^ NEG;
+            a3l[j] = il;
+            a3l[NG + j] = rl;
+        }
         nb[j] = nb[NG + j] = nib[j];
     }
     mA = nb[0] | (nb[1] << 4) | (nb[2] << 8) | (nb[3] << 12);
@@ -735,7 +746,7 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
             if constexpr (RW == 32)
                 sparse_rows32<W, SPLIT>(o, w, sn, cs, a1h, a3h, a1l, a3l, mA, mB);
             else
-                sparse_rows<W, RW, SPLIT>(o, w, sn, cs, a1h, a3h, a1l, a3l, mA, mB);
+                sparse_rows<W, RW, SPLIT, !PLANAR>(o, w, sn, cs, a1h, a3h, a1l, a3l, mA, mB);
             // metadata word of this lane: rows (r, r + 8) of its 16-lane block,
             // K 0..15 in lanes r < 8 and K 16..31 in lanes r + 8
             const uint32_t oA = __shfl_xor_sync(0xffffffffu, mA, 8);
@@ -827,11 +838,16 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
                     // interleaved: P += Re A B, Q += Im A B
                     tc05::mma_sp_ts(tmem, a1, sh, meta, idsp, acc);
                     tc05::mma_sp_ts(tmem + N, a1 + 8, sh, meta, idsp, acc);
-                    if (SPLIT == 3) {
+                    if (SPLIT == 3 && (PLANAR || RW == 32)) {
                         const uint64_t sl = sh + lo16;
                         tc05::mma_sp_ts(tmem, a1, sl, meta, idsp, 1u);
                         tc05::mma_sp_ts(tmem, a1 + 16, sh, meta, idsp, 1u);
                         tc05::mma_sp_ts(tmem + N, a1 + 8, sl, meta, idsp, 1u);
+                        tc05::mma_sp_ts(tmem + N, a1 + 24, sh, meta, idsp, 1u);
+                    } else if (SPLIT == 3) {
+                        // interleaved 16-row windows: S = [hi rows | lo rows],
+                        // the first two products took A_hi (b_hi + b_lo)
+                        tc05::mma_sp_ts(tmem, a1 + 16, sh, meta, idsp, 1u);
                         tc05::mma_sp_ts(tmem + N, a1 + 24, sh, meta, idsp, 1u);
                     }
                     tc05::mma_commit(&a_done[k * NSET + g % NSET]);
@@ -1177,6 +1193,17 @@ cudaError_t launch_spw(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, c
             default: return cudaErrorInvalidValue;
         }
     }
+    if (!ta.planar) {                   // interleaved layout, 16-row windows
+        if constexpr (SPLIT == 3) {
+            switch (p.w) {
+                case 4: return launch_sp<4, 3, NPAR, 16, false>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+                case 6: return launch_sp<6, 3, NPAR, 16, false>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+                case 8: return launch_sp<8, 3, NPAR, 16, false>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+                default: return cudaErrorInvalidValue;
+            }
+        }
+        return cudaErrorInvalidValue;
+    }
     if (ta.rw == 12) {                  // 12-row windows: w <= 6
         switch (p.w) {
             case 4: return launch_sp<4, SPLIT, NPAR, 12>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
@@ -1253,7 +1280,9 @@ cudaError_t launch_backproject_tc(const BpDesc &p, const CoefTable &ct, const Tc
                                   float2 *G, int *err, cudaStream_t st) {
     if (ta.sparse) {
         const bool ok = ta.cpr == 1 && ((ta.planar && ta.ks == 1 && ta.rw != 32) ||
-                                        (!ta.planar && ta.ks == 2 && ta.rw == 32));
+                                        (!ta.planar && ta.ks == 2 && ta.rw == 32) ||
+                                        (!ta.planar && ta.ks == 1 && ta.rw == 16 &&
+                                         ta.split == 3));
         if (!ok) return cudaErrorInvalidValue;
         if (ta.npar == 3)
             return ta.split == 3 ? launch_spw<3, 3>(p, ct, ta, tm, tgeo, kc_hl, G, err, st)

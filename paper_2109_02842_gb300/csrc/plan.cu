@@ -82,14 +82,13 @@ EncodeTiledFn encode_tiled_fn();
 // over overlapping rows, so any first row i is reachable; the last group
 // ends inside the channel's plane (rows NG (ng - 1) + 2 NG - 2 < L).
 // The interleaved table [c][hi/lo][row][tc_cols columns of (re, im) pairs]
-// with 32-row windows (rw = 32, `part` = tc_cols): no Re / Im dimension
-// (extent 1), 8 row groups of 4 rows, a box holding rows i + j + 4 e in the
-// order [plane][j][e] (j < 4, e < 8).
+// (planar = false, `part` = tc_cols, rw = 16 or 32): no Re / Im dimension
+// (extent 1), rw / 4 row groups of 4 rows, a box holding rows i + j + 4 e in
+// the order [plane][j][e] (j < 4, e < rw / 4).
 bool encode_sparse_map(CUtensorMap *m, void *table, int part, int L, int C, int planes,
-                       int rw) {
+                       int rw, bool planar) {
     EncodeTiledFn enc = encode_tiled_fn();
     const int NG = rw == 12 ? 3 : 4;
-    const bool planar = rw != 32;
     if (!enc || (rw != 16 && rw != 12 && rw != 32) || L < 2 * NG) return false;
     const cuuint64_t pitch = (cuuint64_t)part * 2 * (planar ? 2 : 1);
     const cuuint64_t ng = (cuuint64_t)((L - (2 * NG - 1)) / NG + 1);
@@ -533,11 +532,14 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         // sparse product per real product covers the whole window).
         P->tc.sparse = 0;
         P->tc.rw = 16;
+        // (interleaved 16-row windows only with the hi/lo split: the K = 32
+        // operand is the window's hi rows and lo rows)
         const bool sp_planar = P->tc.planar && ks == 1 && tc_npar_sp(P->tile_u, npl) > 0;
-        const bool sp_inter = !P->tc.planar && ks == 2 && tc_npar_sp(2 * P->tile_u, npl) > 0;
+        const bool sp_inter = !P->tc.planar && tc_npar_sp(2 * P->tile_u, npl) > 0 &&
+                              (ks == 2 || P->precision == 0);
         if (!o.dense_products && (sp_planar || sp_inter) && !o.one_block_per_sm &&
             (W == 4 || W == 6 || W == 8)) {
-            const int rw = sp_inter ? 32
+            const int rw = sp_inter ? 16 * ks
                                     : (stats[0] <= 12 && W <= 6 && o.sparse_window_rows == 12) ? 12
                                                                                                : 16;
             const int part = sp_inter ? 2 * P->tile_u * ((P->Np + P->tile_u - 1) / P->tile_u)
@@ -547,7 +549,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
             // the encoder only checks the layout (the address is not read)
             const uintptr_t fake = (reinterpret_cast<uintptr_t>(probe_buf) + 63) & ~(uintptr_t)63;
             if (encode_sparse_map(&trial, reinterpret_cast<void *>(fake), part, L + 4, P->C,
-                                  P->precision >= 1 ? 1 : 2, rw)) {
+                                  P->precision >= 1 ? 1 : 2, rw, !sp_inter)) {
                 P->tc.sparse = 1;
                 P->tc.rw = rw;
                 P->R = rw;
@@ -596,7 +598,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         if (ta.sparse) {
             // per 64-column block: planar [hi: Re rows, Im rows][lo: Re rows,
             // Im rows] (rw rows each; 12-row windows end in a 1 KB zero pad),
-            // interleaved [hi rows][lo rows] (32 each)
+            // interleaved [hi rows][lo rows] (rw each)
             ta.cb_bytes = (unsigned)(planes * (ta.planar ? 2 : 1) * ta.rw * 128);
             ta.im_off = 0;
             ta.slot_bytes = (unsigned)ta.ncb * ta.cb_bytes + (ta.rw == 12 ? 1024u : 0u);
@@ -725,7 +727,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         const TcArgs &ta = P->tc;
         if (ta.sparse) {
             if (!encode_sparse_map(&P->tmap, P->d_table, ta.planar ? ta.UT : d.tc_cols, L, P->C,
-                                   ta.split == 3 ? 2 : 1, ta.rw))
+                                   ta.split == 3 ? 2 : 1, ta.rw, ta.planar != 0))
                 return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled failed (sparse table map)");
         } else {
             const cuuint64_t dims[3] = {(cuuint64_t)d.tc_cols, (cuuint64_t)L, 2 * (cuuint64_t)P->C};

@@ -436,15 +436,26 @@ def test_sparse_products_match_dense_and_oracle(binding, case, rows):
     check("image tc sparse %s" % case, img.reshape(nz, -1), image_ref(w, echo), tol)
 
 
-@pytest.mark.parametrize("case", ["tile16", "tile48", "multi", "ragged", "taps8", "bf16"])
-def test_sparse_products_interleaved_32_row_windows(binding, case):
-    # the interleaved layout (blocks of tile_u bins, accumulators P and Q)
-    # with 32-row windows (the 6.25 mm grid of small_mono): one sparse product
-    # per real product covers the whole window, rows in residue order mod 4
-    # (K position 8 j + e <-> row j + 4 e)
-    opts = {"tile_u": 48 if case == "tile48" else 16}
+@pytest.mark.parametrize("case", ["tile16", "tile48", "multi", "ragged", "taps8", "bf16",
+                                  "fine16", "fine48", "fine_multi", "fine_taps4"])
+def test_sparse_products_interleaved_layout(binding, case):
+    # the interleaved layout (blocks of tile_u bins, accumulators P and Q).
+    # 32-row windows (the 6.25 mm grid of small_mono): one sparse product per
+    # real product covers the whole window, rows in residue order mod 4 (K
+    # position 8 j + e <-> row j + 4 e). 16-row windows (fine*: a 2 mm grid):
+    # the K = 32 operand is the window's hi rows then its lo rows, so
+    # [A_hi | A_hi] takes A_hi (b_hi + b_lo) in one sparse product and
+    # [A_lo | 0] the A_lo b_hi term
+    opts = {"tile_u": 48 if case in ("tile48", "fine48") else 16}
     tol = TOL_FP32
-    w = small_multi() if case == "multi" else wl.small_mono(seed=8)
+    w = small_multi() if case in ("multi", "fine_multi") else wl.small_mono(seed=8)
+    fine = case.startswith("fine")
+    if fine:
+        x0, dx = wl.centred_axis(0.128, 64)
+        w.grid = dict(w.grid, x0=x0, dx=dx, nx=64, y0=x0, dy=dx, ny=64, nz=8)
+    if case == "fine_taps4":
+        opts["nufft_w"] = 4
+        tol = 2e-3
     if case == "ragged":
         # pixel counts off the tile and heights off the scan grid
         w.grid = dict(w.grid, nx=37, ny=23, nz=7, z0=-0.031, dz=0.0093)
@@ -459,7 +470,7 @@ def test_sparse_products_interleaved_32_row_windows(binding, case):
     de, img_d = run_gpu(binding, w, echo, block_config=4, dense_products=True, **opts)
     print("%s: window rows %d, bins per block %d, table rows %d" % (
         case, sp.info["slab_rows"], sp.info["tile_u"], sp.info["table_len"]))
-    assert sp.info["slab_rows"] == 32 and sp.info["table_layout"] == 2
+    assert sp.info["slab_rows"] == (16 if fine else 32) and sp.info["table_layout"] == 2
     assert sp.info["sparse_products"] == 1 and de.info["sparse_products"] == 0
     d = float(np.linalg.norm(img - img_d) / np.linalg.norm(img_d))
     print("%s: sparse vs dense rel L2 %.3e" % (case, d))
