@@ -162,14 +162,18 @@ typedef struct {
      * memory, so that the call returns PL_ERR_OOM and frees what it had
      * allocated. 0 = off (default). */
     int debug_fail_alloc;
-    /* block_config 4, planar layout with 16-row windows: by default the
-     * back-projection's products are 2:4 sparse (tcgen05.mma.sp). A window's
-     * rows are taken in residue order (K index 4 j + e <-> row j + 4 e), in
-     * which a pixel's w consecutive taps leave at most two nonzeros in every
-     * group of four; with the K operand [Re rows; Im rows] of the table a
-     * channel takes six sparse products instead of twelve dense ones. The
-     * sums are the same up to rounding order. dense_products = 1 keeps the
-     * dense products. */
+    /* block_config 4: by default the back-projection's products are 2:4
+     * sparse (tcgen05.mma.sp) in the planar layout with 16-row windows and in
+     * the interleaved layout (16-row windows with the hi/lo split, 32-row
+     * windows). A window's rows are taken in residue order (K index 4 j + e
+     * <-> row j + 4 e; over 32 rows 8 j + e), in which a pixel's w
+     * consecutive taps leave at most two nonzeros in every group of four. The
+     * K = 32 operand is the window's [Re rows; Im rows] (planar: six sparse
+     * products per channel instead of twelve dense), its [hi rows; lo rows]
+     * (interleaved, 16 rows: four instead of six) or its 32 rows
+     * (interleaved, 32 rows: six instead of twelve). The sums are the same up
+     * to rounding order. dense_products = 1 keeps the dense products
+     * (pl_info.sparse_products says which run). */
     int dense_products;
     /* The sparse products' window: 0 = 16 rows (default); 12 = 12 rows
      * (residues mod 3) where every tile's taps span at most 12 rows and
