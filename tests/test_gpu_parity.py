@@ -479,6 +479,38 @@ def test_sparse_products_interleaved_layout(binding, case):
           image_ref(w, echo), tol)
 
 
+@pytest.mark.parametrize("case", ["one_channel", "three_channels", "one_pixel", "one_frequency",
+                                  "seven_bins"])
+def test_sparse_products_degenerate_sizes(binding, case):
+    # the sparse kernel at the edges of its sizes (2 mm grid, 16-row
+    # windows): fewer channels than channel classes x warp sets (classes and
+    # sets without a round), a single pixel (one tile, 127 idle lanes), a
+    # single frequency (a band of one wavenumber), seven k_z bins (N = 16)
+    w = wl.small_mono(seed=9)
+    x0, dx = wl.centred_axis(0.128, 64)
+    w.grid = dict(w.grid, x0=x0, dx=dx, nx=64, y0=x0, dy=dx, ny=64, nz=8)
+    if case == "one_channel":
+        idx = np.array([21])
+    elif case == "three_channels":
+        idx = np.array([3, 30, 57])
+    else:
+        idx = None
+    if idx is not None:
+        w.elem_xy, w.elem_section = w.elem_xy[idx], w.elem_section[idx]
+    if case == "one_pixel":
+        w.grid = dict(w.grid, x0=0.013, nx=1, y0=-0.021, ny=1, nz=3)
+    elif case == "one_frequency":
+        w.f_hz = w.f_hz[7:8]
+    elif case == "seven_bins":
+        w.n_scan, w.n_pad = 7, 7
+        w.grid = dict(w.grid, nz=5, z0=w.z0, dz=w.dz)
+    echo = scene_echo(w, 9)
+    plan, img = run_gpu(binding, w, echo, block_config=4)
+    assert plan.info["sparse_products"] == 1, plan.info
+    check("image tc sparse %s" % case, img.reshape(w.grid["nz"], -1), image_ref(w, echo),
+          TOL_FP32)
+
+
 @pytest.mark.parametrize("rows", [0, 12])
 @pytest.mark.parametrize("which", ["full_mono", "multi"])
 def test_sparse_products_full_size(binding, which, rows):
