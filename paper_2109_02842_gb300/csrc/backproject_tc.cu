@@ -279,7 +279,8 @@ __device__ __forceinline__ void bp_tc_item(const BpDesc &p, const CoefTable &ct,
             const bool inside = ix < p.nx && iy < p.ny;
             const size_t plane = (size_t)p.nx * p.ny;
             const size_t pofs = (size_t)iy * p.nx + ix;
-            float2 *Gp = G + (size_t)part * p.n_pad * plane;   // this channel part's spectrum
+            // this channel part's spectrum, or the one all parts add into
+            float2 *Gp = G + (size_t)(ta.g_atomic ? 0 : part) * p.n_pad * plane;
             for (int ch = par; ch < (int)(N / 16); ch += NPAR) {
                 uint32_t pv[16], qv[16];
                 tc05::tmem_ld16(lane_base + 16 * ch, pv);
@@ -297,7 +298,10 @@ __device__ __forceinline__ void bp_tc_item(const BpDesc &p, const CoefTable &ct,
                         PLANAR ? make_float2(__uint_as_float(pv[b]), __uint_as_float(qv[b]))
                                : make_float2(__uint_as_float(pv[2 * b]) - __uint_as_float(qv[2 * b + 1]),
                                              __uint_as_float(pv[2 * b + 1]) + __uint_as_float(qv[2 * b]));
-                    Gp[u * plane + pofs] = v;
+                    if (ta.g_atomic)
+                        atomicAdd(&Gp[u * plane + pofs], v);
+                    else
+                        Gp[u * plane + pofs] = v;
                 }
             }
         } else if (lane == 0) {
@@ -783,7 +787,7 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
             const bool inside = ix < p.nx && iy < p.ny;
             const size_t plane = (size_t)p.nx * p.ny;
             const size_t pofs = (size_t)iy * p.nx + ix;
-            float2 *Gp = G + (size_t)part * p.n_pad * plane;
+            float2 *Gp = G + (size_t)(ta.g_atomic ? 0 : part) * p.n_pad * plane;
             for (int ch = warp >> 2; ch < (int)(N / 16); ch += NPAR * NSET) {
                 uint32_t pv[16], qv[16];
                 tc05::tmem_ld16(lane_base + 16 * ch, pv);
@@ -801,7 +805,10 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
                         PLANAR ? make_float2(__uint_as_float(pv[b]), __uint_as_float(qv[b]))
                                : make_float2(__uint_as_float(pv[2 * b]) - __uint_as_float(qv[2 * b + 1]),
                                              __uint_as_float(pv[2 * b + 1]) + __uint_as_float(qv[2 * b]));
-                    Gp[u * plane + pofs] = v;
+                    if (ta.g_atomic)
+                        atomicAdd(&Gp[u * plane + pofs], v);
+                    else
+                        Gp[u * plane + pofs] = v;
                 }
             }
         } else if (lane == 0) {

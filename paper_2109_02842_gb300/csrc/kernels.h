@@ -163,6 +163,9 @@ struct TcArgs {
     int mcol;            // sparse: first TMEM column of the classes' metadata (8 apart)
     int rw;              // sparse: window rows, 16 (residues mod 4) or 12 (mod 3, w <= 6;
                          // each window slot then ends in a 1 KB zero pad)
+    int g_atomic;        // 1: the channel parts add their sums into one spectrum G
+                         // (atomic adds onto a zeroed G: two terms per value, in either
+                         // order the same sum); 0: part p writes spectrum p
 };
 // blocks of a whole back-projection
 int backproject_tc_blocks(const BpDesc &p, const TcArgs &ta);

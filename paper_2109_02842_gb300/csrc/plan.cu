@@ -636,6 +636,10 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         // proportion to that count); the parts also fill the SMs' last wave
         // better than one block per tile.
         ta.nsplit = ta.planar && P->C >= 2 * ta.npar ? 2 : 1;
+        // the parts add into one spectrum (zeroed first), so the inverse
+        // transform reads one spectrum instead of two; the batch's
+        // persistent kernel (one_block_per_sm) keeps one spectrum per part
+        ta.g_atomic = (ta.nsplit == 2 && !o.one_block_per_sm) ? 1 : 0;
     } else if (backproject_smem_bytes(P->R, P->tile_u, P->C, P->precision >= 1, P->block_config) > 200 * 1024)
         return fail(PL_ERR_UNSUPPORTED, "table window too tall for shared memory (grid too coarse)");
     for (int tp = 0; tp < W; ++tp) es_tap_polynomial(W, (double)d.beta, tp, W + 1, P->coef.c[tp]);
@@ -825,6 +829,8 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
                     "cudaStreamCreateWithFlags");
             PL_CUDA(cudaEventCreateWithFlags(&P->ev_bpA, cudaEventDisableTiming), "cudaEventCreate");
             PL_CUDA(cudaEventCreateWithFlags(&P->ev_bpB, cudaEventDisableTiming), "cudaEventCreate");
+            PL_CUDA(cudaEventCreateWithFlags(&P->ev_z0, cudaEventDisableTiming), "cudaEventCreate");
+            PL_CUDA(cudaEventCreateWithFlags(&P->ev_z1, cudaEventDisableTiming), "cudaEventCreate");
             P->bp_full = wsplit.full;
             P->zi_cols = wsplit.cols;
         }
@@ -878,8 +884,18 @@ pl_status pl_stage_range_table(pl_plan *P, cudaStream_t st) {
     return PL_OK;
 }
 
+// Spectra of the back-projection's output: one per channel part, or one that
+// all parts add into.
+static int g_parts(const pl_plan *P) {
+    return (P->block_config == 4 && !P->tc.g_atomic) ? P->tc.nsplit : 1;
+}
+static size_t g_bytes(const pl_plan *P) {
+    return (size_t)P->Np * P->grid.nx * P->grid.ny * sizeof(float2);
+}
+
 pl_status pl_stage_backproject(pl_plan *P, cudaStream_t st) {
     if (P->block_config == 4) {
+        if (P->tc.g_atomic) PL_CUDA(cudaMemsetAsync(P->d_G, 0, g_bytes(P), st), "zero G");
         PL_CUDA(launch_backproject_tc(P->bp, P->coef, P->tc, P->tmap, P->d_tgeo, P->d_kchl,
                                       P->d_G, P->d_err, st),
                 "backproject_tc");
@@ -908,7 +924,7 @@ static pl_status stage_zifft(pl_plan *P, float2 *image, cudaStream_t st, int par
 }
 
 pl_status pl_stage_zifft(pl_plan *P, float2 *image, cudaStream_t st) {
-    return stage_zifft(P, image, st, P->block_config == 4 ? P->tc.nsplit : 1);
+    return stage_zifft(P, image, st, g_parts(P));
 }
 
 // a5 + a6 with the back-projection's last partial wave beside the z-IFFT of
@@ -921,9 +937,14 @@ pl_status pl_stage_zifft(pl_plan *P, float2 *image, cudaStream_t st) {
 static pl_status stage_bp_zifft_overlapped(pl_plan *P, float2 *image, cudaStream_t st,
                                            const cudaEvent_t (&t)[4]) {
     const int P2 = P->grid.nx * P->grid.ny;
-    const int parts = P->tc.nsplit;
+    const int parts = g_parts(P);
     const float2 *G2 = parts > 1 ? P->d_G + (size_t)P->Np * P2 : nullptr;
     TcArgs a = P->tc;
+    if (P->tc.g_atomic) {
+        // G zeroed on the side stream, beside the caller's stream's z-FFT and
+        // range table, after the previous execution's readers of G
+        PL_CUDA(cudaStreamWaitEvent(st, P->ev_z1, 0), "cudaStreamWaitEvent");
+    }
     if (t[0]) PL_CUDA(cudaEventRecord(t[0], st), "event");
     a.blk0 = 0;
     a.nblk = P->bp_full;
@@ -968,6 +989,14 @@ pl_status run(pl_plan *P, const float2 *echo, float2 *image, cudaStream_t st) {
         return cudaEventRecord(ev[sidx][which], st);
     };
     pl_status s;
+    if (P->tc.g_atomic && P->bp_full > 0) {
+        // the channel parts add into one spectrum: zero it on the side
+        // stream, beside a1-a4 (the back-projection waits for it)
+        PL_CUDA(cudaEventRecord(P->ev_z0, st), "event");
+        PL_CUDA(cudaStreamWaitEvent(P->s_bp, P->ev_z0, 0), "cudaStreamWaitEvent");
+        PL_CUDA(cudaMemsetAsync(P->d_G, 0, g_bytes(P), P->s_bp), "zero G");
+        PL_CUDA(cudaEventRecord(P->ev_z1, P->s_bp), "event");
+    }
     // a1: transform over the scan axis, Eq. (2)
     PL_CUDA(mark(0, 0), "event");
     if ((s = pl_stage_zfft(P, echo, st)) != PL_OK) return s;
@@ -1402,8 +1431,7 @@ pl_status pl_plan_workspace(pl_plan *P, int stage, void **dev_ptr, size_t *bytes
             return PL_OK;
         case PL_STAGE_BACKPROJECT:
             *dev_ptr = P->d_G;
-            *bytes = (size_t)(P->block_config == 4 ? P->tc.nsplit : 1) * P->Np * P->grid.nx *
-                     P->grid.ny * sizeof(float2);
+            *bytes = (size_t)g_parts(P) * g_bytes(P);
             return PL_OK;
     }
     return fail(PL_ERR_ARG, "no workspace for this stage");

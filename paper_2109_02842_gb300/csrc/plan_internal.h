@@ -58,6 +58,7 @@ struct pl_plan {
     int bp_full = 0, zi_cols = 0;
     cudaStream_t s_bp = nullptr;
     cudaEvent_t ev_bpA = nullptr, ev_bpB = nullptr;
+    cudaEvent_t ev_z0 = nullptr, ev_z1 = nullptr;   // zeroing G on s_bp (atomic parts)
     // transforms
     bool fwd_fft = true, inv_fft = true;
     int inv_off = 0;
@@ -123,7 +124,7 @@ struct pl_plan {
         if (s_d2h) cudaStreamDestroy(s_d2h);
         if (s_twin) cudaStreamDestroy(s_twin);
         if (s_bp) cudaStreamDestroy(s_bp);
-        for (cudaEvent_t e : {ev_bpA, ev_bpB})
+        for (cudaEvent_t e : {ev_bpA, ev_bpB, ev_z0, ev_z1})
             if (e) cudaEventDestroy(e);
         delete twin;
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
