@@ -441,7 +441,7 @@ __device__ __forceinline__ void bp_tc_item(const BpDesc &p, const CoefTable &ct,
                                           (PLANAR ? u0 : 2 * u0) + 64 * j, ilo[k], cz);
                         if (PLANAR)
                             tc05::tma_load_3d(dst + ta.im_off + (size_t)j * ta.cb_bytes, tmap,
-                                              &b_full[sg], ta.im_col + 64 * j, ilo[k], cz);
+                                              &b_full[sg], ta.im_col + u0 + 64 * j, ilo[k], cz);
                     }
                 }
             }
@@ -908,7 +908,7 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
                     // ilo % NG + j (NG = RW / 4)
                     constexpr int NG = RW == 12 ? 3 : 4;
                     const int a0 = ilo[k] / NG, g0 = ilo[k] - a0 * NG;
-                    const int x0 = PLANAR ? 0 : 2 * u0;
+                    const int x0 = PLANAR ? u0 : 2 * u0;
                     for (int j = 0; j < ta.ncb; ++j)
                         tc05::tma_load_5d(dst + (size_t)j * ta.cb_bytes, tmap, &b_full[sg],
                                           x0 + 64 * j, a0, g0, 0, cz);

@@ -507,13 +507,22 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
                 return fail(PL_ERR_UNSUPPORTED,
                             "a 16 x 8 pixel tile spans more than 32 table rows (grid too coarse for block_config 4)");
             if (tc_fits(P->tile_u, npl, ks, P->tc.planar != 0, o.one_block_per_sm != 0)) break;
-            if (attempt > 1 || o.tile_u != 0)
+            if (attempt > 2 || o.tile_u != 0)
                 return fail(PL_ERR_UNSUPPORTED, "tile_u too large for tensor memory");
-            // the planar layout does not fit (too many bins, or two K steps,
-            // for tensor or shared memory): interleaved blocks of bins, sized
+            // the planar layout with every bin in one block does not fit (too
+            // many bins, or two K steps, for tensor or shared memory): planar
+            // blocks of at most 208 bins where one K step does (with 16-row
+            // windows; half the blocks of bins of the interleaved layout, and
+            // fewer products per bin), else interleaved blocks of bins, sized
             // for ks, and their band
-            P->tc.planar = 0;
-            P->tile_u = tc_auto_tile(P->Np, npl, ks);
+            const int nb_pl = (P->Np + 207) / 208;
+            const int ut_pl = ((P->Np + nb_pl - 1) / nb_pl + 15) / 16 * 16;
+            if (P->tc.planar && ks == 1 && nb_pl > 1 && P->tile_u != ut_pl) {
+                P->tile_u = ut_pl;
+            } else {
+                P->tc.planar = 0;
+                P->tile_u = tc_auto_tile(P->Np, npl, ks);
+            }
             const pl_status bs = band(P->tile_u);
             if (bs != PL_OK) return bs;
             h = PL_TWO_PI / (o.nufft_sigma * kmax);
@@ -542,8 +551,8 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
             const int rw = sp_inter ? 16 * ks
                                     : (stats[0] <= 12 && W <= 6 && o.sparse_window_rows == 12) ? 12
                                                                                                : 16;
-            const int part = sp_inter ? 2 * P->tile_u * ((P->Np + P->tile_u - 1) / P->tile_u)
-                                      : P->tile_u;
+            const int n_ut = (P->Np + P->tile_u - 1) / P->tile_u;
+            const int part = sp_inter ? 2 * P->tile_u * n_ut : P->tile_u * n_ut;
             CUtensorMap trial{};
             alignas(64) static unsigned char probe_buf[64];
             // the encoder only checks the layout (the address is not read)
@@ -586,11 +595,12 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         const int N = ta.planar ? ta.UT : 2 * ta.UT;
         ta.ncb = (N + 63) / 64;
         ta.n_utiles = (P->Np + ta.UT - 1) / ta.UT;
+        // planar rows: [Re of every bin | Im of every bin], blocks of UT bins
         ta.split = P->precision >= 1 ? 1 : 3;
         const int planes = ta.split == 3 ? 2 : 1, npl = ta.split == 3 ? 4 : 2;
         ta.cb_bytes = (unsigned)(planes * 16 * ta.ks * 128);
         ta.im_off = ta.planar ? (unsigned)ta.ncb * ta.cb_bytes : 0u;
-        ta.im_col = ta.planar ? ta.UT : 0;
+        ta.im_col = ta.planar ? ta.n_utiles * ta.UT : 0;
         ta.slot_bytes = (unsigned)(ta.planar ? 2 : 1) * ta.ncb * ta.cb_bytes;
         ta.npar = tc_npar(ta.UT, npl, ta.ks, ta.planar != 0, o.one_block_per_sm != 0);
         ta.tmem_cols = ta.npar == 2 ? 256 : 512;
@@ -627,7 +637,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         ta.idesc = tc05::idesc_bf16(128, N, 1);
         ta.budget = wait_budget_cycles(o.wait_timeout_us);
         ta.dbg_wait = o.debug_unsatisfiable == 1 ? 1 : 0;
-        d.tc_cols = ta.planar ? 2 * ta.UT : 2 * ta.n_utiles * ta.UT;
+        d.tc_cols = 2 * ta.n_utiles * ta.UT;
         d.tc_planar = ta.planar;
         // planar: two channel parts per tile. Each accumulator then takes as
         // many products as an interleaved P or Q accumulator over all channels
@@ -730,7 +740,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         if (!enc) return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled not available");
         const TcArgs &ta = P->tc;
         if (ta.sparse) {
-            if (!encode_sparse_map(&P->tmap, P->d_table, ta.planar ? ta.UT : d.tc_cols, L, P->C,
+            if (!encode_sparse_map(&P->tmap, P->d_table, ta.planar ? d.tc_cols / 2 : d.tc_cols, L, P->C,
                                    ta.split == 3 ? 2 : 1, ta.rw, ta.planar != 0))
                 return fail(PL_ERR_CUDA, "cuTensorMapEncodeTiled failed (sparse table map)");
         } else {

@@ -479,6 +479,34 @@ def test_sparse_products_interleaved_layout(binding, case):
           image_ref(w, echo), tol)
 
 
+@pytest.mark.parametrize("case", ["sparse300", "dense300", "sparse420_bf16", "multi300",
+                                  "sparse250"])
+def test_planar_layout_in_blocks_of_bins(binding, case):
+    # more bins than one planar block holds (N at most 208 next to the A
+    # buffers): planar blocks of bins, each with its own band centre, Re and
+    # Im columns of the block's bins read at u0 and Im offset + u0
+    opts = {}
+    tol = TOL_FP32
+    w = small_multi() if case == "multi300" else wl.small_mono(seed=10)
+    x0, dx = wl.centred_axis(0.128, 64)
+    w.grid = dict(w.grid, x0=x0, dx=dx, nx=64, y0=x0, dy=dx, ny=64, nz=8)
+    w.n_pad = 420 if "420" in case else (250 if "250" in case else 300)
+    if case.startswith("dense"):
+        opts["dense_products"] = True
+    if case.endswith("bf16"):
+        opts["precision"] = 1
+        tol = TOL_BF16
+    echo = scene_echo(w, 10)
+    plan, img = run_gpu(binding, w, echo, block_config=4, **opts)
+    i = plan.info
+    print("%s: bins per block %d of %d, window rows %d, sparse %d" % (
+        case, i["tile_u"], w.n_pad, i["slab_rows"], i["sparse_products"]))
+    assert i["table_layout"] == 3 and i["tile_u"] < w.n_pad and i["tile_u"] <= 208
+    assert i["sparse_products"] == (0 if case.startswith("dense") else 1)
+    check("image tc planar blocks %s" % case, img.reshape(w.grid["nz"], -1), image_ref(w, echo),
+          tol)
+
+
 @pytest.mark.parametrize("case", ["one_channel", "three_channels", "one_pixel", "one_frequency",
                                   "seven_bins"])
 def test_sparse_products_degenerate_sizes(binding, case):
