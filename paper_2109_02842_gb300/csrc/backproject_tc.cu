@@ -1117,7 +1117,22 @@ k_backproject_tc_batch(const __grid_constant__ TcBatchMaps maps, CoefTable ct,
         const TcScene &sd = scenes[s_scene];
         const CUtensorMap *tm = &maps.m[s_scene];
         const int lin = item - sd.begin;
-        if (s_ta.ks == 1) {
+        if (s_ta.sparse) {
+            // sparse products (one warp set per class buffer; barriers laid
+            // out as for the dense products)
+            if (s_ta.planar)
+                bp_tc_item_sp<W, SPLIT, 3, 1, 16, true>(s_bp, ct, s_ta, tm, sd.tgeo, sd.kc_hl,
+                                                        sd.G, err, lin, smem, bars, tmem,
+                                                        &dbg_bar);
+            else if (s_ta.rw == 32)
+                bp_tc_item_sp<W, SPLIT, 3, 1, 32, false>(s_bp, ct, s_ta, tm, sd.tgeo, sd.kc_hl,
+                                                         sd.G, err, lin, smem, bars, tmem,
+                                                         &dbg_bar);
+            else if constexpr (SPLIT == 3)
+                bp_tc_item_sp<W, SPLIT, 3, 1, 16, false>(s_bp, ct, s_ta, tm, sd.tgeo, sd.kc_hl,
+                                                         sd.G, err, lin, smem, bars, tmem,
+                                                         &dbg_bar);
+        } else if (s_ta.ks == 1) {
             if (s_ta.planar)
                 bp_tc_item<W, 1, SPLIT, 3, true, 1>(s_bp, ct, s_ta, tm, sd.tgeo, sd.kc_hl, sd.G,
                                                     err, lin, smem, bars, tmem, &dbg_bar);

@@ -543,11 +543,15 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         P->tc.rw = 16;
         // (interleaved 16-row windows only with the hi/lo split: the K = 32
         // operand is the window's hi rows and lo rows)
-        const bool sp_planar = P->tc.planar && ks == 1 && tc_npar_sp(P->tile_u, npl) > 0;
-        const bool sp_inter = !P->tc.planar && tc_npar_sp(2 * P->tile_u, npl) > 0 &&
+        // (one_block_per_sm: the layout of three channel classes, so that a
+        // batch's persistent back-projection can run the scene)
+        auto sp_fits = [&](int n) {
+            return o.one_block_per_sm ? tc_cols_sp(n, 3, npl) <= 512 : tc_npar_sp(n, npl) > 0;
+        };
+        const bool sp_planar = P->tc.planar && ks == 1 && sp_fits(P->tile_u);
+        const bool sp_inter = !P->tc.planar && sp_fits(2 * P->tile_u) &&
                               (ks == 2 || P->precision == 0);
-        if (!o.dense_products && (sp_planar || sp_inter) && !o.one_block_per_sm &&
-            (W == 4 || W == 6 || W == 8)) {
+        if (!o.dense_products && (sp_planar || sp_inter) && (W == 4 || W == 6 || W == 8)) {
             const int rw = sp_inter ? 16 * ks
                                     : (stats[0] <= 12 && W <= 6 && o.sparse_window_rows == 12) ? 12
                                                                                                : 16;
@@ -612,7 +616,7 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
             ta.cb_bytes = (unsigned)(planes * (ta.planar ? 2 : 1) * ta.rw * 128);
             ta.im_off = 0;
             ta.slot_bytes = (unsigned)ta.ncb * ta.cb_bytes + (ta.rw == 12 ? 1024u : 0u);
-            ta.npar = tc_npar_sp(N, npl);
+            ta.npar = o.one_block_per_sm ? 3 : tc_npar_sp(N, npl);
             ta.tmem_cols = tc_cols_sp(N, ta.npar, npl) <= 256 ? 256 : 512;
             ta.mcol = ta.acol + ta.npar * npl * 8;
         }
