@@ -694,7 +694,10 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
                                               uint64_t *dbg_bar) {
     static_assert(W == 4 || W == 6 || W == 8, "taps");
     constexpr int NCW = 4 * NPAR * NSET;         // A-building warps
-    constexpr int NMAT = SPLIT == 3 ? 4 : 2;    // compressed A matrices per channel
+    // compressed A matrices per channel: Re A, Im A (hi, lo); planar 32-row
+    // windows also -Im A (the Re and Im rows are separate K = 32 operands)
+    constexpr bool P32 = PLANAR && RW == 32;
+    constexpr int NMAT = (SPLIT == 3 ? 4 : 2) + (P32 ? (SPLIT == 3 ? 2 : 1) : 0);
     const int NSG = ta.nst / NPAR;
     uint64_t *b_full = bars;
     uint64_t *done = b_full + NSG;
@@ -766,6 +769,19 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
             if (SPLIT == 3) {
                 tc05::tmem_st8(abuf + 16, a1l);                // a1 lo
                 tc05::tmem_st8(abuf + 24, a3l);                // a3 lo
+            }
+            if constexpr (P32) {
+                // -Im A (hi, lo) after them
+                constexpr uint32_t NEG = 0x80008000u;
+                uint32_t v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = a3h[j] ^ NEG;
+                tc05::tmem_st8(abuf + (SPLIT == 3 ? 32 : 16), v);
+                if (SPLIT == 3) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j] = a3l[j] ^ NEG;
+                    tc05::tmem_st8(abuf + 40, v);
+                }
             }
             tc05::tmem_st1(mbuf, mword);
             tc05::tmem_wait_st();
@@ -841,21 +857,48 @@ __device__ __forceinline__ void bp_tc_item_sp(const BpDesc &p, const CoefTable &
                     const uint32_t meta = tmem + ta.mcol + k * 8;
                     const uint64_t sh = d0 + (uint64_t)((sg * NPAR + k) * slot16);
                     const uint32_t acc = (g > 0 || k > 0) ? 1u : 0u;
-                    // planar: Re G += [Re A | -Im A] S, Im G += [Im A | Re A] S;
-                    // interleaved: P += Re A B, Q += Im A B
-                    tc05::mma_sp_ts(tmem, a1, sh, meta, idsp, acc);
-                    tc05::mma_sp_ts(tmem + N, a1 + 8, sh, meta, idsp, acc);
-                    if (SPLIT == 3 && (PLANAR || RW == 32)) {
-                        const uint64_t sl = sh + lo16;
-                        tc05::mma_sp_ts(tmem, a1, sl, meta, idsp, 1u);
-                        tc05::mma_sp_ts(tmem, a1 + 16, sh, meta, idsp, 1u);
-                        tc05::mma_sp_ts(tmem + N, a1 + 8, sl, meta, idsp, 1u);
-                        tc05::mma_sp_ts(tmem + N, a1 + 24, sh, meta, idsp, 1u);
-                    } else if (SPLIT == 3) {
-                        // interleaved 16-row windows: S = [hi rows | lo rows],
-                        // the first two products took A_hi (b_hi + b_lo)
-                        tc05::mma_sp_ts(tmem, a1 + 16, sh, meta, idsp, 1u);
-                        tc05::mma_sp_ts(tmem + N, a1 + 24, sh, meta, idsp, 1u);
+                    if constexpr (P32) {
+                        // planar 32-row windows: K = the Re rows, then the Im
+                        // rows, of the window (Re b, Im b; hi, lo planes)
+                        //   Re G += Re A Re b + (-Im A) Im b
+                        //   Im G += Im A Re b + Re A Im b
+                        constexpr uint32_t PART16 = (32 * 128) >> 4;
+                        const uint64_t rbh = sh, ibh = sh + PART16;
+                        const uint32_t ar = a1, ai = a1 + 8;
+                        const uint32_t ani = a1 + (SPLIT == 3 ? 32 : 16);
+                        tc05::mma_sp_ts(tmem, ar, rbh, meta, idsp, acc);
+                        tc05::mma_sp_ts(tmem, ani, ibh, meta, idsp, 1u);
+                        tc05::mma_sp_ts(tmem + N, ai, rbh, meta, idsp, acc);
+                        tc05::mma_sp_ts(tmem + N, ar, ibh, meta, idsp, 1u);
+                        if (SPLIT == 3) {
+                            const uint64_t rbl = sh + 2 * PART16, ibl = sh + 3 * PART16;
+                            const uint32_t arl = a1 + 16, ail = a1 + 24, anil = a1 + 40;
+                            tc05::mma_sp_ts(tmem, ar, rbl, meta, idsp, 1u);
+                            tc05::mma_sp_ts(tmem, arl, rbh, meta, idsp, 1u);
+                            tc05::mma_sp_ts(tmem, ani, ibl, meta, idsp, 1u);
+                            tc05::mma_sp_ts(tmem, anil, ibh, meta, idsp, 1u);
+                            tc05::mma_sp_ts(tmem + N, ai, rbl, meta, idsp, 1u);
+                            tc05::mma_sp_ts(tmem + N, ail, rbh, meta, idsp, 1u);
+                            tc05::mma_sp_ts(tmem + N, ar, ibl, meta, idsp, 1u);
+                            tc05::mma_sp_ts(tmem + N, arl, ibh, meta, idsp, 1u);
+                        }
+                    } else {
+                        // planar: Re G += [Re A | -Im A] S, Im G += [Im A | Re A] S;
+                        // interleaved: P += Re A B, Q += Im A B
+                        tc05::mma_sp_ts(tmem, a1, sh, meta, idsp, acc);
+                        tc05::mma_sp_ts(tmem + N, a1 + 8, sh, meta, idsp, acc);
+                        if (SPLIT == 3 && (PLANAR || RW == 32)) {
+                            const uint64_t sl = sh + lo16;
+                            tc05::mma_sp_ts(tmem, a1, sl, meta, idsp, 1u);
+                            tc05::mma_sp_ts(tmem, a1 + 16, sh, meta, idsp, 1u);
+                            tc05::mma_sp_ts(tmem + N, a1 + 8, sl, meta, idsp, 1u);
+                            tc05::mma_sp_ts(tmem + N, a1 + 24, sh, meta, idsp, 1u);
+                        } else if (SPLIT == 3) {
+                            // interleaved 16-row windows: S = [hi rows | lo rows],
+                            // the first two products took A_hi (b_hi + b_lo)
+                            tc05::mma_sp_ts(tmem, a1 + 16, sh, meta, idsp, 1u);
+                            tc05::mma_sp_ts(tmem + N, a1 + 24, sh, meta, idsp, 1u);
+                        }
                     }
                     tc05::mma_commit(&a_done[k * NSET + g % NSET]);
                 }
@@ -1207,6 +1250,17 @@ template <int SPLIT, int NPAR>
 cudaError_t launch_spw(const BpDesc &p, const CoefTable &ct, const TcArgs &ta, const CUtensorMap &tm,
                        const TileGeo *tgeo, const float2 *kc_hl, float2 *G, int *err,
                        cudaStream_t st) {
+    if (ta.rw == 32 && ta.planar) {     // planar layout, 32-row windows (two classes)
+        if constexpr (NPAR == 2) {
+            switch (p.w) {
+                case 4: return launch_sp<4, SPLIT, 2, 32, true>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+                case 6: return launch_sp<6, SPLIT, 2, 32, true>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+                case 8: return launch_sp<8, SPLIT, 2, 32, true>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
+                default: return cudaErrorInvalidValue;
+            }
+        }
+        return cudaErrorInvalidValue;
+    }
     if (ta.rw == 32) {                  // interleaved layout, 32-row windows
         switch (p.w) {
             case 4: return launch_sp<4, SPLIT, NPAR, 32, false>(p, ct, ta, tm, tgeo, kc_hl, G, err, st);
@@ -1302,6 +1356,7 @@ cudaError_t launch_backproject_tc(const BpDesc &p, const CoefTable &ct, const Tc
                                   float2 *G, int *err, cudaStream_t st) {
     if (ta.sparse) {
         const bool ok = ta.cpr == 1 && ((ta.planar && ta.ks == 1 && ta.rw != 32) ||
+                                        (ta.planar && ta.ks == 2 && ta.rw == 32 && ta.npar == 2) ||
                                         (!ta.planar && ta.ks == 2 && ta.rw == 32) ||
                                         (!ta.planar && ta.ks == 1 && ta.rw == 16 &&
                                          ta.split == 3));

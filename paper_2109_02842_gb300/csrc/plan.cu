@@ -490,6 +490,33 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         const int npl = P->precision >= 1 ? 2 : 4;
         PL_CUDA(dalloc(&P->d_tgeo, (size_t)ntx * nty * P->C, ws), "cudaMalloc");
         int stats[2] = {0, 0}, ks = 0;
+        const bool sp_allowed = !o.dense_products && (W == 4 || W == 6 || W == 8);
+        // a sparse table map of this layout encodes (the encoder only checks
+        // the layout: the address is not read)
+        auto trial_map = [&](int part, int rows, int rw, bool planar) {
+            CUtensorMap trial{};
+            alignas(64) static unsigned char probe_buf[64];
+            const uintptr_t fake = (reinterpret_cast<uintptr_t>(probe_buf) + 63) & ~(uintptr_t)63;
+            return encode_sparse_map(&trial, reinterpret_cast<void *>(fake), part, rows, P->C,
+                                     P->precision >= 1 ? 1 : 2, rw, planar);
+        };
+        // the planar layout with two K steps takes the sparse products with
+        // 32-row windows: two channel classes of 1.5 npl compressed A
+        // matrices (Re A, Im A and -Im A) beside the accumulators, and two
+        // slot groups of two windows (a 64-column block of a window: Re and
+        // Im rows of each plane, 32 rows each) within 200 KB
+        auto sp32_fits = [&](int ut, int rows) {
+            if (!sp_allowed || o.one_block_per_sm || ut > 256) return false;
+            const size_t cb = (size_t)(npl == 4 ? 2 : 1) * 2 * 32 * 128;
+            return tc_cols_sp(ut, 2, npl + npl / 2) <= 512 &&
+                   2 * 2 * (size_t)((ut + 63) / 64) * cb <= 200 * 1024 &&
+                   trial_map(ut * ((P->Np + ut - 1) / ut), rows, 32, true);
+        };
+        // table rows of the sparse map over windows of 16 ks rows
+        auto sp_rows = [&](int ks_) {
+            int r = stats[1] + 16 * ks_;
+            return r + (r & 1) + 4;
+        };
         for (int attempt = 0;; ++attempt) {
             d.h = h;
             d.l0 = amin - h * (0.5 * W + 2.0);
@@ -506,19 +533,26 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
             if (ks == 0)
                 return fail(PL_ERR_UNSUPPORTED,
                             "a 16 x 8 pixel tile spans more than 32 table rows (grid too coarse for block_config 4)");
+            if (P->tc.planar && ks == 2 && sp32_fits(P->tile_u, sp_rows(2))) break;
             if (tc_fits(P->tile_u, npl, ks, P->tc.planar != 0, o.one_block_per_sm != 0)) break;
-            if (attempt > 2 || o.tile_u != 0)
+            if (attempt > 3 || o.tile_u != 0)
                 return fail(PL_ERR_UNSUPPORTED, "tile_u too large for tensor memory");
             // the planar layout with every bin in one block does not fit (too
             // many bins, or two K steps, for tensor or shared memory): planar
             // blocks of at most 208 bins where one K step does (with 16-row
             // windows; half the blocks of bins of the interleaved layout, and
-            // fewer products per bin), else interleaved blocks of bins, sized
-            // for ks, and their band
+            // fewer products per bin), or of at most 192 bins where two K
+            // steps take the sparse products (32-row windows), else
+            // interleaved blocks of bins, sized for ks, and their band
             const int nb_pl = (P->Np + 207) / 208;
             const int ut_pl = ((P->Np + nb_pl - 1) / nb_pl + 15) / 16 * 16;
+            const int nb_32 = (P->Np + 191) / 192;
+            const int ut_32 = ((P->Np + nb_32 - 1) / nb_32 + 15) / 16 * 16;
             if (P->tc.planar && ks == 1 && nb_pl > 1 && P->tile_u != ut_pl) {
                 P->tile_u = ut_pl;
+            } else if (P->tc.planar && ks == 2 && sp_allowed && !o.one_block_per_sm &&
+                       P->tile_u != ut_32) {
+                P->tile_u = ut_32;
             } else {
                 P->tc.planar = 0;
                 P->tile_u = tc_auto_tile(P->Np, npl, ks);
@@ -548,27 +582,28 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
         auto sp_fits = [&](int n) {
             return o.one_block_per_sm ? tc_cols_sp(n, 3, npl) <= 512 : tc_npar_sp(n, npl) > 0;
         };
-        const bool sp_planar = P->tc.planar && ks == 1 && sp_fits(P->tile_u);
+        const bool sp_planar = P->tc.planar && ((ks == 1 && sp_fits(P->tile_u)) ||
+                                                (ks == 2 && sp32_fits(P->tile_u, L + 4)));
         const bool sp_inter = !P->tc.planar && sp_fits(2 * P->tile_u) &&
                               (ks == 2 || P->precision == 0);
-        if (!o.dense_products && (sp_planar || sp_inter) && (W == 4 || W == 6 || W == 8)) {
-            const int rw = sp_inter ? 16 * ks
-                                    : (stats[0] <= 12 && W <= 6 && o.sparse_window_rows == 12) ? 12
-                                                                                               : 16;
+        if (sp_allowed && (sp_planar || sp_inter)) {
+            const int rw = sp_inter || ks == 2 ? 16 * ks
+                           : (stats[0] <= 12 && W <= 6 && o.sparse_window_rows == 12) ? 12
+                                                                                      : 16;
             const int n_ut = (P->Np + P->tile_u - 1) / P->tile_u;
             const int part = sp_inter ? 2 * P->tile_u * n_ut : P->tile_u * n_ut;
-            CUtensorMap trial{};
-            alignas(64) static unsigned char probe_buf[64];
-            // the encoder only checks the layout (the address is not read)
-            const uintptr_t fake = (reinterpret_cast<uintptr_t>(probe_buf) + 63) & ~(uintptr_t)63;
-            if (encode_sparse_map(&trial, reinterpret_cast<void *>(fake), part, L + 4, P->C,
-                                  P->precision >= 1 ? 1 : 2, rw, !sp_inter)) {
+            if (trial_map(part, L + 4, rw, !sp_inter)) {
                 P->tc.sparse = 1;
                 P->tc.rw = rw;
                 P->R = rw;
                 L += 4;
             }
         }
+        // (a planar layout with two K steps chosen for the sparse products
+        // and not taking them has no dense kernel)
+        if (P->tc.planar && !P->tc.sparse &&
+            !tc_fits(P->tile_u, npl, ks, true, o.one_block_per_sm != 0))
+            return fail(PL_ERR_UNSUPPORTED, "tensor-core layout without a kernel");
     } else {
         // every tile's R-row window [i_lo, i_lo + R), centred on its range, fits:
         // l0 = amin - ((R+1)/2 + 2) h, L = (amax - amin)/h + R + 6
@@ -616,9 +651,12 @@ pl_status build_plan(pl_plan *P, const pl_geometry *g, const pl_scan *s, const p
             ta.cb_bytes = (unsigned)(planes * (ta.planar ? 2 : 1) * ta.rw * 128);
             ta.im_off = 0;
             ta.slot_bytes = (unsigned)ta.ncb * ta.cb_bytes + (ta.rw == 12 ? 1024u : 0u);
-            ta.npar = o.one_block_per_sm ? 3 : tc_npar_sp(N, npl);
-            ta.tmem_cols = tc_cols_sp(N, ta.npar, npl) <= 256 ? 256 : 512;
-            ta.mcol = ta.acol + ta.npar * npl * 8;
+            // (planar 32-row windows: two classes of Re A, Im A, -Im A)
+            const bool p32 = ta.planar && ta.rw == 32;
+            const int nmat = p32 ? npl + npl / 2 : npl;
+            ta.npar = p32 ? 2 : o.one_block_per_sm ? 3 : tc_npar_sp(N, npl);
+            ta.tmem_cols = tc_cols_sp(N, ta.npar, nmat) <= 256 ? 256 : 512;
+            ta.mcol = ta.acol + ta.npar * nmat * 8;
         }
         // two channels per class round (twice the products per A wait and
         // release) where three classes of two-channel A buffers fit next to

@@ -479,6 +479,51 @@ def test_sparse_products_interleaved_layout(binding, case):
           image_ref(w, echo), tol)
 
 
+@pytest.mark.parametrize("case", ["mono", "multi", "ragged", "taps8", "bf16", "np192",
+                                  "blocks300", "blocks300_bf16"])
+def test_sparse_products_planar_32_row_windows(binding, case):
+    # the planar layout with two K steps (the 6.25 mm grid of small_mono:
+    # 32-row windows): the K = 32 operands are the window's Re rows and its
+    # Im rows (residue order mod 4), so each accumulator takes A S_re and
+    # the other A matrix times S_im: Re G += Re A Re b + (-Im A) Im b, Im G
+    # += Im A Re b + Re A Im b (twelve sparse products per channel with the
+    # hi/lo split). More bins than 192: planar blocks of bins
+    opts = {}
+    tol = TOL_FP32
+    w = small_multi() if case == "multi" else wl.small_mono(seed=11)
+    if case == "ragged":
+        w.grid = dict(w.grid, nx=37, ny=23, nz=7, z0=-0.031, dz=0.0093)
+    elif case == "taps8":
+        opts["nufft_w"] = 8             # (4 taps span at most 16 rows here)
+    if case.endswith("bf16"):
+        opts["precision"] = 1
+        tol = TOL_BF16
+    if case == "np192":
+        w.n_pad = 192
+    elif case.startswith("blocks"):
+        w.n_pad = int(case[6:9])
+    echo = scene_echo(w, 11)
+    sp, img = run_gpu(binding, w, echo, block_config=4, **opts)
+    de, img_d = run_gpu(binding, w, echo, block_config=4, dense_products=True, **opts)
+    i = sp.info
+    print("%s: window rows %d, bins per block %d of %d, table rows %d" % (
+        case, i["slab_rows"], i["tile_u"], w.n_pad, i["table_len"]))
+    assert i["slab_rows"] == 32 and i["table_layout"] == 3 and i["sparse_products"] == 1
+    assert de.info["sparse_products"] == 0
+    if case.startswith("blocks"):
+        assert i["tile_u"] < w.n_pad and i["tile_u"] <= 192
+    else:
+        assert i["tile_u"] >= w.n_pad
+    d = float(np.linalg.norm(img - img_d) / np.linalg.norm(img_d))
+    print("%s: sparse vs dense rel L2 %.3e" % (case, d))
+    # (BF16 tables: the dense run of 300 bins takes interleaved blocks of
+    # other band centres, so the two round different table values; each is
+    # held to the BF16 tolerance against the oracle)
+    assert d < ((5e-3 if case.startswith("blocks") else 1e-3) if case.endswith("bf16") else 3e-5)
+    check("image tc sparse planar 32 rows %s" % case, img.reshape(w.grid["nz"], -1),
+          image_ref(w, echo), tol)
+
+
 @pytest.mark.parametrize("case", ["sparse300", "dense300", "sparse420_bf16", "multi300",
                                   "sparse250"])
 def test_planar_layout_in_blocks_of_bins(binding, case):

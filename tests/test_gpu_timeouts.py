@@ -37,8 +37,12 @@ def echo_of(w):
     return wl.add_noise(clean, w.snr_db, wl.rng_for(130, 0)).astype(np.complex64)
 
 
-@pytest.mark.parametrize("hook,fine", [(1, False), (1, True), (2, False), (3, False)])
-def test_unsatisfiable_wait_times_out_and_device_stays_usable(binding, hook, fine):
+@pytest.mark.parametrize("hook,fine,dense", [(1, False, True), (1, False, False), (1, True, False),
+                                              (2, False, False), (3, False, False)])
+def test_unsatisfiable_wait_times_out_and_device_stays_usable(binding, hook, fine, dense):
+    # hook 1 in the dense kernel (6.25 mm grid, dense products), the sparse
+    # kernel with planar 32-row windows (6.25 mm) and with 16-row windows
+    # (2 mm)
     w = wl.small_mono(seed=0)
     if hook == 3:
         # 24 voxel heights off the scan grid: the tensor-core inverse DFT
@@ -49,11 +53,12 @@ def test_unsatisfiable_wait_times_out_and_device_stays_usable(binding, hook, fin
         w.grid = dict(w.grid, x0=x0, dx=dx, nx=64, y0=x0, dy=dx, ny=64, nz=8)
     echo = torch.from_numpy(echo_of(w)).cuda()
     plan = binding.Plan.from_workload(w, block_config=4, debug_unsatisfiable=hook,
-                                      wait_timeout_us=2000)
+                                      wait_timeout_us=2000, dense_products=dense)
     assert plan.info["block_config"] == 4 and plan.info["table_exact"] == 1
     if hook == 3:
         assert plan.info["z_transform_fft"] == 0
-    assert plan.info["sparse_products"] == (1 if fine else 0)
+    assert plan.info["sparse_products"] == (0 if dense else 1)
+    assert plan.info["slab_rows"] == (16 if fine else 32)
     plan.execute(echo)
     torch.cuda.synchronize()            # the kernels returned: no CUDA error
     with pytest.raises(binding.PolylineError) as ei:
