@@ -163,14 +163,15 @@ typedef struct {
      * allocated. 0 = off (default). */
     int debug_fail_alloc;
     /* block_config 4: by default the back-projection's products are 2:4
-     * sparse (tcgen05.mma.sp) in the planar layout with 16-row windows and in
-     * the interleaved layout (16-row windows with the hi/lo split, 32-row
-     * windows). A window's rows are taken in residue order (K index 4 j + e
-     * <-> row j + 4 e; over 32 rows 8 j + e), in which a pixel's w
+     * sparse (tcgen05.mma.sp) in the planar layout (16- and 32-row windows)
+     * and in the interleaved layout (16-row windows with the hi/lo split,
+     * 32-row windows). A window's rows are taken in residue order (K index
+     * 4 j + e <-> row j + 4 e; over 32 rows 8 j + e), in which a pixel's w
      * consecutive taps leave at most two nonzeros in every group of four. The
-     * K = 32 operand is the window's [Re rows; Im rows] (planar: six sparse
-     * products per channel instead of twelve dense), its [hi rows; lo rows]
-     * (interleaved, 16 rows: four instead of six) or its 32 rows
+     * K = 32 operand is the window's [Re rows; Im rows] (planar, 16 rows: six
+     * sparse products per channel instead of twelve dense), its Re rows and
+     * its Im rows (planar, 32 rows: twelve instead of 24), its [hi rows; lo
+     * rows] (interleaved, 16 rows: four instead of six) or its 32 rows
      * (interleaved, 32 rows: six instead of twelve). The sums are the same up
      * to rounding order. dense_products = 1 keeps the dense products
      * (pl_info.sparse_products says which run). */
