@@ -662,6 +662,31 @@ def test_uneven_scene_at_the_edge_of_the_batch_ranges(binding):
     check("image edge scene sampled", got, ref, TOL_FP32)
 
 
+def test_coarse_batch_scene_planar_32_row_windows(binding):
+    # one of the batched workload's coarse-grid scenes at its own size (135
+    # channels, 138 scans, N_p 288, 75 frequencies: two atoms of the exact-sum
+    # table, a 79^3 image at 5 mm): planar sparse products with 32-row
+    # windows in two blocks of 144 bins, against the dense products and the
+    # oracle on 32 sampled columns x all 79 heights
+    w = wl.batch_scene(63)
+    assert (w.n_chan, w.n_pad, w.n_f, w.grid["nx"]) == (135, 288, 75, 79)
+    echo = scene_echo(w, 13, n_pts=48)
+    sp, img = run_gpu(binding, w, echo)
+    de, img_d = run_gpu(binding, w, echo, dense_products=True)
+    i = sp.info
+    print("coarse batch scene: bins per block %d, window rows %d, table rows %d, exact %d"
+          % (i["tile_u"], i["slab_rows"], i["table_len"], i["table_exact"]))
+    assert i["block_config"] == 4 and i["sparse_products"] == 1 and i["table_layout"] == 3
+    assert i["slab_rows"] == 32 and i["tile_u"] == 144 and i["table_exact"] == 1
+    d = float(np.linalg.norm(img - img_d) / np.linalg.norm(img_d))
+    print("coarse batch scene: sparse vs dense rel L2 %.3e" % d)
+    assert d < 3e-5
+    idx = sampled_columns(w, 32, 4)
+    ref = image_ref(w, echo, w.pix_xy()[idx])
+    check("image coarse batch scene sampled", img.reshape(w.grid["nz"], -1)[:, idx], ref,
+          TOL_FP32)
+
+
 @pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("bc", [4, 1])
 def test_full_size_multistatic_bf16_variants(binding, bc, precision):
