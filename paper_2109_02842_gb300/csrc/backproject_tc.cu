@@ -24,9 +24,21 @@
 // Operands are BF16; for FP32-level accuracy each is split into hi + lo
 // and the product taken as hi.hi + hi.lo + lo.hi (SPLIT = 3), relative
 // error ~1e-5; SPLIT = 1 takes hi.hi only (~1e-3). In the planar layout a
-// tile's channels go to two blocks (nsplit = 2) that write their sums to two
-// spectra G[0], G[1] (added by the inverse z transform as it loads them):
-// each accumulator then sums as many products as an interleaved one.
+// tile's channels go to two blocks (nsplit = 2), so that each accumulator
+// sums as many products as an interleaved one; the two add their sums into
+// one spectrum (atomic adds onto G zeroed beforehand) or, in a batch's
+// persistent launch, write spectra G[0], G[1] that the inverse z transform
+// adds as it loads them.
+//
+// By default the products are 2:4 sparse (tcgen05.mma.sp, the kernel
+// k_backproject_tc_sp below): a window's rows taken in residue order put at
+// most two of a pixel's w taps in every group of four K indices, so a
+// product of logical K = 32 covers twice the rows of a dense one at the
+// same cost (planar 16-row windows: K = [Re rows; Im rows]; planar 32-row
+// windows: the Re rows and the Im rows as two operands; interleaved: the
+// window's 32 rows, or its hi and lo rows). The dense kernel below
+// (k_backproject_tc) serves dense_products = 1 and the layouts without a
+// sparse variant.
 //
 // Block = 16 x 8 pixels x UT bins, 4 NPAR + 2 warps (NPAR = 2 and two blocks
 // per SM when the accumulators and three A buffers fit in 256 TMEM columns,
