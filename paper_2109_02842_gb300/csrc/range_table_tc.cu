@@ -22,9 +22,11 @@
 //                      prod [u][hi, lo][row][Cp] of (re, im) pairs, channels
 //                      innermost (full 128-byte lines). Row parts of Lh rows
 //                      (a multiple of 16, at most 96 so that two items'
-//                      operands fit in shared memory). Double-buffered: one
-//                      item's conversion and stores overlap the next item's
-//                      products and the copies of the one after.
+//                      operands fit in shared memory). Warp-specialised
+//                      (a copy warp, a product warp, eight store warps) over
+//                      two operand buffers and two accumulator pairs: one
+//                      item's stores overlap the next item's products and
+//                      the copies of the one after.
 //   k_rt_transpose     prod -> table [c][hi, lo][L][column 2u + (re, im)] (or
 //                      planar: Re at column u, Im at row_words + u), the layout
 //                      the back-projection streams (u innermost)
@@ -102,34 +104,42 @@ __global__ void k_rt_prep(const float2 *__restrict__ S, int C, int Np, int M, in
     if (!hi_only) A[base + 3 * plane] = l;
 }
 
-// One block per SM (persistent, 8 warps) walks the work items (128-channel
-// block, bin, row part) gridDim.x apart as a pipeline of stages, one stage
-// per 64-frequency atom of an item (natoms = 1 or 2): stage s is atom
-// s % natoms of the block's item s / natoms, its operands go to buffer s & 1,
-// its products accumulate into the item's accumulator pair (item & 1). While
-// the warps convert and store item k (after its last stage), the operands of
-// the next stage are already in shared memory and its products run on the
-// tensor cores, and the copies of the stage after it are issued as soon as
-// their buffer is free again.
-__global__ void __launch_bounds__(256, 1)
+// One block per SM (persistent) walks the work items (128-channel block, bin,
+// row part) gridDim.x apart; an item is natoms stages, one per 64-frequency
+// atom, stage st's operands in buffer st & 1 and the item's products in
+// accumulator pair item & 1. The block is warp-specialised so that the
+// copies, the products and the stores of consecutive items overlap:
+//  * warp 8 (one lane) issues a stage's copies once its buffer is free (the
+//    products of stage st - 2 completed: empty[st & 1]);
+//  * warp 9 (one lane) issues a stage's products once its operands landed
+//    (full[st & 1]) and, at an item's first stage, once the item's
+//    accumulator pair has been read out for item - 2 (acc_empty), then
+//    commits them to empty[] and, at the item's last stage, to acc_full[];
+//  * warps 0-7 read each item's accumulators back once its products
+//    completed, release them (acc_empty) and convert and store the item.
+// Every wait is bounded; one that runs out sets a bit in *err and the abort
+// flag, the roles stop taking stages, and before tensor memory is released
+// the copies and products issued have completed.
+__global__ void __launch_bounds__(320, 1)
 k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
                  const __grid_constant__ CUtensorMap tmB, uint32_t *__restrict__ prod, int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t bar_tma[2], bar_mma[2], dbg_bar;
+    __shared__ __align__(8) uint64_t full[2], empty[2], acc_full[2], acc_empty[2], drain, dbg_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
+    volatile int *abortp = &abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t a_tile = 128 * 128;                 // one plane x 64-frequency atom of A
     const uint32_t b_tile = (uint32_t)ra.Lh * 128;     // of E (one row part)
     const uint32_t buf_bytes = 4 * (a_tile + b_tile);  // one stage's operands
-    int n_tma = 0, n_mma = 0;    // stages whose copies / products thread 0 issued
     const int NA = ra.natoms;
     const int ncb = (ra.C + 127) / 128;
     const int items = ncb * ra.Np * ra.nh;
     const int nmine = (items - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
     const int nstages = nmine * NA;
+    const long long budget = ra.budget;
     // item -> (first channel, bin, row part); channel blocks vary fastest so
     // the blocks running together share each bin's E tile in L2
     auto coords = [&](int k, int &c0, int &u, int &h) {
@@ -139,73 +149,15 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
         u = r % ra.Np;
         h = r / ra.Np;
     };
-    // the copies of stage st into buffer st & 1
-    auto issue_tma = [&](int st) {
-        int c0, u, h;
-        coords(st / NA, c0, u, h);
-        const int at = st % NA, b = st & 1;
-        unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
-        n_tma = st + 1;
-        // with a BF16 spectrum only A's hi planes (0 and 2) are loaded
-        tc05::mbar_arrive_expect_tx(&bar_tma[b], buf_bytes - (ra.a_hi_only ? 2 * a_tile : 0u));
-        for (int p = 0; p < 4; ++p) {
-            if (!ra.a_hi_only || (p & 1) == 0)
-                tc05::tma_load_3d(As + p * a_tile, &tmA, &bar_tma[b], 64 * at, c0, 4 * u + p);
-            tc05::tma_load_3d(Bs + p * b_tile, &tmB, &bar_tma[b], 64 * at, h * ra.Lh, 4 * u + p);
-        }
-    };
-    // the products of stage st, once its operands landed, into the
-    // accumulator pair of its item (overwriting at the item's first atom);
-    // the commit always follows so that the waits on bar_mma end
-    auto issue_mma = [&](int st) {
-        const int b = st & 1, k = st / NA, at = st % NA;
-        // (test hook: the first stage waits on a barrier nothing completes)
-        const bool landed = (ra.dbg_wait && st == 0)
-                                ? tc05::mbar_wait(&dbg_bar, 0, ra.budget)
-                                : tc05::mbar_wait(&bar_tma[b], (st >> 1) & 1, ra.budget);
-        if (landed) {
-            tc05::fence_after_sync();
-            const unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
-            const uint32_t id = ra.idesc, idn = ra.idesc | (1u << 13);   // negate A
-            const uint32_t dre = tmem_slot + (uint32_t)((k & 1) * 2 * ra.Lh), dim = dre + ra.Lh;
-            for (int ks = 0; ks < 4; ++ks) {
-                const uint32_t ko = ks * 32;
-                auto da = [&](int p) {
-                    return tc05::smem_desc_sw128(tc05::smem_addr(As + p * a_tile) + ko, 16, 1024);
-                };
-                auto db = [&](int p) {
-                    return tc05::smem_desc_sw128(tc05::smem_addr(Bs + p * b_tile) + ko, 16, 1024);
-                };
-                const uint32_t acc = (at > 0 || ks > 0) ? 1u : 0u;
-                // planes: 0 re hi, 1 re lo, 2 im hi, 3 im lo
-                // Re += a_r b_r - a_i b_i
-                tc05::mma_ss(dre, da(0), db(0), id, acc);
-                tc05::mma_ss(dre, da(0), db(1), id, 1u);
-                if (!ra.a_hi_only) tc05::mma_ss(dre, da(1), db(0), id, 1u);
-                tc05::mma_ss(dre, da(2), db(2), idn, 1u);
-                tc05::mma_ss(dre, da(2), db(3), idn, 1u);
-                if (!ra.a_hi_only) tc05::mma_ss(dre, da(3), db(2), idn, 1u);
-                // Im += a_r b_i + a_i b_r
-                tc05::mma_ss(dim, da(0), db(2), id, acc);
-                tc05::mma_ss(dim, da(0), db(3), id, 1u);
-                if (!ra.a_hi_only) tc05::mma_ss(dim, da(1), db(2), id, 1u);
-                tc05::mma_ss(dim, da(2), db(0), id, 1u);
-                tc05::mma_ss(dim, da(2), db(1), id, 1u);
-                if (!ra.a_hi_only) tc05::mma_ss(dim, da(3), db(0), id, 1u);
-            }
-        } else {
-            atomicOr(err, 1);
-            abort_flag = 1;
-        }
-        tc05::mma_commit(&bar_mma[b]);   // arrives once every issued MMA completed
-        n_mma = st + 1;
-    };
 
     if (threadIdx.x == 0) {
         tc05::mbar_init(&dbg_bar, 1);
+        tc05::mbar_init(&drain, 1);
         for (int b = 0; b < 2; ++b) {
-            tc05::mbar_init(&bar_tma[b], 1);
-            tc05::mbar_init(&bar_mma[b], 1);
+            tc05::mbar_init(&full[b], 1);
+            tc05::mbar_init(&empty[b], 1);
+            tc05::mbar_init(&acc_full[b], 1);
+            tc05::mbar_init(&acc_empty[b], 8);          // the eight store warps
         }
         tc05::fence_mbar_init();
         abort_flag = 0;
@@ -219,38 +171,122 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
     tc05::fence_after_sync();
     const uint32_t tmem = tmem_slot;
 
-    if (threadIdx.x == 0) {
-        issue_tma(0);
-        if (nstages > 1) issue_tma(1);
-        issue_mma(0);
-    }
-    const int Cp = ncb * 128;                // channel stride of prod
-    const int R = ra.nh * ra.Lh;             // rows of prod per (bin, plane)
-    for (int st = 0; st < nstages; ++st) {
-        const int b = st & 1;
-        const int k = st / NA;
-        // the next stage's products, before this stage's completion and
-        // (at an item's last stage) its epilogue
-        if (threadIdx.x == 0 && st + 1 < nstages) issue_mma(st + 1);
+    if (warp == 8) {
+        // ------------------------------------------------ copies
+        if (lane == 0) {
+            int issued = 0;
+            for (int st = 0; st < nstages && !*abortp; ++st) {
+                const int b = st & 1, at = st % NA;
+                if (st >= 2 && !tc05::mbar_wait(&empty[b], (uint32_t)((st >> 1) - 1) & 1u, budget)) {
+                    atomicOr(err, 4);
+                    *abortp = 1;
+                    break;
+                }
+                int c0, u, h;
+                coords(st / NA, c0, u, h);
+                unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
+                // with a BF16 spectrum only A's hi planes (0 and 2) are loaded
+                tc05::mbar_arrive_expect_tx(&full[b], buf_bytes - (ra.a_hi_only ? 2 * a_tile : 0u));
+                for (int p = 0; p < 4; ++p) {
+                    if (!ra.a_hi_only || (p & 1) == 0)
+                        tc05::tma_load_3d(As + p * a_tile, &tmA, &full[b], 64 * at, c0, 4 * u + p);
+                    tc05::tma_load_3d(Bs + p * b_tile, &tmB, &full[b], 64 * at, h * ra.Lh,
+                                      4 * u + p);
+                }
+                issued = st + 1;
+            }
+            // the last copies issued (at most one per buffer outstanding) have
+            // landed before shared memory is released
+            for (int st = issued > 2 ? issued - 2 : 0; st < issued; ++st)
+                if (!tc05::mbar_wait(&full[st & 1], (uint32_t)(st >> 1) & 1u, budget))
+                    atomicOr(err, 16);
+        }
         __syncwarp();
-        bool done = tc05::mbar_wait(&bar_mma[b], (st >> 1) & 1, ra.budget);
-        done = __all_sync(0xffffffffu, done);
-        // this stage's operands are consumed: the copies of stage st + 2 go
-        // into its buffer now and overlap the next products and the epilogue
-        if (threadIdx.x == 0 && done && !abort_flag && st + 2 < nstages) issue_tma(st + 2);
-        if (done && st % NA == NA - 1) {
+    } else if (warp == 9) {
+        // ------------------------------------------------ products
+        if (lane == 0) {
+            for (int st = 0; st < nstages && !*abortp; ++st) {
+                const int b = st & 1, k = st / NA, at = st % NA;
+                // (an item's first stage) its accumulator pair read out for item k - 2
+                if (at == 0 && k >= 2 &&
+                    !tc05::mbar_wait(&acc_empty[k & 1], (uint32_t)((k >> 1) - 1) & 1u, budget)) {
+                    atomicOr(err, 8);
+                    *abortp = 1;
+                    break;
+                }
+                // (test hook: the first stage waits on a barrier nothing completes)
+                const bool landed = (ra.dbg_wait && st == 0)
+                                        ? tc05::mbar_wait(&dbg_bar, 0, budget)
+                                        : tc05::mbar_wait(&full[b], (uint32_t)(st >> 1) & 1u, budget);
+                if (!landed) {
+                    atomicOr(err, 1);
+                    *abortp = 1;
+                    break;
+                }
+                tc05::fence_after_sync();
+                const unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
+                const uint32_t id = ra.idesc, idn = ra.idesc | (1u << 13);   // negate A
+                const uint32_t dre = tmem + (uint32_t)((k & 1) * 2 * ra.Lh), dim = dre + ra.Lh;
+                for (int ks = 0; ks < 4; ++ks) {
+                    const uint32_t ko = ks * 32;
+                    auto da = [&](int p) {
+                        return tc05::smem_desc_sw128(tc05::smem_addr(As + p * a_tile) + ko, 16, 1024);
+                    };
+                    auto db = [&](int p) {
+                        return tc05::smem_desc_sw128(tc05::smem_addr(Bs + p * b_tile) + ko, 16, 1024);
+                    };
+                    const uint32_t acc = (at > 0 || ks > 0) ? 1u : 0u;
+                    // planes: 0 re hi, 1 re lo, 2 im hi, 3 im lo
+                    // Re += a_r b_r - a_i b_i
+                    tc05::mma_ss(dre, da(0), db(0), id, acc);
+                    tc05::mma_ss(dre, da(0), db(1), id, 1u);
+                    if (!ra.a_hi_only) tc05::mma_ss(dre, da(1), db(0), id, 1u);
+                    tc05::mma_ss(dre, da(2), db(2), idn, 1u);
+                    tc05::mma_ss(dre, da(2), db(3), idn, 1u);
+                    if (!ra.a_hi_only) tc05::mma_ss(dre, da(3), db(2), idn, 1u);
+                    // Im += a_r b_i + a_i b_r
+                    tc05::mma_ss(dim, da(0), db(2), id, acc);
+                    tc05::mma_ss(dim, da(0), db(3), id, 1u);
+                    if (!ra.a_hi_only) tc05::mma_ss(dim, da(1), db(2), id, 1u);
+                    tc05::mma_ss(dim, da(2), db(0), id, 1u);
+                    tc05::mma_ss(dim, da(2), db(1), id, 1u);
+                    if (!ra.a_hi_only) tc05::mma_ss(dim, da(3), db(0), id, 1u);
+                }
+                tc05::mma_commit(&empty[b]);                    // the buffer may be refilled
+                if (at == NA - 1) tc05::mma_commit(&acc_full[k & 1]);   // the item is done
+            }
+            // every product issued has completed before tensor memory is released
+            tc05::mma_commit(&drain);
+            if (!tc05::mbar_wait(&drain, 0, budget)) atomicOr(err, 32);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------ stores (warps 0-7)
+        // each thread (one channel: its TMEM lane) converts 16 rows at a time
+        // to BF16 hi/lo (re, im) pairs and stores them into prod
+        // [u][hi, lo][row][Cp], channels innermost, so each store instruction
+        // of a warp writes 32 consecutive channels (a full 128-byte line).
+        // Warps 0-3 and 4-7 take alternate 16-row chunks of their TMEM lane
+        // quarter.
+        const int Cp = ncb * 128;                // channel stride of prod
+        const int R = ra.nh * ra.Lh;             // rows of prod per (bin, plane)
+        const int q = warp & 3;
+        for (int k = 0; k < nmine; ++k) {
+            bool ok = !*abortp && tc05::mbar_wait(&acc_full[k & 1], (uint32_t)(k >> 1) & 1u, budget);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) {
+                    if (!*abortp) atomicOr(err, 2);
+                    *abortp = 1;
+                }
+                break;
+            }
+            tc05::fence_after_sync();
             int c0, u, h;
             coords(k, c0, u, h);
-            // output: each thread (one channel: its TMEM lane) converts 16
-            // rows at a time to BF16 hi/lo (re, im) pairs and stores them
-            // into prod [u][hi, lo][row][Cp], channels innermost, so each
-            // store instruction of a warp writes 32 consecutive channels (a
-            // full 128-byte line). Warps 0-3 and 4-7 take alternate 16-row
-            // chunks of their TMEM lane quarter.
             const int rows_here = min(ra.Lh, ra.L - h * ra.Lh);     // table rows of this part
-            tc05::fence_after_sync();
-            const int q = warp & 3;
-            const uint32_t lane_base = tmem + (uint32_t)((k & 1) * 2 * ra.Lh) + ((uint32_t)(32 * q) << 16);
+            const uint32_t lane_base =
+                tmem + (uint32_t)((k & 1) * 2 * ra.Lh) + ((uint32_t)(32 * q) << 16);
             const int c = c0 + 32 * q + lane;
             uint32_t *g_hi = prod + ((size_t)(2 * u + 0) * R + h * ra.Lh) * Cp + c;
             uint32_t *g_lo = prod + ((size_t)(2 * u + 1) * R + h * ra.Lh) * Cp + c;
@@ -272,25 +308,11 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
                     }
                 }
             }
-        } else if (!done) {
-            if (lane == 0) atomicOr(err, 2);
-            abort_flag = 1;
+            // the accumulator pair is free for item k + 2's products
+            tc05::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc05::mbar_arrive(&acc_empty[k & 1]);
         }
-        // the TMEM reads finish before the accumulators take new products
-        tc05::fence_before_sync();
-        __syncthreads();
-        tc05::fence_after_sync();
-        if (abort_flag) break;
-    }
-    // before shared and tensor memory are released, the copies and products
-    // thread 0 issued have completed: only the last stage on each buffer can
-    // still be outstanding (after a timed-out wait), and waiting again on a
-    // completed phase returns at once
-    if (threadIdx.x == 0) {
-        for (int st = n_tma > 2 ? n_tma - 2 : 0; st < n_tma; ++st)
-            tc05::mbar_wait(&bar_tma[st & 1], (st >> 1) & 1, ra.budget);
-        for (int st = n_mma > 2 ? n_mma - 2 : 0; st < n_mma; ++st)
-            tc05::mbar_wait(&bar_mma[st & 1], (st >> 1) & 1, ra.budget);
     }
     tc05::fence_before_sync();
     __syncthreads();
@@ -381,7 +403,7 @@ cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
                              (int)smem);
     if (e != cudaSuccess) return e;
     const int items = (ra.C + 127) / 128 * ra.Np * ra.nh;
-    k_range_table_tc<<<min(items, ra.grid), 256, smem, st>>>(ra, tmA, tmB, (uint32_t *)prod, err);
+    k_range_table_tc<<<min(items, ra.grid), 320, smem, st>>>(ra, tmA, tmB, (uint32_t *)prod, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int Cp = (ra.C + 127) / 128 * 128, R = ra.nh * ra.Lh;
