@@ -126,36 +126,49 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full[2], empty[2], acc_full[2], acc_empty[2], drain, dbg_bar;
+    __shared__ __align__(8) uint64_t a_full[2], a_empty[2], e_full[2], e_empty[2];
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], drain, dbg_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     volatile int *abortp = &abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t a_tile = 128 * 128;                 // one plane x 64-frequency atom of A
     const uint32_t b_tile = (uint32_t)ra.Lh * 128;     // of E (one row part)
-    const uint32_t buf_bytes = 4 * (a_tile + b_tile);  // one stage's operands
     const int NA = ra.natoms;
     const int ncb = (ra.C + 127) / 128;
-    const int items = ncb * ra.Np * ra.nh;
-    const int nmine = (items - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    // pairs (128-channel block, bin) gridDim.x apart, channel blocks varying
+    // fastest so that the blocks running together share each bin's E tiles
+    // in L2; a block takes all row parts of its pair in turn (item k = pair
+    // k / nh, row part k % nh), so that with one atom the pair's A tile is
+    // copied once for all its row parts
+    const int npairs = ncb * ra.Np;
+    const int pmine = (npairs - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int nmine = pmine * ra.nh;
     const int nstages = nmine * NA;
+    const bool share_a = NA == 1;
     const long long budget = ra.budget;
-    // item -> (first channel, bin, row part); channel blocks vary fastest so
-    // the blocks running together share each bin's E tile in L2
     auto coords = [&](int k, int &c0, int &u, int &h) {
-        const int it = (int)blockIdx.x + k * (int)gridDim.x;
-        const int cb = it % ncb, r = it / ncb;
-        c0 = 128 * cb;
-        u = r % ra.Np;
-        h = r / ra.Np;
+        const int pr = (int)blockIdx.x + (k / ra.nh) * (int)gridDim.x;
+        c0 = 128 * (pr % ncb);
+        u = pr / ncb;
+        h = k % ra.nh;
     };
+    // stage st: its A load (the pair's with one atom, else the stage's own)
+    // goes to A slot ai & 1, its E tile to E slot st & 1
+    auto a_index = [&](int st) { return share_a ? st / ra.nh : st; };
+    auto loads_a = [&](int st) { return !share_a || st % ra.nh == 0; };
+    auto frees_a = [&](int st) { return !share_a || st % ra.nh == ra.nh - 1; };
+    unsigned char *Abuf = smem, *Ebuf = smem + 2 * 4 * a_tile;
+    const uint32_t a_bytes = 4 * a_tile - (ra.a_hi_only ? 2 * a_tile : 0u);
 
     if (threadIdx.x == 0) {
         tc05::mbar_init(&dbg_bar, 1);
         tc05::mbar_init(&drain, 1);
         for (int b = 0; b < 2; ++b) {
-            tc05::mbar_init(&full[b], 1);
-            tc05::mbar_init(&empty[b], 1);
+            tc05::mbar_init(&a_full[b], 1);
+            tc05::mbar_init(&a_empty[b], 1);
+            tc05::mbar_init(&e_full[b], 1);
+            tc05::mbar_init(&e_empty[b], 1);
             tc05::mbar_init(&acc_full[b], 1);
             tc05::mbar_init(&acc_empty[b], 8);          // the eight store warps
         }
@@ -174,31 +187,50 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
     if (warp == 8) {
         // ------------------------------------------------ copies
         if (lane == 0) {
-            int issued = 0;
+            int issued = 0, a_issued = 0;
             for (int st = 0; st < nstages && !*abortp; ++st) {
-                const int b = st & 1, at = st % NA;
-                if (st >= 2 && !tc05::mbar_wait(&empty[b], (uint32_t)((st >> 1) - 1) & 1u, budget)) {
+                const int at = st % NA, k = st / NA;
+                int c0, u, h;
+                coords(k, c0, u, h);
+                if (loads_a(st)) {
+                    // the A slot is free once the products of A load ai - 2 completed
+                    const int ai = a_index(st), b = ai & 1;
+                    if (ai >= 2 &&
+                        !tc05::mbar_wait(&a_empty[b], (uint32_t)((ai >> 1) - 1) & 1u, budget)) {
+                        atomicOr(err, 4);
+                        *abortp = 1;
+                        break;
+                    }
+                    unsigned char *As = Abuf + b * 4 * a_tile;
+                    // with a BF16 spectrum only A's hi planes (0 and 2) are loaded
+                    tc05::mbar_arrive_expect_tx(&a_full[b], a_bytes);
+                    for (int p = 0; p < 4; ++p)
+                        if (!ra.a_hi_only || (p & 1) == 0)
+                            tc05::tma_load_3d(As + p * a_tile, &tmA, &a_full[b], 64 * at, c0,
+                                              4 * u + p);
+                    a_issued = ai + 1;
+                }
+                const int e = st & 1;
+                if (st >= 2 &&
+                    !tc05::mbar_wait(&e_empty[e], (uint32_t)((st >> 1) - 1) & 1u, budget)) {
                     atomicOr(err, 4);
                     *abortp = 1;
                     break;
                 }
-                int c0, u, h;
-                coords(st / NA, c0, u, h);
-                unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
-                // with a BF16 spectrum only A's hi planes (0 and 2) are loaded
-                tc05::mbar_arrive_expect_tx(&full[b], buf_bytes - (ra.a_hi_only ? 2 * a_tile : 0u));
-                for (int p = 0; p < 4; ++p) {
-                    if (!ra.a_hi_only || (p & 1) == 0)
-                        tc05::tma_load_3d(As + p * a_tile, &tmA, &full[b], 64 * at, c0, 4 * u + p);
-                    tc05::tma_load_3d(Bs + p * b_tile, &tmB, &full[b], 64 * at, h * ra.Lh,
+                unsigned char *Bs = Ebuf + e * 4 * b_tile;
+                tc05::mbar_arrive_expect_tx(&e_full[e], 4 * b_tile);
+                for (int p = 0; p < 4; ++p)
+                    tc05::tma_load_3d(Bs + p * b_tile, &tmB, &e_full[e], 64 * at, h * ra.Lh,
                                       4 * u + p);
-                }
                 issued = st + 1;
             }
-            // the last copies issued (at most one per buffer outstanding) have
+            // the last copies issued (at most one per slot outstanding) have
             // landed before shared memory is released
+            for (int ai = a_issued > 2 ? a_issued - 2 : 0; ai < a_issued; ++ai)
+                if (!tc05::mbar_wait(&a_full[ai & 1], (uint32_t)(ai >> 1) & 1u, budget))
+                    atomicOr(err, 16);
             for (int st = issued > 2 ? issued - 2 : 0; st < issued; ++st)
-                if (!tc05::mbar_wait(&full[st & 1], (uint32_t)(st >> 1) & 1u, budget))
+                if (!tc05::mbar_wait(&e_full[st & 1], (uint32_t)(st >> 1) & 1u, budget))
                     atomicOr(err, 16);
         }
         __syncwarp();
@@ -206,7 +238,8 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
         // ------------------------------------------------ products
         if (lane == 0) {
             for (int st = 0; st < nstages && !*abortp; ++st) {
-                const int b = st & 1, k = st / NA, at = st % NA;
+                const int k = st / NA, at = st % NA;
+                const int ai = a_index(st), ab = ai & 1, e = st & 1;
                 // (an item's first stage) its accumulator pair read out for item k - 2
                 if (at == 0 && k >= 2 &&
                     !tc05::mbar_wait(&acc_empty[k & 1], (uint32_t)((k >> 1) - 1) & 1u, budget)) {
@@ -215,16 +248,18 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
                     break;
                 }
                 // (test hook: the first stage waits on a barrier nothing completes)
-                const bool landed = (ra.dbg_wait && st == 0)
-                                        ? tc05::mbar_wait(&dbg_bar, 0, budget)
-                                        : tc05::mbar_wait(&full[b], (uint32_t)(st >> 1) & 1u, budget);
+                bool landed = (ra.dbg_wait && st == 0)
+                                  ? tc05::mbar_wait(&dbg_bar, 0, budget)
+                                  : tc05::mbar_wait(&e_full[e], (uint32_t)(st >> 1) & 1u, budget);
+                if (landed && loads_a(st))
+                    landed = tc05::mbar_wait(&a_full[ab], (uint32_t)(ai >> 1) & 1u, budget);
                 if (!landed) {
                     atomicOr(err, 1);
                     *abortp = 1;
                     break;
                 }
                 tc05::fence_after_sync();
-                const unsigned char *As = smem + b * buf_bytes, *Bs = As + 4 * a_tile;
+                const unsigned char *As = Abuf + ab * 4 * a_tile, *Bs = Ebuf + e * 4 * b_tile;
                 const uint32_t id = ra.idesc, idn = ra.idesc | (1u << 13);   // negate A
                 const uint32_t dre = tmem + (uint32_t)((k & 1) * 2 * ra.Lh), dim = dre + ra.Lh;
                 for (int ks = 0; ks < 4; ++ks) {
@@ -252,7 +287,8 @@ k_range_table_tc(RtTcArgs ra, const __grid_constant__ CUtensorMap tmA,
                     tc05::mma_ss(dim, da(2), db(1), id, 1u);
                     if (!ra.a_hi_only) tc05::mma_ss(dim, da(3), db(0), id, 1u);
                 }
-                tc05::mma_commit(&empty[b]);                    // the buffer may be refilled
+                tc05::mma_commit(&e_empty[e]);                  // the E slot may be refilled
+                if (frees_a(st)) tc05::mma_commit(&a_empty[ab]);   // and the A slot
                 if (at == NA - 1) tc05::mma_commit(&acc_full[k & 1]);   // the item is done
             }
             // every product issued has completed before tensor memory is released
@@ -402,8 +438,9 @@ cudaError_t launch_range_table_tc(const RtTcArgs &ra, const CUtensorMap &tmA,
     e = cudaFuncSetAttribute(k_range_table_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    const int items = (ra.C + 127) / 128 * ra.Np * ra.nh;
-    k_range_table_tc<<<min(items, ra.grid), 320, smem, st>>>(ra, tmA, tmB, (uint32_t *)prod, err);
+    // (blocks take (channel block, bin) pairs with all their row parts)
+    const int pairs = (ra.C + 127) / 128 * ra.Np;
+    k_range_table_tc<<<min(pairs, ra.grid), 320, smem, st>>>(ra, tmA, tmB, (uint32_t *)prod, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int Cp = (ra.C + 127) / 128 * 128, R = ra.nh * ra.Lh;
